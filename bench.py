@@ -1,0 +1,367 @@
+"""Benchmark: MG-preconditioned SQMR (Tao & Sifakis, Alg. 4) on the 256^3 MAC Stokes workload.
+
+One step = one full solve of a 256^3 box problem (Gaussian-bump forcing, 16 bumps, seed = step mod 5,
+eta = 1, gamma = 1e-3, no-slip walls) from x0 = 0 to true relative residual 1e-8, with inputs resident in
+HBM.  The headline runs the FP32 V-cycle with FP64 SQMR recurrences; the plain FP64 V-cycle solve of the
+same problems is timed beside it.  Under torchrun every rank solves its own problems (weak scaling, no
+collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--n 256]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a bounded sample of the same
+workload (see cpu_sample()).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solved unknowns/sec to rel. residual 1e-8 at 256^3; V-cycle HBM GB/s vs peak"
+UNIT = "unknowns/s"
+
+
+def unknowns(n):
+    return 3 * n * n * (n - 1) + n ** 3
+
+
+def packed_len(n):
+    return 3 * (n + 1) * n * n + n ** 3
+
+
+def workload_name(n):
+    return (f"{n}^3 MAC Stokes box, 16 Gaussian bumps (seeds 0-4), eta=1, gamma=1e-3, no-slip walls, "
+            f"MG(V-cycle, Alg. 3 smoother)-preconditioned SQMR from x0=0 to rel. residual 1e-8")
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_iterations(n, seed=0, tol=1e-8):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_iterations.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = [v.strip() for v in line.split(",")]
+        if int(f[0]) == n and int(f[1]) == seed and float(f[2]) == tol:
+            return int(f[3])
+    return None
+
+
+# ------------------------------------------------------------------------------------------ CPU oracle
+
+def cpu_sample(n, steps=1, warmup=0, iters=None):
+    """Time the oracle on a bounded sample of the n^3 workload.
+
+    Sample = one Alg. 3 smoothing application on the finest level of the n^3 problem (its single
+    largest piece of work).  It is scaled to a full solve by (a) the ratio between one SQMR iteration
+    (V-cycle + 2 operator applies, as the oracle runs it) and one finest-level smoothing, measured on
+    the oracle at 64^3, and (b) the oracle's iteration count for this workload
+    (tests/golden/oracle_iterations.txt, written by the oracle alone).
+    """
+    import oracle
+    import synthetic
+    o64 = oracle.Oracle(64, coarsest_max=8)
+    b64 = o64.rhs(synthetic.bumps(64, seed=0)["f"].numpy(), None)
+    z = np.zeros(o64.n())
+    t0 = time.perf_counter()
+    o64.smooth(z, b64, level=0)
+    t1 = time.perf_counter()
+    o64.vcycle(b64)
+    o64.apply(b64)
+    o64.apply(b64)
+    t2 = time.perf_counter()
+    ratio = (t2 - t1) / (t1 - t0)
+    o = oracle.Oracle(n, coarsest_max=8)
+    b = o.rhs(synthetic.bumps(n, seed=0)["f"].numpy(), None)
+    x0 = np.zeros(o.n())
+    times = []
+    for s in range(warmup + steps):
+        t0 = time.perf_counter()
+        o.smooth(x0, b, level=0)
+        dt = time.perf_counter() - t0
+        if s >= warmup:
+            times.append(dt)
+    if iters is None:
+        iters = oracle_iterations(n) or 14
+    t_smooth = float(np.mean(times))
+    t_solve = t_smooth * ratio * (iters + 1)
+    return {
+        "value": unknowns(n) / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": (f"one finest-level Alg. 3 smoothing of the {n}^3 problem ({t_smooth:.2f} s, single-threaded C "
+                   f"oracle), scaled by the oracle's iteration/smoothing cost ratio at 64^3 ({ratio:.2f}) and its "
+                   f"{iters}+1 V-cycles to 1e-8"),
+        "seconds_per_step": t_smooth, "est_solve_seconds": t_solve, "times": times,
+    }
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_sample(args.n, steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["est_solve_seconds"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.n), "n": args.n, "unknowns": unknowns(args.n), "tol": 1e-8},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows if len(r) > 8 for j in range(4) if r[5 + j] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------------------ roofline
+
+def alg_bytes(kind, n, e, launches_per_level0=1):
+    """Algorithmic bytes of ONE level-0 launch of a kernel kind on the n^3 grid.
+
+    Counted as compulsory traffic: every array the launch must read is read once, every array it
+    writes is written once (e = element size of the V-cycle, FP64 = 8 for SQMR vectors).
+    nf = face entries, np = cells, npk = nf + np (packed length)."""
+    np_ = n ** 3
+    npk = packed_len(n)
+    nf = npk - np_
+    v1 = n ** 3 - (n - 2) ** 3
+    table = {
+        "dgs_u": (3 * nf + np_) * e,              # read x faces, p, b faces; write x faces
+        "dgs_p_bwd": (2 * npk + np_ / 8) * e,     # read x and b (radius-2 stencils), write p of one colour
+        "dgs_p_fwd": (2 * nf / 4 + 3 * np_ / 4) * e,  # a colour touches 1/4 of the rows of faces and cells
+        "dgs_p_gather": 3 * np_ * e,              # read delta, read+write p
+        "residual": 3 * npk * e,                  # read x, b; write r
+        "restrict": (npk + npk / 8) * e,
+        "prolong": (2 * npk + npk / 8) * e,
+        "memset": npk * e,
+        "vanka_compute": v1 / 8 * 21 * e,         # b and x of the patch, 7 corrections written
+        "vanka_apply": v1 / 8 * 21 * e,
+        "apply_dot": 2 * npk * 8,
+        "update_s": 3 * npk * 8 + (npk * e if e == 4 else 0),
+        "dot2": npk * e + npk * 8,
+        "update_x": 9 * npk * 8 + npk * e,
+    }
+    return table.get(kind)
+
+
+def roofline(prof, n, e, peak, traffic_db, precision):
+    # dominant kernel by total time over all levels
+    kind = max(prof, key=lambda k: prof[k][0])
+    ms_all, cnt_all, ms0, cnt0 = prof[kind]
+    if cnt0 == 0:
+        return None
+    avg_ms = ms0 / cnt0
+    b = alg_bytes(kind, n, e if kind not in ("apply_dot",) else 8)
+    achieved = b / (avg_ms * 1e-3) / 1e9 if b else None
+    tr = traffic_db.get(f"{precision}:{kind}:{n}")
+    return {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": peak[0],
+            "peak_source": f"{peak[1]} hbm_gbs (MEASURED_PEAKS.json)" if peak[1] == "measured" else "fallback 6.8 TB/s",
+            "unit": "GB/s", "frac": achieved / peak[0] if achieved else None, "traffic": tr,
+            "algorithmic_bytes_per_launch": b, "avg_launch_ms": avg_ms, "launches_level0_per_iteration": cnt0,
+            "share_of_iteration": ms_all / sum(v[0] for v in prof.values())}
+
+
+# ------------------------------------------------------------------------------------------ native arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 V-cycle solve beside the headline")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_2312_10615_gb300 as smg
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    n = args.n
+    npk = packed_len(n)
+    seeds = [(rank * 1000 + s) % 5 for s in range(5)]
+    rhs = {}
+    S32 = smg.Stokes(n, precision=smg.PREC_FP32)
+    for sd in sorted(set(seeds)):
+        rhs[sd] = S32.rhs(synthetic.bumps(n, seed=sd, device=dev)["f"], None)
+    x = torch.zeros(npk, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(S, k, w, collect):
+        for s in range(w):
+            x.zero_()
+            smg.sqmr_solve(S.h, rhs[seeds[s % len(seeds)]], x, args.tol, 200)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for s in range(k):
+            x.zero_()
+            info = smg.sqmr_solve(S.h, rhs[seeds[s % len(seeds)]], x, args.tol, 200)
+            collect.append((info.iterations, info.rel_residual))
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # headline: FP32 V-cycle, FP64 SQMR
+    its32 = []
+    with ClockSampler(local) as clk:
+        ms32 = timed(S32, args.steps, args.warmup, its32)
+    assert all(r < args.tol for _, r in its32), its32
+    value = unknowns(n) * args.steps * world / (ms32 * 1e-3)
+
+    prof32 = smg.stokes_profile_iteration(S32.h)
+    launches_iter = sum(v[1] for v in prof32.values())
+    launches_vc = launches_iter - sum(prof32[k][1] for k in ("apply_dot", "update_s", "dot2", "update_x", "scalars"))
+    fixed = 16  # masks, norms, initial residual, first V-cycle bookkeeping, final mean removal and check
+    gpu_launches = sum(it * launches_iter + launches_vc + fixed for it, _ in its32)
+
+    peak = read_peaks()
+    traffic_db = {}
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        traffic_db = json.load(open(tp))
+    roof = roofline(prof32, n, 4, peak, traffic_db, "fp32")
+
+    # e2e through the C ABI with pinned host buffers: H2D of rhs and x0, D2H of x inside the timed region
+    bh = torch.empty(npk, dtype=torch.float64, pin_memory=True)
+    bh.copy_(rhs[seeds[0]].cpu())
+    xh = torch.zeros(npk, dtype=torch.float64, pin_memory=True)
+    for _ in range(max(1, args.warmup)):
+        xh.zero_()
+        smg.sqmr_solve(S32.h, bh, xh, args.tol, 200)
+    barrier()
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        xh.zero_()
+        smg.sqmr_solve(S32.h, bh, xh, args.tol, 200)
+    ev1.record(stream)
+    barrier()
+    ms_e2e = max(ev0.elapsed_time(ev1), (time.perf_counter() - t0) * 1e3)
+    e2e = {"value": unknowns(n) * args.steps * world / (ms_e2e * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * npk * 8, "d2h_bytes_per_step": npk * 8,
+           "note": "sqmr_solve with pinned host rhs/x0/x; copies inside the call"}
+
+    # the plain FP64 V-cycle beside it
+    fp64 = None
+    if not args.no_fp64:
+        S64 = smg.Stokes(n, precision=smg.PREC_FP64)
+        its64 = []
+        ms64 = timed(S64, max(1, args.steps // 2), 1, its64)
+        prof64 = smg.stokes_profile_iteration(S64.h)
+        k64 = max(prof64, key=lambda k: prof64[k][0])
+        fp64 = {"value": unknowns(n) * len(its64) * world / (ms64 * 1e-3), "unit": UNIT,
+                "ms_per_step": ms64 / len(its64), "iterations": [it for it, _ in its64],
+                "rel_residual": [r for _, r in its64], "dominant_kernel": k64,
+                "kernel_ms_per_iteration": {k: round(v[0], 4) for k, v in prof64.items()}}
+        S64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_sample(n)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 SQMR + f32 V-cycle", "data": "synthetic",
+            "config": {"workload": workload_name(n), "n": n, "unknowns": unknowns(n), "levels": S32.levels,
+                       "tol": args.tol, "vcycle_precision": "fp32", "sqmr_precision": "fp64",
+                       "l2": "inputs larger than L2 (each FP64 vector 537 MB)", "parallelism": f"replicas x{world}"},
+            "iterations": [it for it, _ in its32], "rel_residual": [r for _, r in its32],
+            "kernel_ms_per_iteration": {k: round(v[0], 4) for k, v in prof32.items()},
+            "fp64_vcycle": fp64, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": gpu_launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    S32.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

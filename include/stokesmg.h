@@ -1,0 +1,175 @@
+/*
+ * stokesmg.h -- C ABI of the GB300 (sm_103a) symmetric multigrid-preconditioned SQMR solver for
+ * the 3D staggered-grid (MAC) Stokes system of Tao & Sifakis, arXiv 2312.10615.
+ *
+ * Problem (Sec. 2, Eq. 2):  L x = b,  L = [[A, B^T], [B, 0]],  A = -eta Lap_h (7-point, per face
+ * velocity component), B^T = grad_h (face = difference of the two adjacent cell pressures / h),
+ * B = -div_h.  Domain: an nx x ny x nz box of interior cells with one Dirichlet ghost shell
+ * (Sec. 5: faces between two interior cells and all cell pressures are the unknowns; faces of
+ * Dirichlet cells carry Dirichlet data).  With all-Dirichlet walls constant pressure lies in ker L;
+ * solutions are returned with zero pressure mean.
+ *
+ * VECTOR LAYOUT ("packed", FP64, x index fastest):
+ *   [ u: (nx+1)*ny*nz | v: nx*(ny+1)*nz | w: nx*ny*(nz+1) | p: nx*ny*nz ]
+ *   u(i,j,k) at face x = i*h between cells i-1 and i, index i + (nx+1)*(j + ny*k); v, w analogous;
+ *   p(i,j,k) at the cell centre, index i + nx*(j + ny*k).  Entries that are not unknowns (the
+ *   wall-normal faces i = 0, nx of u, etc.) are ignored on input and written as 0 on output.
+ * DIRICHLET LAYOUT ("ghost-extended", FP64): [u: (nx+1)(ny+2)(nz+2) | v: (nx+2)(ny+1)(nz+2) |
+ *   w: (nx+2)(ny+2)(nz+1)], each tangential index running -1..n (stored at offset +1), the normal
+ *   index 0..n.  Only entries on faces of ghost cells are read.
+ *
+ * POINTERS: every vector argument may be a device pointer (CUDA device or managed memory of the
+ * handle's device) or a host pointer (pageable or pinned); host data is staged through
+ * handle-owned device buffers inside the call.  The caller owns all vectors; the handle owns
+ * every internal buffer (hierarchy, smoother tables, coarse inverse, CUDA graphs, scratch).
+ * STREAMS: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ * stream-ordered and asynchronous with respect to the host except where stated.
+ * ERRORS: every call returns STOKES_OK (0) or a negative code below; no call aborts the process.
+ * A handle is not thread-safe: one host thread (or external synchronisation) per handle.
+ */
+#ifndef STOKESMG_H
+#define STOKESMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STOKES_OK 0
+#define STOKES_ERR_INVALID_ARG -1   /* bad size, NULL where required, unsupported combination */
+#define STOKES_ERR_OOM -2           /* device or host allocation failed */
+#define STOKES_ERR_CUDA -3          /* a CUDA runtime call failed (context is left usable) */
+#define STOKES_ERR_BREAKDOWN -4     /* SQMR: sigma = q^T L q = 0 or rho = s^T t = 0 (Alg. 4 divides by both) */
+#define STOKES_ERR_NOT_CONVERGED -5 /* SQMR: max_iter reached before the tolerance */
+#define STOKES_ERR_NAN -6           /* a NaN/Inf appeared in the SQMR scalars */
+#define STOKES_ERR_TIMEOUT -7       /* reserved: a device-side wait ran out of its iteration limit */
+#define STOKES_ERR_UNSUPPORTED -8   /* valid request this build does not implement (e.g. exterior cells) */
+
+/* precision of the V-cycle (the SQMR recurrences, the true-residual check and the coarsest
+ * solve always run in FP64) */
+#define STOKES_PREC_FP64 0
+#define STOKES_PREC_FP32 1
+
+typedef struct stokes_s *stokes_t;
+
+typedef struct {
+    int nx, ny, nz;   /* interior cells per axis (>= 2) */
+    double h;         /* cell size (> 0); <= 0 selects 1/nx (unit-width box) */
+    int levels;       /* multigrid levels; 0 = automatic: halve while every dimension is even and
+                         one exceeds coarsest_max (Alg. 1; 128^3 -> 5 levels) */
+    int coarsest_max; /* 0 = 8 */
+} stokes_grid_t;
+
+typedef struct {
+    /* cell labels on the ghost-extended cell grid (nx+2)(ny+2)(nz+2), 0 interior, 1 Dirichlet,
+     * 2 exterior (Sec. 5).  NULL = the box (all interior, one Dirichlet ghost shell).  Only NULL
+     * is implemented; anything else returns STOKES_ERR_UNSUPPORTED. */
+    const uint8_t *cell_labels;
+} stokes_bc_t;
+
+typedef struct {
+    double gamma;  /* penalty of L~ = [[A, B^T], [B, -gamma I]] used only inside the V-cycle (Sec. 4); default 1e-3 */
+    int kb_vanka;  /* symmetric Vanka sweeps before and after the symmetric DGS in Alg. 3; default 1 */
+    int precision; /* STOKES_PREC_FP64 (default) or STOKES_PREC_FP32 V-cycle */
+    int use_graphs;/* capture the V-cycle / SQMR iteration in CUDA graphs (default 1) */
+} stokes_opts_t;
+
+typedef struct {
+    int iterations;        /* SQMR iterations performed (Alg. 4 loop index j) */
+    double rel_residual;   /* true ||b - L x||_2 / ||b||_2 of the returned x, recomputed in FP64 */
+    int status;            /* same value as the call's return code */
+    int vcycles;           /* preconditioner applications (iterations + 1) */
+} sqmr_info_t;
+
+/* Fill *opts with the defaults listed above. */
+void stokes_opts_default(stokes_opts_t *opts);
+
+/* Build the multigrid hierarchy on the current CUDA device (Sec. 5 labels and DOF classes,
+ * Alg. 1 re-discretised coarse levels, Alg. 2 diagonals, Sec. 6 pre-factorised Vanka local
+ * problems, the exact coarsest solve as a symmetrised dense FP64 inverse).  `bc` and `opts` may
+ * be NULL (box, defaults).  viscosity = eta > 0.  On success *out owns all device memory. */
+int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double viscosity, const stokes_opts_t *opts,
+                  stokes_t *out);
+
+/* Free everything the handle owns (after synchronising its work).  NULL is accepted. */
+int stokes_destroy(stokes_t h);
+
+/* Packed vector length of level `level` (0 = finest); 0 if out of range. */
+long long stokes_vector_length(stokes_t h, int level);
+/* Ghost-extended Dirichlet array length of the finest level. */
+long long stokes_ghost_length(stokes_t h);
+/* Number of multigrid levels. */
+int stokes_num_levels(stokes_t h);
+
+/* b = f on the unknowns with the Dirichlet data moved to the right-hand side (Sec. 5):
+ * velocity rows add eta/h^2 * (Dirichlet neighbour values), pressure rows add
+ * (g_high - g_low)/h over Dirichlet faces.  f: packed (the p block is the continuity source);
+ * g: ghost-extended, NULL = homogeneous.  b: packed, written completely. */
+int stokes_rhs(stokes_t h, const double *f, const double *g, double *b, void *stream);
+
+/* y = L x on the unknowns (Eq. 2); other entries of y are set to 0.  FP64. */
+int stokes_apply(stokes_t h, const double *x, double *y, void *stream);
+
+/* t = V-cycle(L~, s, 0, n) (Alg. 1 with the Alg. 3 smoother, zero initial guess, Sec. 3), the
+ * symmetric preconditioner W^dagger s of Alg. 4.  Linear and symmetric in s.  s, t packed FP64;
+ * in FP32 precision the cycle runs on FP32 copies.  s and t may not alias. */
+int mg_precondition(stokes_t h, const double *s, double *t, void *stream);
+
+/* Alg. 4: MG-preconditioned SQMR on L.  rhs: packed b; x: x0 on entry, the solution on exit
+ * (pressure mean removed).  Stops when the true relative residual ||b - Lx||/||b|| < tol
+ * (tracked by the exact recursion r_j = (1 - c_j^2) r_{j-1} + c_j^2 s_j and confirmed by an
+ * explicit FP64 b - Lx).  Synchronises the stream once per iteration (convergence flag) and
+ * fills *info (may be NULL).  Returns STOKES_ERR_NOT_CONVERGED / BREAKDOWN / NAN with x holding
+ * the last iterate. */
+int sqmr_solve(stokes_t h, const double *rhs, double *x, double tol, int max_iter, sqmr_info_t *info, void *stream);
+
+/* *out = ||b - L x||_2 (FP64, deterministic reduction); synchronises the stream.  Uses the
+ * handle's reduction scratch. */
+int stokes_residual_norm(stokes_t h, const double *b, const double *x, double *out, void *stream);
+
+/* ---- diagnostics: single pieces of the V-cycle on one level (FP64 packed vectors of that level) ----
+ * which: 0 Alg. 3 smoother, 1 symmetric DGS, 2 one symmetric Vanka sweep (colours 0..7, 7..0),
+ *        3 forward DGS (Alg. 2), 4 backward DGS (Eq. ldist), 10+c one Vanka colour c (0..7).
+ * x is updated in place with right-hand side b; level must be smoothed (< levels-1). */
+int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, void *stream);
+/* b_coarse = R r_fine (R = P^T/8, Sec. 2), level -> level+1 */
+int stokes_restrict(stokes_t h, int level, const double *r_fine, double *b_coarse, void *stream);
+/* x_fine += P e_coarse, level+1 -> level */
+int stokes_prolong_add(stokes_t h, int level, const double *e_coarse, double *x_fine, void *stream);
+/* x = L~^{-1} b on the coarsest level (Alg. 1 exact solve) */
+int stokes_coarse_solve(stokes_t h, const double *b, double *x, void *stream);
+
+/* ---- diagnostics: per-kernel timing ----
+ * Runs one SQMR iteration (Alg. 4 loop body, V-cycle included) eagerly on `stream` with a CUDA
+ * event pair around every kernel launch and returns, per kernel kind k (STOKES_K_*), the summed
+ * duration in ms and the launch count, over all levels and over level 0 only.  Arrays have nkinds
+ * >= STOKES_K_COUNT entries.  Meant to follow a sqmr_solve on the same handle (it advances the
+ * handle's SQMR state); synchronises the stream. */
+#define STOKES_K_APPLY_DOT 0
+#define STOKES_K_UPDATE_S 1
+#define STOKES_K_DOT2 2
+#define STOKES_K_UPDATE_X 3
+#define STOKES_K_SCALARS 4
+#define STOKES_K_MEMSET 5
+#define STOKES_K_VANKA_COMPUTE 6
+#define STOKES_K_VANKA_APPLY 7
+#define STOKES_K_DGS_U 8
+#define STOKES_K_DGS_P_FWD 9
+#define STOKES_K_DGS_P_GATHER 10
+#define STOKES_K_DGS_P_BWD 11
+#define STOKES_K_RESIDUAL 12
+#define STOKES_K_RESTRICT 13
+#define STOKES_K_PROLONG 14
+#define STOKES_K_COARSE 15
+#define STOKES_K_COUNT 16
+int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launches_all, double *ms_level0,
+                             int *launches_level0, void *stream);
+
+/* Human-readable message for a status code (static storage). */
+const char *stokes_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STOKESMG_H */

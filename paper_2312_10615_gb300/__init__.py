@@ -1,0 +1,271 @@
+"""Python binding of libstokesmg -- the GB300 symmetric multigrid-preconditioned SQMR solver for the
+3D MAC Stokes system (Tao & Sifakis, arXiv 2312.10615).
+
+Argument marshalling only: every numerical step runs in the library's CUDA kernels.  Functions carry
+the C-ABI names of ``include/stokesmg.h``; vectors may be torch tensors (CUDA or CPU, float64,
+contiguous) or numpy float64 arrays.  ``Stokes`` wraps a handle for convenience.
+
+If the native library is missing, the first call raises ImportError: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstokesmg.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_UNSUPPORTED = \
+    -1, -2, -3, -4, -5, -6, -7, -8
+PREC_FP64, PREC_FP32 = 0, 1
+
+# every entry point declared in include/stokesmg.h
+EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vector_length", "stokes_ghost_length",
+           "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
+           "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
+           "stokes_profile_iteration", "stokes_strerror"]
+
+# kernel kinds reported by stokes_profile_iteration (STOKES_K_* in the header)
+KERNEL_KINDS = ["apply_dot", "update_s", "dot2", "update_x", "scalars", "memset", "vanka_compute", "vanka_apply",
+                "dgs_u", "dgs_p_fwd", "dgs_p_gather", "dgs_p_bwd", "residual", "restrict", "prolong", "coarse"]
+
+
+class stokes_grid_t(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+                ("levels", ctypes.c_int), ("coarsest_max", ctypes.c_int)]
+
+
+class stokes_bc_t(ctypes.Structure):
+    _fields_ = [("cell_labels", ctypes.POINTER(ctypes.c_uint8))]
+
+
+class stokes_opts_t(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("kb_vanka", ctypes.c_int), ("precision", ctypes.c_int),
+                ("use_graphs", ctypes.c_int)]
+
+
+class sqmr_info_t(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("status", ctypes.c_int),
+                ("vcycles", ctypes.c_int)]
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {stokes_strerror(code)} ({code})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libstokesmg.so not built ({LIB_PATH}); run paper_2312_10615_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, d, i, ll = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+    sig = {
+        "stokes_opts_default": (None, [ctypes.POINTER(stokes_opts_t)]),
+        "stokes_create": (i, [ctypes.POINTER(stokes_grid_t), ctypes.POINTER(stokes_bc_t), d,
+                              ctypes.POINTER(stokes_opts_t), ctypes.POINTER(vp)]),
+        "stokes_destroy": (i, [vp]),
+        "stokes_vector_length": (ll, [vp, i]),
+        "stokes_ghost_length": (ll, [vp]),
+        "stokes_num_levels": (i, [vp]),
+        "stokes_rhs": (i, [vp, vp, vp, vp, vp]),
+        "stokes_apply": (i, [vp, vp, vp, vp]),
+        "mg_precondition": (i, [vp, vp, vp, vp]),
+        "sqmr_solve": (i, [vp, vp, vp, d, i, ctypes.POINTER(sqmr_info_t), vp]),
+        "stokes_residual_norm": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
+        "stokes_smooth": (i, [vp, i, i, vp, vp, vp]),
+        "stokes_restrict": (i, [vp, i, vp, vp, vp]),
+        "stokes_prolong_add": (i, [vp, i, vp, vp, vp]),
+        "stokes_coarse_solve": (i, [vp, vp, vp, vp]),
+        "stokes_profile_iteration": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d),
+                                         ctypes.POINTER(i), vp]),
+        "stokes_strerror": (ctypes.c_char_p, [i]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    """The loaded native library (loaded on first use; ImportError if it was never built)."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def stokes_strerror(code):
+    return lib().stokes_strerror(int(code)).decode()
+
+
+def _ptr(a):
+    """Raw pointer of a float64 contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy vectors must be float64 and C-contiguous")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("torch vectors must be float64 and contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported vector type {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise StokesError(rc, where)
+
+
+def stokes_opts_default():
+    o = stokes_opts_t()
+    lib().stokes_opts_default(ctypes.byref(o))
+    return o
+
+
+def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest_max=8, gamma=1e-3, kb_vanka=1,
+                  precision=PREC_FP64, use_graphs=True):
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    g = stokes_grid_t(nx, ny, nz, h, levels, coarsest_max)
+    o = stokes_opts_t(gamma, kb_vanka, precision, int(bool(use_graphs)))
+    hdl = ctypes.c_void_p()
+    _check(lib().stokes_create(ctypes.byref(g), None, viscosity, ctypes.byref(o), ctypes.byref(hdl)), "stokes_create")
+    return hdl
+
+
+def stokes_destroy(h):
+    _check(lib().stokes_destroy(h), "stokes_destroy")
+
+
+def stokes_vector_length(h, level=0):
+    return int(lib().stokes_vector_length(h, level))
+
+
+def stokes_ghost_length(h):
+    return int(lib().stokes_ghost_length(h))
+
+
+def stokes_num_levels(h):
+    return int(lib().stokes_num_levels(h))
+
+
+def stokes_rhs(h, f, g, b, stream=None):
+    _check(lib().stokes_rhs(h, _ptr(f), _ptr(g), _ptr(b), _stream(stream)), "stokes_rhs")
+
+
+def stokes_apply(h, x, y, stream=None):
+    _check(lib().stokes_apply(h, _ptr(x), _ptr(y), _stream(stream)), "stokes_apply")
+
+
+def mg_precondition(h, s, t, stream=None):
+    _check(lib().mg_precondition(h, _ptr(s), _ptr(t), _stream(stream)), "mg_precondition")
+
+
+def sqmr_solve(h, rhs, x, tol=1e-8, max_iter=200, stream=None, check=True):
+    info = sqmr_info_t()
+    rc = lib().sqmr_solve(h, _ptr(rhs), _ptr(x), tol, max_iter, ctypes.byref(info), _stream(stream))
+    if check:
+        _check(rc, "sqmr_solve")
+    return info
+
+
+def stokes_residual_norm(h, b, x, stream=None):
+    out = ctypes.c_double()
+    _check(lib().stokes_residual_norm(h, _ptr(b), _ptr(x), ctypes.byref(out), _stream(stream)), "stokes_residual_norm")
+    return out.value
+
+
+def stokes_smooth(h, level, which, x, b, stream=None):
+    _check(lib().stokes_smooth(h, level, which, _ptr(x), _ptr(b), _stream(stream)), "stokes_smooth")
+
+
+def stokes_restrict(h, level, r_fine, b_coarse, stream=None):
+    _check(lib().stokes_restrict(h, level, _ptr(r_fine), _ptr(b_coarse), _stream(stream)), "stokes_restrict")
+
+
+def stokes_prolong_add(h, level, e_coarse, x_fine, stream=None):
+    _check(lib().stokes_prolong_add(h, level, _ptr(e_coarse), _ptr(x_fine), _stream(stream)), "stokes_prolong_add")
+
+
+def stokes_coarse_solve(h, b, x, stream=None):
+    _check(lib().stokes_coarse_solve(h, _ptr(b), _ptr(x), _stream(stream)), "stokes_coarse_solve")
+
+
+def stokes_profile_iteration(h, stream=None):
+    """Per kernel kind: (ms all levels, launches all levels, ms level 0, launches level 0)."""
+    k = len(KERNEL_KINDS)
+    ma, ca, m0, c0 = (ctypes.c_double * k)(), (ctypes.c_int * k)(), (ctypes.c_double * k)(), (ctypes.c_int * k)()
+    _check(lib().stokes_profile_iteration(h, k, ma, ca, m0, c0, _stream(stream)), "stokes_profile_iteration")
+    return {name: (ma[j], ca[j], m0[j], c0[j]) for j, name in enumerate(KERNEL_KINDS)}
+
+
+class Stokes:
+    """Owning wrapper of a solver handle (one box problem on the current CUDA device)."""
+
+    def __init__(self, nx, ny=None, nz=None, viscosity=1.0, **kw):
+        self.h = stokes_create(nx, ny, nz, viscosity, **kw)
+        self.dims = (nx, nx if ny is None else ny, nx if nz is None else nz)
+        self.n = stokes_vector_length(self.h)
+        self.levels = stokes_num_levels(self.h)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            stokes_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def length(self, level=0):
+        return stokes_vector_length(self.h, level)
+
+    def rhs(self, f, g=None, out=None):
+        import torch
+        out = torch.empty(self.n, dtype=torch.float64, device="cuda") if out is None else out
+        stokes_rhs(self.h, f, g, out)
+        return out
+
+    def apply(self, x, out=None):
+        import torch
+        out = torch.empty_like(x) if out is None else out
+        stokes_apply(self.h, x, out)
+        return out
+
+    def precondition(self, s, out=None):
+        import torch
+        out = torch.empty_like(s) if out is None else out
+        mg_precondition(self.h, s, out)
+        return out
+
+    def solve(self, b, x0=None, tol=1e-8, max_iter=200, check=True):
+        import torch
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        info = sqmr_solve(self.h, b, x, tol, max_iter, check=check)
+        return x, info
+
+    def residual_norm(self, b, x):
+        return stokes_residual_norm(self.h, b, x)

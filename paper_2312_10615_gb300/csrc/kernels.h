@@ -1,0 +1,71 @@
+// kernels.h -- host-side launchers of the CUDA kernels (definitions in kernels_level.cu and
+// kernels_sqmr.cu).  T is the V-cycle precision (float or double); SQMR kernels are FP64.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "stokes_internal.cuh"
+
+namespace smg {
+
+// ---- per-level operators (kernels_level.cu) ----
+// y = L~x (gamma_on) or Lx on the unknowns, 0 elsewhere; if b != nullptr: y = b - (L~x)
+template <class T> void launch_apply(const Lev &L, const T *x, const T *b, T *y, double gam, cudaStream_t s);
+// b = f + Dirichlet folding (finest level, FP64)
+void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaStream_t s);
+// symmetric DGS pieces (Alg. 2 / Eq. ldist) on the V2 set
+template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s);
+template <class T> void launch_dgs_p_fwd(const Lev &L, T *x, const T *b, T *delta, int colour, cudaStream_t s);
+template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s);
+template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *b, int colour, cudaStream_t s);
+// one colour of the multiplicative Vanka sweep on V1 (compute corrections, then add them)
+template <class T>
+void launch_vanka_compute(const Lev &L, const T *x, const T *b, const int *cells, int ncell, const T *kinv, T *corr,
+                          int cap, cudaStream_t s);
+template <class T>
+void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s);
+// transfers (Sec. 2): bc = R rf,  xf += P ec
+template <class T> void launch_restrict(const Lev &F, const Lev &C, const T *rf, T *bc, cudaStream_t s);
+template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s);
+// coarsest level: x = Kinv b over the compact unknown list (FP64 matrix)
+template <class T>
+void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, const T *b, T *x, cudaStream_t s);
+// set every entry that is not an unknown to 0
+void launch_mask(const Lev &L, double *x, cudaStream_t s);
+// precision conversion of a packed vector
+template <class A, class B> void launch_convert(long long n, const A *in, B *out, cudaStream_t s);
+
+// ---- SQMR (kernels_sqmr.cu), all FP64 except the preconditioned vector t of type T ----
+struct SqmrState {
+    double rho, sigma, alpha, tau, nu, nu_prev, c2, coefA, coefB, beta, rho_new;
+    double tt, st, rr, bb, pmean;
+    int breakdown, nonfinite, iter, pad;
+};
+
+constexpr int kRedBlocks = 1184;  // 152 SMs x 8 resident 256-thread blocks: grid of every reduction kernel
+constexpr int kRedParts = 3;      // partial sums per block
+
+// w = L q (FP64, gamma = 0) with per-block partials of q.w ; unknowns only
+void launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s);
+// w = b - L x with partials of |w|^2
+void launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s);
+// partials of a.a (and optionally a.b)
+template <class T> void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s);
+// scalar stages on one thread block: 0 alpha (after q.Lq), 1 nu/c/tau/beta (after |t|^2, s.t),
+// 2 residual norm (after |r|^2), 3 init (after |t|^2, s.t of the first V-cycle), 4 |b|^2, 5 pressure mean
+void launch_scalars(int stage, const double *partials, SqmrState *st, double *host_out, cudaStream_t s);
+void launch_scalars_aux(int stage, const double *partials, SqmrState *st, double *host_out, double aux,
+                        cudaStream_t s);
+// s -= alpha w ; optionally b32 = (T) s for a lower-precision V-cycle
+template <class T>
+void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream);
+// d = coefA d + coefB q ; x += d ; r = (1-c2) r + c2 s ; q = t + beta q ; partials of |r|^2
+template <class T>
+void launch_update_x(long long n, double *x, double *d, double *q, const T *t, double *r, const double *sv,
+                     const SqmrState *st, double *partials, cudaStream_t s);
+// q = t (widening), d = 0
+template <class T> void launch_init_q(long long n, const T *t, double *q, double *d, cudaStream_t s);
+// partial sum of the pressure block (for the mean) and subtraction of st->pmean
+void launch_psum(const Lev &L, const double *x, double *partials, cudaStream_t s);
+void launch_psub(const Lev &L, double *x, const SqmrState *st, cudaStream_t s);
+
+}  // namespace smg

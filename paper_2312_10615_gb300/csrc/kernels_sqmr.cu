@@ -1,0 +1,272 @@
+// kernels_sqmr.cu -- FP64 kernels of MG-preconditioned SQMR (Tao & Sifakis, Alg. 4):
+// operator apply fused with q^T L q, fused vector recurrences, deterministic dot products
+// (fixed grid, warp shuffles, fixed-order final sum) and the scalar recurrences on the device,
+// so an iteration needs no host round trip except the convergence flag.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace smg {
+
+namespace {
+constexpr int kBlock = 256;
+
+// sum NV values over the block (warp shuffles, then warp 0 over the per-warp sums) and store
+// them as partials[blockIdx.x * kRedParts + m]; fixed order, so the result is reproducible
+template <int NV> __device__ __forceinline__ void block_store(double (&v)[NV], double *partials) {
+    __shared__ double sh[NV][kBlock / 32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+        if (lane == 0) sh[m][warp] = v[m];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            double s = lane < kBlock / 32 ? sh[m][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) partials[blockIdx.x * kRedParts + m] = s;
+        }
+    }
+}
+
+__device__ __forceinline__ int comp_of(const Lev &L, long long q) {
+    return q < L.off[1] ? 0 : (q < L.off[2] ? 1 : (q < L.off[3] ? 2 : 3));
+}
+
+// (L x)_q on the unknown set (0 elsewhere), gamma = 0
+__device__ __forceinline__ double lx_at(const Lev &L, const double *__restrict__ x, long long q, const Coef<double> &K,
+                                        bool &act) {
+    int c = comp_of(L, q);
+    int i, j, k;
+    decode3(q - L.off[c], ext(L, c, 0), ext(L, c, 1), i, j, k);
+    act = active(L, c, i, j, k);
+    if (!act) return 0.0;
+    return c < 3 ? face_Lx(x, L, c, i, j, k, K) : cell_Lx(x, L, i, j, k, K);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_apply_dot(Lev L, const double *__restrict__ q, double *__restrict__ w,
+                                                   double *partials, Coef<double> K) {
+    double v[1] = {0.0};
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < L.n; t += (long long)gridDim.x * blockDim.x) {
+        bool act;
+        double y = lx_at(L, q, t, K, act);
+        w[t] = y;
+        if (act) v[0] += q[t] * y;
+    }
+    block_store<1>(v, partials);
+}
+
+__global__ void __launch_bounds__(256) k_residual_dot(Lev L, const double *__restrict__ b, const double *__restrict__ x,
+                                                      double *__restrict__ w, double *partials, Coef<double> K) {
+    double v[1] = {0.0};
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < L.n; t += (long long)gridDim.x * blockDim.x) {
+        bool act;
+        double y = lx_at(L, x, t, K, act);
+        double r = act ? b[t] - y : 0.0;
+        if (w) w[t] = r;
+        v[0] += r * r;
+    }
+    block_store<1>(v, partials);
+}
+
+void launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s) {
+    k_apply_dot<<<kRedBlocks, kBlock, 0, s>>>(L, q, w, partials, coef<double>(L, 0.0));
+}
+void launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s) {
+    k_residual_dot<<<kRedBlocks, kBlock, 0, s>>>(L, b, x, w, partials, coef<double>(L, 0.0));
+}
+
+// a.a and a.b
+template <class T>
+__global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__ a, const double *__restrict__ b,
+                                              double *partials) {
+    double v[2] = {0.0, 0.0};
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        double x = (double)a[t];
+        v[0] += x * x;
+        if (b) v[1] += x * b[t];
+    }
+    block_store<2>(v, partials);
+}
+template <class T> void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s) {
+    k_dot2<T><<<kRedBlocks, kBlock, 0, s>>>(n, a, b, partials);
+}
+
+// scalar recurrences of Alg. 4 (one block; fixed-order sum of the kRedBlocks partials)
+__global__ void __launch_bounds__(256) k_scalars(int stage, const double *partials, SqmrState *st, double *host_out,
+                                                 double aux) {
+    __shared__ double sh[kRedParts][kBlock];
+    double v[kRedParts] = {0.0, 0.0, 0.0};
+    for (int t = threadIdx.x; t < kRedBlocks; t += blockDim.x)
+#pragma unroll
+        for (int m = 0; m < kRedParts; ++m) v[m] += partials[t * kRedParts + m];
+#pragma unroll
+    for (int m = 0; m < kRedParts; ++m) sh[m][threadIdx.x] = v[m];
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int m = 0; m < kRedParts; ++m) sh[m][threadIdx.x] += sh[m][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double p0 = sh[0][0], p1 = sh[1][0];
+    switch (stage) {
+    case 0: {  // sigma = q^T L q, alpha = rho / sigma
+        st->sigma = p0;
+        if (!isfinite(p0)) st->nonfinite = 1;
+        if (p0 == 0.0 || st->rho == 0.0) st->breakdown = 1;
+        st->alpha = (p0 != 0.0) ? st->rho / p0 : 0.0;
+        break;
+    }
+    case 1: {  // nu_j, c_j, tau_j, rho_j, beta_j and the coefficients of d_j
+        st->tt = p0;
+        st->st = p1;
+        double nu = sqrt(p0) / st->tau;
+        double c2 = 1.0 / (1.0 + nu * nu);
+        st->nu = nu;
+        st->c2 = c2;
+        st->tau = st->tau * nu * sqrt(c2);
+        st->coefA = c2 * st->nu_prev * st->nu_prev;
+        st->coefB = c2 * st->alpha;
+        st->rho_new = p1;
+        st->beta = (st->rho != 0.0) ? p1 / st->rho : 0.0;
+        if (!isfinite(nu) || !isfinite(p1)) st->nonfinite = 1;
+        break;
+    }
+    case 2: {  // |r_j|^2 of the recursive true residual; advance the iteration
+        st->rr = p0;
+        st->rho = st->rho_new;
+        st->nu_prev = st->nu;
+        st->iter += 1;
+        if (!isfinite(p0)) st->nonfinite = 1;
+        host_out[0] = p0;
+        host_out[1] = (double)(st->breakdown | (st->nonfinite << 1));
+        break;
+    }
+    case 3: {  // initial tau_0 = |t_0|, rho_0 = s_0^T t_0, nu_0 = 0
+        st->tt = p0;
+        st->tau = sqrt(p0);
+        st->rho = p1;
+        st->nu_prev = 0.0;
+        st->iter = 0;
+        st->breakdown = 0;
+        st->nonfinite = (!isfinite(p0) || !isfinite(p1)) ? 1 : 0;
+        host_out[0] = p0;
+        host_out[1] = p1;
+        break;
+    }
+    case 4: {  // a plain sum (norms) to the host
+        host_out[0] = p0;
+        host_out[1] = p1;
+        break;
+    }
+    case 5: {  // pressure mean (aux = number of pressures)
+        st->pmean = p0 / aux;
+        break;
+    }
+    }
+}
+
+void launch_scalars(int stage, const double *partials, SqmrState *st, double *host_out, cudaStream_t s) {
+    k_scalars<<<1, kBlock, 0, s>>>(stage, partials, st, host_out, 0.0);
+}
+void launch_scalars_aux(int stage, const double *partials, SqmrState *st, double *host_out, double aux,
+                        cudaStream_t s) {
+    k_scalars<<<1, kBlock, 0, s>>>(stage, partials, st, host_out, aux);
+}
+
+// s_j = s_{j-1} - alpha t  (t = L q_{j-1}); optional narrowed copy for the V-cycle
+template <class T>
+__global__ void __launch_bounds__(256) k_update_s(long long n, double *__restrict__ s, const double *__restrict__ w,
+                                                  const SqmrState *__restrict__ st, T *__restrict__ bT) {
+    double alpha = st->alpha;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        double v = s[t] - alpha * w[t];
+        s[t] = v;
+        if (bT) bT[t] = (T)v;
+    }
+}
+template <class T>
+void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream) {
+    k_update_s<T><<<kRedBlocks, kBlock, 0, stream>>>(n, s, w, st, bT);
+}
+
+// d_j = c^2 nu_{j-1}^2 d_{j-1} + c^2 alpha q_{j-1};  x_j = x_{j-1} + d_j;
+// r_j = (1 - c^2) r_{j-1} + c^2 s_j  (true residual of the QMR-smoothed iterate);
+// q_j = t + beta q_{j-1};  partial |r_j|^2
+template <class T>
+__global__ void __launch_bounds__(256) k_update_x(long long n, double *__restrict__ x, double *__restrict__ d,
+                                                  double *__restrict__ q, const T *__restrict__ tv,
+                                                  double *__restrict__ r, const double *__restrict__ sv,
+                                                  const SqmrState *__restrict__ st, double *partials) {
+    double A = st->coefA, B = st->coefB, c2 = st->c2, beta = st->beta;
+    double v[1] = {0.0};
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        double qo = q[t];
+        double dn = A * d[t] + B * qo;
+        d[t] = dn;
+        x[t] += dn;
+        double rn = (1.0 - c2) * r[t] + c2 * sv[t];
+        r[t] = rn;
+        q[t] = (double)tv[t] + beta * qo;
+        v[0] += rn * rn;
+    }
+    block_store<1>(v, partials);
+}
+template <class T>
+void launch_update_x(long long n, double *x, double *d, double *q, const T *t, double *r, const double *sv,
+                     const SqmrState *st, double *partials, cudaStream_t s) {
+    k_update_x<T><<<kRedBlocks, kBlock, 0, s>>>(n, x, d, q, t, r, sv, st, partials);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_init_q(long long n, const T *__restrict__ tv, double *__restrict__ q,
+                                                double *__restrict__ d) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        q[t] = (double)tv[t];
+        d[t] = 0.0;
+    }
+}
+template <class T> void launch_init_q(long long n, const T *t, double *q, double *d, cudaStream_t s) {
+    k_init_q<T><<<kRedBlocks, kBlock, 0, s>>>(n, t, q, d);
+}
+
+__global__ void __launch_bounds__(256) k_psum(Lev L, const double *__restrict__ x, double *partials) {
+    double v[1] = {0.0};
+    long long np = L.n - L.off[3];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
+        v[0] += x[L.off[3] + t];
+    block_store<1>(v, partials);
+}
+__global__ void __launch_bounds__(256) k_psub(Lev L, double *__restrict__ x, const SqmrState *__restrict__ st) {
+    double m = st->pmean;
+    long long np = L.n - L.off[3];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
+        x[L.off[3] + t] -= m;
+}
+void launch_psum(const Lev &L, const double *x, double *partials, cudaStream_t s) {
+    k_psum<<<kRedBlocks, kBlock, 0, s>>>(L, x, partials);
+}
+void launch_psub(const Lev &L, double *x, const SqmrState *st, cudaStream_t s) {
+    k_psub<<<kRedBlocks, kBlock, 0, s>>>(L, x, st);
+}
+
+template void launch_dot2<float>(long long, const float *, const double *, double *, cudaStream_t);
+template void launch_dot2<double>(long long, const double *, const double *, double *, cudaStream_t);
+template void launch_update_s<float>(long long, double *, const double *, const SqmrState *, float *, cudaStream_t);
+template void launch_update_s<double>(long long, double *, const double *, const SqmrState *, double *, cudaStream_t);
+template void launch_update_x<float>(long long, double *, double *, double *, const float *, double *,
+                                     const double *, const SqmrState *, double *, cudaStream_t);
+template void launch_update_x<double>(long long, double *, double *, double *, const double *, double *,
+                                      const double *, const SqmrState *, double *, cudaStream_t);
+template void launch_init_q<float>(long long, const float *, double *, double *, cudaStream_t);
+template void launch_init_q<double>(long long, const double *, double *, double *, cudaStream_t);
+
+}  // namespace smg

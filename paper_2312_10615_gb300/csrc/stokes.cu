@@ -1,0 +1,907 @@
+// stokes.cu -- host orchestration and C ABI of the GB300 symmetric multigrid-preconditioned SQMR
+// solver for the MAC Stokes system (Tao & Sifakis, arXiv 2312.10615).
+//
+//   stokes_create ...... Sec. 5 DOF classes, Alg. 1 re-discretised hierarchy, Sec. 6 Vanka tables,
+//                        exact coarsest solve (symmetrised dense FP64 inverse)
+//   mg_precondition .... Alg. 1 V-cycle with the Alg. 3 smoother, zero initial guess (Sec. 3)
+//   sqmr_solve ......... Alg. 4
+// Every numerical step runs in the CUDA kernels of kernels_level.cu / kernels_sqmr.cu; this file
+// only schedules them, captures them in CUDA graphs and moves data across the C ABI.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "kernels.h"
+#include "setup_host.h"
+#include "stokesmg.h"
+
+using namespace smg;
+
+namespace {
+
+struct LevelBuf {
+    Lev L;
+    void *x = nullptr, *b = nullptr, *r = nullptr, *delta = nullptr, *kinv = nullptr, *corr = nullptr;
+    int *vcells[8] = {};
+    int vcount[8] = {};
+    int vcap = 0;
+};
+
+int cuda_status(cudaError_t e) {
+    cudaGetLastError();  // clear a non-sticky error so the context stays usable
+    return e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA;
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_status(e_);    \
+    } while (0)
+
+#define CKLAUNCH()                                        \
+    do {                                                  \
+        cudaError_t e_ = cudaGetLastError();              \
+        if (e_ != cudaSuccess) return cuda_status(e_);    \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else if (prev == dev) prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+Lev make_level(int nx, int ny, int nz, double h, double eta, double gamma) {
+    Lev L;
+    L.nx = nx; L.ny = ny; L.nz = nz;
+    long long nu = (long long)(nx + 1) * ny * nz, nv = (long long)nx * (ny + 1) * nz, nw = (long long)nx * ny * (nz + 1);
+    L.off[0] = 0; L.off[1] = nu; L.off[2] = nu + nv; L.off[3] = nu + nv + nw;
+    L.n = L.off[3] + (long long)nx * ny * nz;
+    L.h = h; L.eta = eta; L.gamma = gamma;
+    return L;
+}
+
+// process-wide cache of coarsest-level inverses (set-up cost grows as n^3)
+std::mutex g_cache_mu;
+std::map<std::tuple<int, int, int, double, double, double>, std::shared_ptr<std::vector<double>>> g_coarse_cache;
+
+// dense L~ on the unknowns of level C (written from the stencil of Eq. 2 / Sec. 4), inverted
+// and symmetrised: K^{-1} <- (K^{-1} + K^{-T}) / 2
+int coarse_inverse(const Lev &C, std::vector<int> &cidx, std::shared_ptr<std::vector<double>> &out) {
+    std::vector<long long> comp(C.n, -1);
+    cidx.clear();
+    for (int c = 0; c < 4; ++c)
+        for (int k = 0; k < ext(C, c, 2); ++k)
+            for (int j = 0; j < ext(C, c, 1); ++j)
+                for (int i = 0; i < ext(C, c, 0); ++i)
+                    if (active(C, c, i, j, k)) {
+                        long long q = pidx(C, c, i, j, k);
+                        comp[q] = (long long)cidx.size();
+                        cidx.push_back((int)q);
+                    }
+    int nc = (int)cidx.size();
+    auto key = std::make_tuple(C.nx * 1000003 + C.ny, C.nz, nc, C.h, C.eta, C.gamma);
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_coarse_cache.find(key);
+        if (it != g_coarse_cache.end()) { out = it->second; return 0; }
+    }
+    auto K = std::make_shared<std::vector<double>>((size_t)nc * nc, 0.0);
+    double e2 = C.eta / (C.h * C.h), ih = 1.0 / C.h;
+    auto put = [&](long long r, int c, int i, int j, int k, double v) {
+        if (!active(C, c, i, j, k)) return;
+        (*K)[(size_t)comp[r] * nc + comp[pidx(C, c, i, j, k)]] += v;
+    };
+    for (int a = 0; a < nc; ++a) {
+        long long q = cidx[a];
+        int c = q < C.off[1] ? 0 : (q < C.off[2] ? 1 : (q < C.off[3] ? 2 : 3));
+        long long t = q - C.off[c];
+        int i = (int)(t % ext(C, c, 0)), j = (int)((t / ext(C, c, 0)) % ext(C, c, 1)),
+            k = (int)(t / ((long long)ext(C, c, 0) * ext(C, c, 1)));
+        if (c < 3) {
+            put(q, c, i, j, k, 6.0 * e2);
+            put(q, c, i - 1, j, k, -e2); put(q, c, i + 1, j, k, -e2);
+            put(q, c, i, j - 1, k, -e2); put(q, c, i, j + 1, k, -e2);
+            put(q, c, i, j, k - 1, -e2); put(q, c, i, j, k + 1, -e2);
+            put(q, 3, i, j, k, ih);
+            put(q, 3, i - (c == 0), j - (c == 1), k - (c == 2), -ih);
+        } else {
+            put(q, 0, i + 1, j, k, -ih); put(q, 0, i, j, k, ih);
+            put(q, 1, i, j + 1, k, -ih); put(q, 1, i, j, k, ih);
+            put(q, 2, i, j, k + 1, -ih); put(q, 2, i, j, k, ih);
+            put(q, 3, i, j, k, -C.gamma);
+        }
+    }
+    if (dense_inverse(nc, K->data())) return STOKES_ERR_INVALID_ARG;
+    std::vector<double> &A = *K;
+    for (int r = 0; r < nc; ++r)
+        for (int c = r + 1; c < nc; ++c) {
+            double v = 0.5 * (A[(size_t)r * nc + c] + A[(size_t)c * nc + r]);
+            A[(size_t)r * nc + c] = v;
+            A[(size_t)c * nc + r] = v;
+        }
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        g_coarse_cache[key] = K;
+    }
+    out = K;
+    return 0;
+}
+
+}  // namespace
+
+struct stokes_s {
+    int dev = 0;
+    int prec = STOKES_PREC_FP64;
+    int kb = 1;
+    int use_graphs = 1;
+    double eta = 1.0, gamma = 1e-3;
+    std::vector<LevelBuf> lev;
+    int nc = 0;
+    int *cidx = nullptr;
+    double *ckinv = nullptr;
+    // FP64 vectors of the finest level used by SQMR (s aliases lev[0].b in FP64 precision)
+    double *x = nullptr, *s = nullptr, *q = nullptr, *d = nullptr, *r = nullptr, *w = nullptr, *bvec = nullptr;
+    double *stage_in = nullptr, *stage_out = nullptr;
+    double *partials = nullptr;
+    SqmrState *st = nullptr;
+    double *hout = nullptr;  // mapped pinned host memory written by the scalar kernel
+    cudaStream_t cs = nullptr;
+    cudaGraphExec_t g_vcycle = nullptr, g_iter = nullptr;
+    std::vector<void *> allocs;
+
+    ~stokes_s() {
+        if (g_vcycle) cudaGraphExecDestroy(g_vcycle);
+        if (g_iter) cudaGraphExecDestroy(g_iter);
+        for (void *p : allocs) cudaFree(p);
+        if (hout) cudaFreeHost(hout);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    template <class P> int alloc(P **p, size_t bytes) {
+        void *v = nullptr;
+        cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+        if (e != cudaSuccess) return cuda_status(e);
+        allocs.push_back(v);
+        e = cudaMemset(v, 0, bytes ? bytes : 16);
+        if (e != cudaSuccess) return cuda_status(e);
+        *p = (P *)v;
+        return 0;
+    }
+    long long n0() const { return lev[0].L.n; }
+    int nlev() const { return (int)lev.size(); }
+};
+
+namespace {
+
+// ---- optional per-launch timing (stokes_profile_iteration): an event pair around every launch ----
+struct Prof {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind, level;
+};
+thread_local Prof *g_prof = nullptr;
+template <class F> inline void prof(int kind, int level, cudaStream_t s, F f) {
+    if (!g_prof || 2 * g_prof->kind.size() + 1 >= g_prof->ev.size()) {
+        f();
+        return;
+    }
+    size_t i = g_prof->kind.size();
+    g_prof->kind.push_back(kind);
+    g_prof->level.push_back(level);
+    cudaEventRecord(g_prof->ev[2 * i], s);
+    f();
+    cudaEventRecord(g_prof->ev[2 * i + 1], s);
+}
+
+// ---- the V-cycle schedule (Alg. 1 with the Alg. 3 smoother) ----
+template <class T> void vanka_colour(stokes_s *h, int l, int col, cudaStream_t s) {
+    LevelBuf &B = h->lev[l];
+    if (B.vcount[col] == 0) return;
+    prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
+        launch_vanka_compute<T>(B.L, (const T *)B.x, (const T *)B.b, B.vcells[col], B.vcount[col],
+                                (const T *)B.kinv, (T *)B.corr, B.vcap, s);
+    });
+    prof(STOKES_K_VANKA_APPLY, l, s,
+         [&] { launch_vanka_apply<T>(B.L, (T *)B.x, B.vcells[col], B.vcount[col], (const T *)B.corr, B.vcap, s); });
+}
+template <class T> void vanka_sym(stokes_s *h, int l, cudaStream_t s) {
+    for (int c = 0; c < 8; ++c) vanka_colour<T>(h, l, c, s);
+    for (int c = 7; c >= 0; --c) vanka_colour<T>(h, l, c, s);
+}
+template <class T> void dgs_forward(stokes_s *h, int l, cudaStream_t s) {
+    LevelBuf &B = h->lev[l];
+    T *x = (T *)B.x;
+    const T *b = (const T *)B.b;
+    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 0, s); });
+    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 1, s); });
+    for (int c = 0; c < 8; ++c)
+        prof(STOKES_K_DGS_P_FWD, l, s, [&] { launch_dgs_p_fwd<T>(B.L, x, b, (T *)B.delta, c, s); });
+    prof(STOKES_K_DGS_P_GATHER, l, s, [&] { launch_dgs_p_gather<T>(B.L, x, (const T *)B.delta, s); });
+}
+template <class T> void dgs_backward(stokes_s *h, int l, cudaStream_t s) {
+    LevelBuf &B = h->lev[l];
+    T *x = (T *)B.x;
+    const T *b = (const T *)B.b;
+    for (int c = 7; c >= 0; --c) prof(STOKES_K_DGS_P_BWD, l, s, [&] { launch_dgs_p_bwd<T>(B.L, x, b, c, s); });
+    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 1, s); });
+    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 0, s); });
+}
+template <class T> void smooth(stokes_s *h, int l, cudaStream_t s) {
+    for (int k = 0; k < h->kb; ++k) vanka_sym<T>(h, l, s);
+    dgs_forward<T>(h, l, s);
+    dgs_backward<T>(h, l, s);
+    for (int k = 0; k < h->kb; ++k) vanka_sym<T>(h, l, s);
+}
+template <class T> void vcycle(stokes_s *h, cudaStream_t s) {
+    int n = h->nlev();
+    for (int l = 0; l < n - 1; ++l) {
+        LevelBuf &B = h->lev[l];
+        prof(STOKES_K_MEMSET, l, s, [&] { cudaMemsetAsync(B.x, 0, sizeof(T) * B.L.n, s); });
+        smooth<T>(h, l, s);
+        prof(STOKES_K_RESIDUAL, l, s,
+             [&] { launch_apply<T>(B.L, (const T *)B.x, (const T *)B.b, (T *)B.r, B.L.gamma, s); });
+        prof(STOKES_K_RESTRICT, l, s,
+             [&] { launch_restrict<T>(B.L, h->lev[l + 1].L, (const T *)B.r, (T *)h->lev[l + 1].b, s); });
+    }
+    LevelBuf &C = h->lev[n - 1];
+    prof(STOKES_K_COARSE, n - 1, s,
+         [&] { launch_coarse<T>(C.L, h->cidx, h->nc, h->ckinv, (const T *)C.b, (T *)C.x, s); });
+    for (int l = n - 2; l >= 0; --l) {
+        LevelBuf &B = h->lev[l];
+        prof(STOKES_K_PROLONG, l, s,
+             [&] { launch_prolong<T>(B.L, h->lev[l + 1].L, (const T *)h->lev[l + 1].x, (T *)B.x, s); });
+        smooth<T>(h, l, s);
+    }
+}
+void vcycle_any(stokes_s *h, cudaStream_t s) {
+    if (h->prec == STOKES_PREC_FP64) vcycle<double>(h, s);
+    else vcycle<float>(h, s);
+}
+
+// one SQMR iteration (Alg. 4, loop body) on the finest level
+template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s) {
+    const Lev &L = h->lev[0].L;
+    long long n = L.n;
+    T *t = (T *)h->lev[0].x;
+    // t <- L q_{j-1}, sigma = q^T t ; alpha = rho / sigma
+    prof(STOKES_K_APPLY_DOT, 0, s, [&] { launch_apply_dot(L, h->q, h->w, h->partials, s); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(0, h->partials, h->st, h->hout, s); });
+    // s_j = s_{j-1} - alpha t
+    prof(STOKES_K_UPDATE_S, 0, s, [&] {
+        launch_update_s<T>(n, h->s, h->w, h->st, h->prec == STOKES_PREC_FP64 ? nullptr : (T *)h->lev[0].b, s);
+    });
+    vcycle<T>(h, s);  // t <- V-cycle(L~, s_j, 0, n)
+    // |t|^2, rho_j = s_j^T t ; nu, c, tau, beta
+    prof(STOKES_K_DOT2, 0, s, [&] { launch_dot2<T>(n, t, h->s, h->partials, s); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(1, h->partials, h->st, h->hout, s); });
+    // d_j, x_j, recursive true residual r_j, q_j ; |r_j|^2 to the host
+    prof(STOKES_K_UPDATE_X, 0, s,
+         [&] { launch_update_x<T>(n, h->x, h->d, h->q, t, h->r, h->s, h->st, h->partials, s); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(2, h->partials, h->st, h->hout, s); });
+}
+void sqmr_iteration_any(stokes_s *h, cudaStream_t s) {
+    if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s);
+    else sqmr_iteration<float>(h, s);
+}
+
+template <class F> int capture(stokes_s *h, F body, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cs, cudaStreamCaptureModeThreadLocal));
+    body(h, h->cs);
+    cudaError_t e = cudaStreamEndCapture(h->cs, &g);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_status(e);
+    return 0;
+}
+
+int run_vcycle(stokes_s *h, cudaStream_t s) {
+    if (h->use_graphs) {
+        if (!h->g_vcycle) {
+            int rc = capture(h, vcycle_any, &h->g_vcycle);
+            if (rc) return rc;
+        }
+        CK(cudaGraphLaunch(h->g_vcycle, s));
+    } else {
+        vcycle_any(h, s);
+        CKLAUNCH();
+    }
+    return 0;
+}
+
+int run_iteration(stokes_s *h, cudaStream_t s) {
+    if (h->use_graphs) {
+        if (!h->g_iter) {
+            int rc = capture(h, sqmr_iteration_any, &h->g_iter);
+            if (rc) return rc;
+        }
+        CK(cudaGraphLaunch(h->g_iter, s));
+    } else {
+        sqmr_iteration_any(h, s);
+        CKLAUNCH();
+    }
+    return 0;
+}
+
+// copy a caller vector (host or device) of n doubles into a device buffer the call may read
+int stage_in(stokes_s *h, const double *p, long long n, double *dst_if_host, const double **out, cudaStream_t s) {
+    if (is_device_ptr(p)) {
+        *out = p;
+        return 0;
+    }
+    CK(cudaMemcpyAsync(dst_if_host, p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    *out = dst_if_host;
+    return 0;
+}
+int ensure_stage(stokes_s *h) {
+    if (!h->stage_in) {
+        int rc = h->alloc(&h->stage_in, sizeof(double) * h->n0());
+        if (rc) return rc;
+        rc = h->alloc(&h->stage_out, sizeof(double) * h->n0());
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+// level vector in/out (FP64 caller layout <-> precision T of the level buffers)
+int to_level(stokes_s *h, const double *src_dev, void *dst, long long n, cudaStream_t s) {
+    if (h->prec == STOKES_PREC_FP64) CK(cudaMemcpyAsync(dst, src_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else launch_convert<double, float>(n, src_dev, (float *)dst, s);
+    CKLAUNCH();
+    return 0;
+}
+int from_level(stokes_s *h, const void *src, double *dst_dev, long long n, cudaStream_t s) {
+    if (h->prec == STOKES_PREC_FP64) CK(cudaMemcpyAsync(dst_dev, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else launch_convert<float, double>(n, (const float *)src, dst_dev, s);
+    CKLAUNCH();
+    return 0;
+}
+
+// read the two doubles the scalar kernel wrote to mapped host memory
+int sync_read(stokes_s *h, cudaStream_t s, double *a, double *b) {
+    CK(cudaStreamSynchronize(s));
+    if (a) *a = h->hout[0];
+    if (b) *b = h->hout[1];
+    return 0;
+}
+
+int residual_norm2(stokes_s *h, const double *b, const double *x, double *w, double *out, cudaStream_t s) {
+    launch_residual_dot(h->lev[0].L, b, x, w, h->partials, s);
+    launch_scalars(4, h->partials, h->st, h->hout, s);
+    CKLAUNCH();
+    return sync_read(h, s, out, nullptr);
+}
+
+}  // namespace
+
+// ======================================================================================== C ABI
+
+extern "C" {
+
+void stokes_opts_default(stokes_opts_t *o) {
+    if (!o) return;
+    o->gamma = 1e-3;
+    o->kb_vanka = 1;
+    o->precision = STOKES_PREC_FP64;
+    o->use_graphs = 1;
+}
+
+const char *stokes_strerror(int st) {
+    switch (st) {
+    case STOKES_OK: return "ok";
+    case STOKES_ERR_INVALID_ARG: return "invalid argument";
+    case STOKES_ERR_OOM: return "out of memory";
+    case STOKES_ERR_CUDA: return "CUDA runtime error";
+    case STOKES_ERR_BREAKDOWN: return "SQMR breakdown (q^T L q = 0 or s^T t = 0)";
+    case STOKES_ERR_NOT_CONVERGED: return "SQMR did not reach the tolerance within max_iter";
+    case STOKES_ERR_NAN: return "non-finite value in the SQMR recurrences";
+    case STOKES_ERR_TIMEOUT: return "device wait timed out";
+    case STOKES_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double viscosity, const stokes_opts_t *opts,
+                  stokes_t *out) {
+    if (!grid || !out) return STOKES_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 || !(viscosity > 0.0)) return STOKES_ERR_INVALID_ARG;
+    if (bc && bc->cell_labels) return STOKES_ERR_UNSUPPORTED;
+    stokes_opts_t o;
+    stokes_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.gamma >= 0.0) || o.kb_vanka < 0 || (o.precision != STOKES_PREC_FP64 && o.precision != STOKES_PREC_FP32))
+        return STOKES_ERR_INVALID_ARG;
+    int cmax = grid->coarsest_max > 0 ? grid->coarsest_max : 8;
+    int nlev = grid->levels;
+    if (nlev <= 0) {
+        nlev = 1;
+        int a = grid->nx, b = grid->ny, c = grid->nz;
+        while (a % 2 == 0 && b % 2 == 0 && c % 2 == 0 && (a > cmax || b > cmax || c > cmax) && a >= 4 && b >= 4 &&
+               c >= 4) {
+            a /= 2; b /= 2; c /= 2; ++nlev;
+        }
+    } else {
+        int a = grid->nx, b = grid->ny, c = grid->nz;
+        for (int l = 1; l < nlev; ++l) {
+            if (a % 2 || b % 2 || c % 2 || a < 4 || b < 4 || c < 4) return STOKES_ERR_INVALID_ARG;
+            a /= 2; b /= 2; c /= 2;
+        }
+    }
+    std::unique_ptr<stokes_s> h(new stokes_s());
+    CK(cudaGetDevice(&h->dev));
+    h->prec = o.precision;
+    h->kb = o.kb_vanka;
+    h->use_graphs = o.use_graphs;
+    h->eta = viscosity;
+    h->gamma = o.gamma;
+    double hh = grid->h > 0 ? grid->h : 1.0 / grid->nx;
+    size_t es = h->prec == STOKES_PREC_FP64 ? sizeof(double) : sizeof(float);
+    int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    for (int l = 0; l < nlev; ++l) {
+        LevelBuf B;
+        B.L = make_level(nx, ny, nz, hh, viscosity, o.gamma);
+        h->lev.push_back(B);
+        nx /= 2; ny /= 2; nz /= 2; hh *= 2.0;
+    }
+    // coarsest level: exact solve
+    {
+        LevelBuf &C = h->lev[nlev - 1];
+        std::vector<int> cidx;
+        long long nact = 0;
+        for (int c = 0; c < 4; ++c) {
+            long long cnt = 1;
+            for (int d = 0; d < 3; ++d) {
+                int n = d == 0 ? C.L.nx : (d == 1 ? C.L.ny : C.L.nz);
+                cnt *= (c == d) ? (n - 1) : n;
+            }
+            nact += cnt;
+        }
+        if (nact > 6000) return STOKES_ERR_INVALID_ARG;  // dense inverse would not fit the design
+        std::shared_ptr<std::vector<double>> K;
+        int rc = coarse_inverse(C.L, cidx, K);
+        if (rc) return rc;
+        h->nc = (int)cidx.size();
+        if ((rc = h->alloc(&h->cidx, sizeof(int) * h->nc))) return rc;
+        if ((rc = h->alloc(&h->ckinv, sizeof(double) * (size_t)h->nc * h->nc))) return rc;
+        CK(cudaMemcpy(h->cidx, cidx.data(), sizeof(int) * h->nc, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->ckinv, K->data(), sizeof(double) * (size_t)h->nc * h->nc, cudaMemcpyHostToDevice));
+        if ((rc = h->alloc(&C.x, es * C.L.n))) return rc;
+        if ((rc = h->alloc(&C.b, es * C.L.n))) return rc;
+    }
+    // smoothed levels
+    for (int l = 0; l < nlev - 1; ++l) {
+        LevelBuf &B = h->lev[l];
+        const Lev &L = B.L;
+        int rc;
+        if ((rc = h->alloc(&B.x, es * L.n))) return rc;
+        if ((rc = h->alloc(&B.b, es * L.n))) return rc;
+        if ((rc = h->alloc(&B.r, es * L.n))) return rc;
+        if ((rc = h->alloc(&B.delta, es * (size_t)L.nx * L.ny * L.nz))) return rc;
+        // V1 cells (interior cells with a face on the ghost shell) by colour
+        std::vector<int> cells[8];
+        for (int k = 0; k < L.nz; ++k)
+            for (int j = 0; j < L.ny; ++j)
+                for (int i = 0; i < L.nx; ++i) {
+                    bool v1 = i == 0 || j == 0 || k == 0 || i == L.nx - 1 || j == L.ny - 1 || k == L.nz - 1;
+                    if (!v1) continue;
+                    int col = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+                    cells[col].push_back(i + L.nx * (j + L.ny * k));
+                }
+        B.vcap = 1;
+        for (int c = 0; c < 8; ++c) {
+            B.vcount[c] = (int)cells[c].size();
+            B.vcap = B.vcount[c] > B.vcap ? B.vcount[c] : B.vcap;
+            if ((rc = h->alloc(&B.vcells[c], sizeof(int) * (cells[c].size() + 1)))) return rc;
+            if (!cells[c].empty())
+                CK(cudaMemcpy(B.vcells[c], cells[c].data(), sizeof(int) * cells[c].size(), cudaMemcpyHostToDevice));
+        }
+        if ((rc = h->alloc(&B.corr, es * 7 * (size_t)B.vcap))) return rc;
+        // Sec. 6: pre-factorised local problems, one per configuration of unknown faces
+        std::vector<double> kd(64 * 49, 0.0);
+        for (int cfg = 0; cfg < 64; ++cfg)
+            if (vanka_local_inverse(L.h, L.eta, L.gamma, cfg, &kd[cfg * 49])) std::fill(&kd[cfg * 49], &kd[cfg * 49] + 49, 0.0);
+        if ((rc = h->alloc(&B.kinv, es * 64 * 49))) return rc;
+        if (h->prec == STOKES_PREC_FP64) {
+            CK(cudaMemcpy(B.kinv, kd.data(), sizeof(double) * 64 * 49, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> kf(kd.begin(), kd.end());
+            CK(cudaMemcpy(B.kinv, kf.data(), sizeof(float) * 64 * 49, cudaMemcpyHostToDevice));
+        }
+    }
+    // SQMR vectors and scalar state
+    {
+        long long n = h->n0();
+        int rc;
+        if ((rc = h->alloc(&h->x, sizeof(double) * n))) return rc;
+        if ((rc = h->alloc(&h->q, sizeof(double) * n))) return rc;
+        if ((rc = h->alloc(&h->d, sizeof(double) * n))) return rc;
+        if ((rc = h->alloc(&h->r, sizeof(double) * n))) return rc;
+        if ((rc = h->alloc(&h->w, sizeof(double) * n))) return rc;
+        if ((rc = h->alloc(&h->bvec, sizeof(double) * n))) return rc;
+        if (h->prec == STOKES_PREC_FP64) h->s = (double *)h->lev[0].b;
+        else if ((rc = h->alloc(&h->s, sizeof(double) * n))) return rc;
+        if ((rc = h->alloc(&h->partials, sizeof(double) * kRedBlocks * kRedParts))) return rc;
+        if ((rc = h->alloc(&h->st, sizeof(SqmrState)))) return rc;
+        CK(cudaHostAlloc((void **)&h->hout, 4 * sizeof(double), cudaHostAllocMapped));
+        std::memset(h->hout, 0, 4 * sizeof(double));
+    }
+    CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+    CK(cudaDeviceSynchronize());
+    *out = h.release();
+    return STOKES_OK;
+}
+
+int stokes_destroy(stokes_t h) {
+    if (!h) return STOKES_OK;
+    DeviceGuard g(h->dev);
+    cudaDeviceSynchronize();
+    delete h;
+    return STOKES_OK;
+}
+
+long long stokes_vector_length(stokes_t h, int level) {
+    if (!h || level < 0 || level >= h->nlev()) return 0;
+    return h->lev[level].L.n;
+}
+long long stokes_ghost_length(stokes_t h) {
+    if (!h) return 0;
+    const Lev &L = h->lev[0].L;
+    return (long long)(L.nx + 1) * (L.ny + 2) * (L.nz + 2) + (long long)(L.nx + 2) * (L.ny + 1) * (L.nz + 2) +
+           (long long)(L.nx + 2) * (L.ny + 2) * (L.nz + 1);
+}
+int stokes_num_levels(stokes_t h) { return h ? h->nlev() : 0; }
+
+int stokes_rhs(stokes_t h, const double *f, const double *g, double *b, void *stream) {
+    if (!h || !b) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = ensure_stage(h))) return rc;
+    const double *fd = nullptr, *gd = nullptr;
+    double *gbuf = nullptr;
+    if (f && (rc = stage_in(h, f, h->n0(), h->stage_in, &fd, s))) return rc;
+    if (g) {
+        if (is_device_ptr(g)) gd = g;
+        else {
+            long long ng = stokes_ghost_length(h);
+            CK(cudaMallocAsync((void **)&gbuf, sizeof(double) * ng, s));
+            CK(cudaMemcpyAsync(gbuf, g, sizeof(double) * ng, cudaMemcpyHostToDevice, s));
+            gd = gbuf;
+        }
+    }
+    bool bdev = is_device_ptr(b);
+    double *bd = bdev ? b : h->stage_out;
+    launch_rhs(h->lev[0].L, fd, gd, bd, s);
+    CKLAUNCH();
+    if (gbuf) CK(cudaFreeAsync(gbuf, s));
+    if (!bdev) {
+        CK(cudaMemcpyAsync(b, bd, sizeof(double) * h->n0(), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return STOKES_OK;
+}
+
+int stokes_apply(stokes_t h, const double *x, double *y, void *stream) {
+    if (!h || !x || !y) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    const double *xd;
+    if (!is_device_ptr(x) || !is_device_ptr(y))
+        if ((rc = ensure_stage(h))) return rc;
+    if ((rc = stage_in(h, x, h->n0(), h->stage_in, &xd, s))) return rc;
+    bool ydev = is_device_ptr(y);
+    double *yd = ydev ? y : h->stage_out;
+    launch_apply<double>(h->lev[0].L, xd, nullptr, yd, 0.0, s);
+    CKLAUNCH();
+    if (!ydev) {
+        CK(cudaMemcpyAsync(y, yd, sizeof(double) * h->n0(), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return STOKES_OK;
+}
+
+int mg_precondition(stokes_t h, const double *sv, double *tv, void *stream) {
+    if (!h || !sv || !tv || (const double *)tv == sv) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    long long n = h->n0();
+    if (!is_device_ptr(sv) || !is_device_ptr(tv))
+        if ((rc = ensure_stage(h))) return rc;
+    const double *sd;
+    if ((rc = stage_in(h, sv, n, h->stage_in, &sd, s))) return rc;
+    if ((rc = to_level(h, sd, h->lev[0].b, n, s))) return rc;
+    if (h->prec == STOKES_PREC_FP64) launch_mask(h->lev[0].L, (double *)h->lev[0].b, s);
+    if ((rc = run_vcycle(h, s))) return rc;
+    bool tdev = is_device_ptr(tv);
+    double *td = tdev ? tv : h->stage_out;
+    if ((rc = from_level(h, h->lev[0].x, td, n, s))) return rc;
+    if (!tdev) {
+        CK(cudaMemcpyAsync(tv, td, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return STOKES_OK;
+}
+
+int stokes_residual_norm(stokes_t h, const double *b, const double *x, double *out, void *stream) {
+    if (!h || !b || !x || !out) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    const double *bd, *xd;
+    bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    if ((!bdev || !xdev) && (rc = ensure_stage(h))) return rc;
+    if ((rc = stage_in(h, b, h->n0(), h->stage_in, &bd, s))) return rc;
+    if ((rc = stage_in(h, x, h->n0(), h->stage_out, &xd, s))) return rc;
+    double r2 = 0.0;
+    if ((rc = residual_norm2(h, bd, xd, nullptr, &r2, s))) return rc;
+    *out = std::sqrt(r2);
+    return STOKES_OK;
+}
+
+int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info, void *stream) {
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (!h || !rhs || !xv || !(tol > 0.0) || max_iter < 0) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Lev &L = h->lev[0].L;
+    long long n = L.n;
+    int rc = 0;
+    // inputs
+    if (is_device_ptr(rhs)) CK(cudaMemcpyAsync(h->bvec, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else CK(cudaMemcpyAsync(h->bvec, rhs, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    bool xdev = is_device_ptr(xv);
+    CK(cudaMemcpyAsync(h->x, xv, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    launch_mask(L, h->bvec, s);
+    launch_mask(L, h->x, s);
+    // |b|
+    double bb = 0.0, ss = 0.0, rr = 0.0, flags = 0.0;
+    launch_dot2<double>(n, h->bvec, nullptr, h->partials, s);
+    launch_scalars(4, h->partials, h->st, h->hout, s);
+    CKLAUNCH();
+    if ((rc = sync_read(h, s, &bb, nullptr))) return rc;
+    double nb = std::sqrt(bb);
+    int it = 0, status = STOKES_OK;
+    double rel = 0.0;
+    if (!std::isfinite(nb)) {
+        status = STOKES_ERR_NAN;
+        goto finish;
+    }
+    if (nb == 0.0) {
+        CK(cudaMemsetAsync(h->x, 0, sizeof(double) * n, s));
+        goto finish;
+    }
+    // s_0 = b - L x_0 ; r_0 = s_0
+    if ((rc = residual_norm2(h, h->bvec, h->x, h->s, &ss, s))) return rc;
+    CK(cudaMemcpyAsync(h->r, h->s, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    rel = std::sqrt(ss) / nb;
+    if (rel < tol) goto finish;
+    // t = V-cycle(L~, s_0, 0, n); q_0 = t; tau_0 = |t|; rho_0 = s_0^T q_0; d = 0
+    if (h->prec != STOKES_PREC_FP64) launch_convert<double, float>(n, h->s, (float *)h->lev[0].b, s);
+    if ((rc = run_vcycle(h, s))) return rc;
+    if (h->prec == STOKES_PREC_FP64) {
+        launch_dot2<double>(n, (const double *)h->lev[0].x, h->s, h->partials, s);
+        launch_init_q<double>(n, (const double *)h->lev[0].x, h->q, h->d, s);
+    } else {
+        launch_dot2<float>(n, (const float *)h->lev[0].x, h->s, h->partials, s);
+        launch_init_q<float>(n, (const float *)h->lev[0].x, h->q, h->d, s);
+    }
+    launch_scalars(3, h->partials, h->st, h->hout, s);
+    CKLAUNCH();
+    {
+        double tt = 0.0, st0 = 0.0;
+        if ((rc = sync_read(h, s, &tt, &st0))) return rc;
+        if (!std::isfinite(tt) || !std::isfinite(st0)) { status = STOKES_ERR_NAN; goto finish; }
+        if (tt == 0.0 || st0 == 0.0) { status = STOKES_ERR_BREAKDOWN; goto finish; }
+    }
+    status = STOKES_ERR_NOT_CONVERGED;
+    for (it = 1; it <= max_iter; ++it) {
+        if ((rc = run_iteration(h, s))) return rc;
+        if ((rc = sync_read(h, s, &rr, &flags))) return rc;
+        int fl = (int)flags;
+        if (fl & 2 || !std::isfinite(rr)) { status = STOKES_ERR_NAN; break; }
+        if (fl & 1) { status = STOKES_ERR_BREAKDOWN; break; }
+        if (std::sqrt(rr) / nb < tol) {
+            // confirm with the explicit FP64 residual b - L x_j; keep iterating from it otherwise
+            double r2 = 0.0;
+            if ((rc = residual_norm2(h, h->bvec, h->x, h->w, &r2, s))) return rc;
+            rel = std::sqrt(r2) / nb;
+            if (rel < tol) { status = STOKES_OK; break; }
+            CK(cudaMemcpyAsync(h->r, h->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    if (it > max_iter) it = max_iter;
+finish:
+    // pressure fixed to zero mean (constant p lies in ker L)
+    launch_psum(L, h->x, h->partials, s);
+    launch_scalars_aux(5, h->partials, h->st, h->hout, (double)L.nx * L.ny * L.nz, s);
+    launch_psub(L, h->x, h->st, s);
+    CKLAUNCH();
+    {
+        double r2 = 0.0;
+        if ((rc = residual_norm2(h, h->bvec, h->x, nullptr, &r2, s))) return rc;
+        rel = nb > 0 ? std::sqrt(r2) / nb : 0.0;
+    }
+    CK(cudaMemcpyAsync(xv, h->x, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (info) {
+        info->iterations = it;
+        info->rel_residual = rel;
+        info->status = status;
+        info->vcycles = it + (it > 0 ? 1 : 0);
+    }
+    return status;
+}
+
+int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launches_all, double *ms_level0,
+                             int *launches_level0, void *stream) {
+    if (!h || nkinds < STOKES_K_COUNT || !ms_all || !launches_all || !ms_level0 || !launches_level0)
+        return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    Prof P;
+    P.ev.resize(8192);
+    for (auto &e : P.ev) CK(cudaEventCreate(&e));
+    g_prof = &P;
+    sqmr_iteration_any(h, s);
+    g_prof = nullptr;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int k = 0; k < nkinds; ++k) ms_all[k] = ms_level0[k] = 0.0, launches_all[k] = launches_level0[k] = 0;
+    if (e == cudaSuccess)
+        for (size_t i = 0; i < P.kind.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]);
+            ms_all[P.kind[i]] += ms;
+            launches_all[P.kind[i]] += 1;
+            if (P.level[i] == 0) {
+                ms_level0[P.kind[i]] += ms;
+                launches_level0[P.kind[i]] += 1;
+            }
+        }
+    for (auto &ev : P.ev) cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_status(e);
+    return STOKES_OK;
+}
+
+int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, void *stream) {
+    if (!h || !x || !b || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
+    if (!(which >= 0 && which <= 4) && !(which >= 10 && which <= 17)) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelBuf &B = h->lev[level];
+    long long n = B.L.n;
+    int rc;
+    if ((rc = ensure_stage(h))) return rc;
+    const double *xd, *bd;
+    bool xdev = is_device_ptr(x);
+    if ((rc = stage_in(h, x, n, h->stage_in, &xd, s))) return rc;
+    if ((rc = to_level(h, xd, B.x, n, s))) return rc;
+    if ((rc = stage_in(h, b, n, h->stage_in, &bd, s))) return rc;
+    if ((rc = to_level(h, bd, B.b, n, s))) return rc;
+    auto body = [&](auto tag) {
+        using T = decltype(tag);
+        switch (which) {
+        case 0: smooth<T>(h, level, s); break;
+        case 1: dgs_forward<T>(h, level, s); dgs_backward<T>(h, level, s); break;
+        case 2: vanka_sym<T>(h, level, s); break;
+        case 3: dgs_forward<T>(h, level, s); break;
+        case 4: dgs_backward<T>(h, level, s); break;
+        default: vanka_colour<T>(h, level, which - 10, s); break;
+        }
+    };
+    if (h->prec == STOKES_PREC_FP64) body(double());
+    else body(float());
+    CKLAUNCH();
+    double *out = xdev ? x : h->stage_out;
+    if ((rc = from_level(h, B.x, out, n, s))) return rc;
+    launch_mask(B.L, out, s);
+    if (!xdev) CK(cudaMemcpyAsync(x, out, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return STOKES_OK;
+}
+
+int stokes_restrict(stokes_t h, int level, const double *rf, double *bc, void *stream) {
+    if (!h || !rf || !bc || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelBuf &F = h->lev[level], &C = h->lev[level + 1];
+    int rc;
+    if ((rc = ensure_stage(h))) return rc;
+    const double *rd;
+    if ((rc = stage_in(h, rf, F.L.n, h->stage_in, &rd, s))) return rc;
+    if ((rc = to_level(h, rd, F.r, F.L.n, s))) return rc;
+    auto run = [&](auto tag) {
+        using T = decltype(tag);
+        launch_restrict<T>(F.L, C.L, (const T *)F.r, (T *)C.b, s);
+    };
+    if (h->prec == STOKES_PREC_FP64) run(double());
+    else run(float());
+    CKLAUNCH();
+    bool dev = is_device_ptr(bc);
+    double *out = dev ? bc : h->stage_out;
+    if ((rc = from_level(h, C.b, out, C.L.n, s))) return rc;
+    if (!dev) CK(cudaMemcpyAsync(bc, out, sizeof(double) * C.L.n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return STOKES_OK;
+}
+
+int stokes_prolong_add(stokes_t h, int level, const double *ec, double *xf, void *stream) {
+    if (!h || !ec || !xf || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelBuf &F = h->lev[level], &C = h->lev[level + 1];
+    int rc;
+    if ((rc = ensure_stage(h))) return rc;
+    const double *ed, *xd;
+    if ((rc = stage_in(h, ec, C.L.n, h->stage_in, &ed, s))) return rc;
+    if ((rc = to_level(h, ed, C.x, C.L.n, s))) return rc;
+    bool xdev = is_device_ptr(xf);
+    if ((rc = stage_in(h, xf, F.L.n, h->stage_in, &xd, s))) return rc;
+    if ((rc = to_level(h, xd, F.x, F.L.n, s))) return rc;
+    auto run = [&](auto tag) {
+        using T = decltype(tag);
+        launch_prolong<T>(F.L, C.L, (const T *)C.x, (T *)F.x, s);
+    };
+    if (h->prec == STOKES_PREC_FP64) run(double());
+    else run(float());
+    CKLAUNCH();
+    // the coarse x buffer must hold zeros off the unknowns for later V-cycles
+    CK(cudaMemsetAsync(C.x, 0, (h->prec == STOKES_PREC_FP64 ? 8 : 4) * C.L.n, s));
+    double *out = xdev ? xf : h->stage_out;
+    if ((rc = from_level(h, F.x, out, F.L.n, s))) return rc;
+    launch_mask(F.L, out, s);
+    if (!xdev) CK(cudaMemcpyAsync(xf, out, sizeof(double) * F.L.n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return STOKES_OK;
+}
+
+int stokes_coarse_solve(stokes_t h, const double *b, double *x, void *stream) {
+    if (!h || !b || !x) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelBuf &C = h->lev[h->nlev() - 1];
+    int rc;
+    if ((rc = ensure_stage(h))) return rc;
+    const double *bd;
+    if ((rc = stage_in(h, b, C.L.n, h->stage_in, &bd, s))) return rc;
+    if ((rc = to_level(h, bd, C.b, C.L.n, s))) return rc;
+    CK(cudaMemsetAsync(C.x, 0, (h->prec == STOKES_PREC_FP64 ? 8 : 4) * C.L.n, s));
+    auto run = [&](auto tag) {
+        using T = decltype(tag);
+        launch_coarse<T>(C.L, h->cidx, h->nc, h->ckinv, (const T *)C.b, (T *)C.x, s);
+    };
+    if (h->prec == STOKES_PREC_FP64) run(double());
+    else run(float());
+    CKLAUNCH();
+    bool dev = is_device_ptr(x);
+    double *out = dev ? x : h->stage_out;
+    if ((rc = from_level(h, C.x, out, C.L.n, s))) return rc;
+    if (!dev) CK(cudaMemcpyAsync(x, out, sizeof(double) * C.L.n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return STOKES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// stokes_internal.cuh -- level descriptor, index math and stencil device functions shared by the
+// CUDA kernels of the MAC Stokes multigrid-preconditioned SQMR solver (sm_103a).
+//
+// Discretisation (Tao & Sifakis, Sec. 2 Eq. 2 and Sec. 4):  for an active face f of component c
+//   (L~x)_f = eta/h^2 (6 x_f - sum of its 6 same-component neighbours) + (p_plus - p_minus)/h
+// and for a cell
+//   (L~x)_c = -(sum over axes of (u_high - u_low))/h - gamma p_c      (gamma = 0 gives L).
+// Box domain: a face is an unknown when its normal index lies in [1, n-1] and its tangential
+// indices in [0, n-1]; every other referenced face (walls, ghost rows) contributes 0.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace smg {
+
+struct Lev {
+    int nx, ny, nz;
+    long long off[4];  // offsets of the u, v, w, p blocks in the packed vector
+    long long n;       // packed length
+    double h, eta, gamma;
+};
+
+__host__ __device__ inline int ext(const Lev &L, int c, int d) {
+    int n = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
+    return n + (c == d ? 1 : 0);
+}
+
+// linear index of entry (i,j,k) of component c (0 u, 1 v, 2 w, 3 p) in the packed vector
+__host__ __device__ inline long long pidx(const Lev &L, int c, int i, int j, int k) {
+    long long ex = ext(L, c, 0), ey = ext(L, c, 1);
+    return L.off[c] + i + ex * (j + ey * (long long)k);
+}
+
+// is (c,i,j,k) an unknown of the box problem?
+__host__ __device__ inline bool active(const Lev &L, int c, int i, int j, int k) {
+    if (c == 3) return i >= 0 && j >= 0 && k >= 0 && i < L.nx && j < L.ny && k < L.nz;
+    int a[3] = {i, j, k};
+    int n[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d == c) {
+            if (a[d] < 1 || a[d] > n[d] - 1) return false;
+        } else if (a[d] < 0 || a[d] > n[d] - 1) {
+            return false;
+        }
+    }
+    return true;
+}
+
+template <class T>
+__device__ __forceinline__ T xget(const T *__restrict__ x, const Lev &L, int c, int i, int j, int k) {
+    return active(L, c, i, j, k) ? x[pidx(L, c, i, j, k)] : T(0);
+}
+
+template <class T> struct Coef {
+    T eh2, ih, gam;  // eta/h^2, 1/h, gamma
+};
+template <class T> __host__ __device__ inline Coef<T> coef(const Lev &L, double gam) {
+    Coef<T> k;
+    k.eh2 = T(L.eta / (L.h * L.h));
+    k.ih = T(1.0 / L.h);
+    k.gam = T(gam);
+    return k;
+}
+
+// (L~x) on an active face of component c at (i,j,k); neighbours that are not unknowns count 0
+template <class T>
+__device__ __forceinline__ T face_Lx(const T *__restrict__ x, const Lev &L, int c, int i, int j, int k,
+                                     const Coef<T> &K) {
+    T s = T(6) * x[pidx(L, c, i, j, k)];
+    s -= xget(x, L, c, i - 1, j, k);
+    s -= xget(x, L, c, i + 1, j, k);
+    s -= xget(x, L, c, i, j - 1, k);
+    s -= xget(x, L, c, i, j + 1, k);
+    s -= xget(x, L, c, i, j, k - 1);
+    s -= xget(x, L, c, i, j, k + 1);
+    T pp = x[pidx(L, 3, i, j, k)];
+    T pm = x[pidx(L, 3, i - (c == 0), j - (c == 1), k - (c == 2))];
+    return K.eh2 * s + K.ih * (pp - pm);
+}
+
+// (L~x) on cell (i,j,k)
+template <class T>
+__device__ __forceinline__ T cell_Lx(const T *__restrict__ x, const Lev &L, int i, int j, int k, const Coef<T> &K) {
+    T div = xget(x, L, 0, i + 1, j, k) - xget(x, L, 0, i, j, k) + xget(x, L, 1, i, j + 1, k) - xget(x, L, 1, i, j, k) +
+            xget(x, L, 2, i, j, k + 1) - xget(x, L, 2, i, j, k);
+    return -K.ih * div - K.gam * x[pidx(L, 3, i, j, k)];
+}
+
+// decode a per-component thread index t (< ex*ey*ez) into (i,j,k)
+__device__ __forceinline__ void decode3(long long t, int ex, int ey, int &i, int &j, int &k) {
+    i = (int)(t % ex);
+    long long r = t / ex;
+    j = (int)(r % ey);
+    k = (int)(r / ey);
+}
+
+}  // namespace smg

@@ -1,0 +1,337 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element on the same
+seeded inputs, plus full-size properties and edge cases.  Needs a GB300 (sm_103a).
+
+Tolerances (relative to the max-norm of the oracle result):
+* FP64 path: every kernel does the oracle's arithmetic in a different order, so single pieces agree to
+  ~1e-15 per operation; 1e-12 covers a smoother sweep / transfer, 1e-11 a V-cycle (about 200 dependent
+  updates), 1e-10 an SQMR iterate (the FP64 bound the solver states).
+* FP32 V-cycle: unit round-off 6e-8 times ~200 dependent updates on O(1) data -> 1e-4 for a V-cycle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+smg = pytest.importorskip("paper_2312_10615_gb300")
+DEV = torch.device("cuda:0")
+
+
+def rel_err(got, ref):
+    got = got.cpu().numpy() if isinstance(got, torch.Tensor) else got
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def rand_masked(o, seed, level=0):
+    act, _ = o.masks(level)
+    v = np.random.default_rng(seed).standard_normal(o.n(level))
+    v[~act] = 0.0
+    return v
+
+
+def cuda(v):
+    return torch.from_numpy(np.ascontiguousarray(v)).to(DEV)
+
+
+_cache = {}
+
+
+def pair(dims, precision=smg.PREC_FP64, **kw):
+    """(oracle, GPU handle) for a box, cached per module run."""
+    key = (dims, precision, tuple(sorted(kw.items())))
+    if key not in _cache:
+        nx, ny, nz = dims
+        o = oracle.Oracle(nx, ny, nz, coarsest_max=8, **kw)
+        S = smg.Stokes(nx, ny, nz, precision=precision, **kw)
+        assert S.levels == o.nlevels
+        _cache[key] = (o, S)
+    return _cache[key]
+
+
+# ---------------------------------------------------------------------------------------------- a1
+
+@pytest.mark.parametrize("dims", [(32, 32, 32), (24, 16, 20), (9, 7, 5), (2, 2, 2)])
+def test_apply_parity(dims):
+    o, S = pair(dims)
+    x = rand_masked(o, 1)
+    y = S.apply(cuda(x))
+    assert rel_err(y, o.apply(x)) < 1e-13
+
+
+def test_apply_ignores_entries_off_the_unknowns():
+    o, S = pair((24, 16, 20))
+    x = np.random.default_rng(2).standard_normal(o.n())  # garbage on walls too
+    act, _ = o.masks()
+    y = S.apply(cuda(x)).cpu().numpy()
+    assert rel_err(y, o.apply(np.where(act, x, 0.0))) < 1e-13
+    assert np.all(y[~act] == 0.0)
+
+
+def test_rhs_parity_mms():
+    o, S = pair((24, 24, 24))
+    prob = synthetic.mms(24)
+    b = S.rhs(prob["f"].to(DEV), prob["g"].to(DEV))
+    assert rel_err(b, o.rhs(prob["f"].numpy(), prob["g"].numpy())) < 1e-13
+
+
+def test_rhs_parity_lid_and_host_pointers():
+    o, S = pair((24, 24, 24))
+    prob = synthetic.lid(24)
+    ref = o.rhs(prob["f"].numpy(), prob["g"].numpy())
+    b = np.zeros(o.n())
+    smg.stokes_rhs(S.h, prob["f"].numpy().copy(), prob["g"].numpy().copy(), b)  # host in, host out
+    assert rel_err(b, ref) < 1e-13
+
+
+# ---------------------------------------------------------------------------------------------- a4-a6
+
+SMOOTH_CASES = [(3, "dgs_fwd"), (4, "dgs_bwd"), (1, "dgs_sym"), (2, "vanka_sym"), (0, "alg3")] + \
+    [(10 + c, f"vanka_colour{c}") for c in range(8)]
+
+
+@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("which,name", SMOOTH_CASES)
+def test_smoother_piece_parity(which, name, level):
+    o, S = pair((32, 32, 32))
+    x = rand_masked(o, 3, level)
+    b = rand_masked(o, 4, level)
+    got = cuda(x)
+    smg.stokes_smooth(S.h, level, which, got, cuda(b))
+    if which == 0:
+        ref = o.smooth(x, b, level=level)
+    elif which in (1, 3, 4):
+        ref = o.dgs(x, b, level=level, direction={1: 0, 3: 1, 4: -1}[which])
+    elif which == 2:
+        ref = o.vanka(x, b, level=level, colour=-1)
+    else:
+        ref = o.vanka(x, b, level=level, colour=which - 10)
+    assert rel_err(got, ref) < 1e-12, name
+
+
+def test_smoother_non_cubic():
+    o, S = pair((24, 16, 32))
+    x, b = rand_masked(o, 5), rand_masked(o, 6)
+    got = cuda(x)
+    smg.stokes_smooth(S.h, 0, 0, got, cuda(b))
+    assert rel_err(got, o.smooth(x, b)) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------- a2, a3, a7
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_restrict_parity(level):
+    o, S = pair((32, 32, 32))
+    r = rand_masked(o, 7, level)
+    bc = torch.zeros(o.n(level + 1), dtype=torch.float64, device=DEV)
+    smg.stokes_restrict(S.h, level, cuda(r), bc)
+    assert rel_err(bc, o.restrict(r, level=level)) < 1e-13
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_prolong_parity(level):
+    o, S = pair((32, 32, 32))
+    e = rand_masked(o, 8, level + 1)
+    x = rand_masked(o, 9, level)
+    got = cuda(x)
+    smg.stokes_prolong_add(S.h, level, cuda(e), got)
+    assert rel_err(got, o.prolong_add(e, x, level=level)) < 1e-13
+
+
+@pytest.mark.parametrize("dims", [(32, 32, 32), (48, 48, 48)])
+def test_coarse_solve_parity(dims):
+    o, S = pair(dims)
+    lc = o.nlevels - 1
+    b = rand_masked(o, 10, lc)
+    x = torch.zeros(o.n(lc), dtype=torch.float64, device=DEV)
+    smg.stokes_coarse_solve(S.h, cuda(b), x)
+    assert rel_err(x, o.coarse_solve(b)) < 1e-10
+
+
+# ---------------------------------------------------------------------------------------------- a8
+
+@pytest.mark.parametrize("dims", [(32, 32, 32), (48, 48, 48), (24, 16, 32), (16, 16, 16)])
+def test_vcycle_parity(dims):
+    o, S = pair(dims)
+    s = rand_masked(o, 11)
+    t = S.precondition(cuda(s))
+    assert rel_err(t, o.vcycle(s)) < 1e-11
+
+
+def test_vcycle_parity_kb2():
+    o, S = pair((32, 32, 32), kb=2)
+    s = rand_masked(o, 12)
+    assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-11
+
+
+def test_vcycle_is_linear_and_symmetric_fp64():
+    o, S = pair((32, 32, 32))
+    x, y = cuda(rand_masked(o, 13)), cuda(rand_masked(o, 14))
+    Mx, My = S.precondition(x), S.precondition(y)
+    a, b = float(x @ My), float(y @ Mx)
+    assert abs(a - b) <= 1e-12 * float(torch.linalg.norm(x) * torch.linalg.norm(My))
+    Mxy = S.precondition(2.0 * x + y)
+    assert float(torch.max(torch.abs(Mxy - 2.0 * Mx - My))) <= 1e-12 * float(torch.max(torch.abs(Mxy)))
+
+
+def test_vcycle_fp32_parity_and_symmetry():
+    o, S = pair((32, 32, 32), precision=smg.PREC_FP32)
+    s = rand_masked(o, 15)
+    assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-4
+    x, y = cuda(rand_masked(o, 16)), cuda(rand_masked(o, 17))
+    a, b = float(x @ S.precondition(y)), float(y @ S.precondition(x))
+    assert abs(a - b) <= 1e-5 * float(torch.linalg.norm(x) * torch.linalg.norm(S.precondition(y)))
+
+
+def test_graph_and_eager_paths_agree():
+    o, Sg = pair((32, 32, 32))
+    Se = smg.Stokes(32, use_graphs=False)
+    s = cuda(rand_masked(o, 18))
+    assert float(torch.max(torch.abs(Sg.precondition(s) - Se.precondition(s)))) == 0.0
+    Se.close()
+
+
+# ---------------------------------------------------------------------------------------------- a9, a10
+
+def test_sqmr_manufactured_32_parity():
+    # 32^3, unit viscosity, manufactured solution, x0 = 0, tol 1e-10 (the parity workload)
+    o, S = pair((32, 32, 32))
+    prob = synthetic.mms(32)
+    b_ref = o.rhs(prob["f"].numpy(), prob["g"].numpy())
+    x_ref, rc, it_ref, rr_ref, _ = o.sqmr(b_ref, tol=1e-10, maxit=100)
+    assert rc == 0 and rr_ref < 1e-10
+    b = S.rhs(prob["f"].to(DEV), prob["g"].to(DEV))
+    # equal iteration count: compare the iterates
+    x = torch.zeros_like(b)
+    info = smg.sqmr_solve(S.h, b, x, tol=1e-30, max_iter=it_ref, check=False)
+    assert info.iterations == it_ref
+    assert rel_err(x, x_ref) < 1e-10
+    # on its own the GPU solve meets the tolerance, within one iteration of the oracle
+    x2, info2 = S.solve(b, tol=1e-10, max_iter=100)
+    assert info2.status == 0 and info2.rel_residual < 1e-10
+    assert abs(info2.iterations - it_ref) <= 1
+    assert rel_err(x2, x_ref) < 1e-9
+
+
+def test_sqmr_bumps_48_parity():
+    o, S = pair((48, 48, 48))
+    prob = synthetic.bumps(48, seed=3)
+    b_ref = o.rhs(prob["f"].numpy(), None)
+    x_ref, rc, it_ref, _, _ = o.sqmr(b_ref, tol=1e-8, maxit=100, fixed_iters=8)
+    b = S.rhs(prob["f"].to(DEV), None)
+    x = torch.zeros_like(b)
+    info = smg.sqmr_solve(S.h, b, x, tol=1e-30, max_iter=8, check=False)
+    assert info.iterations == 8
+    assert rel_err(x, x_ref) < 1e-10
+
+
+def test_sqmr_fp32_vcycle_accuracy():
+    # FP32 V-cycle, FP64 SQMR: the same tolerance is met; the solution agrees with the FP64 oracle
+    o, S = pair((32, 32, 32), precision=smg.PREC_FP32)
+    prob = synthetic.bumps(32, seed=1)
+    b_ref = o.rhs(prob["f"].numpy(), None)
+    x_ref, rc, it_ref, _, _ = o.sqmr(b_ref, tol=1e-12, maxit=200)
+    b = S.rhs(prob["f"].to(DEV), None)
+    x, info = S.solve(b, tol=1e-10, max_iter=200)
+    assert info.status == 0 and info.rel_residual < 1e-10
+    assert rel_err(x, x_ref) < 1e-7
+
+
+def test_sqmr_host_pointers_match_device():
+    o, S = pair((32, 32, 32))
+    prob = synthetic.bumps(32, seed=2)
+    b = S.rhs(prob["f"].to(DEV), None)
+    xd, info_d = S.solve(b, tol=1e-8)
+    bh = b.cpu().numpy().copy()
+    xh = np.zeros_like(bh)
+    info_h = smg.sqmr_solve(S.h, bh, xh, tol=1e-8)
+    assert info_h.iterations == info_d.iterations
+    assert rel_err(xh, xd.cpu().numpy()) == 0.0
+
+
+def test_residual_norm_entry():
+    o, S = pair((24, 16, 20))
+    b, x = rand_masked(o, 19), rand_masked(o, 20)
+    ref = np.linalg.norm(b - o.apply(x))
+    assert abs(smg.stokes_residual_norm(S.h, cuda(b), cuda(x)) - ref) <= 1e-12 * ref
+
+
+# ---------------------------------------------------------------------------------------------- edges
+
+def test_zero_rhs_gives_zero_solution():
+    o, S = pair((16, 16, 16))
+    b = torch.zeros(o.n(), dtype=torch.float64, device=DEV)
+    x0 = cuda(rand_masked(o, 21))
+    x, info = S.solve(b, x0=x0)
+    assert info.status == 0 and float(torch.max(torch.abs(x))) == 0.0
+
+
+def test_max_iter_zero_and_nan():
+    o, S = pair((16, 16, 16))
+    b = cuda(rand_masked(o, 22))
+    x = torch.zeros_like(b)
+    info = smg.sqmr_solve(S.h, b, x, tol=1e-8, max_iter=0, check=False)
+    assert info.status == smg.ERR_NOT_CONVERGED
+    b[5] = float("nan")
+    info = smg.sqmr_solve(S.h, b, x, tol=1e-8, max_iter=5, check=False)
+    assert info.status == smg.ERR_NAN
+
+
+def test_invalid_arguments():
+    with pytest.raises(smg.StokesError) as e:
+        smg.Stokes(1, 4, 4)
+    assert e.value.code == smg.ERR_INVALID_ARG
+    with pytest.raises(smg.StokesError):
+        smg.Stokes(8, viscosity=0.0)
+    with pytest.raises(smg.StokesError):
+        smg.Stokes(9, 9, 9, levels=2)  # odd dimensions cannot be coarsened
+    with pytest.raises(smg.StokesError) as e:
+        smg.Stokes(64, levels=1)  # dense coarsest solve of a 64^3 grid is refused
+    assert e.value.code == smg.ERR_INVALID_ARG
+
+
+def test_smallest_grid_solve():
+    o, S = pair((2, 2, 2))
+    b = rand_masked(o, 23)
+    b[o.n() - 8:] -= b[o.n() - 8:].mean()
+    x_ref, rc, it, _, _ = o.sqmr(b, tol=1e-12, maxit=50)
+    x, info = S.solve(cuda(b), tol=1e-12, max_iter=50)
+    assert info.status == 0 and rel_err(x, x_ref) < 1e-10
+
+
+# ---------------------------------------------------------------------------------------------- full size
+
+@pytest.fixture(scope="module")
+def big():
+    n = 256
+    o = oracle.Oracle(n, coarsest_max=8)
+    S = smg.Stokes(n)
+    return n, o, S
+
+
+def test_full_size_apply_parity(big):
+    n, o, S = big
+    x = rand_masked(o, 24)
+    assert rel_err(S.apply(cuda(x)), o.apply(x)) < 1e-13
+
+
+def test_full_size_vcycle_parity(big):
+    # one V-cycle at 256^3 in the bench's launch configuration (CUDA graph), against the oracle
+    n, o, S = big
+    s = rand_masked(o, 25)
+    assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-11
+
+
+def test_full_size_solve_properties(big):
+    n, o, S = big
+    prob = synthetic.bumps(n, seed=0, device=DEV)
+    b = S.rhs(prob["f"], None)
+    x, info = S.solve(b, tol=1e-8, max_iter=100)
+    assert info.status == 0 and info.rel_residual < 1e-8
+    r = torch.zeros_like(b)
+    smg.stokes_apply(S.h, x, r)
+    assert float(torch.linalg.norm(b - r) / torch.linalg.norm(b)) < 1e-8
+    nf = S.n - n ** 3
+    assert abs(float(x[nf:].mean())) < 1e-12 * float(torch.max(torch.abs(x[nf:])))
