@@ -228,6 +228,9 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 V-cycle solve beside the headline")
+    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle"],
+                    help="vcycle: only time mg_precondition (one V-cycle per step) -- for profiler captures")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of --mode vcycle")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -251,6 +254,24 @@ def main():
 
     n = args.n
     npk = packed_len(n)
+    if args.mode == "vcycle":
+        S = smg.Stokes(n, precision=smg.PREC_FP32 if args.precision == "fp32" else smg.PREC_FP64)
+        sv = S.rhs(synthetic.bumps(n, seed=0, device=dev)["f"], None)
+        tv = torch.empty_like(sv)
+        for _ in range(args.warmup):
+            smg.mg_precondition(S.h, sv, tv)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            smg.mg_precondition(S.h, sv, tv)
+        e1.record()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"mode": "vcycle", "n": n, "precision": args.precision, "steps": args.steps,
+                              "ms_per_vcycle": e0.elapsed_time(e1) / args.steps}), flush=True)
+        S.close()
+        return
     seeds = [(rank * 1000 + s) % 5 for s in range(5)]
     rhs = {}
     S32 = smg.Stokes(n, precision=smg.PREC_FP32)

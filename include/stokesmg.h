@@ -54,7 +54,7 @@ extern "C" {
 typedef struct stokes_s *stokes_t;
 
 typedef struct {
-    int nx, ny, nz;   /* interior cells per axis (>= 2) */
+    int nx, ny, nz;   /* interior cells per axis (2 <= nx, ny <= 2047, 2 <= nz <= 1023) */
     double h;         /* cell size (> 0); <= 0 selects 1/nx (unit-width box) */
     int levels;       /* multigrid levels; 0 = automatic: halve while every dimension is even and
                          one exceeds coarsest_max (Alg. 1; 128^3 -> 5 levels) */
@@ -162,7 +162,8 @@ int stokes_coarse_solve(stokes_t h, const double *b, double *x, void *stream);
 #define STOKES_K_RESTRICT 13
 #define STOKES_K_PROLONG 14
 #define STOKES_K_COARSE 15
-#define STOKES_K_COUNT 16
+#define STOKES_K_DGS_P_BWD_PREP 16
+#define STOKES_K_COUNT 17
 int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launches_all, double *ms_level0,
                              int *launches_level0, void *stream);
 

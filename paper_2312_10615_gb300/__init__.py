@@ -28,7 +28,8 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
 
 # kernel kinds reported by stokes_profile_iteration (STOKES_K_* in the header)
 KERNEL_KINDS = ["apply_dot", "update_s", "dot2", "update_x", "scalars", "memset", "vanka_compute", "vanka_apply",
-                "dgs_u", "dgs_p_fwd", "dgs_p_gather", "dgs_p_bwd", "residual", "restrict", "prolong", "coarse"]
+                "dgs_u", "dgs_p_fwd", "dgs_p_gather", "dgs_p_bwd", "residual", "restrict", "prolong", "coarse",
+                "dgs_p_bwd_prep"]
 
 
 class stokes_grid_t(ctypes.Structure):

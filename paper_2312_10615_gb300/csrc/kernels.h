@@ -16,7 +16,9 @@ void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaS
 template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s);
 template <class T> void launch_dgs_p_fwd(const Lev &L, T *x, const T *b, T *delta, int colour, cudaStream_t s);
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s);
-template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *b, int colour, cudaStream_t s);
+// backward pressure colours read g = b - Au (faces) and h = b - Bu (cells) precomputed into gh
+template <class T> void launch_dgs_p_bwd_prep(const Lev &L, const T *x, const T *b, T *gh, cudaStream_t s);
+template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s);
 // one colour of the multiplicative Vanka sweep on V1 (compute corrections, then add them)
 template <class T>
 void launch_vanka_compute(const Lev &L, const T *x, const T *b, const int *cells, int ncell, const T *kinv, T *corr,
@@ -44,16 +46,19 @@ struct SqmrState {
 constexpr int kRedBlocks = 1184;  // 152 SMs x 8 resident 256-thread blocks: grid of every reduction kernel
 constexpr int kRedParts = 3;      // partial sums per block
 
-// w = L q (FP64, gamma = 0) with per-block partials of q.w ; unknowns only
-void launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s);
-// w = b - L x with partials of |w|^2
-void launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s);
+// w = L q (FP64, gamma = 0) with per-block partials of q.w ; unknowns only.  Returns the number
+// of partials written (reduce_parts(L)); the 1D vector kernels below write kRedBlocks.
+int reduce_parts(const Lev &L);
+int launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s);
+// w = b - L x (w may be null) with partials of |b - Lx|^2
+int launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s);
 // partials of a.a (and optionally a.b)
 template <class T> void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s);
 // scalar stages on one thread block: 0 alpha (after q.Lq), 1 nu/c/tau/beta (after |t|^2, s.t),
 // 2 residual norm (after |r|^2), 3 init (after |t|^2, s.t of the first V-cycle), 4 |b|^2, 5 pressure mean
-void launch_scalars(int stage, const double *partials, SqmrState *st, double *host_out, cudaStream_t s);
-void launch_scalars_aux(int stage, const double *partials, SqmrState *st, double *host_out, double aux,
+void launch_scalars(int stage, const double *partials, int nparts, SqmrState *st, double *host_out,
+                    cudaStream_t s);
+void launch_scalars_aux(int stage, const double *partials, int nparts, SqmrState *st, double *host_out, double aux,
                         cudaStream_t s);
 // s -= alpha w ; optionally b32 = (T) s for a lower-precision V-cycle
 template <class T>

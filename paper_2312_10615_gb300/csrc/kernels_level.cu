@@ -3,24 +3,31 @@
 // Gauss-Seidel (Alg. 2, Eq. ldist, App. A), 8-colour multiplicative Vanka (Sec. 3.2, App. C,
 // Sec. 6), restriction / prolongation (Sec. 2) and the exact coarsest solve (Alg. 1).
 //
-// Every kernel is bandwidth-shaped: one thread per unknown (or per cell of a colour), coalesced
-// along x, stencil neighbours served by L1/L2.  No tensor cores: nothing here is a contraction.
+// Every kernel is bandwidth-shaped: 32 x 8 thread blocks over (x, y) of one z-plane (x fastest,
+// so a warp reads one 128-byte line of FP32 values), the component folded into gridDim.y, 32-bit
+// coordinates taken straight from the block/thread indices (no integer division), 64-bit only in
+// the final address.  No tensor cores: nothing here is a contraction.
 #include "kernels.h"
 
 namespace smg {
 
 namespace {
-constexpr int kBlock = 256;
+constexpr int BX = 32, BY = 8;
+const dim3 kBlock3(BX, BY, 1);
 
-inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
 
-inline long long comp_box(const Lev &L, int c) {
-    return (long long)ext(L, c, 0) * ext(L, c, 1) * ext(L, c, 2);
-}
-inline long long max_box(const Lev &L, int ncomp) {
-    long long m = 0;
-    for (int c = 0; c < ncomp; ++c) m = comp_box(L, c) > m ? comp_box(L, c) : m;
-    return m;
+// geometry of a launch over the packed entries of ncomp components: grid (x tiles, y tiles x ncomp, z)
+struct Geo {
+    dim3 grid;
+    int gy;  // y tiles per component
+};
+inline Geo geo_components(const Lev &L, int ncomp) {
+    int mx = L.nx + 1, my = L.ny + 1, mz = L.nz + 1;
+    Geo g;
+    g.gy = cdiv(my, BY);
+    g.grid = dim3(cdiv(mx, BX), g.gy * ncomp, mz);
+    return g;
 }
 
 // V2 index ranges of the box problem: faces of component c with normal index in [2, n-2] and
@@ -33,7 +40,6 @@ __host__ __device__ inline void v2_face_range(const Lev &L, int c, int lo[3], in
         if (cnt[d] < 0) cnt[d] = 0;
     }
 }
-
 // cells of colour (bx, by, bz) inside the V2 cell range [1, n-2]
 __host__ __device__ inline void v2_colour_range(const Lev &L, int colour, int lo[3], int cnt[3]) {
     int n[3] = {L.nx, L.ny, L.nz};
@@ -43,28 +49,30 @@ __host__ __device__ inline void v2_colour_range(const Lev &L, int colour, int lo
         cnt[d] = (n[d] - 2 >= lo[d]) ? (n[d] - 2 - lo[d]) / 2 + 1 : 0;
     }
 }
-
 __device__ __forceinline__ bool in_v2_cell(const Lev &L, int i, int j, int k) {
     return i >= 1 && j >= 1 && k >= 1 && i <= L.nx - 2 && j <= L.ny - 2 && k <= L.nz - 2;
 }
-
 __device__ __forceinline__ long long cell_lin(const Lev &L, int i, int j, int k) {
     return i + (long long)L.nx * (j + (long long)L.ny * k);
+}
+// (c, i, j, k) of the calling thread in a geo_components launch; false if outside component c's box
+__device__ __forceinline__ bool thread_entry(const Lev &L, int gy, int &c, int &i, int &j, int &k) {
+    c = blockIdx.y / gy;
+    i = blockIdx.x * BX + threadIdx.x;
+    j = (blockIdx.y - c * gy) * BY + threadIdx.y;
+    k = blockIdx.z;
+    return i < ext(L, c, 0) && j < ext(L, c, 1) && k < ext(L, c, 2);
 }
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// y = L~x or b - L~x on every packed entry (0 off the unknowns); blockIdx.y = component
+// y = L~x or b - L~x on every packed entry (0 off the unknowns)
 template <class T>
-__global__ void __launch_bounds__(256) k_apply(Lev L, const T *__restrict__ x, const T *__restrict__ b,
+__global__ void __launch_bounds__(256) k_apply(Lev L, int gy, const T *__restrict__ x, const T *__restrict__ b,
                                                T *__restrict__ y, Coef<T> K) {
-    int c = blockIdx.y;
-    int ex = ext(L, c, 0), ey = ext(L, c, 1), ez = ext(L, c, 2);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)ex * ey * ez) return;
-    int i, j, k;
-    decode3(t, ex, ey, i, j, k);
-    long long q = L.off[c] + t;
+    int c, i, j, k;
+    if (!thread_entry(L, gy, c, i, j, k)) return;
+    long long q = pidx(L, c, i, j, k);
     if (!active(L, c, i, j, k)) {
         y[q] = T(0);
         return;
@@ -74,8 +82,8 @@ __global__ void __launch_bounds__(256) k_apply(Lev L, const T *__restrict__ x, c
 }
 
 template <class T> void launch_apply(const Lev &L, const T *x, const T *b, T *y, double gam, cudaStream_t s) {
-    dim3 grid(blocks_for(max_box(L, 4)), 4);
-    k_apply<T><<<grid, kBlock, 0, s>>>(L, x, b, y, coef<T>(L, gam));
+    Geo g = geo_components(L, 4);
+    k_apply<T><<<g.grid, kBlock3, 0, s>>>(L, g.gy, x, b, y, coef<T>(L, gam));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -88,15 +96,11 @@ __device__ __forceinline__ long long gidx(const Lev &L, int c, int i, int j, int
     return G2 + (i + 1) + (nx + 2) * ((j + 1) + (ny + 2) * (long long)k);
 }
 
-__global__ void __launch_bounds__(256) k_rhs(Lev L, const double *__restrict__ f, const double *__restrict__ g,
+__global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__restrict__ f, const double *__restrict__ g,
                                              double *__restrict__ b, Coef<double> K) {
-    int c = blockIdx.y;
-    int ex = ext(L, c, 0), ey = ext(L, c, 1), ez = ext(L, c, 2);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)ex * ey * ez) return;
-    int i, j, k;
-    decode3(t, ex, ey, i, j, k);
-    long long q = L.off[c] + t;
+    int c, i, j, k;
+    if (!thread_entry(L, gy, c, i, j, k)) return;
+    long long q = pidx(L, c, i, j, k);
     if (!active(L, c, i, j, k)) {
         b[q] = 0.0;
         return;
@@ -121,43 +125,44 @@ __global__ void __launch_bounds__(256) k_rhs(Lev L, const double *__restrict__ f
 }
 
 void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaStream_t s) {
-    dim3 grid(blocks_for(max_box(L, 4)), 4);
-    k_rhs<<<grid, kBlock, 0, s>>>(L, f, g, b, coef<double>(L, 0.0));
+    Geo gg = geo_components(L, 4);
+    k_rhs<<<gg.grid, kBlock3, 0, s>>>(L, gg.gy, f, g, b, coef<double>(L, 0.0));
 }
 
 // ------------------------------------------------------------------------------------------
 // Alg. 2 velocity block: V2 faces of one parity (i+j+k), u, v, w together (A does not couple
 // components; same-parity faces are not A-neighbours, pressures are not written) -- in place.
+// Thread x covers every other face of a row so no thread idles.
 template <class T>
-__global__ void __launch_bounds__(256) k_dgs_u(Lev L, T *__restrict__ x, const T *__restrict__ b, int parity,
+__global__ void __launch_bounds__(256) k_dgs_u(Lev L, int gy, T *__restrict__ x, const T *__restrict__ b, int parity,
                                                Coef<T> K) {
-    int c = blockIdx.y;
+    int c = blockIdx.y / gy;
     int lo[3], cnt[3];
     v2_face_range(L, c, lo, cnt);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)cnt[0] * cnt[1] * cnt[2]) return;
-    int i, j, k;
-    decode3(t, cnt[0], cnt[1], i, j, k);
-    i += lo[0];
-    j += lo[1];
-    k += lo[2];
-    if (((i + j + k) & 1) != parity) return;
+    int j = lo[1] + (blockIdx.y - c * gy) * BY + threadIdx.y;
+    int k = lo[2] + blockIdx.z;
+    if (j >= lo[1] + cnt[1] || k >= lo[2] + cnt[2]) return;
+    int i = lo[0] + 2 * (blockIdx.x * BX + threadIdx.x);
+    i += (i + j + k + parity) & 1;
+    if (i >= lo[0] + cnt[0]) return;
     long long q = pidx(L, c, i, j, k);
     T r = b[q] - face_Lx(x, L, c, i, j, k, K);
     x[q] += r / (T(6) * K.eh2);
 }
 
 template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s) {
-    long long m = 0;
+    int mx = 0, my = 0, mz = 0;
     for (int c = 0; c < 3; ++c) {
         int lo[3], cnt[3];
         v2_face_range(L, c, lo, cnt);
-        long long v = (long long)cnt[0] * cnt[1] * cnt[2];
-        m = v > m ? v : m;
+        if (cnt[0] * cnt[1] * cnt[2] == 0) return;
+        mx = cnt[0] > mx ? cnt[0] : mx;
+        my = cnt[1] > my ? cnt[1] : my;
+        mz = cnt[2] > mz ? cnt[2] : mz;
     }
-    if (m == 0) return;
-    dim3 grid(blocks_for(m), 3);
-    k_dgs_u<T><<<grid, kBlock, 0, s>>>(L, x, b, parity, coef<T>(L, L.gamma));
+    int gy = cdiv(my, BY);
+    dim3 grid(cdiv((mx + 1) / 2, BX), gy * 3, mz);
+    k_dgs_u<T><<<grid, kBlock3, 0, s>>>(L, gy, x, b, parity, coef<T>(L, L.gamma));
 }
 
 // Alg. 2 pressure block, one colour (i mod 2, j mod 2, k mod 2):
@@ -172,22 +177,17 @@ __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, con
                                                    T *__restrict__ delta, int colour, Coef<T> K, T dP) {
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)cnt[0] * cnt[1] * cnt[2]) return;
-    int i, j, k;
-    decode3(t, cnt[0], cnt[1], i, j, k);
-    i = lo[0] + 2 * i;
-    j = lo[1] + 2 * j;
-    k = lo[2] + 2 * k;
+    int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
+    if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
+    int i = lo[0] + 2 * ti, j = lo[1] + 2 * tj, k = lo[2] + 2 * tk;
     long long cl = cell_lin(L, i, j, k);
     long long qp = L.off[3] + cl;
-    T p = x[qp];
     long long sy = L.nx, sz = (long long)L.nx * L.ny;
     T g = T(0);
     if (colour & 1) g += delta[cl - 1] + delta[cl + 1];
     if (colour & 2) g += delta[cl - sy] + delta[cl + sy];
     if (colour & 4) g += delta[cl - sz] + delta[cl + sz];
-    p -= K.eh2 * g;
+    T p = x[qp] - K.eh2 * g;
     long long u0 = pidx(L, 0, i, j, k), v0 = pidx(L, 1, i, j, k), w0 = pidx(L, 2, i, j, k);
     long long vs = L.nx, ws = (long long)L.nx * L.ny;
     T div = (x[u0 + 1] - x[u0]) + (x[v0 + vs] - x[v0]) + (x[w0 + ws] - x[w0]);
@@ -207,10 +207,9 @@ __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, con
 template <class T>
 __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, const T *__restrict__ delta,
                                                       Coef<T> K) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)L.nx * L.ny * L.nz) return;
-    int i, j, k;
-    decode3(t, L.nx, L.ny, i, j, k);
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny || k >= L.nz) return;
+    long long t = cell_lin(L, i, j, k);
     bool v2 = in_v2_cell(L, i, j, k);
     int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
     long long sy = L.nx, sz = (long long)L.nx * L.ny;
@@ -230,38 +229,65 @@ __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, 
     if (g != T(0)) x[L.off[3] + t] -= K.eh2 * g;
 }
 
-// Eq. (ldist) backward sweep, one pressure colour: p_c += M_{.c}^T (b - L~x) / d with
-//   M_{.c}^T r = sum_axes (r_high_face - r_low_face)/h + eta/h^2 (6 r_c - sum of the 6 neighbour r)
-// Only p_c changes; same-colour cells read none of each other's values.
+// Eq. (ldist) backward sweep, pressure block.  Only pressures change during its colours, so the
+// parts of the residual that do not depend on p are computed once (k_dgs_p_bwd_prep):
+//   g_f = b_f - (A u)_f on every unknown face,   h_c = b_c - (B u)_c on every cell,
+// and a colour then needs r_f = g_f - (p_plus - p_minus)/h and r_n = h_n + gamma p_n only:
+//   p_c += [ sum_axes (r_high_face - r_low_face)/h + eta/h^2 (6 r_c - sum of the 6 neighbour r) ] / d
+// (M_{.c}^T r with the full column of M).  Same-colour cells read none of each other's values.
 template <class T>
-__global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const T *__restrict__ b, int colour,
+__global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, int gy, const T *__restrict__ x,
+                                                        const T *__restrict__ b, T *__restrict__ gh, Coef<T> K) {
+    int c, i, j, k;
+    if (!thread_entry(L, gy, c, i, j, k)) return;
+    long long q = pidx(L, c, i, j, k);
+    if (!active(L, c, i, j, k)) {
+        gh[q] = T(0);
+        return;
+    }
+    T v;
+    if (c < 3) {
+        T s = T(6) * x[q];
+        s -= xget(x, L, c, i - 1, j, k);
+        s -= xget(x, L, c, i + 1, j, k);
+        s -= xget(x, L, c, i, j - 1, k);
+        s -= xget(x, L, c, i, j + 1, k);
+        s -= xget(x, L, c, i, j, k - 1);
+        s -= xget(x, L, c, i, j, k + 1);
+        v = b[q] - K.eh2 * s;
+    } else {
+        T div = xget(x, L, 0, i + 1, j, k) - xget(x, L, 0, i, j, k) + xget(x, L, 1, i, j + 1, k) -
+                xget(x, L, 1, i, j, k) + xget(x, L, 2, i, j, k + 1) - xget(x, L, 2, i, j, k);
+        v = b[q] + K.ih * div;
+    }
+    gh[q] = v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const T *__restrict__ gh, int colour,
                                                    Coef<T> K, T dP) {
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)cnt[0] * cnt[1] * cnt[2]) return;
-    int i, j, k;
-    decode3(t, cnt[0], cnt[1], i, j, k);
-    i = lo[0] + 2 * i;
-    j = lo[1] + 2 * j;
-    k = lo[2] + 2 * k;
-    T sf = T(0);
-    sf += b[pidx(L, 0, i + 1, j, k)] - face_Lx(x, L, 0, i + 1, j, k, K);
-    sf -= b[pidx(L, 0, i, j, k)] - face_Lx(x, L, 0, i, j, k, K);
-    sf += b[pidx(L, 1, i, j + 1, k)] - face_Lx(x, L, 1, i, j + 1, k, K);
-    sf -= b[pidx(L, 1, i, j, k)] - face_Lx(x, L, 1, i, j, k, K);
-    sf += b[pidx(L, 2, i, j, k + 1)] - face_Lx(x, L, 2, i, j, k + 1, K);
-    sf -= b[pidx(L, 2, i, j, k)] - face_Lx(x, L, 2, i, j, k, K);
-    T rc = b[pidx(L, 3, i, j, k)] - cell_Lx(x, L, i, j, k, K);
-    T rn = T(0);
-    rn += b[pidx(L, 3, i - 1, j, k)] - cell_Lx(x, L, i - 1, j, k, K);
-    rn += b[pidx(L, 3, i + 1, j, k)] - cell_Lx(x, L, i + 1, j, k, K);
-    rn += b[pidx(L, 3, i, j - 1, k)] - cell_Lx(x, L, i, j - 1, k, K);
-    rn += b[pidx(L, 3, i, j + 1, k)] - cell_Lx(x, L, i, j + 1, k, K);
-    rn += b[pidx(L, 3, i, j, k - 1)] - cell_Lx(x, L, i, j, k - 1, K);
-    rn += b[pidx(L, 3, i, j, k + 1)] - cell_Lx(x, L, i, j, k + 1, K);
-    T s = K.ih * sf + K.eh2 * (T(6) * rc - rn);
-    x[pidx(L, 3, i, j, k)] += s / dP;
+    int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
+    if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
+    int i = lo[0] + 2 * ti, j = lo[1] + 2 * tj, k = lo[2] + 2 * tk;
+    long long sy = L.nx, sz = (long long)L.nx * L.ny;
+    long long qc = L.off[3] + cell_lin(L, i, j, k);
+    const T *p = x;
+    T pc = p[qc], pxm = p[qc - 1], pxp = p[qc + 1], pym = p[qc - sy], pyp = p[qc + sy], pzm = p[qc - sz],
+      pzp = p[qc + sz];
+    long long u0 = pidx(L, 0, i, j, k), v0 = pidx(L, 1, i, j, k), w0 = pidx(L, 2, i, j, k);
+    long long vs = L.nx, ws = (long long)L.nx * L.ny;
+    // face residuals r_f = g_f - (p_plus - p_minus)/h
+    T rul = gh[u0] - K.ih * (pc - pxm), ruh = gh[u0 + 1] - K.ih * (pxp - pc);
+    T rvl = gh[v0] - K.ih * (pc - pym), rvh = gh[v0 + vs] - K.ih * (pyp - pc);
+    T rwl = gh[w0] - K.ih * (pc - pzm), rwh = gh[w0 + ws] - K.ih * (pzp - pc);
+    // cell residuals r_n = h_n + gamma p_n
+    T rc = gh[qc] + K.gam * pc;
+    T rn = (gh[qc - 1] + K.gam * pxm) + (gh[qc + 1] + K.gam * pxp) + (gh[qc - sy] + K.gam * pym) +
+           (gh[qc + sy] + K.gam * pyp) + (gh[qc - sz] + K.gam * pzm) + (gh[qc + sz] + K.gam * pzp);
+    T s = K.ih * ((ruh - rul) + (rvh - rvl) + (rwh - rwl)) + K.eh2 * (T(6) * rc - rn);
+    x[qc] = pc + s / dP;
 }
 
 template <class T> static T dgs_pressure_diag(const Lev &L) {
@@ -271,21 +297,24 @@ template <class T> static T dgs_pressure_diag(const Lev &L) {
 template <class T> void launch_dgs_p_fwd(const Lev &L, T *x, const T *b, T *delta, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
-    long long m = (long long)cnt[0] * cnt[1] * cnt[2];
-    if (m == 0) return;
-    k_dgs_p_fwd<T><<<blocks_for(m), kBlock, 0, s>>>(L, x, b, delta, colour, coef<T>(L, L.gamma),
-                                                     dgs_pressure_diag<T>(L));
+    if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
+    dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
+    k_dgs_p_fwd<T><<<grid, kBlock3, 0, s>>>(L, x, b, delta, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
 }
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s) {
-    long long m = (long long)L.nx * L.ny * L.nz;
-    k_dgs_p_gather<T><<<blocks_for(m), kBlock, 0, s>>>(L, x, delta, coef<T>(L, L.gamma));
+    dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz);
+    k_dgs_p_gather<T><<<grid, kBlock3, 0, s>>>(L, x, delta, coef<T>(L, L.gamma));
 }
-template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *b, int colour, cudaStream_t s) {
+template <class T> void launch_dgs_p_bwd_prep(const Lev &L, const T *x, const T *b, T *gh, cudaStream_t s) {
+    Geo g = geo_components(L, 4);
+    k_dgs_p_bwd_prep<T><<<g.grid, kBlock3, 0, s>>>(L, g.gy, x, b, gh, coef<T>(L, L.gamma));
+}
+template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
-    long long m = (long long)cnt[0] * cnt[1] * cnt[2];
-    if (m == 0) return;
-    k_dgs_p_bwd<T><<<blocks_for(m), kBlock, 0, s>>>(L, x, b, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
+    if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
+    dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
+    k_dgs_p_bwd<T><<<grid, kBlock3, 0, s>>>(L, x, gh, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -293,6 +322,13 @@ template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *b, int col
 // p_c; correction = (C L~ C^T)^{-1} C (b - L~x) with the inverse of the cell's configuration
 // (which faces are unknowns: 6-bit mask, 64 pre-factorised 7x7 inverses per level, Sec. 6).
 // Corrections of one colour are computed from the pre-colour state, stored, then added.
+// Cell lists hold packed coordinates i | j << 11 | k << 22.
+__device__ __forceinline__ void unpack_cell(int w, int &i, int &j, int &k) {
+    i = w & 2047;
+    j = (w >> 11) & 2047;
+    k = (w >> 22) & 1023;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const T *__restrict__ b,
                                                        const int *__restrict__ cells, int ncell,
@@ -300,9 +336,8 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
                                                        Coef<T> K) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncell) return;
-    int cl = cells[t];
     int i, j, k;
-    decode3(cl, L.nx, L.ny, i, j, k);
+    unpack_cell(cells[t], i, j, k);
     T r[7];
     int cfg = 0;
 #pragma unroll
@@ -329,9 +364,8 @@ __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, c
                                                      int ncell, const T *__restrict__ corr, int cap) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncell) return;
-    int cl = cells[t];
     int i, j, k;
-    decode3(cl, L.nx, L.ny, i, j, k);
+    unpack_cell(cells[t], i, j, k);
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
         int d = a >> 1, side = a & 1;
@@ -345,13 +379,12 @@ template <class T>
 void launch_vanka_compute(const Lev &L, const T *x, const T *b, const int *cells, int ncell, const T *kinv, T *corr,
                           int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    k_vanka_compute<T><<<blocks_for(ncell), kBlock, 0, s>>>(L, x, b, cells, ncell, kinv, corr, cap,
-                                                             coef<T>(L, L.gamma));
+    k_vanka_compute<T><<<cdiv(ncell, 256), 256, 0, s>>>(L, x, b, cells, ncell, kinv, corr, cap, coef<T>(L, L.gamma));
 }
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    k_vanka_apply<T><<<blocks_for(ncell), kBlock, 0, s>>>(L, x, cells, ncell, corr, cap);
+    k_vanka_apply<T><<<cdiv(ncell, 256), 256, 0, s>>>(L, x, cells, ncell, corr, cap);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -359,92 +392,113 @@ void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T
 // weight 1 from a coincident coarse face or 1/2 + 1/2 from the two coarse faces around it along
 // its normal, and 3/4 (coarse row containing it) + 1/4 (next coarse row on the far side) along
 // each tangential axis; coarse entries that are not unknowns contribute 0.  R = P^T / 8.
+// component C of the face transfers, with every index known at compile time
+template <class T, int C>
+__device__ __forceinline__ T restrict_face(const Lev &F, const T *__restrict__ rf, int I, int J, int Kk) {
+    const T nw[3] = {T(0.5), T(1), T(0.5)};
+    const T tw[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
+    T s = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+            T sr = T(0);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                // offsets: a along the normal axis C, bb and g along the two tangential axes
+                int di = C == 0 ? a - 1 : bb - 1;
+                int dj = C == 0 ? bb - 1 : (C == 1 ? a - 1 : g - 1);
+                int dk = C == 2 ? a - 1 : g - 1;
+                sr += tw[g] * xget(rf, F, C, 2 * I + di, 2 * J + dj, 2 * Kk + dk);
+            }
+            s += nw[a] * tw[bb] * sr;
+        }
+    return s * T(0.125);
+}
+
 template <class T>
-__global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, const T *__restrict__ rf, T *__restrict__ bc) {
-    int c = blockIdx.y;
-    int ex = ext(C, c, 0), ey = ext(C, c, 1), ez = ext(C, c, 2);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)ex * ey * ez) return;
-    int I, J, Kk;
-    decode3(t, ex, ey, I, J, Kk);
-    long long q = C.off[c] + t;
+__global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const T *__restrict__ rf,
+                                                  T *__restrict__ bc) {
+    int c, I, J, Kk;
+    if (!thread_entry(C, gy, c, I, J, Kk)) return;
+    long long q = pidx(C, c, I, J, Kk);
     if (!active(C, c, I, J, Kk)) {
         bc[q] = T(0);
         return;
     }
-    if (c == 3) {
+    T v;
+    switch (c) {
+    case 0: v = restrict_face<T, 0>(F, rf, I, J, Kk); break;
+    case 1: v = restrict_face<T, 1>(F, rf, I, J, Kk); break;
+    case 2: v = restrict_face<T, 2>(F, rf, I, J, Kk); break;
+    default: {
         T s = T(0);
 #pragma unroll
         for (int m = 0; m < 8; ++m)
             s += rf[pidx(F, 3, 2 * I + (m & 1), 2 * J + ((m >> 1) & 1), 2 * Kk + ((m >> 2) & 1))];
-        bc[q] = s * T(0.125);
-        return;
+        v = s * T(0.125);
     }
-    const int no[3] = {-1, 0, 1};
-    const T nw[3] = {T(0.5), T(1), T(0.5)};
-    const int to[4] = {-1, 0, 1, 2};
-    const T tw[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
-    int base[3] = {2 * I, 2 * J, 2 * Kk};
-    int t1 = c == 0 ? 1 : 0, t2 = c == 2 ? 1 : 2;  // the two tangential axes
+    }
+    bc[q] = v;
+}
+
+// 1D prolongation weights along one axis: normal axis (coincident: {I, 1}; between: {I0, I1, 1/2})
+// or tangential axis ({row, 3/4}, {far-side row, 1/4})
+struct W2 {
+    int i0, i1;
+    float w0, w1;
+};
+__device__ __forceinline__ W2 pw_axis(int f, bool normal) {
+    W2 r;
+    if (normal) {
+        if ((f & 1) == 0) { r.i0 = f >> 1; r.i1 = -1; r.w0 = 1.f; r.w1 = 0.f; }
+        else { r.i0 = (f - 1) >> 1; r.i1 = (f + 1) >> 1; r.w0 = r.w1 = 0.5f; }
+    } else {
+        r.i0 = f >> 1; r.w0 = 0.75f;
+        r.i1 = (f & 1) == 0 ? (f >> 1) - 1 : (f >> 1) + 1; r.w1 = 0.25f;
+    }
+    return r;
+}
+
+template <class T, int CC>
+__device__ __forceinline__ T prolong_face(const Lev &C, const T *__restrict__ ec, int fi, int fj, int fk) {
+    W2 a = pw_axis(fi, CC == 0), b = pw_axis(fj, CC == 1), g = pw_axis(fk, CC == 2);
+    int ii[2] = {a.i0, a.i1}, jj[2] = {b.i0, b.i1}, kk[2] = {g.i0, g.i1};
+    T wi[2] = {T(a.w0), T(a.w1)}, wj[2] = {T(b.w0), T(b.w1)}, wk[2] = {T(g.w0), T(g.w1)};
     T s = T(0);
-    for (int a = 0; a < 3; ++a)
-        for (int bb = 0; bb < 4; ++bb)
-            for (int g = 0; g < 4; ++g) {
-                int f[3];
-                f[c] = base[c] + no[a];
-                f[t1] = base[t1] + to[bb];
-                f[t2] = base[t2] + to[g];
-                s += nw[a] * tw[bb] * tw[g] * xget(rf, F, c, f[0], f[1], f[2]);
-            }
-    bc[q] = s * T(0.125);
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y)
+#pragma unroll
+            for (int z = 0; z < 2; ++z)
+                s += wi[x] * wj[y] * wk[z] * xget(ec, C, CC, ii[x], jj[y], kk[z]);  // index -1 is never active
+    return s;
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_prolong(Lev F, Lev C, const T *__restrict__ ec, T *__restrict__ xf) {
-    int c = blockIdx.y;
-    int ex = ext(F, c, 0), ey = ext(F, c, 1), ez = ext(F, c, 2);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)ex * ey * ez) return;
-    int fi[3];
-    decode3(t, ex, ey, fi[0], fi[1], fi[2]);
-    if (!active(F, c, fi[0], fi[1], fi[2])) return;
-    long long q = F.off[c] + t;
-    if (c == 3) {
-        xf[q] += ec[pidx(C, 3, fi[0] / 2, fi[1] / 2, fi[2] / 2)];
-        return;
+__global__ void __launch_bounds__(256) k_prolong(Lev F, Lev C, int gy, const T *__restrict__ ec, T *__restrict__ xf) {
+    int c, fi, fj, fk;
+    if (!thread_entry(F, gy, c, fi, fj, fk)) return;
+    if (!active(F, c, fi, fj, fk)) return;
+    long long q = pidx(F, c, fi, fj, fk);
+    T v;
+    switch (c) {
+    case 0: v = prolong_face<T, 0>(C, ec, fi, fj, fk); break;
+    case 1: v = prolong_face<T, 1>(C, ec, fi, fj, fk); break;
+    case 2: v = prolong_face<T, 2>(C, ec, fi, fj, fk); break;
+    default: v = ec[pidx(C, 3, fi >> 1, fj >> 1, fk >> 1)];
     }
-    int ci[3][2];
-    T cw[3][2];
-    int cn[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (d == c) {
-            if ((fi[d] & 1) == 0) {
-                cn[d] = 1; ci[d][0] = fi[d] / 2; cw[d][0] = T(1);
-            } else {
-                cn[d] = 2; ci[d][0] = (fi[d] - 1) / 2; ci[d][1] = (fi[d] + 1) / 2; cw[d][0] = cw[d][1] = T(0.5);
-            }
-        } else {
-            cn[d] = 2;
-            ci[d][0] = fi[d] / 2; cw[d][0] = T(0.75);
-            ci[d][1] = (fi[d] & 1) == 0 ? fi[d] / 2 - 1 : fi[d] / 2 + 1; cw[d][1] = T(0.25);
-        }
-    }
-    T s = T(0);
-    for (int a = 0; a < cn[0]; ++a)
-        for (int bb = 0; bb < cn[1]; ++bb)
-            for (int g = 0; g < cn[2]; ++g)
-                s += cw[0][a] * cw[1][bb] * cw[2][g] * xget(ec, C, c, ci[0][a], ci[1][bb], ci[2][g]);
-    xf[q] += s;
+    xf[q] += v;
 }
 
 template <class T> void launch_restrict(const Lev &F, const Lev &C, const T *rf, T *bc, cudaStream_t s) {
-    dim3 grid(blocks_for(max_box(C, 4)), 4);
-    k_restrict<T><<<grid, kBlock, 0, s>>>(F, C, rf, bc);
+    Geo g = geo_components(C, 4);
+    k_restrict<T><<<g.grid, kBlock3, 0, s>>>(F, C, g.gy, rf, bc);
 }
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s) {
-    dim3 grid(blocks_for(max_box(F, 4)), 4);
-    k_prolong<T><<<grid, kBlock, 0, s>>>(F, C, ec, xf);
+    Geo g = geo_components(F, 4);
+    k_prolong<T><<<g.grid, kBlock3, 0, s>>>(F, C, g.gy, ec, xf);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -470,23 +524,19 @@ __global__ void __launch_bounds__(256) k_coarse(const int *__restrict__ cidx, in
 template <class T>
 void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, const T *b, T *x, cudaStream_t s) {
     (void)C;
-    int rows_per_block = kBlock / 32;
-    k_coarse<T><<<(nc + rows_per_block - 1) / rows_per_block, kBlock, nc * sizeof(double), s>>>(cidx, nc, kinv, b, x);
+    int rows_per_block = 256 / 32;
+    k_coarse<T><<<(nc + rows_per_block - 1) / rows_per_block, 256, nc * sizeof(double), s>>>(cidx, nc, kinv, b, x);
 }
 
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mask(Lev L, double *__restrict__ x) {
-    int c = blockIdx.y;
-    int ex = ext(L, c, 0), ey = ext(L, c, 1), ez = ext(L, c, 2);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)ex * ey * ez) return;
-    int i, j, k;
-    decode3(t, ex, ey, i, j, k);
-    if (!active(L, c, i, j, k)) x[L.off[c] + t] = 0.0;
+__global__ void __launch_bounds__(256) k_mask(Lev L, int gy, double *__restrict__ x) {
+    int c, i, j, k;
+    if (!thread_entry(L, gy, c, i, j, k)) return;
+    if (!active(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = 0.0;
 }
 void launch_mask(const Lev &L, double *x, cudaStream_t s) {
-    dim3 grid(blocks_for(max_box(L, 4)), 4);
-    k_mask<<<grid, kBlock, 0, s>>>(L, x);
+    Geo g = geo_components(L, 4);
+    k_mask<<<g.grid, kBlock3, 0, s>>>(L, g.gy, x);
 }
 
 template <class A, class B> __global__ void k_convert(long long n, const A *__restrict__ in, B *__restrict__ out) {
@@ -494,8 +544,8 @@ template <class A, class B> __global__ void k_convert(long long n, const A *__re
         out[t] = (B)in[t];
 }
 template <class A, class B> void launch_convert(long long n, const A *in, B *out, cudaStream_t s) {
-    long long nb = (n + kBlock - 1) / kBlock;
-    k_convert<A, B><<<(unsigned)(nb < 4736 ? nb : 4736), kBlock, 0, s>>>(n, in, out);
+    long long nb = (n + 255) / 256;
+    k_convert<A, B><<<(unsigned)(nb < 4736 ? nb : 4736), 256, 0, s>>>(n, in, out);
 }
 
 // explicit instantiations
@@ -504,6 +554,7 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template void launch_dgs_u<T>(const Lev &, T *, const T *, int, cudaStream_t);                                \
     template void launch_dgs_p_fwd<T>(const Lev &, T *, const T *, T *, int, cudaStream_t);                       \
     template void launch_dgs_p_gather<T>(const Lev &, T *, const T *, cudaStream_t);                              \
+    template void launch_dgs_p_bwd_prep<T>(const Lev &, const T *, const T *, T *, cudaStream_t);                 \
     template void launch_dgs_p_bwd<T>(const Lev &, T *, const T *, int, cudaStream_t);                            \
     template void launch_vanka_compute<T>(const Lev &, const T *, const T *, const int *, int, const T *, T *, int, \
                                           cudaStream_t);                                                          \

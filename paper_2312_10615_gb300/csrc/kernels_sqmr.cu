@@ -1,7 +1,7 @@
 // kernels_sqmr.cu -- FP64 kernels of MG-preconditioned SQMR (Tao & Sifakis, Alg. 4):
 // operator apply fused with q^T L q, fused vector recurrences, deterministic dot products
-// (fixed grid, warp shuffles, fixed-order final sum) and the scalar recurrences on the device,
-// so an iteration needs no host round trip except the convergence flag.
+// (per-block partials, warp shuffles, fixed-order final sum) and the scalar recurrences on the
+// device, so an iteration needs no host round trip except the convergence flag.
 #include <math.h>
 
 #include "kernels.h"
@@ -10,12 +10,14 @@ namespace smg {
 
 namespace {
 constexpr int kBlock = 256;
+constexpr int BX = 32, BY = 8;
 
-// sum NV values over the block (warp shuffles, then warp 0 over the per-warp sums) and store
-// them as partials[blockIdx.x * kRedParts + m]; fixed order, so the result is reproducible
-template <int NV> __device__ __forceinline__ void block_store(double (&v)[NV], double *partials) {
+// sum NV values over the block (warp shuffles, then warp 0 over the per-warp sums) and store them
+// as partials[slot * kRedParts + m]; fixed order, so the result is reproducible
+template <int NV> __device__ __forceinline__ void block_store(double (&v)[NV], double *partials, int slot) {
     __shared__ double sh[NV][kBlock / 32];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int m = 0; m < NV; ++m) {
 #pragma unroll
@@ -29,57 +31,69 @@ template <int NV> __device__ __forceinline__ void block_store(double (&v)[NV], d
             double s = lane < kBlock / 32 ? sh[m][lane] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) partials[blockIdx.x * kRedParts + m] = s;
+            if (lane == 0) partials[slot * kRedParts + m] = s;
         }
     }
 }
-
-__device__ __forceinline__ int comp_of(const Lev &L, long long q) {
-    return q < L.off[1] ? 0 : (q < L.off[2] ? 1 : (q < L.off[3] ? 2 : 3));
-}
-
-// (L x)_q on the unknown set (0 elsewhere), gamma = 0
-__device__ __forceinline__ double lx_at(const Lev &L, const double *__restrict__ x, long long q, const Coef<double> &K,
-                                        bool &act) {
-    int c = comp_of(L, q);
-    int i, j, k;
-    decode3(q - L.off[c], ext(L, c, 0), ext(L, c, 1), i, j, k);
-    act = active(L, c, i, j, k);
-    if (!act) return 0.0;
-    return c < 3 ? face_Lx(x, L, c, i, j, k, K) : cell_Lx(x, L, i, j, k, K);
-}
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_apply_dot(Lev L, const double *__restrict__ q, double *__restrict__ w,
+// 3D launch over the packed entries of the 4 components: blocks of 32 x 8 over (x, y), the
+// component folded into gridDim.y, each thread marching over z; one partial sum per block.
+int reduce_parts(const Lev &L) {
+    int gx = (L.nx + 1 + BX - 1) / BX, gy = (L.ny + 1 + BY - 1) / BY;
+    return gx * gy * 4;
+}
+
+__global__ void __launch_bounds__(256) k_apply_dot(Lev L, int gy, const double *__restrict__ q, double *__restrict__ w,
                                                    double *partials, Coef<double> K) {
+    int c = blockIdx.y / gy;
+    int i = blockIdx.x * BX + threadIdx.x, j = (blockIdx.y - c * gy) * BY + threadIdx.y;
     double v[1] = {0.0};
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < L.n; t += (long long)gridDim.x * blockDim.x) {
-        bool act;
-        double y = lx_at(L, q, t, K, act);
-        w[t] = y;
-        if (act) v[0] += q[t] * y;
+    if (i < ext(L, c, 0) && j < ext(L, c, 1)) {
+        int ez = ext(L, c, 2);
+        for (int k = 0; k < ez; ++k) {
+            long long t = pidx(L, c, i, j, k);
+            double y = 0.0;
+            if (active(L, c, i, j, k)) {
+                y = c < 3 ? face_Lx(q, L, c, i, j, k, K) : cell_Lx(q, L, i, j, k, K);
+                v[0] += q[t] * y;
+            }
+            w[t] = y;
+        }
     }
-    block_store<1>(v, partials);
+    block_store<1>(v, partials, blockIdx.x + gridDim.x * blockIdx.y);
 }
 
-__global__ void __launch_bounds__(256) k_residual_dot(Lev L, const double *__restrict__ b, const double *__restrict__ x,
-                                                      double *__restrict__ w, double *partials, Coef<double> K) {
+__global__ void __launch_bounds__(256) k_residual_dot(Lev L, int gy, const double *__restrict__ b,
+                                                      const double *__restrict__ x, double *__restrict__ w,
+                                                      double *partials, Coef<double> K) {
+    int c = blockIdx.y / gy;
+    int i = blockIdx.x * BX + threadIdx.x, j = (blockIdx.y - c * gy) * BY + threadIdx.y;
     double v[1] = {0.0};
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < L.n; t += (long long)gridDim.x * blockDim.x) {
-        bool act;
-        double y = lx_at(L, x, t, K, act);
-        double r = act ? b[t] - y : 0.0;
-        if (w) w[t] = r;
-        v[0] += r * r;
+    if (i < ext(L, c, 0) && j < ext(L, c, 1)) {
+        int ez = ext(L, c, 2);
+        for (int k = 0; k < ez; ++k) {
+            long long t = pidx(L, c, i, j, k);
+            double r = 0.0;
+            if (active(L, c, i, j, k)) r = b[t] - (c < 3 ? face_Lx(x, L, c, i, j, k, K) : cell_Lx(x, L, i, j, k, K));
+            if (w) w[t] = r;
+            v[0] += r * r;
+        }
     }
-    block_store<1>(v, partials);
+    block_store<1>(v, partials, blockIdx.x + gridDim.x * blockIdx.y);
 }
 
-void launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s) {
-    k_apply_dot<<<kRedBlocks, kBlock, 0, s>>>(L, q, w, partials, coef<double>(L, 0.0));
+int launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s) {
+    int gy = (L.ny + 1 + BY - 1) / BY;
+    dim3 grid((L.nx + 1 + BX - 1) / BX, gy * 4, 1);
+    k_apply_dot<<<grid, dim3(BX, BY, 1), 0, s>>>(L, gy, q, w, partials, coef<double>(L, 0.0));
+    return reduce_parts(L);
 }
-void launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s) {
-    k_residual_dot<<<kRedBlocks, kBlock, 0, s>>>(L, b, x, w, partials, coef<double>(L, 0.0));
+int launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s) {
+    int gy = (L.ny + 1 + BY - 1) / BY;
+    dim3 grid((L.nx + 1 + BX - 1) / BX, gy * 4, 1);
+    k_residual_dot<<<grid, dim3(BX, BY, 1), 0, s>>>(L, gy, b, x, w, partials, coef<double>(L, 0.0));
+    return reduce_parts(L);
 }
 
 // a.a and a.b
@@ -92,18 +106,18 @@ __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__
         v[0] += x * x;
         if (b) v[1] += x * b[t];
     }
-    block_store<2>(v, partials);
+    block_store<2>(v, partials, blockIdx.x);
 }
 template <class T> void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s) {
     k_dot2<T><<<kRedBlocks, kBlock, 0, s>>>(n, a, b, partials);
 }
 
-// scalar recurrences of Alg. 4 (one block; fixed-order sum of the kRedBlocks partials)
-__global__ void __launch_bounds__(256) k_scalars(int stage, const double *partials, SqmrState *st, double *host_out,
-                                                 double aux) {
+// scalar recurrences of Alg. 4 (one block; fixed-order sum of the nparts partials)
+__global__ void __launch_bounds__(256) k_scalars(int stage, const double *partials, int nparts, SqmrState *st,
+                                                 double *host_out, double aux) {
     __shared__ double sh[kRedParts][kBlock];
     double v[kRedParts] = {0.0, 0.0, 0.0};
-    for (int t = threadIdx.x; t < kRedBlocks; t += blockDim.x)
+    for (int t = threadIdx.x; t < nparts; t += blockDim.x)
 #pragma unroll
         for (int m = 0; m < kRedParts; ++m) v[m] += partials[t * kRedParts + m];
 #pragma unroll
@@ -174,12 +188,13 @@ __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partia
     }
 }
 
-void launch_scalars(int stage, const double *partials, SqmrState *st, double *host_out, cudaStream_t s) {
-    k_scalars<<<1, kBlock, 0, s>>>(stage, partials, st, host_out, 0.0);
+void launch_scalars(int stage, const double *partials, int nparts, SqmrState *st, double *host_out,
+                    cudaStream_t s) {
+    k_scalars<<<1, kBlock, 0, s>>>(stage, partials, nparts, st, host_out, 0.0);
 }
-void launch_scalars_aux(int stage, const double *partials, SqmrState *st, double *host_out, double aux,
+void launch_scalars_aux(int stage, const double *partials, int nparts, SqmrState *st, double *host_out, double aux,
                         cudaStream_t s) {
-    k_scalars<<<1, kBlock, 0, s>>>(stage, partials, st, host_out, aux);
+    k_scalars<<<1, kBlock, 0, s>>>(stage, partials, nparts, st, host_out, aux);
 }
 
 // s_j = s_{j-1} - alpha t  (t = L q_{j-1}); optional narrowed copy for the V-cycle
@@ -208,6 +223,7 @@ __global__ void __launch_bounds__(256) k_update_x(long long n, double *__restric
                                                   const SqmrState *__restrict__ st, double *partials) {
     double A = st->coefA, B = st->coefB, c2 = st->c2, beta = st->beta;
     double v[1] = {0.0};
+#pragma unroll 1
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         double qo = q[t];
         double dn = A * d[t] + B * qo;
@@ -218,7 +234,7 @@ __global__ void __launch_bounds__(256) k_update_x(long long n, double *__restric
         q[t] = (double)tv[t] + beta * qo;
         v[0] += rn * rn;
     }
-    block_store<1>(v, partials);
+    block_store<1>(v, partials, blockIdx.x);
 }
 template <class T>
 void launch_update_x(long long n, double *x, double *d, double *q, const T *t, double *r, const double *sv,
@@ -243,7 +259,7 @@ __global__ void __launch_bounds__(256) k_psum(Lev L, const double *__restrict__ 
     long long np = L.n - L.off[3];
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
         v[0] += x[L.off[3] + t];
-    block_store<1>(v, partials);
+    block_store<1>(v, partials, blockIdx.x);
 }
 __global__ void __launch_bounds__(256) k_psub(Lev L, double *__restrict__ x, const SqmrState *__restrict__ st) {
     double m = st->pmean;

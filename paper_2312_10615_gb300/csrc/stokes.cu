@@ -241,7 +241,9 @@ template <class T> void dgs_backward(stokes_s *h, int l, cudaStream_t s) {
     LevelBuf &B = h->lev[l];
     T *x = (T *)B.x;
     const T *b = (const T *)B.b;
-    for (int c = 7; c >= 0; --c) prof(STOKES_K_DGS_P_BWD, l, s, [&] { launch_dgs_p_bwd<T>(B.L, x, b, c, s); });
+    prof(STOKES_K_DGS_P_BWD_PREP, l, s, [&] { launch_dgs_p_bwd_prep<T>(B.L, x, b, (T *)B.r, s); });
+    for (int c = 7; c >= 0; --c)
+        prof(STOKES_K_DGS_P_BWD, l, s, [&] { launch_dgs_p_bwd<T>(B.L, x, (const T *)B.r, c, s); });
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 1, s); });
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 0, s); });
 }
@@ -283,8 +285,9 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s) {
     long long n = L.n;
     T *t = (T *)h->lev[0].x;
     // t <- L q_{j-1}, sigma = q^T t ; alpha = rho / sigma
+    int np = reduce_parts(L);
     prof(STOKES_K_APPLY_DOT, 0, s, [&] { launch_apply_dot(L, h->q, h->w, h->partials, s); });
-    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(0, h->partials, h->st, h->hout, s); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(0, h->partials, np, h->st, h->hout, s); });
     // s_j = s_{j-1} - alpha t
     prof(STOKES_K_UPDATE_S, 0, s, [&] {
         launch_update_s<T>(n, h->s, h->w, h->st, h->prec == STOKES_PREC_FP64 ? nullptr : (T *)h->lev[0].b, s);
@@ -292,11 +295,11 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s) {
     vcycle<T>(h, s);  // t <- V-cycle(L~, s_j, 0, n)
     // |t|^2, rho_j = s_j^T t ; nu, c, tau, beta
     prof(STOKES_K_DOT2, 0, s, [&] { launch_dot2<T>(n, t, h->s, h->partials, s); });
-    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(1, h->partials, h->st, h->hout, s); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(1, h->partials, kRedBlocks, h->st, h->hout, s); });
     // d_j, x_j, recursive true residual r_j, q_j ; |r_j|^2 to the host
     prof(STOKES_K_UPDATE_X, 0, s,
          [&] { launch_update_x<T>(n, h->x, h->d, h->q, t, h->r, h->s, h->st, h->partials, s); });
-    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(2, h->partials, h->st, h->hout, s); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(2, h->partials, kRedBlocks, h->st, h->hout, s); });
 }
 void sqmr_iteration_any(stokes_s *h, cudaStream_t s) {
     if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s);
@@ -386,8 +389,8 @@ int sync_read(stokes_s *h, cudaStream_t s, double *a, double *b) {
 }
 
 int residual_norm2(stokes_s *h, const double *b, const double *x, double *w, double *out, cudaStream_t s) {
-    launch_residual_dot(h->lev[0].L, b, x, w, h->partials, s);
-    launch_scalars(4, h->partials, h->st, h->hout, s);
+    int np = launch_residual_dot(h->lev[0].L, b, x, w, h->partials, s);
+    launch_scalars(4, h->partials, np, h->st, h->hout, s);
     CKLAUNCH();
     return sync_read(h, s, out, nullptr);
 }
@@ -426,6 +429,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     if (!grid || !out) return STOKES_ERR_INVALID_ARG;
     *out = nullptr;
     if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 || !(viscosity > 0.0)) return STOKES_ERR_INVALID_ARG;
+    // packed Vanka cell coordinates hold 11 + 11 + 10 bits; the z extent folds into gridDim.z
+    if (grid->nx > 2047 || grid->ny > 2047 || grid->nz > 1023) return STOKES_ERR_INVALID_ARG;
     if (bc && bc->cell_labels) return STOKES_ERR_UNSUPPORTED;
     stokes_opts_t o;
     stokes_opts_default(&o);
@@ -506,7 +511,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
                     bool v1 = i == 0 || j == 0 || k == 0 || i == L.nx - 1 || j == L.ny - 1 || k == L.nz - 1;
                     if (!v1) continue;
                     int col = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-                    cells[col].push_back(i + L.nx * (j + L.ny * k));
+                    cells[col].push_back(i | (j << 11) | (k << 22));  // packed coordinates
                 }
         B.vcap = 1;
         for (int c = 0; c < 8; ++c) {
@@ -541,7 +546,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
         if ((rc = h->alloc(&h->bvec, sizeof(double) * n))) return rc;
         if (h->prec == STOKES_PREC_FP64) h->s = (double *)h->lev[0].b;
         else if ((rc = h->alloc(&h->s, sizeof(double) * n))) return rc;
-        if ((rc = h->alloc(&h->partials, sizeof(double) * kRedBlocks * kRedParts))) return rc;
+        int nparts = reduce_parts(h->lev[0].L) > kRedBlocks ? reduce_parts(h->lev[0].L) : kRedBlocks;
+        if ((rc = h->alloc(&h->partials, sizeof(double) * nparts * kRedParts))) return rc;
         if ((rc = h->alloc(&h->st, sizeof(SqmrState)))) return rc;
         CK(cudaHostAlloc((void **)&h->hout, 4 * sizeof(double), cudaHostAllocMapped));
         std::memset(h->hout, 0, 4 * sizeof(double));
@@ -679,7 +685,7 @@ int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_it
     // |b|
     double bb = 0.0, ss = 0.0, rr = 0.0, flags = 0.0;
     launch_dot2<double>(n, h->bvec, nullptr, h->partials, s);
-    launch_scalars(4, h->partials, h->st, h->hout, s);
+    launch_scalars(4, h->partials, kRedBlocks, h->st, h->hout, s);
     CKLAUNCH();
     if ((rc = sync_read(h, s, &bb, nullptr))) return rc;
     double nb = std::sqrt(bb);
@@ -708,7 +714,7 @@ int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_it
         launch_dot2<float>(n, (const float *)h->lev[0].x, h->s, h->partials, s);
         launch_init_q<float>(n, (const float *)h->lev[0].x, h->q, h->d, s);
     }
-    launch_scalars(3, h->partials, h->st, h->hout, s);
+    launch_scalars(3, h->partials, kRedBlocks, h->st, h->hout, s);
     CKLAUNCH();
     {
         double tt = 0.0, st0 = 0.0;
@@ -736,7 +742,7 @@ int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_it
 finish:
     // pressure fixed to zero mean (constant p lies in ker L)
     launch_psum(L, h->x, h->partials, s);
-    launch_scalars_aux(5, h->partials, h->st, h->hout, (double)L.nx * L.ny * L.nz, s);
+    launch_scalars_aux(5, h->partials, kRedBlocks, h->st, h->hout, (double)L.nx * L.ny * L.nz, s);
     launch_psub(L, h->x, h->st, s);
     CKLAUNCH();
     {

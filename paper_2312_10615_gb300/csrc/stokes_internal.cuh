@@ -28,23 +28,14 @@ __host__ __device__ inline int ext(const Lev &L, int c, int d) {
 // linear index of entry (i,j,k) of component c (0 u, 1 v, 2 w, 3 p) in the packed vector
 __host__ __device__ inline long long pidx(const Lev &L, int c, int i, int j, int k) {
     long long ex = ext(L, c, 0), ey = ext(L, c, 1);
-    return L.off[c] + i + ex * (j + ey * (long long)k);
+    // select chain instead of L.off[c]: a runtime index into the parameter struct would spill it
+    long long base = c == 0 ? L.off[0] : (c == 1 ? L.off[1] : (c == 2 ? L.off[2] : L.off[3]));
+    return base + i + ex * (j + ey * (long long)k);
 }
 
-// is (c,i,j,k) an unknown of the box problem?
+// is (c,i,j,k) an unknown of the box problem?  (normal index in [1, n-1], tangential in [0, n-1])
 __host__ __device__ inline bool active(const Lev &L, int c, int i, int j, int k) {
-    if (c == 3) return i >= 0 && j >= 0 && k >= 0 && i < L.nx && j < L.ny && k < L.nz;
-    int a[3] = {i, j, k};
-    int n[3] = {L.nx, L.ny, L.nz};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (d == c) {
-            if (a[d] < 1 || a[d] > n[d] - 1) return false;
-        } else if (a[d] < 0 || a[d] > n[d] - 1) {
-            return false;
-        }
-    }
-    return true;
+    return i >= (c == 0) && j >= (c == 1) && k >= (c == 2) && i <= L.nx - 1 && j <= L.ny - 1 && k <= L.nz - 1;
 }
 
 template <class T>

@@ -45,7 +45,8 @@ def pair(dims, precision=smg.PREC_FP64, **kw):
     if key not in _cache:
         nx, ny, nz = dims
         o = oracle.Oracle(nx, ny, nz, coarsest_max=8, **kw)
-        S = smg.Stokes(nx, ny, nz, precision=precision, **kw)
+        skw = {("kb_vanka" if k == "kb" else k): v for k, v in kw.items()}
+        S = smg.Stokes(nx, ny, nz, precision=precision, **skw)
         assert S.levels == o.nlevels
         _cache[key] = (o, S)
     return _cache[key]
