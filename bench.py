@@ -375,6 +375,7 @@ def main():
                        "l2": "inputs larger than L2 (each FP64 vector 537 MB)", "parallelism": f"replicas x{world}"},
             "iterations": [it for it, _ in its32], "rel_residual": [r for _, r in its32],
             "kernel_ms_per_iteration": {k: round(v[0], 4) for k, v in prof32.items()},
+            "kernel_ms_per_iteration_level0": {k: round(v[2], 4) for k, v in prof32.items()},
             "fp64_vcycle": fp64, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk.summary(),
         }

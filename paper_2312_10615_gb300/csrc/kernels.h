@@ -16,8 +16,11 @@ void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaS
 template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s);
 template <class T> void launch_dgs_p_fwd(const Lev &L, T *x, const T *b, T *delta, int colour, cudaStream_t s);
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s);
-// backward pressure colours read g = b - Au (faces) and h = b - Bu (cells) precomputed into gh
-template <class T> void launch_dgs_p_bwd_prep(const Lev &L, const T *x, const T *b, T *gh, cudaStream_t s);
+// backward pressure colours read g = b - Au (faces) and h = b - Bu (cells) precomputed into gh;
+// with delta != null the same launch applies the pending neighbour-pressure part of the forward
+// sweep (what launch_dgs_p_gather does)
+template <class T>
+void launch_dgs_p_bwd_prep(const Lev &L, T *x, const T *b, T *gh, const T *delta, cudaStream_t s);
 template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s);
 // one colour of the multiplicative Vanka sweep on V1 (compute corrections, then add them)
 template <class T>

@@ -235,9 +235,11 @@ __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, 
 // and a colour then needs r_f = g_f - (p_plus - p_minus)/h and r_n = h_n + gamma p_n only:
 //   p_c += [ sum_axes (r_high_face - r_low_face)/h + eta/h^2 (6 r_c - sum of the 6 neighbour r) ] / d
 // (M_{.c}^T r with the full column of M).  Same-colour cells read none of each other's values.
+// The same launch also finishes the forward sweep: the neighbour-pressure part of the last
+// colours (gather form of k_dgs_p_gather), which the prep never reads.
 template <class T>
-__global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, int gy, const T *__restrict__ x,
-                                                        const T *__restrict__ b, T *__restrict__ gh, Coef<T> K) {
+__global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, int gy, T *__restrict__ x, const T *__restrict__ b,
+                                                        T *__restrict__ gh, const T *__restrict__ delta, Coef<T> K) {
     int c, i, j, k;
     if (!thread_entry(L, gy, c, i, j, k)) return;
     long long q = pidx(L, c, i, j, k);
@@ -246,6 +248,17 @@ __global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, int gy, const T *
         return;
     }
     T v;
+    if (c == 3 && delta) {
+        long long t = cell_lin(L, i, j, k);
+        bool v2 = in_v2_cell(L, i, j, k);
+        int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+        long long sy = L.nx, sz = (long long)L.nx * L.ny;
+        T g = T(0);
+        if (!v2 || !(colour & 1)) g += (i > 0 ? delta[t - 1] : T(0)) + (i < L.nx - 1 ? delta[t + 1] : T(0));
+        if (!v2 || !(colour & 2)) g += (j > 0 ? delta[t - sy] : T(0)) + (j < L.ny - 1 ? delta[t + sy] : T(0));
+        if (!v2 || !(colour & 4)) g += (k > 0 ? delta[t - sz] : T(0)) + (k < L.nz - 1 ? delta[t + sz] : T(0));
+        if (g != T(0)) x[q] -= K.eh2 * g;
+    }
     if (c < 3) {
         T s = T(6) * x[q];
         s -= xget(x, L, c, i - 1, j, k);
@@ -305,9 +318,10 @@ template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, 
     dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz);
     k_dgs_p_gather<T><<<grid, kBlock3, 0, s>>>(L, x, delta, coef<T>(L, L.gamma));
 }
-template <class T> void launch_dgs_p_bwd_prep(const Lev &L, const T *x, const T *b, T *gh, cudaStream_t s) {
+template <class T>
+void launch_dgs_p_bwd_prep(const Lev &L, T *x, const T *b, T *gh, const T *delta, cudaStream_t s) {
     Geo g = geo_components(L, 4);
-    k_dgs_p_bwd_prep<T><<<g.grid, kBlock3, 0, s>>>(L, g.gy, x, b, gh, coef<T>(L, L.gamma));
+    k_dgs_p_bwd_prep<T><<<g.grid, kBlock3, 0, s>>>(L, g.gy, x, b, gh, delta, coef<T>(L, L.gamma));
 }
 template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
@@ -329,62 +343,64 @@ __device__ __forceinline__ void unpack_cell(int w, int &i, int &j, int &k) {
     k = (w >> 22) & 1023;
 }
 
+// 8 lanes per cell: lane a < 6 owns face a of the patch, lane 6 the pressure, lane 7 idles; the
+// 7 residuals are exchanged with width-8 shuffles and lane a forms row a of K^{-1} r.
 template <class T>
 __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const T *__restrict__ b,
                                                        const int *__restrict__ cells, int ncell,
                                                        const T *__restrict__ kinv, T *__restrict__ corr, int cap,
                                                        Coef<T> K) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncell) return;
+    int slot = t >> 3, a = t & 7;
+    if (slot >= ncell) return;  // whole 8-lane groups leave together
+    unsigned gmask = 0xffu << (threadIdx.x & 24);
     int i, j, k;
-    unpack_cell(cells[t], i, j, k);
-    T r[7];
-    int cfg = 0;
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
+    unpack_cell(cells[slot], i, j, k);
+    int cfg = (i >= 1) | ((i + 1 <= L.nx - 1) << 1) | ((j >= 1) << 2) | ((j + 1 <= L.ny - 1) << 3) |
+              ((k >= 1) << 4) | ((k + 1 <= L.nz - 1) << 5);
+    T r = T(0);
+    if (a < 6) {
         int d = a >> 1, side = a & 1;
         int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-        bool act = active(L, d, fi, fj, fk);
-        cfg |= act ? (1 << a) : 0;
-        r[a] = act ? b[pidx(L, d, fi, fj, fk)] - face_Lx(x, L, d, fi, fj, fk, K) : T(0);
+        if ((cfg >> a) & 1) r = b[pidx(L, d, fi, fj, fk)] - face_Lx(x, L, d, fi, fj, fk, K);
+    } else if (a == 6) {
+        r = b[pidx(L, 3, i, j, k)] - cell_Lx(x, L, i, j, k, K);
     }
-    r[6] = b[pidx(L, 3, i, j, k)] - cell_Lx(x, L, i, j, k, K);
-    const T *Ki = kinv + cfg * 49;
+    const T *Ki = kinv + cfg * 49 + (a < 7 ? a : 6) * 7;
+    T s = T(0);
 #pragma unroll
-    for (int a = 0; a < 7; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int bb = 0; bb < 7; ++bb) s += Ki[a * 7 + bb] * r[bb];
-        corr[(long long)a * cap + t] = s;
-    }
+    for (int bb = 0; bb < 7; ++bb) s += Ki[bb] * __shfl_sync(gmask, r, bb, 8);
+    if (a < 7) corr[(long long)a * cap + slot] = s;
 }
 
 template <class T>
 __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, const int *__restrict__ cells,
                                                      int ncell, const T *__restrict__ corr, int cap) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncell) return;
+    int slot = t >> 3, a = t & 7;
+    if (slot >= ncell || a == 7) return;
     int i, j, k;
-    unpack_cell(cells[t], i, j, k);
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        int d = a >> 1, side = a & 1;
-        int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-        if (active(L, d, fi, fj, fk)) x[pidx(L, d, fi, fj, fk)] += corr[(long long)a * cap + t];
+    unpack_cell(cells[slot], i, j, k);
+    if (a == 6) {
+        x[pidx(L, 3, i, j, k)] += corr[6LL * cap + slot];
+        return;
     }
-    x[pidx(L, 3, i, j, k)] += corr[6LL * cap + t];
+    int d = a >> 1, side = a & 1;
+    int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+    if (active(L, d, fi, fj, fk)) x[pidx(L, d, fi, fj, fk)] += corr[(long long)a * cap + slot];
 }
 
 template <class T>
 void launch_vanka_compute(const Lev &L, const T *x, const T *b, const int *cells, int ncell, const T *kinv, T *corr,
                           int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    k_vanka_compute<T><<<cdiv(ncell, 256), 256, 0, s>>>(L, x, b, cells, ncell, kinv, corr, cap, coef<T>(L, L.gamma));
+    k_vanka_compute<T><<<cdiv(8LL * ncell, 256), 256, 0, s>>>(L, x, b, cells, ncell, kinv, corr, cap,
+                                                               coef<T>(L, L.gamma));
 }
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    k_vanka_apply<T><<<cdiv(ncell, 256), 256, 0, s>>>(L, x, cells, ncell, corr, cap);
+    k_vanka_apply<T><<<cdiv(8LL * ncell, 256), 256, 0, s>>>(L, x, cells, ncell, corr, cap);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -554,7 +570,7 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template void launch_dgs_u<T>(const Lev &, T *, const T *, int, cudaStream_t);                                \
     template void launch_dgs_p_fwd<T>(const Lev &, T *, const T *, T *, int, cudaStream_t);                       \
     template void launch_dgs_p_gather<T>(const Lev &, T *, const T *, cudaStream_t);                              \
-    template void launch_dgs_p_bwd_prep<T>(const Lev &, const T *, const T *, T *, cudaStream_t);                 \
+    template void launch_dgs_p_bwd_prep<T>(const Lev &, T *, const T *, T *, const T *, cudaStream_t);            \
     template void launch_dgs_p_bwd<T>(const Lev &, T *, const T *, int, cudaStream_t);                            \
     template void launch_vanka_compute<T>(const Lev &, const T *, const T *, const int *, int, const T *, T *, int, \
                                           cudaStream_t);                                                          \

@@ -235,13 +235,19 @@ template <class T> void dgs_forward(stokes_s *h, int l, cudaStream_t s) {
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 1, s); });
     for (int c = 0; c < 8; ++c)
         prof(STOKES_K_DGS_P_FWD, l, s, [&] { launch_dgs_p_fwd<T>(B.L, x, b, (T *)B.delta, c, s); });
-    prof(STOKES_K_DGS_P_GATHER, l, s, [&] { launch_dgs_p_gather<T>(B.L, x, (const T *)B.delta, s); });
 }
-template <class T> void dgs_backward(stokes_s *h, int l, cudaStream_t s) {
+// the forward sweep's pending neighbour-pressure part is applied by the first launch after it
+template <class T> void dgs_finish_forward(stokes_s *h, int l, cudaStream_t s) {
+    LevelBuf &B = h->lev[l];
+    prof(STOKES_K_DGS_P_GATHER, l, s, [&] { launch_dgs_p_gather<T>(B.L, (T *)B.x, (const T *)B.delta, s); });
+}
+template <class T> void dgs_backward(stokes_s *h, int l, cudaStream_t s, bool forward_pending) {
     LevelBuf &B = h->lev[l];
     T *x = (T *)B.x;
     const T *b = (const T *)B.b;
-    prof(STOKES_K_DGS_P_BWD_PREP, l, s, [&] { launch_dgs_p_bwd_prep<T>(B.L, x, b, (T *)B.r, s); });
+    prof(STOKES_K_DGS_P_BWD_PREP, l, s, [&] {
+        launch_dgs_p_bwd_prep<T>(B.L, x, b, (T *)B.r, forward_pending ? (const T *)B.delta : nullptr, s);
+    });
     for (int c = 7; c >= 0; --c)
         prof(STOKES_K_DGS_P_BWD, l, s, [&] { launch_dgs_p_bwd<T>(B.L, x, (const T *)B.r, c, s); });
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 1, s); });
@@ -250,7 +256,7 @@ template <class T> void dgs_backward(stokes_s *h, int l, cudaStream_t s) {
 template <class T> void smooth(stokes_s *h, int l, cudaStream_t s) {
     for (int k = 0; k < h->kb; ++k) vanka_sym<T>(h, l, s);
     dgs_forward<T>(h, l, s);
-    dgs_backward<T>(h, l, s);
+    dgs_backward<T>(h, l, s, true);
     for (int k = 0; k < h->kb; ++k) vanka_sym<T>(h, l, s);
 }
 template <class T> void vcycle(stokes_s *h, cudaStream_t s) {
@@ -811,10 +817,10 @@ int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, 
         using T = decltype(tag);
         switch (which) {
         case 0: smooth<T>(h, level, s); break;
-        case 1: dgs_forward<T>(h, level, s); dgs_backward<T>(h, level, s); break;
+        case 1: dgs_forward<T>(h, level, s); dgs_backward<T>(h, level, s, true); break;
         case 2: vanka_sym<T>(h, level, s); break;
-        case 3: dgs_forward<T>(h, level, s); break;
-        case 4: dgs_backward<T>(h, level, s); break;
+        case 3: dgs_forward<T>(h, level, s); dgs_finish_forward<T>(h, level, s); break;
+        case 4: dgs_backward<T>(h, level, s, false); break;
         default: vanka_colour<T>(h, level, which - 10, s); break;
         }
     };
