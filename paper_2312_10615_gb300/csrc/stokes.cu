@@ -540,18 +540,9 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
             CK(cudaMemcpy(B.kinv, kf.data(), sizeof(float) * 64 * 49, cudaMemcpyHostToDevice));
         }
     }
-    // SQMR vectors and scalar state
+    // reduction scratch and scalar state (the SQMR vectors are allocated by the first sqmr_solve)
     {
-        long long n = h->n0();
         int rc;
-        if ((rc = h->alloc(&h->x, sizeof(double) * n))) return rc;
-        if ((rc = h->alloc(&h->q, sizeof(double) * n))) return rc;
-        if ((rc = h->alloc(&h->d, sizeof(double) * n))) return rc;
-        if ((rc = h->alloc(&h->r, sizeof(double) * n))) return rc;
-        if ((rc = h->alloc(&h->w, sizeof(double) * n))) return rc;
-        if ((rc = h->alloc(&h->bvec, sizeof(double) * n))) return rc;
-        if (h->prec == STOKES_PREC_FP64) h->s = (double *)h->lev[0].b;
-        else if ((rc = h->alloc(&h->s, sizeof(double) * n))) return rc;
         int nparts = reduce_parts(h->lev[0].L) > kRedBlocks ? reduce_parts(h->lev[0].L) : kRedBlocks;
         if ((rc = h->alloc(&h->partials, sizeof(double) * nparts * kRedParts))) return rc;
         if ((rc = h->alloc(&h->st, sizeof(SqmrState)))) return rc;
@@ -673,14 +664,34 @@ int stokes_residual_norm(stokes_t h, const double *b, const double *x, double *o
     return STOKES_OK;
 }
 
-int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info, void *stream) {
+namespace {
+// FP64 vectors of Alg. 4 on the finest level, allocated on first use
+int ensure_sqmr(stokes_s *h) {
+    if (h->x) return 0;
+    long long n = h->n0();
+    int rc;
+    if ((rc = h->alloc(&h->x, sizeof(double) * n))) return rc;
+    if ((rc = h->alloc(&h->q, sizeof(double) * n))) return rc;
+    if ((rc = h->alloc(&h->d, sizeof(double) * n))) return rc;
+    if ((rc = h->alloc(&h->r, sizeof(double) * n))) return rc;
+    if ((rc = h->alloc(&h->w, sizeof(double) * n))) return rc;
+    if ((rc = h->alloc(&h->bvec, sizeof(double) * n))) return rc;
+    if (h->prec == STOKES_PREC_FP64) h->s = (double *)h->lev[0].b;
+    else if ((rc = h->alloc(&h->s, sizeof(double) * n))) return rc;
+    return 0;
+}
+}  // namespace
+
+extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info,
+                          void *stream) {
     if (info) std::memset(info, 0, sizeof(*info));
     if (!h || !rhs || !xv || !(tol > 0.0) || max_iter < 0) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
     const Lev &L = h->lev[0].L;
     long long n = L.n;
-    int rc = 0;
+    int rc = ensure_sqmr(h);
+    if (rc) return rc;
     // inputs
     if (is_device_ptr(rhs)) CK(cudaMemcpyAsync(h->bvec, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     else CK(cudaMemcpyAsync(h->bvec, rhs, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -773,6 +784,8 @@ int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launch
         return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = ensure_sqmr(h);
+    if (rc0) return rc0;
     Prof P;
     P.ev.resize(8192);
     for (auto &e : P.ev) CK(cudaEventCreate(&e));
