@@ -34,8 +34,9 @@ template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, 
 // coarsest level: x = Kinv b over the compact unknown list (FP64 matrix)
 template <class T>
 void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, const T *b, T *x, cudaStream_t s);
-// set every entry that is not an unknown to 0
-void launch_mask(const Lev &L, double *x, cudaStream_t s);
+// set every entry that is not an unknown to 0 (every internal vector keeps this invariant: the fast
+// stencils read wall-normal faces as zeros)
+template <class T> void launch_mask(const Lev &L, T *x, cudaStream_t s);
 // precision conversion of a packed vector
 template <class A, class B> void launch_convert(long long n, const A *in, B *out, cudaStream_t s);
 

@@ -66,7 +66,7 @@ __device__ __forceinline__ bool thread_entry(const Lev &L, int gy, int &c, int &
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// y = L~x or b - L~x on every packed entry (0 off the unknowns)
+// y = L~x or b - L~x on every packed entry (0 off the unknowns); x must hold 0 off the unknowns
 template <class T>
 __global__ void __launch_bounds__(256) k_apply(Lev L, int gy, const T *__restrict__ x, const T *__restrict__ b,
                                                T *__restrict__ y, Coef<T> K) {
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) k_apply(Lev L, int gy, const T *__restric
         y[q] = T(0);
         return;
     }
-    T v = c < 3 ? face_Lx(x, L, c, i, j, k, K) : cell_Lx(x, L, i, j, k, K);
+    T v = c < 3 ? face_Lx_any(x, L, c, i, j, k, K) : cell_Lx_fast(x, L, i, j, k, K);
     y[q] = b ? b[q] - v : v;
 }
 
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_dgs_u(Lev L, int gy, T *__restrict__ x,
     i += (i + j + k + parity) & 1;
     if (i >= lo[0] + cnt[0]) return;
     long long q = pidx(L, c, i, j, k);
-    T r = b[q] - face_Lx(x, L, c, i, j, k, K);
+    T r = b[q] - face_Lx_any(x, L, c, i, j, k, K);
     x[q] += r / (T(6) * K.eh2);
 }
 
@@ -260,18 +260,15 @@ __global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, int gy, T *__rest
         if (g != T(0)) x[q] -= K.eh2 * g;
     }
     if (c < 3) {
-        T s = T(6) * x[q];
-        s -= xget(x, L, c, i - 1, j, k);
-        s -= xget(x, L, c, i + 1, j, k);
-        s -= xget(x, L, c, i, j - 1, k);
-        s -= xget(x, L, c, i, j + 1, k);
-        s -= xget(x, L, c, i, j, k - 1);
-        s -= xget(x, L, c, i, j, k + 1);
-        v = b[q] - K.eh2 * s;
+        // b - (A u)_f: the face operator without its pressure part (K with ih = 0 drops it)
+        Coef<T> KA = K;
+        KA.ih = T(0);
+        v = b[q] - face_Lx_any(x, L, c, i, j, k, KA);
     } else {
-        T div = xget(x, L, 0, i + 1, j, k) - xget(x, L, 0, i, j, k) + xget(x, L, 1, i, j + 1, k) -
-                xget(x, L, 1, i, j, k) + xget(x, L, 2, i, j, k + 1) - xget(x, L, 2, i, j, k);
-        v = b[q] + K.ih * div;
+        // b - (B u)_c: the cell operator without its pressure part
+        Coef<T> KB = K;
+        KB.gam = T(0);
+        v = b[q] - cell_Lx_fast(x, L, i, j, k, KB);
     }
     gh[q] = v;
 }
@@ -362,9 +359,9 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
     if (a < 6) {
         int d = a >> 1, side = a & 1;
         int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-        if ((cfg >> a) & 1) r = b[pidx(L, d, fi, fj, fk)] - face_Lx(x, L, d, fi, fj, fk, K);
+        if ((cfg >> a) & 1) r = b[pidx(L, d, fi, fj, fk)] - face_Lx_any(x, L, d, fi, fj, fk, K);
     } else if (a == 6) {
-        r = b[pidx(L, 3, i, j, k)] - cell_Lx(x, L, i, j, k, K);
+        r = b[pidx(L, 3, i, j, k)] - cell_Lx_fast(x, L, i, j, k, K);
     }
     const T *Ki = kinv + cfg * 49 + (a < 7 ? a : 6) * 7;
     T s = T(0);
@@ -408,27 +405,32 @@ void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T
 // weight 1 from a coincident coarse face or 1/2 + 1/2 from the two coarse faces around it along
 // its normal, and 3/4 (coarse row containing it) + 1/4 (next coarse row on the far side) along
 // each tangential axis; coarse entries that are not unknowns contribute 0.  R = P^T / 8.
-// component C of the face transfers, with every index known at compile time
+// component C of the face transfers, with every index known at compile time; offsets are strides
+// from one base address.  Along the normal axis every referenced fine/coarse face lies inside the
+// array (walls hold 0); along a tangential axis the rows outside the box are skipped.
 template <class T, int C>
-__device__ __forceinline__ T restrict_face(const Lev &F, const T *__restrict__ rf, int I, int J, int Kk) {
+__device__ __forceinline__ T restrict_face(const Lev &F, const Lev &Cl, const T *__restrict__ rf, int I, int J,
+                                           int Kk) {
+    const long long sy = F.nx + (C == 0), sz = sy * (F.ny + (C == 1));
+    const long long st[3] = {1, sy, sz};
+    const T *fb = rf + comp_base(F, C) + 2 * I + sy * (2 * J) + sz * (2LL * Kk);
+    const int t1 = C == 0 ? 1 : 0, t2 = C == 2 ? 1 : 2;  // tangential axes
+    const int T1 = t1 == 0 ? I : (t1 == 1 ? J : Kk), T2 = t2 == 1 ? J : Kk;
+    const int n1 = t1 == 0 ? Cl.nx : (t1 == 1 ? Cl.ny : Cl.nz), n2 = t2 == 1 ? Cl.ny : Cl.nz;
     const T nw[3] = {T(0.5), T(1), T(0.5)};
     const T tw[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
     T s = T(0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int bb = 0; bb < 4; ++bb) {
+        if ((bb == 0 && T1 == 0) || (bb == 3 && T1 == n1 - 1)) continue;
 #pragma unroll
-        for (int bb = 0; bb < 4; ++bb) {
-            T sr = T(0);
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                // offsets: a along the normal axis C, bb and g along the two tangential axes
-                int di = C == 0 ? a - 1 : bb - 1;
-                int dj = C == 0 ? bb - 1 : (C == 1 ? a - 1 : g - 1);
-                int dk = C == 2 ? a - 1 : g - 1;
-                sr += tw[g] * xget(rf, F, C, 2 * I + di, 2 * J + dj, 2 * Kk + dk);
-            }
-            s += nw[a] * tw[bb] * sr;
+        for (int g = 0; g < 4; ++g) {
+            if ((g == 0 && T2 == 0) || (g == 3 && T2 == n2 - 1)) continue;
+            const T *row = fb + (bb - 1) * st[t1] + (g - 1) * st[t2];
+            T sn = nw[0] * row[-st[C]] + nw[1] * row[0] + nw[2] * row[st[C]];
+            s += tw[bb] * tw[g] * sn;
         }
+    }
     return s * T(0.125);
 }
 
@@ -444,9 +446,9 @@ __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const T 
     }
     T v;
     switch (c) {
-    case 0: v = restrict_face<T, 0>(F, rf, I, J, Kk); break;
-    case 1: v = restrict_face<T, 1>(F, rf, I, J, Kk); break;
-    case 2: v = restrict_face<T, 2>(F, rf, I, J, Kk); break;
+    case 0: v = restrict_face<T, 0>(F, C, rf, I, J, Kk); break;
+    case 1: v = restrict_face<T, 1>(F, C, rf, I, J, Kk); break;
+    case 2: v = restrict_face<T, 2>(F, C, rf, I, J, Kk); break;
     default: {
         T s = T(0);
 #pragma unroll
@@ -479,16 +481,28 @@ __device__ __forceinline__ W2 pw_axis(int f, bool normal) {
 template <class T, int CC>
 __device__ __forceinline__ T prolong_face(const Lev &C, const T *__restrict__ ec, int fi, int fj, int fk) {
     W2 a = pw_axis(fi, CC == 0), b = pw_axis(fj, CC == 1), g = pw_axis(fk, CC == 2);
+    const long long sy = C.nx + (CC == 0), sz = sy * (C.ny + (CC == 1));
+    const int nx = C.nx, ny = C.ny, nz = C.nz;
+    // a coarse index outside the box (tangential -1 or n) contributes 0; a normal index is always
+    // in [0, n] (walls hold 0); the unused second normal weight is 0
+    auto ok = [](int idx, int n, bool normal) { return normal ? idx >= 0 : (idx >= 0 && idx < n); };
+    const T *cb = ec + comp_base(C, CC);
     int ii[2] = {a.i0, a.i1}, jj[2] = {b.i0, b.i1}, kk[2] = {g.i0, g.i1};
     T wi[2] = {T(a.w0), T(a.w1)}, wj[2] = {T(b.w0), T(b.w1)}, wk[2] = {T(g.w0), T(g.w1)};
     T s = T(0);
 #pragma unroll
-    for (int x = 0; x < 2; ++x)
+    for (int x = 0; x < 2; ++x) {
+        if (!ok(ii[x], nx, CC == 0) || wi[x] == T(0)) continue;
 #pragma unroll
-        for (int y = 0; y < 2; ++y)
+        for (int y = 0; y < 2; ++y) {
+            if (!ok(jj[y], ny, CC == 1) || wj[y] == T(0)) continue;
 #pragma unroll
-            for (int z = 0; z < 2; ++z)
-                s += wi[x] * wj[y] * wk[z] * xget(ec, C, CC, ii[x], jj[y], kk[z]);  // index -1 is never active
+            for (int z = 0; z < 2; ++z) {
+                if (!ok(kk[z], nz, CC == 2) || wk[z] == T(0)) continue;
+                s += wi[x] * wj[y] * wk[z] * cb[ii[x] + sy * jj[y] + sz * kk[z]];
+            }
+        }
+    }
     return s;
 }
 
@@ -545,15 +559,17 @@ void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, co
 }
 
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mask(Lev L, int gy, double *__restrict__ x) {
+template <class T> __global__ void __launch_bounds__(256) k_mask(Lev L, int gy, T *__restrict__ x) {
     int c, i, j, k;
     if (!thread_entry(L, gy, c, i, j, k)) return;
-    if (!active(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = 0.0;
+    if (!active(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = T(0);
 }
-void launch_mask(const Lev &L, double *x, cudaStream_t s) {
+template <class T> void launch_mask(const Lev &L, T *x, cudaStream_t s) {
     Geo g = geo_components(L, 4);
-    k_mask<<<g.grid, kBlock3, 0, s>>>(L, g.gy, x);
+    k_mask<T><<<g.grid, kBlock3, 0, s>>>(L, g.gy, x);
 }
+template void launch_mask<float>(const Lev &, float *, cudaStream_t);
+template void launch_mask<double>(const Lev &, double *, cudaStream_t);
 
 template <class A, class B> __global__ void k_convert(long long n, const A *__restrict__ in, B *__restrict__ out) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)

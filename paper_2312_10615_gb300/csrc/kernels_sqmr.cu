@@ -39,6 +39,7 @@ template <int NV> __device__ __forceinline__ void block_store(double (&v)[NV], d
 
 // 3D launch over the packed entries of the 4 components: blocks of 32 x 8 over (x, y), the
 // component folded into gridDim.y, each thread marching over z; one partial sum per block.
+// The input vectors hold 0 off the unknowns (the fast stencils rely on it).
 int reduce_parts(const Lev &L) {
     int gx = (L.nx + 1 + BX - 1) / BX, gy = (L.ny + 1 + BY - 1) / BY;
     return gx * gy * 4;
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(256) k_apply_dot(Lev L, int gy, const double *
             long long t = pidx(L, c, i, j, k);
             double y = 0.0;
             if (active(L, c, i, j, k)) {
-                y = c < 3 ? face_Lx(q, L, c, i, j, k, K) : cell_Lx(q, L, i, j, k, K);
+                y = c < 3 ? face_Lx_any(q, L, c, i, j, k, K) : cell_Lx_fast(q, L, i, j, k, K);
                 v[0] += q[t] * y;
             }
             w[t] = y;
@@ -75,7 +76,8 @@ __global__ void __launch_bounds__(256) k_residual_dot(Lev L, int gy, const doubl
         for (int k = 0; k < ez; ++k) {
             long long t = pidx(L, c, i, j, k);
             double r = 0.0;
-            if (active(L, c, i, j, k)) r = b[t] - (c < 3 ? face_Lx(x, L, c, i, j, k, K) : cell_Lx(x, L, i, j, k, K));
+            if (active(L, c, i, j, k))
+                r = b[t] - (c < 3 ? face_Lx_any(x, L, c, i, j, k, K) : cell_Lx_fast(x, L, i, j, k, K));
             if (w) w[t] = r;
             v[0] += r * r;
         }

@@ -372,10 +372,25 @@ int ensure_stage(stokes_s *h) {
     return 0;
 }
 
-// level vector in/out (FP64 caller layout <-> precision T of the level buffers)
-int to_level(stokes_s *h, const double *src_dev, void *dst, long long n, cudaStream_t s) {
-    if (h->prec == STOKES_PREC_FP64) CK(cudaMemcpyAsync(dst, src_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    else launch_convert<double, float>(n, src_dev, (float *)dst, s);
+// level vector in/out (FP64 caller layout <-> precision T of the level buffers); entries off the
+// unknowns are zeroed on the way in
+int to_level(stokes_s *h, const Lev &L, const double *src_dev, void *dst, cudaStream_t s) {
+    long long n = L.n;
+    if (h->prec == STOKES_PREC_FP64) {
+        CK(cudaMemcpyAsync(dst, src_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        launch_mask<double>(L, (double *)dst, s);
+    } else {
+        launch_convert<double, float>(n, src_dev, (float *)dst, s);
+        launch_mask<float>(L, (float *)dst, s);
+    }
+    CKLAUNCH();
+    return 0;
+}
+// a caller vector copied into a handle buffer with the entries off the unknowns zeroed
+int stage_masked(stokes_s *h, const double *p, double *dst, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, p, sizeof(double) * h->n0(), is_device_ptr(p) ? cudaMemcpyDeviceToDevice
+                                                                           : cudaMemcpyHostToDevice, s));
+    launch_mask<double>(h->lev[0].L, dst, s);
     CKLAUNCH();
     return 0;
 }
@@ -610,13 +625,11 @@ int stokes_apply(stokes_t h, const double *x, double *y, void *stream) {
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
-    const double *xd;
-    if (!is_device_ptr(x) || !is_device_ptr(y))
-        if ((rc = ensure_stage(h))) return rc;
-    if ((rc = stage_in(h, x, h->n0(), h->stage_in, &xd, s))) return rc;
+    if ((rc = ensure_stage(h))) return rc;
+    if ((rc = stage_masked(h, x, h->stage_in, s))) return rc;
     bool ydev = is_device_ptr(y);
     double *yd = ydev ? y : h->stage_out;
-    launch_apply<double>(h->lev[0].L, xd, nullptr, yd, 0.0, s);
+    launch_apply<double>(h->lev[0].L, h->stage_in, nullptr, yd, 0.0, s);
     CKLAUNCH();
     if (!ydev) {
         CK(cudaMemcpyAsync(y, yd, sizeof(double) * h->n0(), cudaMemcpyDeviceToHost, s));
@@ -635,8 +648,7 @@ int mg_precondition(stokes_t h, const double *sv, double *tv, void *stream) {
         if ((rc = ensure_stage(h))) return rc;
     const double *sd;
     if ((rc = stage_in(h, sv, n, h->stage_in, &sd, s))) return rc;
-    if ((rc = to_level(h, sd, h->lev[0].b, n, s))) return rc;
-    if (h->prec == STOKES_PREC_FP64) launch_mask(h->lev[0].L, (double *)h->lev[0].b, s);
+    if ((rc = to_level(h, h->lev[0].L, sd, h->lev[0].b, s))) return rc;
     if ((rc = run_vcycle(h, s))) return rc;
     bool tdev = is_device_ptr(tv);
     double *td = tdev ? tv : h->stage_out;
@@ -653,13 +665,12 @@ int stokes_residual_norm(stokes_t h, const double *b, const double *x, double *o
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
-    const double *bd, *xd;
-    bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    if ((!bdev || !xdev) && (rc = ensure_stage(h))) return rc;
+    const double *bd;
+    if ((rc = ensure_stage(h))) return rc;
     if ((rc = stage_in(h, b, h->n0(), h->stage_in, &bd, s))) return rc;
-    if ((rc = stage_in(h, x, h->n0(), h->stage_out, &xd, s))) return rc;
+    if ((rc = stage_masked(h, x, h->stage_out, s))) return rc;
     double r2 = 0.0;
-    if ((rc = residual_norm2(h, bd, xd, nullptr, &r2, s))) return rc;
+    if ((rc = residual_norm2(h, bd, h->stage_out, nullptr, &r2, s))) return rc;
     *out = std::sqrt(r2);
     return STOKES_OK;
 }
@@ -697,8 +708,8 @@ extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol,
     else CK(cudaMemcpyAsync(h->bvec, rhs, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     bool xdev = is_device_ptr(xv);
     CK(cudaMemcpyAsync(h->x, xv, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    launch_mask(L, h->bvec, s);
-    launch_mask(L, h->x, s);
+    launch_mask<double>(L, h->bvec, s);
+    launch_mask<double>(L, h->x, s);
     // |b|
     double bb = 0.0, ss = 0.0, rr = 0.0, flags = 0.0;
     launch_dot2<double>(n, h->bvec, nullptr, h->partials, s);
@@ -823,9 +834,9 @@ int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, 
     const double *xd, *bd;
     bool xdev = is_device_ptr(x);
     if ((rc = stage_in(h, x, n, h->stage_in, &xd, s))) return rc;
-    if ((rc = to_level(h, xd, B.x, n, s))) return rc;
+    if ((rc = to_level(h, B.L, xd, B.x, s))) return rc;
     if ((rc = stage_in(h, b, n, h->stage_in, &bd, s))) return rc;
-    if ((rc = to_level(h, bd, B.b, n, s))) return rc;
+    if ((rc = to_level(h, B.L, bd, B.b, s))) return rc;
     auto body = [&](auto tag) {
         using T = decltype(tag);
         switch (which) {
@@ -842,7 +853,7 @@ int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, 
     CKLAUNCH();
     double *out = xdev ? x : h->stage_out;
     if ((rc = from_level(h, B.x, out, n, s))) return rc;
-    launch_mask(B.L, out, s);
+    launch_mask<double>(B.L, out, s);
     if (!xdev) CK(cudaMemcpyAsync(x, out, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return STOKES_OK;
@@ -857,7 +868,7 @@ int stokes_restrict(stokes_t h, int level, const double *rf, double *bc, void *s
     if ((rc = ensure_stage(h))) return rc;
     const double *rd;
     if ((rc = stage_in(h, rf, F.L.n, h->stage_in, &rd, s))) return rc;
-    if ((rc = to_level(h, rd, F.r, F.L.n, s))) return rc;
+    if ((rc = to_level(h, F.L, rd, F.r, s))) return rc;
     auto run = [&](auto tag) {
         using T = decltype(tag);
         launch_restrict<T>(F.L, C.L, (const T *)F.r, (T *)C.b, s);
@@ -882,10 +893,10 @@ int stokes_prolong_add(stokes_t h, int level, const double *ec, double *xf, void
     if ((rc = ensure_stage(h))) return rc;
     const double *ed, *xd;
     if ((rc = stage_in(h, ec, C.L.n, h->stage_in, &ed, s))) return rc;
-    if ((rc = to_level(h, ed, C.x, C.L.n, s))) return rc;
+    if ((rc = to_level(h, C.L, ed, C.x, s))) return rc;
     bool xdev = is_device_ptr(xf);
     if ((rc = stage_in(h, xf, F.L.n, h->stage_in, &xd, s))) return rc;
-    if ((rc = to_level(h, xd, F.x, F.L.n, s))) return rc;
+    if ((rc = to_level(h, F.L, xd, F.x, s))) return rc;
     auto run = [&](auto tag) {
         using T = decltype(tag);
         launch_prolong<T>(F.L, C.L, (const T *)C.x, (T *)F.x, s);
@@ -897,7 +908,7 @@ int stokes_prolong_add(stokes_t h, int level, const double *ec, double *xf, void
     CK(cudaMemsetAsync(C.x, 0, (h->prec == STOKES_PREC_FP64 ? 8 : 4) * C.L.n, s));
     double *out = xdev ? xf : h->stage_out;
     if ((rc = from_level(h, F.x, out, F.L.n, s))) return rc;
-    launch_mask(F.L, out, s);
+    launch_mask<double>(F.L, out, s);
     if (!xdev) CK(cudaMemcpyAsync(xf, out, sizeof(double) * F.L.n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return STOKES_OK;
@@ -912,7 +923,7 @@ int stokes_coarse_solve(stokes_t h, const double *b, double *x, void *stream) {
     if ((rc = ensure_stage(h))) return rc;
     const double *bd;
     if ((rc = stage_in(h, b, C.L.n, h->stage_in, &bd, s))) return rc;
-    if ((rc = to_level(h, bd, C.b, C.L.n, s))) return rc;
+    if ((rc = to_level(h, C.L, bd, C.b, s))) return rc;
     CK(cudaMemsetAsync(C.x, 0, (h->prec == STOKES_PREC_FP64 ? 8 : 4) * C.L.n, s));
     auto run = [&](auto tag) {
         using T = decltype(tag);

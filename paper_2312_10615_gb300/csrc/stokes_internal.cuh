@@ -78,6 +78,53 @@ __device__ __forceinline__ T cell_Lx(const T *__restrict__ x, const Lev &L, int 
     return -K.ih * div - K.gam * x[pidx(L, 3, i, j, k)];
 }
 
+// ---- fast stencils.  They rely on the invariant kept by every internal vector: entries that are
+// not unknowns (wall-normal faces) hold 0.  A face stencil then needs a guard only for tangential
+// neighbours outside the box (no array entry exists there); a cell stencil needs none.  All
+// neighbour addresses are constant strides from one base address.
+__host__ __device__ inline long long comp_base(const Lev &L, int c) {
+    return c == 0 ? L.off[0] : (c == 1 ? L.off[1] : (c == 2 ? L.off[2] : L.off[3]));
+}
+
+// (L~x)_f on the active face (i,j,k) of component C
+template <class T, int C>
+__device__ __forceinline__ T face_Lx_fast(const T *__restrict__ x, const Lev &L, int i, int j, int k,
+                                          const Coef<T> &K) {
+    const long long sy = L.nx + (C == 0), sz = sy * (L.ny + (C == 1));
+    const T *xc = x + comp_base(L, C) + i + sy * j + sz * k;
+    T s = T(6) * xc[0];
+    if (C == 0) s -= xc[-1] + xc[1];
+    else s -= (i > 0 ? xc[-1] : T(0)) + (i < L.nx - 1 ? xc[1] : T(0));
+    if (C == 1) s -= xc[-sy] + xc[sy];
+    else s -= (j > 0 ? xc[-sy] : T(0)) + (j < L.ny - 1 ? xc[sy] : T(0));
+    if (C == 2) s -= xc[-sz] + xc[sz];
+    else s -= (k > 0 ? xc[-sz] : T(0)) + (k < L.nz - 1 ? xc[sz] : T(0));
+    const long long cy = L.nx, cz = (long long)L.nx * L.ny;
+    const T *pc = x + L.off[3] + i + cy * j + cz * k;
+    const long long ps = C == 0 ? 1 : (C == 1 ? cy : cz);
+    return K.eh2 * s + K.ih * (pc[0] - pc[-ps]);
+}
+
+// (L~x)_c on cell (i,j,k)
+template <class T>
+__device__ __forceinline__ T cell_Lx_fast(const T *__restrict__ x, const Lev &L, int i, int j, int k,
+                                          const Coef<T> &K) {
+    const long long nx = L.nx, ny = L.ny;
+    const T *u = x + L.off[0] + i + (nx + 1) * (j + ny * k);
+    const T *v = x + L.off[1] + i + nx * (j + (ny + 1) * k);
+    const T *w = x + L.off[2] + i + nx * (j + ny * k);
+    T div = (u[1] - u[0]) + (v[nx] - v[0]) + (w[nx * ny] - w[0]);
+    return -K.ih * div - K.gam * x[L.off[3] + i + nx * (j + ny * k)];
+}
+
+// runtime component dispatch (the component is uniform across a thread block)
+template <class T>
+__device__ __forceinline__ T face_Lx_any(const T *__restrict__ x, const Lev &L, int c, int i, int j, int k,
+                                         const Coef<T> &K) {
+    return c == 0 ? face_Lx_fast<T, 0>(x, L, i, j, k, K)
+                  : (c == 1 ? face_Lx_fast<T, 1>(x, L, i, j, k, K) : face_Lx_fast<T, 2>(x, L, i, j, k, K));
+}
+
 // decode a per-component thread index t (< ex*ey*ez) into (i,j,k)
 __device__ __forceinline__ void decode3(long long t, int ex, int ey, int &i, int &j, int &k) {
     i = (int)(t % ex);
