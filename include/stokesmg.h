@@ -43,7 +43,7 @@ extern "C" {
 #define STOKES_ERR_BREAKDOWN -4     /* SQMR: sigma = q^T L q = 0 or rho = s^T t = 0 (Alg. 4 divides by both) */
 #define STOKES_ERR_NOT_CONVERGED -5 /* SQMR: max_iter reached before the tolerance */
 #define STOKES_ERR_NAN -6           /* a NaN/Inf appeared in the SQMR scalars */
-#define STOKES_ERR_TIMEOUT -7       /* reserved: a device-side wait ran out of its iteration limit */
+#define STOKES_ERR_TIMEOUT -7       /* a device-side grid barrier ran out of its iteration limit */
 #define STOKES_ERR_UNSUPPORTED -8   /* valid request this build does not implement (e.g. exterior cells) */
 
 /* precision of the V-cycle (the SQMR recurrences, the true-residual check and the coarsest
@@ -73,6 +73,8 @@ typedef struct {
     int kb_vanka;  /* symmetric Vanka sweeps before and after the symmetric DGS in Alg. 3; default 1 */
     int precision; /* STOKES_PREC_FP64 (default) or STOKES_PREC_FP32 V-cycle */
     int use_graphs;/* capture the V-cycle / SQMR iteration in CUDA graphs (default 1) */
+    int vanka_persistent; /* 1 (default): one cooperative launch per symmetric Vanka sweep (grid barrier
+                             with a bounded spin; expiry -> STOKES_ERR_TIMEOUT); 0: two launches per colour */
 } stokes_opts_t;
 
 typedef struct {

@@ -28,6 +28,22 @@ void launch_vanka_compute(const Lev &L, const T *x, const T *b, const int *cells
                           int cap, cudaStream_t s);
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s);
+// a whole symmetric Vanka sweep (colours 0..7 then 7..0), `sweeps` times, in ONE cooperative
+// launch: compute / grid barrier / apply / grid barrier per colour.  The barrier spins at most
+// kBarrierSpinLimit polls; on expiry it sets bar->err and every block stops waiting.
+struct GridBarrier {
+    unsigned count, gen;
+    int err, pad;
+};
+constexpr unsigned kBarrierSpinLimit = 1u << 22;
+struct VankaLists {
+    const int *cells[8];
+    int count[8];
+};
+template <class T>
+void launch_vanka_sweep(const Lev &L, T *x, const T *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
+                        int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s);
+template <class T> int vanka_sweep_blocks_per_sm();
 // transfers (Sec. 2): bc = R rf,  xf += P ec
 template <class T> void launch_restrict(const Lev &F, const Lev &C, const T *rf, T *bc, cudaStream_t s);
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s);

@@ -13,6 +13,7 @@ namespace smg {
 
 namespace {
 constexpr int BX = 32, BY = 8;
+constexpr int KZ = 8;  // z-planes marched by one thread (fewer, longer-lived blocks)
 const dim3 kBlock3(BX, BY, 1);
 
 inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
@@ -26,7 +27,7 @@ inline Geo geo_components(const Lev &L, int ncomp) {
     int mx = L.nx + 1, my = L.ny + 1, mz = L.nz + 1;
     Geo g;
     g.gy = cdiv(my, BY);
-    g.grid = dim3(cdiv(mx, BX), g.gy * ncomp, mz);
+    g.grid = dim3(cdiv(mx, BX), g.gy * ncomp, cdiv(mz, KZ));
     return g;
 }
 
@@ -55,13 +56,16 @@ __device__ __forceinline__ bool in_v2_cell(const Lev &L, int i, int j, int k) {
 __device__ __forceinline__ long long cell_lin(const Lev &L, int i, int j, int k) {
     return i + (long long)L.nx * (j + (long long)L.ny * k);
 }
-// (c, i, j, k) of the calling thread in a geo_components launch; false if outside component c's box
-__device__ __forceinline__ bool thread_entry(const Lev &L, int gy, int &c, int &i, int &j, int &k) {
+// (c, i, j) and the z range [k0, k1) of the calling thread in a geo_components launch; false if the
+// thread lies outside component c's box
+__device__ __forceinline__ bool thread_entry(const Lev &L, int gy, int &c, int &i, int &j, int &k0, int &k1) {
     c = blockIdx.y / gy;
     i = blockIdx.x * BX + threadIdx.x;
     j = (blockIdx.y - c * gy) * BY + threadIdx.y;
-    k = blockIdx.z;
-    return i < ext(L, c, 0) && j < ext(L, c, 1) && k < ext(L, c, 2);
+    k0 = blockIdx.z * KZ;
+    int ez = ext(L, c, 2);
+    k1 = k0 + KZ < ez ? k0 + KZ : ez;
+    return i < ext(L, c, 0) && j < ext(L, c, 1) && k0 < ez;
 }
 }  // namespace
 
@@ -70,15 +74,17 @@ __device__ __forceinline__ bool thread_entry(const Lev &L, int gy, int &c, int &
 template <class T>
 __global__ void __launch_bounds__(256) k_apply(Lev L, int gy, const T *__restrict__ x, const T *__restrict__ b,
                                                T *__restrict__ y, Coef<T> K) {
-    int c, i, j, k;
-    if (!thread_entry(L, gy, c, i, j, k)) return;
-    long long q = pidx(L, c, i, j, k);
-    if (!active(L, c, i, j, k)) {
-        y[q] = T(0);
-        return;
+    int c, i, j, k0, k1;
+    if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
+    for (int k = k0; k < k1; ++k) {
+        long long q = pidx(L, c, i, j, k);
+        if (!active(L, c, i, j, k)) {
+            y[q] = T(0);
+            continue;
+        }
+        T v = c < 3 ? face_Lx_any(x, L, c, i, j, k, K) : cell_Lx_fast(x, L, i, j, k, K);
+        y[q] = b ? b[q] - v : v;
     }
-    T v = c < 3 ? face_Lx_any(x, L, c, i, j, k, K) : cell_Lx_fast(x, L, i, j, k, K);
-    y[q] = b ? b[q] - v : v;
 }
 
 template <class T> void launch_apply(const Lev &L, const T *x, const T *b, T *y, double gam, cudaStream_t s) {
@@ -98,12 +104,13 @@ __device__ __forceinline__ long long gidx(const Lev &L, int c, int i, int j, int
 
 __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__restrict__ f, const double *__restrict__ g,
                                              double *__restrict__ b, Coef<double> K) {
-    int c, i, j, k;
-    if (!thread_entry(L, gy, c, i, j, k)) return;
+    int c, i, j, k0, k1;
+    if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
+    for (int k = k0; k < k1; ++k) {
     long long q = pidx(L, c, i, j, k);
     if (!active(L, c, i, j, k)) {
         b[q] = 0.0;
-        return;
+        continue;
     }
     double v = f ? f[q] : 0.0;
     if (g) {
@@ -122,6 +129,7 @@ __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__rest
         }
     }
     b[q] = v;
+    }
 }
 
 void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaStream_t s) {
@@ -140,14 +148,16 @@ __global__ void __launch_bounds__(256) k_dgs_u(Lev L, int gy, T *__restrict__ x,
     int lo[3], cnt[3];
     v2_face_range(L, c, lo, cnt);
     int j = lo[1] + (blockIdx.y - c * gy) * BY + threadIdx.y;
-    int k = lo[2] + blockIdx.z;
-    if (j >= lo[1] + cnt[1] || k >= lo[2] + cnt[2]) return;
-    int i = lo[0] + 2 * (blockIdx.x * BX + threadIdx.x);
-    i += (i + j + k + parity) & 1;
-    if (i >= lo[0] + cnt[0]) return;
-    long long q = pidx(L, c, i, j, k);
-    T r = b[q] - face_Lx_any(x, L, c, i, j, k, K);
-    x[q] += r / (T(6) * K.eh2);
+    if (j >= lo[1] + cnt[1]) return;
+    int kend = lo[2] + cnt[2];
+    for (int k = lo[2] + blockIdx.z * KZ; k < kend && k < lo[2] + (int)(blockIdx.z + 1) * KZ; ++k) {
+        int i = lo[0] + 2 * (blockIdx.x * BX + threadIdx.x);
+        i += (i + j + k + parity) & 1;
+        if (i >= lo[0] + cnt[0]) continue;
+        long long q = pidx(L, c, i, j, k);
+        T r = b[q] - face_Lx_any(x, L, c, i, j, k, K);
+        x[q] += r / (T(6) * K.eh2);
+    }
 }
 
 template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s) {
@@ -161,7 +171,7 @@ template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity,
         mz = cnt[2] > mz ? cnt[2] : mz;
     }
     int gy = cdiv(my, BY);
-    dim3 grid(cdiv((mx + 1) / 2, BX), gy * 3, mz);
+    dim3 grid(cdiv((mx + 1) / 2, BX), gy * 3, cdiv(mz, KZ));
     k_dgs_u<T><<<grid, kBlock3, 0, s>>>(L, gy, x, b, parity, coef<T>(L, L.gamma));
 }
 
@@ -240,12 +250,13 @@ __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, 
 template <class T>
 __global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, int gy, T *__restrict__ x, const T *__restrict__ b,
                                                         T *__restrict__ gh, const T *__restrict__ delta, Coef<T> K) {
-    int c, i, j, k;
-    if (!thread_entry(L, gy, c, i, j, k)) return;
+    int c, i, j, k0, k1;
+    if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
+    for (int k = k0; k < k1; ++k) {
     long long q = pidx(L, c, i, j, k);
     if (!active(L, c, i, j, k)) {
         gh[q] = T(0);
-        return;
+        continue;
     }
     T v;
     if (c == 3 && delta) {
@@ -271,6 +282,7 @@ __global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, int gy, T *__rest
         v = b[q] - cell_Lx_fast(x, L, i, j, k, KB);
     }
     gh[q] = v;
+    }
 }
 
 template <class T>
@@ -400,6 +412,124 @@ void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T
     k_vanka_apply<T><<<cdiv(8LL * ncell, 256), 256, 0, s>>>(L, x, cells, ncell, corr, cap);
 }
 
+// ---- one cooperative launch per symmetric Vanka sweep ----
+// grid-wide barrier: generation counter in global memory, bounded spin (see kernels.h)
+__device__ __forceinline__ void grid_sync(GridBarrier *bar, unsigned nblocks) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &bar->gen;
+        volatile int *verr = &bar->err;
+        if (!*verr) {
+            unsigned g = *vgen;
+            __threadfence();
+            if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+                atomicExch(&bar->count, 0u);
+                __threadfence();
+                atomicAdd(&bar->gen, 1u);
+            } else {
+                unsigned spins = 0;
+                while (*vgen == g && !*verr) {
+                    if (++spins > kBarrierSpinLimit) {
+                        atomicExch(&bar->err, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const T *__restrict__ b,
+                                                   int cellw, int a, unsigned gmask, const T *__restrict__ kinv,
+                                                   T *__restrict__ corr, int cap, int slot, const Coef<T> &K) {
+    int i, j, k;
+    unpack_cell(cellw, i, j, k);
+    int cfg = (i >= 1) | ((i + 1 <= L.nx - 1) << 1) | ((j >= 1) << 2) | ((j + 1 <= L.ny - 1) << 3) |
+              ((k >= 1) << 4) | ((k + 1 <= L.nz - 1) << 5);
+    T r = T(0);
+    if (a < 6) {
+        int d = a >> 1, side = a & 1;
+        int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+        if ((cfg >> a) & 1) r = b[pidx(L, d, fi, fj, fk)] - face_Lx_any(x, L, d, fi, fj, fk, K);
+    } else if (a == 6) {
+        r = b[pidx(L, 3, i, j, k)] - cell_Lx_fast(x, L, i, j, k, K);
+    }
+    const T *Ki = kinv + cfg * 49 + (a < 7 ? a : 6) * 7;
+    T s = T(0);
+#pragma unroll
+    for (int bb = 0; bb < 7; ++bb) s += Ki[bb] * __shfl_sync(gmask, r, bb, 8);
+    if (a < 7) corr[(long long)a * cap + slot] = s;
+}
+
+template <class T>
+__device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x, int cellw, int a,
+                                                 const T *__restrict__ corr, int cap, int slot) {
+    if (a == 7) return;
+    int i, j, k;
+    unpack_cell(cellw, i, j, k);
+    if (a == 6) {
+        x[pidx(L, 3, i, j, k)] += corr[6LL * cap + slot];
+        return;
+    }
+    int d = a >> 1, side = a & 1;
+    int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+    if (active(L, d, fi, fj, fk)) x[pidx(L, d, fi, fj, fk)] += corr[(long long)a * cap + slot];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, const T *__restrict__ b,
+                                                     VankaLists lists, const T *__restrict__ kinv,
+                                                     T *__restrict__ corr, int cap, Coef<T> K, int sweeps,
+                                                     GridBarrier *bar) {
+    const unsigned nb = gridDim.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 8: lanes keep their group
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);
+    for (int sw = 0; sw < sweeps; ++sw)
+        for (int ph = 0; ph < 16; ++ph) {
+            int col = ph < 8 ? ph : 15 - ph;
+            int n = lists.count[col];
+            if (n == 0) continue;
+            const int *cells = lists.cells[col];
+            for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; (t >> 3) < n; t += stride)
+                vanka_compute_lane(L, x, b, cells[t >> 3], (int)(t & 7), gmask, kinv, corr, cap, (int)(t >> 3), K);
+            grid_sync(bar, nb);
+            for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; (t >> 3) < n; t += stride)
+                vanka_apply_lane(L, x, cells[t >> 3], (int)(t & 7), corr, cap, (int)(t >> 3));
+            grid_sync(bar, nb);
+        }
+}
+
+template <class T> int vanka_sweep_blocks_per_sm() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vanka_sweep<T>, 256, 0);
+    return nb;
+}
+
+template <class T>
+void launch_vanka_sweep(const Lev &L, T *x, const T *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
+                        int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s) {
+    int mx = 0;
+    for (int c = 0; c < 8; ++c) mx = lists.count[c] > mx ? lists.count[c] : mx;
+    if (mx == 0 || sweeps <= 0) return;
+    int need = cdiv(8LL * mx, 256);
+    int nb = need < max_blocks ? need : max_blocks;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_vanka_sweep<T>, L, x, b, lists, kinv, corr, cap, coef<T>(L, L.gamma), sweeps, bar);
+}
+
 // ------------------------------------------------------------------------------------------
 // Sec. 2 transfers.  P (coarse -> fine): pressure constant per coarse cell; a face value takes
 // weight 1 from a coincident coarse face or 1/2 + 1/2 from the two coarse faces around it along
@@ -437,12 +567,13 @@ __device__ __forceinline__ T restrict_face(const Lev &F, const Lev &Cl, const T 
 template <class T>
 __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const T *__restrict__ rf,
                                                   T *__restrict__ bc) {
-    int c, I, J, Kk;
-    if (!thread_entry(C, gy, c, I, J, Kk)) return;
+    int c, I, J, k0, k1;
+    if (!thread_entry(C, gy, c, I, J, k0, k1)) return;
+    for (int Kk = k0; Kk < k1; ++Kk) {
     long long q = pidx(C, c, I, J, Kk);
     if (!active(C, c, I, J, Kk)) {
         bc[q] = T(0);
-        return;
+        continue;
     }
     T v;
     switch (c) {
@@ -458,6 +589,7 @@ __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const T 
     }
     }
     bc[q] = v;
+    }
 }
 
 // 1D prolongation weights along one axis: normal axis (coincident: {I, 1}; between: {I0, I1, 1/2})
@@ -508,9 +640,10 @@ __device__ __forceinline__ T prolong_face(const Lev &C, const T *__restrict__ ec
 
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev C, int gy, const T *__restrict__ ec, T *__restrict__ xf) {
-    int c, fi, fj, fk;
-    if (!thread_entry(F, gy, c, fi, fj, fk)) return;
-    if (!active(F, c, fi, fj, fk)) return;
+    int c, fi, fj, k0, k1;
+    if (!thread_entry(F, gy, c, fi, fj, k0, k1)) return;
+    for (int fk = k0; fk < k1; ++fk) {
+    if (!active(F, c, fi, fj, fk)) continue;
     long long q = pidx(F, c, fi, fj, fk);
     T v;
     switch (c) {
@@ -520,6 +653,7 @@ __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev C, int gy, const T *
     default: v = ec[pidx(C, 3, fi >> 1, fj >> 1, fk >> 1)];
     }
     xf[q] += v;
+    }
 }
 
 template <class T> void launch_restrict(const Lev &F, const Lev &C, const T *rf, T *bc, cudaStream_t s) {
@@ -560,9 +694,10 @@ void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, co
 
 // ------------------------------------------------------------------------------------------
 template <class T> __global__ void __launch_bounds__(256) k_mask(Lev L, int gy, T *__restrict__ x) {
-    int c, i, j, k;
-    if (!thread_entry(L, gy, c, i, j, k)) return;
-    if (!active(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = T(0);
+    int c, i, j, k0, k1;
+    if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
+    for (int k = k0; k < k1; ++k)
+        if (!active(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = T(0);
 }
 template <class T> void launch_mask(const Lev &L, T *x, cudaStream_t s) {
     Geo g = geo_components(L, 4);
@@ -593,7 +728,10 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template void launch_vanka_apply<T>(const Lev &, T *, const int *, int, const T *, int, cudaStream_t);        \
     template void launch_restrict<T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);                     \
     template void launch_prolong<T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);                      \
-    template void launch_coarse<T>(const Lev &, const int *, int, const double *, const T *, T *, cudaStream_t);
+    template void launch_coarse<T>(const Lev &, const int *, int, const double *, const T *, T *, cudaStream_t);   \
+    template void launch_vanka_sweep<T>(const Lev &, T *, const T *, const VankaLists &, const T *, T *, int, int,  \
+                                        GridBarrier *, int, cudaStream_t);                                         \
+    template int vanka_sweep_blocks_per_sm<T>();
 SMG_INST(float)
 SMG_INST(double)
 template void launch_convert<double, float>(long long, const double *, float *, cudaStream_t);

@@ -32,6 +32,7 @@ struct LevelBuf {
     int *vcells[8] = {};
     int vcount[8] = {};
     int vcap = 0;
+    VankaLists lists;
 };
 
 int cuda_status(cudaError_t e) {
@@ -155,6 +156,9 @@ struct stokes_s {
     int prec = STOKES_PREC_FP64;
     int kb = 1;
     int use_graphs = 1;
+    int vanka_persistent = 1;
+    int vanka_max_blocks = 0;  // co-resident blocks of the cooperative Vanka sweep
+    GridBarrier *bar = nullptr;
     double eta = 1.0, gamma = 1e-3;
     std::vector<LevelBuf> lev;
     int nc = 0;
@@ -223,9 +227,20 @@ template <class T> void vanka_colour(stokes_s *h, int l, int col, cudaStream_t s
     prof(STOKES_K_VANKA_APPLY, l, s,
          [&] { launch_vanka_apply<T>(B.L, (T *)B.x, B.vcells[col], B.vcount[col], (const T *)B.corr, B.vcap, s); });
 }
-template <class T> void vanka_sym(stokes_s *h, int l, cudaStream_t s) {
-    for (int c = 0; c < 8; ++c) vanka_colour<T>(h, l, c, s);
-    for (int c = 7; c >= 0; --c) vanka_colour<T>(h, l, c, s);
+// `sweeps` symmetric Vanka sweeps (App. C: colours 0..7 then 7..0)
+template <class T> void vanka_sym(stokes_s *h, int l, cudaStream_t s, int sweeps = 1) {
+    LevelBuf &B = h->lev[l];
+    if (h->vanka_persistent) {
+        prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
+            launch_vanka_sweep<T>(B.L, (T *)B.x, (const T *)B.b, B.lists, (const T *)B.kinv, (T *)B.corr, B.vcap, sweeps,
+                                  h->bar, h->vanka_max_blocks, s);
+        });
+        return;
+    }
+    for (int k = 0; k < sweeps; ++k) {
+        for (int c = 0; c < 8; ++c) vanka_colour<T>(h, l, c, s);
+        for (int c = 7; c >= 0; --c) vanka_colour<T>(h, l, c, s);
+    }
 }
 template <class T> void dgs_forward(stokes_s *h, int l, cudaStream_t s) {
     LevelBuf &B = h->lev[l];
@@ -254,10 +269,10 @@ template <class T> void dgs_backward(stokes_s *h, int l, cudaStream_t s, bool fo
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 0, s); });
 }
 template <class T> void smooth(stokes_s *h, int l, cudaStream_t s) {
-    for (int k = 0; k < h->kb; ++k) vanka_sym<T>(h, l, s);
+    vanka_sym<T>(h, l, s, h->kb);
     dgs_forward<T>(h, l, s);
     dgs_backward<T>(h, l, s, true);
-    for (int k = 0; k < h->kb; ++k) vanka_sym<T>(h, l, s);
+    vanka_sym<T>(h, l, s, h->kb);
 }
 template <class T> void vcycle(stokes_s *h, cudaStream_t s) {
     int n = h->nlev();
@@ -428,6 +443,7 @@ void stokes_opts_default(stokes_opts_t *o) {
     o->kb_vanka = 1;
     o->precision = STOKES_PREC_FP64;
     o->use_graphs = 1;
+    o->vanka_persistent = 1;
 }
 
 const char *stokes_strerror(int st) {
@@ -479,6 +495,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     h->prec = o.precision;
     h->kb = o.kb_vanka;
     h->use_graphs = o.use_graphs;
+    h->vanka_persistent = o.vanka_persistent;
     h->eta = viscosity;
     h->gamma = o.gamma;
     double hh = grid->h > 0 ? grid->h : 1.0 / grid->nx;
@@ -543,6 +560,10 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
                 CK(cudaMemcpy(B.vcells[c], cells[c].data(), sizeof(int) * cells[c].size(), cudaMemcpyHostToDevice));
         }
         if ((rc = h->alloc(&B.corr, es * 7 * (size_t)B.vcap))) return rc;
+        for (int c = 0; c < 8; ++c) {
+            B.lists.cells[c] = B.vcells[c];
+            B.lists.count[c] = B.vcount[c];
+        }
         // Sec. 6: pre-factorised local problems, one per configuration of unknown faces
         std::vector<double> kd(64 * 49, 0.0);
         for (int cfg = 0; cfg < 64; ++cfg)
@@ -565,6 +586,15 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
         std::memset(h->hout, 0, 4 * sizeof(double));
     }
     CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+    {
+        int rc, nsm = 0, coop = 0;
+        if ((rc = h->alloc(&h->bar, sizeof(GridBarrier)))) return rc;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
+        CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev));
+        int per_sm = h->prec == STOKES_PREC_FP64 ? vanka_sweep_blocks_per_sm<double>() : vanka_sweep_blocks_per_sm<float>();
+        h->vanka_max_blocks = per_sm * nsm;
+        if (!coop || h->vanka_max_blocks <= 0) h->vanka_persistent = 0;
+    }
     CK(cudaDeviceSynchronize());
     *out = h.release();
     return STOKES_OK;
@@ -649,6 +679,7 @@ int mg_precondition(stokes_t h, const double *sv, double *tv, void *stream) {
     const double *sd;
     if ((rc = stage_in(h, sv, n, h->stage_in, &sd, s))) return rc;
     if ((rc = to_level(h, h->lev[0].L, sd, h->lev[0].b, s))) return rc;
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
     if ((rc = run_vcycle(h, s))) return rc;
     bool tdev = is_device_ptr(tv);
     double *td = tdev ? tv : h->stage_out;
@@ -710,6 +741,7 @@ extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol,
     CK(cudaMemcpyAsync(h->x, xv, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     launch_mask<double>(L, h->bvec, s);
     launch_mask<double>(L, h->x, s);
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
     // |b|
     double bb = 0.0, ss = 0.0, rr = 0.0, flags = 0.0;
     launch_dot2<double>(n, h->bvec, nullptr, h->partials, s);
@@ -779,7 +811,12 @@ finish:
         rel = nb > 0 ? std::sqrt(r2) / nb : 0.0;
     }
     CK(cudaMemcpyAsync(xv, h->x, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    {
+        GridBarrier hb;
+        CK(cudaMemcpyAsync(&hb, h->bar, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hb.err) status = STOKES_ERR_TIMEOUT;
+    }
     if (info) {
         info->iterations = it;
         info->rel_residual = rel;
@@ -837,6 +874,7 @@ int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, 
     if ((rc = to_level(h, B.L, xd, B.x, s))) return rc;
     if ((rc = stage_in(h, b, n, h->stage_in, &bd, s))) return rc;
     if ((rc = to_level(h, B.L, bd, B.b, s))) return rc;
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
     auto body = [&](auto tag) {
         using T = decltype(tag);
         switch (which) {

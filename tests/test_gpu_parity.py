@@ -186,6 +186,15 @@ def test_vcycle_fp32_parity_and_symmetry():
     assert abs(a - b) <= 1e-5 * float(torch.linalg.norm(x) * torch.linalg.norm(S.precondition(y)))
 
 
+def test_persistent_vanka_matches_per_colour_launches():
+    # one cooperative launch per symmetric sweep (grid barriers) vs two launches per colour
+    o, S = pair((32, 32, 32))
+    Sc = smg.Stokes(32, vanka_persistent=False)
+    s = cuda(rand_masked(o, 26))
+    assert float(torch.max(torch.abs(S.precondition(s) - Sc.precondition(s)))) == 0.0
+    Sc.close()
+
+
 def test_graph_and_eager_paths_agree():
     o, Sg = pair((32, 32, 32))
     Se = smg.Stokes(32, use_graphs=False)
