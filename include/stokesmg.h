@@ -73,8 +73,8 @@ typedef struct {
     int kb_vanka;  /* symmetric Vanka sweeps before and after the symmetric DGS in Alg. 3; default 1 */
     int precision; /* STOKES_PREC_FP64 (default) or STOKES_PREC_FP32 V-cycle */
     int use_graphs;/* capture the V-cycle / SQMR iteration in CUDA graphs (default 1) */
-    int vanka_persistent; /* 1 (default): one cooperative launch per symmetric Vanka sweep (grid barrier
-                             with a bounded spin; expiry -> STOKES_ERR_TIMEOUT); 0: two launches per colour */
+    int vanka_persistent; /* 0 (default): two launches per Vanka colour; 1: one cooperative launch per
+                             symmetric sweep (grid barrier with a bounded spin; expiry -> STOKES_ERR_TIMEOUT) */
 } stokes_opts_t;
 
 typedef struct {

@@ -145,7 +145,7 @@ def stokes_opts_default():
 
 
 def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest_max=8, gamma=1e-3, kb_vanka=1,
-                  precision=PREC_FP64, use_graphs=True, vanka_persistent=True):
+                  precision=PREC_FP64, use_graphs=True, vanka_persistent=False):
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     g = stokes_grid_t(nx, ny, nz, h, levels, coarsest_max)

@@ -443,7 +443,7 @@ void stokes_opts_default(stokes_opts_t *o) {
     o->kb_vanka = 1;
     o->precision = STOKES_PREC_FP64;
     o->use_graphs = 1;
-    o->vanka_persistent = 1;
+    o->vanka_persistent = 0;
 }
 
 const char *stokes_strerror(int st) {

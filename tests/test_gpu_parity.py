@@ -189,7 +189,7 @@ def test_vcycle_fp32_parity_and_symmetry():
 def test_persistent_vanka_matches_per_colour_launches():
     # one cooperative launch per symmetric sweep (grid barriers) vs two launches per colour
     o, S = pair((32, 32, 32))
-    Sc = smg.Stokes(32, vanka_persistent=False)
+    Sc = smg.Stokes(32, vanka_persistent=True)
     s = cuda(rand_masked(o, 26))
     assert float(torch.max(torch.abs(S.precondition(s) - Sc.precondition(s)))) == 0.0
     Sc.close()
