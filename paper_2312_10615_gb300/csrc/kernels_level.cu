@@ -70,26 +70,30 @@ __device__ __forceinline__ bool thread_entry(const Lev &L, int gy, int &c, int &
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// y = L~x or b - L~x on every packed entry (0 off the unknowns); x must hold 0 off the unknowns
+// y = L~x or b - L~x on every packed entry (0 off the unknowns); x must hold 0 off the unknowns.
+// Cell-centric: one thread per position (i,j) marching KZ planes, four entries per position.
+inline dim3 cell_grid_h(const Lev &L) {
+    return dim3(cdiv(L.nx + 1, BX), cdiv(L.ny + 1, BY), cdiv(L.nz + 1, KZ));
+}
+
 template <class T>
-__global__ void __launch_bounds__(256) k_apply(Lev L, int gy, const T *__restrict__ x, const T *__restrict__ b,
+__global__ void __launch_bounds__(256) k_apply(Lev L, const T *__restrict__ x, const T *__restrict__ b,
                                                T *__restrict__ y, Coef<T> K) {
-    int c, i, j, k0, k1;
-    if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > L.nx || j > L.ny) return;
+    int k0 = blockIdx.z * KZ, k1 = k0 + KZ < L.nz + 1 ? k0 + KZ : L.nz + 1;
     for (int k = k0; k < k1; ++k) {
-        long long q = pidx(L, c, i, j, k);
-        if (!active(L, c, i, j, k)) {
-            y[q] = T(0);
-            continue;
-        }
-        T v = c < 3 ? face_Lx_any(x, L, c, i, j, k, K) : cell_Lx_fast(x, L, i, j, k, K);
-        y[q] = b ? b[q] - v : v;
+        Quad Q = quad_at(L, i, j, k);
+        T o[4];
+        quad_eval<T, OP_APPLY>(x, L, i, j, k, Q, K, o);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (Q.ex[c]) y[Q.q[c]] = Q.act[c] ? (b ? b[Q.q[c]] - o[c] : o[c]) : T(0);
     }
 }
 
 template <class T> void launch_apply(const Lev &L, const T *x, const T *b, T *y, double gam, cudaStream_t s) {
-    Geo g = geo_components(L, 4);
-    k_apply<T><<<g.grid, kBlock3, 0, s>>>(L, g.gy, x, b, y, coef<T>(L, gam));
+    k_apply<T><<<cell_grid_h(L), kBlock3, 0, s>>>(L, x, b, y, coef<T>(L, gam));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -141,38 +145,42 @@ void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaS
 // Alg. 2 velocity block: V2 faces of one parity (i+j+k), u, v, w together (A does not couple
 // components; same-parity faces are not A-neighbours, pressures are not written) -- in place.
 // Thread x covers every other face of a row so no thread idles.
+// Cell-centric: the thread of V2 cell (i,j,k) of the given parity updates its low faces u, v, w (all
+// three share the cell's parity), each if it lies in that component's V2 range.  Inside the V2
+// cell range every stencil neighbour exists, so no guards are needed.
 template <class T>
-__global__ void __launch_bounds__(256) k_dgs_u(Lev L, int gy, T *__restrict__ x, const T *__restrict__ b, int parity,
+__device__ __forceinline__ void dgs_face(T *__restrict__ x, const T *__restrict__ b, long long q, long long sy,
+                                         long long sz, T pc, T pm, const Coef<T> &K) {
+    T s = T(6) * x[q] - x[q - 1] - x[q + 1] - x[q - sy] - x[q + sy] - x[q - sz] - x[q + sz];
+    T r = b[q] - (K.eh2 * s + K.ih * (pc - pm));
+    x[q] += r / (T(6) * K.eh2);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_dgs_u(Lev L, T *__restrict__ x, const T *__restrict__ b, int parity,
                                                Coef<T> K) {
-    int c = blockIdx.y / gy;
-    int lo[3], cnt[3];
-    v2_face_range(L, c, lo, cnt);
-    int j = lo[1] + (blockIdx.y - c * gy) * BY + threadIdx.y;
-    if (j >= lo[1] + cnt[1]) return;
-    int kend = lo[2] + cnt[2];
-    for (int k = lo[2] + blockIdx.z * KZ; k < kend && k < lo[2] + (int)(blockIdx.z + 1) * KZ; ++k) {
-        int i = lo[0] + 2 * (blockIdx.x * BX + threadIdx.x);
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    int j = 1 + blockIdx.y * BY + threadIdx.y;
+    if (j > ny - 2) return;
+    const long long lnx = nx, lny = ny;
+    const long long uy = lnx + 1, uz = (lnx + 1) * lny, vy = lnx, vz = lnx * (lny + 1), wz = lnx * lny;
+    int k0 = 1 + blockIdx.z * KZ, k1 = k0 + KZ < nz - 1 ? k0 + KZ : nz - 1;
+    for (int k = k0; k < k1; ++k) {
+        int i = 1 + 2 * (blockIdx.x * BX + threadIdx.x);
         i += (i + j + k + parity) & 1;
-        if (i >= lo[0] + cnt[0]) continue;
-        long long q = pidx(L, c, i, j, k);
-        T r = b[q] - face_Lx_any(x, L, c, i, j, k, K);
-        x[q] += r / (T(6) * K.eh2);
+        if (i > nx - 2) continue;
+        long long pq = L.off[3] + i + lnx * (j + lny * k);
+        T pc = x[pq];
+        if (i >= 2) dgs_face(x, b, L.off[0] + i + uy * j + uz * k, uy, uz, pc, x[pq - 1], K);
+        if (j >= 2) dgs_face(x, b, L.off[1] + i + vy * j + vz * k, vy, vz, pc, x[pq - lnx], K);
+        if (k >= 2) dgs_face(x, b, L.off[2] + i + lnx * j + wz * k, lnx, wz, pc, x[pq - lnx * lny], K);
     }
 }
 
 template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s) {
-    int mx = 0, my = 0, mz = 0;
-    for (int c = 0; c < 3; ++c) {
-        int lo[3], cnt[3];
-        v2_face_range(L, c, lo, cnt);
-        if (cnt[0] * cnt[1] * cnt[2] == 0) return;
-        mx = cnt[0] > mx ? cnt[0] : mx;
-        my = cnt[1] > my ? cnt[1] : my;
-        mz = cnt[2] > mz ? cnt[2] : mz;
-    }
-    int gy = cdiv(my, BY);
-    dim3 grid(cdiv((mx + 1) / 2, BX), gy * 3, cdiv(mz, KZ));
-    k_dgs_u<T><<<grid, kBlock3, 0, s>>>(L, gy, x, b, parity, coef<T>(L, L.gamma));
+    if (L.nx < 3 || L.ny < 3 || L.nz < 3) return;
+    dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), cdiv(L.nz - 2, KZ));
+    k_dgs_u<T><<<grid, kBlock3, 0, s>>>(L, x, b, parity, coef<T>(L, L.gamma));
 }
 
 // Alg. 2 pressure block, one colour (i mod 2, j mod 2, k mod 2):
@@ -246,42 +254,31 @@ __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, 
 //   p_c += [ sum_axes (r_high_face - r_low_face)/h + eta/h^2 (6 r_c - sum of the 6 neighbour r) ] / d
 // (M_{.c}^T r with the full column of M).  Same-colour cells read none of each other's values.
 // The same launch also finishes the forward sweep: the neighbour-pressure part of the last
-// colours (gather form of k_dgs_p_gather), which the prep never reads.
+// colours (gather form of k_dgs_p_gather), which the prep never reads.  Cell-centric like k_apply.
 template <class T>
-__global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, int gy, T *__restrict__ x, const T *__restrict__ b,
+__global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const T *__restrict__ b,
                                                         T *__restrict__ gh, const T *__restrict__ delta, Coef<T> K) {
-    int c, i, j, k0, k1;
-    if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > L.nx || j > L.ny) return;
+    int k0 = blockIdx.z * KZ, k1 = k0 + KZ < L.nz + 1 ? k0 + KZ : L.nz + 1;
     for (int k = k0; k < k1; ++k) {
-    long long q = pidx(L, c, i, j, k);
-    if (!active(L, c, i, j, k)) {
-        gh[q] = T(0);
-        continue;
-    }
-    T v;
-    if (c == 3 && delta) {
-        long long t = cell_lin(L, i, j, k);
-        bool v2 = in_v2_cell(L, i, j, k);
-        int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-        long long sy = L.nx, sz = (long long)L.nx * L.ny;
-        T g = T(0);
-        if (!v2 || !(colour & 1)) g += (i > 0 ? delta[t - 1] : T(0)) + (i < L.nx - 1 ? delta[t + 1] : T(0));
-        if (!v2 || !(colour & 2)) g += (j > 0 ? delta[t - sy] : T(0)) + (j < L.ny - 1 ? delta[t + sy] : T(0));
-        if (!v2 || !(colour & 4)) g += (k > 0 ? delta[t - sz] : T(0)) + (k < L.nz - 1 ? delta[t + sz] : T(0));
-        if (g != T(0)) x[q] -= K.eh2 * g;
-    }
-    if (c < 3) {
-        // b - (A u)_f: the face operator without its pressure part (K with ih = 0 drops it)
-        Coef<T> KA = K;
-        KA.ih = T(0);
-        v = b[q] - face_Lx_any(x, L, c, i, j, k, KA);
-    } else {
-        // b - (B u)_c: the cell operator without its pressure part
-        Coef<T> KB = K;
-        KB.gam = T(0);
-        v = b[q] - cell_Lx_fast(x, L, i, j, k, KB);
-    }
-    gh[q] = v;
+        Quad Q = quad_at(L, i, j, k);
+        T o[4];
+        quad_eval<T, OP_A_B>(x, L, i, j, k, Q, K, o);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (Q.ex[c]) gh[Q.q[c]] = Q.act[c] ? b[Q.q[c]] - o[c] : T(0);
+        if (delta && Q.ex[3]) {
+            long long t = cell_lin(L, i, j, k);
+            bool v2 = in_v2_cell(L, i, j, k);
+            int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+            long long sy = L.nx, sz = (long long)L.nx * L.ny;
+            T g = T(0);
+            if (!v2 || !(colour & 1)) g += (i > 0 ? delta[t - 1] : T(0)) + (i < L.nx - 1 ? delta[t + 1] : T(0));
+            if (!v2 || !(colour & 2)) g += (j > 0 ? delta[t - sy] : T(0)) + (j < L.ny - 1 ? delta[t + sy] : T(0));
+            if (!v2 || !(colour & 4)) g += (k > 0 ? delta[t - sz] : T(0)) + (k < L.nz - 1 ? delta[t + sz] : T(0));
+            if (g != T(0)) x[Q.q[3]] -= K.eh2 * g;
+        }
     }
 }
 
@@ -329,8 +326,7 @@ template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, 
 }
 template <class T>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const T *b, T *gh, const T *delta, cudaStream_t s) {
-    Geo g = geo_components(L, 4);
-    k_dgs_p_bwd_prep<T><<<g.grid, kBlock3, 0, s>>>(L, g.gy, x, b, gh, delta, coef<T>(L, L.gamma));
+    k_dgs_p_bwd_prep<T><<<cell_grid_h(L), kBlock3, 0, s>>>(L, x, b, gh, delta, coef<T>(L, L.gamma));
 }
 template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
@@ -592,67 +588,72 @@ __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const T 
     }
 }
 
-// 1D prolongation weights along one axis: normal axis (coincident: {I, 1}; between: {I0, I1, 1/2})
-// or tangential axis ({row, 3/4}, {far-side row, 1/4})
-struct W2 {
-    int i0, i1;
-    float w0, w1;
-};
-__device__ __forceinline__ W2 pw_axis(int f, bool normal) {
-    W2 r;
-    if (normal) {
-        if ((f & 1) == 0) { r.i0 = f >> 1; r.i1 = -1; r.w0 = 1.f; r.w1 = 0.f; }
-        else { r.i0 = (f - 1) >> 1; r.i1 = (f + 1) >> 1; r.w0 = r.w1 = 0.5f; }
-    } else {
-        r.i0 = f >> 1; r.w0 = 0.75f;
-        r.i1 = (f & 1) == 0 ? (f >> 1) - 1 : (f >> 1) + 1; r.w1 = 0.25f;
-    }
-    return r;
-}
-
-template <class T, int CC>
-__device__ __forceinline__ T prolong_face(const Lev &C, const T *__restrict__ ec, int fi, int fj, int fk) {
-    W2 a = pw_axis(fi, CC == 0), b = pw_axis(fj, CC == 1), g = pw_axis(fk, CC == 2);
-    const long long sy = C.nx + (CC == 0), sz = sy * (C.ny + (CC == 1));
-    const int nx = C.nx, ny = C.ny, nz = C.nz;
-    // a coarse index outside the box (tangential -1 or n) contributes 0; a normal index is always
-    // in [0, n] (walls hold 0); the unused second normal weight is 0
-    auto ok = [](int idx, int n, bool normal) { return normal ? idx >= 0 : (idx >= 0 && idx < n); };
-    const T *cb = ec + comp_base(C, CC);
-    int ii[2] = {a.i0, a.i1}, jj[2] = {b.i0, b.i1}, kk[2] = {g.i0, g.i1};
-    T wi[2] = {T(a.w0), T(a.w1)}, wj[2] = {T(b.w0), T(b.w1)}, wk[2] = {T(g.w0), T(g.w1)};
-    T s = T(0);
+// Coarse-cell-centric prolongation: the thread of coarse cell (I,J,K) adds P e to the 8 fine cells
+// and to the fine faces (2I+a, 2J+b, 2K+c), a,b,c in {0,1}, of each velocity component.  For
+// component C it loads the coarse faces at normal index {I, I+1} and tangential rows {T-1, T, T+1}
+// once (18 values; rows outside the box are 0).
+template <class T, int C>
+__device__ __forceinline__ void prolong_comp(const Lev &F, const Lev &Cl, const T *__restrict__ ec, T *__restrict__ xf,
+                                             int I, int J, int Kk) {
+    const long long csy = Cl.nx + (C == 0), csz = csy * (Cl.ny + (C == 1));
+    const long long fsy = F.nx + (C == 0), fsz = fsy * (F.ny + (C == 1));
+    const int cn[3] = {Cl.nx, Cl.ny, Cl.nz};
+    const int ci[3] = {I, J, Kk};
+    // axes: n = normal (C), t1, t2 = tangential
+    const int t1 = C == 0 ? 1 : 0, t2 = C == 2 ? 1 : 2;
+    const long long cst[3] = {1, csy, csz}, fst[3] = {1, fsy, fsz};
+    const T *cb = ec + comp_base(Cl, C) + I + csy * J + csz * Kk;
+    T c[2][3][3];
 #pragma unroll
-    for (int x = 0; x < 2; ++x) {
-        if (!ok(ii[x], nx, CC == 0) || wi[x] == T(0)) continue;
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int y = 0; y < 2; ++y) {
-            if (!ok(jj[y], ny, CC == 1) || wj[y] == T(0)) continue;
+        for (int p = 0; p < 3; ++p)
 #pragma unroll
-            for (int z = 0; z < 2; ++z) {
-                if (!ok(kk[z], nz, CC == 2) || wk[z] == T(0)) continue;
-                s += wi[x] * wj[y] * wk[z] * cb[ii[x] + sy * jj[y] + sz * kk[z]];
+            for (int q = 0; q < 3; ++q) {
+                int r1 = ci[t1] + p - 1, r2 = ci[t2] + q - 1;
+                bool ok = r1 >= 0 && r1 < cn[t1] && r2 >= 0 && r2 < cn[t2];
+                c[a][p][q] = ok ? cb[a * cst[C] + (p - 1) * cst[t1] + (q - 1) * cst[t2]] : T(0);
             }
-        }
+    const int fn = C == 0 ? F.nx : (C == 1 ? F.ny : F.nz);
+    T *fb = xf + comp_base(F, C) + 2 * I + fsy * (2LL * J) + fsz * (2LL * Kk);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        int fidx = 2 * ci[C] + a;
+        if (fidx < 1 || fidx > fn - 1) continue;  // wall-normal fine faces are not unknowns
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                // tangential: 3/4 from row T, 1/4 from row T-1 (even fine index) or T+1 (odd)
+                const T w1[3] = {bb == 0 ? T(0.25) : T(0), T(0.75), bb == 1 ? T(0.25) : T(0)};
+                const T w2[3] = {g == 0 ? T(0.25) : T(0), T(0.75), g == 1 ? T(0.25) : T(0)};
+                T s = T(0);
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        T tv = a == 0 ? c[0][p][q] : T(0.5) * (c[0][p][q] + c[1][p][q]);
+                        s += w1[p] * w2[q] * tv;
+                    }
+                fb[a * fst[C] + bb * fst[t1] + g * fst[t2]] += s;
+            }
     }
-    return s;
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_prolong(Lev F, Lev C, int gy, const T *__restrict__ ec, T *__restrict__ xf) {
-    int c, fi, fj, k0, k1;
-    if (!thread_entry(F, gy, c, fi, fj, k0, k1)) return;
-    for (int fk = k0; fk < k1; ++fk) {
-    if (!active(F, c, fi, fj, fk)) continue;
-    long long q = pidx(F, c, fi, fj, fk);
-    T v;
-    switch (c) {
-    case 0: v = prolong_face<T, 0>(C, ec, fi, fj, fk); break;
-    case 1: v = prolong_face<T, 1>(C, ec, fi, fj, fk); break;
-    case 2: v = prolong_face<T, 2>(C, ec, fi, fj, fk); break;
-    default: v = ec[pidx(C, 3, fi >> 1, fj >> 1, fk >> 1)];
-    }
-    xf[q] += v;
+__global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, const T *__restrict__ ec, T *__restrict__ xf) {
+    int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+    if (I >= Cl.nx || J >= Cl.ny) return;
+    int k0 = blockIdx.z * KZ, k1 = k0 + KZ < Cl.nz ? k0 + KZ : Cl.nz;
+    const long long fy = F.nx, fz = (long long)F.nx * F.ny;
+    for (int Kk = k0; Kk < k1; ++Kk) {
+        T pcv = ec[pidx(Cl, 3, I, J, Kk)];
+        T *pf = xf + F.off[3] + 2 * I + fy * (2 * J) + fz * (2LL * Kk);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) pf[(m & 1) + fy * ((m >> 1) & 1) + fz * ((m >> 2) & 1)] += pcv;
+        prolong_comp<T, 0>(F, Cl, ec, xf, I, J, Kk);
+        prolong_comp<T, 1>(F, Cl, ec, xf, I, J, Kk);
+        prolong_comp<T, 2>(F, Cl, ec, xf, I, J, Kk);
     }
 }
 
@@ -661,8 +662,8 @@ template <class T> void launch_restrict(const Lev &F, const Lev &C, const T *rf,
     k_restrict<T><<<g.grid, kBlock3, 0, s>>>(F, C, g.gy, rf, bc);
 }
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s) {
-    Geo g = geo_components(F, 4);
-    k_prolong<T><<<g.grid, kBlock3, 0, s>>>(F, C, g.gy, ec, xf);
+    dim3 grid(cdiv(C.nx, BX), cdiv(C.ny, BY), cdiv(C.nz, KZ));
+    k_prolong<T><<<grid, kBlock3, 0, s>>>(F, C, ec, xf);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -37,64 +37,55 @@ template <int NV> __device__ __forceinline__ void block_store(double (&v)[NV], d
 }
 }  // namespace
 
-// 3D launch over the packed entries of the 4 components: blocks of 32 x 8 over (x, y), the
-// component folded into gridDim.y, each thread marching over z; one partial sum per block.
-// The input vectors hold 0 off the unknowns (the fast stencils rely on it).
+// Cell-centric 3D launch (as k_apply): blocks of 32 x 8 positions (i, j), KZR planes marched by
+// each thread, four packed entries per position; one partial sum per block.  The input vectors
+// hold 0 off the unknowns (the fast stencils rely on it).
+constexpr int KZR = 16;
+static dim3 red_grid(const Lev &L) {
+    return dim3((L.nx + 1 + BX - 1) / BX, (L.ny + 1 + BY - 1) / BY, (L.nz + 1 + KZR - 1) / KZR);
+}
 int reduce_parts(const Lev &L) {
-    int gx = (L.nx + 1 + BX - 1) / BX, gy = (L.ny + 1 + BY - 1) / BY;
-    return gx * gy * 4;
+    dim3 g = red_grid(L);
+    return (int)(g.x * g.y * g.z);
 }
 
-__global__ void __launch_bounds__(256) k_apply_dot(Lev L, int gy, const double *__restrict__ q, double *__restrict__ w,
-                                                   double *partials, Coef<double> K) {
-    int c = blockIdx.y / gy;
-    int i = blockIdx.x * BX + threadIdx.x, j = (blockIdx.y - c * gy) * BY + threadIdx.y;
+template <bool RESIDUAL>
+__global__ void __launch_bounds__(256) k_apply_red(Lev L, const double *__restrict__ x, const double *__restrict__ b,
+                                                   double *__restrict__ w, double *partials, Coef<double> K) {
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     double v[1] = {0.0};
-    if (i < ext(L, c, 0) && j < ext(L, c, 1)) {
-        int ez = ext(L, c, 2);
-        for (int k = 0; k < ez; ++k) {
-            long long t = pidx(L, c, i, j, k);
-            double y = 0.0;
-            if (active(L, c, i, j, k)) {
-                y = c < 3 ? face_Lx_any(q, L, c, i, j, k, K) : cell_Lx_fast(q, L, i, j, k, K);
-                v[0] += q[t] * y;
+    if (i <= L.nx && j <= L.ny) {
+        int k0 = blockIdx.z * KZR, k1 = k0 + KZR < L.nz + 1 ? k0 + KZR : L.nz + 1;
+        for (int k = k0; k < k1; ++k) {
+            Quad Q = quad_at(L, i, j, k);
+            double o[4];
+            quad_eval<double, OP_APPLY>(x, L, i, j, k, Q, K, o);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (!Q.ex[c]) continue;
+                double y = 0.0;
+                if (Q.act[c]) {
+                    if (RESIDUAL) {
+                        y = b[Q.q[c]] - o[c];
+                        v[0] += y * y;
+                    } else {
+                        y = o[c];
+                        v[0] += x[Q.q[c]] * y;
+                    }
+                }
+                if (w) w[Q.q[c]] = y;
             }
-            w[t] = y;
         }
     }
-    block_store<1>(v, partials, blockIdx.x + gridDim.x * blockIdx.y);
-}
-
-__global__ void __launch_bounds__(256) k_residual_dot(Lev L, int gy, const double *__restrict__ b,
-                                                      const double *__restrict__ x, double *__restrict__ w,
-                                                      double *partials, Coef<double> K) {
-    int c = blockIdx.y / gy;
-    int i = blockIdx.x * BX + threadIdx.x, j = (blockIdx.y - c * gy) * BY + threadIdx.y;
-    double v[1] = {0.0};
-    if (i < ext(L, c, 0) && j < ext(L, c, 1)) {
-        int ez = ext(L, c, 2);
-        for (int k = 0; k < ez; ++k) {
-            long long t = pidx(L, c, i, j, k);
-            double r = 0.0;
-            if (active(L, c, i, j, k))
-                r = b[t] - (c < 3 ? face_Lx_any(x, L, c, i, j, k, K) : cell_Lx_fast(x, L, i, j, k, K));
-            if (w) w[t] = r;
-            v[0] += r * r;
-        }
-    }
-    block_store<1>(v, partials, blockIdx.x + gridDim.x * blockIdx.y);
+    block_store<1>(v, partials, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
 int launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s) {
-    int gy = (L.ny + 1 + BY - 1) / BY;
-    dim3 grid((L.nx + 1 + BX - 1) / BX, gy * 4, 1);
-    k_apply_dot<<<grid, dim3(BX, BY, 1), 0, s>>>(L, gy, q, w, partials, coef<double>(L, 0.0));
+    k_apply_red<false><<<red_grid(L), dim3(BX, BY, 1), 0, s>>>(L, q, nullptr, w, partials, coef<double>(L, 0.0));
     return reduce_parts(L);
 }
 int launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s) {
-    int gy = (L.ny + 1 + BY - 1) / BY;
-    dim3 grid((L.nx + 1 + BX - 1) / BX, gy * 4, 1);
-    k_residual_dot<<<grid, dim3(BX, BY, 1), 0, s>>>(L, gy, b, x, w, partials, coef<double>(L, 0.0));
+    k_apply_red<true><<<red_grid(L), dim3(BX, BY, 1), 0, s>>>(L, x, b, w, partials, coef<double>(L, 0.0));
     return reduce_parts(L);
 }
 

@@ -125,6 +125,74 @@ __device__ __forceinline__ T face_Lx_any(const T *__restrict__ x, const Lev &L, 
                   : (c == 1 ? face_Lx_fast<T, 1>(x, L, i, j, k, K) : face_Lx_fast<T, 2>(x, L, i, j, k, K));
 }
 
+// ---- cell-centric evaluation: the thread that owns cell position (i,j,k), 0 <= i <= nx, ... ,
+// produces the four packed entries sharing that index -- u(i,j,k), v(i,j,k), w(i,j,k), p(i,j,k) --
+// as far as they exist, in one pass (shared index math, p(i,j,k) and the low faces loaded once).
+// OP_APPLY: L~x  (faces eta/h^2 (6x - sum nbrs) + grad p, cells -div u - gamma p)
+// OP_A_B:   faces eta/h^2 (6x - sum nbrs) only, cells -div u only (the p-free parts)
+enum { OP_APPLY = 0, OP_A_B = 1 };
+struct Quad {
+    long long q[4];  // packed indices (valid where ex[c])
+    bool ex[4];      // entry exists in the packed array
+    bool act[4];     // entry is an unknown
+};
+__device__ __forceinline__ Quad quad_at(const Lev &L, int i, int j, int k) {
+    Quad Q;
+    const long long nx = L.nx, ny = L.ny;
+    Q.ex[0] = j < L.ny && k < L.nz;
+    Q.ex[1] = i < L.nx && k < L.nz;
+    Q.ex[2] = i < L.nx && j < L.ny;
+    Q.ex[3] = i < L.nx && j < L.ny && k < L.nz;
+    Q.q[0] = L.off[0] + i + (nx + 1) * (j + ny * k);
+    Q.q[1] = L.off[1] + i + nx * (j + (ny + 1) * k);
+    Q.q[2] = L.off[2] + i + nx * (j + ny * k);
+    Q.q[3] = L.off[3] + i + nx * (j + ny * k);
+    Q.act[0] = Q.ex[0] && i >= 1 && i <= L.nx - 1;
+    Q.act[1] = Q.ex[1] && j >= 1 && j <= L.ny - 1;
+    Q.act[2] = Q.ex[2] && k >= 1 && k <= L.nz - 1;
+    Q.act[3] = Q.ex[3];
+    return Q;
+}
+// values of the four operator rows at (i,j,k) (0 for entries that are not unknowns); x holds 0
+// off the unknowns
+template <class T, int OP>
+__device__ __forceinline__ void quad_eval(const T *__restrict__ x, const Lev &L, int i, int j, int k, const Quad &Q,
+                                          const Coef<T> &K, T out[4]) {
+    const long long nx = L.nx, ny = L.ny;
+    const long long uy = nx + 1, uz = (nx + 1) * ny, vy = nx, vz = nx * (ny + 1), wy = nx, wz = nx * ny;
+    const long long py = nx, pz = nx * ny;
+    T pc = Q.ex[3] ? x[Q.q[3]] : T(0);
+    const bool gxm = i > 0, gxp = i < L.nx - 1, gym = j > 0, gyp = j < L.ny - 1, gzm = k > 0, gzp = k < L.nz - 1;
+    out[0] = out[1] = out[2] = out[3] = T(0);
+    if (Q.act[0]) {
+        const T *u = x + Q.q[0];
+        T s = T(6) * u[0] - u[-1] - u[1] - (gym ? u[-uy] : T(0)) - (gyp ? u[uy] : T(0)) - (gzm ? u[-uz] : T(0)) -
+              (gzp ? u[uz] : T(0));
+        out[0] = K.eh2 * s;
+        if (OP == OP_APPLY) out[0] += K.ih * (pc - x[Q.q[3] - 1]);
+    }
+    if (Q.act[1]) {
+        const T *v = x + Q.q[1];
+        T s = T(6) * v[0] - (gxm ? v[-1] : T(0)) - (gxp ? v[1] : T(0)) - v[-vy] - v[vy] - (gzm ? v[-vz] : T(0)) -
+              (gzp ? v[vz] : T(0));
+        out[1] = K.eh2 * s;
+        if (OP == OP_APPLY) out[1] += K.ih * (pc - x[Q.q[3] - py]);
+    }
+    if (Q.act[2]) {
+        const T *w = x + Q.q[2];
+        T s = T(6) * w[0] - (gxm ? w[-1] : T(0)) - (gxp ? w[1] : T(0)) - (gym ? w[-wy] : T(0)) -
+              (gyp ? w[wy] : T(0)) - w[-wz] - w[wz];
+        out[2] = K.eh2 * s;
+        if (OP == OP_APPLY) out[2] += K.ih * (pc - x[Q.q[3] - pz]);
+    }
+    if (Q.act[3]) {
+        const T *u = x + Q.q[0], *v = x + Q.q[1], *w = x + Q.q[2];
+        T div = (u[1] - u[0]) + (v[vy] - v[0]) + (w[wz] - w[0]);
+        out[3] = -K.ih * div;
+        if (OP == OP_APPLY) out[3] -= K.gam * pc;
+    }
+}
+
 // decode a per-component thread index t (< ex*ey*ez) into (i,j,k)
 __device__ __forceinline__ void decode3(long long t, int ex, int ey, int &i, int &j, int &k) {
     i = (int)(t % ex);
