@@ -72,28 +72,44 @@ __device__ __forceinline__ bool thread_entry(const Lev &L, int gy, int &c, int &
 // ------------------------------------------------------------------------------------------
 // y = L~x or b - L~x on every packed entry (0 off the unknowns); x must hold 0 off the unknowns.
 // Cell-centric: one thread per position (i,j) marching KZ planes, four entries per position.
-inline dim3 cell_grid_h(const Lev &L) {
-    return dim3(cdiv(L.nx + 1, BX), cdiv(L.ny + 1, BY), cdiv(L.nz + 1, KZ));
+
+// one entry per thread: blockIdx.z = 4 k + component, so the component is a compile-time branch
+// and no integer division is needed; one plane per thread keeps registers low and occupancy high
+template <class T, int OPX>
+__device__ __forceinline__ bool entry_eval(const T *__restrict__ x, const Lev &L, int c, int i, int j, int k,
+                                           const Coef<T> &K, long long &q, T &v) {
+    if (!(i < ext(L, c, 0) && j < ext(L, c, 1) && k < ext(L, c, 2))) return false;
+    q = pidx(L, c, i, j, k);
+    v = T(0);
+    if (!active(L, c, i, j, k)) return true;
+    Coef<T> Kx = K;
+    if (OPX == OP_A_B) {
+        Kx.ih = c < 3 ? T(0) : K.ih;  // faces: A u only; cells: -div u only
+        Kx.gam = T(0);
+    }
+    switch (c) {
+    case 0: v = face_Lx_fast<T, 0>(x, L, i, j, k, Kx); break;
+    case 1: v = face_Lx_fast<T, 1>(x, L, i, j, k, Kx); break;
+    case 2: v = face_Lx_fast<T, 2>(x, L, i, j, k, Kx); break;
+    default: v = cell_Lx_fast<T>(x, L, i, j, k, Kx);
+    }
+    return true;
 }
+inline dim3 entry_grid(const Lev &L) { return dim3(cdiv(L.nx + 1, BX), cdiv(L.ny + 1, BY), 4 * (L.nz + 1)); }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_apply(Lev L, const T *__restrict__ x, const T *__restrict__ b,
-                                               T *__restrict__ y, Coef<T> K) {
+__global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x, const T *__restrict__ b,
+                                                  T *__restrict__ y, Coef<T> K) {
+    int c = blockIdx.z & 3, k = blockIdx.z >> 2;
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i > L.nx || j > L.ny) return;
-    int k0 = blockIdx.z * KZ, k1 = k0 + KZ < L.nz + 1 ? k0 + KZ : L.nz + 1;
-    for (int k = k0; k < k1; ++k) {
-        Quad Q = quad_at(L, i, j, k);
-        T o[4];
-        quad_eval<T, OP_APPLY>(x, L, i, j, k, Q, K, o);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (Q.ex[c]) y[Q.q[c]] = Q.act[c] ? (b ? b[Q.q[c]] - o[c] : o[c]) : T(0);
-    }
+    long long q;
+    T v;
+    if (!entry_eval<T, OP_APPLY>(x, L, c, i, j, k, K, q, v)) return;
+    y[q] = active(L, c, i, j, k) ? (b ? b[q] - v : v) : T(0);
 }
 
 template <class T> void launch_apply(const Lev &L, const T *x, const T *b, T *y, double gam, cudaStream_t s) {
-    k_apply<T><<<cell_grid_h(L), kBlock3, 0, s>>>(L, x, b, y, coef<T>(L, gam));
+    k_apply<T><<<entry_grid(L), kBlock3, 0, s>>>(L, x, b, y, coef<T>(L, gam));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -157,18 +173,18 @@ __device__ __forceinline__ void dgs_face(T *__restrict__ x, const T *__restrict_
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_dgs_u(Lev L, T *__restrict__ x, const T *__restrict__ b, int parity,
-                                               Coef<T> K) {
+__global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, const T *__restrict__ b, int parity,
+                                                  Coef<T> K) {
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     int j = 1 + blockIdx.y * BY + threadIdx.y;
     if (j > ny - 2) return;
     const long long lnx = nx, lny = ny;
     const long long uy = lnx + 1, uz = (lnx + 1) * lny, vy = lnx, vz = lnx * (lny + 1), wz = lnx * lny;
-    int k0 = 1 + blockIdx.z * KZ, k1 = k0 + KZ < nz - 1 ? k0 + KZ : nz - 1;
-    for (int k = k0; k < k1; ++k) {
+    {
+        int k = 1 + blockIdx.z;
         int i = 1 + 2 * (blockIdx.x * BX + threadIdx.x);
         i += (i + j + k + parity) & 1;
-        if (i > nx - 2) continue;
+        if (i > nx - 2) return;
         long long pq = L.off[3] + i + lnx * (j + lny * k);
         T pc = x[pq];
         if (i >= 2) dgs_face(x, b, L.off[0] + i + uy * j + uz * k, uy, uz, pc, x[pq - 1], K);
@@ -179,7 +195,7 @@ __global__ void __launch_bounds__(256) k_dgs_u(Lev L, T *__restrict__ x, const T
 
 template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s) {
     if (L.nx < 3 || L.ny < 3 || L.nz < 3) return;
-    dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), cdiv(L.nz - 2, KZ));
+    dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), L.nz - 2);
     k_dgs_u<T><<<grid, kBlock3, 0, s>>>(L, x, b, parity, coef<T>(L, L.gamma));
 }
 
@@ -254,31 +270,27 @@ __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, 
 //   p_c += [ sum_axes (r_high_face - r_low_face)/h + eta/h^2 (6 r_c - sum of the 6 neighbour r) ] / d
 // (M_{.c}^T r with the full column of M).  Same-colour cells read none of each other's values.
 // The same launch also finishes the forward sweep: the neighbour-pressure part of the last
-// colours (gather form of k_dgs_p_gather), which the prep never reads.  Cell-centric like k_apply.
+// colours (gather form of k_dgs_p_gather), which the prep never reads.  One entry per thread as k_apply.
 template <class T>
-__global__ void __launch_bounds__(256) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const T *__restrict__ b,
-                                                        T *__restrict__ gh, const T *__restrict__ delta, Coef<T> K) {
+__global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const T *__restrict__ b,
+                                                           T *__restrict__ gh, const T *__restrict__ delta,
+                                                           Coef<T> K) {
+    int c = blockIdx.z & 3, k = blockIdx.z >> 2;
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i > L.nx || j > L.ny) return;
-    int k0 = blockIdx.z * KZ, k1 = k0 + KZ < L.nz + 1 ? k0 + KZ : L.nz + 1;
-    for (int k = k0; k < k1; ++k) {
-        Quad Q = quad_at(L, i, j, k);
-        T o[4];
-        quad_eval<T, OP_A_B>(x, L, i, j, k, Q, K, o);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (Q.ex[c]) gh[Q.q[c]] = Q.act[c] ? b[Q.q[c]] - o[c] : T(0);
-        if (delta && Q.ex[3]) {
-            long long t = cell_lin(L, i, j, k);
-            bool v2 = in_v2_cell(L, i, j, k);
-            int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-            long long sy = L.nx, sz = (long long)L.nx * L.ny;
-            T g = T(0);
-            if (!v2 || !(colour & 1)) g += (i > 0 ? delta[t - 1] : T(0)) + (i < L.nx - 1 ? delta[t + 1] : T(0));
-            if (!v2 || !(colour & 2)) g += (j > 0 ? delta[t - sy] : T(0)) + (j < L.ny - 1 ? delta[t + sy] : T(0));
-            if (!v2 || !(colour & 4)) g += (k > 0 ? delta[t - sz] : T(0)) + (k < L.nz - 1 ? delta[t + sz] : T(0));
-            if (g != T(0)) x[Q.q[3]] -= K.eh2 * g;
-        }
+    long long q;
+    T v;
+    if (!entry_eval<T, OP_A_B>(x, L, c, i, j, k, K, q, v)) return;
+    gh[q] = active(L, c, i, j, k) ? b[q] - v : T(0);
+    if (c == 3 && delta) {
+        long long t = cell_lin(L, i, j, k);
+        bool v2 = in_v2_cell(L, i, j, k);
+        int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+        long long sy = L.nx, sz = (long long)L.nx * L.ny;
+        T g = T(0);
+        if (!v2 || !(colour & 1)) g += (i > 0 ? delta[t - 1] : T(0)) + (i < L.nx - 1 ? delta[t + 1] : T(0));
+        if (!v2 || !(colour & 2)) g += (j > 0 ? delta[t - sy] : T(0)) + (j < L.ny - 1 ? delta[t + sy] : T(0));
+        if (!v2 || !(colour & 4)) g += (k > 0 ? delta[t - sz] : T(0)) + (k < L.nz - 1 ? delta[t + sz] : T(0));
+        if (g != T(0)) x[q] -= K.eh2 * g;
     }
 }
 
@@ -326,7 +338,7 @@ template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, 
 }
 template <class T>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const T *b, T *gh, const T *delta, cudaStream_t s) {
-    k_dgs_p_bwd_prep<T><<<cell_grid_h(L), kBlock3, 0, s>>>(L, x, b, gh, delta, coef<T>(L, L.gamma));
+    k_dgs_p_bwd_prep<T><<<entry_grid(L), kBlock3, 0, s>>>(L, x, b, gh, delta, coef<T>(L, L.gamma));
 }
 template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
