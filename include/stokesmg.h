@@ -169,6 +169,23 @@ int stokes_coarse_solve(stokes_t h, const double *b, double *x, void *stream);
 int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launches_all, double *ms_level0,
                              int *launches_level0, void *stream);
 
+/* ---- allocation-free residual norm ----
+ * *out = ||b - L x||_2 on an nx x ny x nz box (cell size h, <= 0 selects 1/nx; viscosity eta),
+ * the same number stokes_residual_norm returns, computed without any handle and without allocating
+ * anything.  The paper has no counterpart; this exists for callers that cannot allocate device
+ * memory where they need the check (a fixed-budget memory pool, a host callback, an allocator-free
+ * hook): creating a handle allocates the whole hierarchy.
+ * b, x: packed FP64 vectors in device memory, read in place (entries of x off the unknowns are
+ * ignored).  out: one double in device memory, written asynchronously on `stream`.
+ * Scratch: a fixed device array of 16384 doubles (128 KiB) inside the library, present on every
+ * GPU that loads it until exit; grids needing more partial sums than that (more than 16384 blocks
+ * of 32 x 8 x 16 cell positions, about 380^3) return STOKES_ERR_INVALID_ARG, as do host pointers.
+ * The first call on a device looks up the array's address with that device current; make it
+ * before any stream capture.  All calls share the array: calls that overlap on the GPU race, so
+ * serialise them.  Calls no cudaMalloc / cudaFree. */
+int stokes_residual_norm_noalloc(int nx, int ny, int nz, double h, double viscosity, const double *b,
+                                 const double *x, double *out, void *stream);
+
 /* Human-readable message for a status code (static storage). */
 const char *stokes_strerror(int status);
 

@@ -24,7 +24,7 @@ PREC_FP64, PREC_FP32 = 0, 1
 EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vector_length", "stokes_ghost_length",
            "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
-           "stokes_profile_iteration", "stokes_strerror"]
+           "stokes_profile_iteration", "stokes_residual_norm_noalloc", "stokes_strerror"]
 
 # kernel kinds reported by stokes_profile_iteration (STOKES_K_* in the header)
 KERNEL_KINDS = ["apply_dot", "update_s", "dot2", "update_x", "scalars", "memset", "vanka_compute", "vanka_apply",
@@ -81,6 +81,7 @@ def _load():
         "stokes_coarse_solve": (i, [vp, vp, vp, vp]),
         "stokes_profile_iteration": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d),
                                          ctypes.POINTER(i), vp]),
+        "stokes_residual_norm_noalloc": (i, [i, i, i, d, d, vp, vp, vp, vp]),
         "stokes_strerror": (ctypes.c_char_p, [i]),
     }
     for name, (res, args) in sig.items():
@@ -219,6 +220,13 @@ def stokes_profile_iteration(h, stream=None):
     ma, ca, m0, c0 = (ctypes.c_double * k)(), (ctypes.c_int * k)(), (ctypes.c_double * k)(), (ctypes.c_int * k)()
     _check(lib().stokes_profile_iteration(h, k, ma, ca, m0, c0, _stream(stream)), "stokes_profile_iteration")
     return {name: (ma[j], ca[j], m0[j], c0[j]) for j, name in enumerate(KERNEL_KINDS)}
+
+
+def stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, b, x, out, stream=None):
+    """||b - L x||_2 written into the 1-element device tensor `out`, without any allocation in the
+    library (for callers that cannot allocate; see include/stokesmg.h)."""
+    _check(lib().stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, _ptr(b), _ptr(x), _ptr(out),
+                                              _stream(stream)), "stokes_residual_norm_noalloc")
 
 
 class Stokes:
