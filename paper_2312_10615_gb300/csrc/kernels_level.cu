@@ -100,6 +100,7 @@ inline dim3 entry_grid(const Lev &L) { return dim3(cdiv(L.nx + 1, BX), cdiv(L.ny
 template <class T>
 __global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x, const T *__restrict__ b,
                                                   T *__restrict__ y, Coef<T> K) {
+    pdl_wait();
     int c = blockIdx.z & 3, k = blockIdx.z >> 2;
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     long long q;
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x
 }
 
 template <class T> void launch_apply(const Lev &L, const T *x, const T *b, T *y, double gam, cudaStream_t s) {
-    k_apply<T><<<entry_grid(L), kBlock3, 0, s>>>(L, x, b, y, coef<T>(L, gam));
+    launch_k(k_apply<T>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -124,6 +125,7 @@ __device__ __forceinline__ long long gidx(const Lev &L, int c, int i, int j, int
 
 __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__restrict__ f, const double *__restrict__ g,
                                              double *__restrict__ b, Coef<double> K) {
+    pdl_wait();
     int c, i, j, k0, k1;
     if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
     for (int k = k0; k < k1; ++k) {
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__rest
 
 void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaStream_t s) {
     Geo gg = geo_components(L, 4);
-    k_rhs<<<gg.grid, kBlock3, 0, s>>>(L, gg.gy, f, g, b, coef<double>(L, 0.0));
+    launch_k(k_rhs, dim3(gg.grid), dim3(kBlock3), 0, s, L, gg.gy, f, g, b, coef<double>(L, 0.0));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -175,6 +177,7 @@ __device__ __forceinline__ void dgs_face(T *__restrict__ x, const T *__restrict_
 template <class T>
 __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, const T *__restrict__ b, int parity,
                                                   Coef<T> K) {
+    pdl_wait();
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     int j = 1 + blockIdx.y * BY + threadIdx.y;
     if (j > ny - 2) return;
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, cons
 template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s) {
     if (L.nx < 3 || L.ny < 3 || L.nz < 3) return;
     dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), L.nz - 2);
-    k_dgs_u<T><<<grid, kBlock3, 0, s>>>(L, x, b, parity, coef<T>(L, L.gamma));
+    launch_k(k_dgs_u<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
 }
 
 // Alg. 2 pressure block, one colour (i mod 2, j mod 2, k mod 2):
@@ -209,6 +212,7 @@ template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity,
 template <class T>
 __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const T *__restrict__ b,
                                                    T *__restrict__ delta, int colour, Coef<T> K, T dP) {
+    pdl_wait();
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
@@ -241,6 +245,7 @@ __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, con
 template <class T>
 __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, const T *__restrict__ delta,
                                                       Coef<T> K) {
+    pdl_wait();
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     if (i >= L.nx || j >= L.ny || k >= L.nz) return;
     long long t = cell_lin(L, i, j, k);
@@ -275,6 +280,7 @@ template <class T>
 __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const T *__restrict__ b,
                                                            T *__restrict__ gh, const T *__restrict__ delta,
                                                            Coef<T> K) {
+    pdl_wait();
     int c = blockIdx.z & 3, k = blockIdx.z >> 2;
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     long long q;
@@ -297,6 +303,7 @@ __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict_
 template <class T>
 __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const T *__restrict__ gh, int colour,
                                                    Coef<T> K, T dP) {
+    pdl_wait();
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
@@ -330,22 +337,22 @@ template <class T> void launch_dgs_p_fwd(const Lev &L, T *x, const T *b, T *delt
     v2_colour_range(L, colour, lo, cnt);
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
     dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
-    k_dgs_p_fwd<T><<<grid, kBlock3, 0, s>>>(L, x, b, delta, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
+    launch_k(k_dgs_p_fwd<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
 }
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s) {
     dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz);
-    k_dgs_p_gather<T><<<grid, kBlock3, 0, s>>>(L, x, delta, coef<T>(L, L.gamma));
+    launch_k(k_dgs_p_gather<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, delta, coef<T>(L, L.gamma));
 }
 template <class T>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const T *b, T *gh, const T *delta, cudaStream_t s) {
-    k_dgs_p_bwd_prep<T><<<entry_grid(L), kBlock3, 0, s>>>(L, x, b, gh, delta, coef<T>(L, L.gamma));
+    launch_k(k_dgs_p_bwd_prep<T>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta, coef<T>(L, L.gamma));
 }
 template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
     dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
-    k_dgs_p_bwd<T><<<grid, kBlock3, 0, s>>>(L, x, gh, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
+    launch_k(k_dgs_p_bwd<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -367,6 +374,7 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
                                                        const int *__restrict__ cells, int ncell,
                                                        const T *__restrict__ kinv, T *__restrict__ corr, int cap,
                                                        Coef<T> K) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = t >> 3, a = t & 7;
     if (slot >= ncell) return;  // whole 8-lane groups leave together
@@ -393,6 +401,7 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
 template <class T>
 __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, const int *__restrict__ cells,
                                                      int ncell, const T *__restrict__ corr, int cap) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = t >> 3, a = t & 7;
     if (slot >= ncell || a == 7) return;
@@ -411,13 +420,13 @@ template <class T>
 void launch_vanka_compute(const Lev &L, const T *x, const T *b, const int *cells, int ncell, const T *kinv, T *corr,
                           int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    k_vanka_compute<T><<<cdiv(8LL * ncell, 256), 256, 0, s>>>(L, x, b, cells, ncell, kinv, corr, cap,
+    launch_k(k_vanka_compute<T>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, ncell, kinv, corr, cap,
                                                                coef<T>(L, L.gamma));
 }
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    k_vanka_apply<T><<<cdiv(8LL * ncell, 256), 256, 0, s>>>(L, x, cells, ncell, corr, cap);
+    launch_k(k_vanka_apply<T>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, cells, ncell, corr, cap);
 }
 
 // ---- one cooperative launch per symmetric Vanka sweep ----
@@ -493,6 +502,7 @@ __global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, c
                                                      VankaLists lists, const T *__restrict__ kinv,
                                                      T *__restrict__ corr, int cap, Coef<T> K, int sweeps,
                                                      GridBarrier *bar) {
+    pdl_wait();
     const unsigned nb = gridDim.x;
     const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 8: lanes keep their group
     const unsigned gmask = 0xffu << (threadIdx.x & 24);
@@ -575,6 +585,7 @@ __device__ __forceinline__ T restrict_face(const Lev &F, const Lev &Cl, const T 
 template <class T>
 __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const T *__restrict__ rf,
                                                   T *__restrict__ bc) {
+    pdl_wait();
     int c, I, J, k0, k1;
     if (!thread_entry(C, gy, c, I, J, k0, k1)) return;
     for (int Kk = k0; Kk < k1; ++Kk) {
@@ -654,6 +665,7 @@ __device__ __forceinline__ void prolong_comp(const Lev &F, const Lev &Cl, const 
 
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, const T *__restrict__ ec, T *__restrict__ xf) {
+    pdl_wait();
     int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
     if (I >= Cl.nx || J >= Cl.ny) return;
     int k0 = blockIdx.z * KZ, k1 = k0 + KZ < Cl.nz ? k0 + KZ : Cl.nz;
@@ -671,11 +683,11 @@ __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, const T *__restr
 
 template <class T> void launch_restrict(const Lev &F, const Lev &C, const T *rf, T *bc, cudaStream_t s) {
     Geo g = geo_components(C, 4);
-    k_restrict<T><<<g.grid, kBlock3, 0, s>>>(F, C, g.gy, rf, bc);
+    launch_k(k_restrict<T>, dim3(g.grid), dim3(kBlock3), 0, s, F, C, g.gy, rf, bc);
 }
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s) {
     dim3 grid(cdiv(C.nx, BX), cdiv(C.ny, BY), cdiv(C.nz, KZ));
-    k_prolong<T><<<grid, kBlock3, 0, s>>>(F, C, ec, xf);
+    launch_k(k_prolong<T>, dim3(grid), dim3(kBlock3), 0, s, F, C, ec, xf);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -684,6 +696,7 @@ template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, 
 template <class T>
 __global__ void __launch_bounds__(256) k_coarse(const int *__restrict__ cidx, int nc, const double *__restrict__ kinv,
                                                 const T *__restrict__ b, T *__restrict__ x) {
+    pdl_wait();
     extern __shared__ double sb[];
     for (int m = threadIdx.x; m < nc; m += blockDim.x) sb[m] = (double)b[cidx[m]];
     __syncthreads();
@@ -702,11 +715,12 @@ template <class T>
 void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, const T *b, T *x, cudaStream_t s) {
     (void)C;
     int rows_per_block = 256 / 32;
-    k_coarse<T><<<(nc + rows_per_block - 1) / rows_per_block, 256, nc * sizeof(double), s>>>(cidx, nc, kinv, b, x);
+    launch_k(k_coarse<T>, dim3((nc + rows_per_block - 1) / rows_per_block), dim3(256), nc * sizeof(double), s, cidx, nc, kinv, b, x);
 }
 
 // ------------------------------------------------------------------------------------------
 template <class T> __global__ void __launch_bounds__(256) k_mask(Lev L, int gy, T *__restrict__ x) {
+    pdl_wait();
     int c, i, j, k0, k1;
     if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
     for (int k = k0; k < k1; ++k)
@@ -714,18 +728,19 @@ template <class T> __global__ void __launch_bounds__(256) k_mask(Lev L, int gy, 
 }
 template <class T> void launch_mask(const Lev &L, T *x, cudaStream_t s) {
     Geo g = geo_components(L, 4);
-    k_mask<T><<<g.grid, kBlock3, 0, s>>>(L, g.gy, x);
+    launch_k(k_mask<T>, dim3(g.grid), dim3(kBlock3), 0, s, L, g.gy, x);
 }
 template void launch_mask<float>(const Lev &, float *, cudaStream_t);
 template void launch_mask<double>(const Lev &, double *, cudaStream_t);
 
 template <class A, class B> __global__ void k_convert(long long n, const A *__restrict__ in, B *__restrict__ out) {
+    pdl_wait();
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         out[t] = (B)in[t];
 }
 template <class A, class B> void launch_convert(long long n, const A *in, B *out, cudaStream_t s) {
     long long nb = (n + 255) / 256;
-    k_convert<A, B><<<(unsigned)(nb < 4736 ? nb : 4736), 256, 0, s>>>(n, in, out);
+    launch_k(k_convert<A, B>, dim3((unsigned)(nb < 4736 ? nb : 4736)), dim3(256), 0, s, n, in, out);
 }
 
 // explicit instantiations

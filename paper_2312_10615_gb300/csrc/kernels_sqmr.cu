@@ -52,6 +52,7 @@ int reduce_parts(const Lev &L) {
 template <bool RESIDUAL>
 __global__ void __launch_bounds__(256) k_apply_red(Lev L, const double *__restrict__ x, const double *__restrict__ b,
                                                    double *__restrict__ w, double *partials, Coef<double> K) {
+    pdl_wait();
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     double v[1] = {0.0};
     if (i <= L.nx && j <= L.ny) {
@@ -81,11 +82,11 @@ __global__ void __launch_bounds__(256) k_apply_red(Lev L, const double *__restri
 }
 
 int launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s) {
-    k_apply_red<false><<<red_grid(L), dim3(BX, BY, 1), 0, s>>>(L, q, nullptr, w, partials, coef<double>(L, 0.0));
+    launch_k(k_apply_red<false>, red_grid(L), dim3(BX, BY, 1), 0, s, L, q, nullptr, w, partials, coef<double>(L, 0.0));
     return reduce_parts(L);
 }
 int launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s) {
-    k_apply_red<true><<<red_grid(L), dim3(BX, BY, 1), 0, s>>>(L, x, b, w, partials, coef<double>(L, 0.0));
+    launch_k(k_apply_red<true>, red_grid(L), dim3(BX, BY, 1), 0, s, L, x, b, w, partials, coef<double>(L, 0.0));
     return reduce_parts(L);
 }
 
@@ -93,6 +94,7 @@ int launch_residual_dot(const Lev &L, const double *b, const double *x, double *
 template <class T>
 __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__ a, const double *__restrict__ b,
                                               double *partials) {
+    pdl_wait();
     double v[2] = {0.0, 0.0};
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         double x = (double)a[t];
@@ -102,12 +104,13 @@ __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__
     block_store<2>(v, partials, blockIdx.x);
 }
 template <class T> void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s) {
-    k_dot2<T><<<kRedBlocks, kBlock, 0, s>>>(n, a, b, partials);
+    launch_k(k_dot2<T>, dim3(kRedBlocks), dim3(kBlock), 0, s, n, a, b, partials);
 }
 
 // scalar recurrences of Alg. 4 (one block; fixed-order sum of the nparts partials)
 __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partials, int nparts, SqmrState *st,
                                                  double *host_out, double aux) {
+    pdl_wait();
     __shared__ double sh[kRedParts][kBlock];
     double v[kRedParts] = {0.0, 0.0, 0.0};
     for (int t = threadIdx.x; t < nparts; t += blockDim.x)
@@ -183,17 +186,18 @@ __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partia
 
 void launch_scalars(int stage, const double *partials, int nparts, SqmrState *st, double *host_out,
                     cudaStream_t s) {
-    k_scalars<<<1, kBlock, 0, s>>>(stage, partials, nparts, st, host_out, 0.0);
+    launch_k(k_scalars, dim3(1), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, 0.0);
 }
 void launch_scalars_aux(int stage, const double *partials, int nparts, SqmrState *st, double *host_out, double aux,
                         cudaStream_t s) {
-    k_scalars<<<1, kBlock, 0, s>>>(stage, partials, nparts, st, host_out, aux);
+    launch_k(k_scalars, dim3(1), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, aux);
 }
 
 // s_j = s_{j-1} - alpha t  (t = L q_{j-1}); optional narrowed copy for the V-cycle
 template <class T>
 __global__ void __launch_bounds__(256) k_update_s(long long n, double *__restrict__ s, const double *__restrict__ w,
                                                   const SqmrState *__restrict__ st, T *__restrict__ bT) {
+    pdl_wait();
     double alpha = st->alpha;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         double v = s[t] - alpha * w[t];
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(256) k_update_s(long long n, double *__restric
 }
 template <class T>
 void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream) {
-    k_update_s<T><<<kRedBlocks, kBlock, 0, stream>>>(n, s, w, st, bT);
+    launch_k(k_update_s<T>, dim3(kRedBlocks), dim3(kBlock), 0, stream, n, s, w, st, bT);
 }
 
 // d_j = c^2 nu_{j-1}^2 d_{j-1} + c^2 alpha q_{j-1};  x_j = x_{j-1} + d_j;
@@ -214,6 +218,7 @@ __global__ void __launch_bounds__(256) k_update_x(long long n, double *__restric
                                                   double *__restrict__ q, const T *__restrict__ tv,
                                                   double *__restrict__ r, const double *__restrict__ sv,
                                                   const SqmrState *__restrict__ st, double *partials) {
+    pdl_wait();
     double A = st->coefA, B = st->coefB, c2 = st->c2, beta = st->beta;
     double v[1] = {0.0};
 #pragma unroll 1
@@ -232,22 +237,24 @@ __global__ void __launch_bounds__(256) k_update_x(long long n, double *__restric
 template <class T>
 void launch_update_x(long long n, double *x, double *d, double *q, const T *t, double *r, const double *sv,
                      const SqmrState *st, double *partials, cudaStream_t s) {
-    k_update_x<T><<<kRedBlocks, kBlock, 0, s>>>(n, x, d, q, t, r, sv, st, partials);
+    launch_k(k_update_x<T>, dim3(kRedBlocks), dim3(kBlock), 0, s, n, x, d, q, t, r, sv, st, partials);
 }
 
 template <class T>
 __global__ void __launch_bounds__(256) k_init_q(long long n, const T *__restrict__ tv, double *__restrict__ q,
                                                 double *__restrict__ d) {
+    pdl_wait();
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         q[t] = (double)tv[t];
         d[t] = 0.0;
     }
 }
 template <class T> void launch_init_q(long long n, const T *t, double *q, double *d, cudaStream_t s) {
-    k_init_q<T><<<kRedBlocks, kBlock, 0, s>>>(n, t, q, d);
+    launch_k(k_init_q<T>, dim3(kRedBlocks), dim3(kBlock), 0, s, n, t, q, d);
 }
 
 __global__ void __launch_bounds__(256) k_psum(Lev L, const double *__restrict__ x, double *partials) {
+    pdl_wait();
     double v[1] = {0.0};
     long long np = L.n - L.off[3];
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
@@ -255,16 +262,17 @@ __global__ void __launch_bounds__(256) k_psum(Lev L, const double *__restrict__ 
     block_store<1>(v, partials, blockIdx.x);
 }
 __global__ void __launch_bounds__(256) k_psub(Lev L, double *__restrict__ x, const SqmrState *__restrict__ st) {
+    pdl_wait();
     double m = st->pmean;
     long long np = L.n - L.off[3];
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
         x[L.off[3] + t] -= m;
 }
 void launch_psum(const Lev &L, const double *x, double *partials, cudaStream_t s) {
-    k_psum<<<kRedBlocks, kBlock, 0, s>>>(L, x, partials);
+    launch_k(k_psum, dim3(kRedBlocks), dim3(kBlock), 0, s, L, x, partials);
 }
 void launch_psub(const Lev &L, double *x, const SqmrState *st, cudaStream_t s) {
-    k_psub<<<kRedBlocks, kBlock, 0, s>>>(L, x, st);
+    launch_k(k_psub, dim3(kRedBlocks), dim3(kBlock), 0, s, L, x, st);
 }
 
 template void launch_dot2<float>(long long, const float *, const double *, double *, cudaStream_t);

@@ -13,6 +13,32 @@
 
 namespace smg {
 
+// ---- programmatic dependent launch: every kernel is launched with programmatic stream
+// serialisation, so its launch and block scheduling overlap the tail of the previous kernel in the
+// stream; pdl_wait() (griddepcontrol.wait, a hardware dependency wait) holds the kernel until the
+// previous kernel has completed and its memory is visible.  Every kernel calls it before touching
+// global memory.
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 struct Lev {
     int nx, ny, nz;
     long long off[4];  // offsets of the u, v, w, p blocks in the packed vector
