@@ -182,7 +182,8 @@ def alg_bytes(kind, n, e, launches_per_level0=1):
     v1 = n ** 3 - (n - 2) ** 3
     table = {
         "dgs_u": (3 * nf + np_) * e,              # read x faces, p, b faces; write x faces
-        "dgs_p_bwd": (2 * npk + np_ / 8) * e,     # read x and b (radius-2 stencils), write p of one colour
+        "dgs_p_bwd": (nf / 2 + 3 * np_ / 2) * e,  # g on the colour's face rows, p and h at radius 1, write p
+        "dgs_p_bwd_prep": 3 * npk * e,            # read x, b; write g (faces) and h (cells)
         "dgs_p_fwd": (2 * nf / 4 + 3 * np_ / 4) * e,  # a colour touches 1/4 of the rows of faces and cells
         "dgs_p_gather": 3 * np_ * e,              # read delta, read+write p
         "residual": 3 * npk * e,                  # read x, b; write r
