@@ -244,6 +244,111 @@ def run_e2e(smg, S, rhs_dev, npk, args, barrier, stream, world, n):
             "note": "sqmr_solve with pinned host rhs/x0/x; copies inside the call"}
 
 
+BATCH_SIZES = (32, 48, 64, 96, 128)
+
+
+def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
+    """Independent problems with cube sizes drawn uniformly from BATCH_SIZES (seeded per rank), Gaussian-bump
+    forcing per problem, FP32 V-cycle + FP64 SQMR to args.tol; solved with sqmr_solve_batch (args.streams
+    concurrent streams).  Beside it: the same problems solved one after another (FP32 V-cycle, and the plain
+    FP64 V-cycle).  sqmr_solve_batch returns once every problem has converged, so a step is timed on the
+    host with the device synchronised on both sides."""
+    import numpy as np
+    rng = np.random.default_rng(4000 + rank)
+    sizes = [int(v) for v in rng.choice(BATCH_SIZES, size=args.batch)]
+    S32, rhs, xs = [], [], []
+    for i, n in enumerate(sizes):
+        S = smg.Stokes(n, precision=smg.PREC_FP32)
+        S32.append(S)
+        rhs.append(S.rhs(synthetic.bumps(n, seed=rank * 100000 + i, device=dev)["f"], None))
+        xs.append(torch.zeros(S.n, dtype=torch.float64, device=dev))
+    total_unknowns = sum(unknowns(n) for n in sizes)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def maxrank(ms):
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    def batch_step():
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        return smg.sqmr_solve_batch([S.h for S in S32], rhs, xs, args.tol, 200, nstreams=args.streams)
+
+    for _ in range(args.warmup):
+        batch_step()
+    barrier()
+    lat, its, res = [], [], []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            infos, done = batch_step()
+            lat += done
+            its.append([inf.iterations for inf in infos])
+            res += [inf.rel_residual for inf in infos]
+        barrier()
+        ms = maxrank((time.perf_counter() - t0) * 1e3)
+    assert all(r < args.tol for r in res), max(res)
+    value = total_unknowns * args.steps * world / (ms * 1e-3)
+
+    def sequential(handles, k):
+        durations = []
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            for S, b, x in zip(handles, rhs, xs):
+                t1 = time.perf_counter()
+                x.zero_()
+                smg.sqmr_solve(S.h, b, x, args.tol, 200)
+                durations.append((time.perf_counter() - t1) * 1e3)
+        barrier()
+        return maxrank((time.perf_counter() - t0) * 1e3), durations
+
+    sequential(S32, 1)  # warm
+    ms_seq32, dur32 = sequential(S32, 1)
+    S64 = [smg.Stokes(n, precision=smg.PREC_FP64) for n in sizes]
+    sequential(S64, 1)
+    ms_seq64, dur64 = sequential(S64, 1)
+    for S in S64:
+        S.close()
+    gpu_launches = 0
+    for S, row in zip(S32, zip(*its)):
+        prof = smg.stokes_profile_iteration(S.h)
+        per_iter = sum(v[1] for v in prof.values())
+        gpu_launches += sum(row) * per_iter + per_iter + 16
+    if rank == 0:
+        q = lambda a, p: float(np.percentile(np.asarray(a), p))
+        line = {
+            "metric": "batched solved unknowns/sec to rel. residual %g" % args.tol, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 SQMR + f32 V-cycle",
+            "data": "synthetic",
+            "config": {"workload": "batch of %d problems, n^3 cells with n drawn from %s, 16 Gaussian bumps each"
+                                   % (args.batch, list(BATCH_SIZES)),
+                       "sizes": sizes, "unknowns_per_batch": total_unknowns, "streams": args.streams, "tol": args.tol,
+                       "timer": "host clock, device synchronised on both sides (the batch call blocks until done)",
+                       "parallelism": f"replicas x{world}"},
+            "iterations": its[-1],
+            "latency_ms": {"p50": q(lat, 50), "p99": q(lat, 99), "max": max(lat),
+                           "meaning": "time from the batch call's start to the problem's solution"},
+            "sequential_fp32_vcycle": {"value": total_unknowns * world / (ms_seq32 * 1e-3), "unit": UNIT,
+                                       "ms_per_batch": ms_seq32, "solve_ms_p50": q(dur32, 50), "solve_ms_p99": q(dur32, 99)},
+            "sequential_fp64_vcycle": {"value": total_unknowns * world / (ms_seq64 * 1e-3), "unit": UNIT,
+                                       "ms_per_batch": ms_seq64, "solve_ms_p50": q(dur64, 50), "solve_ms_p99": q(dur64, 99)},
+            "gpu_launches": gpu_launches * args.steps, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    for S in S32:
+        S.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,8 +360,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 V-cycle solve beside the headline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle"],
-                    help="vcycle: only time mg_precondition (one V-cycle per step) -- for profiler captures")
+    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch"],
+                    help="vcycle: only time mg_precondition (one V-cycle per step) -- for profiler captures; "
+                         "batch: independent problems of uneven sizes solved concurrently")
+    ap.add_argument("--batch", type=int, default=64, help="problems per batch (--mode batch)")
+    ap.add_argument("--streams", type=int, default=8, help="concurrent streams / host threads (--mode batch)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of --mode vcycle")
     args = ap.parse_args()
 
@@ -298,6 +406,9 @@ def main():
             print(json.dumps({"mode": "vcycle", "n": n, "precision": args.precision, "steps": args.steps,
                               "ms_per_vcycle": e0.elapsed_time(e1) / args.steps}), flush=True)
         S.close()
+        return
+    if args.mode == "batch":
+        run_batch(args, smg, synthetic, torch, dev, rank, world, dist)
         return
     seeds = [(rank * 1000 + s) % 5 for s in range(5)]
     rhs = {}

@@ -126,6 +126,16 @@ int mg_precondition(stokes_t h, const double *s, double *t, void *stream);
  * the last iterate. */
 int sqmr_solve(stokes_t h, const double *rhs, double *x, double tol, int max_iter, sqmr_info_t *info, void *stream);
 
+/* Batch of independent problems (the handles may have different grid sizes, all on one device):
+ * solves problem i = sqmr_solve(handles[i], rhs[i], x[i], tol, max_iter, &infos[i]) for all i, with
+ * nstreams host threads (1..64), each owning its own CUDA stream and pulling the next unsolved
+ * problem, so solves of different problems overlap on the GPU (each replays its handle's CUDA
+ * graphs).  done_ms[i] (may be NULL): milliseconds from the call's start to problem i's completion.
+ * Returns STOKES_OK or the first non-OK status; infos (may be NULL) carries every problem's result.
+ * A handle must not appear twice in one batch. */
+int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rhs, double *const *x, double tol,
+                     int max_iter, sqmr_info_t *infos, double *done_ms, int nstreams);
+
 /* *out = ||b - L x||_2 (FP64, deterministic reduction); synchronises the stream.  Uses the
  * handle's reduction scratch. */
 int stokes_residual_norm(stokes_t h, const double *b, const double *x, double *out, void *stream);

@@ -24,7 +24,7 @@ PREC_FP64, PREC_FP32 = 0, 1
 EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vector_length", "stokes_ghost_length",
            "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
-           "stokes_profile_iteration", "stokes_residual_norm_noalloc", "stokes_strerror"]
+           "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_strerror"]
 
 # kernel kinds reported by stokes_profile_iteration (STOKES_K_* in the header)
 KERNEL_KINDS = ["apply_dot", "update_s", "dot2", "update_x", "scalars", "memset", "vanka_compute", "vanka_apply",
@@ -82,6 +82,8 @@ def _load():
         "stokes_profile_iteration": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d),
                                          ctypes.POINTER(i), vp]),
         "stokes_residual_norm_noalloc": (i, [i, i, i, d, d, vp, vp, vp, vp]),
+        "sqmr_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,
+                                 ctypes.POINTER(sqmr_info_t), ctypes.POINTER(d), i]),
         "stokes_strerror": (ctypes.c_char_p, [i]),
     }
     for name, (res, args) in sig.items():
@@ -227,6 +229,20 @@ def stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, b, x, out, stream=Non
     library (for callers that cannot allocate; see include/stokesmg.h)."""
     _check(lib().stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, _ptr(b), _ptr(x), _ptr(out),
                                               _stream(stream)), "stokes_residual_norm_noalloc")
+
+
+def sqmr_solve_batch(handles, rhs, xs, tol=1e-8, max_iter=200, nstreams=8, check=True):
+    """Solve independent problems concurrently (one stream per host thread).  Returns (infos, done_ms)."""
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[h.value if hasattr(h, "value") else h for h in handles])
+    R = (ctypes.c_void_p * n)(*[_ptr(b) for b in rhs])
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    infos = (sqmr_info_t * n)()
+    done = (ctypes.c_double * n)()
+    rc = lib().sqmr_solve_batch(n, H, R, X, tol, max_iter, infos, done, nstreams)
+    if check:
+        _check(rc, "sqmr_solve_batch")
+    return list(infos), list(done)
 
 
 class Stokes:

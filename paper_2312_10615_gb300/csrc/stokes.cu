@@ -12,9 +12,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <chrono>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -856,6 +859,44 @@ int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launch
         }
     for (auto &ev : P.ev) cudaEventDestroy(ev);
     if (e != cudaSuccess) return cuda_status(e);
+    return STOKES_OK;
+}
+
+int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rhs, double *const *x, double tol,
+                     int max_iter, sqmr_info_t *infos, double *done_ms, int nstreams) {
+    if (nprob <= 0 || !handles || !rhs || !x) return STOKES_ERR_INVALID_ARG;
+    int dev = -1;
+    for (int i = 0; i < nprob; ++i) {
+        if (!handles[i] || !rhs[i] || !x[i]) return STOKES_ERR_INVALID_ARG;
+        if (dev < 0) dev = handles[i]->dev;
+        if (handles[i]->dev != dev) return STOKES_ERR_INVALID_ARG;  // one device per batch
+    }
+    int nt = nstreams < 1 ? 1 : (nstreams > nprob ? nprob : (nstreams > 64 ? 64 : nstreams));
+    std::vector<int> status(nprob, STOKES_OK);
+    std::atomic<int> next(0);
+    std::atomic<int> setup_err(0);
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&]() {
+            if (cudaSetDevice(dev) != cudaSuccess) { cudaGetLastError(); setup_err = STOKES_ERR_CUDA; return; }
+            cudaStream_t st = nullptr;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                setup_err = STOKES_ERR_CUDA;
+                return;
+            }
+            for (int i = next++; i < nprob; i = next++) {
+                status[i] = sqmr_solve(handles[i], rhs[i], x[i], tol, max_iter, infos ? &infos[i] : nullptr, st);
+                if (done_ms)
+                    done_ms[i] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            }
+            cudaStreamDestroy(st);
+        });
+    for (auto &th : pool) th.join();
+    if (setup_err) return setup_err;
+    for (int i = 0; i < nprob; ++i)
+        if (status[i] != STOKES_OK) return status[i];
     return STOKES_OK;
 }
 
