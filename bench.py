@@ -349,24 +349,73 @@ def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
         S.close()
 
 
+def run_cavity(args, smg, synthetic, torch, dev, rank, world, dist):
+    """3D lid-driven cavity (Sec. 7): n^3 cells, lid u = 1 on the top, no slip elsewhere,
+    eta = gamma = 1e-3, from x0 = 0 to args.tol; FP32 V-cycle + FP64 SQMR beside the plain FP64 V-cycle."""
+    n = args.n
+    prob = synthetic.lid(n, device=dev)
+    res = {}
+    for name, prec in (("fp32_vcycle", smg.PREC_FP32), ("fp64_vcycle", smg.PREC_FP64)):
+        S = smg.Stokes(n, viscosity=1e-3, gamma=1e-3, precision=prec)
+        b = S.rhs(prob["f"], prob["g"])
+        x = torch.zeros_like(b)
+        for _ in range(args.warmup):
+            x.zero_()
+            smg.sqmr_solve(S.h, b, x, args.tol, 400)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            x.zero_()
+            info = smg.sqmr_solve(S.h, b, x, args.tol, 400)
+            its.append((info.iterations, info.rel_residual))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        res[name] = {"value": unknowns(n) * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                     "iterations": [i for i, _ in its], "rel_residual": [r for _, r in its], "levels": S.levels}
+        S.close()
+    if rank == 0:
+        h = res["fp32_vcycle"]
+        line = {"metric": "solved unknowns/sec to rel. residual %g, 3D lid-driven cavity" % args.tol,
+                "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 SQMR + f32 V-cycle", "data": "synthetic",
+                "config": {"workload": "3D lid-driven cavity %d^3, eta = gamma = 1e-3" % n, "n": n,
+                           "unknowns": unknowns(n), "tol": args.tol, "parallelism": f"replicas x{world}"},
+                "fp32_vcycle": h, "fp64_vcycle": res["fp64_vcycle"]}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", type=int, default=None, help="cells per axis (default 256; 128 for --mode cavity)")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 V-cycle solve beside the headline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity"],
                     help="vcycle: only time mg_precondition (one V-cycle per step) -- for profiler captures; "
-                         "batch: independent problems of uneven sizes solved concurrently")
+                         "batch: independent problems of uneven sizes solved concurrently; "
+                         "cavity: the 3D lid-driven cavity (eta = gamma = 1e-3)")
     ap.add_argument("--batch", type=int, default=64, help="problems per batch (--mode batch)")
     ap.add_argument("--streams", type=int, default=8, help="concurrent streams / host threads (--mode batch)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of --mode vcycle")
     args = ap.parse_args()
+    if args.n is None:
+        args.n = 128 if args.mode == "cavity" else 256
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -409,6 +458,9 @@ def main():
         return
     if args.mode == "batch":
         run_batch(args, smg, synthetic, torch, dev, rank, world, dist)
+        return
+    if args.mode == "cavity":
+        run_cavity(args, smg, synthetic, torch, dev, rank, world, dist)
         return
     seeds = [(rank * 1000 + s) % 5 for s in range(5)]
     rhs = {}
@@ -479,9 +531,19 @@ def main():
         ms64 = timed(S64, max(1, args.steps // 2), 1, its64)
         prof64 = smg.stokes_profile_iteration(S64.h)
         k64 = max(prof64, key=lambda k: prof64[k][0])
+        # error of the mixed-precision solution against the plain FP64 GPU run on the same right-hand side
+        xa, xb = torch.zeros_like(x), torch.zeros_like(x)
+        smg.sqmr_solve(S32.h, rhs[seeds[0]], xa, args.tol, 200)
+        smg.sqmr_solve(S64.h, rhs[seeds[0]], xb, args.tol, 200)
+        diff_max = float(torch.max(torch.abs(xa - xb)) / torch.max(torch.abs(xb)))
+        diff_l2 = float(torch.linalg.norm(xa - xb) / torch.linalg.norm(xb))
+        del xa, xb
         fp64 = {"value": unknowns(n) * len(its64) * world / (ms64 * 1e-3), "unit": UNIT,
                 "ms_per_step": ms64 / len(its64), "iterations": [it for it, _ in its64],
                 "rel_residual": [r for _, r in its64], "dominant_kernel": k64,
+                "fp32_vcycle_solution_rel_diff": {"max": diff_max, "l2": diff_l2,
+                                                  "meaning": "FP32-V-cycle solve vs this FP64-V-cycle solve, "
+                                                             "same right-hand side, both to the tolerance"},
                 "kernel_ms_per_iteration": {k: round(v[0], 4) for k, v in prof64.items()}}
         S64.close()
 

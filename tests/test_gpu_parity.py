@@ -249,6 +249,56 @@ def test_sqmr_fp32_vcycle_accuracy():
     assert rel_err(x, x_ref) < 1e-7
 
 
+# ---------------------------------------------------------------------------------------------- F1
+
+def test_lid_cavity_32_parity():
+    # 3D lid-driven cavity (Sec. 7): eta = gamma = 1e-3, lid u = 1 on the top ghost row; the GPU
+    # iterates equal the oracle's at the same iteration count
+    o = oracle.Oracle(32, 32, 32, eta=1e-3, gamma=1e-3, coarsest_max=8)
+    S = smg.Stokes(32, viscosity=1e-3, gamma=1e-3)
+    prob = synthetic.lid(32)
+    b_ref = o.rhs(prob["f"].numpy(), prob["g"].numpy())
+    x_ref, rc, it_ref, _, _ = o.sqmr(b_ref, tol=1e-8, maxit=100, fixed_iters=8)
+    b = S.rhs(prob["f"].to(DEV), prob["g"].to(DEV))
+    assert rel_err(b, b_ref) < 1e-13
+    x = torch.zeros_like(b)
+    info = smg.sqmr_solve(S.h, b, x, tol=1e-30, max_iter=8, check=False)
+    assert info.iterations == 8
+    assert rel_err(x, x_ref) < 1e-10
+    S.close()
+
+
+def test_lid_cavity_128():
+    # the paper's 3D cavity at 128^3, 5 levels: FP64 and FP32 V-cycles reach 1e-8; the flow is mirror
+    # symmetric about y = 1/2 (u, w, p even, v odd); the two solutions agree
+    n = 128
+    prob = synthetic.lid(n, device=DEV)
+    out = {}
+    for prec in (smg.PREC_FP64, smg.PREC_FP32):
+        S = smg.Stokes(n, viscosity=1e-3, gamma=1e-3, precision=prec)
+        assert S.levels == 5
+        b = S.rhs(prob["f"], prob["g"])
+        x, info = S.solve(b, tol=1e-10, max_iter=200)
+        assert info.status == 0 and info.rel_residual < 1e-10
+        assert S.residual_norm(b, x) / float(torch.linalg.norm(b)) < 1e-10
+        out[prec] = (x, info.iterations)
+        S.close()
+    x64, it64 = out[smg.PREC_FP64]
+    x32, it32 = out[smg.PREC_FP32]
+    assert abs(it64 - it32) <= 2
+    assert float(torch.max(torch.abs(x32 - x64)) / torch.max(torch.abs(x64))) < 1e-7
+    u, v, w, p = synthetic.unpack(x64.cpu(), n)
+    scale = float(torch.max(torch.abs(x64[: 3 * (n + 1) * n * n])))
+    # the colour orders of the smoothers are not mirror symmetric, so the mirror image agrees to the
+    # solve's accuracy only
+    assert float(torch.max(torch.abs(u - u.flip(1)))) < 1e-7 * scale
+    assert float(torch.max(torch.abs(v + v.flip(1)))) < 1e-7 * scale
+    assert float(torch.max(torch.abs(w - w.flip(1)))) < 1e-7 * scale
+    assert abs(float(p.mean())) < 1e-12 * float(torch.max(torch.abs(p)))
+    # the lid drags the top layer forward (u > 0 just under the lid) and the return flow runs below
+    assert float(u[-1, n // 2, n // 2]) > 0.1 and float(u[n // 2, n // 2, n // 2]) < 0.0
+
+
 def test_sqmr_host_pointers_match_device():
     o, S = pair((32, 32, 32))
     prob = synthetic.bumps(32, seed=2)
