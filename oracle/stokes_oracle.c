@@ -195,12 +195,15 @@ static int og_lu(long n, double *A, long *piv) {
     return OG_OK;
 }
 
+/* solve with the factors of og_lu: og_lu swaps whole rows (multipliers included), so LU holds the
+ * factors of P A with P the product of all its swaps; apply P to y first, then L and U */
 static void og_lu_solve(long n, const double *LU, const long *piv, double *y) {
     for (long col = 0; col < n; ++col) {
         long p = piv[col];
         if (p != col) { double s = y[col]; y[col] = y[p]; y[p] = s; }
-        for (long r = col + 1; r < n; ++r) y[r] -= LU[r * n + col] * y[col];
     }
+    for (long col = 0; col < n; ++col)
+        for (long r = col + 1; r < n; ++r) y[r] -= LU[r * n + col] * y[col];
     for (long r = n - 1; r >= 0; --r) {
         double s = y[r];
         for (long t = r + 1; t < n; ++t) s -= LU[r * n + t] * y[t];

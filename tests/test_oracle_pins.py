@@ -147,9 +147,11 @@ def _assemble(fn, n, active):
     return C
 
 
+# eta = 1e-3 is the paper's viscosity (Sec. 7); there the local saddle-point matrices need row pivoting
+@pytest.mark.parametrize("eta", [1.0, 1e-3])
 @pytest.mark.parametrize("which", ["dgs", "vanka", "smooth"])
-def test_smoother_C_symmetric(which):
-    o = oracle.Oracle(6, gamma=1e-3, levels=1, kb=1)
+def test_smoother_C_symmetric(which, eta):
+    o = oracle.Oracle(6, eta=eta, gamma=1e-3, levels=1, kb=1)
     act, _ = o.masks()
     z = np.zeros(o.n())
     fn = {"dgs": lambda e: o.dgs(z, e, direction=0),
@@ -169,11 +171,12 @@ def test_forward_dgs_alone_is_not_symmetric():
     assert np.max(np.abs(C - C.T)) > 1e-3 * np.max(np.abs(C))
 
 
-def test_vanka_single_patch_is_exact_local_solve():
+@pytest.mark.parametrize("eta", [1.0, 1e-3])
+def test_vanka_single_patch_is_exact_local_solve(eta):
     # Sec. 3.2: on a 2^3 grid every colour holds one cell, so after that colour the residual of
     # L~ vanishes on the cell's patch (exact local saddle-point solve).
-    o = oracle.Oracle(2, levels=1, coarsest_max=2)
-    D = DenseBox(2)
+    o = oracle.Oracle(2, eta=eta, levels=1, coarsest_max=2)
+    D = DenseBox(2, eta=eta)
     x = _masked(_rand(D.n, 6), D.active)
     b = _masked(_rand(D.n, 7), D.active)
     for col in range(8):
@@ -267,16 +270,18 @@ def test_pressure_restriction_is_mean_of_children():
 # ----------------------------------------------------------------------------------------------
 # Alg. 1: coarse solve, V-cycle linearity/symmetry (Sec. 3, conditions for a symmetric W^dagger)
 
-def test_one_level_vcycle_is_exact_inverse():
-    o = oracle.Oracle(4, levels=1, gamma=1e-2)
-    D = DenseBox(4, gamma=1e-2)
+@pytest.mark.parametrize("eta", [1.0, 1e-3])
+def test_one_level_vcycle_is_exact_inverse(eta):
+    o = oracle.Oracle(4, eta=eta, levels=1, gamma=1e-2)
+    D = DenseBox(4, eta=eta, gamma=1e-2)
     s = _masked(_rand(D.n, 9), D.active)
     t = o.vcycle(s)
     assert np.max(np.abs(D.Lt @ t - s)) < 1e-10 * np.max(np.abs(s))
 
 
-def test_vcycle_dense_symmetric():
-    o = oracle.Oracle(8, levels=2, coarsest_max=4)
+@pytest.mark.parametrize("eta", [1.0, 1e-3])
+def test_vcycle_dense_symmetric(eta):
+    o = oracle.Oracle(8, eta=eta, levels=2, coarsest_max=4)
     act, _ = o.masks()
     W = _assemble(o.vcycle, o.n(), act)
     assert np.max(np.abs(W - W.T)) <= 1e-11 * np.max(np.abs(W))
@@ -314,10 +319,11 @@ def test_unpreconditioned_sqmr_equals_minres():
         assert np.max(np.abs(xj - ref)) <= 1e-8 * np.max(np.abs(ref)), j
 
 
-def test_mg_sqmr_matches_direct_solve():
+@pytest.mark.parametrize("eta", [1.0, 1e-3])
+def test_mg_sqmr_matches_direct_solve(eta):
     n = 8
-    o = oracle.Oracle(n, levels=2, coarsest_max=4)
-    D = DenseBox(n)
+    o = oracle.Oracle(n, eta=eta, levels=2, coarsest_max=4)
+    D = DenseBox(n, eta=eta)
     b = _masked(_rand(D.n, 13), D.active)
     b[D.offsets[3]:] -= b[D.offsets[3]:].mean()
     x, rc, it, rr, _ = o.sqmr(b, tol=1e-13, maxit=200)
