@@ -395,6 +395,98 @@ def run_cavity(args, smg, synthetic, torch, dev, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args, smg, synthetic, torch, dev, rank, world):
+    """Learned initial guess: args.train + args.test problems (n^3, 8 Gaussian bumps each, seeds
+    20000 + i); every problem is solved by the method (FP32 V-cycle, FP64 SQMR, tol 1e-8) to give the
+    training targets; the network (BF16 activations, FP32 accumulation) is trained with Adam for
+    args.epochs passes; on the held-out seeds the solve from the network's guess is timed against the
+    solve from x0 = 0 (same handle, same tolerance)."""
+    import numpy as np
+    n = args.n
+    S = smg.Stokes(n, precision=smg.PREC_FP32)
+    npk = S.n
+    seeds = [20000 + rank * 1000000 + i for i in range(args.train + args.test)]
+
+    def rhs(sd):
+        return S.rhs(synthetic.bumps(n, seed=sd, nbumps=8, device=dev)["f"], None)
+
+    t0 = time.perf_counter()
+    xs_store = torch.empty((len(seeds), npk), dtype=torch.float32, device=dev)
+    its0 = []
+    ratio = []
+    for i, sd in enumerate(seeds):
+        b = rhs(sd)
+        x = torch.zeros_like(b)
+        info = smg.sqmr_solve(S.h, b, x, 1e-8, 200)
+        its0.append(info.iterations)
+        xs_store[i] = x.float()
+        if i < 64:
+            ratio.append(float(x.norm() / b.norm()))
+    gen_s = time.perf_counter() - t0
+    scale = float(np.median(ratio))  # ||x*|| / ||b||: the network's output is scale * ||b|| * O(1)
+    ws = smg.WarmStart(n, smg.STORE_BF16, scale=scale)
+    ws.set_weights(synthetic.net_weights(7).astype(np.float32))
+    steps = args.epochs * args.train
+    rng = np.random.default_rng(5)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = []
+    for st in range(steps):
+        i = int(rng.integers(args.train))
+        lr = 1e-3 * 0.5 * (1 + np.cos(np.pi * st / steps))  # cosine decay
+        b = rhs(seeds[i])
+        want = st % 200 == 0 or st == steps - 1
+        loss = ws.train_step(b, xs_store[i].double(), lr, want_loss=want)
+        if want:
+            losses.append((st, loss))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    # held-out evaluation
+    stream = torch.cuda.current_stream()
+    rows = []
+    for k in range(args.test):
+        i = args.train + k
+        b = rhs(seeds[i])
+        xstar = xs_store[i].double()
+        x = torch.zeros_like(b)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        info0 = smg.sqmr_solve(S.h, b, x, 1e-8, 200)
+        e1.record(stream)
+        xw, infow, used = ws.solve(S, b, tol=1e-8)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        x0 = ws.predict(b)
+        err = float((x0 - xstar).norm() / xstar.norm())
+        rows.append((info0.iterations, e0.elapsed_time(e1), infow.iterations, e1.elapsed_time(e2), used, err,
+                     infow.rel_residual))
+    r = np.array([[a, b_, c, d, float(e), f, g] for a, b_, c, d, e, f, g in rows])
+    if rank == 0:
+        line = {
+            "metric": "solved unknowns/sec to rel. residual 1e-8, learned initial guess vs x0 = 0",
+            "value": unknowns(n) * world / (r[:, 3].mean() * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.test, "warmup": 1, "ms_per_step": float(r[:, 3].mean()), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 net (f32 acc) + f32 V-cycle + f64 SQMR",
+            "data": "synthetic",
+            "config": {"workload": "%d^3 box, 8 Gaussian bumps per seed; %d training solves, %d held-out seeds"
+                                   % (n, args.train, args.test), "n": n, "epochs": args.epochs,
+                       "network": "4 levels, 16 channels, 3x3x3 convolutions, leaky ReLU 0.1, no bias",
+                       "parallelism": f"replicas x{world}"},
+            "x0_zero": {"iterations_mean": float(r[:, 0].mean()), "ms_mean": float(r[:, 1].mean()),
+                        "value": unknowns(n) / (r[:, 1].mean() * 1e-3)},
+            "learned_x0": {"iterations_mean": float(r[:, 2].mean()), "ms_mean": float(r[:, 3].mean()),
+                           "value": unknowns(n) / (r[:, 3].mean() * 1e-3), "guess_used": float(r[:, 4].mean()),
+                           "x0_rel_error_mean": float(r[:, 5].mean()), "max_rel_residual": float(r[:, 6].max())},
+            "training": {"solves_s": gen_s, "train_s": train_s, "steps": steps, "ms_per_step": train_s * 1e3 / steps,
+                         "loss_trace": losses[:: max(1, len(losses) // 12)] + losses[-1:],
+                         "data_iterations_mean": float(np.mean(its0))},
+        }
+        print(json.dumps(line), flush=True)
+    ws.close()
+    S.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,16 +498,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 V-cycle solve beside the headline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity"],
+    ap.add_argument("--train", type=int, default=2000, help="training solves (--mode warmstart)")
+    ap.add_argument("--test", type=int, default=200, help="held-out seeds (--mode warmstart)")
+    ap.add_argument("--epochs", type=int, default=2, help="passes over the training solves (--mode warmstart)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity", "warmstart"],
                     help="vcycle: only time mg_precondition (one V-cycle per step) -- for profiler captures; "
                          "batch: independent problems of uneven sizes solved concurrently; "
-                         "cavity: the 3D lid-driven cavity (eta = gamma = 1e-3)")
+                         "cavity: the 3D lid-driven cavity (eta = gamma = 1e-3); "
+                         "warmstart: train the initial-guess network on solves, then solve held-out seeds")
     ap.add_argument("--batch", type=int, default=64, help="problems per batch (--mode batch)")
     ap.add_argument("--streams", type=int, default=8, help="concurrent streams / host threads (--mode batch)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of --mode vcycle")
     args = ap.parse_args()
     if args.n is None:
-        args.n = 128 if args.mode == "cavity" else 256
+        args.n = 128 if args.mode in ("cavity", "warmstart") else 256
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -461,6 +557,9 @@ def main():
         return
     if args.mode == "cavity":
         run_cavity(args, smg, synthetic, torch, dev, rank, world, dist)
+        return
+    if args.mode == "warmstart":
+        run_warmstart(args, smg, synthetic, torch, dev, rank, world)
         return
     seeds = [(rank * 1000 + s) % 5 for s in range(5)]
     rhs = {}

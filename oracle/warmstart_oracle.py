@@ -54,13 +54,6 @@ def split_weights(w):
     return out
 
 
-def init_weights(seed):
-    """He-style initial weights N(0, 2 / fan_in), seeded (PCG64)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    parts = [rng.standard_normal(a * b * c) * np.sqrt(2.0 / (a * b)) for a, b, c in SHAPES]
-    return np.concatenate(parts)
-
-
 # ---------------------------------------------------------------------------------- packed <-> cells
 
 def _split(x, n):

@@ -24,7 +24,11 @@ PREC_FP64, PREC_FP32 = 0, 1
 EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vector_length", "stokes_ghost_length",
            "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
-           "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_strerror"]
+           "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_strerror",
+           # learned initial guess (include/warmstart.h)
+           "warmstart_num_weights", "warmstart_create", "warmstart_destroy", "warmstart_set_scale",
+           "warmstart_set_weights", "warmstart_get_weights", "warmstart_predict", "warmstart_loss_grad",
+           "warmstart_adam_step", "warmstart_solve"]
 
 # kernel kinds reported by stokes_profile_iteration (STOKES_K_* in the header)
 KERNEL_KINDS = ["apply_dot", "update_s", "dot2", "update_x", "scalars", "memset", "vanka_compute", "vanka_apply",
@@ -85,6 +89,16 @@ def _load():
         "sqmr_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,
                                  ctypes.POINTER(sqmr_info_t), ctypes.POINTER(d), i]),
         "stokes_strerror": (ctypes.c_char_p, [i]),
+        "warmstart_num_weights": (ll, []),
+        "warmstart_create": (i, [i, i, d, ctypes.POINTER(vp)]),
+        "warmstart_destroy": (i, [vp]),
+        "warmstart_set_scale": (i, [vp, d]),
+        "warmstart_set_weights": (i, [vp, vp]),
+        "warmstart_get_weights": (i, [vp, vp]),
+        "warmstart_predict": (i, [vp, vp, vp, vp]),
+        "warmstart_loss_grad": (i, [vp, vp, vp, ctypes.POINTER(d), vp, vp]),
+        "warmstart_adam_step": (i, [vp, d, d, d, d, vp]),
+        "warmstart_solve": (i, [vp, vp, vp, vp, d, i, ctypes.POINTER(sqmr_info_t), ctypes.POINTER(i), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -294,3 +308,93 @@ class Stokes:
 
     def residual_norm(self, b, x):
         return stokes_residual_norm(self.h, b, x)
+
+
+# ------------------------------------------------------------------------------------------------
+# learned initial guess (include/warmstart.h)
+
+STORE_FP32, STORE_BF16 = 0, 1
+
+
+def _fptr(a):
+    """Raw pointer of a float32 contiguous torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("weight arrays must be float32 and C-contiguous")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise TypeError("weight tensors must be float32 and contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def warmstart_num_weights():
+    return int(lib().warmstart_num_weights())
+
+
+class WarmStart:
+    """Owning wrapper of the initial-guess network for n^3 problems (activations FP32 or BF16)."""
+
+    def __init__(self, n, storage=STORE_BF16, scale=1.0):
+        self.n = n
+        self.h = ctypes.c_void_p()
+        _check(lib().warmstart_create(n, storage, float(scale), ctypes.byref(self.h)), "warmstart_create")
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            _check(lib().warmstart_destroy(self.h), "warmstart_destroy")
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_scale(self, scale):
+        _check(lib().warmstart_set_scale(self.h, float(scale)), "warmstart_set_scale")
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32) if isinstance(w, np.ndarray) else w
+        assert (w.size if isinstance(w, np.ndarray) else w.numel()) == warmstart_num_weights()
+        _check(lib().warmstart_set_weights(self.h, _fptr(w)), "warmstart_set_weights")
+
+    def get_weights(self):
+        w = np.zeros(warmstart_num_weights(), dtype=np.float32)
+        _check(lib().warmstart_get_weights(self.h, _fptr(w)), "warmstart_get_weights")
+        return w
+
+    def predict(self, b, out=None, stream=None):
+        import torch
+        out = torch.empty_like(b) if out is None else out
+        _check(lib().warmstart_predict(self.h, _ptr(b), _ptr(out), _stream(stream)), "warmstart_predict")
+        return out
+
+    def loss_grad(self, b, xstar, want_loss=True, want_grad=False, stream=None):
+        loss = ctypes.c_double(0.0)
+        g = np.zeros(warmstart_num_weights(), dtype=np.float32) if want_grad else None
+        _check(lib().warmstart_loss_grad(self.h, _ptr(b), _ptr(xstar), ctypes.byref(loss) if want_loss else None,
+                                         _fptr(g) if want_grad else None, _stream(stream)), "warmstart_loss_grad")
+        return (loss.value if want_loss else None), g
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(lib().warmstart_adam_step(self.h, lr, beta1, beta2, eps, _stream(stream)), "warmstart_adam_step")
+
+    def train_step(self, b, xstar, lr, want_loss=False, stream=None):
+        loss, _ = self.loss_grad(b, xstar, want_loss=want_loss, stream=stream)
+        self.adam_step(lr, stream=stream)
+        return loss
+
+    def solve(self, S, b, x=None, tol=1e-8, max_iter=200, check=True, stream=None):
+        """SQMR solve of Stokes handle S from the network's guess; returns (x, info, used_guess)."""
+        import torch
+        x = torch.empty_like(b) if x is None else x
+        info = sqmr_info_t()
+        used = ctypes.c_int(0)
+        rc = lib().warmstart_solve(self.h, S.h if isinstance(S, Stokes) else S, _ptr(b), _ptr(x), tol, max_iter,
+                                   ctypes.byref(info), ctypes.byref(used), _stream(stream))
+        if check:
+            _check(rc, "warmstart_solve")
+        return x, info, bool(used.value)

@@ -194,3 +194,14 @@ def random_vector(n, seed, nx=None, device="cpu"):
     rng = np.random.Generator(np.random.PCG64(seed))
     m = packed_len(n) if nx is None else packed_len(*nx)
     return torch.from_numpy(rng.standard_normal(m)).to(device)
+
+
+# ---------------------------------------------------------------------------------------------
+# initial weights of the learned initial-guess network: He-style N(0, 2 / fan_in), seeded (PCG64).
+# Tensor shapes (taps, in channels, out channels) in the order of the flat weight vector.
+NET_SHAPES = [(27, 4, 16)] + [(27, 16, 16)] * 10 + [(1, 16, 4)]
+
+
+def net_weights(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.concatenate([rng.standard_normal(a * b * c) * np.sqrt(2.0 / (a * b)) for a, b, c in NET_SHAPES])

@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point include/stokesmg.h
-declares (no compute calls: runs without a GPU)."""
+and include/warmstart.h declare (no compute calls: runs without a GPU)."""
 import ctypes
 import os
 import re
@@ -8,9 +8,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "stokesmg.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?(?:[a-z_0-9]+\s+)+\**\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
+    names = []
+    for hdr in ("stokesmg.h", "warmstart.h"):
+        src = open(os.path.join(ROOT, "include", hdr)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?(?:[a-z_0-9]+\s+)+\**\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 

@@ -4,6 +4,7 @@ finite differences of its own forward map."""
 import numpy as np
 import pytest
 
+import synthetic
 from oracle import warmstart_oracle as wo
 
 
@@ -79,7 +80,7 @@ def _problem(n, seed):
 
 def test_forward_positively_homogeneous():
     n = 8
-    w = wo.init_weights(0)
+    w = synthetic.net_weights(0)
     b, _ = _problem(n, 11)
     x1 = wo.predict(b, w, n, 0.3)
     x2 = wo.predict(2.5 * b, w, n, 0.3)
@@ -88,7 +89,7 @@ def test_forward_positively_homogeneous():
 
 def test_gradient_matches_finite_differences():
     n = 16  # level 3 is 2^3, so every tap of the coarsest convolutions is exercised
-    w = wo.init_weights(1) * 0.5
+    w = synthetic.net_weights(1) * 0.5
     b, xs = _problem(n, 12)
     L, g = wo.loss_and_grad(b, xs, w, n, 0.7)
     assert abs(L - wo.loss(b, xs, w, n, 0.7)) < 1e-14 * L
