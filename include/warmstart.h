@@ -19,7 +19,8 @@
  *   c2 = act(conv(up(b3) + s2, W8)), c1 = act(conv(up(c2) + s1, W9))   up: nearest-neighbour x2
  *   c0 = act(conv(up(c1) + s0, W10)), P = c0 W11 (1x1x1, 16 -> 4 channels)
  *   x0 = scale * rms(b) * faces(P)    interior face = mean of its two cells, wall face 0, pressure P
- * Loss for training: ||x0 - x*||^2 / ||x*||^2 over the packed vector.
+ * Loss for training (x* = the solver's solution for b): ||x0 - x*||^2 / ||x*||^2, or
+ * ||L (x0 - x*)||^2 / ||b||^2 with the problem's operator L (warmstart_loss_grad).
  * WEIGHTS: one flat FP32 vector of warmstart_num_weights() entries: W0 [27][4][16], W1..W10
  * [27][16][16], W11 [16][4]; tap t = 9 (dz+1) + 3 (dy+1) + (dx+1); last index fastest.
  * STORAGE: activations are kept as FP32 or BF16 (WARMSTART_STORE_*); every convolution accumulates
@@ -60,18 +61,24 @@ int warmstart_get_weights(warmstart_t ws, float *w);
 /* x0 = network(b) (packed, 0 on the wall-normal faces) */
 int warmstart_predict(warmstart_t ws, const double *b, double *x0, void *stream);
 
-/* forward + loss + backward: the gradient of the loss goes into the handle's gradient buffer and,
- * if grad != NULL, is copied to grad (host or device, num_weights floats; synchronises).  If
- * loss != NULL the stream is synchronised and *loss receives the loss. */
-int warmstart_loss_grad(warmstart_t ws, const double *b, const double *xstar, double *loss, float *grad,
+/* forward + loss + backward for right-hand side b and the method's solution xstar of it (device
+ * vectors).  h == NULL: loss ||x0 - x*||^2 / ||x*||^2; h = the n^3 Stokes handle of the problem:
+ * loss ||L (x0 - x*)||^2 / ||b||^2 (what SQMR's stopping test measures; two stokes_apply calls).
+ * The gradient goes into the handle's gradient buffer and, if grad != NULL, is copied to grad (host
+ * or device, num_weights floats; synchronises).  If loss != NULL the stream is synchronised and
+ * *loss receives the loss. */
+int warmstart_loss_grad(warmstart_t ws, stokes_t h, const double *b, const double *xstar, double *loss, float *grad,
                         void *stream);
 
 /* one Adam update (Kingma & Ba, Algorithm 1) of the weights from the handle's gradient buffer */
 int warmstart_adam_step(warmstart_t ws, double lr, double beta1, double beta2, double eps, void *stream);
 
-/* SQMR solve of stokes handle h from the network's guess: x <- network(b); if ||b - L x|| >= ||b||
- * the guess is discarded (x <- 0); then sqmr_solve(h, b, x, tol, max_iter, info).  *used_guess
- * (may be NULL) tells which start was taken.  h must be an n^3 problem on the same device. */
+/* SQMR solve of stokes handle h from the network's guess: x <- network(b); SQMR's first quantity
+ * tau_0 = ||M (b - L x)|| (Alg. 4, M = the V-cycle) is compared with its value for x0 = 0, ||M b||,
+ * and a guess that does not lower it is discarded (x <- 0); then sqmr_solve(h, b, x, tol, max_iter,
+ * info).  Costs one network evaluation, one operator apply and two V-cycles before the solve.
+ * *used_guess (may be NULL) tells which start was taken.  h must be an n^3 problem on the same
+ * device. */
 int warmstart_solve(warmstart_t ws, stokes_t h, const double *b, double *x, double tol, int max_iter,
                     sqmr_info_t *info, int *used_guess, void *stream);
 

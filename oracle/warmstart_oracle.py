@@ -30,7 +30,9 @@ conv: 3 x 3 x 3, zero padding, weights W[t, ci, co] with tap t = 9 (dz+1) + 3 (d
 pool: mean over 2 x 2 x 2 blocks; up: nearest-neighbour doubling; cells(b): the velocity component
 of a cell is the mean of its two faces along that axis, the pressure is b's pressure entry;
 faces(P): an interior face takes the mean of its two cells, a wall face 0, the pressure is P's.
-Loss: ||x0 - x*||^2 / ||x*||^2 on the packed vector.
+Loss, with x* a solution the method produced for b:  ||x0 - x*||^2 / ||x*||^2 (error form), or
+with the operator L of the problem ||L (x0 - x*)||^2 / ||b||^2 (residual form: the quantity SQMR's
+stopping test measures, since L x* = b up to the solve's tolerance).
 """
 import numpy as np
 
@@ -193,19 +195,28 @@ def predict(b, w, n, scale):
     return forward(b, w, n, scale)[0]
 
 
-def loss(b, xstar, w, n, scale):
+def loss(b, xstar, w, n, scale, apply=None):
     x0, _ = forward(b, w, n, scale)
-    return float(np.sum((x0 - xstar) ** 2) / np.sum(xstar ** 2))
+    if apply is None:
+        return float(np.sum((x0 - xstar) ** 2) / np.sum(xstar ** 2))
+    return float(np.sum(apply(x0 - xstar) ** 2) / np.sum(np.asarray(b) ** 2))
 
 
-def loss_and_grad(b, xstar, w, n, scale):
-    """Loss and its gradient with respect to the flat weight vector (reverse mode, by hand)."""
+def loss_and_grad(b, xstar, w, n, scale, apply=None):
+    """Loss and its gradient with respect to the flat weight vector (reverse mode, by hand).
+    apply: None for the error form, else a function x -> L x (L symmetric) for the residual form."""
     W = split_weights(w)
     x0, c = forward(b, w, n, scale)
-    den = float(np.sum(xstar ** 2))
     diff = x0 - xstar
-    L = float(np.sum(diff ** 2) / den)
-    dx0 = 2.0 * diff / den
+    if apply is None:
+        den = float(np.sum(xstar ** 2))
+        L = float(np.sum(diff ** 2) / den)
+        dx0 = 2.0 * diff / den
+    else:
+        den = float(np.sum(np.asarray(b) ** 2))
+        r = apply(diff)
+        L = float(np.sum(r ** 2) / den)
+        dx0 = 2.0 * apply(r) / den
     dP = scale * c["rms"] * faces_T(dx0, n)
     g = [None] * 12
     g[11] = (c["c0"].reshape(-1, CH).T @ dP.reshape(-1, 4))[None]

@@ -96,7 +96,7 @@ def _load():
         "warmstart_set_weights": (i, [vp, vp]),
         "warmstart_get_weights": (i, [vp, vp]),
         "warmstart_predict": (i, [vp, vp, vp, vp]),
-        "warmstart_loss_grad": (i, [vp, vp, vp, ctypes.POINTER(d), vp, vp]),
+        "warmstart_loss_grad": (i, [vp, vp, vp, vp, ctypes.POINTER(d), vp, vp]),
         "warmstart_adam_step": (i, [vp, d, d, d, d, vp]),
         "warmstart_solve": (i, [vp, vp, vp, vp, d, i, ctypes.POINTER(sqmr_info_t), ctypes.POINTER(i), vp]),
     }
@@ -372,18 +372,20 @@ class WarmStart:
         _check(lib().warmstart_predict(self.h, _ptr(b), _ptr(out), _stream(stream)), "warmstart_predict")
         return out
 
-    def loss_grad(self, b, xstar, want_loss=True, want_grad=False, stream=None):
+    def loss_grad(self, b, xstar, S=None, want_loss=True, want_grad=False, stream=None):
+        """S None: error-form loss; S a Stokes handle: residual-form loss ||L (x0 - x*)||^2 / ||b||^2."""
         loss = ctypes.c_double(0.0)
         g = np.zeros(warmstart_num_weights(), dtype=np.float32) if want_grad else None
-        _check(lib().warmstart_loss_grad(self.h, _ptr(b), _ptr(xstar), ctypes.byref(loss) if want_loss else None,
+        hs = None if S is None else (S.h if isinstance(S, Stokes) else S)
+        _check(lib().warmstart_loss_grad(self.h, hs, _ptr(b), _ptr(xstar), ctypes.byref(loss) if want_loss else None,
                                          _fptr(g) if want_grad else None, _stream(stream)), "warmstart_loss_grad")
         return (loss.value if want_loss else None), g
 
     def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         _check(lib().warmstart_adam_step(self.h, lr, beta1, beta2, eps, _stream(stream)), "warmstart_adam_step")
 
-    def train_step(self, b, xstar, lr, want_loss=False, stream=None):
-        loss, _ = self.loss_grad(b, xstar, want_loss=want_loss, stream=stream)
+    def train_step(self, b, xstar, lr, S=None, want_loss=False, stream=None):
+        loss, _ = self.loss_grad(b, xstar, S=S, want_loss=want_loss, stream=stream)
         self.adam_step(lr, stream=stream)
         return loss
 

@@ -63,6 +63,25 @@ def test_loss_and_gradient_parity_fp32():
     ws.close()
 
 
+def test_residual_form_loss_and_gradient_parity_fp32():
+    import oracle
+    o = oracle.Oracle(N, coarsest_max=8)
+    act, _ = o.masks()
+    S = smg.Stokes(N)
+    w = _weights(9)
+    ws = smg.WarmStart(N, smg.STORE_FP32, scale=0.7)
+    ws.set_weights(w)
+    b, xs = _vec(N, 8), _vec(N, 9)
+    b[~act] = 0.0
+    xs[~act] = 0.0
+    loss, g = ws.loss_grad(torch.from_numpy(b).to(DEV), torch.from_numpy(xs).to(DEV), S=S, want_grad=True)
+    L, G = wo.loss_and_grad(b, xs, w.astype(np.float64), N, 0.7, apply=o.apply)
+    assert abs(loss - L) < 1e-5 * L
+    assert _rel(g, G) < 1e-4
+    ws.close()
+    S.close()
+
+
 def test_bf16_activations_close():
     w = _weights(5)
     b, xs = _vec(N, 4), _vec(N, 5)
@@ -123,7 +142,7 @@ def test_warmstart_solve_guard_and_tolerance():
     b, xref = data[0]
     ws = smg.WarmStart(N, smg.STORE_FP32, scale=1.0)
     ws.set_weights(np.zeros(smg.warmstart_num_weights(), dtype=np.float32))
-    # a zero network predicts x0 = 0: ||b - L x0|| = ||b|| is not a reduction, the guess is discarded
+    # a zero network predicts x0 = 0: tau_0 = ||M b|| is not a reduction, the guess is discarded
     x, info, used = ws.solve(S, b, tol=1e-8)
     assert not used and info.status == 0
     x_plain, info_plain = S.solve(b, tol=1e-8)
@@ -134,6 +153,10 @@ def test_warmstart_solve_guard_and_tolerance():
     x, info, used = ws.solve(S, b, tol=1e-8)
     assert info.status == 0 and info.rel_residual < 1e-8
     assert S.residual_norm(b, x) / float(b.norm()) < 1e-8
+    # a perfect guess (the method's own solution, here passed straight to SQMR) needs fewer iterations
+    x = xref.clone()
+    info_exact = smg.sqmr_solve(S.h, b, x, 1e-8, 200)
+    assert info_exact.iterations < info_plain.iterations
     ws.close()
     S.close()
 

@@ -116,3 +116,22 @@ def test_adam_first_step_moves_by_learning_rate():
     g = _r(50, 15)
     w1 = wo.adam(w.copy(), g, np.zeros(50), np.zeros(50), 1, 1e-2, eps=0.0)
     assert np.allclose(w - w1, 1e-2 * np.sign(g))
+
+
+def test_residual_form_gradient_matches_finite_differences():
+    import oracle
+    n = 16
+    o = oracle.Oracle(n, coarsest_max=8)
+    act, _ = o.masks()
+    w = synthetic.net_weights(2) * 0.5
+    b, xs = _problem(n, 20)
+    b[~act] = 0.0
+    xs[~act] = 0.0
+    L, g = wo.loss_and_grad(b, xs, w, n, 0.7, apply=o.apply)
+    assert abs(L - wo.loss(b, xs, w, n, 0.7, apply=o.apply)) < 1e-13 * L
+    rng = np.random.default_rng(21)
+    d = rng.standard_normal(w.size)
+    d /= np.linalg.norm(d)
+    eps = 1e-6
+    fd = (wo.loss(b, xs, w + eps * d, n, 0.7, apply=o.apply) - wo.loss(b, xs, w - eps * d, n, 0.7, apply=o.apply)) / (2 * eps)
+    assert abs(fd - g @ d) <= 1e-5 * np.linalg.norm(g)
