@@ -50,6 +50,11 @@ extern "C" {
  * solve always run in FP64) */
 #define STOKES_PREC_FP64 0
 #define STOKES_PREC_FP32 1
+/* FP32 V-cycle whose two finest levels (never the coarsest) store their right-hand side b, residual
+ * r and the pressure-sweep residual parts as BF16 (8 significant bits), read into FP32 arithmetic.
+ * The preconditioner is then symmetric only up to BF16 rounding; SQMR, the true-residual check and
+ * the tolerance are unchanged (FP64). */
+#define STOKES_PREC_MIXED_BF16 2
 
 typedef struct stokes_s *stokes_t;
 

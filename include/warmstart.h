@@ -73,10 +73,11 @@ int warmstart_loss_grad(warmstart_t ws, stokes_t h, const double *b, const doubl
 /* one Adam update (Kingma & Ba, Algorithm 1) of the weights from the handle's gradient buffer */
 int warmstart_adam_step(warmstart_t ws, double lr, double beta1, double beta2, double eps, void *stream);
 
-/* SQMR solve of stokes handle h from the network's guess: x <- network(b); SQMR's first quantity
- * tau_0 = ||M (b - L x)|| (Alg. 4, M = the V-cycle) is compared with its value for x0 = 0, ||M b||,
- * and a guess that does not lower it is discarded (x <- 0); then sqmr_solve(h, b, x, tol, max_iter,
- * info).  Costs one network evaluation, one operator apply and two V-cycles before the solve.
+/* SQMR solve of stokes handle h from the network's guess: x <- network(b); the guess is kept only
+ * if it lowers both the residual (||b - L x|| < ||b||) and SQMR's first quantity tau_0 =
+ * ||M (b - L x)|| (Alg. 4, M = the V-cycle) below its value for x0 = 0, ||M b||; otherwise x <- 0.
+ * Then sqmr_solve(h, b, x, tol, max_iter, info).  Costs one network evaluation, one operator apply
+ * and two V-cycles before the solve.
  * *used_guess (may be NULL) tells which start was taken.  h must be an n^3 problem on the same
  * device. */
 int warmstart_solve(warmstart_t ws, stokes_t h, const double *b, double *x, double tol, int max_iter,

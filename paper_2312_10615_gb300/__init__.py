@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libstokesmg.so")
 OK = 0
 ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_UNSUPPORTED = \
     -1, -2, -3, -4, -5, -6, -7, -8
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_MIXED_BF16 = 0, 1, 2
 
 # every entry point declared in include/stokesmg.h
 EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vector_length", "stokes_ghost_length",

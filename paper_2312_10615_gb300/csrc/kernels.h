@@ -9,22 +9,25 @@ namespace smg {
 
 // ---- per-level operators (kernels_level.cu) ----
 // y = L~x (gamma_on) or Lx on the unknowns, 0 elsewhere; if b != nullptr: y = b - (L~x)
-template <class T> void launch_apply(const Lev &L, const T *x, const T *b, T *y, double gam, cudaStream_t s);
+// T: arithmetic precision of a level kernel; TB: storage type of the level operands b, r, g/h
+// (T itself, or BF16 on the finest levels of the mixed-precision V-cycle)
+template <class T, class TB> void launch_apply(const Lev &L, const T *x, const TB *b, TB *y, double gam, cudaStream_t s);
 // b = f + Dirichlet folding (finest level, FP64)
 void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaStream_t s);
 // symmetric DGS pieces (Alg. 2 / Eq. ldist) on the V2 set
-template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s);
-template <class T> void launch_dgs_p_fwd(const Lev &L, T *x, const T *b, T *delta, int colour, cudaStream_t s);
+template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, int parity, cudaStream_t s);
+template <class T, class TB>
+void launch_dgs_p_fwd(const Lev &L, T *x, const TB *b, T *delta, int colour, cudaStream_t s);
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s);
 // backward pressure colours read g = b - Au (faces) and h = b - Bu (cells) precomputed into gh;
 // with delta != null the same launch applies the pending neighbour-pressure part of the forward
 // sweep (what launch_dgs_p_gather does)
-template <class T>
-void launch_dgs_p_bwd_prep(const Lev &L, T *x, const T *b, T *gh, const T *delta, cudaStream_t s);
-template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s);
+template <class T, class TB>
+void launch_dgs_p_bwd_prep(const Lev &L, T *x, const TB *b, TB *gh, const T *delta, cudaStream_t s);
+template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s);
 // one colour of the multiplicative Vanka sweep on V1 (compute corrections, then add them)
-template <class T>
-void launch_vanka_compute(const Lev &L, const T *x, const T *b, const int *cells, int ncell, const T *kinv, T *corr,
+template <class T, class TB>
+void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, int ncell, const T *kinv, T *corr,
                           int cap, cudaStream_t s);
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s);
@@ -40,12 +43,12 @@ struct VankaLists {
     const int *cells[8];
     int count[8];
 };
-template <class T>
-void launch_vanka_sweep(const Lev &L, T *x, const T *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
+template <class T, class TB>
+void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
                         int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s);
 template <class T> int vanka_sweep_blocks_per_sm();
 // transfers (Sec. 2): bc = R rf,  xf += P ec
-template <class T> void launch_restrict(const Lev &F, const Lev &C, const T *rf, T *bc, cudaStream_t s);
+template <class T, class TF, class TC> void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s);
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s);
 // coarsest level: x = Kinv b over the compact unknown list (FP64 matrix)
 template <class T>

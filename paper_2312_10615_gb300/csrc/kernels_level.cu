@@ -97,20 +97,21 @@ __device__ __forceinline__ bool entry_eval(const T *__restrict__ x, const Lev &L
 }
 inline dim3 entry_grid(const Lev &L) { return dim3(cdiv(L.nx + 1, BX), cdiv(L.ny + 1, BY), 4 * (L.nz + 1)); }
 
-template <class T>
-__global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x, const T *__restrict__ b,
-                                                  T *__restrict__ y, Coef<T> K) {
+template <class T, class TB>
+__global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
+                                                  TB *__restrict__ y, Coef<T> K) {
     pdl_wait();
     int c = blockIdx.z & 3, k = blockIdx.z >> 2;
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     long long q;
     T v;
     if (!entry_eval<T, OP_APPLY>(x, L, c, i, j, k, K, q, v)) return;
-    y[q] = active(L, c, i, j, k) ? (b ? b[q] - v : v) : T(0);
+    y[q] = cvt<TB>(active(L, c, i, j, k) ? (b ? T(ldv(b[q])) - v : v) : T(0));
 }
 
-template <class T> void launch_apply(const Lev &L, const T *x, const T *b, T *y, double gam, cudaStream_t s) {
-    launch_k(k_apply<T>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+template <class T, class TB>
+void launch_apply(const Lev &L, const T *x, const TB *b, TB *y, double gam, cudaStream_t s) {
+    launch_k(k_apply<T, TB>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -166,16 +167,16 @@ void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaS
 // Cell-centric: the thread of V2 cell (i,j,k) of the given parity updates its low faces u, v, w (all
 // three share the cell's parity), each if it lies in that component's V2 range.  Inside the V2
 // cell range every stencil neighbour exists, so no guards are needed.
-template <class T>
-__device__ __forceinline__ void dgs_face(T *__restrict__ x, const T *__restrict__ b, long long q, long long sy,
+template <class T, class TB>
+__device__ __forceinline__ void dgs_face(T *__restrict__ x, const TB *__restrict__ b, long long q, long long sy,
                                          long long sz, T pc, T pm, const Coef<T> &K) {
     T s = T(6) * x[q] - x[q - 1] - x[q + 1] - x[q - sy] - x[q + sy] - x[q - sz] - x[q + sz];
-    T r = b[q] - (K.eh2 * s + K.ih * (pc - pm));
+    T r = T(ldv(b[q])) - (K.eh2 * s + K.ih * (pc - pm));
     x[q] += r / (T(6) * K.eh2);
 }
 
-template <class T>
-__global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, const T *__restrict__ b, int parity,
+template <class T, class TB>
+__global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, const TB *__restrict__ b, int parity,
                                                   Coef<T> K) {
     pdl_wait();
     const int nx = L.nx, ny = L.ny, nz = L.nz;
@@ -196,10 +197,10 @@ __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, cons
     }
 }
 
-template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity, cudaStream_t s) {
+template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, int parity, cudaStream_t s) {
     if (L.nx < 3 || L.ny < 3 || L.nz < 3) return;
     dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), L.nz - 2);
-    launch_k(k_dgs_u<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
+    launch_k(k_dgs_u<T, TB>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
 }
 
 // Alg. 2 pressure block, one colour (i mod 2, j mod 2, k mod 2):
@@ -209,8 +210,8 @@ template <class T> void launch_dgs_u(const Lev &L, T *x, const T *b, int parity,
 // The neighbour-pressure part is applied in gather form: a cell first collects the deltas of
 // neighbours whose colour came earlier in this sweep (pre-gather); k_dgs_p_gather applies the rest
 // after the last colour.  delta is stored per cell and stays 0 outside V2.
-template <class T>
-__global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const T *__restrict__ b,
+template <class T, class TB>
+__global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                    T *__restrict__ delta, int colour, Coef<T> K, T dP) {
     pdl_wait();
     int lo[3], cnt[3];
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, con
     long long u0 = pidx(L, 0, i, j, k), v0 = pidx(L, 1, i, j, k), w0 = pidx(L, 2, i, j, k);
     long long vs = L.nx, ws = (long long)L.nx * L.ny;
     T div = (x[u0 + 1] - x[u0]) + (x[v0 + vs] - x[v0]) + (x[w0 + ws] - x[w0]);
-    T r = b[qp] + K.ih * div + K.gam * p;
+    T r = T(ldv(b[qp])) + K.ih * div + K.gam * p;
     T dl = r / dP;
     T fd = dl * K.ih;
     x[u0] -= fd;
@@ -276,9 +277,9 @@ __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, 
 // (M_{.c}^T r with the full column of M).  Same-colour cells read none of each other's values.
 // The same launch also finishes the forward sweep: the neighbour-pressure part of the last
 // colours (gather form of k_dgs_p_gather), which the prep never reads.  One entry per thread as k_apply.
-template <class T>
-__global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const T *__restrict__ b,
-                                                           T *__restrict__ gh, const T *__restrict__ delta,
+template <class T, class TB>
+__global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const TB *__restrict__ b,
+                                                           TB *__restrict__ gh, const T *__restrict__ delta,
                                                            Coef<T> K) {
     pdl_wait();
     int c = blockIdx.z & 3, k = blockIdx.z >> 2;
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict_
     long long q;
     T v;
     if (!entry_eval<T, OP_A_B>(x, L, c, i, j, k, K, q, v)) return;
-    gh[q] = active(L, c, i, j, k) ? b[q] - v : T(0);
+    gh[q] = cvt<TB>(active(L, c, i, j, k) ? T(ldv(b[q])) - v : T(0));
     if (c == 3 && delta) {
         long long t = cell_lin(L, i, j, k);
         bool v2 = in_v2_cell(L, i, j, k);
@@ -300,8 +301,8 @@ __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict_
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const T *__restrict__ gh, int colour,
+template <class T, class TB>
+__global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const TB *__restrict__ ghs, int colour,
                                                    Coef<T> K, T dP) {
     pdl_wait();
     int lo[3], cnt[3];
@@ -314,16 +315,17 @@ __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, con
     const T *p = x;
     T pc = p[qc], pxm = p[qc - 1], pxp = p[qc + 1], pym = p[qc - sy], pyp = p[qc + sy], pzm = p[qc - sz],
       pzp = p[qc + sz];
+    auto gh = [&](long long q) { return T(ldv(ghs[q])); };
     long long u0 = pidx(L, 0, i, j, k), v0 = pidx(L, 1, i, j, k), w0 = pidx(L, 2, i, j, k);
     long long vs = L.nx, ws = (long long)L.nx * L.ny;
     // face residuals r_f = g_f - (p_plus - p_minus)/h
-    T rul = gh[u0] - K.ih * (pc - pxm), ruh = gh[u0 + 1] - K.ih * (pxp - pc);
-    T rvl = gh[v0] - K.ih * (pc - pym), rvh = gh[v0 + vs] - K.ih * (pyp - pc);
-    T rwl = gh[w0] - K.ih * (pc - pzm), rwh = gh[w0 + ws] - K.ih * (pzp - pc);
+    T rul = gh(u0) - K.ih * (pc - pxm), ruh = gh(u0 + 1) - K.ih * (pxp - pc);
+    T rvl = gh(v0) - K.ih * (pc - pym), rvh = gh(v0 + vs) - K.ih * (pyp - pc);
+    T rwl = gh(w0) - K.ih * (pc - pzm), rwh = gh(w0 + ws) - K.ih * (pzp - pc);
     // cell residuals r_n = h_n + gamma p_n
-    T rc = gh[qc] + K.gam * pc;
-    T rn = (gh[qc - 1] + K.gam * pxm) + (gh[qc + 1] + K.gam * pxp) + (gh[qc - sy] + K.gam * pym) +
-           (gh[qc + sy] + K.gam * pyp) + (gh[qc - sz] + K.gam * pzm) + (gh[qc + sz] + K.gam * pzp);
+    T rc = gh(qc) + K.gam * pc;
+    T rn = (gh(qc - 1) + K.gam * pxm) + (gh(qc + 1) + K.gam * pxp) + (gh(qc - sy) + K.gam * pym) +
+           (gh(qc + sy) + K.gam * pyp) + (gh(qc - sz) + K.gam * pzm) + (gh(qc + sz) + K.gam * pzp);
     T s = K.ih * ((ruh - rul) + (rvh - rvl) + (rwh - rwl)) + K.eh2 * (T(6) * rc - rn);
     x[qc] = pc + s / dP;
 }
@@ -332,27 +334,28 @@ template <class T> static T dgs_pressure_diag(const Lev &L) {
     return T(-6.0 * (1.0 + L.gamma * L.eta) / (L.h * L.h));
 }
 
-template <class T> void launch_dgs_p_fwd(const Lev &L, T *x, const T *b, T *delta, int colour, cudaStream_t s) {
+template <class T, class TB>
+void launch_dgs_p_fwd(const Lev &L, T *x, const TB *b, T *delta, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
     dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
-    launch_k(k_dgs_p_fwd<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
+    launch_k(k_dgs_p_fwd<T, TB>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
 }
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s) {
     dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz);
     launch_k(k_dgs_p_gather<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, delta, coef<T>(L, L.gamma));
 }
-template <class T>
-void launch_dgs_p_bwd_prep(const Lev &L, T *x, const T *b, T *gh, const T *delta, cudaStream_t s) {
-    launch_k(k_dgs_p_bwd_prep<T>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta, coef<T>(L, L.gamma));
+template <class T, class TB>
+void launch_dgs_p_bwd_prep(const Lev &L, T *x, const TB *b, TB *gh, const T *delta, cudaStream_t s) {
+    launch_k(k_dgs_p_bwd_prep<T, TB>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta, coef<T>(L, L.gamma));
 }
-template <class T> void launch_dgs_p_bwd(const Lev &L, T *x, const T *gh, int colour, cudaStream_t s) {
+template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
     dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
-    launch_k(k_dgs_p_bwd<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
+    launch_k(k_dgs_p_bwd<T, TB>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -369,8 +372,8 @@ __device__ __forceinline__ void unpack_cell(int w, int &i, int &j, int &k) {
 
 // 8 lanes per cell: lane a < 6 owns face a of the patch, lane 6 the pressure, lane 7 idles; the
 // 7 residuals are exchanged with width-8 shuffles and lane a forms row a of K^{-1} r.
-template <class T>
-__global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const T *__restrict__ b,
+template <class T, class TB>
+__global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                        const int *__restrict__ cells, int ncell,
                                                        const T *__restrict__ kinv, T *__restrict__ corr, int cap,
                                                        Coef<T> K) {
@@ -387,9 +390,9 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
     if (a < 6) {
         int d = a >> 1, side = a & 1;
         int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-        if ((cfg >> a) & 1) r = b[pidx(L, d, fi, fj, fk)] - face_Lx_any(x, L, d, fi, fj, fk, K);
+        if ((cfg >> a) & 1) r = T(ldv(b[pidx(L, d, fi, fj, fk)])) - face_Lx_any(x, L, d, fi, fj, fk, K);
     } else if (a == 6) {
-        r = b[pidx(L, 3, i, j, k)] - cell_Lx_fast(x, L, i, j, k, K);
+        r = T(ldv(b[pidx(L, 3, i, j, k)])) - cell_Lx_fast(x, L, i, j, k, K);
     }
     const T *Ki = kinv + cfg * 49 + (a < 7 ? a : 6) * 7;
     T s = T(0);
@@ -416,11 +419,11 @@ __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, c
     if (active(L, d, fi, fj, fk)) x[pidx(L, d, fi, fj, fk)] += corr[(long long)a * cap + slot];
 }
 
-template <class T>
-void launch_vanka_compute(const Lev &L, const T *x, const T *b, const int *cells, int ncell, const T *kinv, T *corr,
+template <class T, class TB>
+void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, int ncell, const T *kinv, T *corr,
                           int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    launch_k(k_vanka_compute<T>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, ncell, kinv, corr, cap,
+    launch_k(k_vanka_compute<T, TB>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, ncell, kinv, corr, cap,
                                                                coef<T>(L, L.gamma));
 }
 template <class T>
@@ -459,8 +462,8 @@ __device__ __forceinline__ void grid_sync(GridBarrier *bar, unsigned nblocks) {
     __syncthreads();
 }
 
-template <class T>
-__device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const T *__restrict__ b,
+template <class T, class TB>
+__device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
                                                    int cellw, int a, unsigned gmask, const T *__restrict__ kinv,
                                                    T *__restrict__ corr, int cap, int slot, const Coef<T> &K) {
     int i, j, k;
@@ -471,9 +474,9 @@ __device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__rest
     if (a < 6) {
         int d = a >> 1, side = a & 1;
         int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-        if ((cfg >> a) & 1) r = b[pidx(L, d, fi, fj, fk)] - face_Lx_any(x, L, d, fi, fj, fk, K);
+        if ((cfg >> a) & 1) r = T(ldv(b[pidx(L, d, fi, fj, fk)])) - face_Lx_any(x, L, d, fi, fj, fk, K);
     } else if (a == 6) {
-        r = b[pidx(L, 3, i, j, k)] - cell_Lx_fast(x, L, i, j, k, K);
+        r = T(ldv(b[pidx(L, 3, i, j, k)])) - cell_Lx_fast(x, L, i, j, k, K);
     }
     const T *Ki = kinv + cfg * 49 + (a < 7 ? a : 6) * 7;
     T s = T(0);
@@ -497,8 +500,8 @@ __device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x
     if (active(L, d, fi, fj, fk)) x[pidx(L, d, fi, fj, fk)] += corr[(long long)a * cap + slot];
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, const T *__restrict__ b,
+template <class T, class TB>
+__global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                      VankaLists lists, const T *__restrict__ kinv,
                                                      T *__restrict__ corr, int cap, Coef<T> K, int sweeps,
                                                      GridBarrier *bar) {
@@ -523,12 +526,12 @@ __global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, c
 
 template <class T> int vanka_sweep_blocks_per_sm() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vanka_sweep<T>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vanka_sweep<T, T>, 256, 0);
     return nb;
 }
 
-template <class T>
-void launch_vanka_sweep(const Lev &L, T *x, const T *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
+template <class T, class TB>
+void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
                         int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s) {
     int mx = 0;
     for (int c = 0; c < 8; ++c) mx = lists.count[c] > mx ? lists.count[c] : mx;
@@ -545,7 +548,7 @@ void launch_vanka_sweep(const Lev &L, T *x, const T *b, const VankaLists &lists,
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_vanka_sweep<T>, L, x, b, lists, kinv, corr, cap, coef<T>(L, L.gamma), sweeps, bar);
+    cudaLaunchKernelEx(&cfg, k_vanka_sweep<T, TB>, L, x, b, lists, kinv, corr, cap, coef<T>(L, L.gamma), sweeps, bar);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -556,12 +559,12 @@ void launch_vanka_sweep(const Lev &L, T *x, const T *b, const VankaLists &lists,
 // component C of the face transfers, with every index known at compile time; offsets are strides
 // from one base address.  Along the normal axis every referenced fine/coarse face lies inside the
 // array (walls hold 0); along a tangential axis the rows outside the box are skipped.
-template <class T, int C>
-__device__ __forceinline__ T restrict_face(const Lev &F, const Lev &Cl, const T *__restrict__ rf, int I, int J,
+template <class T, int C, class TF>
+__device__ __forceinline__ T restrict_face(const Lev &F, const Lev &Cl, const TF *__restrict__ rf, int I, int J,
                                            int Kk) {
     const long long sy = F.nx + (C == 0), sz = sy * (F.ny + (C == 1));
     const long long st[3] = {1, sy, sz};
-    const T *fb = rf + comp_base(F, C) + 2 * I + sy * (2 * J) + sz * (2LL * Kk);
+    const TF *fb = rf + comp_base(F, C) + 2 * I + sy * (2 * J) + sz * (2LL * Kk);
     const int t1 = C == 0 ? 1 : 0, t2 = C == 2 ? 1 : 2;  // tangential axes
     const int T1 = t1 == 0 ? I : (t1 == 1 ? J : Kk), T2 = t2 == 1 ? J : Kk;
     const int n1 = t1 == 0 ? Cl.nx : (t1 == 1 ? Cl.ny : Cl.nz), n2 = t2 == 1 ? Cl.ny : Cl.nz;
@@ -574,40 +577,40 @@ __device__ __forceinline__ T restrict_face(const Lev &F, const Lev &Cl, const T 
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             if ((g == 0 && T2 == 0) || (g == 3 && T2 == n2 - 1)) continue;
-            const T *row = fb + (bb - 1) * st[t1] + (g - 1) * st[t2];
-            T sn = nw[0] * row[-st[C]] + nw[1] * row[0] + nw[2] * row[st[C]];
+            const TF *row = fb + (bb - 1) * st[t1] + (g - 1) * st[t2];
+            T sn = nw[0] * T(ldv(row[-st[C]])) + nw[1] * T(ldv(row[0])) + nw[2] * T(ldv(row[st[C]]));
             s += tw[bb] * tw[g] * sn;
         }
     }
     return s * T(0.125);
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const T *__restrict__ rf,
-                                                  T *__restrict__ bc) {
+template <class T, class TF, class TC>
+__global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const TF *__restrict__ rf,
+                                                  TC *__restrict__ bc) {
     pdl_wait();
     int c, I, J, k0, k1;
     if (!thread_entry(C, gy, c, I, J, k0, k1)) return;
     for (int Kk = k0; Kk < k1; ++Kk) {
     long long q = pidx(C, c, I, J, Kk);
     if (!active(C, c, I, J, Kk)) {
-        bc[q] = T(0);
+        bc[q] = cvt<TC>(T(0));
         continue;
     }
     T v;
     switch (c) {
-    case 0: v = restrict_face<T, 0>(F, C, rf, I, J, Kk); break;
-    case 1: v = restrict_face<T, 1>(F, C, rf, I, J, Kk); break;
-    case 2: v = restrict_face<T, 2>(F, C, rf, I, J, Kk); break;
+    case 0: v = restrict_face<T, 0, TF>(F, C, rf, I, J, Kk); break;
+    case 1: v = restrict_face<T, 1, TF>(F, C, rf, I, J, Kk); break;
+    case 2: v = restrict_face<T, 2, TF>(F, C, rf, I, J, Kk); break;
     default: {
         T s = T(0);
 #pragma unroll
         for (int m = 0; m < 8; ++m)
-            s += rf[pidx(F, 3, 2 * I + (m & 1), 2 * J + ((m >> 1) & 1), 2 * Kk + ((m >> 2) & 1))];
+            s += T(ldv(rf[pidx(F, 3, 2 * I + (m & 1), 2 * J + ((m >> 1) & 1), 2 * Kk + ((m >> 2) & 1))]));
         v = s * T(0.125);
     }
     }
-    bc[q] = v;
+    bc[q] = cvt<TC>(v);
     }
 }
 
@@ -681,9 +684,10 @@ __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, const T *__restr
     }
 }
 
-template <class T> void launch_restrict(const Lev &F, const Lev &C, const T *rf, T *bc, cudaStream_t s) {
+template <class T, class TF, class TC>
+void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s) {
     Geo g = geo_components(C, 4);
-    launch_k(k_restrict<T>, dim3(g.grid), dim3(kBlock3), 0, s, F, C, g.gy, rf, bc);
+    launch_k(k_restrict<T, TF, TC>, dim3(g.grid), dim3(kBlock3), 0, s, F, C, g.gy, rf, bc);
 }
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s) {
     dim3 grid(cdiv(C.nx, BX), cdiv(C.ny, BY), cdiv(C.nz, KZ));
@@ -724,7 +728,7 @@ template <class T> __global__ void __launch_bounds__(256) k_mask(Lev L, int gy, 
     int c, i, j, k0, k1;
     if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
     for (int k = k0; k < k1; ++k)
-        if (!active(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = T(0);
+        if (!active(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = cvt<T>(0.0f);
 }
 template <class T> void launch_mask(const Lev &L, T *x, cudaStream_t s) {
     Geo g = geo_components(L, 4);
@@ -732,38 +736,48 @@ template <class T> void launch_mask(const Lev &L, T *x, cudaStream_t s) {
 }
 template void launch_mask<float>(const Lev &, float *, cudaStream_t);
 template void launch_mask<double>(const Lev &, double *, cudaStream_t);
+template void launch_mask<bf16>(const Lev &, bf16 *, cudaStream_t);
 
 template <class A, class B> __global__ void k_convert(long long n, const A *__restrict__ in, B *__restrict__ out) {
     pdl_wait();
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-        out[t] = (B)in[t];
+        out[t] = cvt<B>(in[t]);
 }
 template <class A, class B> void launch_convert(long long n, const A *in, B *out, cudaStream_t s) {
     long long nb = (n + 255) / 256;
     launch_k(k_convert<A, B>, dim3((unsigned)(nb < 4736 ? nb : 4736)), dim3(256), 0, s, n, in, out);
 }
 
-// explicit instantiations
+// explicit instantiations: T the arithmetic precision, TB the storage of the level operands
+// (right-hand side, residual, pressure-sweep residual parts)
+#define SMG_INST_TB(T, TB)                                                                                          \
+    template void launch_apply<T, TB>(const Lev &, const T *, const TB *, TB *, double, cudaStream_t);             \
+    template void launch_dgs_u<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                           \
+    template void launch_dgs_p_fwd<T, TB>(const Lev &, T *, const TB *, T *, int, cudaStream_t);                  \
+    template void launch_dgs_p_bwd_prep<T, TB>(const Lev &, T *, const TB *, TB *, const T *, cudaStream_t);      \
+    template void launch_dgs_p_bwd<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                       \
+    template void launch_vanka_compute<T, TB>(const Lev &, const T *, const TB *, const int *, int, const T *, T *,  \
+                                              int, cudaStream_t);                                                   \
+    template void launch_vanka_sweep<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, T *, int,  \
+                                            int, GridBarrier *, int, cudaStream_t);
 #define SMG_INST(T)                                                                                               \
-    template void launch_apply<T>(const Lev &, const T *, const T *, T *, double, cudaStream_t);                  \
-    template void launch_dgs_u<T>(const Lev &, T *, const T *, int, cudaStream_t);                                \
-    template void launch_dgs_p_fwd<T>(const Lev &, T *, const T *, T *, int, cudaStream_t);                       \
+    SMG_INST_TB(T, T)                                                                                             \
     template void launch_dgs_p_gather<T>(const Lev &, T *, const T *, cudaStream_t);                              \
-    template void launch_dgs_p_bwd_prep<T>(const Lev &, T *, const T *, T *, const T *, cudaStream_t);            \
-    template void launch_dgs_p_bwd<T>(const Lev &, T *, const T *, int, cudaStream_t);                            \
-    template void launch_vanka_compute<T>(const Lev &, const T *, const T *, const int *, int, const T *, T *, int, \
-                                          cudaStream_t);                                                          \
     template void launch_vanka_apply<T>(const Lev &, T *, const int *, int, const T *, int, cudaStream_t);        \
-    template void launch_restrict<T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);                     \
+    template void launch_restrict<T, T, T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);               \
     template void launch_prolong<T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);                      \
     template void launch_coarse<T>(const Lev &, const int *, int, const double *, const T *, T *, cudaStream_t);   \
-    template void launch_vanka_sweep<T>(const Lev &, T *, const T *, const VankaLists &, const T *, T *, int, int,  \
-                                        GridBarrier *, int, cudaStream_t);                                         \
     template int vanka_sweep_blocks_per_sm<T>();
 SMG_INST(float)
 SMG_INST(double)
+SMG_INST_TB(float, bf16)
+template void launch_restrict<float, bf16, bf16>(const Lev &, const Lev &, const bf16 *, bf16 *, cudaStream_t);
+template void launch_restrict<float, bf16, float>(const Lev &, const Lev &, const bf16 *, float *, cudaStream_t);
+template void launch_restrict<float, float, bf16>(const Lev &, const Lev &, const float *, bf16 *, cudaStream_t);
 template void launch_convert<double, float>(long long, const double *, float *, cudaStream_t);
 template void launch_convert<float, double>(long long, const float *, double *, cudaStream_t);
 template void launch_convert<double, double>(long long, const double *, double *, cudaStream_t);
+template void launch_convert<double, bf16>(long long, const double *, bf16 *, cudaStream_t);
+template void launch_convert<bf16, double>(long long, const bf16 *, double *, cudaStream_t);
 
 }  // namespace smg

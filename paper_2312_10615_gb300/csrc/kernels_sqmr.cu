@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) k_update_s(long long n, double *__restric
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         double v = s[t] - alpha * w[t];
         s[t] = v;
-        if (bT) bT[t] = (T)v;
+        if (bT) bT[t] = cvt<T>(v);
     }
 }
 template <class T>
@@ -279,6 +279,7 @@ template void launch_dot2<float>(long long, const float *, const double *, doubl
 template void launch_dot2<double>(long long, const double *, const double *, double *, cudaStream_t);
 template void launch_update_s<float>(long long, double *, const double *, const SqmrState *, float *, cudaStream_t);
 template void launch_update_s<double>(long long, double *, const double *, const SqmrState *, double *, cudaStream_t);
+template void launch_update_s<bf16>(long long, double *, const double *, const SqmrState *, bf16 *, cudaStream_t);
 template void launch_update_x<float>(long long, double *, double *, double *, const float *, double *,
                                      const double *, const SqmrState *, double *, cudaStream_t);
 template void launch_update_x<double>(long long, double *, double *, double *, const double *, double *,

@@ -17,8 +17,10 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <algorithm>
 #include <thread>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.h"
@@ -161,6 +163,7 @@ struct stokes_s {
     int use_graphs = 1;
     int vanka_persistent = 1;
     int vanka_max_blocks = 0;  // co-resident blocks of the cooperative Vanka sweep
+    int nbf = 0;               // finest levels whose b, r are stored as BF16 (STOKES_PREC_MIXED_BF16)
     GridBarrier *bar = nullptr;
     double eta = 1.0, gamma = 1e-3;
     std::vector<LevelBuf> lev;
@@ -220,73 +223,95 @@ template <class F> inline void prof(int kind, int level, cudaStream_t s, F f) {
 }
 
 // ---- the V-cycle schedule (Alg. 1 with the Alg. 3 smoother) ----
-template <class T> void vanka_colour(stokes_s *h, int l, int col, cudaStream_t s) {
+// T: arithmetic precision of the V-cycle; TB: storage of level l's b and r (T, or BF16 on the
+// finest levels of the mixed-precision V-cycle); with_tb calls f(T(), TB()) for level l
+template <class T, class F> void with_tb(const stokes_s *h, int l, F &&f) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (l < h->nbf) {
+            f(float(), bf16());
+            return;
+        }
+    }
+    f(T(), T());
+}
+
+template <class T, class TB> void vanka_colour(stokes_s *h, int l, int col, cudaStream_t s) {
     LevelBuf &B = h->lev[l];
     if (B.vcount[col] == 0) return;
     prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
-        launch_vanka_compute<T>(B.L, (const T *)B.x, (const T *)B.b, B.vcells[col], B.vcount[col],
-                                (const T *)B.kinv, (T *)B.corr, B.vcap, s);
+        launch_vanka_compute<T, TB>(B.L, (const T *)B.x, (const TB *)B.b, B.vcells[col], B.vcount[col],
+                                    (const T *)B.kinv, (T *)B.corr, B.vcap, s);
     });
     prof(STOKES_K_VANKA_APPLY, l, s,
          [&] { launch_vanka_apply<T>(B.L, (T *)B.x, B.vcells[col], B.vcount[col], (const T *)B.corr, B.vcap, s); });
 }
 // `sweeps` symmetric Vanka sweeps (App. C: colours 0..7 then 7..0)
-template <class T> void vanka_sym(stokes_s *h, int l, cudaStream_t s, int sweeps = 1) {
+template <class T, class TB> void vanka_sym(stokes_s *h, int l, cudaStream_t s, int sweeps = 1) {
     LevelBuf &B = h->lev[l];
     if (h->vanka_persistent) {
         prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
-            launch_vanka_sweep<T>(B.L, (T *)B.x, (const T *)B.b, B.lists, (const T *)B.kinv, (T *)B.corr, B.vcap, sweeps,
-                                  h->bar, h->vanka_max_blocks, s);
+            launch_vanka_sweep<T, TB>(B.L, (T *)B.x, (const TB *)B.b, B.lists, (const T *)B.kinv, (T *)B.corr, B.vcap,
+                                      sweeps, h->bar, h->vanka_max_blocks, s);
         });
         return;
     }
     for (int k = 0; k < sweeps; ++k) {
-        for (int c = 0; c < 8; ++c) vanka_colour<T>(h, l, c, s);
-        for (int c = 7; c >= 0; --c) vanka_colour<T>(h, l, c, s);
+        for (int c = 0; c < 8; ++c) vanka_colour<T, TB>(h, l, c, s);
+        for (int c = 7; c >= 0; --c) vanka_colour<T, TB>(h, l, c, s);
     }
 }
-template <class T> void dgs_forward(stokes_s *h, int l, cudaStream_t s) {
+template <class T, class TB> void dgs_forward(stokes_s *h, int l, cudaStream_t s) {
     LevelBuf &B = h->lev[l];
     T *x = (T *)B.x;
-    const T *b = (const T *)B.b;
-    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 0, s); });
-    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 1, s); });
+    const TB *b = (const TB *)B.b;
+    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
+    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
     for (int c = 0; c < 8; ++c)
-        prof(STOKES_K_DGS_P_FWD, l, s, [&] { launch_dgs_p_fwd<T>(B.L, x, b, (T *)B.delta, c, s); });
+        prof(STOKES_K_DGS_P_FWD, l, s, [&] { launch_dgs_p_fwd<T, TB>(B.L, x, b, (T *)B.delta, c, s); });
 }
 // the forward sweep's pending neighbour-pressure part is applied by the first launch after it
 template <class T> void dgs_finish_forward(stokes_s *h, int l, cudaStream_t s) {
     LevelBuf &B = h->lev[l];
     prof(STOKES_K_DGS_P_GATHER, l, s, [&] { launch_dgs_p_gather<T>(B.L, (T *)B.x, (const T *)B.delta, s); });
 }
-template <class T> void dgs_backward(stokes_s *h, int l, cudaStream_t s, bool forward_pending) {
+template <class T, class TB> void dgs_backward(stokes_s *h, int l, cudaStream_t s, bool forward_pending) {
     LevelBuf &B = h->lev[l];
     T *x = (T *)B.x;
-    const T *b = (const T *)B.b;
+    const TB *b = (const TB *)B.b;
     prof(STOKES_K_DGS_P_BWD_PREP, l, s, [&] {
-        launch_dgs_p_bwd_prep<T>(B.L, x, b, (T *)B.r, forward_pending ? (const T *)B.delta : nullptr, s);
+        launch_dgs_p_bwd_prep<T, TB>(B.L, x, b, (TB *)B.r, forward_pending ? (const T *)B.delta : nullptr, s);
     });
     for (int c = 7; c >= 0; --c)
-        prof(STOKES_K_DGS_P_BWD, l, s, [&] { launch_dgs_p_bwd<T>(B.L, x, (const T *)B.r, c, s); });
-    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 1, s); });
-    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T>(B.L, x, b, 0, s); });
+        prof(STOKES_K_DGS_P_BWD, l, s, [&] { launch_dgs_p_bwd<T, TB>(B.L, x, (const TB *)B.r, c, s); });
+    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
+    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
 }
-template <class T> void smooth(stokes_s *h, int l, cudaStream_t s) {
-    vanka_sym<T>(h, l, s, h->kb);
-    dgs_forward<T>(h, l, s);
-    dgs_backward<T>(h, l, s, true);
-    vanka_sym<T>(h, l, s, h->kb);
+template <class T, class TB> void smooth(stokes_s *h, int l, cudaStream_t s) {
+    vanka_sym<T, TB>(h, l, s, h->kb);
+    dgs_forward<T, TB>(h, l, s);
+    dgs_backward<T, TB>(h, l, s, true);
+    vanka_sym<T, TB>(h, l, s, h->kb);
+}
+template <class T> void smooth_level(stokes_s *h, int l, cudaStream_t s) {
+    with_tb<T>(h, l, [&](auto t, auto tb) { smooth<decltype(t), decltype(tb)>(h, l, s); });
 }
 template <class T> void vcycle(stokes_s *h, cudaStream_t s) {
     int n = h->nlev();
     for (int l = 0; l < n - 1; ++l) {
         LevelBuf &B = h->lev[l];
         prof(STOKES_K_MEMSET, l, s, [&] { cudaMemsetAsync(B.x, 0, sizeof(T) * B.L.n, s); });
-        smooth<T>(h, l, s);
-        prof(STOKES_K_RESIDUAL, l, s,
-             [&] { launch_apply<T>(B.L, (const T *)B.x, (const T *)B.b, (T *)B.r, B.L.gamma, s); });
-        prof(STOKES_K_RESTRICT, l, s,
-             [&] { launch_restrict<T>(B.L, h->lev[l + 1].L, (const T *)B.r, (T *)h->lev[l + 1].b, s); });
+        smooth_level<T>(h, l, s);
+        with_tb<T>(h, l, [&](auto t, auto tf) {
+            using TT = decltype(t);
+            using TF = decltype(tf);
+            prof(STOKES_K_RESIDUAL, l, s,
+                 [&] { launch_apply<TT, TF>(B.L, (const TT *)B.x, (const TF *)B.b, (TF *)B.r, B.L.gamma, s); });
+            with_tb<T>(h, l + 1, [&](auto, auto tc) {
+                using TC = decltype(tc);
+                prof(STOKES_K_RESTRICT, l, s,
+                     [&] { launch_restrict<TT, TF, TC>(B.L, h->lev[l + 1].L, (const TF *)B.r, (TC *)h->lev[l + 1].b, s); });
+            });
+        });
     }
     LevelBuf &C = h->lev[n - 1];
     prof(STOKES_K_COARSE, n - 1, s,
@@ -295,7 +320,7 @@ template <class T> void vcycle(stokes_s *h, cudaStream_t s) {
         LevelBuf &B = h->lev[l];
         prof(STOKES_K_PROLONG, l, s,
              [&] { launch_prolong<T>(B.L, h->lev[l + 1].L, (const T *)h->lev[l + 1].x, (T *)B.x, s); });
-        smooth<T>(h, l, s);
+        smooth_level<T>(h, l, s);
     }
 }
 void vcycle_any(stokes_s *h, cudaStream_t s) {
@@ -313,8 +338,11 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s) {
     prof(STOKES_K_APPLY_DOT, 0, s, [&] { launch_apply_dot(L, h->q, h->w, h->partials, s); });
     prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(0, h->partials, np, h->st, h->hout, s); });
     // s_j = s_{j-1} - alpha t
-    prof(STOKES_K_UPDATE_S, 0, s, [&] {
-        launch_update_s<T>(n, h->s, h->w, h->st, h->prec == STOKES_PREC_FP64 ? nullptr : (T *)h->lev[0].b, s);
+    with_tb<T>(h, 0, [&](auto, auto tb) {
+        using TB = decltype(tb);
+        prof(STOKES_K_UPDATE_S, 0, s, [&] {
+            launch_update_s<TB>(n, h->s, h->w, h->st, h->prec == STOKES_PREC_FP64 ? nullptr : (TB *)h->lev[0].b, s);
+        });
     });
     vcycle<T>(h, s);  // t <- V-cycle(L~, s_j, 0, n)
     // |t|^2, rho_j = s_j^T t ; nu, c, tau, beta
@@ -392,9 +420,13 @@ int ensure_stage(stokes_s *h) {
 
 // level vector in/out (FP64 caller layout <-> precision T of the level buffers); entries off the
 // unknowns are zeroed on the way in
-int to_level(stokes_s *h, const Lev &L, const double *src_dev, void *dst, cudaStream_t s) {
+// bf: the destination is a BF16 operand buffer (b or r of a level below h->nbf)
+int to_level(stokes_s *h, const Lev &L, const double *src_dev, void *dst, cudaStream_t s, bool bf = false) {
     long long n = L.n;
-    if (h->prec == STOKES_PREC_FP64) {
+    if (bf) {
+        launch_convert<double, bf16>(n, src_dev, (bf16 *)dst, s);
+        launch_mask<bf16>(L, (bf16 *)dst, s);
+    } else if (h->prec == STOKES_PREC_FP64) {
         CK(cudaMemcpyAsync(dst, src_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         launch_mask<double>(L, (double *)dst, s);
     } else {
@@ -412,8 +444,9 @@ int stage_masked(stokes_s *h, const double *p, double *dst, cudaStream_t s) {
     CKLAUNCH();
     return 0;
 }
-int from_level(stokes_s *h, const void *src, double *dst_dev, long long n, cudaStream_t s) {
-    if (h->prec == STOKES_PREC_FP64) CK(cudaMemcpyAsync(dst_dev, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+int from_level(stokes_s *h, const void *src, double *dst_dev, long long n, cudaStream_t s, bool bf = false) {
+    if (bf) launch_convert<bf16, double>(n, (const bf16 *)src, dst_dev, s);
+    else if (h->prec == STOKES_PREC_FP64) CK(cudaMemcpyAsync(dst_dev, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     else launch_convert<float, double>(n, (const float *)src, dst_dev, s);
     CKLAUNCH();
     return 0;
@@ -475,7 +508,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     stokes_opts_t o;
     stokes_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.gamma >= 0.0) || o.kb_vanka < 0 || (o.precision != STOKES_PREC_FP64 && o.precision != STOKES_PREC_FP32))
+    if (!(o.gamma >= 0.0) || o.kb_vanka < 0 ||
+        (o.precision != STOKES_PREC_FP64 && o.precision != STOKES_PREC_FP32 && o.precision != STOKES_PREC_MIXED_BF16))
         return STOKES_ERR_INVALID_ARG;
     int cmax = grid->coarsest_max > 0 ? grid->coarsest_max : 8;
     int nlev = grid->levels;
@@ -503,6 +537,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     h->gamma = o.gamma;
     double hh = grid->h > 0 ? grid->h : 1.0 / grid->nx;
     size_t es = h->prec == STOKES_PREC_FP64 ? sizeof(double) : sizeof(float);
+    // mixed precision: the two finest levels (never the coarsest) keep b and r as BF16
+    h->nbf = h->prec == STOKES_PREC_MIXED_BF16 ? std::min(2, nlev - 1) : 0;
     int nx = grid->nx, ny = grid->ny, nz = grid->nz;
     for (int l = 0; l < nlev; ++l) {
         LevelBuf B;
@@ -541,8 +577,9 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
         const Lev &L = B.L;
         int rc;
         if ((rc = h->alloc(&B.x, es * L.n))) return rc;
-        if ((rc = h->alloc(&B.b, es * L.n))) return rc;
-        if ((rc = h->alloc(&B.r, es * L.n))) return rc;
+        const size_t esb = l < h->nbf ? sizeof(bf16) : es;
+        if ((rc = h->alloc(&B.b, esb * L.n))) return rc;
+        if ((rc = h->alloc(&B.r, esb * L.n))) return rc;
         if ((rc = h->alloc(&B.delta, es * (size_t)L.nx * L.ny * L.nz))) return rc;
         // V1 cells (interior cells with a face on the ghost shell) by colour
         std::vector<int> cells[8];
@@ -662,7 +699,7 @@ int stokes_apply(stokes_t h, const double *x, double *y, void *stream) {
     if ((rc = stage_masked(h, x, h->stage_in, s))) return rc;
     bool ydev = is_device_ptr(y);
     double *yd = ydev ? y : h->stage_out;
-    launch_apply<double>(h->lev[0].L, h->stage_in, nullptr, yd, 0.0, s);
+    launch_apply<double, double>(h->lev[0].L, h->stage_in, nullptr, yd, 0.0, s);
     CKLAUNCH();
     if (!ydev) {
         CK(cudaMemcpyAsync(y, yd, sizeof(double) * h->n0(), cudaMemcpyDeviceToHost, s));
@@ -681,7 +718,7 @@ int mg_precondition(stokes_t h, const double *sv, double *tv, void *stream) {
         if ((rc = ensure_stage(h))) return rc;
     const double *sd;
     if ((rc = stage_in(h, sv, n, h->stage_in, &sd, s))) return rc;
-    if ((rc = to_level(h, h->lev[0].L, sd, h->lev[0].b, s))) return rc;
+    if ((rc = to_level(h, h->lev[0].L, sd, h->lev[0].b, s, h->nbf > 0))) return rc;
     CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
     if ((rc = run_vcycle(h, s))) return rc;
     bool tdev = is_device_ptr(tv);
@@ -768,7 +805,8 @@ extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol,
     rel = std::sqrt(ss) / nb;
     if (rel < tol) goto finish;
     // t = V-cycle(L~, s_0, 0, n); q_0 = t; tau_0 = |t|; rho_0 = s_0^T q_0; d = 0
-    if (h->prec != STOKES_PREC_FP64) launch_convert<double, float>(n, h->s, (float *)h->lev[0].b, s);
+    if (h->nbf > 0) launch_convert<double, bf16>(n, h->s, (bf16 *)h->lev[0].b, s);
+    else if (h->prec != STOKES_PREC_FP64) launch_convert<double, float>(n, h->s, (float *)h->lev[0].b, s);
     if ((rc = run_vcycle(h, s))) return rc;
     if (h->prec == STOKES_PREC_FP64) {
         launch_dot2<double>(n, (const double *)h->lev[0].x, h->s, h->partials, s);
@@ -914,21 +952,22 @@ int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, 
     if ((rc = stage_in(h, x, n, h->stage_in, &xd, s))) return rc;
     if ((rc = to_level(h, B.L, xd, B.x, s))) return rc;
     if ((rc = stage_in(h, b, n, h->stage_in, &bd, s))) return rc;
-    if ((rc = to_level(h, B.L, bd, B.b, s))) return rc;
+    if ((rc = to_level(h, B.L, bd, B.b, s, level < h->nbf))) return rc;
     CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
-    auto body = [&](auto tag) {
-        using T = decltype(tag);
+    auto body = [&](auto t, auto tb) {
+        using T = decltype(t);
+        using TB = decltype(tb);
         switch (which) {
-        case 0: smooth<T>(h, level, s); break;
-        case 1: dgs_forward<T>(h, level, s); dgs_backward<T>(h, level, s, true); break;
-        case 2: vanka_sym<T>(h, level, s); break;
-        case 3: dgs_forward<T>(h, level, s); dgs_finish_forward<T>(h, level, s); break;
-        case 4: dgs_backward<T>(h, level, s, false); break;
-        default: vanka_colour<T>(h, level, which - 10, s); break;
+        case 0: smooth<T, TB>(h, level, s); break;
+        case 1: dgs_forward<T, TB>(h, level, s); dgs_backward<T, TB>(h, level, s, true); break;
+        case 2: vanka_sym<T, TB>(h, level, s); break;
+        case 3: dgs_forward<T, TB>(h, level, s); dgs_finish_forward<T>(h, level, s); break;
+        case 4: dgs_backward<T, TB>(h, level, s, false); break;
+        default: vanka_colour<T, TB>(h, level, which - 10, s); break;
         }
     };
-    if (h->prec == STOKES_PREC_FP64) body(double());
-    else body(float());
+    if (h->prec == STOKES_PREC_FP64) with_tb<double>(h, level, body);
+    else with_tb<float>(h, level, body);
     CKLAUNCH();
     double *out = xdev ? x : h->stage_out;
     if ((rc = from_level(h, B.x, out, n, s))) return rc;
@@ -947,17 +986,22 @@ int stokes_restrict(stokes_t h, int level, const double *rf, double *bc, void *s
     if ((rc = ensure_stage(h))) return rc;
     const double *rd;
     if ((rc = stage_in(h, rf, F.L.n, h->stage_in, &rd, s))) return rc;
-    if ((rc = to_level(h, F.L, rd, F.r, s))) return rc;
-    auto run = [&](auto tag) {
-        using T = decltype(tag);
-        launch_restrict<T>(F.L, C.L, (const T *)F.r, (T *)C.b, s);
+    if ((rc = to_level(h, F.L, rd, F.r, s, level < h->nbf))) return rc;
+    auto run = [&](auto t, auto tf) {
+        using T = decltype(t);
+        using TF = decltype(tf);
+        auto inner = [&](auto, auto tc) {
+            using TC = decltype(tc);
+            launch_restrict<T, TF, TC>(F.L, C.L, (const TF *)F.r, (TC *)C.b, s);
+        };
+        with_tb<T>(h, level + 1, inner);
     };
-    if (h->prec == STOKES_PREC_FP64) run(double());
-    else run(float());
+    if (h->prec == STOKES_PREC_FP64) with_tb<double>(h, level, run);
+    else with_tb<float>(h, level, run);
     CKLAUNCH();
     bool dev = is_device_ptr(bc);
     double *out = dev ? bc : h->stage_out;
-    if ((rc = from_level(h, C.b, out, C.L.n, s))) return rc;
+    if ((rc = from_level(h, C.b, out, C.L.n, s, level + 1 < h->nbf))) return rc;
     if (!dev) CK(cudaMemcpyAsync(bc, out, sizeof(double) * C.L.n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return STOKES_OK;

@@ -8,10 +8,23 @@
 // Box domain: a face is an unknown when its normal index lies in [1, n-1] and its tangential
 // indices in [0, n-1]; every other referenced face (walls, ghost rows) contributes 0.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace smg {
+
+// ---- storage vs arithmetic precision: level operands may be stored narrower (BF16) than the
+// precision T a kernel computes in; ldv() widens a stored value, cvt<D>() rounds to storage type D
+typedef __nv_bfloat16 bf16;
+__device__ __forceinline__ float ldv(float v) { return v; }
+__device__ __forceinline__ double ldv(double v) { return v; }
+__device__ __forceinline__ float ldv(bf16 v) { return __bfloat162float(v); }
+template <class D, class S> __device__ __forceinline__ D cvt(S v) { return (D)v; }
+template <> __device__ __forceinline__ bf16 cvt<bf16, float>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ bf16 cvt<bf16, double>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ float cvt<float, bf16>(bf16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ double cvt<double, bf16>(bf16 v) { return (double)__bfloat162float(v); }
 
 // ---- programmatic dependent launch: every kernel is launched with programmatic stream
 // serialisation, so its launch and block scheduling overlap the tail of the previous kernel in the

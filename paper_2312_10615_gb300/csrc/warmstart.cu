@@ -712,7 +712,7 @@ int warmstart_create(int n, int storage, double scale, warmstart_t *out) {
     if ((size_t)NRED * CH * 4 > wp) wp = (size_t)NRED * CH * 4;
     A((void **)&h->wpart, wp * 4);
     A((void **)&h->red, NRED * 2 * sizeof(double));
-    A((void **)&h->sc, 8 * sizeof(double));
+    A((void **)&h->sc, 16 * sizeof(double));
     A((void **)&h->xp, h->pk.npk * sizeof(double));
     A((void **)&h->xd, h->pk.npk * sizeof(double));
     A((void **)&h->xr, h->pk.npk * sizeof(double));
@@ -804,11 +804,15 @@ int warmstart_solve(warmstart_t h, stokes_t st, const double *b, double *x, doub
     if (stokes_vector_length(st, 0) != h->pk.npk) return STOKES_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = warmstart_predict(h, b, x, stream);
-    // SQMR stays the judge: its first quantity is tau_0 = ||M (b - L x0)|| (M the V-cycle); a guess
-    // whose tau_0 is not below that of x0 = 0, ||M b||, is discarded
+    // SQMR stays the judge.  A guess is kept only if it lowers both the residual, ||b - L x0|| <
+    // ||b|| (the tolerance is relative to ||b||, and a reduction far beyond the V-cycle's own
+    // precision cannot be asked of the preconditioned iteration), and SQMR's first quantity
+    // tau_0 = ||M (b - L x0)|| (M the V-cycle) below its value for x0 = 0, ||M b||
     if (rc == STOKES_OK) rc = stokes_apply(st, x, h->xr, stream);
     if (rc == STOKES_OK) {
         launch_k(k_sub, dim3(NRED), dim3(256), 0, s, h->pk.npk, b, (const double *)h->xr, h->xd);
+        launch_k(k_loss_parts, dim3(NRED), dim3(256), 0, s, h->pk.npk, (const double *)nullptr, (const double *)h->xd, h->red);
+        launch_k(k_finish2, dim3(1), dim3(256), 0, s, (const double *)h->red, NRED, h->sc, 8);
         rc = mg_precondition(st, h->xd, h->xr, stream);
     }
     if (rc == STOKES_OK) {
@@ -819,11 +823,12 @@ int warmstart_solve(warmstart_t h, stokes_t st, const double *b, double *x, doub
     if (rc != STOKES_OK) return rc;
     launch_k(k_loss_parts, dim3(NRED), dim3(256), 0, s, h->pk.npk, (const double *)nullptr, (const double *)h->xd, h->red);
     launch_k(k_finish2, dim3(1), dim3(256), 0, s, (const double *)h->red, NRED, h->sc, 6);
-    double sc[8];
-    cudaError_t e = cudaMemcpyAsync(sc, h->sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    double sc[10];
+    cudaError_t e = cudaMemcpyAsync(sc, h->sc, 10 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_rc(e);
-    const int use = std::isfinite(sc[4]) && sc[4] < sc[6];
+    // sc[0] = ||b||^2, sc[8] = ||b - L x0||^2, sc[4] = ||M (b - L x0)||^2, sc[6] = ||M b||^2
+    const int use = std::isfinite(sc[4]) && std::isfinite(sc[8]) && sc[8] < sc[0] && sc[4] < sc[6];
     if (!use) {
         e = cudaMemsetAsync(x, 0, h->pk.npk * sizeof(double), s);
         if (e != cudaSuccess) return cuda_rc(e);

@@ -249,6 +249,41 @@ def test_sqmr_fp32_vcycle_accuracy():
     assert rel_err(x, x_ref) < 1e-7
 
 
+# ---------------------------------------------------------------------------------------------- BF16 levels
+
+def test_mixed_bf16_pieces_close_to_oracle():
+    # the two finest levels store b and r as BF16 (8 significant bits): a V-cycle, a smoothing step
+    # and a restriction agree with the FP64 oracle to the BF16 rounding of their operands
+    o, S = pair((32, 32, 32), precision=smg.PREC_MIXED_BF16)
+    s = rand_masked(o, 31)
+    assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 3e-2
+    for level in (0, 1):  # the BF16 levels (level 2 is the coarsest)
+        x, b = rand_masked(o, 32, level), rand_masked(o, 33, level)
+        got = cuda(x)
+        smg.stokes_smooth(S.h, level, 0, got, cuda(b))
+        assert rel_err(got, o.smooth(x, b, level=level)) < 3e-2, level
+    r = rand_masked(o, 34, 0)
+    bc = torch.zeros(S.length(1), dtype=torch.float64, device=DEV)
+    smg.stokes_restrict(S.h, 0, cuda(r), bc)
+    assert rel_err(bc, o.restrict(r, level=0)) < 1e-2
+
+
+def test_sqmr_mixed_bf16_accuracy():
+    # BF16 operand storage changes the preconditioner, not the tolerance: the solution matches the
+    # FP64 oracle's as closely as the FP32 V-cycle's does
+    o, S = pair((32, 32, 32), precision=smg.PREC_MIXED_BF16)
+    prob = synthetic.bumps(32, seed=1)
+    b_ref = o.rhs(prob["f"].numpy(), None)
+    x_ref, rc, it_ref, _, _ = o.sqmr(b_ref, tol=1e-12, maxit=200)
+    b = S.rhs(prob["f"].to(DEV), None)
+    x, info = S.solve(b, tol=1e-10, max_iter=200)
+    assert info.status == 0 and info.rel_residual < 1e-10
+    assert rel_err(x, x_ref) < 1e-7
+    _, info8 = S.solve(b, tol=1e-8, max_iter=200)
+    _, o8, it8, _, _ = o.sqmr(b_ref, tol=1e-8, maxit=200)
+    assert info8.iterations <= it8 + 2
+
+
 # ---------------------------------------------------------------------------------------------- F1
 
 def test_lid_cavity_32_parity():
