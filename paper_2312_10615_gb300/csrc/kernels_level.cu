@@ -82,16 +82,13 @@ __device__ __forceinline__ bool entry_eval(const T *__restrict__ x, const Lev &L
     q = pidx(L, c, i, j, k);
     v = T(0);
     if (!active(L, c, i, j, k)) return true;
-    Coef<T> Kx = K;
-    if (OPX == OP_A_B) {
-        Kx.ih = c < 3 ? T(0) : K.ih;  // faces: A u only; cells: -div u only
-        Kx.gam = T(0);
-    }
+    // OP_A_B: faces A u only, cells -div u only (no pressure is loaded)
+    constexpr bool P = OPX == OP_APPLY;
     switch (c) {
-    case 0: v = face_Lx_fast<T, 0>(x, L, i, j, k, Kx); break;
-    case 1: v = face_Lx_fast<T, 1>(x, L, i, j, k, Kx); break;
-    case 2: v = face_Lx_fast<T, 2>(x, L, i, j, k, Kx); break;
-    default: v = cell_Lx_fast<T>(x, L, i, j, k, Kx);
+    case 0: v = face_Lx_fast<T, 0, P>(x, L, i, j, k, K); break;
+    case 1: v = face_Lx_fast<T, 1, P>(x, L, i, j, k, K); break;
+    case 2: v = face_Lx_fast<T, 2, P>(x, L, i, j, k, K); break;
+    default: v = cell_Lx_fast<T, P>(x, L, i, j, k, K);
     }
     return true;
 }

@@ -125,8 +125,8 @@ __host__ __device__ inline long long comp_base(const Lev &L, int c) {
     return c == 0 ? L.off[0] : (c == 1 ? L.off[1] : (c == 2 ? L.off[2] : L.off[3]));
 }
 
-// (L~x)_f on the active face (i,j,k) of component C
-template <class T, int C>
+// (L~x)_f on the active face (i,j,k) of component C (WITHP = false: the A part alone, no pressure loads)
+template <class T, int C, bool WITHP = true>
 __device__ __forceinline__ T face_Lx_fast(const T *__restrict__ x, const Lev &L, int i, int j, int k,
                                           const Coef<T> &K) {
     const long long sy = L.nx + (C == 0), sz = sy * (L.ny + (C == 1));
@@ -138,14 +138,15 @@ __device__ __forceinline__ T face_Lx_fast(const T *__restrict__ x, const Lev &L,
     else s -= (j > 0 ? xc[-sy] : T(0)) + (j < L.ny - 1 ? xc[sy] : T(0));
     if (C == 2) s -= xc[-sz] + xc[sz];
     else s -= (k > 0 ? xc[-sz] : T(0)) + (k < L.nz - 1 ? xc[sz] : T(0));
+    if (!WITHP) return K.eh2 * s;
     const long long cy = L.nx, cz = (long long)L.nx * L.ny;
     const T *pc = x + L.off[3] + i + cy * j + cz * k;
     const long long ps = C == 0 ? 1 : (C == 1 ? cy : cz);
     return K.eh2 * s + K.ih * (pc[0] - pc[-ps]);
 }
 
-// (L~x)_c on cell (i,j,k)
-template <class T>
+// (L~x)_c on cell (i,j,k) (WITHG = false: -div u alone, no pressure load)
+template <class T, bool WITHG = true>
 __device__ __forceinline__ T cell_Lx_fast(const T *__restrict__ x, const Lev &L, int i, int j, int k,
                                           const Coef<T> &K) {
     const long long nx = L.nx, ny = L.ny;
@@ -153,6 +154,7 @@ __device__ __forceinline__ T cell_Lx_fast(const T *__restrict__ x, const Lev &L,
     const T *v = x + L.off[1] + i + nx * (j + (ny + 1) * k);
     const T *w = x + L.off[2] + i + nx * (j + ny * k);
     T div = (u[1] - u[0]) + (v[nx] - v[0]) + (w[nx * ny] - w[0]);
+    if (!WITHG) return -K.ih * div;
     return -K.ih * div - K.gam * x[L.off[3] + i + nx * (j + ny * k)];
 }
 
