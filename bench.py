@@ -207,9 +207,20 @@ def roofline(prof, n, e, peak, traffic_db, precision):
     if cnt0 == 0:
         return None
     avg_ms = ms0 / cnt0
-    b = alg_bytes(kind, n, e if kind not in ("apply_dot",) else 8)
-    achieved = b / (avg_ms * 1e-3) / 1e9 if b else None
     tr = traffic_db.get(f"{precision}:{kind}:{n}")
+    if kind in ("apply_dot", "update_x"):
+        # FP64 kernels of SQMR: bound by the DP pipe; count DP instructions (per packed entry: apply
+        # ~9.25 = 3/4 face rows x 9 + 1/4 cell rows x 6 + the dot's DFMA; update_x 8), against the
+        # measured FP64 FMA rate of 1.20 TFLOP/s = 600 G DP instructions/s
+        per = 9.25 if kind == "apply_dot" else 8.0
+        npk = packed_len(n)
+        achieved = per * npk / (avg_ms * 1e-3) / 1e9
+        return {"kernel": kind, "bound": "alu", "achieved": achieved, "peak": 600.0,
+                "peak_source": "measured FP64 FMA rate (1.20 TFLOP/s, 600 G DFMA/s)", "unit": "G DP-instr/s",
+                "frac": achieved / 600.0, "traffic": tr, "dp_instr_per_launch": per * npk, "avg_launch_ms": avg_ms,
+                "launches_level0_per_iteration": cnt0, "share_of_iteration": ms_all / sum(v[0] for v in prof.values())}
+    b = alg_bytes(kind, n, e)
+    achieved = b / (avg_ms * 1e-3) / 1e9 if b else None
     return {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": peak[0],
             "peak_source": f"{peak[1]} hbm_gbs (MEASURED_PEAKS.json)" if peak[1] == "measured" else "fallback 6.8 TB/s",
             "unit": "GB/s", "frac": achieved / peak[0] if achieved else None, "traffic": tr,
@@ -683,6 +694,8 @@ def main():
             "config": {"workload": workload_name(n), "n": n, "unknowns": unknowns(n), "levels": S32.levels,
                        "tol": args.tol, "vcycle_precision": "fp32", "sqmr_precision": "fp64",
                        "l2": "inputs larger than L2 (each FP64 vector 537 MB)", "parallelism": f"replicas x{world}"},
+            "vanka_schedule_per_level": [dict(zip(("mode", "blocks", "ms_per_sweep"), smg.stokes_level_schedule(S32.h, l)))
+                                         for l in range(S32.levels - 1)],
             "iterations": [it for it, _ in its32], "rel_residual": [r for _, r in its32],
             "kernel_ms_per_iteration": {k: round(v[0], 4) for k, v in prof32.items()},
             "kernel_ms_per_iteration_level0": {k: round(v[2], 4) for k, v in prof32.items()},

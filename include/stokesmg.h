@@ -79,7 +79,11 @@ typedef struct {
     int precision; /* STOKES_PREC_FP64 (default) or STOKES_PREC_FP32 V-cycle */
     int use_graphs;/* capture the V-cycle / SQMR iteration in CUDA graphs (default 1) */
     int vanka_persistent; /* 0 (default): two launches per Vanka colour; 1: one cooperative launch per
-                             symmetric sweep (grid barrier with a bounded spin; expiry -> STOKES_ERR_TIMEOUT) */
+                             symmetric sweep on every level (grid barrier with a bounded spin; expiry ->
+                             STOKES_ERR_TIMEOUT) */
+    int autotune;  /* 1 (default): at creation, time the Vanka schedule candidates of every smoothed
+                      level (per-colour launches; one cooperative sweep with 5 grid sizes) and keep the
+                      fastest; all candidates give bit-identical results.  0: per-colour launches. */
 } stokes_opts_t;
 
 typedef struct {
@@ -140,6 +144,11 @@ int sqmr_solve(stokes_t h, const double *rhs, double *x, double tol, int max_ite
  * A handle must not appear twice in one batch. */
 int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rhs, double *const *x, double tol,
                      int max_iter, sqmr_info_t *infos, double *done_ms, int nstreams);
+
+/* the Vanka schedule the autotuner chose for a smoothed level: *mode 0 = two launches per colour,
+ * 1 = one cooperative launch per symmetric sweep with *blocks thread blocks; *ms = its measured time
+ * per symmetric sweep (0 if not measured).  Any output pointer may be NULL. */
+int stokes_level_schedule(stokes_t h, int level, int *mode, int *blocks, float *ms);
 
 /* *out = ||b - L x||_2 (FP64, deterministic reduction); synchronises the stream.  Uses the
  * handle's reduction scratch. */

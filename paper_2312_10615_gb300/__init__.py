@@ -24,7 +24,8 @@ PREC_FP64, PREC_FP32, PREC_MIXED_BF16 = 0, 1, 2
 EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vector_length", "stokes_ghost_length",
            "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
-           "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_strerror",
+           "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
+           "stokes_strerror",
            # learned initial guess (include/warmstart.h)
            "warmstart_num_weights", "warmstart_create", "warmstart_destroy", "warmstart_set_scale",
            "warmstart_set_weights", "warmstart_get_weights", "warmstart_predict", "warmstart_loss_grad",
@@ -47,7 +48,7 @@ class stokes_bc_t(ctypes.Structure):
 
 class stokes_opts_t(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("kb_vanka", ctypes.c_int), ("precision", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("vanka_persistent", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("vanka_persistent", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class sqmr_info_t(ctypes.Structure):
@@ -88,6 +89,7 @@ def _load():
         "stokes_residual_norm_noalloc": (i, [i, i, i, d, d, vp, vp, vp, vp]),
         "sqmr_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,
                                  ctypes.POINTER(sqmr_info_t), ctypes.POINTER(d), i]),
+        "stokes_level_schedule": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
         "stokes_strerror": (ctypes.c_char_p, [i]),
         "warmstart_num_weights": (ll, []),
         "warmstart_create": (i, [i, i, d, ctypes.POINTER(vp)]),
@@ -162,11 +164,12 @@ def stokes_opts_default():
 
 
 def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest_max=8, gamma=1e-3, kb_vanka=1,
-                  precision=PREC_FP64, use_graphs=True, vanka_persistent=False):
+                  precision=PREC_FP64, use_graphs=True, vanka_persistent=False, autotune=True):
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     g = stokes_grid_t(nx, ny, nz, h, levels, coarsest_max)
-    o = stokes_opts_t(gamma, kb_vanka, precision, int(bool(use_graphs)), int(bool(vanka_persistent)))
+    o = stokes_opts_t(gamma, kb_vanka, precision, int(bool(use_graphs)), int(bool(vanka_persistent)),
+                      int(bool(autotune)))
     hdl = ctypes.c_void_p()
     _check(lib().stokes_create(ctypes.byref(g), None, viscosity, ctypes.byref(o), ctypes.byref(hdl)), "stokes_create")
     return hdl
@@ -236,6 +239,14 @@ def stokes_profile_iteration(h, stream=None):
     ma, ca, m0, c0 = (ctypes.c_double * k)(), (ctypes.c_int * k)(), (ctypes.c_double * k)(), (ctypes.c_int * k)()
     _check(lib().stokes_profile_iteration(h, k, ma, ca, m0, c0, _stream(stream)), "stokes_profile_iteration")
     return {name: (ma[j], ca[j], m0[j], c0[j]) for j, name in enumerate(KERNEL_KINDS)}
+
+
+def stokes_level_schedule(h, level):
+    """(mode, blocks, ms per symmetric sweep) of the Vanka schedule of a smoothed level."""
+    m, b, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().stokes_level_schedule(h, level, ctypes.byref(m), ctypes.byref(b), ctypes.byref(t)),
+           "stokes_level_schedule")
+    return m.value, b.value, t.value
 
 
 def stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, b, x, out, stream=None):

@@ -46,7 +46,7 @@ struct VankaLists {
 template <class T, class TB>
 void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
                         int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s);
-template <class T> int vanka_sweep_blocks_per_sm();
+template <class T, class TB> int vanka_sweep_blocks_per_sm();
 // transfers (Sec. 2): bc = R rf,  xf += P ec
 template <class T, class TF, class TC> void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s);
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s);

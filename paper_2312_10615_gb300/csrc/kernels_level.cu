@@ -521,9 +521,9 @@ __global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, c
         }
 }
 
-template <class T> int vanka_sweep_blocks_per_sm() {
+template <class T, class TB> int vanka_sweep_blocks_per_sm() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vanka_sweep<T, T>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vanka_sweep<T, TB>, 256, 0);
     return nb;
 }
 
@@ -756,15 +756,15 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template void launch_vanka_compute<T, TB>(const Lev &, const T *, const TB *, const int *, int, const T *, T *,  \
                                               int, cudaStream_t);                                                   \
     template void launch_vanka_sweep<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, T *, int,  \
-                                            int, GridBarrier *, int, cudaStream_t);
+                                            int, GridBarrier *, int, cudaStream_t);                                 \
+    template int vanka_sweep_blocks_per_sm<T, TB>();
 #define SMG_INST(T)                                                                                               \
     SMG_INST_TB(T, T)                                                                                             \
     template void launch_dgs_p_gather<T>(const Lev &, T *, const T *, cudaStream_t);                              \
     template void launch_vanka_apply<T>(const Lev &, T *, const int *, int, const T *, int, cudaStream_t);        \
     template void launch_restrict<T, T, T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);               \
     template void launch_prolong<T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);                      \
-    template void launch_coarse<T>(const Lev &, const int *, int, const double *, const T *, T *, cudaStream_t);   \
-    template int vanka_sweep_blocks_per_sm<T>();
+    template void launch_coarse<T>(const Lev &, const int *, int, const double *, const T *, T *, cudaStream_t);
 SMG_INST(float)
 SMG_INST(double)
 SMG_INST_TB(float, bf16)

@@ -38,6 +38,8 @@ struct LevelBuf {
     int vcount[8] = {};
     int vcap = 0;
     VankaLists lists;
+    int vmode = 0, vblocks = 0;  // Vanka schedule: 0 per-colour launches, 1 cooperative sweep of vblocks blocks
+    float vms = 0.f;             // autotuner's time per symmetric sweep
 };
 
 int cuda_status(cudaError_t e) {
@@ -248,10 +250,11 @@ template <class T, class TB> void vanka_colour(stokes_s *h, int l, int col, cuda
 // `sweeps` symmetric Vanka sweeps (App. C: colours 0..7 then 7..0)
 template <class T, class TB> void vanka_sym(stokes_s *h, int l, cudaStream_t s, int sweeps = 1) {
     LevelBuf &B = h->lev[l];
-    if (h->vanka_persistent) {
+    if (h->vanka_persistent || B.vmode == 1) {
+        const int nb = B.vblocks > 0 && !h->vanka_persistent ? B.vblocks : h->vanka_max_blocks;
         prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
             launch_vanka_sweep<T, TB>(B.L, (T *)B.x, (const TB *)B.b, B.lists, (const T *)B.kinv, (T *)B.corr, B.vcap,
-                                      sweeps, h->bar, h->vanka_max_blocks, s);
+                                      sweeps, h->bar, nb, s);
         });
         return;
     }
@@ -398,6 +401,70 @@ int run_iteration(stokes_s *h, cudaStream_t s) {
     return 0;
 }
 
+// ---- autotuner: per smoothed level, time the Vanka schedule candidates on the level's own buffers
+// (their contents do not matter for the timing and are zero at creation) and keep the fastest.
+// Every candidate computes the same bits, so the choice changes speed only.
+template <class T, class TB> float time_vanka(stokes_s *h, int l, int mode, int blocks, cudaStream_t s) {
+    LevelBuf &B = h->lev[l];
+    B.vmode = mode;
+    B.vblocks = blocks;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s);
+    for (int r = 0; r < 2; ++r) vanka_sym<T, TB>(h, l, s, 1);
+    cudaEventRecord(e0, s);
+    const int reps = 5;
+    for (int r = 0; r < reps; ++r) vanka_sym<T, TB>(h, l, s, 1);
+    cudaEventRecord(e1, s);
+    float ms = -1.f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        GridBarrier hb;
+        if (cudaMemcpy(&hb, h->bar, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess || hb.err) ms = -1.f;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+int autotune_vanka(stokes_s *h, int nsm) {
+    cudaStream_t s = h->cs;
+    for (int l = 0; l < h->nlev() - 1; ++l) {
+        LevelBuf &B = h->lev[l];
+        int mx = 0;
+        for (int c = 0; c < 8; ++c) mx = std::max(mx, B.vcount[c]);
+        const int need = (int)((8LL * mx + 255) / 256);
+        int best_mode = 0, best_blocks = 0;
+        float best = -1.f;
+        auto run = [&](auto t, auto tb) {
+            using T = decltype(t);
+            using TB = decltype(tb);
+            best = time_vanka<T, TB>(h, l, 0, 0, s);
+            const int cand[5] = {h->vanka_max_blocks, h->vanka_max_blocks / 2, nsm, nsm / 2, nsm / 4};
+            for (int c = 0; c < 5; ++c) {
+                const int nb = std::min(cand[c], need);
+                if (nb < 1 || (c > 0 && nb == std::min(cand[c - 1], need))) continue;
+                const float ms = time_vanka<T, TB>(h, l, 1, nb, s);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    best_mode = 1;
+                    best_blocks = nb;
+                }
+            }
+        };
+        if (h->prec == STOKES_PREC_FP64) with_tb<double>(h, l, run);
+        else with_tb<float>(h, l, run);
+        B.vmode = best_mode;
+        B.vblocks = best_blocks;
+        B.vms = best > 0.f ? best : 0.f;
+    }
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
 // copy a caller vector (host or device) of n doubles into a device buffer the call may read
 int stage_in(stokes_s *h, const double *p, long long n, double *dst_if_host, const double **out, cudaStream_t s) {
     if (is_device_ptr(p)) {
@@ -480,6 +547,7 @@ void stokes_opts_default(stokes_opts_t *o) {
     o->precision = STOKES_PREC_FP64;
     o->use_graphs = 1;
     o->vanka_persistent = 0;
+    o->autotune = 1;
 }
 
 const char *stokes_strerror(int st) {
@@ -631,9 +699,14 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
         if ((rc = h->alloc(&h->bar, sizeof(GridBarrier)))) return rc;
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev));
-        int per_sm = h->prec == STOKES_PREC_FP64 ? vanka_sweep_blocks_per_sm<double>() : vanka_sweep_blocks_per_sm<float>();
+        int per_sm = h->prec == STOKES_PREC_FP64 ? vanka_sweep_blocks_per_sm<double, double>()
+                                                 : std::min(vanka_sweep_blocks_per_sm<float, float>(),
+                                                            vanka_sweep_blocks_per_sm<float, bf16>());
         h->vanka_max_blocks = per_sm * nsm;
         if (!coop || h->vanka_max_blocks <= 0) h->vanka_persistent = 0;
+        if (coop && h->vanka_max_blocks > 0 && !h->vanka_persistent && o.autotune) {
+            if ((rc = autotune_vanka(h.get(), nsm))) return rc;
+        }
     }
     CK(cudaDeviceSynchronize());
     *out = h.release();
@@ -935,6 +1008,16 @@ int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rh
     if (setup_err) return setup_err;
     for (int i = 0; i < nprob; ++i)
         if (status[i] != STOKES_OK) return status[i];
+    return STOKES_OK;
+}
+
+int stokes_level_schedule(stokes_t h, int level, int *mode, int *blocks, float *ms) {
+    if (!h || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
+    const LevelBuf &B = h->lev[level];
+    const bool coop = h->vanka_persistent || B.vmode == 1;
+    if (mode) *mode = coop ? 1 : 0;
+    if (blocks) *blocks = coop ? (B.vblocks > 0 && !h->vanka_persistent ? B.vblocks : h->vanka_max_blocks) : 0;
+    if (ms) *ms = B.vms;
     return STOKES_OK;
 }
 

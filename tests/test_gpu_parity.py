@@ -188,11 +188,33 @@ def test_vcycle_fp32_parity_and_symmetry():
 
 def test_persistent_vanka_matches_per_colour_launches():
     # one cooperative launch per symmetric sweep (grid barriers) vs two launches per colour
-    o, S = pair((32, 32, 32))
+    o, _ = pair((32, 32, 32))
+    Sp = smg.Stokes(32, autotune=False)
     Sc = smg.Stokes(32, vanka_persistent=True)
+    for l in range(Sp.levels - 1):
+        assert smg.stokes_level_schedule(Sp.h, l)[0] == 0 and smg.stokes_level_schedule(Sc.h, l)[0] == 1
     s = cuda(rand_masked(o, 26))
-    assert float(torch.max(torch.abs(S.precondition(s) - Sc.precondition(s)))) == 0.0
+    assert float(torch.max(torch.abs(Sp.precondition(s) - Sc.precondition(s)))) == 0.0
+    Sp.close()
     Sc.close()
+
+
+@pytest.mark.parametrize("precision", [smg.PREC_FP64, smg.PREC_FP32, smg.PREC_MIXED_BF16])
+def test_autotuned_schedule_is_bit_identical(precision):
+    # the autotuner only picks how the Vanka sweeps are launched, never what they compute
+    Sa = smg.Stokes(64, precision=precision)
+    Sp = smg.Stokes(64, precision=precision, autotune=False)
+    for l in range(Sa.levels - 1):
+        mode, blocks, ms = smg.stokes_level_schedule(Sa.h, l)
+        assert mode in (0, 1) and ms > 0 and (mode == 0 or blocks >= 1)
+    s = cuda(np.random.default_rng(27).standard_normal(Sa.n))
+    assert float(torch.max(torch.abs(Sa.precondition(s) - Sp.precondition(s)))) == 0.0
+    b = Sa.rhs(synthetic.bumps(64, seed=4, device=DEV)["f"], None)
+    xa, ia = Sa.solve(b, tol=1e-8)
+    xp, ip = Sp.solve(b, tol=1e-8)
+    assert ia.iterations == ip.iterations and float(torch.max(torch.abs(xa - xp))) == 0.0
+    Sa.close()
+    Sp.close()
 
 
 def test_graph_and_eager_paths_agree():
