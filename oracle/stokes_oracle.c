@@ -19,7 +19,7 @@
  *   V-cycle ................... Alg. 1
  *   SQMR ...................... Sec. 4, Alg. 4
  *
- * Readings of places where the paper is silent or ambiguous (all listed in the design doc):
+ * Readings of places where the paper is silent or ambiguous:
  *  - scaling: A = (eta/h^2)(7-point stencil), B^T = gradient/h, B = -divergence/h.
  *  - a Dirichlet face neighbour keeps its value (grid-cell precision), the diagonal
  *    stays 6 eta/h^2; inside the preconditioner the Dirichlet values are zero.

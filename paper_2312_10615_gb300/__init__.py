@@ -25,6 +25,7 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
            "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
+           "stokes_set_level_schedule",
            "stokes_strerror",
            # learned initial guess (include/warmstart.h)
            "warmstart_num_weights", "warmstart_create", "warmstart_destroy", "warmstart_set_scale",
@@ -90,6 +91,7 @@ def _load():
         "sqmr_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,
                                  ctypes.POINTER(sqmr_info_t), ctypes.POINTER(d), i]),
         "stokes_level_schedule": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
+        "stokes_set_level_schedule": (i, [vp, i, i, i]),
         "stokes_strerror": (ctypes.c_char_p, [i]),
         "warmstart_num_weights": (ll, []),
         "warmstart_create": (i, [i, i, d, ctypes.POINTER(vp)]),
@@ -247,6 +249,10 @@ def stokes_level_schedule(h, level):
     _check(lib().stokes_level_schedule(h, level, ctypes.byref(m), ctypes.byref(b), ctypes.byref(t)),
            "stokes_level_schedule")
     return m.value, b.value, t.value
+
+
+def stokes_set_level_schedule(h, level, mode, blocks=0):
+    _check(lib().stokes_set_level_schedule(h, level, mode, blocks), "stokes_set_level_schedule")
 
 
 def stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, b, x, out, stream=None):

@@ -47,6 +47,12 @@ template <class T, class TB>
 void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
                         int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s);
 template <class T, class TB> int vanka_sweep_blocks_per_sm();
+// one symmetric Vanka sweep (x sweeps) in a single thread-block cluster of `cluster` CTAs x 1024
+// threads separated by hardware cluster barriers (no software wait); returns the launch status
+template <class T, class TB> cudaError_t vanka_cluster_prepare();
+template <class T, class TB>
+cudaError_t launch_vanka_cluster(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr,
+                                 int cap, int sweeps, int cluster, cudaStream_t s);
 // transfers (Sec. 2): bc = R rf,  xf += P ec
 template <class T, class TF, class TC> void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s);
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s);

@@ -548,6 +548,73 @@ void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists
     cudaLaunchKernelEx(&cfg, k_vanka_sweep<T, TB>, L, x, b, lists, kinv, corr, cap, coef<T>(L, L.gamma), sweeps, bar);
 }
 
+// ---- one symmetric Vanka sweep in one thread-block cluster (small levels) ----
+// The cluster's CTAs stride over the cells of a colour; hardware cluster barriers (release/acquire
+// at cluster scope) separate the compute and apply steps, so no launch and no software spin sits
+// between colours.  Every thread executes every barrier (no early exit), the colour counts are
+// uniform, and the result is bit-identical to the per-colour launches.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+template <class T, class TB>
+__global__ void __launch_bounds__(1024) k_vanka_cluster(Lev L, T *__restrict__ x, const TB *__restrict__ b,
+                                                        VankaLists lists, const T *__restrict__ kinv,
+                                                        T *__restrict__ corr, int cap, Coef<T> K, int sweeps) {
+    pdl_wait();
+    const long long stride = (long long)cluster_size() * blockDim.x;  // a multiple of 8: lanes keep their group
+    const long long t0 = (long long)cluster_rank() * blockDim.x + threadIdx.x;
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);
+    for (int sw = 0; sw < sweeps; ++sw)
+        for (int ph = 0; ph < 16; ++ph) {
+            const int col = ph < 8 ? ph : 15 - ph;
+            const int n = lists.count[col];
+            if (n == 0) continue;  // uniform across the cluster
+            const int *cells = lists.cells[col];
+            for (long long t = t0; (t >> 3) < n; t += stride)
+                vanka_compute_lane(L, x, b, cells[t >> 3], (int)(t & 7), gmask, kinv, corr, cap, (int)(t >> 3), K);
+            cluster_sync_all();
+            for (long long t = t0; (t >> 3) < n; t += stride)
+                vanka_apply_lane(L, x, cells[t >> 3], (int)(t & 7), corr, cap, (int)(t >> 3));
+            cluster_sync_all();
+        }
+}
+
+// clusters above the portable size of 8 need the kernel attribute, set once (outside any capture)
+template <class T, class TB> cudaError_t vanka_cluster_prepare() {
+    return cudaFuncSetAttribute(k_vanka_cluster<T, TB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+template <class T, class TB>
+cudaError_t launch_vanka_cluster(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr,
+                                 int cap, int sweeps, int cluster, cudaStream_t s) {
+    if (sweeps <= 0) return cudaSuccess;
+    if (cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_vanka_cluster<T, TB>, L, x, b, lists, kinv, corr, cap, coef<T>(L, L.gamma), sweeps);
+}
+
 // ------------------------------------------------------------------------------------------
 // Sec. 2 transfers.  P (coarse -> fine): pressure constant per coarse cell; a face value takes
 // weight 1 from a coincident coarse face or 1/2 + 1/2 from the two coarse faces around it along
@@ -757,6 +824,9 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
                                               int, cudaStream_t);                                                   \
     template void launch_vanka_sweep<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, T *, int,  \
                                             int, GridBarrier *, int, cudaStream_t);                                 \
+    template cudaError_t vanka_cluster_prepare<T, TB>();                                                          \
+    template cudaError_t launch_vanka_cluster<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *,   \
+                                                     T *, int, int, int, cudaStream_t);                             \
     template int vanka_sweep_blocks_per_sm<T, TB>();
 #define SMG_INST(T)                                                                                               \
     SMG_INST_TB(T, T)                                                                                             \

@@ -38,7 +38,8 @@ struct LevelBuf {
     int vcount[8] = {};
     int vcap = 0;
     VankaLists lists;
-    int vmode = 0, vblocks = 0;  // Vanka schedule: 0 per-colour launches, 1 cooperative sweep of vblocks blocks
+    int vmode = 0, vblocks = 0;  // Vanka schedule: 0 per-colour launches, 1 cooperative sweep of vblocks blocks,
+                                 // 2 one-cluster sweep of vblocks CTAs
     float vms = 0.f;             // autotuner's time per symmetric sweep
 };
 
@@ -250,6 +251,13 @@ template <class T, class TB> void vanka_colour(stokes_s *h, int l, int col, cuda
 // `sweeps` symmetric Vanka sweeps (App. C: colours 0..7 then 7..0)
 template <class T, class TB> void vanka_sym(stokes_s *h, int l, cudaStream_t s, int sweeps = 1) {
     LevelBuf &B = h->lev[l];
+    if (B.vmode == 2 && !h->vanka_persistent) {
+        prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
+            launch_vanka_cluster<T, TB>(B.L, (T *)B.x, (const TB *)B.b, B.lists, (const T *)B.kinv, (T *)B.corr, B.vcap,
+                                        sweeps, B.vblocks, s);
+        });
+        return;
+    }
     if (h->vanka_persistent || B.vmode == 1) {
         const int nb = B.vblocks > 0 && !h->vanka_persistent ? B.vblocks : h->vanka_max_blocks;
         prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
@@ -431,6 +439,13 @@ template <class T, class TB> float time_vanka(stokes_s *h, int l, int mode, int 
 }
 int autotune_vanka(stokes_s *h, int nsm) {
     cudaStream_t s = h->cs;
+    // cluster sizes above 8 need the non-portable attribute; without it those candidates just fail
+    if (h->prec == STOKES_PREC_FP64) vanka_cluster_prepare<double, double>();
+    else {
+        vanka_cluster_prepare<float, float>();
+        vanka_cluster_prepare<float, bf16>();
+    }
+    cudaGetLastError();
     for (int l = 0; l < h->nlev() - 1; ++l) {
         LevelBuf &B = h->lev[l];
         int mx = 0;
@@ -451,6 +466,17 @@ int autotune_vanka(stokes_s *h, int nsm) {
                     best = ms;
                     best_mode = 1;
                     best_blocks = nb;
+                }
+            }
+            // one cluster of 4, 8 or 16 CTAs: worth it only where a colour fits in a few passes
+            const int cl_need = (int)((8LL * mx + 1023) / 1024);
+            for (int cl : {4, 8, 16}) {
+                if (cl_need > 8 * cl || (cl > 4 && cl_need <= cl / 2)) continue;
+                const float ms = time_vanka<T, TB>(h, l, 2, cl, s);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    best_mode = 2;
+                    best_blocks = cl;
                 }
             }
         };
@@ -1014,10 +1040,33 @@ int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rh
 int stokes_level_schedule(stokes_t h, int level, int *mode, int *blocks, float *ms) {
     if (!h || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
     const LevelBuf &B = h->lev[level];
-    const bool coop = h->vanka_persistent || B.vmode == 1;
-    if (mode) *mode = coop ? 1 : 0;
-    if (blocks) *blocks = coop ? (B.vblocks > 0 && !h->vanka_persistent ? B.vblocks : h->vanka_max_blocks) : 0;
+    const int m = h->vanka_persistent ? 1 : B.vmode;
+    if (mode) *mode = m;
+    if (blocks) *blocks = m == 0 ? 0 : (m == 1 && (h->vanka_persistent || B.vblocks <= 0) ? h->vanka_max_blocks : B.vblocks);
     if (ms) *ms = B.vms;
+    return STOKES_OK;
+}
+
+int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
+    if (!h || level < 0 || level >= h->nlev() - 1 || mode < 0 || mode > 2) return STOKES_ERR_INVALID_ARG;
+    if (mode == 1 && (h->vanka_max_blocks <= 0 || blocks < 1 || blocks > h->vanka_max_blocks)) return STOKES_ERR_INVALID_ARG;
+    if (mode == 2 && (blocks < 1 || blocks > 16)) return STOKES_ERR_INVALID_ARG;
+    if (mode == 2 && blocks > 8) {
+        DeviceGuard dg(h->dev);
+        if (h->prec == STOKES_PREC_FP64) vanka_cluster_prepare<double, double>();
+        else {
+            vanka_cluster_prepare<float, float>();
+            vanka_cluster_prepare<float, bf16>();
+        }
+        cudaGetLastError();
+    }
+    LevelBuf &B = h->lev[level];
+    B.vmode = mode;
+    B.vblocks = mode == 0 ? 0 : blocks;
+    B.vms = 0.f;
+    // the captured graphs hold the old schedule
+    if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
+    if (h->g_iter) { cudaGraphExecDestroy(h->g_iter); h->g_iter = nullptr; }
     return STOKES_OK;
 }
 

@@ -804,7 +804,7 @@ int warmstart_solve(warmstart_t h, stokes_t st, const double *b, double *x, doub
     if (stokes_vector_length(st, 0) != h->pk.npk) return STOKES_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = warmstart_predict(h, b, x, stream);
-    // SQMR stays the judge.  A guess is kept only if it lowers both the residual, ||b - L x0|| <
+    // SQMR decides convergence as always.  A guess is kept only if it lowers both the residual, ||b - L x0|| <
     // ||b|| (the tolerance is relative to ||b||, and a reduction far beyond the V-cycle's own
     // precision cannot be asked of the preconditioned iteration), and SQMR's first quantity
     // tau_0 = ||M (b - L x0)|| (M the V-cycle) below its value for x0 = 0, ||M b||

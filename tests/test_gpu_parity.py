@@ -199,6 +199,20 @@ def test_persistent_vanka_matches_per_colour_launches():
     Sc.close()
 
 
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+def test_cluster_vanka_sweep_matches_per_colour_launches(cluster):
+    # every level's symmetric Vanka sweep in one thread-block cluster with hardware barriers
+    Sp = smg.Stokes(48, precision=smg.PREC_FP32, autotune=False)
+    Sc = smg.Stokes(48, precision=smg.PREC_FP32, autotune=False)
+    for l in range(Sc.levels - 1):
+        smg.stokes_set_level_schedule(Sc.h, l, 2, cluster)
+        assert smg.stokes_level_schedule(Sc.h, l)[:2] == (2, cluster)
+    s = cuda(np.random.default_rng(28).standard_normal(Sc.n))
+    assert float(torch.max(torch.abs(Sp.precondition(s) - Sc.precondition(s)))) == 0.0
+    Sp.close()
+    Sc.close()
+
+
 @pytest.mark.parametrize("precision", [smg.PREC_FP64, smg.PREC_FP32, smg.PREC_MIXED_BF16])
 def test_autotuned_schedule_is_bit_identical(precision):
     # the autotuner only picks how the Vanka sweeps are launched, never what they compute
