@@ -71,44 +71,95 @@ __device__ __forceinline__ bool thread_entry(const Lev &L, int gy, int &c, int &
 
 // ------------------------------------------------------------------------------------------
 // y = L~x or b - L~x on every packed entry (0 off the unknowns); x must hold 0 off the unknowns.
-// Cell-centric: one thread per position (i,j) marching KZ planes, four entries per position.
+//
+// One entry per thread, blockIdx.z = 4 k + component.  The component is dispatched once at the top
+// of the kernel, so every extent, stride and guard of the entry's row is specialised at compile
+// time, and offsets within a component are IDX = 32-bit integers whenever the largest component
+// has fewer than 2^31 entries (the kernels are instruction-bound, not DRAM-bound: 32-bit offsets
+// halve the address arithmetic of the neighbour loads).
 
-// one entry per thread: blockIdx.z = 4 k + component, so the component is a compile-time branch
-// and no integer division is needed; one plane per thread keeps registers low and occupancy high
-template <class T, int OPX>
-__device__ __forceinline__ bool entry_eval(const T *__restrict__ x, const Lev &L, int c, int i, int j, int k,
-                                           const Coef<T> &K, long long &q, T &v) {
-    if (!(i < ext(L, c, 0) && j < ext(L, c, 1) && k < ext(L, c, 2))) return false;
-    q = pidx(L, c, i, j, k);
-    v = T(0);
-    if (!active(L, c, i, j, k)) return true;
-    // OP_A_B: faces A u only, cells -div u only (no pressure is loaded)
-    constexpr bool P = OPX == OP_APPLY;
-    switch (c) {
-    case 0: v = face_Lx_fast<T, 0, P>(x, L, i, j, k, K); break;
-    case 1: v = face_Lx_fast<T, 1, P>(x, L, i, j, k, K); break;
-    case 2: v = face_Lx_fast<T, 2, P>(x, L, i, j, k, K); break;
-    default: v = cell_Lx_fast<T, P>(x, L, i, j, k, K);
+// row C of L~x at (i,j,k) (an unknown); P = false: faces A u only, cells -div u only
+template <class T, int C, bool P, class IDX>
+__device__ __forceinline__ T row_at(const T *__restrict__ x, const Lev &L, int i, int j, int k, const Coef<T> &K) {
+    if constexpr (C < 3) {
+        const IDX sy = (IDX)(L.nx + (C == 0)), sz = sy * (IDX)(L.ny + (C == 1));
+        const T *xc = x + L.off[C] + ((IDX)i + sy * (IDX)j + sz * (IDX)k);
+        T s = T(6) * xc[0];
+        if (C == 0) s -= xc[-1] + xc[1];
+        else s -= (i > 0 ? xc[-1] : T(0)) + (i < L.nx - 1 ? xc[1] : T(0));
+        if (C == 1) s -= xc[-sy] + xc[sy];
+        else s -= (j > 0 ? xc[-sy] : T(0)) + (j < L.ny - 1 ? xc[sy] : T(0));
+        if (C == 2) s -= xc[-sz] + xc[sz];
+        else s -= (k > 0 ? xc[-sz] : T(0)) + (k < L.nz - 1 ? xc[sz] : T(0));
+        if constexpr (!P) {
+            return K.eh2 * s;
+        } else {
+            const IDX cy = (IDX)L.nx, cz = cy * (IDX)L.ny;
+            const T *pc = x + L.off[3] + ((IDX)i + cy * (IDX)j + cz * (IDX)k);
+            const IDX ps = C == 0 ? (IDX)1 : (C == 1 ? cy : cz);
+            return K.eh2 * s + K.ih * (pc[0] - pc[-ps]);
+        }
+    } else {
+        const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
+        const T *u = x + L.off[0] + ((IDX)i + (nx + 1) * ((IDX)j + ny * (IDX)k));
+        const T *v = x + L.off[1] + ((IDX)i + nx * ((IDX)j + (ny + 1) * (IDX)k));
+        const T *w = x + L.off[2] + ((IDX)i + nx * ((IDX)j + ny * (IDX)k));
+        const T div = (u[1] - u[0]) + (v[nx] - v[0]) + (w[nx * ny] - w[0]);
+        if constexpr (!P) return -K.ih * div;
+        else return -K.ih * div - K.gam * x[L.off[3] + ((IDX)i + nx * ((IDX)j + ny * (IDX)k))];
     }
+}
+// does entry (C; i,j,k) exist in the packed array, and is it an unknown?
+template <int C> __device__ __forceinline__ bool entry_exists(const Lev &L, int i, int j, int k) {
+    return i < L.nx + (C == 0) && j < L.ny + (C == 1) && k < L.nz + (C == 2);
+}
+template <int C> __device__ __forceinline__ bool entry_active(const Lev &L, int i, int j, int k) {
+    if (C == 0) return i >= 1 && i <= L.nx - 1;
+    if (C == 1) return j >= 1 && j <= L.ny - 1;
+    if (C == 2) return k >= 1 && k <= L.nz - 1;
     return true;
 }
+template <int C, class IDX> __device__ __forceinline__ long long entry_index(const Lev &L, int i, int j, int k) {
+    const IDX sy = (IDX)(L.nx + (C == 0)), sz = sy * (IDX)(L.ny + (C == 1));
+    return L.off[C] + (long long)((IDX)i + sy * (IDX)j + sz * (IDX)k);
+}
 inline dim3 entry_grid(const Lev &L) { return dim3(cdiv(L.nx + 1, BX), cdiv(L.ny + 1, BY), 4 * (L.nz + 1)); }
+// offsets of every component fit 32 bits
+inline bool idx32(const Lev &L) { return (long long)(L.nx + 1) * (L.ny + 1) * (L.nz + 1) < (1LL << 31); }
 
-template <class T, class TB>
+template <class T, class TB, int C, class IDX>
+__device__ __forceinline__ void apply_entry(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
+                                            TB *__restrict__ y, const Coef<T> &K, int i, int j, int k) {
+    if (!entry_exists<C>(L, i, j, k)) return;
+    const long long q = entry_index<C, IDX>(L, i, j, k);
+    T v = T(0);
+    if (entry_active<C>(L, i, j, k)) {
+        v = row_at<T, C, true, IDX>(x, L, i, j, k, K);
+        if (b) v = T(ldv(b[q])) - v;
+    }
+    y[q] = cvt<TB>(v);
+}
+
+template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                   TB *__restrict__ y, Coef<T> K) {
     pdl_wait();
-    int c = blockIdx.z & 3, k = blockIdx.z >> 2;
-    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    long long q;
-    T v;
-    if (!entry_eval<T, OP_APPLY>(x, L, c, i, j, k, K, q, v)) return;
-    y[q] = cvt<TB>(active(L, c, i, j, k) ? (b ? T(ldv(b[q])) - v : v) : T(0));
+    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    switch (c) {
+    case 0: apply_entry<T, TB, 0, IDX>(L, x, b, y, K, i, j, k); break;
+    case 1: apply_entry<T, TB, 1, IDX>(L, x, b, y, K, i, j, k); break;
+    case 2: apply_entry<T, TB, 2, IDX>(L, x, b, y, K, i, j, k); break;
+    default: apply_entry<T, TB, 3, IDX>(L, x, b, y, K, i, j, k);
+    }
 }
 
 template <class T, class TB>
 void launch_apply(const Lev &L, const T *x, const TB *b, TB *y, double gam, cudaStream_t s) {
-    launch_k(k_apply<T, TB>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+    if (idx32(L))
+        launch_k(k_apply<T, TB, int>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+    else
+        launch_k(k_apply<T, TB, long long>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -274,27 +325,40 @@ __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, 
 // (M_{.c}^T r with the full column of M).  Same-colour cells read none of each other's values.
 // The same launch also finishes the forward sweep: the neighbour-pressure part of the last
 // colours (gather form of k_dgs_p_gather), which the prep never reads.  One entry per thread as k_apply.
-template <class T, class TB>
+template <class T, class TB, int C, class IDX>
+__device__ __forceinline__ void prep_entry(const Lev &L, T *__restrict__ x, const TB *__restrict__ b,
+                                           TB *__restrict__ gh, const T *__restrict__ delta, const Coef<T> &K, int i,
+                                           int j, int k) {
+    if (!entry_exists<C>(L, i, j, k)) return;
+    const long long q = entry_index<C, IDX>(L, i, j, k);
+    T v = T(0);
+    if (entry_active<C>(L, i, j, k)) v = T(ldv(b[q])) - row_at<T, C, false, IDX>(x, L, i, j, k, K);
+    gh[q] = cvt<TB>(v);
+    if (C == 3 && delta) {
+        const IDX sy = (IDX)L.nx, sz = sy * (IDX)L.ny;
+        const T *dc = delta + ((IDX)i + sy * (IDX)j + sz * (IDX)k);
+        const bool v2 = in_v2_cell(L, i, j, k);
+        const int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+        T g = T(0);
+        if (!v2 || !(colour & 1)) g += (i > 0 ? dc[-1] : T(0)) + (i < L.nx - 1 ? dc[1] : T(0));
+        if (!v2 || !(colour & 2)) g += (j > 0 ? dc[-sy] : T(0)) + (j < L.ny - 1 ? dc[sy] : T(0));
+        if (!v2 || !(colour & 4)) g += (k > 0 ? dc[-sz] : T(0)) + (k < L.nz - 1 ? dc[sz] : T(0));
+        if (g != T(0)) x[q] -= K.eh2 * g;
+    }
+}
+
+template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                            TB *__restrict__ gh, const T *__restrict__ delta,
                                                            Coef<T> K) {
     pdl_wait();
-    int c = blockIdx.z & 3, k = blockIdx.z >> 2;
-    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    long long q;
-    T v;
-    if (!entry_eval<T, OP_A_B>(x, L, c, i, j, k, K, q, v)) return;
-    gh[q] = cvt<TB>(active(L, c, i, j, k) ? T(ldv(b[q])) - v : T(0));
-    if (c == 3 && delta) {
-        long long t = cell_lin(L, i, j, k);
-        bool v2 = in_v2_cell(L, i, j, k);
-        int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-        long long sy = L.nx, sz = (long long)L.nx * L.ny;
-        T g = T(0);
-        if (!v2 || !(colour & 1)) g += (i > 0 ? delta[t - 1] : T(0)) + (i < L.nx - 1 ? delta[t + 1] : T(0));
-        if (!v2 || !(colour & 2)) g += (j > 0 ? delta[t - sy] : T(0)) + (j < L.ny - 1 ? delta[t + sy] : T(0));
-        if (!v2 || !(colour & 4)) g += (k > 0 ? delta[t - sz] : T(0)) + (k < L.nz - 1 ? delta[t + sz] : T(0));
-        if (g != T(0)) x[q] -= K.eh2 * g;
+    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    switch (c) {
+    case 0: prep_entry<T, TB, 0, IDX>(L, x, b, gh, delta, K, i, j, k); break;
+    case 1: prep_entry<T, TB, 1, IDX>(L, x, b, gh, delta, K, i, j, k); break;
+    case 2: prep_entry<T, TB, 2, IDX>(L, x, b, gh, delta, K, i, j, k); break;
+    default: prep_entry<T, TB, 3, IDX>(L, x, b, gh, delta, K, i, j, k);
     }
 }
 
@@ -345,7 +409,12 @@ template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, 
 }
 template <class T, class TB>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const TB *b, TB *gh, const T *delta, cudaStream_t s) {
-    launch_k(k_dgs_p_bwd_prep<T, TB>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta, coef<T>(L, L.gamma));
+    if (idx32(L))
+        launch_k(k_dgs_p_bwd_prep<T, TB, int>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta,
+                 coef<T>(L, L.gamma));
+    else
+        launch_k(k_dgs_p_bwd_prep<T, TB, long long>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta,
+                 coef<T>(L, L.gamma));
 }
 template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s) {
     int lo[3], cnt[3];
