@@ -215,40 +215,48 @@ void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaS
 // Cell-centric: the thread of V2 cell (i,j,k) of the given parity updates its low faces u, v, w (all
 // three share the cell's parity), each if it lies in that component's V2 range.  Inside the V2
 // cell range every stencil neighbour exists, so no guards are needed.
-template <class T, class TB>
-__device__ __forceinline__ void dgs_face(T *__restrict__ x, const TB *__restrict__ b, long long q, long long sy,
-                                         long long sz, T pc, T pm, const Coef<T> &K) {
-    T s = T(6) * x[q] - x[q - 1] - x[q + 1] - x[q - sy] - x[q + sy] - x[q - sz] - x[q + sz];
-    T r = T(ldv(b[q])) - (K.eh2 * s + K.ih * (pc - pm));
-    x[q] += r / (T(6) * K.eh2);
+template <class T, class TB, class IDX>
+__device__ __forceinline__ void dgs_face(T *__restrict__ xq, const TB *__restrict__ bq, IDX sy, IDX sz, T pc, T pm,
+                                         const Coef<T> &K) {
+    T s = T(6) * xq[0] - xq[-1] - xq[1] - xq[-sy] - xq[sy] - xq[-sz] - xq[sz];
+    T r = T(ldv(bq[0])) - (K.eh2 * s + K.ih * (pc - pm));
+    xq[0] += r / (T(6) * K.eh2);
 }
 
-template <class T, class TB>
+template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, const TB *__restrict__ b, int parity,
                                                   Coef<T> K) {
     pdl_wait();
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
-    int j = 1 + blockIdx.y * BY + threadIdx.y;
-    if (j > ny - 2) return;
-    const long long lnx = nx, lny = ny;
-    const long long uy = lnx + 1, uz = (lnx + 1) * lny, vy = lnx, vz = lnx * (lny + 1), wz = lnx * lny;
-    {
-        int k = 1 + blockIdx.z;
-        int i = 1 + 2 * (blockIdx.x * BX + threadIdx.x);
-        i += (i + j + k + parity) & 1;
-        if (i > nx - 2) return;
-        long long pq = L.off[3] + i + lnx * (j + lny * k);
-        T pc = x[pq];
-        if (i >= 2) dgs_face(x, b, L.off[0] + i + uy * j + uz * k, uy, uz, pc, x[pq - 1], K);
-        if (j >= 2) dgs_face(x, b, L.off[1] + i + vy * j + vz * k, vy, vz, pc, x[pq - lnx], K);
-        if (k >= 2) dgs_face(x, b, L.off[2] + i + lnx * j + wz * k, lnx, wz, pc, x[pq - lnx * lny], K);
+    const int j = 1 + blockIdx.y * BY + threadIdx.y;
+    if (j > L.ny - 2) return;
+    const int k = 1 + blockIdx.z;
+    int i = 1 + 2 * (blockIdx.x * BX + threadIdx.x);
+    i += (i + j + k + parity) & 1;
+    if (i > L.nx - 2) return;
+    const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
+    const IDX uy = nx + 1, uz = (nx + 1) * ny, vz = nx * (ny + 1), wz = nx * ny;
+    const IDX ci = (IDX)i, cj = (IDX)j, ck = (IDX)k;
+    const T *pp = x + L.off[3] + (ci + nx * (cj + ny * ck));
+    const T pc = pp[0];
+    if (i >= 2) {
+        const IDX o = ci + uy * cj + uz * ck;
+        dgs_face<T, TB, IDX>(x + L.off[0] + o, b + L.off[0] + o, uy, uz, pc, pp[-1], K);
+    }
+    if (j >= 2) {
+        const IDX o = ci + nx * cj + vz * ck;
+        dgs_face<T, TB, IDX>(x + L.off[1] + o, b + L.off[1] + o, nx, vz, pc, pp[-nx], K);
+    }
+    if (k >= 2) {
+        const IDX o = ci + nx * cj + wz * ck;
+        dgs_face<T, TB, IDX>(x + L.off[2] + o, b + L.off[2] + o, nx, wz, pc, pp[-wz], K);
     }
 }
 
 template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, int parity, cudaStream_t s) {
     if (L.nx < 3 || L.ny < 3 || L.nz < 3) return;
     dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), L.nz - 2);
-    launch_k(k_dgs_u<T, TB>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
+    if (idx32(L)) launch_k(k_dgs_u<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
+    else launch_k(k_dgs_u<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
 }
 
 // Alg. 2 pressure block, one colour (i mod 2, j mod 2, k mod 2):
@@ -258,37 +266,40 @@ template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, 
 // The neighbour-pressure part is applied in gather form: a cell first collects the deltas of
 // neighbours whose colour came earlier in this sweep (pre-gather); k_dgs_p_gather applies the rest
 // after the last colour.  delta is stored per cell and stays 0 outside V2.
-template <class T, class TB>
+template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                    T *__restrict__ delta, int colour, Coef<T> K, T dP) {
     pdl_wait();
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
-    int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
+    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
     if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
-    int i = lo[0] + 2 * ti, j = lo[1] + 2 * tj, k = lo[2] + 2 * tk;
-    long long cl = cell_lin(L, i, j, k);
-    long long qp = L.off[3] + cl;
-    long long sy = L.nx, sz = (long long)L.nx * L.ny;
+    const IDX i = lo[0] + 2 * ti, j = lo[1] + 2 * tj, k = lo[2] + 2 * tk;
+    const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
+    const IDX sy = nx, sz = nx * ny;
+    const IDX cl = i + nx * (j + ny * k);
+    T *dc = delta + cl;
     T g = T(0);
-    if (colour & 1) g += delta[cl - 1] + delta[cl + 1];
-    if (colour & 2) g += delta[cl - sy] + delta[cl + sy];
-    if (colour & 4) g += delta[cl - sz] + delta[cl + sz];
-    T p = x[qp] - K.eh2 * g;
-    long long u0 = pidx(L, 0, i, j, k), v0 = pidx(L, 1, i, j, k), w0 = pidx(L, 2, i, j, k);
-    long long vs = L.nx, ws = (long long)L.nx * L.ny;
-    T div = (x[u0 + 1] - x[u0]) + (x[v0 + vs] - x[v0]) + (x[w0 + ws] - x[w0]);
-    T r = T(ldv(b[qp])) + K.ih * div + K.gam * p;
-    T dl = r / dP;
-    T fd = dl * K.ih;
-    x[u0] -= fd;
-    x[u0 + 1] += fd;
-    x[v0] -= fd;
-    x[v0 + vs] += fd;
-    x[w0] -= fd;
-    x[w0 + ws] += fd;
-    x[qp] = p + T(6) * K.eh2 * dl;
-    delta[cl] = dl;
+    if (colour & 1) g += dc[-1] + dc[1];
+    if (colour & 2) g += dc[-sy] + dc[sy];
+    if (colour & 4) g += dc[-sz] + dc[sz];
+    T *pp = x + L.off[3] + cl;
+    const T p = pp[0] - K.eh2 * g;
+    T *u = x + L.off[0] + (i + (nx + 1) * (j + ny * k));
+    T *v = x + L.off[1] + (i + nx * (j + (ny + 1) * k));
+    T *w = x + L.off[2] + (i + nx * (j + ny * k));
+    const T div = (u[1] - u[0]) + (v[sy] - v[0]) + (w[sz] - w[0]);
+    const T r = T(ldv(b[L.off[3] + cl])) + K.ih * div + K.gam * p;
+    const T dl = r / dP;
+    const T fd = dl * K.ih;
+    u[0] -= fd;
+    u[1] += fd;
+    v[0] -= fd;
+    v[sy] += fd;
+    w[0] -= fd;
+    w[sz] += fd;
+    pp[0] = p + T(6) * K.eh2 * dl;
+    dc[0] = dl;
 }
 
 template <class T>
@@ -362,33 +373,35 @@ __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict_
     }
 }
 
-template <class T, class TB>
+template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const TB *__restrict__ ghs, int colour,
                                                    Coef<T> K, T dP) {
     pdl_wait();
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
-    int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
+    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
     if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
-    int i = lo[0] + 2 * ti, j = lo[1] + 2 * tj, k = lo[2] + 2 * tk;
-    long long sy = L.nx, sz = (long long)L.nx * L.ny;
-    long long qc = L.off[3] + cell_lin(L, i, j, k);
-    const T *p = x;
-    T pc = p[qc], pxm = p[qc - 1], pxp = p[qc + 1], pym = p[qc - sy], pyp = p[qc + sy], pzm = p[qc - sz],
-      pzp = p[qc + sz];
-    auto gh = [&](long long q) { return T(ldv(ghs[q])); };
-    long long u0 = pidx(L, 0, i, j, k), v0 = pidx(L, 1, i, j, k), w0 = pidx(L, 2, i, j, k);
-    long long vs = L.nx, ws = (long long)L.nx * L.ny;
+    const IDX i = lo[0] + 2 * ti, j = lo[1] + 2 * tj, k = lo[2] + 2 * tk;
+    const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
+    const IDX sy = nx, sz = nx * ny;
+    const IDX cl = i + nx * (j + ny * k);
+    T *pp = x + L.off[3] + cl;
+    const T pc = pp[0], pxm = pp[-1], pxp = pp[1], pym = pp[-sy], pyp = pp[sy], pzm = pp[-sz], pzp = pp[sz];
+    const TB *gc = ghs + L.off[3] + cl;
+    const TB *gu = ghs + L.off[0] + (i + (nx + 1) * (j + ny * k));
+    const TB *gv = ghs + L.off[1] + (i + nx * (j + (ny + 1) * k));
+    const TB *gw = ghs + L.off[2] + (i + nx * (j + ny * k));
+    auto G = [](TB v) { return T(ldv(v)); };
     // face residuals r_f = g_f - (p_plus - p_minus)/h
-    T rul = gh(u0) - K.ih * (pc - pxm), ruh = gh(u0 + 1) - K.ih * (pxp - pc);
-    T rvl = gh(v0) - K.ih * (pc - pym), rvh = gh(v0 + vs) - K.ih * (pyp - pc);
-    T rwl = gh(w0) - K.ih * (pc - pzm), rwh = gh(w0 + ws) - K.ih * (pzp - pc);
+    const T rul = G(gu[0]) - K.ih * (pc - pxm), ruh = G(gu[1]) - K.ih * (pxp - pc);
+    const T rvl = G(gv[0]) - K.ih * (pc - pym), rvh = G(gv[sy]) - K.ih * (pyp - pc);
+    const T rwl = G(gw[0]) - K.ih * (pc - pzm), rwh = G(gw[sz]) - K.ih * (pzp - pc);
     // cell residuals r_n = h_n + gamma p_n
-    T rc = gh(qc) + K.gam * pc;
-    T rn = (gh(qc - 1) + K.gam * pxm) + (gh(qc + 1) + K.gam * pxp) + (gh(qc - sy) + K.gam * pym) +
-           (gh(qc + sy) + K.gam * pyp) + (gh(qc - sz) + K.gam * pzm) + (gh(qc + sz) + K.gam * pzp);
-    T s = K.ih * ((ruh - rul) + (rvh - rvl) + (rwh - rwl)) + K.eh2 * (T(6) * rc - rn);
-    x[qc] = pc + s / dP;
+    const T rc = G(gc[0]) + K.gam * pc;
+    const T rn = (G(gc[-1]) + K.gam * pxm) + (G(gc[1]) + K.gam * pxp) + (G(gc[-sy]) + K.gam * pym) +
+                 (G(gc[sy]) + K.gam * pyp) + (G(gc[-sz]) + K.gam * pzm) + (G(gc[sz]) + K.gam * pzp);
+    const T s = K.ih * ((ruh - rul) + (rvh - rvl) + (rwh - rwl)) + K.eh2 * (T(6) * rc - rn);
+    pp[0] = pc + s / dP;
 }
 
 template <class T> static T dgs_pressure_diag(const Lev &L) {
@@ -401,7 +414,12 @@ void launch_dgs_p_fwd(const Lev &L, T *x, const TB *b, T *delta, int colour, cud
     v2_colour_range(L, colour, lo, cnt);
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
     dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
-    launch_k(k_dgs_p_fwd<T, TB>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
+    if (idx32(L))
+        launch_k(k_dgs_p_fwd<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
+                 dgs_pressure_diag<T>(L));
+    else
+        launch_k(k_dgs_p_fwd<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour,
+                 coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
 }
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s) {
     dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz);
@@ -421,7 +439,12 @@ template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB 
     v2_colour_range(L, colour, lo, cnt);
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
     dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
-    launch_k(k_dgs_p_bwd<T, TB>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
+    if (idx32(L))
+        launch_k(k_dgs_p_bwd<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
+                 dgs_pressure_diag<T>(L));
+    else
+        launch_k(k_dgs_p_bwd<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
+                 dgs_pressure_diag<T>(L));
 }
 
 // ------------------------------------------------------------------------------------------
