@@ -83,8 +83,9 @@ typedef struct {
                              STOKES_ERR_TIMEOUT) */
     int autotune;  /* 1 (default): at creation, time the Vanka schedule candidates of every smoothed
                       level (per-colour launches; one cooperative sweep with up to 5 grid sizes; one
-                      cluster of 4, 8 or 16 CTAs) and keep the fastest; all candidates give
-                      bit-identical results.  0: per-colour launches. */
+                      cluster of 4, 8 or 16 CTAs; one block on a shared-memory copy of a small
+                      level) and keep the fastest; all candidates give bit-identical results.
+                      0: per-colour launches. */
 } stokes_opts_t;
 
 typedef struct {
@@ -149,12 +150,14 @@ int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rh
 /* the Vanka schedule of a smoothed level (chosen by the autotuner): *mode 0 = two launches per
  * colour, 1 = one cooperative launch per symmetric sweep with *blocks thread blocks (grid barrier),
  * 2 = one launch per symmetric sweep in a single thread-block cluster of *blocks CTAs (hardware
- * cluster barriers); *ms = the autotuner's time per symmetric sweep (0 if not measured).  Any
- * output pointer may be NULL. */
+ * cluster barriers), 3 = one launch per symmetric sweep in one thread block working on a
+ * shared-memory copy of the level (small levels only; *blocks = 1); *ms = the autotuner's time per
+ * symmetric sweep (0 if not measured).  Any output pointer may be NULL. */
 int stokes_level_schedule(stokes_t h, int level, int *mode, int *blocks, float *ms);
 /* override the schedule of one level (mode and blocks as above; blocks <= the co-resident limit for
- * mode 1, <= 16 for mode 2); the handle's captured graphs are re-captured on next use.  All
- * schedules compute the same bits. */
+ * mode 1, <= 16 for mode 2; mode 3 returns STOKES_ERR_UNSUPPORTED if the level does not fit in
+ * shared memory); the handle's captured graphs are re-captured on next use.  All schedules compute
+ * the same bits. */
 int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks);
 
 /* *out = ||b - L x||_2 (FP64, deterministic reduction); synchronises the stream.  Uses the

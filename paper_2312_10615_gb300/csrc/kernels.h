@@ -50,6 +50,12 @@ template <class T, class TB> int vanka_sweep_blocks_per_sm();
 // one symmetric Vanka sweep (x sweeps) in a single thread-block cluster of `cluster` CTAs x 1024
 // threads separated by hardware cluster barriers (no software wait); returns the launch status
 template <class T, class TB> cudaError_t vanka_cluster_prepare();
+// one symmetric Vanka sweep (x sweeps) in one 1024-thread block on a shared-memory copy of the level
+// (x, b, corrections); vanka_smem_prepare sets the shared-memory opt-in and says whether it fits
+template <class T, class TB> bool vanka_smem_prepare(const Lev &L, int cap);
+template <class T, class TB>
+void launch_vanka_smem(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, int cap, int sweeps,
+                       cudaStream_t s);
 template <class T, class TB>
 cudaError_t launch_vanka_cluster(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr,
                                  int cap, int sweeps, int cluster, cudaStream_t s);

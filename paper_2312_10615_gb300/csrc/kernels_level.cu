@@ -640,6 +640,68 @@ void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists
     cudaLaunchKernelEx(&cfg, k_vanka_sweep<T, TB>, L, x, b, lists, kinv, corr, cap, coef<T>(L, L.gamma), sweeps, bar);
 }
 
+// ---- one symmetric Vanka sweep in one thread block with the level in shared memory ----
+// Small levels only (x, b and the corrections must fit in shared memory): the level's x and b are
+// copied in, the 16 colour steps run on the shared copies with __syncthreads() between the compute
+// and apply steps, and x is copied back.  The per-lane arithmetic is the same code as the global
+// version (generic pointers), so the result is bit-identical.
+template <class T, class TB> size_t vanka_smem_bytes(const Lev &L, int cap) {
+    const size_t xb = ((size_t)L.n * sizeof(T) + 15) / 16 * 16, bb = ((size_t)L.n * sizeof(TB) + 15) / 16 * 16;
+    return xb + bb + (size_t)7 * cap * sizeof(T);
+}
+
+template <class T, class TB>
+__global__ void __launch_bounds__(1024) k_vanka_smem(Lev L, T *__restrict__ x, const TB *__restrict__ b,
+                                                     VankaLists lists, const T *__restrict__ kinv, int cap, Coef<T> K,
+                                                     int sweeps) {
+    extern __shared__ __align__(16) unsigned char vsm[];
+    T *xs = reinterpret_cast<T *>(vsm);
+    TB *bs = reinterpret_cast<TB *>(vsm + ((size_t)L.n * sizeof(T) + 15) / 16 * 16);
+    T *cs = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(bs) + ((size_t)L.n * sizeof(TB) + 15) / 16 * 16);
+    pdl_wait();
+    const int n = (int)L.n;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        xs[e] = x[e];
+        bs[e] = b[e];
+    }
+    __syncthreads();
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);
+    for (int sw = 0; sw < sweeps; ++sw)
+        for (int ph = 0; ph < 16; ++ph) {
+            const int col = ph < 8 ? ph : 15 - ph;
+            const int nc = lists.count[col];
+            if (nc == 0) continue;  // uniform across the block
+            const int *cells = lists.cells[col];
+            for (int t = threadIdx.x; (t >> 3) < nc; t += blockDim.x)
+                vanka_compute_lane(L, (const T *)xs, (const TB *)bs, cells[t >> 3], t & 7, gmask, kinv, cs, cap, t >> 3, K);
+            __syncthreads();
+            for (int t = threadIdx.x; (t >> 3) < nc; t += blockDim.x)
+                vanka_apply_lane(L, xs, cells[t >> 3], t & 7, (const T *)cs, cap, t >> 3);
+            __syncthreads();
+        }
+    for (int e = threadIdx.x; e < n; e += blockDim.x) x[e] = xs[e];
+}
+
+// the dynamic shared-memory opt-in, set once outside any capture; false if the level does not fit
+template <class T, class TB> bool vanka_smem_prepare(const Lev &L, int cap) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t need = vanka_smem_bytes<T, TB>(L, cap);
+    if (need > (size_t)optin || L.n >= (1LL << 31)) return false;
+    // the attribute is per kernel, shared by every handle: always the device maximum
+    return cudaFuncSetAttribute(k_vanka_smem<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) ==
+           cudaSuccess;
+}
+
+template <class T, class TB>
+void launch_vanka_smem(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, int cap, int sweeps,
+                       cudaStream_t s) {
+    if (sweeps <= 0) return;
+    launch_k(k_vanka_smem<T, TB>, dim3(1), dim3(1024), vanka_smem_bytes<T, TB>(L, cap), s, L, x, b, lists, kinv, cap,
+             coef<T>(L, L.gamma), sweeps);
+}
+
 // ---- one symmetric Vanka sweep in one thread-block cluster (small levels) ----
 // The cluster's CTAs stride over the cells of a colour; hardware cluster barriers (release/acquire
 // at cluster scope) separate the compute and apply steps, so no launch and no software spin sits
@@ -917,6 +979,9 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template void launch_vanka_sweep<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, T *, int,  \
                                             int, GridBarrier *, int, cudaStream_t);                                 \
     template cudaError_t vanka_cluster_prepare<T, TB>();                                                          \
+    template bool vanka_smem_prepare<T, TB>(const Lev &, int);                                                     \
+    template void launch_vanka_smem<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, int, int,   \
+                                           cudaStream_t);                                                          \
     template cudaError_t launch_vanka_cluster<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *,   \
                                                      T *, int, int, int, cudaStream_t);                             \
     template int vanka_sweep_blocks_per_sm<T, TB>();

@@ -251,6 +251,12 @@ template <class T, class TB> void vanka_colour(stokes_s *h, int l, int col, cuda
 // `sweeps` symmetric Vanka sweeps (App. C: colours 0..7 then 7..0)
 template <class T, class TB> void vanka_sym(stokes_s *h, int l, cudaStream_t s, int sweeps = 1) {
     LevelBuf &B = h->lev[l];
+    if (B.vmode == 3 && !h->vanka_persistent) {
+        prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
+            launch_vanka_smem<T, TB>(B.L, (T *)B.x, (const TB *)B.b, B.lists, (const T *)B.kinv, B.vcap, sweeps, s);
+        });
+        return;
+    }
     if (B.vmode == 2 && !h->vanka_persistent) {
         prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
             launch_vanka_cluster<T, TB>(B.L, (T *)B.x, (const TB *)B.b, B.lists, (const T *)B.kinv, (T *)B.corr, B.vcap,
@@ -468,6 +474,16 @@ int autotune_vanka(stokes_s *h, int nsm) {
                     best_blocks = nb;
                 }
             }
+            // one block on a shared-memory copy of the level, where it fits
+            if (vanka_smem_prepare<T, TB>(B.L, B.vcap)) {
+                const float ms = time_vanka<T, TB>(h, l, 3, 1, s);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    best_mode = 3;
+                    best_blocks = 1;
+                }
+            }
+            cudaGetLastError();
             // one cluster of 4, 8 or 16 CTAs: worth it only where a colour fits in a few passes
             const int cl_need = (int)((8LL * mx + 1023) / 1024);
             for (int cl : {4, 8, 16}) {
@@ -1048,9 +1064,20 @@ int stokes_level_schedule(stokes_t h, int level, int *mode, int *blocks, float *
 }
 
 int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
-    if (!h || level < 0 || level >= h->nlev() - 1 || mode < 0 || mode > 2) return STOKES_ERR_INVALID_ARG;
+    if (!h || level < 0 || level >= h->nlev() - 1 || mode < 0 || mode > 3) return STOKES_ERR_INVALID_ARG;
     if (mode == 1 && (h->vanka_max_blocks <= 0 || blocks < 1 || blocks > h->vanka_max_blocks)) return STOKES_ERR_INVALID_ARG;
     if (mode == 2 && (blocks < 1 || blocks > 16)) return STOKES_ERR_INVALID_ARG;
+    if (mode == 3) {
+        DeviceGuard dg(h->dev);
+        const LevelBuf &B = h->lev[level];
+        bool fits = false;
+        if (h->prec == STOKES_PREC_FP64) fits = vanka_smem_prepare<double, double>(B.L, B.vcap);
+        else if (level < h->nbf) fits = vanka_smem_prepare<float, bf16>(B.L, B.vcap);
+        else fits = vanka_smem_prepare<float, float>(B.L, B.vcap);
+        cudaGetLastError();
+        if (!fits) return STOKES_ERR_UNSUPPORTED;
+        blocks = 1;
+    }
     if (mode == 2 && blocks > 8) {
         DeviceGuard dg(h->dev);
         if (h->prec == STOKES_PREC_FP64) vanka_cluster_prepare<double, double>();

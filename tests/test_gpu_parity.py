@@ -213,6 +213,24 @@ def test_cluster_vanka_sweep_matches_per_colour_launches(cluster):
     Sc.close()
 
 
+def test_shared_memory_vanka_sweep_matches_per_colour_launches():
+    # small levels: the whole symmetric sweep in one block on a shared-memory copy of the level
+    Sp = smg.Stokes(32, precision=smg.PREC_FP32, autotune=False)
+    Sm = smg.Stokes(32, precision=smg.PREC_FP32, autotune=False)
+    smg.stokes_set_level_schedule(Sm.h, 1, 3)  # the 16^3 level fits
+    assert smg.stokes_level_schedule(Sm.h, 1)[:2] == (3, 1)
+    with pytest.raises(smg.StokesError):
+        smg.stokes_set_level_schedule(Sm.h, 0, 3)  # 32^3 in FP32 does not fit in 227 KB
+    s = cuda(np.random.default_rng(29).standard_normal(Sm.n))
+    assert float(torch.max(torch.abs(Sp.precondition(s) - Sm.precondition(s)))) == 0.0
+    b = Sm.rhs(synthetic.bumps(32, seed=5, device=DEV)["f"], None)
+    xp, ip = Sp.solve(b, tol=1e-8)
+    xm, im = Sm.solve(b, tol=1e-8)
+    assert ip.iterations == im.iterations and float(torch.max(torch.abs(xp - xm))) == 0.0
+    Sp.close()
+    Sm.close()
+
+
 @pytest.mark.parametrize("precision", [smg.PREC_FP64, smg.PREC_FP32, smg.PREC_MIXED_BF16])
 def test_autotuned_schedule_is_bit_identical(precision):
     # the autotuner only picks how the Vanka sweeps are launched, never what they compute
@@ -220,7 +238,7 @@ def test_autotuned_schedule_is_bit_identical(precision):
     Sp = smg.Stokes(64, precision=precision, autotune=False)
     for l in range(Sa.levels - 1):
         mode, blocks, ms = smg.stokes_level_schedule(Sa.h, l)
-        assert mode in (0, 1) and ms > 0 and (mode == 0 or blocks >= 1)
+        assert mode in (0, 1, 2, 3) and ms > 0 and (mode == 0 or blocks >= 1)
     s = cuda(np.random.default_rng(27).standard_normal(Sa.n))
     assert float(torch.max(torch.abs(Sa.precondition(s) - Sp.precondition(s)))) == 0.0
     b = Sa.rhs(synthetic.bumps(64, seed=4, device=DEV)["f"], None)
