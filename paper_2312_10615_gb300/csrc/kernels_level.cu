@@ -460,26 +460,42 @@ __device__ __forceinline__ void unpack_cell(int w, int &i, int &j, int &k) {
 }
 
 // 8 lanes per cell: lane a < 6 owns face a of the patch, lane 6 the pressure, lane 7 idles; the
-// 7 residuals are exchanged with width-8 shuffles and lane a forms row a of K^{-1} r.
+// 7 residuals are exchanged with width-8 shuffles and lane a forms row a of K^{-1} r.  The six face
+// lanes run one code path with the component as data (strides, base and guards selected per lane),
+// so a warp's four cells diverge only between face lanes and the pressure lane.
 template <class T, class TB>
-__global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
-                                                       const int *__restrict__ cells, int ncell,
-                                                       const T *__restrict__ kinv, T *__restrict__ corr, int cap,
-                                                       Coef<T> K) {
-    pdl_wait();
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int slot = t >> 3, a = t & 7;
-    if (slot >= ncell) return;  // whole 8-lane groups leave together
-    unsigned gmask = 0xffu << (threadIdx.x & 24);
+__device__ __forceinline__ T vanka_face_residual(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b, int a,
+                                                 int i, int j, int k, const Coef<T> &K) {
+    const int d = a >> 1, side = a & 1;
+    const int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+    const long long nx = L.nx, ny = L.ny;
+    const long long sy = nx + (d == 0), sz = sy * (ny + (d == 1));
+    const long long q = (d == 0 ? L.off[0] : (d == 1 ? L.off[1] : L.off[2])) + fi + sy * fj + sz * fk;
+    const T *xc = x + q;
+    // neighbours along the face normal always exist (wall faces hold 0); tangential ones only inside
+    const bool xm = d == 0 || fi > 0, xp = d == 0 || fi < L.nx - 1;
+    const bool ym = d == 1 || fj > 0, yp = d == 1 || fj < L.ny - 1;
+    const bool zm = d == 2 || fk > 0, zp = d == 2 || fk < L.nz - 1;
+    T s = T(6) * xc[0];
+    s -= (xm ? xc[-1] : T(0)) + (xp ? xc[1] : T(0));
+    s -= (ym ? xc[-sy] : T(0)) + (yp ? xc[sy] : T(0));
+    s -= (zm ? xc[-sz] : T(0)) + (zp ? xc[sz] : T(0));
+    const T *pc = x + L.off[3] + (fi + nx * (fj + ny * fk));
+    const long long ps = d == 0 ? 1 : (d == 1 ? nx : nx * ny);
+    return T(ldv(b[q])) - (K.eh2 * s + K.ih * (pc[0] - pc[-ps]));
+}
+
+template <class T, class TB>
+__device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
+                                                   int cellw, int a, unsigned gmask, const T *__restrict__ kinv,
+                                                   T *__restrict__ corr, int cap, int slot, const Coef<T> &K) {
     int i, j, k;
-    unpack_cell(cells[slot], i, j, k);
-    int cfg = (i >= 1) | ((i + 1 <= L.nx - 1) << 1) | ((j >= 1) << 2) | ((j + 1 <= L.ny - 1) << 3) |
-              ((k >= 1) << 4) | ((k + 1 <= L.nz - 1) << 5);
+    unpack_cell(cellw, i, j, k);
+    const int cfg = (i >= 1) | ((i + 1 <= L.nx - 1) << 1) | ((j >= 1) << 2) | ((j + 1 <= L.ny - 1) << 3) |
+                    ((k >= 1) << 4) | ((k + 1 <= L.nz - 1) << 5);
     T r = T(0);
     if (a < 6) {
-        int d = a >> 1, side = a & 1;
-        int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-        if ((cfg >> a) & 1) r = T(ldv(b[pidx(L, d, fi, fj, fk)])) - face_Lx_any(x, L, d, fi, fj, fk, K);
+        if ((cfg >> a) & 1) r = vanka_face_residual(L, x, b, a, i, j, k, K);
     } else if (a == 6) {
         r = T(ldv(b[pidx(L, 3, i, j, k)])) - cell_Lx_fast(x, L, i, j, k, K);
     }
@@ -491,21 +507,48 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
 }
 
 template <class T>
+__device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x, int cellw, int a,
+                                                 const T *__restrict__ corr, int cap, int slot) {
+    if (a == 7) return;
+    int i, j, k;
+    unpack_cell(cellw, i, j, k);
+    const long long nx = L.nx, ny = L.ny;
+    long long q;
+    bool act;
+    if (a == 6) {
+        q = L.off[3] + (i + nx * (j + ny * k));
+        act = true;
+    } else {
+        const int d = a >> 1, side = a & 1;
+        const int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+        const long long sy = nx + (d == 0), sz = sy * (ny + (d == 1));
+        q = (d == 0 ? L.off[0] : (d == 1 ? L.off[1] : L.off[2])) + fi + sy * fj + sz * fk;
+        const int nrm = d == 0 ? fi : (d == 1 ? fj : fk), nn = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
+        act = nrm >= 1 && nrm <= nn - 1;
+    }
+    if (act) x[q] += corr[(long long)a * cap + slot];
+}
+
+template <class T, class TB>
+__global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
+                                                       const int *__restrict__ cells, int ncell,
+                                                       const T *__restrict__ kinv, T *__restrict__ corr, int cap,
+                                                       Coef<T> K) {
+    pdl_wait();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slot = t >> 3;
+    if (slot >= ncell) return;  // whole 8-lane groups leave together
+    vanka_compute_lane(L, x, b, cells[slot], t & 7, 0xffu << (threadIdx.x & 24), kinv, corr, cap, slot, K);
+}
+
+template <class T>
 __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, const int *__restrict__ cells,
                                                      int ncell, const T *__restrict__ corr, int cap) {
     pdl_wait();
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int slot = t >> 3, a = t & 7;
-    if (slot >= ncell || a == 7) return;
-    int i, j, k;
-    unpack_cell(cells[slot], i, j, k);
-    if (a == 6) {
-        x[pidx(L, 3, i, j, k)] += corr[6LL * cap + slot];
-        return;
-    }
-    int d = a >> 1, side = a & 1;
-    int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-    if (active(L, d, fi, fj, fk)) x[pidx(L, d, fi, fj, fk)] += corr[(long long)a * cap + slot];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slot = t >> 3;
+    if (slot >= ncell) return;
+    vanka_apply_lane(L, x, cells[slot], t & 7, corr, cap, slot);
 }
 
 template <class T, class TB>
@@ -549,44 +592,6 @@ __device__ __forceinline__ void grid_sync(GridBarrier *bar, unsigned nblocks) {
         }
     }
     __syncthreads();
-}
-
-template <class T, class TB>
-__device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
-                                                   int cellw, int a, unsigned gmask, const T *__restrict__ kinv,
-                                                   T *__restrict__ corr, int cap, int slot, const Coef<T> &K) {
-    int i, j, k;
-    unpack_cell(cellw, i, j, k);
-    int cfg = (i >= 1) | ((i + 1 <= L.nx - 1) << 1) | ((j >= 1) << 2) | ((j + 1 <= L.ny - 1) << 3) |
-              ((k >= 1) << 4) | ((k + 1 <= L.nz - 1) << 5);
-    T r = T(0);
-    if (a < 6) {
-        int d = a >> 1, side = a & 1;
-        int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-        if ((cfg >> a) & 1) r = T(ldv(b[pidx(L, d, fi, fj, fk)])) - face_Lx_any(x, L, d, fi, fj, fk, K);
-    } else if (a == 6) {
-        r = T(ldv(b[pidx(L, 3, i, j, k)])) - cell_Lx_fast(x, L, i, j, k, K);
-    }
-    const T *Ki = kinv + cfg * 49 + (a < 7 ? a : 6) * 7;
-    T s = T(0);
-#pragma unroll
-    for (int bb = 0; bb < 7; ++bb) s += Ki[bb] * __shfl_sync(gmask, r, bb, 8);
-    if (a < 7) corr[(long long)a * cap + slot] = s;
-}
-
-template <class T>
-__device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x, int cellw, int a,
-                                                 const T *__restrict__ corr, int cap, int slot) {
-    if (a == 7) return;
-    int i, j, k;
-    unpack_cell(cellw, i, j, k);
-    if (a == 6) {
-        x[pidx(L, 3, i, j, k)] += corr[6LL * cap + slot];
-        return;
-    }
-    int d = a >> 1, side = a & 1;
-    int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-    if (active(L, d, fi, fj, fk)) x[pidx(L, d, fi, fj, fk)] += corr[(long long)a * cap + slot];
 }
 
 template <class T, class TB>
