@@ -515,6 +515,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 V-cycle solve beside the headline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage V-cycle solve beside the headline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="per-colour Vanka launches on every level (profiler runs: timings under a profiler would "
+                         "steer the autotuner)")
     ap.add_argument("--train", type=int, default=2000, help="training solves (--mode warmstart)")
     ap.add_argument("--test", type=int, default=200, help="held-out seeds (--mode warmstart)")
     ap.add_argument("--epochs", type=int, default=2, help="passes over the training solves (--mode warmstart)")
@@ -554,7 +557,8 @@ def main():
     n = args.n
     npk = packed_len(n)
     if args.mode == "vcycle":
-        S = smg.Stokes(n, precision=smg.PREC_FP32 if args.precision == "fp32" else smg.PREC_FP64)
+        S = smg.Stokes(n, precision=smg.PREC_FP32 if args.precision == "fp32" else smg.PREC_FP64,
+                       autotune=not args.no_autotune)
         sv = S.rhs(synthetic.bumps(n, seed=0, device=dev)["f"], None)
         tv = torch.empty_like(sv)
         for _ in range(args.warmup):
@@ -582,7 +586,7 @@ def main():
         return
     seeds = [(rank * 1000 + s) % 5 for s in range(5)]
     rhs = {}
-    S32 = smg.Stokes(n, precision=smg.PREC_FP32)
+    S32 = smg.Stokes(n, precision=smg.PREC_FP32, autotune=not args.no_autotune)
     for sd in sorted(set(seeds)):
         rhs[sd] = S32.rhs(synthetic.bumps(n, seed=sd, device=dev)["f"], None)
     x = torch.zeros(npk, dtype=torch.float64, device=dev)

@@ -650,25 +650,41 @@ void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists
 // copied in, the 16 colour steps run on the shared copies with __syncthreads() between the compute
 // and apply steps, and x is copied back.  The per-lane arithmetic is the same code as the global
 // version (generic pointers), so the result is bit-identical.
-template <class T, class TB> size_t vanka_smem_bytes(const Lev &L, int cap) {
-    const size_t xb = ((size_t)L.n * sizeof(T) + 15) / 16 * 16, bb = ((size_t)L.n * sizeof(TB) + 15) / 16 * 16;
-    return xb + bb + (size_t)7 * cap * sizeof(T);
-}
+// shared-memory layout: x [n] | b [n] | corrections [7 cap] | local inverses [64 x 49] | cell lists [8 cap]
+template <class T, class TB> struct VankaSmem {
+    size_t xo, bo, co, ko, lo, bytes;
+    __host__ __device__ VankaSmem(long long n, int cap) {
+        auto up = [](size_t v) { return (v + 15) / 16 * 16; };
+        xo = 0;
+        bo = up((size_t)n * sizeof(T));
+        co = bo + up((size_t)n * sizeof(TB));
+        ko = co + up((size_t)7 * cap * sizeof(T));
+        lo = ko + up((size_t)64 * 49 * sizeof(T));
+        bytes = lo + (size_t)8 * cap * sizeof(int);
+    }
+};
+template <class T, class TB> size_t vanka_smem_bytes(const Lev &L, int cap) { return VankaSmem<T, TB>(L.n, cap).bytes; }
 
 template <class T, class TB>
 __global__ void __launch_bounds__(1024) k_vanka_smem(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                      VankaLists lists, const T *__restrict__ kinv, int cap, Coef<T> K,
                                                      int sweeps) {
     extern __shared__ __align__(16) unsigned char vsm[];
-    T *xs = reinterpret_cast<T *>(vsm);
-    TB *bs = reinterpret_cast<TB *>(vsm + ((size_t)L.n * sizeof(T) + 15) / 16 * 16);
-    T *cs = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(bs) + ((size_t)L.n * sizeof(TB) + 15) / 16 * 16);
+    const VankaSmem<T, TB> lay(L.n, cap);
+    T *xs = reinterpret_cast<T *>(vsm + lay.xo);
+    TB *bs = reinterpret_cast<TB *>(vsm + lay.bo);
+    T *cs = reinterpret_cast<T *>(vsm + lay.co);
+    T *ks = reinterpret_cast<T *>(vsm + lay.ko);
+    int *cl = reinterpret_cast<int *>(vsm + lay.lo);
     pdl_wait();
     const int n = (int)L.n;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         xs[e] = x[e];
         bs[e] = b[e];
     }
+    for (int e = threadIdx.x; e < 64 * 49; e += blockDim.x) ks[e] = kinv[e];
+    for (int col = 0; col < 8; ++col)
+        for (int e = threadIdx.x; e < lists.count[col]; e += blockDim.x) cl[col * cap + e] = lists.cells[col][e];
     __syncthreads();
     const unsigned gmask = 0xffu << (threadIdx.x & 24);
     for (int sw = 0; sw < sweeps; ++sw)
@@ -676,9 +692,10 @@ __global__ void __launch_bounds__(1024) k_vanka_smem(Lev L, T *__restrict__ x, c
             const int col = ph < 8 ? ph : 15 - ph;
             const int nc = lists.count[col];
             if (nc == 0) continue;  // uniform across the block
-            const int *cells = lists.cells[col];
+            const int *cells = cl + col * cap;
             for (int t = threadIdx.x; (t >> 3) < nc; t += blockDim.x)
-                vanka_compute_lane(L, (const T *)xs, (const TB *)bs, cells[t >> 3], t & 7, gmask, kinv, cs, cap, t >> 3, K);
+                vanka_compute_lane(L, (const T *)xs, (const TB *)bs, cells[t >> 3], t & 7, gmask, (const T *)ks, cs, cap,
+                                   t >> 3, K);
             __syncthreads();
             for (int t = threadIdx.x; (t >> 3) < nc; t += blockDim.x)
                 vanka_apply_lane(L, xs, cells[t >> 3], t & 7, (const T *)cs, cap, t >> 3);
