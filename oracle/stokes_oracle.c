@@ -77,6 +77,8 @@ typedef struct {
 
 typedef struct {
     int nlev, kb;
+    int additive; /* Sec. 3.2 variant: additive Vanka (Eq. av) in place of the symmetric multiplicative sweep */
+    int cycle;    /* coarse-grid visits per level: 1 V-cycle (Alg. 1), 2 W-cycle (Sec. 8.2) */
     og_level *lev;
 } og_hier;
 
@@ -321,6 +323,42 @@ static void og_vanka_colour(og_level *L, double *x, const double *b, int col) {
     free(dofs); free(nd); free(corr);
 }
 
+/* Eq. (av): additive Vanka, x += w sum_i C_i^T (C_i L~ C_i^T)^{-1} C_i (b - L~ x) over every V1 patch,
+ * every correction computed from the same state, then added (colours 0..7, cells in list order).
+ * Reading: Eq. (av) states no damping; a face lies in the patches of its two cells, and the undamped
+ * sum over-corrects it (SQMR then stagnates near 3e-2 at 16^3), so w = 1/2, the reciprocal of that
+ * overlap, as for additive Schwarz smoothers.  A scalar multiple keeps S_AV symmetric. */
+#define OG_ADDITIVE_DAMPING 0.5
+static void og_vanka_additive(og_level *L, double *x, const double *b) {
+    long ntot = 0;
+    for (int col = 0; col < 8; ++col) ntot += L->nvcell[col];
+    if (ntot == 0) return;
+    long *dofs = (long *)malloc(sizeof(long) * 7 * ntot);
+    int *nd = (int *)malloc(sizeof(int) * ntot);
+    double *corr = (double *)malloc(sizeof(double) * 7 * ntot);
+    long t = 0;
+    for (int col = 0; col < 8; ++col)
+        for (long u = 0; u < L->nvcell[col]; ++u, ++t) {
+            long cl = L->vcell[col][u];
+            int i = (int)(cl % L->nx), j = (int)((cl / L->nx) % L->ny), k = (int)(cl / ((long)L->nx * L->ny));
+            long *D = dofs + 7 * t;
+            int m = og_patch(L, i, j, k, D);
+            nd[t] = m;
+            double K[49], rl[7];
+            long piv[7];
+            for (int a = 0; a < m; ++a) {
+                rl[a] = b[D[a]] - og_row(L, D[a], x, L->gamma);
+                for (int bb = 0; bb < m; ++bb) K[a * m + bb] = og_entry(L, D[a], D[bb], L->gamma);
+            }
+            og_lu(m, K, piv);
+            og_lu_solve(m, K, piv, rl);
+            for (int a = 0; a < m; ++a) corr[7 * t + a] = rl[a];
+        }
+    for (t = 0; t < ntot; ++t)
+        for (int a = 0; a < nd[t]; ++a) x[dofs[7 * t + a]] += OG_ADDITIVE_DAMPING * corr[7 * t + a];
+    free(dofs); free(nd); free(corr);
+}
+
 /* App. C: symmetric multiplicative Vanka = colours 0..7 followed by 7..0 */
 static void og_vanka_sym(og_level *L, double *x, const double *b) {
     for (int col = 0; col < 8; ++col) og_vanka_colour(L, x, b, col);
@@ -332,11 +370,12 @@ static void og_dgs_sym(og_level *L, double *x, const double *b) {
     og_dgs_backward(L, x, b);
 }
 
-/* Alg. 3 (x threaded through the three calls, as in App. D) */
-static void og_smooth(og_level *L, double *x, const double *b, int kb) {
-    for (int s = 0; s < kb; ++s) og_vanka_sym(L, x, b);
+/* Alg. 3 (x threaded through the three calls, as in App. D); additive: Eq. (av) in place of the
+ * symmetric multiplicative Vanka sweep */
+static void og_smooth(og_level *L, double *x, const double *b, int kb, int additive) {
+    for (int s = 0; s < kb; ++s) (additive ? og_vanka_additive : og_vanka_sym)(L, x, b);
     og_dgs_sym(L, x, b);
-    for (int s = 0; s < kb; ++s) og_vanka_sym(L, x, b);
+    for (int s = 0; s < kb; ++s) (additive ? og_vanka_additive : og_vanka_sym)(L, x, b);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -412,20 +451,23 @@ static void og_coarse_solve(const og_level *L, const double *b, double *x) {
     free(y);
 }
 
-/* Alg. 1: V-cycle(L~, b, x0 = 0, n) starting at level l; result in x (overwritten) */
-static void og_vcycle_level(og_hier *H, int l, const double *b, double *x) {
+/* Alg. 1: V-cycle(L~, b, x0, n) starting at level l (x0 = 0 if zero_init, else the given x); result
+ * in x.  H->cycle = 2 visits the coarse problem twice (W-cycle, Sec. 8.2): the second visit starts
+ * from the first one's coarse iterate. */
+static void og_cycle_level(og_hier *H, int l, const double *b, double *x, int zero_init) {
     og_level *L = &H->lev[l];
     if (l == H->nlev - 1) { og_coarse_solve(L, b, x); return; }
     og_level *C = &H->lev[l + 1];
-    memset(x, 0, sizeof(double) * L->n);
-    og_smooth(L, x, b, H->kb);
+    if (zero_init) memset(x, 0, sizeof(double) * L->n);
+    og_smooth(L, x, b, H->kb, H->additive);
     og_apply_level(L, x, L->r, L->gamma);
     for (long q = 0; q < L->n; ++q) L->r[q] = L->active[q] ? b[q] - L->r[q] : 0.0;
     og_restrict(L, C, L->r, C->b);
-    og_vcycle_level(H, l + 1, C->b, C->x);
+    for (int g = 0; g < H->cycle; ++g) og_cycle_level(H, l + 1, C->b, C->x, g == 0);
     og_prolong_add(L, C, C->x, x);
-    og_smooth(L, x, b, H->kb);
+    og_smooth(L, x, b, H->kb, H->additive);
 }
+static void og_vcycle_level(og_hier *H, int l, const double *b, double *x) { og_cycle_level(H, l, b, x, 1); }
 
 /* ------------------------------------------------------------------------------------ */
 /* level construction                                                                    */
@@ -599,6 +641,8 @@ int og_create(int nx, int ny, int nz, double h, double eta, double gamma, int le
     og_hier *H = (og_hier *)calloc(1, sizeof(og_hier));
     if (!H) return OG_ERR_OOM;
     H->kb = kb;
+    H->additive = 0;
+    H->cycle = 1;
     H->lev = (og_level *)calloc(levels, sizeof(og_level));
     int rc = OG_OK;
     uint8_t *clab = NULL;
@@ -697,12 +741,21 @@ void og_dgs(og_hier *H, int l, int direction /* +1 forward, -1 backward, 0 symme
     if (direction >= 0) og_dgs_forward(L, x, b);
     if (direction <= 0) og_dgs_backward(L, x, b);
 }
-void og_vanka(og_hier *H, int l, int colour /* 0..7 one colour, -1 symmetric sweep */, double *x, const double *b) {
+void og_vanka(og_hier *H, int l, int colour /* 0..7 one colour, -1 symmetric sweep (additive step if set) */,
+              double *x, const double *b) {
     og_level *L = &H->lev[l];
     if (colour >= 0) og_vanka_colour(L, x, b, colour);
+    else if (H->additive) og_vanka_additive(L, x, b);
     else og_vanka_sym(L, x, b);
 }
-void og_smooth_level(og_hier *H, int l, double *x, const double *b) { og_smooth(&H->lev[l], x, b, H->kb); }
+void og_smooth_level(og_hier *H, int l, double *x, const double *b) { og_smooth(&H->lev[l], x, b, H->kb, H->additive); }
+/* smoother and cycle variants (Sec. 3.2 additive Vanka; Sec. 8.2 W-cycle) */
+int og_set_variant(og_hier *H, int additive, int cycle) {
+    if (!H || (additive != 0 && additive != 1) || cycle < 1 || cycle > 2) return OG_ERR_ARG;
+    H->additive = additive;
+    H->cycle = cycle;
+    return OG_OK;
+}
 void og_restrict_level(og_hier *H, int l, const double *rf, double *bc) { og_restrict(&H->lev[l], &H->lev[l + 1], rf, bc); }
 void og_prolong_level(og_hier *H, int l, const double *ec, double *xf) { og_prolong_add(&H->lev[l], &H->lev[l + 1], ec, xf); }
 void og_coarse(og_hier *H, const double *b, double *x) { og_coarse_solve(&H->lev[H->nlev - 1], b, x); }

@@ -148,10 +148,13 @@ def _assemble(fn, n, active):
 
 
 # eta = 1e-3 is the paper's viscosity (Sec. 7); there the local saddle-point matrices need row pivoting
+@pytest.mark.parametrize("additive", [False, True])
 @pytest.mark.parametrize("eta", [1.0, 1e-3])
 @pytest.mark.parametrize("which", ["dgs", "vanka", "smooth"])
-def test_smoother_C_symmetric(which, eta):
-    o = oracle.Oracle(6, eta=eta, gamma=1e-3, levels=1, kb=1)
+def test_smoother_C_symmetric(which, eta, additive):
+    if which == "dgs" and additive:
+        pytest.skip("the DGS sweep does not depend on the Vanka variant")
+    o = oracle.Oracle(6, eta=eta, gamma=1e-3, levels=1, kb=1, additive=additive)
     act, _ = o.masks()
     z = np.zeros(o.n())
     fn = {"dgs": lambda e: o.dgs(z, e, direction=0),
@@ -192,6 +195,58 @@ def test_vanka_single_patch_is_exact_local_solve(eta):
         patch += [D.offsets[3] + i + nx * (j + nx * k)]
         patch = [q for q in patch if D.active[q]]
         assert np.max(np.abs(r[patch])) < 1e-12 * np.max(np.abs(b))
+
+
+def test_additive_vanka_is_damped_sum_of_local_solves():
+    # Eq. (av): x + (1/2) sum_i C_i^T (C_i L~ C_i^T)^{-1} C_i (b - L~ x), every V1 patch from the same state
+    n = 4
+    o = oracle.Oracle(n, levels=1, coarsest_max=2, additive=True)
+    D = DenseBox(n)
+    Lt = D.Lt.toarray()
+    x = _masked(_rand(D.n, 40), D.active)
+    b = _masked(_rand(D.n, 41), D.active)
+    r = b - Lt @ x
+    ref = x.copy()
+    nx = n
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                if 0 < i < n - 1 and 0 < j < n - 1 and 0 < k < n - 1:
+                    continue  # interior cells are V2
+                patch = [i + s + (nx + 1) * (j + nx * k) for s in (0, 1)]
+                patch += [D.offsets[1] + i + nx * (j + s + (nx + 1) * k) for s in (0, 1)]
+                patch += [D.offsets[2] + i + nx * (j + nx * (k + s)) for s in (0, 1)]
+                patch += [D.offsets[3] + i + nx * (j + nx * k)]
+                patch = [q for q in patch if D.active[q]]
+                K = Lt[np.ix_(patch, patch)]
+                ref[patch] += 0.5 * np.linalg.solve(K, r[patch])
+    got = o.vanka(x, b, colour=-1)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_wcycle_two_levels_equals_vcycle():
+    # with an exact coarsest solve the second coarse visit of a two-level W-cycle corrects nothing
+    ov = oracle.Oracle(8, levels=2, coarsest_max=4)
+    ow = oracle.Oracle(8, levels=2, coarsest_max=4, cycle=2)
+    act, _ = ov.masks()
+    s = _masked(_rand(ov.n(), 42), act)
+    tv, tw = ov.vcycle(s), ow.vcycle(s)
+    assert np.max(np.abs(tv - tw)) < 1e-11 * np.max(np.abs(tv))
+
+
+def test_wcycle_symmetric_and_at_least_as_fast():
+    o = oracle.Oracle(8, levels=3, coarsest_max=2, cycle=2)
+    act, _ = o.masks()
+    W = _assemble(o.vcycle, o.n(), act)
+    assert np.max(np.abs(W - W.T)) <= 1e-11 * np.max(np.abs(W))
+    # Sec. 8.2: the W-cycle converges at least as fast per iteration as the V-cycle
+    prob = synthetic.bumps(16, seed=0)
+    its = []
+    for cyc in (1, 2):
+        oc = oracle.Oracle(16, coarsest_max=4, cycle=cyc)
+        b = oc.rhs(prob["f"].numpy(), None)
+        its.append(oc.sqmr(b, tol=1e-8, maxit=100)[2])
+    assert its[1] <= its[0]
 
 
 # ----------------------------------------------------------------------------------------------
