@@ -503,6 +503,46 @@ def run_warmstart(args, smg, synthetic, torch, dev, rank, world):
     S.close()
 
 
+def run_variants(args, smg, synthetic, torch, dev, rank, world, dist):
+    """The method's variants on the headline workload (n^3 bumps, FP32 V-cycle, FP64 SQMR, tol): k_b = 1, 2, 3
+    symmetric Vanka sweeps (Alg. 3), the W-cycle (Sec. 8.2) and the damped additive Vanka (Eq. av)."""
+    n = args.n
+    rows = []
+    for name, kw in [("V, k_b=1 (default)", {}), ("V, k_b=2", {"kb_vanka": 2}), ("V, k_b=3", {"kb_vanka": 3}),
+                     ("W, k_b=1", {"cycle": 2}), ("V, additive Vanka, k_b=1", {"additive": True}),
+                     ("V, additive Vanka, k_b=3", {"additive": True, "kb_vanka": 3})]:
+        S = smg.Stokes(n, precision=smg.PREC_FP32, **kw)
+        b = S.rhs(synthetic.bumps(n, seed=0, device=dev)["f"], None)
+        x = torch.zeros_like(b)
+        for _ in range(args.warmup):
+            x.zero_()
+            smg.sqmr_solve(S.h, b, x, args.tol, 200, check=False)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            x.zero_()
+            info = smg.sqmr_solve(S.h, b, x, args.tol, 200, check=False)
+            its.append((info.iterations, info.rel_residual, info.status))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        rows.append({"variant": name, "value": unknowns(n) / (ms * 1e-3), "ms_per_solve": ms,
+                     "iterations": its[-1][0], "rel_residual": its[-1][1], "status": its[-1][2]})
+        S.close()
+    if rank == 0:
+        base = rows[0]
+        line = {"metric": "solved unknowns/sec to rel. residual %g, smoother and cycle variants" % args.tol,
+                "value": base["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": base["ms_per_solve"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 SQMR + f32 V-cycle", "data": "synthetic",
+                "config": {"workload": workload_name(n), "n": n, "tol": args.tol, "parallelism": f"replicas x{world}"},
+                "variants": rows}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -523,11 +563,12 @@ def main():
     ap.add_argument("--epochs", type=int, default=2, help="passes over the training solves (--mode warmstart)")
     ap.add_argument("--ws-loss", default="residual", choices=["error", "residual"],
                     help="training loss of --mode warmstart: ||x0 - x*||^2/||x*||^2 or ||L (x0 - x*)||^2/||b||^2")
-    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity", "warmstart"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity", "warmstart", "variants"],
                     help="vcycle: only time mg_precondition (one V-cycle per step) -- for profiler captures; "
                          "batch: independent problems of uneven sizes solved concurrently; "
                          "cavity: the 3D lid-driven cavity (eta = gamma = 1e-3); "
-                         "warmstart: train the initial-guess network on solves, then solve held-out seeds")
+                         "warmstart: train the initial-guess network on solves, then solve held-out seeds; "
+                         "variants: k_b sweeps, W-cycle and additive Vanka on the headline workload")
     ap.add_argument("--batch", type=int, default=64, help="problems per batch (--mode batch)")
     ap.add_argument("--streams", type=int, default=8, help="concurrent streams / host threads (--mode batch)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of --mode vcycle")
@@ -583,6 +624,9 @@ def main():
         return
     if args.mode == "warmstart":
         run_warmstart(args, smg, synthetic, torch, dev, rank, world)
+        return
+    if args.mode == "variants":
+        run_variants(args, smg, synthetic, torch, dev, rank, world, dist)
         return
     seeds = [(rank * 1000 + s) % 5 for s in range(5)]
     rhs = {}

@@ -86,6 +86,10 @@ typedef struct {
                       cluster of 4, 8 or 16 CTAs; one block on a shared-memory copy of a small
                       level) and keep the fastest; all candidates give bit-identical results.
                       0: per-colour launches. */
+    int vanka_additive; /* 0 (default): symmetric multiplicative Vanka (App. C); 1: the additive Vanka of
+                           Eq. (av) in its place, damped by 1/2 (a face lies in two patches; the
+                           undamped sum over-corrects) -- symmetric as well (Sec. 3.2 variant) */
+    int cycle;     /* coarse-grid visits per level: 1 (default) V-cycle (Alg. 1), 2 W-cycle (Sec. 8.2) */
 } stokes_opts_t;
 
 typedef struct {

@@ -26,9 +26,10 @@ template <class T, class TB>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const TB *b, TB *gh, const T *delta, cudaStream_t s);
 template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s);
 // one colour of the multiplicative Vanka sweep on V1 (compute corrections, then add them)
+// corrections scaled by w (1 for the multiplicative sweep, 1/2 for the damped additive step)
 template <class T, class TB>
 void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, int ncell, const T *kinv, T *corr,
-                          int cap, cudaStream_t s);
+                          int cap, double w, cudaStream_t s);
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s);
 // a whole symmetric Vanka sweep (colours 0..7 then 7..0), `sweeps` times, in ONE cooperative

@@ -488,7 +488,8 @@ __device__ __forceinline__ T vanka_face_residual(const Lev &L, const T *__restri
 template <class T, class TB>
 __device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
                                                    int cellw, int a, unsigned gmask, const T *__restrict__ kinv,
-                                                   T *__restrict__ corr, int cap, int slot, const Coef<T> &K) {
+                                                   T *__restrict__ corr, int cap, int slot, const Coef<T> &K,
+                                                   T w = T(1)) {
     int i, j, k;
     unpack_cell(cellw, i, j, k);
     const int cfg = (i >= 1) | ((i + 1 <= L.nx - 1) << 1) | ((j >= 1) << 2) | ((j + 1 <= L.ny - 1) << 3) |
@@ -503,7 +504,7 @@ __device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__rest
     T s = T(0);
 #pragma unroll
     for (int bb = 0; bb < 7; ++bb) s += Ki[bb] * __shfl_sync(gmask, r, bb, 8);
-    if (a < 7) corr[(long long)a * cap + slot] = s;
+    if (a < 7) corr[(long long)a * cap + slot] = w * s;  // w = 1 (multiplicative) is exact
 }
 
 template <class T>
@@ -533,12 +534,12 @@ template <class T, class TB>
 __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                        const int *__restrict__ cells, int ncell,
                                                        const T *__restrict__ kinv, T *__restrict__ corr, int cap,
-                                                       Coef<T> K) {
+                                                       Coef<T> K, T w) {
     pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3;
     if (slot >= ncell) return;  // whole 8-lane groups leave together
-    vanka_compute_lane(L, x, b, cells[slot], t & 7, 0xffu << (threadIdx.x & 24), kinv, corr, cap, slot, K);
+    vanka_compute_lane(L, x, b, cells[slot], t & 7, 0xffu << (threadIdx.x & 24), kinv, corr, cap, slot, K, w);
 }
 
 template <class T>
@@ -553,10 +554,10 @@ __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, c
 
 template <class T, class TB>
 void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, int ncell, const T *kinv, T *corr,
-                          int cap, cudaStream_t s) {
+                          int cap, double w, cudaStream_t s) {
     if (ncell <= 0) return;
     launch_k(k_vanka_compute<T, TB>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, ncell, kinv, corr, cap,
-                                                               coef<T>(L, L.gamma));
+             coef<T>(L, L.gamma), T(w));
 }
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s) {
@@ -997,7 +998,7 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template void launch_dgs_p_bwd_prep<T, TB>(const Lev &, T *, const TB *, TB *, const T *, cudaStream_t);      \
     template void launch_dgs_p_bwd<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                       \
     template void launch_vanka_compute<T, TB>(const Lev &, const T *, const TB *, const int *, int, const T *, T *,  \
-                                              int, cudaStream_t);                                                   \
+                                              int, double, cudaStream_t);                                           \
     template void launch_vanka_sweep<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, T *, int,  \
                                             int, GridBarrier *, int, cudaStream_t);                                 \
     template cudaError_t vanka_cluster_prepare<T, TB>();                                                          \

@@ -167,6 +167,8 @@ struct stokes_s {
     int vanka_persistent = 1;
     int vanka_max_blocks = 0;  // co-resident blocks of the cooperative Vanka sweep
     int nbf = 0;               // finest levels whose b, r are stored as BF16 (STOKES_PREC_MIXED_BF16)
+    int additive = 0;          // Vanka variant: 0 symmetric multiplicative sweep, 1 damped additive (Eq. av)
+    int cycle = 1;             // coarse-grid visits per level: 1 V-cycle, 2 W-cycle
     GridBarrier *bar = nullptr;
     double eta = 1.0, gamma = 1e-3;
     std::vector<LevelBuf> lev;
@@ -243,14 +245,37 @@ template <class T, class TB> void vanka_colour(stokes_s *h, int l, int col, cuda
     if (B.vcount[col] == 0) return;
     prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
         launch_vanka_compute<T, TB>(B.L, (const T *)B.x, (const TB *)B.b, B.vcells[col], B.vcount[col],
-                                    (const T *)B.kinv, (T *)B.corr, B.vcap, s);
+                                    (const T *)B.kinv, (T *)B.corr, B.vcap, 1.0, s);
     });
     prof(STOKES_K_VANKA_APPLY, l, s,
          [&] { launch_vanka_apply<T>(B.L, (T *)B.x, B.vcells[col], B.vcount[col], (const T *)B.corr, B.vcap, s); });
 }
+// Eq. (av), damped by 1/2 (a face lies in two patches): every colour's corrections from the same
+// state into its own slice of the correction buffer, then added colour by colour
+template <class T, class TB> void vanka_additive(stokes_s *h, int l, cudaStream_t s) {
+    LevelBuf &B = h->lev[l];
+    const size_t slice = (size_t)7 * B.vcap;
+    for (int c = 0; c < 8; ++c) {
+        if (B.vcount[c] == 0) continue;
+        prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
+            launch_vanka_compute<T, TB>(B.L, (const T *)B.x, (const TB *)B.b, B.vcells[c], B.vcount[c],
+                                        (const T *)B.kinv, (T *)B.corr + c * slice, B.vcap, 0.5, s);
+        });
+    }
+    for (int c = 0; c < 8; ++c) {
+        if (B.vcount[c] == 0) continue;
+        prof(STOKES_K_VANKA_APPLY, l, s, [&] {
+            launch_vanka_apply<T>(B.L, (T *)B.x, B.vcells[c], B.vcount[c], (const T *)B.corr + c * slice, B.vcap, s);
+        });
+    }
+}
 // `sweeps` symmetric Vanka sweeps (App. C: colours 0..7 then 7..0)
 template <class T, class TB> void vanka_sym(stokes_s *h, int l, cudaStream_t s, int sweeps = 1) {
     LevelBuf &B = h->lev[l];
+    if (h->additive) {
+        for (int k = 0; k < sweeps; ++k) vanka_additive<T, TB>(h, l, s);
+        return;
+    }
     if (B.vmode == 3 && !h->vanka_persistent) {
         prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
             launch_vanka_smem<T, TB>(B.L, (T *)B.x, (const TB *)B.b, B.lists, (const T *)B.kinv, B.vcap, sweeps, s);
@@ -312,34 +337,36 @@ template <class T, class TB> void smooth(stokes_s *h, int l, cudaStream_t s) {
 template <class T> void smooth_level(stokes_s *h, int l, cudaStream_t s) {
     with_tb<T>(h, l, [&](auto t, auto tb) { smooth<decltype(t), decltype(tb)>(h, l, s); });
 }
-template <class T> void vcycle(stokes_s *h, cudaStream_t s) {
-    int n = h->nlev();
-    for (int l = 0; l < n - 1; ++l) {
-        LevelBuf &B = h->lev[l];
-        prof(STOKES_K_MEMSET, l, s, [&] { cudaMemsetAsync(B.x, 0, sizeof(T) * B.L.n, s); });
-        smooth_level<T>(h, l, s);
-        with_tb<T>(h, l, [&](auto t, auto tf) {
-            using TT = decltype(t);
-            using TF = decltype(tf);
-            prof(STOKES_K_RESIDUAL, l, s,
-                 [&] { launch_apply<TT, TF>(B.L, (const TT *)B.x, (const TF *)B.b, (TF *)B.r, B.L.gamma, s); });
-            with_tb<T>(h, l + 1, [&](auto, auto tc) {
-                using TC = decltype(tc);
-                prof(STOKES_K_RESTRICT, l, s,
-                     [&] { launch_restrict<TT, TF, TC>(B.L, h->lev[l + 1].L, (const TF *)B.r, (TC *)h->lev[l + 1].b, s); });
-            });
+// Alg. 1 from level l; first: x_l starts at 0 (else from its current value, the second coarse visit
+// of a W-cycle); h->cycle coarse visits per level (1 V-cycle, 2 W-cycle, Sec. 8.2)
+template <class T> void cycle_level(stokes_s *h, int l, bool first, cudaStream_t s) {
+    const int n = h->nlev();
+    if (l == n - 1) {
+        LevelBuf &C = h->lev[n - 1];
+        prof(STOKES_K_COARSE, n - 1, s,
+             [&] { launch_coarse<T>(C.L, h->cidx, h->nc, h->ckinv, (const T *)C.b, (T *)C.x, s); });
+        return;
+    }
+    LevelBuf &B = h->lev[l];
+    if (first) prof(STOKES_K_MEMSET, l, s, [&] { cudaMemsetAsync(B.x, 0, sizeof(T) * B.L.n, s); });
+    smooth_level<T>(h, l, s);
+    with_tb<T>(h, l, [&](auto t, auto tf) {
+        using TT = decltype(t);
+        using TF = decltype(tf);
+        prof(STOKES_K_RESIDUAL, l, s,
+             [&] { launch_apply<TT, TF>(B.L, (const TT *)B.x, (const TF *)B.b, (TF *)B.r, B.L.gamma, s); });
+        with_tb<T>(h, l + 1, [&](auto, auto tc) {
+            using TC = decltype(tc);
+            prof(STOKES_K_RESTRICT, l, s,
+                 [&] { launch_restrict<TT, TF, TC>(B.L, h->lev[l + 1].L, (const TF *)B.r, (TC *)h->lev[l + 1].b, s); });
         });
-    }
-    LevelBuf &C = h->lev[n - 1];
-    prof(STOKES_K_COARSE, n - 1, s,
-         [&] { launch_coarse<T>(C.L, h->cidx, h->nc, h->ckinv, (const T *)C.b, (T *)C.x, s); });
-    for (int l = n - 2; l >= 0; --l) {
-        LevelBuf &B = h->lev[l];
-        prof(STOKES_K_PROLONG, l, s,
-             [&] { launch_prolong<T>(B.L, h->lev[l + 1].L, (const T *)h->lev[l + 1].x, (T *)B.x, s); });
-        smooth_level<T>(h, l, s);
-    }
+    });
+    for (int g = 0; g < h->cycle; ++g) cycle_level<T>(h, l + 1, g == 0, s);
+    prof(STOKES_K_PROLONG, l, s,
+         [&] { launch_prolong<T>(B.L, h->lev[l + 1].L, (const T *)h->lev[l + 1].x, (T *)B.x, s); });
+    smooth_level<T>(h, l, s);
 }
+template <class T> void vcycle(stokes_s *h, cudaStream_t s) { cycle_level<T>(h, 0, true, s); }
 void vcycle_any(stokes_s *h, cudaStream_t s) {
     if (h->prec == STOKES_PREC_FP64) vcycle<double>(h, s);
     else vcycle<float>(h, s);
@@ -590,6 +617,8 @@ void stokes_opts_default(stokes_opts_t *o) {
     o->use_graphs = 1;
     o->vanka_persistent = 0;
     o->autotune = 1;
+    o->vanka_additive = 0;
+    o->cycle = 1;
 }
 
 const char *stokes_strerror(int st) {
@@ -619,7 +648,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     stokes_opts_default(&o);
     if (opts) o = *opts;
     if (!(o.gamma >= 0.0) || o.kb_vanka < 0 ||
-        (o.precision != STOKES_PREC_FP64 && o.precision != STOKES_PREC_FP32 && o.precision != STOKES_PREC_MIXED_BF16))
+        (o.precision != STOKES_PREC_FP64 && o.precision != STOKES_PREC_FP32 && o.precision != STOKES_PREC_MIXED_BF16) ||
+        (o.vanka_additive != 0 && o.vanka_additive != 1) || o.cycle < 1 || o.cycle > 2)
         return STOKES_ERR_INVALID_ARG;
     int cmax = grid->coarsest_max > 0 ? grid->coarsest_max : 8;
     int nlev = grid->levels;
@@ -643,6 +673,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     h->kb = o.kb_vanka;
     h->use_graphs = o.use_graphs;
     h->vanka_persistent = o.vanka_persistent;
+    h->additive = o.vanka_additive;
+    h->cycle = o.cycle;
     h->eta = viscosity;
     h->gamma = o.gamma;
     double hh = grid->h > 0 ? grid->h : 1.0 / grid->nx;
@@ -709,7 +741,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
             if (!cells[c].empty())
                 CK(cudaMemcpy(B.vcells[c], cells[c].data(), sizeof(int) * cells[c].size(), cudaMemcpyHostToDevice));
         }
-        if ((rc = h->alloc(&B.corr, es * 7 * (size_t)B.vcap))) return rc;
+        if ((rc = h->alloc(&B.corr, es * 8 * 7 * (size_t)B.vcap))) return rc;  // 8 slices: additive Vanka
         for (int c = 0; c < 8; ++c) {
             B.lists.cells[c] = B.vcells[c];
             B.lists.count[c] = B.vcount[c];
@@ -746,7 +778,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
                                                             vanka_sweep_blocks_per_sm<float, bf16>());
         h->vanka_max_blocks = per_sm * nsm;
         if (!coop || h->vanka_max_blocks <= 0) h->vanka_persistent = 0;
-        if (coop && h->vanka_max_blocks > 0 && !h->vanka_persistent && o.autotune) {
+        if (coop && h->vanka_max_blocks > 0 && !h->vanka_persistent && o.autotune && !h->additive) {
             if ((rc = autotune_vanka(h.get(), nsm))) return rc;
         }
     }

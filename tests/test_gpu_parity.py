@@ -303,6 +303,35 @@ def test_sqmr_fp32_vcycle_accuracy():
     assert rel_err(x, x_ref) < 1e-7
 
 
+# ---------------------------------------------------------------------------------------------- variants
+
+VARIANTS = [dict(kb=2), dict(kb=3), dict(cycle=2), dict(additive=True), dict(additive=True, kb=3)]
+
+
+@pytest.mark.parametrize("kw", VARIANTS, ids=lambda kw: "-".join(f"{k}{v}" for k, v in kw.items()))
+def test_variant_parity(kw):
+    # k_b sweeps (Sec. 7), the W-cycle (Sec. 8.2) and additive Vanka (Eq. av): a smoothing step, a
+    # V/W-cycle and six SQMR iterations against the oracle with the same variant
+    o = oracle.Oracle(32, coarsest_max=8, **kw)
+    S = smg.Stokes(32, **{("kb_vanka" if k == "kb" else k): v for k, v in kw.items()})
+    x, b = rand_masked(o, 51), rand_masked(o, 52)
+    got = cuda(x)
+    smg.stokes_smooth(S.h, 0, 0, got, cuda(b))
+    assert rel_err(got, o.smooth(x, b)) < 1e-12
+    s = rand_masked(o, 50)
+    assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-11
+    prob = synthetic.bumps(32, seed=6)
+    b_ref = o.rhs(prob["f"].numpy(), None)
+    x_ref, _, _, _, _ = o.sqmr(b_ref, tol=1e-30, maxit=6, fixed_iters=6)
+    bb = S.rhs(prob["f"].to(DEV), None)
+    xx = torch.zeros_like(bb)
+    info = smg.sqmr_solve(S.h, bb, xx, tol=1e-30, max_iter=6, check=False)
+    assert info.iterations == 6 and rel_err(xx, x_ref) < 1e-10
+    _, info8 = S.solve(bb, tol=1e-8)
+    assert info8.status == 0
+    S.close()
+
+
 # ---------------------------------------------------------------------------------------------- BF16 levels
 
 def test_mixed_bf16_pieces_close_to_oracle():
