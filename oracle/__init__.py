@@ -67,7 +67,7 @@ def _load():
         "og_coarse": (None, [vp, _d, _d]),
         "og_dgs_diag": (None, [vp, ctypes.c_int, _d]),
         "og_vcycle": (None, [vp, _d, _d]),
-        "og_set_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "og_set_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "og_sqmr": (ctypes.c_int, [vp, _d, _d, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i,
                                    _d, _d]),
     }
@@ -103,7 +103,7 @@ class Oracle:
     """Multigrid hierarchy of the oracle (FP64)."""
 
     def __init__(self, nx, ny=None, nz=None, h=None, eta=1.0, gamma=1e-3, levels=0, coarsest_max=8, kb=1,
-                 labels=None, additive=False, cycle=1):
+                 labels=None, additive=False, cycle=1, dwj=False):
         ny = nx if ny is None else ny
         nz = nx if nz is None else nz
         h = 1.0 / nx if h is None else h
@@ -114,7 +114,7 @@ class Oracle:
         rc = self.lib.og_create(nx, ny, nz, h, eta, gamma, levels, coarsest_max, kb, lab, ctypes.byref(self._h))
         if rc:
             raise RuntimeError(f"og_create failed: {rc}")
-        rc = self.lib.og_set_variant(self._h, int(bool(additive)), int(cycle))
+        rc = self.lib.og_set_variant(self._h, int(bool(additive)), int(cycle), int(bool(dwj)))
         if rc:
             raise RuntimeError(f"og_set_variant failed: {rc}")
         self.dims, self.h, self.eta, self.gamma, self.kb = (nx, ny, nz), h, eta, gamma, kb

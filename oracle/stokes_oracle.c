@@ -78,6 +78,7 @@ typedef struct {
 typedef struct {
     int nlev, kb;
     int additive; /* Sec. 3.2 variant: additive Vanka (Eq. av) in place of the symmetric multiplicative sweep */
+    int dwj;      /* Sec. 3.1 variant: symmetric distributive weighted Jacobi in place of the symmetric DGS */
     int cycle;    /* coarse-grid visits per level: 1 V-cycle (Alg. 1), 2 W-cycle (Sec. 8.2) */
     og_level *lev;
 } og_hier;
@@ -370,11 +371,48 @@ static void og_dgs_sym(og_level *L, double *x, const double *b) {
     og_dgs_backward(L, x, b);
 }
 
+/* Sec. 3.1, distributive weighted Jacobi (S_DWJ = w M D~^{-1}, D~ the diagonal of L~M) made symmetric
+ * like the DGS.  As the DGS applies its smoother block by block (velocities, then pressures, Sec. 3.1),
+ * each block here gets one weighted Jacobi step, every update of a step from the same state:
+ * right-preconditioned velocities, x_j += w r_j / d_j; right-preconditioned pressures,
+ * x += w sum_j M_{.j} r_j / d_j; then in reverse block order the left-preconditioned steps,
+ * pressures x_j += w M_{.j}^T r / d_j and velocities x_j += w r_j / d_j (r = b - L~x before each step).
+ * Reading: the paper gives no w; w = 6/7, the classical smoothing weight of pointwise Jacobi for the
+ * 7-point Laplacian that both diagonal blocks of L~M carry. */
+#define OG_DWJ_OMEGA (6.0 / 7.0)
+static void og_dwj_step(og_level *L, double *x, const double *b, int pressure, int left) {
+    long idx[16]; double val[16];
+    double *r = (double *)malloc(sizeof(double) * L->n);
+    double *dx = (double *)calloc(L->n, sizeof(double));
+    for (long q = 0; q < L->n; ++q) r[q] = L->active[q] ? b[q] - og_row(L, q, x, L->gamma) : 0.0;
+    for (long t = 0; t < L->norder; ++t) {
+        long q = L->order[t];
+        if ((q >= L->op) != pressure) continue;
+        int m = og_mcol(L, q, idx, val);
+        if (left) {
+            double s = 0.0;
+            for (int u = 0; u < m; ++u) s += val[u] * r[idx[u]];
+            dx[q] = s / L->dgs_d[q];
+        } else {
+            double delta = r[q] / L->dgs_d[q];
+            for (int u = 0; u < m; ++u) dx[idx[u]] += delta * val[u];
+        }
+    }
+    for (long q = 0; q < L->n; ++q) x[q] += OG_DWJ_OMEGA * dx[q];
+    free(r); free(dx);
+}
+static void og_dwj_sym(og_level *L, double *x, const double *b) {
+    og_dwj_step(L, x, b, 0, 0);
+    og_dwj_step(L, x, b, 1, 0);
+    og_dwj_step(L, x, b, 1, 1);
+    og_dwj_step(L, x, b, 0, 1);
+}
+
 /* Alg. 3 (x threaded through the three calls, as in App. D); additive: Eq. (av) in place of the
  * symmetric multiplicative Vanka sweep */
-static void og_smooth(og_level *L, double *x, const double *b, int kb, int additive) {
+static void og_smooth(og_level *L, double *x, const double *b, int kb, int additive, int dwj) {
     for (int s = 0; s < kb; ++s) (additive ? og_vanka_additive : og_vanka_sym)(L, x, b);
-    og_dgs_sym(L, x, b);
+    (dwj ? og_dwj_sym : og_dgs_sym)(L, x, b);
     for (int s = 0; s < kb; ++s) (additive ? og_vanka_additive : og_vanka_sym)(L, x, b);
 }
 
@@ -459,13 +497,13 @@ static void og_cycle_level(og_hier *H, int l, const double *b, double *x, int ze
     if (l == H->nlev - 1) { og_coarse_solve(L, b, x); return; }
     og_level *C = &H->lev[l + 1];
     if (zero_init) memset(x, 0, sizeof(double) * L->n);
-    og_smooth(L, x, b, H->kb, H->additive);
+    og_smooth(L, x, b, H->kb, H->additive, H->dwj);
     og_apply_level(L, x, L->r, L->gamma);
     for (long q = 0; q < L->n; ++q) L->r[q] = L->active[q] ? b[q] - L->r[q] : 0.0;
     og_restrict(L, C, L->r, C->b);
     for (int g = 0; g < H->cycle; ++g) og_cycle_level(H, l + 1, C->b, C->x, g == 0);
     og_prolong_add(L, C, C->x, x);
-    og_smooth(L, x, b, H->kb, H->additive);
+    og_smooth(L, x, b, H->kb, H->additive, H->dwj);
 }
 static void og_vcycle_level(og_hier *H, int l, const double *b, double *x) { og_cycle_level(H, l, b, x, 1); }
 
@@ -643,6 +681,7 @@ int og_create(int nx, int ny, int nz, double h, double eta, double gamma, int le
     H->kb = kb;
     H->additive = 0;
     H->cycle = 1;
+    H->dwj = 0;
     H->lev = (og_level *)calloc(levels, sizeof(og_level));
     int rc = OG_OK;
     uint8_t *clab = NULL;
@@ -738,6 +777,7 @@ void og_rhs(og_hier *H, const double *f, const double *g, double *b) {
 
 void og_dgs(og_hier *H, int l, int direction /* +1 forward, -1 backward, 0 symmetric */, double *x, const double *b) {
     og_level *L = &H->lev[l];
+    if (direction == 0 && H->dwj) { og_dwj_sym(L, x, b); return; }
     if (direction >= 0) og_dgs_forward(L, x, b);
     if (direction <= 0) og_dgs_backward(L, x, b);
 }
@@ -748,12 +788,15 @@ void og_vanka(og_hier *H, int l, int colour /* 0..7 one colour, -1 symmetric swe
     else if (H->additive) og_vanka_additive(L, x, b);
     else og_vanka_sym(L, x, b);
 }
-void og_smooth_level(og_hier *H, int l, double *x, const double *b) { og_smooth(&H->lev[l], x, b, H->kb, H->additive); }
+void og_smooth_level(og_hier *H, int l, double *x, const double *b) {
+    og_smooth(&H->lev[l], x, b, H->kb, H->additive, H->dwj);
+}
 /* smoother and cycle variants (Sec. 3.2 additive Vanka; Sec. 8.2 W-cycle) */
-int og_set_variant(og_hier *H, int additive, int cycle) {
-    if (!H || (additive != 0 && additive != 1) || cycle < 1 || cycle > 2) return OG_ERR_ARG;
+int og_set_variant(og_hier *H, int additive, int cycle, int dwj) {
+    if (!H || (additive != 0 && additive != 1) || cycle < 1 || cycle > 2 || (dwj != 0 && dwj != 1)) return OG_ERR_ARG;
     H->additive = additive;
     H->cycle = cycle;
+    H->dwj = dwj;
     return OG_OK;
 }
 void og_restrict_level(og_hier *H, int l, const double *rf, double *bc) { og_restrict(&H->lev[l], &H->lev[l + 1], rf, bc); }

@@ -148,13 +148,13 @@ def _assemble(fn, n, active):
 
 
 # eta = 1e-3 is the paper's viscosity (Sec. 7); there the local saddle-point matrices need row pivoting
-@pytest.mark.parametrize("additive", [False, True])
+@pytest.mark.parametrize("variant", ["", "additive", "dwj"])
 @pytest.mark.parametrize("eta", [1.0, 1e-3])
 @pytest.mark.parametrize("which", ["dgs", "vanka", "smooth"])
-def test_smoother_C_symmetric(which, eta, additive):
-    if which == "dgs" and additive:
-        pytest.skip("the DGS sweep does not depend on the Vanka variant")
-    o = oracle.Oracle(6, eta=eta, gamma=1e-3, levels=1, kb=1, additive=additive)
+def test_smoother_C_symmetric(which, eta, variant):
+    if (which == "dgs" and variant == "additive") or (which == "vanka" and variant == "dwj"):
+        pytest.skip("this piece does not depend on the variant")
+    o = oracle.Oracle(6, eta=eta, gamma=1e-3, levels=1, kb=1, additive=variant == "additive", dwj=variant == "dwj")
     act, _ = o.masks()
     z = np.zeros(o.n())
     fn = {"dgs": lambda e: o.dgs(z, e, direction=0),
@@ -222,6 +222,35 @@ def test_additive_vanka_is_damped_sum_of_local_solves():
                 ref[patch] += 0.5 * np.linalg.solve(K, r[patch])
     got = o.vanka(x, b, colour=-1)
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_dwj_is_block_sequential_weighted_jacobi():
+    # Sec. 3.1 DWJ, symmetric: velocity then pressure Jacobi steps on L~M (right-preconditioned), then
+    # pressure then velocity steps on M^T L~ (left-preconditioned), weight 6/7, V2 rows only
+    n = 6
+    o = oracle.Oracle(n, levels=1, coarsest_max=2, dwj=True)
+    D = DenseBox(n)
+    Lt = D.Lt.toarray()
+    M = D.M.toarray()
+    d = np.diag(Lt @ M)
+    v2 = D.active & ~D.v1
+    vel = v2.copy()
+    vel[D.offsets[3]:] = False
+    pre = v2 & ~vel
+    w = 6.0 / 7.0
+    x = _masked(_rand(D.n, 43), D.active)
+    b = _masked(_rand(D.n, 44), D.active)
+    y = x.copy()
+    r = b - Lt @ y
+    y[vel] += w * r[vel] / d[vel]
+    r = b - Lt @ y
+    y += w * M[:, pre] @ (r[pre] / d[pre])
+    r = b - Lt @ y
+    y[pre] += w * (M[:, pre].T @ r) / d[pre]
+    r = b - Lt @ y
+    y[vel] += w * r[vel] / d[vel]
+    got = o.dgs(x, b, direction=0)
+    assert np.max(np.abs(got - y)) < 1e-12 * np.max(np.abs(y))
 
 
 def test_wcycle_two_levels_equals_vcycle():
