@@ -505,12 +505,14 @@ def run_warmstart(args, smg, synthetic, torch, dev, rank, world):
 
 def run_variants(args, smg, synthetic, torch, dev, rank, world, dist):
     """The method's variants on the headline workload (n^3 bumps, FP32 V-cycle, FP64 SQMR, tol): k_b = 1, 2, 3
-    symmetric Vanka sweeps (Alg. 3), the W-cycle (Sec. 8.2) and the damped additive Vanka (Eq. av)."""
+    symmetric Vanka sweeps (Alg. 3), the W-cycle (Sec. 8.2), the damped additive Vanka (Eq. av) and the
+    symmetric distributive weighted Jacobi (Sec. 3.1)."""
     n = args.n
     rows = []
     for name, kw in [("V, k_b=1 (default)", {}), ("V, k_b=2", {"kb_vanka": 2}), ("V, k_b=3", {"kb_vanka": 3}),
                      ("W, k_b=1", {"cycle": 2}), ("V, additive Vanka, k_b=1", {"additive": True}),
-                     ("V, additive Vanka, k_b=3", {"additive": True, "kb_vanka": 3})]:
+                     ("V, additive Vanka, k_b=3", {"additive": True, "kb_vanka": 3}),
+                     ("V, distributive weighted Jacobi", {"dwj": True})]:
         S = smg.Stokes(n, precision=smg.PREC_FP32, **kw)
         b = S.rhs(synthetic.bumps(n, seed=0, device=dev)["f"], None)
         x = torch.zeros_like(b)

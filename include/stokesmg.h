@@ -90,6 +90,9 @@ typedef struct {
                            Eq. (av) in its place, damped by 1/2 (a face lies in two patches; the
                            undamped sum over-corrects) -- symmetric as well (Sec. 3.2 variant) */
     int cycle;     /* coarse-grid visits per level: 1 (default) V-cycle (Alg. 1), 2 W-cycle (Sec. 8.2) */
+    int distributive_jacobi; /* 0 (default): symmetric DGS on V2 (Alg. 2 + Eq. ldist); 1: symmetric
+                                distributive weighted Jacobi (Sec. 3.1), one Jacobi step per block of
+                                L~M in the DGS block order and its reverse, weight 6/7 */
 } stokes_opts_t;
 
 typedef struct {

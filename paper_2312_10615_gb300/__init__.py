@@ -50,7 +50,7 @@ class stokes_bc_t(ctypes.Structure):
 class stokes_opts_t(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("kb_vanka", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("vanka_persistent", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("vanka_additive", ctypes.c_int), ("cycle", ctypes.c_int)]
+                ("vanka_additive", ctypes.c_int), ("cycle", ctypes.c_int), ("distributive_jacobi", ctypes.c_int)]
 
 
 class sqmr_info_t(ctypes.Structure):
@@ -167,12 +167,13 @@ def stokes_opts_default():
 
 
 def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest_max=8, gamma=1e-3, kb_vanka=1,
-                  precision=PREC_FP64, use_graphs=True, vanka_persistent=False, autotune=True, additive=False, cycle=1):
+                  precision=PREC_FP64, use_graphs=True, vanka_persistent=False, autotune=True, additive=False, cycle=1,
+                  dwj=False):
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     g = stokes_grid_t(nx, ny, nz, h, levels, coarsest_max)
     o = stokes_opts_t(gamma, kb_vanka, precision, int(bool(use_graphs)), int(bool(vanka_persistent)),
-                      int(bool(autotune)), int(bool(additive)), int(cycle))
+                      int(bool(autotune)), int(bool(additive)), int(cycle), int(bool(dwj)))
     hdl = ctypes.c_void_p()
     _check(lib().stokes_create(ctypes.byref(g), None, viscosity, ctypes.byref(o), ctypes.byref(hdl)), "stokes_create")
     return hdl

@@ -25,6 +25,9 @@ template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, 
 template <class T, class TB>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const TB *b, TB *gh, const T *delta, cudaStream_t s);
 template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s);
+// symmetric distributive weighted Jacobi on V2 (Sec. 3.1), weight w; t: level-size scratch, delta: per cell
+template <class T, class TB>
+void launch_dwj_sym(const Lev &L, T *x, const TB *b, T *t, T *delta, double w, cudaStream_t s);
 // one colour of the multiplicative Vanka sweep on V1 (compute corrections, then add them)
 // corrections scaled by w (1 for the multiplicative sweep, 1/2 for the damped additive step)
 template <class T, class TB>

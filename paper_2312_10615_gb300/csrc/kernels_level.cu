@@ -7,6 +7,8 @@
 // so a warp reads one 128-byte line of FP32 values), the component folded into gridDim.y, 32-bit
 // coordinates taken straight from the block/thread indices (no integer division), 64-bit only in
 // the final address.  No tensor cores: nothing here is a contraction.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace smg {
@@ -793,6 +795,153 @@ cudaError_t launch_vanka_cluster(const Lev &L, T *x, const TB *b, const VankaLis
 }
 
 // ------------------------------------------------------------------------------------------
+// Sec. 3.1 distributive weighted Jacobi (symmetric, block by block; see launch order in the host
+// code): every step computes its updates from one state into a buffer, then adds them.
+__device__ __forceinline__ bool v2_face(const Lev &L, int c, int i, int j, int k) {
+    const int n[3] = {L.nx, L.ny, L.nz}, q[3] = {i, j, k};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int lo = d == c ? 2 : 1, hi = d == c ? n[d] - 2 : n[d] - 2;
+        if (q[d] < lo || q[d] > hi) return false;
+    }
+    return true;
+}
+
+// velocity block: t_f = w (b - L~x)_f / (6 eta/h^2) on the V2 faces, 0 on every other face entry
+template <class T, class TB, int C, class IDX>
+__device__ __forceinline__ void dwj_face_entry(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
+                                               T *__restrict__ t, const Coef<T> &K, T w, int i, int j, int k) {
+    if (!entry_exists<C>(L, i, j, k)) return;
+    const long long q = entry_index<C, IDX>(L, i, j, k);
+    T v = T(0);
+    if (v2_face(L, C, i, j, k)) v = w * (T(ldv(b[q])) - row_at<T, C, true, IDX>(x, L, i, j, k, K)) / (T(6) * K.eh2);
+    t[q] = v;
+}
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(256, 8) k_dwj_face(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
+                                                     T *__restrict__ t, Coef<T> K, T w) {
+    pdl_wait();
+    const int c = blockIdx.z % 3, k = blockIdx.z / 3;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    switch (c) {
+    case 0: dwj_face_entry<T, TB, 0, IDX>(L, x, b, t, K, w, i, j, k); break;
+    case 1: dwj_face_entry<T, TB, 1, IDX>(L, x, b, t, K, w, i, j, k); break;
+    default: dwj_face_entry<T, TB, 2, IDX>(L, x, b, t, K, w, i, j, k);
+    }
+}
+// x_f += t_f on the face entries
+template <class T>
+__global__ void __launch_bounds__(256) k_add_faces(long long nf, T *__restrict__ x, const T *__restrict__ t) {
+    pdl_wait();
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += (long long)gridDim.x * blockDim.x)
+        x[q] += t[q];
+}
+// pressure block, right-preconditioned: delta_c = (b - L~x)_c / d on the V2 cells, 0 elsewhere
+template <class T, class TB>
+__global__ void __launch_bounds__(256) k_dwj_pdelta(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
+                                                    T *__restrict__ delta, Coef<T> K, T dP) {
+    pdl_wait();
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny || k >= L.nz) return;
+    const long long cl = cell_lin(L, i, j, k);
+    T v = T(0);
+    if (in_v2_cell(L, i, j, k)) v = (T(ldv(b[L.off[3] + cl])) - row_at<T, 3, true, long long>(x, L, i, j, k, K)) / dP;
+    delta[cl] = v;
+}
+// x += w sum_c delta_c M_{.c}: faces -= w (delta_plus - delta_minus)/h, cells += w eta/h^2 (6 delta_c -
+// sum of the 6 neighbours); delta is 0 outside V2, so every neighbour a nonzero delta needs exists
+template <class T, int C>
+__device__ __forceinline__ void dwj_dist_entry(const Lev &L, T *__restrict__ x, const T *__restrict__ delta,
+                                               const Coef<T> &K, T w, int i, int j, int k) {
+    if (!entry_exists<C>(L, i, j, k) || !entry_active<C>(L, i, j, k)) return;
+    const long long q = entry_index<C, long long>(L, i, j, k);
+    const long long sy = L.nx, sz = (long long)L.nx * L.ny;
+    if constexpr (C < 3) {
+        const long long plus = cell_lin(L, i, j, k), ps = C == 0 ? 1 : (C == 1 ? sy : sz);
+        x[q] -= w * K.ih * (delta[plus] - delta[plus - ps]);
+    } else {
+        const long long t = cell_lin(L, i, j, k);
+        T g = T(6) * delta[t];
+        g -= (i > 0 ? delta[t - 1] : T(0)) + (i < L.nx - 1 ? delta[t + 1] : T(0));
+        g -= (j > 0 ? delta[t - sy] : T(0)) + (j < L.ny - 1 ? delta[t + sy] : T(0));
+        g -= (k > 0 ? delta[t - sz] : T(0)) + (k < L.nz - 1 ? delta[t + sz] : T(0));
+        x[q] += w * K.eh2 * g;
+    }
+}
+template <class T>
+__global__ void __launch_bounds__(256, 8) k_dwj_pdist(Lev L, T *__restrict__ x, const T *__restrict__ delta, Coef<T> K,
+                                                      T w) {
+    pdl_wait();
+    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    switch (c) {
+    case 0: dwj_dist_entry<T, 0>(L, x, delta, K, w, i, j, k); break;
+    case 1: dwj_dist_entry<T, 1>(L, x, delta, K, w, i, j, k); break;
+    case 2: dwj_dist_entry<T, 2>(L, x, delta, K, w, i, j, k); break;
+    default: dwj_dist_entry<T, 3>(L, x, delta, K, w, i, j, k);
+    }
+}
+// r = b - L~x into a buffer of the arithmetic type (every packed entry)
+template <class T, class TB, int C>
+__device__ __forceinline__ void resid_entry(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
+                                            T *__restrict__ r, const Coef<T> &K, int i, int j, int k) {
+    if (!entry_exists<C>(L, i, j, k)) return;
+    const long long q = entry_index<C, long long>(L, i, j, k);
+    r[q] = entry_active<C>(L, i, j, k) ? T(ldv(b[q])) - row_at<T, C, true, long long>(x, L, i, j, k, K) : T(0);
+}
+template <class T, class TB>
+__global__ void __launch_bounds__(256, 8) k_resid_t(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
+                                                    T *__restrict__ r, Coef<T> K) {
+    pdl_wait();
+    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    switch (c) {
+    case 0: resid_entry<T, TB, 0>(L, x, b, r, K, i, j, k); break;
+    case 1: resid_entry<T, TB, 1>(L, x, b, r, K, i, j, k); break;
+    case 2: resid_entry<T, TB, 2>(L, x, b, r, K, i, j, k); break;
+    default: resid_entry<T, TB, 3>(L, x, b, r, K, i, j, k);
+    }
+}
+// pressure block, left-preconditioned: p_c += w M_{.c}^T r / d on the V2 cells
+template <class T>
+__global__ void __launch_bounds__(256) k_dwj_pleft(Lev L, T *__restrict__ x, const T *__restrict__ r, Coef<T> K, T w,
+                                                   T dP) {
+    pdl_wait();
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny || k >= L.nz || !in_v2_cell(L, i, j, k)) return;
+    const long long nx = L.nx, ny = L.ny, sy = nx, sz = nx * ny;
+    const long long cl = cell_lin(L, i, j, k);
+    const T *rc = r + L.off[3] + cl;
+    const T *ru = r + L.off[0] + (i + (nx + 1) * (j + ny * k));
+    const T *rv = r + L.off[1] + (i + nx * (j + (ny + 1) * k));
+    const T *rw = r + L.off[2] + (i + nx * (j + ny * k));
+    const T s = K.ih * ((ru[1] - ru[0]) + (rv[sy] - rv[0]) + (rw[sz] - rw[0])) +
+                K.eh2 * (T(6) * rc[0] - (rc[-1] + rc[1] + rc[-sy] + rc[sy] + rc[-sz] + rc[sz]));
+    x[L.off[3] + cl] += w * s / dP;
+}
+
+template <class T, class TB>
+void launch_dwj_sym(const Lev &L, T *x, const TB *b, T *t, T *delta, double w, cudaStream_t s) {
+    const Coef<T> K = coef<T>(L, L.gamma);
+    const T W = T(w), dP = dgs_pressure_diag<T>(L);
+    const long long nf = L.off[3];
+    const dim3 fgrid(cdiv(L.nx + 1, BX), cdiv(L.ny + 1, BY), 3 * (L.nz + 1));
+    const dim3 cgrid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz);
+    const int ab = (int)std::min<long long>(4736, (nf + 255) / 256);
+    auto vel = [&]() {
+        if (idx32(L)) launch_k(k_dwj_face<T, TB, int>, fgrid, dim3(kBlock3), 0, s, L, (const T *)x, b, t, K, W);
+        else launch_k(k_dwj_face<T, TB, long long>, fgrid, dim3(kBlock3), 0, s, L, (const T *)x, b, t, K, W);
+        launch_k(k_add_faces<T>, dim3(ab), dim3(256), 0, s, nf, x, (const T *)t);
+    };
+    vel();
+    launch_k(k_dwj_pdelta<T, TB>, cgrid, dim3(kBlock3), 0, s, L, (const T *)x, b, delta, K, dP);
+    launch_k(k_dwj_pdist<T>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, (const T *)delta, K, W);
+    launch_k(k_resid_t<T, TB>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, (const T *)x, b, t, K);
+    launch_k(k_dwj_pleft<T>, cgrid, dim3(kBlock3), 0, s, L, x, (const T *)t, K, W, dP);
+    vel();
+}
+
+// ------------------------------------------------------------------------------------------
 // Sec. 2 transfers.  P (coarse -> fine): pressure constant per coarse cell; a face value takes
 // weight 1 from a coincident coarse face or 1/2 + 1/2 from the two coarse faces around it along
 // its normal, and 3/4 (coarse row containing it) + 1/4 (next coarse row on the far side) along
@@ -1018,6 +1167,10 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
 SMG_INST(float)
 SMG_INST(double)
 SMG_INST_TB(float, bf16)
+template void launch_dwj_sym<float, float>(const Lev &, float *, const float *, float *, float *, double, cudaStream_t);
+template void launch_dwj_sym<double, double>(const Lev &, double *, const double *, double *, double *, double,
+                                             cudaStream_t);
+template void launch_dwj_sym<float, bf16>(const Lev &, float *, const bf16 *, float *, float *, double, cudaStream_t);
 template void launch_restrict<float, bf16, bf16>(const Lev &, const Lev &, const bf16 *, bf16 *, cudaStream_t);
 template void launch_restrict<float, bf16, float>(const Lev &, const Lev &, const bf16 *, float *, cudaStream_t);
 template void launch_restrict<float, float, bf16>(const Lev &, const Lev &, const float *, bf16 *, cudaStream_t);

@@ -34,6 +34,7 @@ namespace {
 struct LevelBuf {
     Lev L;
     void *x = nullptr, *b = nullptr, *r = nullptr, *delta = nullptr, *kinv = nullptr, *corr = nullptr;
+    void *t = nullptr;  // level-size scratch of the arithmetic type (distributive weighted Jacobi)
     int *vcells[8] = {};
     int vcount[8] = {};
     int vcap = 0;
@@ -169,6 +170,7 @@ struct stokes_s {
     int nbf = 0;               // finest levels whose b, r are stored as BF16 (STOKES_PREC_MIXED_BF16)
     int additive = 0;          // Vanka variant: 0 symmetric multiplicative sweep, 1 damped additive (Eq. av)
     int cycle = 1;             // coarse-grid visits per level: 1 V-cycle, 2 W-cycle
+    int dwj = 0;               // 1: symmetric distributive weighted Jacobi in place of the symmetric DGS
     GridBarrier *bar = nullptr;
     double eta = 1.0, gamma = 1e-3;
     std::vector<LevelBuf> lev;
@@ -328,10 +330,23 @@ template <class T, class TB> void dgs_backward(stokes_s *h, int l, cudaStream_t 
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
 }
-template <class T, class TB> void smooth(stokes_s *h, int l, cudaStream_t s) {
-    vanka_sym<T, TB>(h, l, s, h->kb);
+// Sec. 3.1 variant: symmetric distributive weighted Jacobi, weight 6/7 (the paper gives none; the
+// classical pointwise-Jacobi smoothing weight of the 7-point Laplacian)
+constexpr double kDwjOmega = 6.0 / 7.0;
+template <class T, class TB> void dist_sym(stokes_s *h, int l, cudaStream_t s) {
+    LevelBuf &B = h->lev[l];
+    if (h->dwj) {
+        prof(STOKES_K_DGS_U, l, s, [&] {
+            launch_dwj_sym<T, TB>(B.L, (T *)B.x, (const TB *)B.b, (T *)B.t, (T *)B.delta, kDwjOmega, s);
+        });
+        return;
+    }
     dgs_forward<T, TB>(h, l, s);
     dgs_backward<T, TB>(h, l, s, true);
+}
+template <class T, class TB> void smooth(stokes_s *h, int l, cudaStream_t s) {
+    vanka_sym<T, TB>(h, l, s, h->kb);
+    dist_sym<T, TB>(h, l, s);
     vanka_sym<T, TB>(h, l, s, h->kb);
 }
 template <class T> void smooth_level(stokes_s *h, int l, cudaStream_t s) {
@@ -619,6 +634,7 @@ void stokes_opts_default(stokes_opts_t *o) {
     o->autotune = 1;
     o->vanka_additive = 0;
     o->cycle = 1;
+    o->distributive_jacobi = 0;
 }
 
 const char *stokes_strerror(int st) {
@@ -649,7 +665,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     if (opts) o = *opts;
     if (!(o.gamma >= 0.0) || o.kb_vanka < 0 ||
         (o.precision != STOKES_PREC_FP64 && o.precision != STOKES_PREC_FP32 && o.precision != STOKES_PREC_MIXED_BF16) ||
-        (o.vanka_additive != 0 && o.vanka_additive != 1) || o.cycle < 1 || o.cycle > 2)
+        (o.vanka_additive != 0 && o.vanka_additive != 1) || o.cycle < 1 || o.cycle > 2 ||
+        (o.distributive_jacobi != 0 && o.distributive_jacobi != 1))
         return STOKES_ERR_INVALID_ARG;
     int cmax = grid->coarsest_max > 0 ? grid->coarsest_max : 8;
     int nlev = grid->levels;
@@ -675,6 +692,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     h->vanka_persistent = o.vanka_persistent;
     h->additive = o.vanka_additive;
     h->cycle = o.cycle;
+    h->dwj = o.distributive_jacobi;
     h->eta = viscosity;
     h->gamma = o.gamma;
     double hh = grid->h > 0 ? grid->h : 1.0 / grid->nx;
@@ -723,6 +741,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
         if ((rc = h->alloc(&B.b, esb * L.n))) return rc;
         if ((rc = h->alloc(&B.r, esb * L.n))) return rc;
         if ((rc = h->alloc(&B.delta, es * (size_t)L.nx * L.ny * L.nz))) return rc;
+        if (h->dwj && (rc = h->alloc(&B.t, es * L.n))) return rc;
         // V1 cells (interior cells with a face on the ghost shell) by colour
         std::vector<int> cells[8];
         for (int k = 0; k < L.nz; ++k)
@@ -1150,7 +1169,7 @@ int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, 
         using TB = decltype(tb);
         switch (which) {
         case 0: smooth<T, TB>(h, level, s); break;
-        case 1: dgs_forward<T, TB>(h, level, s); dgs_backward<T, TB>(h, level, s, true); break;
+        case 1: dist_sym<T, TB>(h, level, s); break;
         case 2: vanka_sym<T, TB>(h, level, s); break;
         case 3: dgs_forward<T, TB>(h, level, s); dgs_finish_forward<T>(h, level, s); break;
         case 4: dgs_backward<T, TB>(h, level, s, false); break;

@@ -305,7 +305,7 @@ def test_sqmr_fp32_vcycle_accuracy():
 
 # ---------------------------------------------------------------------------------------------- variants
 
-VARIANTS = [dict(kb=2), dict(kb=3), dict(cycle=2), dict(additive=True), dict(additive=True, kb=3)]
+VARIANTS = [dict(kb=2), dict(kb=3), dict(cycle=2), dict(additive=True), dict(additive=True, kb=3), dict(dwj=True)]
 
 
 @pytest.mark.parametrize("kw", VARIANTS, ids=lambda kw: "-".join(f"{k}{v}" for k, v in kw.items()))
