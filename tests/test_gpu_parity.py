@@ -332,6 +332,20 @@ def test_variant_parity(kw):
     S.close()
 
 
+def test_variants_non_cubic():
+    # the variant kernels on a box whose axes differ (strides, V2 ranges, colour counts per axis)
+    for kw in (dict(dwj=True), dict(additive=True), dict(cycle=2)):
+        o = oracle.Oracle(24, 16, 32, coarsest_max=8, **kw)
+        S = smg.Stokes(24, 16, 32, **kw)
+        x, b = rand_masked(o, 53), rand_masked(o, 54)
+        got = cuda(x)
+        smg.stokes_smooth(S.h, 0, 0, got, cuda(b))
+        assert rel_err(got, o.smooth(x, b)) < 1e-12, kw
+        s = rand_masked(o, 55)
+        assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-11, kw
+        S.close()
+
+
 # ---------------------------------------------------------------------------------------------- BF16 levels
 
 def test_mixed_bf16_pieces_close_to_oracle():
