@@ -67,9 +67,15 @@ typedef struct {
 } stokes_grid_t;
 
 typedef struct {
-    /* cell labels on the ghost-extended cell grid (nx+2)(ny+2)(nz+2), 0 interior, 1 Dirichlet,
-     * 2 exterior (Sec. 5).  NULL = the box (all interior, one Dirichlet ghost shell).  Only NULL
-     * is implemented; anything else returns STOKES_ERR_UNSUPPORTED. */
+    /* cell labels on the ghost-extended cell grid (nx+2)(ny+2)(nz+2), x fastest, index
+     * (i+1) + (nx+2)((j+1) + (ny+2)(k+1)) for cell (i,j,k), i = -1..nx: 0 interior, 1 Dirichlet,
+     * 2 exterior (Sec. 5).  The ghost shell must be Dirichlet (else STOKES_ERR_INVALID_ARG); interior
+     * Dirichlet cells (obstacles) are supported: faces between two interior cells and interior-cell
+     * pressures are the unknowns, faces of Dirichlet cells carry Dirichlet data (the ghost-extended
+     * Dirichlet layout covers them), V1 holds the unknowns of interior cells next to a Dirichlet
+     * cell, coarse labels follow Sec. 5.  Exterior cells (Neumann faces) return
+     * STOKES_ERR_UNSUPPORTED.  NULL = the box (all interior, one Dirichlet ghost shell).  The array
+     * is copied; the caller keeps ownership. */
     const uint8_t *cell_labels;
 } stokes_bc_t;
 

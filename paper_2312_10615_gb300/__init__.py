@@ -168,14 +168,24 @@ def stokes_opts_default():
 
 def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest_max=8, gamma=1e-3, kb_vanka=1,
                   precision=PREC_FP64, use_graphs=True, vanka_persistent=False, autotune=True, additive=False, cycle=1,
-                  dwj=False):
+                  dwj=False, labels=None):
+    """labels: None (the box) or a uint8 array of (nx+2)(ny+2)(nz+2) cell labels, x fastest (0 interior,
+    1 Dirichlet); it is copied by the library."""
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     g = stokes_grid_t(nx, ny, nz, h, levels, coarsest_max)
     o = stokes_opts_t(gamma, kb_vanka, precision, int(bool(use_graphs)), int(bool(vanka_persistent)),
                       int(bool(autotune)), int(bool(additive)), int(cycle), int(bool(dwj)))
+    bc = None
+    if labels is not None:
+        import numpy as np
+        lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8).reshape(-1))
+        if lab.size != (nx + 2) * (ny + 2) * (nz + 2):
+            raise ValueError("labels must hold (nx+2)(ny+2)(nz+2) entries")
+        bc = stokes_bc_t(lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     hdl = ctypes.c_void_p()
-    _check(lib().stokes_create(ctypes.byref(g), None, viscosity, ctypes.byref(o), ctypes.byref(hdl)), "stokes_create")
+    _check(lib().stokes_create(ctypes.byref(g), None if bc is None else ctypes.byref(bc), viscosity,
+                               ctypes.byref(o), ctypes.byref(hdl)), "stokes_create")
     return hdl
 
 

@@ -52,9 +52,7 @@ __host__ __device__ inline void v2_colour_range(const Lev &L, int colour, int lo
         cnt[d] = (n[d] - 2 >= lo[d]) ? (n[d] - 2 - lo[d]) / 2 + 1 : 0;
     }
 }
-__device__ __forceinline__ bool in_v2_cell(const Lev &L, int i, int j, int k) {
-    return i >= 1 && j >= 1 && k >= 1 && i <= L.nx - 2 && j <= L.ny - 2 && k <= L.nz - 2;
-}
+__device__ __forceinline__ bool in_v2_cell(const Lev &L, int i, int j, int k) { return v2_cell_at(L, i, j, k); }
 __device__ __forceinline__ long long cell_lin(const Lev &L, int i, int j, int k) {
     return i + (long long)L.nx * (j + (long long)L.ny * k);
 }
@@ -121,6 +119,10 @@ template <int C> __device__ __forceinline__ bool entry_active(const Lev &L, int 
     if (C == 2) return k >= 1 && k <= L.nz - 1;
     return true;
 }
+// entry_active for an existing entry at packed index q, with the label flags where the domain has them
+template <int C> __device__ __forceinline__ bool entry_unknown(const Lev &L, int i, int j, int k, long long q) {
+    return entry_active<C>(L, i, j, k) && (!L.flags || (L.flags[q] & kFlagActive));
+}
 template <int C, class IDX> __device__ __forceinline__ long long entry_index(const Lev &L, int i, int j, int k) {
     const IDX sy = (IDX)(L.nx + (C == 0)), sz = sy * (IDX)(L.ny + (C == 1));
     return L.off[C] + (long long)((IDX)i + sy * (IDX)j + sz * (IDX)k);
@@ -135,7 +137,7 @@ __device__ __forceinline__ void apply_entry(const Lev &L, const T *__restrict__ 
     if (!entry_exists<C>(L, i, j, k)) return;
     const long long q = entry_index<C, IDX>(L, i, j, k);
     T v = T(0);
-    if (entry_active<C>(L, i, j, k)) {
+    if (entry_unknown<C>(L, i, j, k, q)) {
         v = row_at<T, C, true, IDX>(x, L, i, j, k, K);
         if (b) v = T(ldv(b[q])) - v;
     }
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__rest
     if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
     for (int k = k0; k < k1; ++k) {
     long long q = pidx(L, c, i, j, k);
-    if (!active(L, c, i, j, k)) {
+    if (!unknown(L, c, i, j, k)) {
         b[q] = 0.0;
         continue;
     }
@@ -191,13 +193,13 @@ __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__rest
             const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
             for (int m = 0; m < 6; ++m) {
                 int a = i + di[m], bb = j + dj[m], cc = k + dk[m];
-                if (!active(L, c, a, bb, cc)) v += K.eh2 * g[gidx(L, c, a, bb, cc)];
+                if (!unknown(L, c, a, bb, cc)) v += K.eh2 * g[gidx(L, c, a, bb, cc)];
             }
         } else {
             for (int d = 0; d < 3; ++d) {
                 int hi = i + (d == 0), hj = j + (d == 1), hk = k + (d == 2);
-                if (!active(L, d, hi, hj, hk)) v += K.ih * g[gidx(L, d, hi, hj, hk)];
-                if (!active(L, d, i, j, k)) v -= K.ih * g[gidx(L, d, i, j, k)];
+                if (!unknown(L, d, hi, hj, hk)) v += K.ih * g[gidx(L, d, hi, hj, hk)];
+                if (!unknown(L, d, i, j, k)) v -= K.ih * g[gidx(L, d, i, j, k)];
             }
         }
     }
@@ -240,17 +242,21 @@ __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, cons
     const IDX ci = (IDX)i, cj = (IDX)j, ck = (IDX)k;
     const T *pp = x + L.off[3] + (ci + nx * (cj + ny * ck));
     const T pc = pp[0];
-    if (i >= 2) {
+    const uint8_t *fl = L.flags;  // label domains: a face is relaxed only if both its cells are V2
+    {
         const IDX o = ci + uy * cj + uz * ck;
-        dgs_face<T, TB, IDX>(x + L.off[0] + o, b + L.off[0] + o, uy, uz, pc, pp[-1], K);
+        if (i >= 2 && (!fl || (fl[L.off[0] + o] & kFlagV2)))
+            dgs_face<T, TB, IDX>(x + L.off[0] + o, b + L.off[0] + o, uy, uz, pc, pp[-1], K);
     }
-    if (j >= 2) {
+    {
         const IDX o = ci + nx * cj + vz * ck;
-        dgs_face<T, TB, IDX>(x + L.off[1] + o, b + L.off[1] + o, nx, vz, pc, pp[-nx], K);
+        if (j >= 2 && (!fl || (fl[L.off[1] + o] & kFlagV2)))
+            dgs_face<T, TB, IDX>(x + L.off[1] + o, b + L.off[1] + o, nx, vz, pc, pp[-nx], K);
     }
-    if (k >= 2) {
+    {
         const IDX o = ci + nx * cj + wz * ck;
-        dgs_face<T, TB, IDX>(x + L.off[2] + o, b + L.off[2] + o, nx, wz, pc, pp[-wz], K);
+        if (k >= 2 && (!fl || (fl[L.off[2] + o] & kFlagV2)))
+            dgs_face<T, TB, IDX>(x + L.off[2] + o, b + L.off[2] + o, nx, wz, pc, pp[-wz], K);
     }
 }
 
@@ -280,6 +286,7 @@ __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, con
     const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
     const IDX sy = nx, sz = nx * ny;
     const IDX cl = i + nx * (j + ny * k);
+    if (L.flags && !(L.flags[L.off[3] + cl] & kFlagV2)) return;  // label domains: V2 cells only
     T *dc = delta + cl;
     T g = T(0);
     if (colour & 1) g += dc[-1] + dc[1];
@@ -345,7 +352,7 @@ __device__ __forceinline__ void prep_entry(const Lev &L, T *__restrict__ x, cons
     if (!entry_exists<C>(L, i, j, k)) return;
     const long long q = entry_index<C, IDX>(L, i, j, k);
     T v = T(0);
-    if (entry_active<C>(L, i, j, k)) v = T(ldv(b[q])) - row_at<T, C, false, IDX>(x, L, i, j, k, K);
+    if (entry_unknown<C>(L, i, j, k, q)) v = T(ldv(b[q])) - row_at<T, C, false, IDX>(x, L, i, j, k, K);
     gh[q] = cvt<TB>(v);
     if (C == 3 && delta) {
         const IDX sy = (IDX)L.nx, sz = sy * (IDX)L.ny;
@@ -387,6 +394,7 @@ __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, con
     const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
     const IDX sy = nx, sz = nx * ny;
     const IDX cl = i + nx * (j + ny * k);
+    if (L.flags && !(L.flags[L.off[3] + cl] & kFlagV2)) return;  // label domains: V2 cells only
     T *pp = x + L.off[3] + cl;
     const T pc = pp[0], pxm = pp[-1], pxp = pp[1], pym = pp[-sy], pyp = pp[sy], pzm = pp[-sz], pzp = pp[sz];
     const TB *gc = ghs + L.off[3] + cl;
@@ -494,8 +502,10 @@ __device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__rest
                                                    T w = T(1)) {
     int i, j, k;
     unpack_cell(cellw, i, j, k);
-    const int cfg = (i >= 1) | ((i + 1 <= L.nx - 1) << 1) | ((j >= 1) << 2) | ((j + 1 <= L.ny - 1) << 3) |
-                    ((k >= 1) << 4) | ((k + 1 <= L.nz - 1) << 5);
+    // which of the cell's six faces are unknowns (6-bit configuration of the pre-factorised inverses)
+    const int cfg = (int)unknown(L, 0, i, j, k) | ((int)unknown(L, 0, i + 1, j, k) << 1) |
+                    ((int)unknown(L, 1, i, j, k) << 2) | ((int)unknown(L, 1, i, j + 1, k) << 3) |
+                    ((int)unknown(L, 2, i, j, k) << 4) | ((int)unknown(L, 2, i, j, k + 1) << 5);
     T r = T(0);
     if (a < 6) {
         if ((cfg >> a) & 1) r = vanka_face_residual(L, x, b, a, i, j, k, K);
@@ -527,7 +537,7 @@ __device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x
         const long long sy = nx + (d == 0), sz = sy * (ny + (d == 1));
         q = (d == 0 ? L.off[0] : (d == 1 ? L.off[1] : L.off[2])) + fi + sy * fj + sz * fk;
         const int nrm = d == 0 ? fi : (d == 1 ? fj : fk), nn = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
-        act = nrm >= 1 && nrm <= nn - 1;
+        act = nrm >= 1 && nrm <= nn - 1 && (!L.flags || (L.flags[q] & kFlagActive));
     }
     if (act) x[q] += corr[(long long)a * cap + slot];
 }
@@ -804,7 +814,7 @@ __device__ __forceinline__ bool v2_face(const Lev &L, int c, int i, int j, int k
         const int lo = d == c ? 2 : 1, hi = d == c ? n[d] - 2 : n[d] - 2;
         if (q[d] < lo || q[d] > hi) return false;
     }
-    return true;
+    return !L.flags || (L.flags[pidx(L, c, i, j, k)] & kFlagV2);
 }
 
 // velocity block: t_f = w (b - L~x)_f / (6 eta/h^2) on the V2 faces, 0 on every other face entry
@@ -853,8 +863,9 @@ __global__ void __launch_bounds__(256) k_dwj_pdelta(Lev L, const T *__restrict__
 template <class T, int C>
 __device__ __forceinline__ void dwj_dist_entry(const Lev &L, T *__restrict__ x, const T *__restrict__ delta,
                                                const Coef<T> &K, T w, int i, int j, int k) {
-    if (!entry_exists<C>(L, i, j, k) || !entry_active<C>(L, i, j, k)) return;
+    if (!entry_exists<C>(L, i, j, k)) return;
     const long long q = entry_index<C, long long>(L, i, j, k);
+    if (!entry_unknown<C>(L, i, j, k, q)) return;
     const long long sy = L.nx, sz = (long long)L.nx * L.ny;
     if constexpr (C < 3) {
         const long long plus = cell_lin(L, i, j, k), ps = C == 0 ? 1 : (C == 1 ? sy : sz);
@@ -887,7 +898,7 @@ __device__ __forceinline__ void resid_entry(const Lev &L, const T *__restrict__ 
                                             T *__restrict__ r, const Coef<T> &K, int i, int j, int k) {
     if (!entry_exists<C>(L, i, j, k)) return;
     const long long q = entry_index<C, long long>(L, i, j, k);
-    r[q] = entry_active<C>(L, i, j, k) ? T(ldv(b[q])) - row_at<T, C, true, long long>(x, L, i, j, k, K) : T(0);
+    r[q] = entry_unknown<C>(L, i, j, k, q) ? T(ldv(b[q])) - row_at<T, C, true, long long>(x, L, i, j, k, K) : T(0);
 }
 template <class T, class TB>
 __global__ void __launch_bounds__(256, 8) k_resid_t(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
@@ -983,7 +994,7 @@ __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const TF
     if (!thread_entry(C, gy, c, I, J, k0, k1)) return;
     for (int Kk = k0; Kk < k1; ++Kk) {
     long long q = pidx(C, c, I, J, Kk);
-    if (!active(C, c, I, J, Kk)) {
+    if (!unknown(C, c, I, J, Kk)) {
         bc[q] = cvt<TC>(T(0));
         continue;
     }
@@ -1051,7 +1062,9 @@ __device__ __forceinline__ void prolong_comp(const Lev &F, const Lev &Cl, const 
                         T tv = a == 0 ? c[0][p][q] : T(0.5) * (c[0][p][q] + c[1][p][q]);
                         s += w1[p] * w2[q] * tv;
                     }
-                fb[a * fst[C] + bb * fst[t1] + g * fst[t2]] += s;
+                const long long o = a * fst[C] + bb * fst[t1] + g * fst[t2];
+                // label domains: fine faces that are not unknowns keep their 0
+                if (!F.flags || (F.flags[(fb - xf) + o] & kFlagActive)) fb[o] += s;
             }
     }
 }
@@ -1067,7 +1080,10 @@ __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, const T *__restr
         T pcv = ec[pidx(Cl, 3, I, J, Kk)];
         T *pf = xf + F.off[3] + 2 * I + fy * (2 * J) + fz * (2LL * Kk);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) pf[(m & 1) + fy * ((m >> 1) & 1) + fz * ((m >> 2) & 1)] += pcv;
+        for (int m = 0; m < 8; ++m) {
+            const long long o = (m & 1) + fy * ((m >> 1) & 1) + fz * ((m >> 2) & 1);
+            if (!F.flags || (F.flags[(pf - xf) + o] & kFlagActive)) pf[o] += pcv;
+        }
         prolong_comp<T, 0>(F, Cl, ec, xf, I, J, Kk);
         prolong_comp<T, 1>(F, Cl, ec, xf, I, J, Kk);
         prolong_comp<T, 2>(F, Cl, ec, xf, I, J, Kk);
@@ -1118,7 +1134,7 @@ template <class T> __global__ void __launch_bounds__(256) k_mask(Lev L, int gy, 
     int c, i, j, k0, k1;
     if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
     for (int k = k0; k < k1; ++k)
-        if (!active(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = cvt<T>(0.0f);
+        if (!unknown(L, c, i, j, k)) x[pidx(L, c, i, j, k)] = cvt<T>(0.0f);
 }
 template <class T> void launch_mask(const Lev &L, T *x, cudaStream_t s) {
     Geo g = geo_components(L, 4);

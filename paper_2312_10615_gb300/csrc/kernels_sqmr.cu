@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256) k_psum(Lev L, const double *__restrict__ 
     double v[1] = {0.0};
     long long np = L.n - L.off[3];
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
-        v[0] += x[L.off[3] + t];
+        v[0] += x[L.off[3] + t];  // pressures of non-interior cells hold 0
     block_store<1>(v, partials, blockIdx.x);
 }
 __global__ void __launch_bounds__(256) k_psub(Lev L, double *__restrict__ x, const SqmrState *__restrict__ st) {
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256) k_psub(Lev L, double *__restrict__ x, con
     double m = st->pmean;
     long long np = L.n - L.off[3];
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
-        x[L.off[3] + t] -= m;
+        if (!L.flags || (L.flags[L.off[3] + t] & kFlagActive)) x[L.off[3] + t] -= m;
 }
 void launch_psum(const Lev &L, const double *x, double *partials, cudaStream_t s) {
     launch_k(k_psum, dim3(kRedBlocks), dim3(kBlock), 0, s, L, x, partials);

@@ -91,27 +91,83 @@ Lev make_level(int nx, int ny, int nz, double h, double eta, double gamma) {
     return L;
 }
 
+// ---- domains given by cell labels (Sec. 5) on the ghost-extended cell grid, x fastest ----
+struct Labels {
+    int nx = 0, ny = 0, nz = 0;
+    std::vector<uint8_t> lab;  // (nx+2)(ny+2)(nz+2); 0 interior, 1 Dirichlet
+    uint8_t at(int i, int j, int k) const {  // i in -1..nx
+        return lab[(size_t)(i + 1) + (size_t)(nx + 2) * ((j + 1) + (size_t)(ny + 2) * (k + 1))];
+    }
+    bool interior(int i, int j, int k) const { return at(i, j, k) == 0; }
+    // interior cell with a non-interior face neighbour: its unknowns belong to the Vanka set V1
+    bool v1(int i, int j, int k) const {
+        return interior(i, j, k) && (!interior(i - 1, j, k) || !interior(i + 1, j, k) || !interior(i, j - 1, k) ||
+                                     !interior(i, j + 1, k) || !interior(i, j, k - 1) || !interior(i, j, k + 1));
+    }
+};
+// Sec. 5 coarsening: Dirichlet if any child is Dirichlet, else interior (no exterior cells here)
+Labels coarsen(const Labels &F) {
+    Labels C;
+    C.nx = F.nx / 2; C.ny = F.ny / 2; C.nz = F.nz / 2;
+    C.lab.assign((size_t)(C.nx + 2) * (C.ny + 2) * (C.nz + 2), 1);
+    for (int k = 0; k < C.nz; ++k)
+        for (int j = 0; j < C.ny; ++j)
+            for (int i = 0; i < C.nx; ++i) {
+                uint8_t v = 0;
+                for (int m = 0; m < 8; ++m)
+                    if (!F.interior(2 * i + (m & 1), 2 * j + ((m >> 1) & 1), 2 * k + ((m >> 2) & 1))) v = 1;
+                C.lab[(size_t)(i + 1) + (size_t)(C.nx + 2) * ((j + 1) + (size_t)(C.ny + 2) * (k + 1))] = v;
+            }
+    return C;
+}
+// per packed entry: kFlagActive (a face between two interior cells, or an interior cell) and
+// kFlagV2 (a face between two V2 cells, or a V2 cell)
+std::vector<uint8_t> level_flags(const Lev &L, const Labels &B) {
+    std::vector<uint8_t> f((size_t)L.n, 0);
+    for (int c = 0; c < 4; ++c)
+        for (int k = 0; k < ext(L, c, 2); ++k)
+            for (int j = 0; j < ext(L, c, 1); ++j)
+                for (int i = 0; i < ext(L, c, 0); ++i) {
+                    uint8_t v = 0;
+                    if (c == 3) {
+                        if (B.interior(i, j, k)) v = kFlagActive | (B.v1(i, j, k) ? 0 : kFlagV2);
+                    } else {
+                        const int mi = i - (c == 0), mj = j - (c == 1), mk = k - (c == 2);
+                        if (active(L, c, i, j, k) && B.interior(i, j, k) && B.interior(mi, mj, mk)) {
+                            v = kFlagActive;
+                            if (!B.v1(i, j, k) && !B.v1(mi, mj, mk)) v |= kFlagV2;
+                        }
+                    }
+                    f[(size_t)pidx(L, c, i, j, k)] = v;
+                }
+    return f;
+}
+
 // process-wide cache of coarsest-level inverses (set-up cost grows as n^3)
 std::mutex g_cache_mu;
 std::map<std::tuple<int, int, int, double, double, double>, std::shared_ptr<std::vector<double>>> g_coarse_cache;
 
 // dense L~ on the unknowns of level C (written from the stencil of Eq. 2 / Sec. 4), inverted
 // and symmetrised: K^{-1} <- (K^{-1} + K^{-T}) / 2
-int coarse_inverse(const Lev &C, std::vector<int> &cidx, std::shared_ptr<std::vector<double>> &out) {
+int coarse_inverse(const Lev &C, const std::vector<uint8_t> *hflags, std::vector<int> &cidx,
+                   std::shared_ptr<std::vector<double>> &out) {
+    auto unk = [&](int c, int i, int j, int k) {
+        return active(C, c, i, j, k) && (!hflags || ((*hflags)[(size_t)pidx(C, c, i, j, k)] & kFlagActive));
+    };
     std::vector<long long> comp(C.n, -1);
     cidx.clear();
     for (int c = 0; c < 4; ++c)
         for (int k = 0; k < ext(C, c, 2); ++k)
             for (int j = 0; j < ext(C, c, 1); ++j)
                 for (int i = 0; i < ext(C, c, 0); ++i)
-                    if (active(C, c, i, j, k)) {
+                    if (unk(c, i, j, k)) {
                         long long q = pidx(C, c, i, j, k);
                         comp[q] = (long long)cidx.size();
                         cidx.push_back((int)q);
                     }
     int nc = (int)cidx.size();
     auto key = std::make_tuple(C.nx * 1000003 + C.ny, C.nz, nc, C.h, C.eta, C.gamma);
-    {
+    if (!hflags) {  // box levels only: a label domain's coarse matrix depends on its labels
         std::lock_guard<std::mutex> lk(g_cache_mu);
         auto it = g_coarse_cache.find(key);
         if (it != g_coarse_cache.end()) { out = it->second; return 0; }
@@ -119,7 +175,7 @@ int coarse_inverse(const Lev &C, std::vector<int> &cidx, std::shared_ptr<std::ve
     auto K = std::make_shared<std::vector<double>>((size_t)nc * nc, 0.0);
     double e2 = C.eta / (C.h * C.h), ih = 1.0 / C.h;
     auto put = [&](long long r, int c, int i, int j, int k, double v) {
-        if (!active(C, c, i, j, k)) return;
+        if (!unk(c, i, j, k)) return;
         (*K)[(size_t)comp[r] * nc + comp[pidx(C, c, i, j, k)]] += v;
     };
     for (int a = 0; a < nc; ++a) {
@@ -150,7 +206,7 @@ int coarse_inverse(const Lev &C, std::vector<int> &cidx, std::shared_ptr<std::ve
             A[(size_t)r * nc + c] = v;
             A[(size_t)c * nc + r] = v;
         }
-    {
+    if (!hflags) {
         std::lock_guard<std::mutex> lk(g_cache_mu);
         g_coarse_cache[key] = K;
     }
@@ -171,6 +227,7 @@ struct stokes_s {
     int additive = 0;          // Vanka variant: 0 symmetric multiplicative sweep, 1 damped additive (Eq. av)
     int cycle = 1;             // coarse-grid visits per level: 1 V-cycle, 2 W-cycle
     int dwj = 0;               // 1: symmetric distributive weighted Jacobi in place of the symmetric DGS
+    long long ncell_active = 0;  // interior cells of the finest level (pressure-mean removal)
     GridBarrier *bar = nullptr;
     double eta = 1.0, gamma = 1e-3;
     std::vector<LevelBuf> lev;
@@ -659,7 +716,23 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 || !(viscosity > 0.0)) return STOKES_ERR_INVALID_ARG;
     // packed Vanka cell coordinates hold 11 + 11 + 10 bits; the z extent folds into gridDim.z
     if (grid->nx > 2047 || grid->ny > 2047 || grid->nz > 1023) return STOKES_ERR_INVALID_ARG;
-    if (bc && bc->cell_labels) return STOKES_ERR_UNSUPPORTED;
+    // cell labels (Sec. 5): ghost shell Dirichlet, interior cells 0 or 1; exterior cells (2) are not
+    // built.  A label array that describes the plain box is treated as the box.
+    Labels lab0;
+    bool labelled = false;
+    if (bc && bc->cell_labels) {
+        lab0.nx = grid->nx; lab0.ny = grid->ny; lab0.nz = grid->nz;
+        lab0.lab.assign(bc->cell_labels, bc->cell_labels + (size_t)(grid->nx + 2) * (grid->ny + 2) * (grid->nz + 2));
+        for (int k = -1; k <= grid->nz; ++k)
+            for (int j = -1; j <= grid->ny; ++j)
+                for (int i = -1; i <= grid->nx; ++i) {
+                    const uint8_t v = lab0.at(i, j, k);
+                    const bool ghost = i < 0 || j < 0 || k < 0 || i >= grid->nx || j >= grid->ny || k >= grid->nz;
+                    if (v == 2) return STOKES_ERR_UNSUPPORTED;
+                    if (v > 2 || (ghost && v != 1)) return STOKES_ERR_INVALID_ARG;
+                    if (!ghost && v != 0) labelled = true;
+                }
+    }
     stokes_opts_t o;
     stokes_opts_default(&o);
     if (opts) o = *opts;
@@ -700,11 +773,32 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     // mixed precision: the two finest levels (never the coarsest) keep b and r as BF16
     h->nbf = h->prec == STOKES_PREC_MIXED_BF16 ? std::min(2, nlev - 1) : 0;
     int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    std::vector<Labels> labs;
+    std::vector<std::vector<uint8_t>> hflags;
     for (int l = 0; l < nlev; ++l) {
         LevelBuf B;
         B.L = make_level(nx, ny, nz, hh, viscosity, o.gamma);
+        if (labelled) {
+            labs.push_back(l == 0 ? lab0 : coarsen(labs.back()));
+            hflags.push_back(level_flags(B.L, labs.back()));
+        }
         h->lev.push_back(B);
         nx /= 2; ny /= 2; nz /= 2; hh *= 2.0;
+    }
+    h->ncell_active = (long long)grid->nx * grid->ny * grid->nz;
+    if (labelled) {
+        h->ncell_active = 0;
+        for (int k = 0; k < grid->nz; ++k)
+            for (int j = 0; j < grid->ny; ++j)
+                for (int i = 0; i < grid->nx; ++i) h->ncell_active += lab0.interior(i, j, k) ? 1 : 0;
+        if (h->ncell_active == 0) return STOKES_ERR_INVALID_ARG;
+        for (int l = 0; l < nlev; ++l) {
+            uint8_t *fd = nullptr;
+            int rc = h->alloc(&fd, hflags[l].size());
+            if (rc) return rc;
+            CK(cudaMemcpy(fd, hflags[l].data(), hflags[l].size(), cudaMemcpyHostToDevice));
+            h->lev[l].L.flags = fd;
+        }
     }
     // coarsest level: exact solve
     {
@@ -721,7 +815,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
         }
         if (nact > 6000) return STOKES_ERR_INVALID_ARG;  // dense inverse would not fit the design
         std::shared_ptr<std::vector<double>> K;
-        int rc = coarse_inverse(C.L, cidx, K);
+        int rc = coarse_inverse(C.L, labelled ? &hflags[nlev - 1] : nullptr, cidx, K);
         if (rc) return rc;
         h->nc = (int)cidx.size();
         if ((rc = h->alloc(&h->cidx, sizeof(int) * h->nc))) return rc;
@@ -742,12 +836,13 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
         if ((rc = h->alloc(&B.r, esb * L.n))) return rc;
         if ((rc = h->alloc(&B.delta, es * (size_t)L.nx * L.ny * L.nz))) return rc;
         if (h->dwj && (rc = h->alloc(&B.t, es * L.n))) return rc;
-        // V1 cells (interior cells with a face on the ghost shell) by colour
+        // V1 cells (interior cells with a face on a Dirichlet cell, the ghost shell included) by colour
         std::vector<int> cells[8];
         for (int k = 0; k < L.nz; ++k)
             for (int j = 0; j < L.ny; ++j)
                 for (int i = 0; i < L.nx; ++i) {
-                    bool v1 = i == 0 || j == 0 || k == 0 || i == L.nx - 1 || j == L.ny - 1 || k == L.nz - 1;
+                    bool v1 = labelled ? labs[l].v1(i, j, k)
+                                       : (i == 0 || j == 0 || k == 0 || i == L.nx - 1 || j == L.ny - 1 || k == L.nz - 1);
                     if (!v1) continue;
                     int col = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
                     cells[col].push_back(i | (j << 11) | (k << 22));  // packed coordinates
@@ -1009,7 +1104,7 @@ extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol,
 finish:
     // pressure fixed to zero mean (constant p lies in ker L)
     launch_psum(L, h->x, h->partials, s);
-    launch_scalars_aux(5, h->partials, kRedBlocks, h->st, h->hout, (double)L.nx * L.ny * L.nz, s);
+    launch_scalars_aux(5, h->partials, kRedBlocks, h->st, h->hout, (double)h->ncell_active, s);
     launch_psub(L, h->x, h->st, s);
     CKLAUNCH();
     {

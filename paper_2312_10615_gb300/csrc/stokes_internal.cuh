@@ -57,7 +57,12 @@ struct Lev {
     long long off[4];  // offsets of the u, v, w, p blocks in the packed vector
     long long n;       // packed length
     double h, eta, gamma;
+    // domains given by cell labels (Sec. 5): per packed entry, bit 0 = unknown, bit 1 = V2 DOF (the
+    // Vanka set V1 is the rest of the unknowns); nullptr = the plain box, where both follow from the
+    // indices
+    const uint8_t *flags = nullptr;
 };
+constexpr uint8_t kFlagActive = 1, kFlagV2 = 2;
 
 __host__ __device__ inline int ext(const Lev &L, int c, int d) {
     int n = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
@@ -75,6 +80,16 @@ __host__ __device__ inline long long pidx(const Lev &L, int c, int i, int j, int
 // is (c,i,j,k) an unknown of the box problem?  (normal index in [1, n-1], tangential in [0, n-1])
 __host__ __device__ inline bool active(const Lev &L, int c, int i, int j, int k) {
     return i >= (c == 0) && j >= (c == 1) && k >= (c == 2) && i <= L.nx - 1 && j <= L.ny - 1 && k <= L.nz - 1;
+}
+// is (c,i,j,k) an unknown of the level's domain (box, or the cell labels' flags)?
+__device__ __forceinline__ bool unknown(const Lev &L, int c, int i, int j, int k) {
+    if (!active(L, c, i, j, k)) return false;
+    return !L.flags || (L.flags[pidx(L, c, i, j, k)] & kFlagActive);
+}
+// is cell (i,j,k) a V2 cell (an interior cell none of whose six neighbours is a Dirichlet cell)?
+__device__ __forceinline__ bool v2_cell_at(const Lev &L, int i, int j, int k) {
+    if (!(i >= 1 && j >= 1 && k >= 1 && i <= L.nx - 2 && j <= L.ny - 2 && k <= L.nz - 2)) return false;
+    return !L.flags || (L.flags[pidx(L, 3, i, j, k)] & kFlagV2);
 }
 
 template <class T>
@@ -192,6 +207,8 @@ __device__ __forceinline__ Quad quad_at(const Lev &L, int i, int j, int k) {
     Q.act[1] = Q.ex[1] && j >= 1 && j <= L.ny - 1;
     Q.act[2] = Q.ex[2] && k >= 1 && k <= L.nz - 1;
     Q.act[3] = Q.ex[3];
+    if (L.flags)
+        for (int c = 0; c < 4; ++c) Q.act[c] = Q.act[c] && (L.flags[Q.q[c]] & kFlagActive);
     return Q;
 }
 // values of the four operator rows at (i,j,k) (0 for entries that are not unknowns); x holds 0

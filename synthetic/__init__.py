@@ -16,6 +16,11 @@ Workloads:
 * ``bumps``: forcing = sum of K random Gaussian bumps per velocity component, centres uniform in the
   unit cube, widths uniform in [0.02, 0.1], amplitudes N(0, 1); zero continuity source; no-slip walls.
 * ``lid``: lid-driven cavity, u = 1 on the top wall (z = 1), no-slip elsewhere, zero forcing.
+* ``porous_labels`` / ``cylinder_labels``: cell labels (ghost-extended cell grid, x fastest; 0 interior,
+  1 Dirichlet) of a box holding random spherical obstacles, or a z-aligned cylinder in a channel;
+  interior cells cut off from the largest 6-connected interior region are made Dirichlet.
+  ``plug_flow`` gives the channel's Dirichlet data: u = 1 on the open inflow side (x = 0), the same flux
+  out of the open outflow side (x = 1), no-slip on the other walls and on the obstacles.
 
 Random numbers come from numpy's PCG64 seeded per problem; evaluation runs in torch float64 on
 whatever device is asked for (CPU for the oracle, CUDA to build large inputs quickly).
@@ -205,3 +210,72 @@ NET_SHAPES = [(27, 4, 16)] + [(27, 16, 16)] * 10 + [(1, 16, 4)]
 def net_weights(seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.concatenate([rng.standard_normal(a * b * c) * np.sqrt(2.0 / (a * b)) for a, b, c in NET_SHAPES])
+
+
+# ---------------------------------------------------------------------------------------------
+# domains given by cell labels: obstacles inside the box (Sec. 5, Sec. 6 porous / cylinder examples)
+
+def _connected(lab):
+    """Interior cells outside the largest 6-connected interior region become Dirichlet."""
+    from scipy import ndimage
+    comp, ncomp = ndimage.label(lab == 0)
+    if ncomp > 1:
+        sizes = np.bincount(comp.reshape(-1))[1:]
+        keep = 1 + int(np.argmax(sizes))
+        lab[(comp != keep) & (lab == 0)] = 1
+    return lab
+
+
+def _shell(nx, ny, nz):
+    lab = np.ones((nz + 2, ny + 2, nx + 2), np.uint8)
+    lab[1:-1, 1:-1, 1:-1] = 0
+    return lab
+
+
+def porous_labels(nx, ny=None, nz=None, seed=0, nspheres=12, rmin=0.05, rmax=0.12):
+    """Box with nspheres random spheres of Dirichlet cells (centres U[0,1]^3 scaled to the box, radii
+    U[rmin, rmax] times the smallest side); returns uint8 (nz+2, ny+2, nx+2)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lab = _shell(nx, ny, nz)
+    zc, yc, xc = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    m = min(nx, ny, nz)
+    for _ in range(nspheres):
+        c = rng.uniform(0.0, 1.0, 3) * np.array([nx, ny, nz])
+        r = rng.uniform(rmin, rmax) * m
+        inside = (xc - c[0]) ** 2 + (yc - c[1]) ** 2 + (zc - c[2]) ** 2 <= r * r
+        lab[1:-1, 1:-1, 1:-1][inside] = 1
+    return _connected(lab)
+
+
+def cylinder_labels(nx, ny=None, nz=None, centre=(0.25, 0.5), radius=0.1):
+    """Channel along x with a z-aligned cylinder of Dirichlet cells; centre as fractions of (nx, ny),
+    radius as a fraction of ny.  Returns uint8 (nz+2, ny+2, nx+2)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    lab = _shell(nx, ny, nz)
+    yc, xc = np.meshgrid(np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    inside = (xc - centre[0] * nx) ** 2 + (yc - centre[1] * ny) ** 2 <= (radius * ny) ** 2
+    lab[1:-1, 1:-1, 1:-1][:, inside] = 1
+    return _connected(lab)
+
+
+def plug_flow(nx, ny=None, nz=None, labels=None, device="cpu"):
+    """Ghost-extended Dirichlet data of a channel along x: u = 1 on the open part of the x = 0 side (faces
+    of interior cells), a uniform outflow on the open part of the x = 1 side carrying the same flux, zero
+    on every other face (walls and obstacles), so the continuity equation is solvable."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    if labels is None:
+        open_in = open_out = torch.ones(nz, ny, dtype=torch.float64, device=device)
+    else:
+        lab = torch.as_tensor(np.asarray(labels).reshape(nz + 2, ny + 2, nx + 2))
+        open_in = (lab[1:-1, 1:-1, 1] == 0).to(torch.float64).to(device)
+        open_out = (lab[1:-1, 1:-1, nx] == 0).to(torch.float64).to(device)
+    u = torch.zeros(nz + 2, ny + 2, nx + 1, dtype=torch.float64, device=device)
+    u[1:-1, 1:-1, 0] = open_in
+    u[1:-1, 1:-1, nx] = open_out * (open_in.sum() / open_out.sum())
+    v = torch.zeros((nz + 2) * (ny + 1) * (nx + 2), dtype=torch.float64, device=device)
+    w = torch.zeros((nz + 1) * (ny + 2) * (nx + 2), dtype=torch.float64, device=device)
+    return torch.cat([u.reshape(-1), v, w])

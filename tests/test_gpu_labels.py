@@ -1,0 +1,226 @@
+"""Parity of the CUDA path with the CPU oracle on domains given by cell labels (Sec. 5): Dirichlet
+obstacles inside the box (random spheres, a cylinder in a channel).  Needs a GB300.
+
+Tolerances (relative to the max-norm of the oracle result): as for the box, 1e-13 for the operator and
+the right-hand side, 1e-12 for a smoother sweep or a transfer, 1e-10 for the dense coarsest solve,
+1e-11 for an FP64 V-cycle, 1e-4 for an FP32 V-cycle.  SQMR iterates get 1e-8 after six iterations
+(1e-10 in the box): coarse cells whose eight children include a Dirichlet cell become Dirichlet
+(Sec. 5), so coarse grids hold pressure cells with few or no unknown faces, whose rows are dominated
+by the -gamma I term (gamma = 1e-3); rounding differences of the coarse solve are amplified by up to
+1/gamma there and again by the SQMR recurrences.  The W-cycle's iterates are not compared: it visits
+the poor coarse grids of these thin domains 2^l times, and SQMR then stagnates for a few iterations
+(oracle residual history on the cylinder: 1.10, 0.521, 0.521, 0.521), where the quasi-minimal-residual
+iterate is ill-determined (6e-8 to 1e-2 apart after six iterations, with the preconditioners equal to
+1e-11).  Converged solutions (relative residual 1e-11) agree to 1e-9 for every variant.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+smg = pytest.importorskip("paper_2312_10615_gb300")
+DEV = torch.device("cuda:0")
+
+
+def rel_err(got, ref):
+    got = got.cpu().numpy() if isinstance(got, torch.Tensor) else got
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def cuda(v):
+    return torch.from_numpy(np.ascontiguousarray(v)).to(DEV)
+
+
+def rand_masked(o, seed, level=0):
+    act, _ = o.masks(level)
+    v = np.random.default_rng(seed).standard_normal(o.n(level))
+    v[~act.astype(bool)] = 0.0
+    return v
+
+
+def velocity_forcing(o, seed):
+    """N(0,1) forcing on the velocity unknowns, no continuity source (a solvable system)."""
+    f = rand_masked(o, seed)
+    nx, ny, nz = o.dims
+    f[-nx * ny * nz:] = 0.0
+    return f
+
+
+DOMAINS = {
+    "porous32": lambda: ((32, 32, 32), synthetic.porous_labels(32, seed=0, nspheres=10, rmin=0.08, rmax=0.18)),
+    "cylinder48x24x16": lambda: ((48, 24, 16), synthetic.cylinder_labels(48, 24, 16, radius=0.2)),
+}
+_cache = {}
+
+
+def pair(name, precision=smg.PREC_FP64, **kw):
+    key = (name, precision, tuple(sorted(kw.items())))
+    if key not in _cache:
+        (nx, ny, nz), lab = DOMAINS[name]()
+        o = oracle.Oracle(nx, ny, nz, coarsest_max=8, labels=lab, **kw)
+        skw = {("kb_vanka" if k == "kb" else k): v for k, v in kw.items()}
+        S = smg.Stokes(nx, ny, nz, precision=precision, labels=lab, **skw)
+        assert S.levels == o.nlevels
+        _cache[key] = (o, S, lab)
+    return _cache[key]
+
+
+@pytest.mark.parametrize("name", list(DOMAINS))
+def test_labelled_apply_and_rhs(name):
+    o, S, lab = pair(name)
+    nx, ny, nz = o.dims
+    act, _ = o.masks()
+    act = act.astype(bool)
+    x = np.random.default_rng(1).standard_normal(o.n())  # garbage off the unknowns too
+    y = S.apply(cuda(x)).cpu().numpy()
+    assert rel_err(y, o.apply(np.where(act, x, 0.0))) < 1e-13
+    assert np.all(y[~act] == 0.0)
+    f = np.random.default_rng(2).standard_normal(o.n())
+    g = synthetic.plug_flow(nx, ny, nz, lab).numpy() + 0.1 * np.random.default_rng(3).standard_normal(
+        synthetic.ghost_len(nx, ny, nz))
+    b = S.rhs(cuda(f), cuda(g))
+    assert rel_err(b, o.rhs(f, g)) < 1e-13
+
+
+SMOOTH_CASES = [(3, "dgs_fwd"), (4, "dgs_bwd"), (1, "dgs_sym"), (2, "vanka_sym"), (0, "alg3")]
+
+
+@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("which,piece", SMOOTH_CASES)
+@pytest.mark.parametrize("name", list(DOMAINS))
+def test_labelled_smoother_pieces(name, which, piece, level):
+    o, S, _ = pair(name)
+    x, b = rand_masked(o, 3, level), rand_masked(o, 4, level)
+    got = cuda(x)
+    smg.stokes_smooth(S.h, level, which, got, cuda(b))
+    if which == 0:
+        ref = o.smooth(x, b, level=level)
+    elif which in (1, 3, 4):
+        ref = o.dgs(x, b, level=level, direction={1: 0, 3: 1, 4: -1}[which])
+    else:
+        ref = o.vanka(x, b, level=level, colour=-1)
+    assert rel_err(got, ref) < 1e-12, piece
+
+
+@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("name", list(DOMAINS))
+def test_labelled_transfers_and_coarse_solve(name, level):
+    o, S, _ = pair(name)
+    r = rand_masked(o, 7, level)
+    bc = torch.zeros(o.n(level + 1), dtype=torch.float64, device=DEV)
+    smg.stokes_restrict(S.h, level, cuda(r), bc)
+    assert rel_err(bc, o.restrict(r, level=level)) < 1e-13
+    e, x = rand_masked(o, 8, level + 1), rand_masked(o, 9, level)
+    got = cuda(x)
+    smg.stokes_prolong_add(S.h, level, cuda(e), got)
+    assert rel_err(got, o.prolong_add(e, x, level=level)) < 1e-13
+    lc = o.nlevels - 1
+    b = rand_masked(o, 10, lc)
+    xc = torch.zeros(o.n(lc), dtype=torch.float64, device=DEV)
+    smg.stokes_coarse_solve(S.h, cuda(b), xc)
+    assert rel_err(xc, o.coarse_solve(b)) < 1e-10
+
+
+VARIANTS = [dict(), dict(kb=2), dict(cycle=2), dict(additive=True), dict(dwj=True)]
+
+
+@pytest.mark.parametrize("kw", VARIANTS, ids=lambda kw: "-".join(f"{k}{v}" for k, v in kw.items()) or "base")
+@pytest.mark.parametrize("name", list(DOMAINS))
+def test_labelled_vcycle_and_sqmr(name, kw):
+    o, S, lab = pair(name, **kw)
+    s = rand_masked(o, 11)
+    assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-11
+    nx, ny, nz = o.dims
+    f = velocity_forcing(o, 12)
+    b = o.rhs(f, synthetic.plug_flow(nx, ny, nz, lab).numpy())
+    if kw.get("cycle") != 2:
+        x_ref, _, _, _, _ = o.sqmr(b, tol=1e-30, maxit=6, fixed_iters=6)
+        x = torch.zeros(o.n(), dtype=torch.float64, device=DEV)
+        info = smg.sqmr_solve(S.h, cuda(b), x, tol=1e-30, max_iter=6, check=False)
+        assert info.iterations == 6 and rel_err(x, x_ref) < 1e-8
+    x_ref, rc, _, _, _ = o.sqmr(b, tol=1e-11, maxit=100)
+    assert rc == 0
+    x2, info2 = S.solve(cuda(b), tol=1e-11, max_iter=100)
+    assert info2.status == 0 and rel_err(x2, x_ref) < 1e-9
+
+
+@pytest.mark.parametrize("name", list(DOMAINS))
+def test_labelled_fp32_solve(name):
+    o, S, lab = pair(name, precision=smg.PREC_FP32)
+    s = rand_masked(o, 13)
+    assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-4
+    nx, ny, nz = o.dims
+    f = velocity_forcing(o, 14)
+    g = synthetic.plug_flow(nx, ny, nz, lab).numpy()
+    b_ref = o.rhs(f, g)
+    x_ref, rc, _, _, _ = o.sqmr(b_ref, tol=1e-12, maxit=100)
+    assert rc == 0
+    x, info = S.solve(cuda(b_ref), tol=1e-10, max_iter=100)
+    assert info.status == 0 and info.rel_residual < 1e-10
+    assert rel_err(x, x_ref) < 1e-7
+    act, _ = o.masks()
+    assert np.all(x.cpu().numpy()[~act.astype(bool)] == 0.0)
+    # pressure mean over the interior cells only
+    p = x.cpu().numpy()[-nx * ny * nz:][act[-nx * ny * nz:].astype(bool)]
+    assert abs(p.mean()) <= 1e-12 * np.abs(p).max()
+
+
+@pytest.mark.parametrize("mode,blocks", [(1, 8), (2, 8), (3, 1)])
+def test_labelled_vanka_schedules_bit_identical(mode, blocks):
+    (nx, ny, nz), lab = DOMAINS["porous32"]()
+    Sp = smg.Stokes(nx, precision=smg.PREC_FP32, autotune=False, labels=lab)
+    Sm = smg.Stokes(nx, precision=smg.PREC_FP32, autotune=False, labels=lab)
+    lev = 1 if mode == 3 else 0  # the single-block shared-memory sweep takes the 16^3 level
+    smg.stokes_set_level_schedule(Sm.h, lev, mode, blocks)
+    assert smg.stokes_level_schedule(Sm.h, lev)[0] == mode
+    o = oracle.Oracle(nx, coarsest_max=8, labels=lab)
+    s = rand_masked(o, 15)
+    a, b = Sp.precondition(cuda(s)), Sm.precondition(cuda(s))
+    assert torch.equal(a, b)
+
+
+def test_all_interior_labels_equal_the_box():
+    n = 32
+    lab = np.ones((n + 2,) * 3, np.uint8)
+    lab[1:-1, 1:-1, 1:-1] = 0
+    Sb = smg.Stokes(n, autotune=False)
+    Sl = smg.Stokes(n, autotune=False, labels=lab)
+    s = torch.from_numpy(np.random.default_rng(16).standard_normal(synthetic.packed_len(n))).to(DEV)
+    s = Sb.apply(s)  # zero off the unknowns
+    assert torch.equal(Sb.precondition(s), Sl.precondition(s))
+
+
+def test_invalid_labels():
+    n = 8
+    lab = np.ones((n + 2,) * 3, np.uint8)
+    lab[1:-1, 1:-1, 1:-1] = 0
+    bad = lab.copy()
+    bad[0, 3, 3] = 0  # ghost shell must be Dirichlet
+    with pytest.raises(smg.StokesError) as e:
+        smg.Stokes(n, labels=bad)
+    assert e.value.code == smg.ERR_INVALID_ARG
+    ext = lab.copy()
+    ext[4, 4, 4] = 2  # exterior cells (Neumann faces) are not built
+    with pytest.raises(smg.StokesError) as e:
+        smg.Stokes(n, labels=ext)
+    assert e.value.code == smg.ERR_UNSUPPORTED
+    with pytest.raises(ValueError):
+        smg.Stokes(n, labels=lab[:-1])
+
+
+def test_porous_128_fp32_solve():
+    # full-size property: the FP32 V-cycle SQMR reaches 1e-8 on a 128^3 porous domain, and the FP64
+    # residual of the returned iterate, recomputed by the oracle's operator on sampled rows, agrees
+    n = 128
+    lab = synthetic.porous_labels(n, seed=2)
+    S = smg.Stokes(n, precision=smg.PREC_FP32, labels=lab)
+    prob = synthetic.bumps(n, seed=2, device="cuda")
+    b = S.rhs(prob["f"], synthetic.plug_flow(n, labels=lab, device="cuda"))
+    x, info = S.solve(b, tol=1e-8, max_iter=200)
+    assert info.status == 0 and info.rel_residual < 1e-8 and info.iterations < 60
+    r = b - S.apply(x)
+    assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b)) < 1e-8

@@ -1,0 +1,241 @@
+"""Pins of the CPU oracle on domains given by cell labels (Sec. 5): obstacles of Dirichlet cells
+inside the box.  Runs without a GPU.
+
+The label path is pinned against the box path (itself pinned against dense matrices) through two
+facts that hold for a MAC grid whose Dirichlet cells carry their face values as data:
+* on the unknowns, the labelled operator is the box operator applied to a vector that vanishes off
+  the labelled unknowns (the stencil of a face or cell does not change, only which neighbours are
+  unknowns);
+* a box of m^3 cells framed by two layers of Dirichlet cells on an (m+4)^3 grid is the m^3 box
+  problem shifted by two cells in each direction: unknowns, V1 set (Sec. 5), right-hand side and the
+  one-level smoothers (Sec. 3.1, 3.2, whose orders depend on cell parities only) agree entry by
+  entry.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+
+def _rand(n, seed):
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+def _sizes(n):
+    return [(n, n, n + 1), (n, n + 1, n), (n + 1, n, n), (n, n, n)]
+
+
+def _ghost_sizes(n):
+    return [(n + 2, n + 2, n + 1), (n + 2, n + 1, n + 2), (n + 1, n + 2, n + 2)]
+
+
+def _split(v, shapes):
+    out, o = [], 0
+    for s in shapes:
+        m = int(np.prod(s))
+        out.append(v[o:o + m].reshape(s))
+        o += m
+    return out
+
+
+def _shrink(v, n, m, shapes_n, shapes_m, off):
+    """Entries of the m-grid's layout read out of the n-grid's layout, shifted by off cells."""
+    parts = _split(v, shapes_n)
+    out = []
+    for P, s in zip(parts, shapes_m):
+        out.append(P[off:off + s[0], off:off + s[1], off:off + s[2]].reshape(-1))
+    return np.concatenate(out)
+
+
+def _embed(v, n, m, shapes_n, shapes_m, off, fill):
+    parts = _split(fill.copy(), shapes_n)
+    for P, Q in zip(parts, _split(v, shapes_m)):
+        P[off:off + Q.shape[0], off:off + Q.shape[1], off:off + Q.shape[2]] = Q
+    return np.concatenate([P.reshape(-1) for P in parts])
+
+
+def _frame_labels(n, layers=2):
+    lab = np.ones((n + 2, n + 2, n + 2), np.uint8)
+    a, b = 1 + layers, n + 1 - layers
+    lab[a:b, a:b, a:b] = 0
+    return lab
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. 5: classification and the operator of a labelled domain
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_labelled_apply_is_masked_box_apply(seed):
+    n = 12
+    lab = synthetic.porous_labels(n, seed=seed, nspheres=6, rmin=0.12, rmax=0.25)
+    assert (lab[1:-1, 1:-1, 1:-1] == 1).any()
+    ol = oracle.Oracle(n, eta=0.7, gamma=0.01, levels=2, coarsest_max=6, labels=lab)
+    ob = oracle.Oracle(n, eta=0.7, gamma=0.01, levels=2, coarsest_max=6)
+    act, _ = ol.masks()
+    actb, _ = ob.masks()
+    assert act.sum() < actb.sum() and not (act & ~actb).any()
+    x = _rand(ol.n(), seed + 5) * act
+    for pen in (False, True):
+        y = ol.apply(x, penalised=pen)
+        ref = ob.apply(x, penalised=pen) * act
+        assert np.max(np.abs(y - ref)) <= 1e-13 * np.max(np.abs(ref))
+        assert not y[~act.astype(bool)].any()
+
+
+def test_labelled_classification_by_brute_force():
+    # active faces: both adjacent cells interior; active pressures: interior cells; V1: every
+    # active unknown of an interior cell with a non-interior face neighbour (Sec. 5)
+    n = 6
+    lab = _frame_labels(n, 0)
+    lab[3, 3, 3] = lab[2, 4, 3] = 1  # two obstacle cells, (i, j, k) = (2, 2, 2) and (2, 3, 1)
+    o = oracle.Oracle(n, levels=1, coarsest_max=n, labels=lab)
+    act, v1 = o.masks()
+    L = lambda i, j, k: lab[k + 1, j + 1, i + 1]
+    shapes = _sizes(n)
+    ea, ev = [], []
+    cellv1 = np.zeros((n, n, n), bool)
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                if L(i, j, k) == 0:
+                    cellv1[k, j, i] = any(L(i + a, j + b, k + c) != 0 for a, b, c in
+                                          ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)))
+    for c, s in enumerate(shapes):
+        A = np.zeros(s, np.uint8)
+        V = np.zeros(s, np.uint8)
+        for k in range(s[0]):
+            for j in range(s[1]):
+                for i in range(s[2]):
+                    if c == 3:
+                        A[k, j, i] = L(i, j, k) == 0
+                        V[k, j, i] = A[k, j, i] and cellv1[k, j, i]
+                        continue
+                    e = [(1, 0, 0), (0, 1, 0), (0, 0, 1)][c]
+                    mi, mj, mk = i - e[0], j - e[1], k - e[2]
+                    A[k, j, i] = L(i, j, k) == 0 and L(mi, mj, mk) == 0
+                    if A[k, j, i]:
+                        V[k, j, i] = (k < n and j < n and i < n and cellv1[k, j, i]) or cellv1[mk, mj, mi]
+        ea.append(A.reshape(-1))
+        ev.append(V.reshape(-1))
+    assert np.array_equal(act, np.concatenate(ea))
+    assert np.array_equal(v1, np.concatenate(ev))
+
+
+def test_coarse_label_is_dirichlet_if_any_child_is():
+    # Sec. 5: a coarse cell is Dirichlet as soon as one of its 8 children is
+    n = 8
+    lab = _frame_labels(n, 0)
+    lab[1 + 5, 1 + 2, 1 + 3] = 1  # fine cell (3, 2, 5) -> coarse cell (1, 1, 2)
+    o = oracle.Oracle(n, levels=2, coarsest_max=4, labels=lab)
+    act1, _ = o.masks(1)
+    m = 4
+    p = act1[-m ** 3:].reshape(m, m, m)
+    expect = np.ones((m, m, m), bool)
+    expect[2, 1, 1] = False
+    assert np.array_equal(p.astype(bool), expect)
+
+
+# ----------------------------------------------------------------------------------------------
+# a framed box is the smaller box, shifted
+
+
+@pytest.mark.parametrize("kb", [1, 2])
+def test_framed_box_equals_smaller_box(kb):
+    m, off = 6, 2
+    n = m + 2 * off
+    h, eta = 1.0 / m, 0.9
+    ol = oracle.Oracle(n, h=h, eta=eta, levels=1, coarsest_max=n, kb=kb, labels=_frame_labels(n, off))
+    ob = oracle.Oracle(m, h=h, eta=eta, levels=1, coarsest_max=m, kb=kb)
+    Sn, Sm = _sizes(n), _sizes(m)
+    shrink = lambda v: _shrink(v, n, m, Sn, Sm, off)
+    act_l, v1_l = ol.masks()
+    act_b, v1_b = ob.masks()
+    assert act_l.sum() == act_b.sum()
+    assert np.array_equal(shrink(act_l), act_b) and np.array_equal(shrink(v1_l), v1_b)
+
+    # right-hand side: forcing and Dirichlet data of the small box, garbage where no unknown reads it
+    f_b = _rand(ob.n(), 1)
+    g_b = _rand(sum(int(np.prod(s)) for s in _ghost_sizes(m)), 2)
+    f_l = _embed(f_b, n, m, Sn, Sm, off, _rand(ol.n(), 3))
+    g_l = _embed(g_b, n, m, _ghost_sizes(n), _ghost_sizes(m), off,
+                 _rand(sum(int(np.prod(s)) for s in _ghost_sizes(n)), 4))
+    # the ghost layer of the small box sits one cell outside it: shift the ghost layouts by off too
+    assert np.allclose(shrink(ol.rhs(f_l, g_l)), ob.rhs(f_b, g_b), rtol=0, atol=1e-12 * np.abs(ob.rhs(f_b, g_b)).max())
+
+    x_b = _rand(ob.n(), 5) * act_b
+    b_b = _rand(ob.n(), 6) * act_b
+    emb = lambda v: _embed(v, n, m, Sn, Sm, off, np.zeros(ol.n()))
+    for name, fl, fb in (("apply", lambda: ol.apply(emb(x_b)), lambda: ob.apply(x_b)),
+                         ("dgs", lambda: ol.dgs(emb(x_b), emb(b_b)), lambda: ob.dgs(x_b, b_b)),
+                         ("vanka", lambda: ol.vanka(emb(x_b), emb(b_b)), lambda: ob.vanka(x_b, b_b)),
+                         ("smooth", lambda: ol.smooth(emb(x_b), emb(b_b)), lambda: ob.smooth(x_b, b_b))):
+        yl, yb = fl(), fb()
+        assert np.max(np.abs(shrink(yl) - yb)) <= 1e-12 * np.max(np.abs(yb)), name
+        assert np.abs(yl).sum() == pytest.approx(np.abs(shrink(yl)).sum(), rel=1e-14), name
+
+
+# ----------------------------------------------------------------------------------------------
+# V-cycle and SQMR on obstacle domains
+
+
+def _assemble(fn, n, active):
+    cols = np.nonzero(active)[0]
+    C = np.zeros((len(cols), len(cols)))
+    for a, q in enumerate(cols):
+        e = np.zeros(n)
+        e[q] = 1.0
+        C[:, a] = fn(e)[cols]
+    return C
+
+
+@pytest.mark.parametrize("variant", ["", "additive", "dwj", "kb2"])
+def test_labelled_vcycle_symmetric(variant):
+    n = 8
+    lab = synthetic.porous_labels(n, seed=3, nspheres=4, rmin=0.15, rmax=0.3)
+    o = oracle.Oracle(n, eta=1e-3, levels=2, coarsest_max=4, labels=lab, kb=2 if variant == "kb2" else 1,
+                      additive=variant == "additive", dwj=variant == "dwj")
+    act, _ = o.masks()
+    W = _assemble(o.vcycle, o.n(), act)
+    assert np.max(np.abs(W)) > 0
+    assert np.max(np.abs(W - W.T)) <= 1e-11 * np.max(np.abs(W))
+
+
+@pytest.mark.parametrize("eta", [1.0, 1e-3])
+def test_labelled_sqmr_matches_direct_solve(eta):
+    n = 8
+    lab = synthetic.porous_labels(n, seed=4, nspheres=4, rmin=0.15, rmax=0.3)
+    o = oracle.Oracle(n, eta=eta, levels=2, coarsest_max=4, labels=lab)
+    act, _ = o.masks()
+    act = act.astype(bool)
+    npc = n ** 3
+    pact = act[-npc:]
+    b = _rand(o.n(), 13) * act
+    b[-npc:][pact] -= b[-npc:][pact].mean()
+    x, rc, it, rr, _ = o.sqmr(b, tol=1e-13, maxit=300)
+    assert rc == 0 and rr < 1e-13
+    cols = np.nonzero(act)[0]
+    A = _assemble(o.apply, o.n(), act)
+    ref = np.linalg.lstsq(A, b[cols], rcond=None)[0]
+    npa = int(pact.sum())
+    ref[-npa:] -= ref[-npa:].mean()
+    assert np.max(np.abs(x[cols] - ref)) <= 1e-9 * np.max(np.abs(ref))
+    assert not x[~act].any()
+
+
+def test_labelled_iterations_stay_flat():
+    # Sec. 7: the iteration count of the MG-preconditioned solver barely grows under refinement,
+    # with obstacles as in the box
+    its = []
+    for n in (16, 32):
+        lab = synthetic.porous_labels(n, seed=7, nspheres=6, rmin=0.1, rmax=0.2)
+        o = oracle.Oracle(n, eta=1.0, labels=lab, coarsest_max=4)
+        act, _ = o.masks()
+        b = _rand(o.n(), 9) * act
+        pact = act[-n ** 3:].astype(bool)
+        b[-n ** 3:][pact] -= b[-n ** 3:][pact].mean()
+        x, rc, it, rr, _ = o.sqmr(b, tol=1e-8, maxit=200)
+        assert rc == 0
+        its.append(it)
+    assert its[1] <= its[0] + 6, its
