@@ -368,14 +368,39 @@ def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
         S.close()
 
 
+def labelled_unknowns(lab):
+    """Faces between two interior cells plus interior cells of a label array (nz+2, ny+2, nx+2)."""
+    it = lab == 0
+    cnt = int(it[1:-1, 1:-1, 1:-1].sum())
+    cnt += int((it[1:-1, 1:-1, 1:-2] & it[1:-1, 1:-1, 2:-1]).sum())
+    cnt += int((it[1:-1, 1:-2, 1:-1] & it[1:-1, 2:-1, 1:-1]).sum())
+    cnt += int((it[1:-2, 1:-1, 1:-1] & it[2:-1, 1:-1, 1:-1]).sum())
+    return cnt
+
+
 def run_cavity(args, smg, synthetic, torch, dev, rank, world, dist):
-    """3D lid-driven cavity (Sec. 7): n^3 cells, lid u = 1 on the top, no slip elsewhere,
-    eta = gamma = 1e-3, from x0 = 0 to args.tol; FP32 V-cycle + FP64 SQMR beside the plain FP64 V-cycle."""
+    """3D lid-driven cavity (Sec. 7): n^3 cells, lid u = 1 on the top, no slip elsewhere, or (porous) a
+    box of random spherical Dirichlet obstacles with a flux-balanced plug inflow/outflow along x and
+    Gaussian-bump forcing; eta = gamma = 1e-3, from x0 = 0 to args.tol; FP32 V-cycle + FP64 SQMR beside
+    the plain FP64 V-cycle."""
     n = args.n
-    prob = synthetic.lid(n, device=dev)
+    labels = None
+    if args.mode == "porous":
+        labels = synthetic.porous_labels(n, seed=0)
+        prob = {"f": synthetic.bumps(n, seed=0, device=dev)["f"],
+                "g": synthetic.plug_flow(n, labels=labels, device=dev)}
+        nunk = labelled_unknowns(labels)
+        workload = "3D porous medium %d^3 (12 random spherical obstacles, %.1f%% of the cells), plug flow " \
+                   "along x + bump forcing, eta = gamma = 1e-3" % (n, 100.0 * (labels[1:-1, 1:-1, 1:-1] == 1).mean())
+        metric = "solved unknowns/sec to rel. residual %g, 3D porous medium" % args.tol
+    else:
+        prob = synthetic.lid(n, device=dev)
+        nunk = unknowns(n)
+        workload = "3D lid-driven cavity %d^3, eta = gamma = 1e-3" % n
+        metric = "solved unknowns/sec to rel. residual %g, 3D lid-driven cavity" % args.tol
     res = {}
     for name, prec in (("fp32_vcycle", smg.PREC_FP32), ("fp64_vcycle", smg.PREC_FP64)):
-        S = smg.Stokes(n, viscosity=1e-3, gamma=1e-3, precision=prec)
+        S = smg.Stokes(n, viscosity=1e-3, gamma=1e-3, precision=prec, labels=labels)
         b = S.rhs(prob["f"], prob["g"])
         x = torch.zeros_like(b)
         for _ in range(args.warmup):
@@ -399,17 +424,17 @@ def run_cavity(args, smg, synthetic, torch, dev, rank, world, dist):
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        res[name] = {"value": unknowns(n) * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps,
+        res[name] = {"value": nunk * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps,
                      "iterations": [i for i, _ in its], "rel_residual": [r for _, r in its], "levels": S.levels}
         S.close()
     if rank == 0:
         h = res["fp32_vcycle"]
-        line = {"metric": "solved unknowns/sec to rel. residual %g, 3D lid-driven cavity" % args.tol,
+        line = {"metric": metric,
                 "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64 SQMR + f32 V-cycle", "data": "synthetic",
-                "config": {"workload": "3D lid-driven cavity %d^3, eta = gamma = 1e-3" % n, "n": n,
-                           "unknowns": unknowns(n), "tol": args.tol, "parallelism": f"replicas x{world}"},
+                "config": {"workload": workload, "n": n,
+                           "unknowns": nunk, "tol": args.tol, "parallelism": f"replicas x{world}"},
                 "fp32_vcycle": h, "fp64_vcycle": res["fp64_vcycle"]}
         print(json.dumps(line), flush=True)
 
@@ -573,10 +598,11 @@ def main():
     ap.add_argument("--epochs", type=int, default=2, help="passes over the training solves (--mode warmstart)")
     ap.add_argument("--ws-loss", default="residual", choices=["error", "residual"],
                     help="training loss of --mode warmstart: ||x0 - x*||^2/||x*||^2 or ||L (x0 - x*)||^2/||b||^2")
-    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity", "warmstart", "variants"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity", "porous", "warmstart", "variants"],
                     help="vcycle: only time mg_precondition (one V-cycle per step) -- for profiler captures; "
                          "batch: independent problems of uneven sizes solved concurrently; "
                          "cavity: the 3D lid-driven cavity (eta = gamma = 1e-3); "
+                         "porous: spherical Dirichlet obstacles given by cell labels, plug flow along x; "
                          "warmstart: train the initial-guess network on solves, then solve held-out seeds; "
                          "variants: k_b sweeps, W-cycle and additive Vanka on the headline workload")
     ap.add_argument("--batch", type=int, default=64, help="problems per batch (--mode batch)")
@@ -629,7 +655,7 @@ def main():
     if args.mode == "batch":
         run_batch(args, smg, synthetic, torch, dev, rank, world, dist)
         return
-    if args.mode == "cavity":
+    if args.mode in ("cavity", "porous"):
         run_cavity(args, smg, synthetic, torch, dev, rank, world, dist)
         return
     if args.mode == "warmstart":
