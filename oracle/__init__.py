@@ -70,6 +70,8 @@ def _load():
         "og_set_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "og_sqmr": (ctypes.c_int, [vp, _d, _d, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i,
                                    _d, _d]),
+        "og_vcycle_x0": (None, [vp, _d, _d]),
+        "og_mg_solve": (ctypes.c_int, [vp, _d, _d, ctypes.c_double, ctypes.c_int, _i, _d, _d]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -199,6 +201,21 @@ class Oracle:
         t = np.zeros(self.n(0))
         self.lib.og_vcycle(self._h, _dp(np.ascontiguousarray(s, np.float64)), _dp(t))
         return t
+
+    def vcycle_x0(self, b, x0):
+        """One V-cycle of Alg. 1 on L~ from the initial guess x0 (not zero)."""
+        x = np.array(x0, np.float64, copy=True)
+        self.lib.og_vcycle_x0(self._h, _dp(np.ascontiguousarray(b, np.float64)), _dp(x))
+        return x
+
+    def mg_solve(self, b, x0=None, tol=1e-8, maxit=200):
+        """Alg. 1 iterated as a solver on L~ x = b.  Returns (x, status, cycles, relative L~ residual, history)."""
+        x = np.zeros(self.n(0)) if x0 is None else np.array(x0, np.float64, copy=True)
+        hist = np.zeros(maxit + 1)
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        rc = self.lib.og_mg_solve(self._h, _dp(np.ascontiguousarray(b, np.float64)), _dp(x), tol, maxit,
+                                  ctypes.byref(it), ctypes.byref(rr), _dp(hist))
+        return x, rc, it.value, rr.value, hist[: it.value + 1].copy()
 
     def sqmr(self, b, x0=None, tol=1e-8, maxit=200, precond=True, fixed_iters=0):
         """Alg. 4.  Returns (x, status, iterations, true relative residual, history)."""

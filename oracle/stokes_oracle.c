@@ -18,6 +18,7 @@
  *   transfers ................. Sec. 2 (P = c R^T, c = 8 in 3D; trilinear velocity, constant pressure)
  *   V-cycle ................... Alg. 1
  *   SQMR ...................... Sec. 4, Alg. 4
+ *   pure multigrid solver ..... Alg. 1 iterated on L~ (Sec. 3, Sec. 6 comparisons)
  *
  * Readings of places where the paper is silent or ambiguous:
  *  - scaling: A = (eta/h^2)(7-point stencil), B^T = gradient/h, B = -divergence/h.
@@ -811,6 +812,41 @@ static double dot(long n, const double *a, const double *b) {
     double s = 0.0;
     for (long q = 0; q < n; ++q) s += a[q] * b[q];
     return s;
+}
+
+/* one V-cycle of Alg. 1 on L~ with a given initial guess: x holds x0 on entry, the cycle's result on exit */
+void og_vcycle_x0(og_hier *H, const double *b, double *x) {
+    og_level *L = &H->lev[0];
+    for (long a = 0; a < L->n; ++a) if (!L->active[a]) x[a] = 0.0;
+    og_cycle_level(H, 0, b, x, 0);
+}
+
+/* Alg. 1 used outright as the solver (Sec. 3: iterating the cycle instead of preconditioning with it),
+ * on the penalised system L~ x = b, as in the paper's pure-multigrid comparisons (Sec. 6):
+ * x_{k+1} = V-cycle(L~, b, x_k, n) until ||b - L~ x_k||_2 / ||b||_2 < tol.
+ * x holds x0 on entry.  hist (optional, maxit+1 entries): that relative residual for k = 0, 1, ... */
+int og_mg_solve(og_hier *H, const double *b, double *x, double tol, int maxit, int *iters, double *relres,
+                double *hist) {
+    og_level *L = &H->lev[0];
+    long n = L->n;
+    double *r = (double *)calloc(n, sizeof(double));
+    if (!r) return OG_ERR_OOM;
+    int rc = OG_ERR_NOT_CONVERGED, k = 0;
+    double nb = sqrt(dot(n, b, b)), rel = 0.0;
+    for (long a = 0; a < n; ++a) if (!L->active[a]) x[a] = 0.0;
+    for (k = 0;; ++k) {
+        og_apply_level(L, x, r, L->gamma);
+        for (long a = 0; a < n; ++a) r[a] = L->active[a] ? b[a] - r[a] : 0.0;
+        rel = nb > 0 ? sqrt(dot(n, r, r)) / nb : 0.0;
+        if (hist) hist[k] = rel;
+        if (rel < tol || nb == 0.0) { rc = OG_OK; break; }
+        if (k == maxit) break;
+        og_cycle_level(H, 0, b, x, 0);
+    }
+    if (iters) *iters = k;
+    if (relres) *relres = rel;
+    free(r);
+    return rc;
 }
 
 /* Alg. 4: MG-preconditioned SQMR on L (precond = 1) or plain SQMR (precond = 0).

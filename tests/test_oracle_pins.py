@@ -476,3 +476,48 @@ def test_iteration_counts_flat_under_refinement():
         assert rc == 0 and rr < 1e-8
         its.append(it)
     assert max(its) <= min(its) + 4, its
+
+
+# ----------------------------------------------------------------------------------------------
+# Alg. 1 iterated as a solver on L~ (Sec. 3; the pure multigrid of the paper's comparisons, Sec. 6)
+
+@pytest.mark.parametrize("variant", ["", "additive", "dwj", "kb2"])
+def test_vcycle_from_initial_guess_is_residual_correction(variant):
+    # every smoother is a linear stationary iteration and the coarse correction is linear, so a cycle
+    # started at x0 equals x0 + W^+ (b - L~ x0): the pure-multigrid iterate can be formed either way
+    o = oracle.Oracle(16, eta=1e-3, levels=3, coarsest_max=4, kb=2 if variant == "kb2" else 1,
+                      additive=variant == "additive", dwj=variant == "dwj")
+    act, _ = o.masks()
+    b, x0 = _masked(_rand(o.n(), 30), act), _masked(_rand(o.n(), 31), act)
+    lit = o.vcycle_x0(b, x0)
+    rc = x0 + o.vcycle(b - o.apply(x0, penalised=True))
+    assert np.max(np.abs(lit - rc)) <= 1e-12 * np.max(np.abs(lit))
+
+
+@pytest.mark.parametrize("eta", [1.0, 1e-3])
+def test_one_level_pure_multigrid_is_a_direct_solve(eta):
+    # with one level the cycle is the exact coarsest solve of L~: one cycle solves L~ x = b
+    D = DenseBox(4, eta=eta)
+    o = oracle.Oracle(4, eta=eta, levels=1, coarsest_max=4)
+    b = _masked(_rand(D.n, 32), D.active)
+    x, rc, it, rr, hist = o.mg_solve(b, tol=1e-10, maxit=5)  # rounding floor of the solve: ~1e-12
+    assert rc == 0 and it == 1 and hist[0] == pytest.approx(1.0)
+    act = np.nonzero(D.active)[0]
+    ref = np.linalg.solve(D.Lt[act][:, act].toarray(), b[act])
+    assert np.max(np.abs(x[act] - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_pure_multigrid_converges_to_the_penalised_solution():
+    # the fixed point of x <- V-cycle(L~, b, x) is L~^{-1} b (not the Stokes solution, which differs by
+    # O(gamma)); on the unit-viscosity box each cycle reduces the residual by a fixed factor
+    n = 8
+    D = DenseBox(n, gamma=1e-3)
+    o = oracle.Oracle(n, levels=2, coarsest_max=4)
+    b = _masked(_rand(D.n, 33), D.active)
+    x, rc, it, rr, hist = o.mg_solve(b, tol=1e-12, maxit=100)
+    assert rc == 0 and rr < 1e-12
+    act = np.nonzero(D.active)[0]
+    ref = np.linalg.solve(D.Lt[act][:, act].toarray(), b[act])
+    assert np.max(np.abs(x[act] - ref)) <= 1e-9 * np.max(np.abs(ref))
+    rates = hist[1:] / hist[:-1]
+    assert np.all(rates < 0.5), rates
