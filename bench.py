@@ -578,6 +578,55 @@ def run_variants(args, smg, synthetic, torch, dev, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_comparators(args, smg, synthetic, torch, dev, rank, world, dist):
+    """The paper's comparison (Sec. 6, Sec. 7): MG-preconditioned SQMR beside Alg. 1 iterated outright on L~
+    (pure multigrid, FP32 cycle, FP64 residual) and SQMR without preconditioner (FP64), on the n^3 bump box
+    and on the porous domain (eta = gamma = 1e-3).  One timed solve each after one warm-up solve; the plain
+    SQMR is capped at --plain-iters iterations."""
+    n = args.n
+    lab = synthetic.porous_labels(n, seed=0)
+    cases = [("box bumps, eta = 1", None, 1.0, synthetic.bumps(n, seed=0, device=dev)["f"], None, unknowns(n)),
+             ("porous, plug flow + bumps, eta = 1e-3", lab, 1e-3, synthetic.bumps(n, seed=0, device=dev)["f"],
+              synthetic.plug_flow(n, labels=lab, device=dev), labelled_unknowns(lab))]
+    rows = []
+    stream = torch.cuda.current_stream()
+    for cname, labels, eta, f, g, nunk in cases:
+        for solver, prec, cap in (("MG-preconditioned SQMR", smg.PREC_FP32, 400),
+                                  ("pure multigrid on L~", smg.PREC_FP32, 400),
+                                  ("SQMR, no preconditioner", smg.PREC_FP64, args.plain_iters)):
+            S = smg.Stokes(n, viscosity=eta, gamma=1e-3, precision=prec, labels=labels)
+            b = S.rhs(f, g)
+            x = torch.zeros_like(b)
+            fn = {"MG-preconditioned SQMR": smg.sqmr_solve, "pure multigrid on L~": smg.mg_solve,
+                  "SQMR, no preconditioner": smg.sqmr_solve_unpreconditioned}[solver]
+            fn(S.h, b, x, args.tol, cap if solver != "SQMR, no preconditioner" else 20, check=False)
+            x.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = fn(S.h, b, x, args.tol, cap, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rows.append({"case": cname, "solver": solver, "precision": "fp32 cycle" if prec == smg.PREC_FP32 else "fp64",
+                         "iterations": info.iterations, "status": smg.stokes_strerror(info.status) if info.status else "ok",
+                         "rel_residual": info.rel_residual, "ms": ms,
+                         "value": nunk / (ms * 1e-3) if info.status == 0 else None})
+            S.close()
+    if rank == 0:
+        base = rows[0]
+        line = {"metric": "solved unknowns/sec to rel. residual %g, MG-SQMR against pure multigrid and plain SQMR"
+                          % args.tol,
+                "value": base["value"], "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
+                "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 SQMR + f32 V-cycle", "data": "synthetic",
+                "config": {"workload": "%d^3 box (16 bumps, eta = 1) and %d^3 porous medium (eta = gamma = 1e-3)"
+                                       % (n, n), "n": n, "tol": args.tol, "plain_sqmr_cap": args.plain_iters,
+                           "parallelism": f"replicas x{world}"},
+                "solvers": rows}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,19 +647,22 @@ def main():
     ap.add_argument("--epochs", type=int, default=2, help="passes over the training solves (--mode warmstart)")
     ap.add_argument("--ws-loss", default="residual", choices=["error", "residual"],
                     help="training loss of --mode warmstart: ||x0 - x*||^2/||x*||^2 or ||L (x0 - x*)||^2/||b||^2")
-    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity", "porous", "warmstart", "variants"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "vcycle", "batch", "cavity", "porous", "warmstart", "variants",
+                                                     "comparators"],
                     help="vcycle: only time mg_precondition (one V-cycle per step) -- for profiler captures; "
                          "batch: independent problems of uneven sizes solved concurrently; "
                          "cavity: the 3D lid-driven cavity (eta = gamma = 1e-3); "
                          "porous: spherical Dirichlet obstacles given by cell labels, plug flow along x; "
+                         "comparators: MG-SQMR against pure multigrid and plain SQMR (Sec. 6); "
                          "warmstart: train the initial-guess network on solves, then solve held-out seeds; "
                          "variants: k_b sweeps, W-cycle and additive Vanka on the headline workload")
+    ap.add_argument("--plain-iters", type=int, default=3000, help="iteration cap of plain SQMR (--mode comparators)")
     ap.add_argument("--batch", type=int, default=64, help="problems per batch (--mode batch)")
     ap.add_argument("--streams", type=int, default=8, help="concurrent streams / host threads (--mode batch)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of --mode vcycle")
     args = ap.parse_args()
     if args.n is None:
-        args.n = 128 if args.mode in ("cavity", "warmstart") else 256
+        args.n = 128 if args.mode in ("cavity", "warmstart", "comparators") else 256
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -663,6 +715,9 @@ def main():
         return
     if args.mode == "variants":
         run_variants(args, smg, synthetic, torch, dev, rank, world, dist)
+        return
+    if args.mode == "comparators":
+        run_comparators(args, smg, synthetic, torch, dev, rank, world, dist)
         return
     seeds = [(rank * 1000 + s) % 5 for s in range(5)]
     rhs = {}

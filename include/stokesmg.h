@@ -150,6 +150,21 @@ int mg_precondition(stokes_t h, const double *s, double *t, void *stream);
  * the last iterate. */
 int sqmr_solve(stokes_t h, const double *rhs, double *x, double tol, int max_iter, sqmr_info_t *info, void *stream);
 
+/* Alg. 4 with the identity in place of the preconditioner (t = s): the plain SQMR the paper compares
+ * against (Sec. 6, Sec. 7).  Arguments, outputs and errors as sqmr_solve; info->vcycles = 0.  With
+ * STOKES_PREC_FP64 every step is FP64; otherwise t is s rounded to FP32. */
+int sqmr_solve_unpreconditioned(stokes_t h, const double *rhs, double *x, double tol, int max_iter,
+                                sqmr_info_t *info, void *stream);
+
+/* Alg. 1 used outright as the solver (Sec. 3), on the penalised system L~ x = b as in the paper's
+ * pure-multigrid comparisons (Sec. 6): x_{k+1} = x_k + V-cycle(L~, b - L~ x_k, 0, n), the same iterate
+ * as the cycle started at x_k.  Stops when ||b - L~ x_k||/||b|| < tol (FP64 residual, one stream
+ * synchronisation per cycle).  The limit of the iteration is L~^{-1} b, which differs from the Stokes
+ * solution by O(gamma); the pressure mean is not removed.  x: x0 on entry, the last iterate on exit.
+ * info->iterations = info->vcycles = cycles run, info->rel_residual = the L~ residual.  Returns
+ * STOKES_ERR_NOT_CONVERGED after max_iter cycles, STOKES_ERR_NAN on a non-finite residual. */
+int mg_solve(stokes_t h, const double *rhs, double *x, double tol, int max_iter, sqmr_info_t *info, void *stream);
+
 /* Batch of independent problems (the handles may have different grid sizes, all on one device):
  * solves problem i = sqmr_solve(handles[i], rhs[i], x[i], tol, max_iter, &infos[i]) for all i, with
  * nstreams host threads (1..64), each owning its own CUDA stream and pulling the next unsolved

@@ -25,7 +25,7 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
            "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
-           "stokes_set_level_schedule",
+           "stokes_set_level_schedule", "sqmr_solve_unpreconditioned", "mg_solve",
            "stokes_strerror",
            # learned initial guess (include/warmstart.h)
            "warmstart_num_weights", "warmstart_create", "warmstart_destroy", "warmstart_set_scale",
@@ -81,6 +81,8 @@ def _load():
         "stokes_apply": (i, [vp, vp, vp, vp]),
         "mg_precondition": (i, [vp, vp, vp, vp]),
         "sqmr_solve": (i, [vp, vp, vp, d, i, ctypes.POINTER(sqmr_info_t), vp]),
+        "sqmr_solve_unpreconditioned": (i, [vp, vp, vp, d, i, ctypes.POINTER(sqmr_info_t), vp]),
+        "mg_solve": (i, [vp, vp, vp, d, i, ctypes.POINTER(sqmr_info_t), vp]),
         "stokes_residual_norm": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
         "stokes_smooth": (i, [vp, i, i, vp, vp, vp]),
         "stokes_restrict": (i, [vp, i, vp, vp, vp]),
@@ -286,6 +288,22 @@ def sqmr_solve_batch(handles, rhs, xs, tol=1e-8, max_iter=200, nstreams=8, check
     if check:
         _check(rc, "sqmr_solve_batch")
     return list(infos), list(done)
+
+
+def sqmr_solve_unpreconditioned(h, rhs, x, tol=1e-8, max_iter=200, stream=None, check=True):
+    info = sqmr_info_t()
+    rc = lib().sqmr_solve_unpreconditioned(h, _ptr(rhs), _ptr(x), tol, max_iter, ctypes.byref(info), _stream(stream))
+    if check:
+        _check(rc, "sqmr_solve_unpreconditioned")
+    return info
+
+
+def mg_solve(h, rhs, x, tol=1e-8, max_iter=200, stream=None, check=True):
+    info = sqmr_info_t()
+    rc = lib().mg_solve(h, _ptr(rhs), _ptr(x), tol, max_iter, ctypes.byref(info), _stream(stream))
+    if check:
+        _check(rc, "mg_solve")
+    return info
 
 
 class Stokes:

@@ -108,6 +108,7 @@ void launch_update_x(long long n, double *x, double *d, double *q, const T *t, d
                      const SqmrState *st, double *partials, cudaStream_t s);
 // q = t (widening), d = 0
 template <class T> void launch_init_q(long long n, const T *t, double *q, double *d, cudaStream_t s);
+template <class T> void launch_add_to(long long n, const T *t, double *x, cudaStream_t s);
 // partial sum of the pressure block (for the mean) and subtraction of st->pmean
 void launch_psum(const Lev &L, const double *x, double *partials, cudaStream_t s);
 void launch_psub(const Lev &L, double *x, const SqmrState *st, cudaStream_t s);

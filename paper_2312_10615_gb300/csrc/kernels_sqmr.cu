@@ -284,6 +284,18 @@ template void launch_update_x<float>(long long, double *, double *, double *, co
                                      const double *, const SqmrState *, double *, cudaStream_t);
 template void launch_update_x<double>(long long, double *, double *, double *, const double *, double *,
                                       const double *, const SqmrState *, double *, cudaStream_t);
+// x += t (the pure-multigrid update x_{k+1} = x_k + W^+ (b - L~ x_k), t in the V-cycle's precision)
+template <class T>
+__global__ void __launch_bounds__(256) k_add_to(long long n, const T *__restrict__ tv, double *__restrict__ x) {
+    pdl_wait();
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        x[t] += (double)tv[t];
+}
+template <class T> void launch_add_to(long long n, const T *t, double *x, cudaStream_t s) {
+    launch_k(k_add_to<T>, dim3(kRedBlocks), dim3(kBlock), 0, s, n, t, x);
+}
+template void launch_add_to<float>(long long, const float *, double *, cudaStream_t);
+template void launch_add_to<double>(long long, const double *, double *, cudaStream_t);
 template void launch_init_q<float>(long long, const float *, double *, double *, cudaStream_t);
 template void launch_init_q<double>(long long, const double *, double *, double *, cudaStream_t);
 

@@ -241,12 +241,14 @@ struct stokes_s {
     SqmrState *st = nullptr;
     double *hout = nullptr;  // mapped pinned host memory written by the scalar kernel
     cudaStream_t cs = nullptr;
-    cudaGraphExec_t g_vcycle = nullptr, g_iter = nullptr;
+    cudaGraphExec_t g_vcycle = nullptr, g_iter = nullptr, g_iter_id = nullptr;
+    double *mgr = nullptr;  // FP64 residual of the pure-multigrid solver (FP32 V-cycles), on first use
     std::vector<void *> allocs;
 
     ~stokes_s() {
         if (g_vcycle) cudaGraphExecDestroy(g_vcycle);
         if (g_iter) cudaGraphExecDestroy(g_iter);
+        if (g_iter_id) cudaGraphExecDestroy(g_iter_id);
         for (void *p : allocs) cudaFree(p);
         if (hout) cudaFreeHost(hout);
         if (cs) cudaStreamDestroy(cs);
@@ -444,8 +446,15 @@ void vcycle_any(stokes_s *h, cudaStream_t s) {
     else vcycle<float>(h, s);
 }
 
-// one SQMR iteration (Alg. 4, loop body) on the finest level
-template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s) {
+// t <- s_j unchanged: the identity in place of the preconditioner (plain SQMR, Alg. 4 with M = I)
+template <class T> void identity_precond(stokes_s *h, cudaStream_t s) {
+    const long long n = h->lev[0].L.n;
+    if (h->prec == STOKES_PREC_FP64) cudaMemcpyAsync(h->lev[0].x, h->s, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    else launch_convert<double, float>(n, h->s, (float *)h->lev[0].x, s);
+}
+
+// one SQMR iteration (Alg. 4, loop body) on the finest level; precond = false: plain SQMR
+template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s, bool precond) {
     const Lev &L = h->lev[0].L;
     long long n = L.n;
     T *t = (T *)h->lev[0].x;
@@ -460,7 +469,8 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s) {
             launch_update_s<TB>(n, h->s, h->w, h->st, h->prec == STOKES_PREC_FP64 ? nullptr : (TB *)h->lev[0].b, s);
         });
     });
-    vcycle<T>(h, s);  // t <- V-cycle(L~, s_j, 0, n)
+    if (precond) vcycle<T>(h, s);  // t <- V-cycle(L~, s_j, 0, n)
+    else identity_precond<T>(h, s);
     // |t|^2, rho_j = s_j^T t ; nu, c, tau, beta
     prof(STOKES_K_DOT2, 0, s, [&] { launch_dot2<T>(n, t, h->s, h->partials, s); });
     prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(1, h->partials, kRedBlocks, h->st, h->hout, s); });
@@ -470,8 +480,12 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s) {
     prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(2, h->partials, kRedBlocks, h->st, h->hout, s); });
 }
 void sqmr_iteration_any(stokes_s *h, cudaStream_t s) {
-    if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s);
-    else sqmr_iteration<float>(h, s);
+    if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s, true);
+    else sqmr_iteration<float>(h, s, true);
+}
+void sqmr_iteration_plain(stokes_s *h, cudaStream_t s) {
+    if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s, false);
+    else sqmr_iteration<float>(h, s, false);
 }
 
 template <class F> int capture(stokes_s *h, F body, cudaGraphExec_t *out) {
@@ -500,15 +514,17 @@ int run_vcycle(stokes_s *h, cudaStream_t s) {
     return 0;
 }
 
-int run_iteration(stokes_s *h, cudaStream_t s) {
+int run_iteration(stokes_s *h, cudaStream_t s, bool precond = true) {
+    cudaGraphExec_t &g = precond ? h->g_iter : h->g_iter_id;
+    void (*body)(stokes_s *, cudaStream_t) = precond ? sqmr_iteration_any : sqmr_iteration_plain;
     if (h->use_graphs) {
-        if (!h->g_iter) {
-            int rc = capture(h, sqmr_iteration_any, &h->g_iter);
+        if (!g) {
+            int rc = capture(h, body, &g);
             if (rc) return rc;
         }
-        CK(cudaGraphLaunch(h->g_iter, s));
+        CK(cudaGraphLaunch(g, s));
     } else {
-        sqmr_iteration_any(h, s);
+        body(h, s);
         CKLAUNCH();
     }
     return 0;
@@ -1025,8 +1041,9 @@ int ensure_sqmr(stokes_s *h) {
 }
 }  // namespace
 
-extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info,
-                          void *stream) {
+namespace {
+int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info, void *stream,
+              bool precond) {
     if (info) std::memset(info, 0, sizeof(*info));
     if (!h || !rhs || !xv || !(tol > 0.0) || max_iter < 0) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
@@ -1065,10 +1082,15 @@ extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol,
     CK(cudaMemcpyAsync(h->r, h->s, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     rel = std::sqrt(ss) / nb;
     if (rel < tol) goto finish;
-    // t = V-cycle(L~, s_0, 0, n); q_0 = t; tau_0 = |t|; rho_0 = s_0^T q_0; d = 0
-    if (h->nbf > 0) launch_convert<double, bf16>(n, h->s, (bf16 *)h->lev[0].b, s);
-    else if (h->prec != STOKES_PREC_FP64) launch_convert<double, float>(n, h->s, (float *)h->lev[0].b, s);
-    if ((rc = run_vcycle(h, s))) return rc;
+    // t = V-cycle(L~, s_0, 0, n) (or t = s_0); q_0 = t; tau_0 = |t|; rho_0 = s_0^T q_0; d = 0
+    if (!precond) {
+        if (h->prec == STOKES_PREC_FP64) identity_precond<double>(h, s);
+        else identity_precond<float>(h, s);
+    } else {
+        if (h->nbf > 0) launch_convert<double, bf16>(n, h->s, (bf16 *)h->lev[0].b, s);
+        else if (h->prec != STOKES_PREC_FP64) launch_convert<double, float>(n, h->s, (float *)h->lev[0].b, s);
+        if ((rc = run_vcycle(h, s))) return rc;
+    }
     if (h->prec == STOKES_PREC_FP64) {
         launch_dot2<double>(n, (const double *)h->lev[0].x, h->s, h->partials, s);
         launch_init_q<double>(n, (const double *)h->lev[0].x, h->q, h->d, s);
@@ -1086,7 +1108,7 @@ extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol,
     }
     status = STOKES_ERR_NOT_CONVERGED;
     for (it = 1; it <= max_iter; ++it) {
-        if ((rc = run_iteration(h, s))) return rc;
+        if ((rc = run_iteration(h, s, precond))) return rc;
         if ((rc = sync_read(h, s, &rr, &flags))) return rc;
         int fl = (int)flags;
         if (fl & 2 || !std::isfinite(rr)) { status = STOKES_ERR_NAN; break; }
@@ -1123,7 +1145,89 @@ finish:
         info->iterations = it;
         info->rel_residual = rel;
         info->status = status;
-        info->vcycles = it + (it > 0 ? 1 : 0);
+        info->vcycles = precond ? it + (it > 0 ? 1 : 0) : 0;
+    }
+    return status;
+}
+}  // namespace
+
+extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info,
+                          void *stream) {
+    return sqmr_impl(h, rhs, xv, tol, max_iter, info, stream, true);
+}
+
+extern "C" int sqmr_solve_unpreconditioned(stokes_t h, const double *rhs, double *xv, double tol, int max_iter,
+                                           sqmr_info_t *info, void *stream) {
+    return sqmr_impl(h, rhs, xv, tol, max_iter, info, stream, false);
+}
+
+// Alg. 1 iterated as the solver on L~ x = b: x_{k+1} = x_k + V-cycle(L~, b - L~ x_k, 0, n), which equals
+// the cycle started at x_k (every smoother step and the coarse correction are linear).  The residual
+// b - L~ x_k and its norm are FP64; the cycle runs in the handle's precision.
+extern "C" int mg_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info,
+                        void *stream) {
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (!h || !rhs || !xv || !(tol > 0.0) || max_iter < 0) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Lev &L = h->lev[0].L;
+    long long n = L.n;
+    int rc = ensure_sqmr(h);
+    if (rc) return rc;
+    const bool f64 = h->prec == STOKES_PREC_FP64;
+    if (!f64 && !h->mgr && (rc = h->alloc(&h->mgr, sizeof(double) * n))) return rc;
+    double *r = f64 ? (double *)h->lev[0].b : h->mgr;
+    if (is_device_ptr(rhs)) CK(cudaMemcpyAsync(h->bvec, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else CK(cudaMemcpyAsync(h->bvec, rhs, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    bool xdev = is_device_ptr(xv);
+    CK(cudaMemcpyAsync(h->x, xv, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    launch_mask<double>(L, h->bvec, s);
+    launch_mask<double>(L, h->x, s);
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
+    double bb = 0.0, rr = 0.0;
+    launch_dot2<double>(n, h->bvec, nullptr, h->partials, s);
+    launch_scalars(4, h->partials, kRedBlocks, h->st, h->hout, s);
+    CKLAUNCH();
+    if ((rc = sync_read(h, s, &bb, nullptr))) return rc;
+    const double nb = std::sqrt(bb);
+    int k = 0, status = STOKES_ERR_NOT_CONVERGED;
+    double rel = 0.0;
+    if (!std::isfinite(nb)) status = STOKES_ERR_NAN;
+    else if (nb == 0.0) {
+        CK(cudaMemsetAsync(h->x, 0, sizeof(double) * n, s));
+        status = STOKES_OK;
+    } else
+        for (k = 0;; ++k) {
+            // r = b - L~ x_k and |r|^2 (FP64)
+            launch_apply<double, double>(L, h->x, h->bvec, r, L.gamma, s);
+            launch_dot2<double>(n, r, nullptr, h->partials, s);
+            launch_scalars(4, h->partials, kRedBlocks, h->st, h->hout, s);
+            CKLAUNCH();
+            if ((rc = sync_read(h, s, &rr, nullptr))) return rc;
+            rel = std::sqrt(rr) / nb;
+            if (!std::isfinite(rel)) { status = STOKES_ERR_NAN; break; }
+            if (rel < tol) { status = STOKES_OK; break; }
+            if (k == max_iter) break;
+            // x_{k+1} = x_k + V-cycle(L~, r, 0, n)
+            if (h->nbf > 0) launch_convert<double, bf16>(n, r, (bf16 *)h->lev[0].b, s);
+            else if (!f64) launch_convert<double, float>(n, r, (float *)h->lev[0].b, s);
+            if ((rc = run_vcycle(h, s))) return rc;
+            if (f64) launch_add_to<double>(n, (const double *)h->lev[0].x, h->x, s);
+            else launch_add_to<float>(n, (const float *)h->lev[0].x, h->x, s);
+            CKLAUNCH();
+        }
+    CK(cudaMemcpyAsync(xv, h->x, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    {
+        GridBarrier hb;
+        CK(cudaMemcpyAsync(&hb, h->bar, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hb.err) status = STOKES_ERR_TIMEOUT;
+    }
+    if (info) {
+        info->iterations = k;
+        info->rel_residual = rel;
+        info->status = status;
+        info->vcycles = k;
     }
     return status;
 }
@@ -1240,6 +1344,7 @@ int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
     // the captured graphs hold the old schedule
     if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
     if (h->g_iter) { cudaGraphExecDestroy(h->g_iter); h->g_iter = nullptr; }
+    if (h->g_iter_id) { cudaGraphExecDestroy(h->g_iter_id); h->g_iter_id = nullptr; }
     return STOKES_OK;
 }
 
