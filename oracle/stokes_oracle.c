@@ -36,6 +36,13 @@
  *  - prolongation of a face value: weight 1 (coincident) or 1/2,1/2 along the normal,
  *    3/4,1/4 along each tangential axis; coarse DOFs that are not active contribute 0.
  *  - convergence: true relative residual ||b - L x||_2 / ||b||_2 < tol.
+ *  - exterior cells (Sec. 5): a face between an interior and an exterior cell carries a
+ *    homogeneous Neumann condition, taken as the known value zero (the paper's examples use zero
+ *    and move nonzero data to the right-hand side without changing the operator); faces with no
+ *    interior cell beside them are inactive and drop out of every stencil.  On the unknowns the
+ *    operator is therefore the one of Dirichlet cells with zero data; exterior cells differ from
+ *    Dirichlet cells in coarsening (an exterior child does not make its coarse cell Dirichlet)
+ *    and in the data: g is read on faces of Dirichlet cells only.
  */
 #include <math.h>
 #include <stdint.h>
@@ -537,9 +544,9 @@ static int level_init(og_level *L, int nx, int ny, int nz, double h, double eta,
                     int ghost = i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz;
                     L->lab[(long)(i + 1) + (long)(nx + 2) * ((j + 1) + (long)(ny + 2) * (k + 1))] = ghost ? LAB_DIRICHLET : LAB_INTERIOR;
                 }
-    /* the ghost shell is always Dirichlet; exterior cells (Neumann faces) are not supported here */
+    /* labels are 0, 1 or 2; the ghost shell is always Dirichlet */
     for (long t = 0; t < nlab; ++t)
-        if (L->lab[t] == LAB_EXTERIOR) return OG_ERR_UNSUPPORTED;
+        if (L->lab[t] > LAB_EXTERIOR) return OG_ERR_ARG;
     for (int k = -1; k <= nz; ++k)
         for (int j = -1; j <= ny; ++j)
             for (int i = -1; i <= nx; ++i) {

@@ -17,7 +17,8 @@ Workloads:
   unit cube, widths uniform in [0.02, 0.1], amplitudes N(0, 1); zero continuity source; no-slip walls.
 * ``lid``: lid-driven cavity, u = 1 on the top wall (z = 1), no-slip elsewhere, zero forcing.
 * ``porous_labels`` / ``cylinder_labels``: cell labels (ghost-extended cell grid, x fastest; 0 interior,
-  1 Dirichlet) of a box holding random spherical obstacles, or a z-aligned cylinder in a channel;
+  1 Dirichlet, 2 exterior) of a box holding random spherical obstacles (optionally some of them
+  exterior), or a z-aligned cylinder in a channel;
   interior cells cut off from the largest 6-connected interior region are made Dirichlet.
   ``plug_flow`` gives the channel's Dirichlet data: u = 1 on the open inflow side (x = 0), the same flux
   out of the open outflow side (x = 1), no-slip on the other walls and on the obstacles.
@@ -232,20 +233,21 @@ def _shell(nx, ny, nz):
     return lab
 
 
-def porous_labels(nx, ny=None, nz=None, seed=0, nspheres=12, rmin=0.05, rmax=0.12):
+def porous_labels(nx, ny=None, nz=None, seed=0, nspheres=12, rmin=0.05, rmax=0.12, exterior_every=0):
     """Box with nspheres random spheres of Dirichlet cells (centres U[0,1]^3 scaled to the box, radii
-    U[rmin, rmax] times the smallest side); returns uint8 (nz+2, ny+2, nx+2)."""
+    U[rmin, rmax] times the smallest side); with exterior_every = m > 0 every m-th sphere (0, m, 2m, ...)
+    is made of exterior cells (label 2) instead.  Returns uint8 (nz+2, ny+2, nx+2)."""
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     rng = np.random.Generator(np.random.PCG64(seed))
     lab = _shell(nx, ny, nz)
     zc, yc, xc = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
     m = min(nx, ny, nz)
-    for _ in range(nspheres):
+    for s_idx in range(nspheres):
         c = rng.uniform(0.0, 1.0, 3) * np.array([nx, ny, nz])
         r = rng.uniform(rmin, rmax) * m
         inside = (xc - c[0]) ** 2 + (yc - c[1]) ** 2 + (zc - c[2]) ** 2 <= r * r
-        lab[1:-1, 1:-1, 1:-1][inside] = 1
+        lab[1:-1, 1:-1, 1:-1][inside] = 2 if exterior_every and s_idx % exterior_every == 0 else 1
     return _connected(lab)
 
 

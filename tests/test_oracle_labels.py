@@ -239,3 +239,98 @@ def test_labelled_iterations_stay_flat():
         assert rc == 0
         its.append(it)
     assert its[1] <= its[0] + 6, its
+
+
+# ----------------------------------------------------------------------------------------------
+# exterior cells (Sec. 5): homogeneous Neumann faces, inactive faces, the coarsening rule
+
+
+def _mixed(n, seed):
+    return synthetic.porous_labels(n, seed=seed, nspheres=8, rmin=0.12, rmax=0.25, exterior_every=2)
+
+
+def test_exterior_operator_equals_dirichlet_zero_on_the_finest_level():
+    # reading of Sec. 5: a face between an interior and an exterior cell is a homogeneous Neumann
+    # condition taken as the known value 0, and faces without an interior neighbour drop out, so on
+    # the unknowns the operator and the V1/V2 split are those of Dirichlet cells with zero data
+    n = 12
+    lab = _mixed(n, 1)
+    assert (lab == 2).any() and (lab[1:-1, 1:-1, 1:-1] == 1).any()
+    dl = np.where(lab == 2, 1, lab).astype(np.uint8)
+    oe = oracle.Oracle(n, eta=0.7, gamma=0.01, levels=2, coarsest_max=6, labels=lab)
+    od = oracle.Oracle(n, eta=0.7, gamma=0.01, levels=2, coarsest_max=6, labels=dl)
+    ae, ve = oe.masks()
+    ad, vd = od.masks()
+    assert np.array_equal(ae, ad) and np.array_equal(ve, vd)
+    x = _rand(oe.n(), 2) * ae
+    for pen in (False, True):
+        y = oe.apply(x, penalised=pen)
+        assert np.max(np.abs(y - od.apply(x, penalised=pen))) <= 1e-14 * np.max(np.abs(y))
+
+
+def test_exterior_rhs_reads_dirichlet_faces_only():
+    n = 12
+    lab = _mixed(n, 1)
+    dl = np.where(lab == 2, 1, lab).astype(np.uint8)
+    oe = oracle.Oracle(n, levels=2, coarsest_max=6, labels=lab)
+    od = oracle.Oracle(n, levels=2, coarsest_max=6, labels=dl)
+    f = _rand(oe.n(), 3)
+    g = _rand(synthetic.ghost_len(n), 4)
+    # the same data with zeros on every face that touches no Dirichlet cell (Neumann / inactive faces)
+    L = lambda i, j, k: lab[k + 1, j + 1, i + 1]
+    gz, o = g.copy(), 0
+    for c, (sz, sy, sx) in enumerate(_ghost_sizes(n)):
+        for kk in range(sz):
+            for jj in range(sy):
+                for ii in range(sx):
+                    i, j, k = ii - (c != 0), jj - (c != 1), kk - (c != 2)
+                    e = [(1, 0, 0), (0, 1, 0), (0, 0, 1)][c]
+                    if L(i, j, k) != 1 and L(i - e[0], j - e[1], k - e[2]) != 1:
+                        gz[o] = 0.0
+                    o += 1
+    assert not np.array_equal(gz, g)
+    be = oe.rhs(f, g)
+    assert np.max(np.abs(be - od.rhs(f, gz))) <= 1e-13 * np.max(np.abs(be))
+    assert np.max(np.abs(be - od.rhs(f, g))) > 1e-3 * np.max(np.abs(be))  # the data does differ
+
+
+@pytest.mark.parametrize("kind,coarse_p_active", [(2, True), (1, False)])
+def test_exterior_children_do_not_make_a_coarse_cell_dirichlet(kind, coarse_p_active):
+    # Sec. 5: Dirichlet if any child is Dirichlet, else interior if any child is interior, else
+    # exterior.  A 2^3 block of exterior (Dirichlet) fine cells becomes one exterior (Dirichlet) cell
+    # on level 1, whose level-2 parent is interior (Dirichlet)
+    n = 16
+    lab = _frame_labels(n, 0)
+    lab[1 + 4:1 + 6, 1 + 4:1 + 6, 1 + 4:1 + 6] = kind  # fine cells 4..5 -> level-1 cell 2 -> level-2 cell 1
+    o = oracle.Oracle(n, levels=3, coarsest_max=4, labels=lab)
+    p1 = o.masks(1)[0][-8 ** 3:].reshape(8, 8, 8)
+    assert not p1[2, 2, 2] and p1.sum() == 8 ** 3 - 1
+    p2 = o.masks(2)[0][-4 ** 3:].reshape(4, 4, 4)
+    assert bool(p2[1, 1, 1]) == coarse_p_active and p2.sum() == 4 ** 3 - (0 if coarse_p_active else 1)
+
+
+@pytest.mark.parametrize("variant", ["", "dwj"])
+def test_exterior_vcycle_symmetric(variant):
+    n = 8
+    lab = synthetic.porous_labels(n, seed=3, nspheres=4, rmin=0.15, rmax=0.3, exterior_every=2)
+    assert (lab == 2).any()
+    o = oracle.Oracle(n, eta=1e-3, levels=2, coarsest_max=4, labels=lab, dwj=variant == "dwj")
+    act, _ = o.masks()
+    W = _assemble(o.vcycle, o.n(), act)
+    assert np.max(np.abs(W - W.T)) <= 1e-11 * np.max(np.abs(W))
+
+
+def test_exterior_sqmr_matches_direct_solve():
+    n = 8
+    lab = synthetic.porous_labels(n, seed=4, nspheres=4, rmin=0.15, rmax=0.3, exterior_every=2)
+    o = oracle.Oracle(n, levels=2, coarsest_max=4, labels=lab)
+    act = o.masks()[0].astype(bool)
+    pact = act[-n ** 3:]
+    b = _rand(o.n(), 13) * act
+    b[-n ** 3:][pact] -= b[-n ** 3:][pact].mean()
+    x, rc, it, rr, _ = o.sqmr(b, tol=1e-13, maxit=300)
+    assert rc == 0 and rr < 1e-13
+    cols = np.nonzero(act)[0]
+    ref = np.linalg.lstsq(_assemble(o.apply, o.n(), act), b[cols], rcond=None)[0]
+    ref[-int(pact.sum()):] -= ref[-int(pact.sum()):].mean()
+    assert np.max(np.abs(x[cols] - ref)) <= 1e-9 * np.max(np.abs(ref))
