@@ -44,7 +44,7 @@ extern "C" {
 #define STOKES_ERR_NOT_CONVERGED -5 /* SQMR: max_iter reached before the tolerance */
 #define STOKES_ERR_NAN -6           /* a NaN/Inf appeared in the SQMR scalars */
 #define STOKES_ERR_TIMEOUT -7       /* a device-side grid barrier ran out of its iteration limit */
-#define STOKES_ERR_UNSUPPORTED -8   /* valid request this build does not implement (e.g. exterior cells) */
+#define STOKES_ERR_UNSUPPORTED -8   /* valid request this build does not implement */
 
 /* precision of the V-cycle (the SQMR recurrences, the true-residual check and the coarsest
  * solve always run in FP64) */
@@ -69,13 +69,15 @@ typedef struct {
 typedef struct {
     /* cell labels on the ghost-extended cell grid (nx+2)(ny+2)(nz+2), x fastest, index
      * (i+1) + (nx+2)((j+1) + (ny+2)(k+1)) for cell (i,j,k), i = -1..nx: 0 interior, 1 Dirichlet,
-     * 2 exterior (Sec. 5).  The ghost shell must be Dirichlet (else STOKES_ERR_INVALID_ARG); interior
-     * Dirichlet cells (obstacles) are supported: faces between two interior cells and interior-cell
-     * pressures are the unknowns, faces of Dirichlet cells carry Dirichlet data (the ghost-extended
-     * Dirichlet layout covers them), V1 holds the unknowns of interior cells next to a Dirichlet
-     * cell, coarse labels follow Sec. 5.  Exterior cells (Neumann faces) return
-     * STOKES_ERR_UNSUPPORTED.  NULL = the box (all interior, one Dirichlet ghost shell).  The array
-     * is copied; the caller keeps ownership. */
+     * 2 exterior (Sec. 5).  The ghost shell must be Dirichlet; a value above 2 or a non-Dirichlet
+     * ghost cell gives STOKES_ERR_INVALID_ARG.  Faces between two interior cells and interior-cell
+     * pressures are the unknowns; faces of Dirichlet cells carry Dirichlet data (the ghost-extended
+     * Dirichlet layout covers every face); a face between an interior and an exterior cell carries
+     * the homogeneous Neumann condition, taken as the value 0 (g is not read there); faces with no
+     * interior cell beside them are inactive.  V1 holds the unknowns of interior cells next to a
+     * non-interior cell.  Coarse labels: Dirichlet if any child is, else interior if any child is,
+     * else exterior.  NULL = the box (all interior, one Dirichlet ghost shell).  The array is copied;
+     * the caller keeps ownership. */
     const uint8_t *cell_labels;
 } stokes_bc_t;
 

@@ -193,13 +193,13 @@ __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__rest
             const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
             for (int m = 0; m < 6; ++m) {
                 int a = i + di[m], bb = j + dj[m], cc = k + dk[m];
-                if (!unknown(L, c, a, bb, cc)) v += K.eh2 * g[gidx(L, c, a, bb, cc)];
+                if (!unknown(L, c, a, bb, cc) && dirichlet_face(L, c, a, bb, cc)) v += K.eh2 * g[gidx(L, c, a, bb, cc)];
             }
         } else {
             for (int d = 0; d < 3; ++d) {
                 int hi = i + (d == 0), hj = j + (d == 1), hk = k + (d == 2);
-                if (!unknown(L, d, hi, hj, hk)) v += K.ih * g[gidx(L, d, hi, hj, hk)];
-                if (!unknown(L, d, i, j, k)) v -= K.ih * g[gidx(L, d, i, j, k)];
+                if (!unknown(L, d, hi, hj, hk) && dirichlet_face(L, d, hi, hj, hk)) v += K.ih * g[gidx(L, d, hi, hj, hk)];
+                if (!unknown(L, d, i, j, k) && dirichlet_face(L, d, i, j, k)) v -= K.ih * g[gidx(L, d, i, j, k)];
             }
         }
     }

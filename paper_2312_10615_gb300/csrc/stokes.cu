@@ -94,18 +94,20 @@ Lev make_level(int nx, int ny, int nz, double h, double eta, double gamma) {
 // ---- domains given by cell labels (Sec. 5) on the ghost-extended cell grid, x fastest ----
 struct Labels {
     int nx = 0, ny = 0, nz = 0;
-    std::vector<uint8_t> lab;  // (nx+2)(ny+2)(nz+2); 0 interior, 1 Dirichlet
+    std::vector<uint8_t> lab;  // (nx+2)(ny+2)(nz+2); 0 interior, 1 Dirichlet, 2 exterior
     uint8_t at(int i, int j, int k) const {  // i in -1..nx
         return lab[(size_t)(i + 1) + (size_t)(nx + 2) * ((j + 1) + (size_t)(ny + 2) * (k + 1))];
     }
     bool interior(int i, int j, int k) const { return at(i, j, k) == 0; }
+    bool dirichlet(int i, int j, int k) const { return at(i, j, k) == 1; }
     // interior cell with a non-interior face neighbour: its unknowns belong to the Vanka set V1
     bool v1(int i, int j, int k) const {
         return interior(i, j, k) && (!interior(i - 1, j, k) || !interior(i + 1, j, k) || !interior(i, j - 1, k) ||
                                      !interior(i, j + 1, k) || !interior(i, j, k - 1) || !interior(i, j, k + 1));
     }
 };
-// Sec. 5 coarsening: Dirichlet if any child is Dirichlet, else interior (no exterior cells here)
+// Sec. 5 coarsening: Dirichlet if any child is Dirichlet, else interior if any child is interior, else
+// exterior
 Labels coarsen(const Labels &F) {
     Labels C;
     C.nx = F.nx / 2; C.ny = F.ny / 2; C.nz = F.nz / 2;
@@ -113,15 +115,20 @@ Labels coarsen(const Labels &F) {
     for (int k = 0; k < C.nz; ++k)
         for (int j = 0; j < C.ny; ++j)
             for (int i = 0; i < C.nx; ++i) {
-                uint8_t v = 0;
-                for (int m = 0; m < 8; ++m)
-                    if (!F.interior(2 * i + (m & 1), 2 * j + ((m >> 1) & 1), 2 * k + ((m >> 2) & 1))) v = 1;
+                bool anyd = false, anyi = false;
+                for (int m = 0; m < 8; ++m) {
+                    const uint8_t l = F.at(2 * i + (m & 1), 2 * j + ((m >> 1) & 1), 2 * k + ((m >> 2) & 1));
+                    anyd |= l == 1;
+                    anyi |= l == 0;
+                }
+                const uint8_t v = anyd ? 1 : (anyi ? 0 : 2);
                 C.lab[(size_t)(i + 1) + (size_t)(C.nx + 2) * ((j + 1) + (size_t)(C.ny + 2) * (k + 1))] = v;
             }
     return C;
 }
-// per packed entry: kFlagActive (a face between two interior cells, or an interior cell) and
-// kFlagV2 (a face between two V2 cells, or a V2 cell)
+// per packed entry: kFlagActive (a face between two interior cells, or an interior cell), kFlagV2 (a face
+// between two V2 cells, or a V2 cell) and kFlagDirichlet (a face of a Dirichlet cell: its value is data;
+// the other faces that are not unknowns border exterior cells and hold the homogeneous Neumann value 0)
 std::vector<uint8_t> level_flags(const Lev &L, const Labels &B) {
     std::vector<uint8_t> f((size_t)L.n, 0);
     for (int c = 0; c < 4; ++c)
@@ -137,6 +144,7 @@ std::vector<uint8_t> level_flags(const Lev &L, const Labels &B) {
                             v = kFlagActive;
                             if (!B.v1(i, j, k) && !B.v1(mi, mj, mk)) v |= kFlagV2;
                         }
+                        if (B.dirichlet(i, j, k) || B.dirichlet(mi, mj, mk)) v |= kFlagDirichlet;
                     }
                     f[(size_t)pidx(L, c, i, j, k)] = v;
                 }
@@ -732,8 +740,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 || !(viscosity > 0.0)) return STOKES_ERR_INVALID_ARG;
     // packed Vanka cell coordinates hold 11 + 11 + 10 bits; the z extent folds into gridDim.z
     if (grid->nx > 2047 || grid->ny > 2047 || grid->nz > 1023) return STOKES_ERR_INVALID_ARG;
-    // cell labels (Sec. 5): ghost shell Dirichlet, interior cells 0 or 1; exterior cells (2) are not
-    // built.  A label array that describes the plain box is treated as the box.
+    // cell labels (Sec. 5): ghost shell Dirichlet (1), inner cells interior (0), Dirichlet (1) or exterior
+    // (2).  A label array that describes the plain box is treated as the box.
     Labels lab0;
     bool labelled = false;
     if (bc && bc->cell_labels) {
@@ -744,7 +752,6 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
                 for (int i = -1; i <= grid->nx; ++i) {
                     const uint8_t v = lab0.at(i, j, k);
                     const bool ghost = i < 0 || j < 0 || k < 0 || i >= grid->nx || j >= grid->ny || k >= grid->nz;
-                    if (v == 2) return STOKES_ERR_UNSUPPORTED;
                     if (v > 2 || (ghost && v != 1)) return STOKES_ERR_INVALID_ARG;
                     if (!ghost && v != 0) labelled = true;
                 }

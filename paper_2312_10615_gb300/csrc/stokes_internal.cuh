@@ -58,11 +58,12 @@ struct Lev {
     long long n;       // packed length
     double h, eta, gamma;
     // domains given by cell labels (Sec. 5): per packed entry, bit 0 = unknown, bit 1 = V2 DOF (the
-    // Vanka set V1 is the rest of the unknowns); nullptr = the plain box, where both follow from the
-    // indices
+    // Vanka set V1 is the rest of the unknowns), bit 2 = face of a Dirichlet cell (its value is data;
+    // other faces that are not unknowns border exterior cells and are 0); nullptr = the plain box,
+    // where all of this follows from the indices
     const uint8_t *flags = nullptr;
 };
-constexpr uint8_t kFlagActive = 1, kFlagV2 = 2;
+constexpr uint8_t kFlagActive = 1, kFlagV2 = 2, kFlagDirichlet = 4;
 
 __host__ __device__ inline int ext(const Lev &L, int c, int d) {
     int n = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
@@ -85,6 +86,14 @@ __host__ __device__ inline bool active(const Lev &L, int c, int i, int j, int k)
 __device__ __forceinline__ bool unknown(const Lev &L, int c, int i, int j, int k) {
     if (!active(L, c, i, j, k)) return false;
     return !L.flags || (L.flags[pidx(L, c, i, j, k)] & kFlagActive);
+}
+// does face (c,i,j,k) (any index, ghost faces included) carry Dirichlet data?  Faces outside the packed
+// arrays touch the ghost shell, which is Dirichlet
+__device__ __forceinline__ bool dirichlet_face(const Lev &L, int c, int i, int j, int k) {
+    if (!L.flags) return true;
+    const bool in = i >= 0 && j >= 0 && k >= 0 && i <= L.nx - 1 + (c == 0) && j <= L.ny - 1 + (c == 1) &&
+                    k <= L.nz - 1 + (c == 2);
+    return !in || (L.flags[pidx(L, c, i, j, k)] & kFlagDirichlet);
 }
 // is cell (i,j,k) a V2 cell (an interior cell none of whose six neighbours is a Dirichlet cell)?
 __device__ __forceinline__ bool v2_cell_at(const Lev &L, int i, int j, int k) {

@@ -1,5 +1,6 @@
 """Parity of the CUDA path with the CPU oracle on domains given by cell labels (Sec. 5): Dirichlet
-obstacles inside the box (random spheres, a cylinder in a channel).  Needs a GB300.
+obstacles inside the box (random spheres, a cylinder in a channel) and exterior cells (spheres whose
+faces carry homogeneous Neumann conditions).  Needs a GB300.
 
 Tolerances (relative to the max-norm of the oracle result): as for the box, 1e-13 for the operator and
 the right-hand side, 1e-12 for a smoother sweep or a transfer, 1e-10 for the dense coarsest solve,
@@ -53,6 +54,9 @@ def velocity_forcing(o, seed):
 DOMAINS = {
     "porous32": lambda: ((32, 32, 32), synthetic.porous_labels(32, seed=0, nspheres=10, rmin=0.08, rmax=0.18)),
     "cylinder48x24x16": lambda: ((48, 24, 16), synthetic.cylinder_labels(48, 24, 16, radius=0.2)),
+    # every other sphere made of exterior cells (homogeneous Neumann faces)
+    "mixed32": lambda: ((32, 32, 32), synthetic.porous_labels(32, seed=0, nspheres=10, rmin=0.08, rmax=0.18,
+                                                              exterior_every=2)),
 }
 _cache = {}
 
@@ -203,11 +207,16 @@ def test_invalid_labels():
     with pytest.raises(smg.StokesError) as e:
         smg.Stokes(n, labels=bad)
     assert e.value.code == smg.ERR_INVALID_ARG
-    ext = lab.copy()
-    ext[4, 4, 4] = 2  # exterior cells (Neumann faces) are not built
+    bad = lab.copy()
+    bad[4, 4, 4] = 3  # labels are 0, 1, 2
     with pytest.raises(smg.StokesError) as e:
-        smg.Stokes(n, labels=ext)
-    assert e.value.code == smg.ERR_UNSUPPORTED
+        smg.Stokes(n, labels=bad)
+    assert e.value.code == smg.ERR_INVALID_ARG
+    bad = lab.copy()
+    bad[0, 4, 4] = 2  # the ghost shell must be Dirichlet, not exterior
+    with pytest.raises(smg.StokesError) as e:
+        smg.Stokes(n, labels=bad)
+    assert e.value.code == smg.ERR_INVALID_ARG
     with pytest.raises(ValueError):
         smg.Stokes(n, labels=lab[:-1])
 
@@ -224,3 +233,16 @@ def test_porous_128_fp32_solve():
     assert info.status == 0 and info.rel_residual < 1e-8 and info.iterations < 60
     r = b - S.apply(x)
     assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b)) < 1e-8
+
+
+def test_exterior_and_dirichlet_labellings_share_the_finest_operator():
+    # the reading of Sec. 5 the oracle pins: on the finest level exterior cells act as Dirichlet cells
+    # with zero data; the hierarchies differ (coarsening), so the V-cycles differ
+    (nx, ny, nz), lab = DOMAINS["mixed32"]()
+    dl = np.where(lab == 2, 1, lab).astype(np.uint8)
+    Se = smg.Stokes(nx, labels=lab, autotune=False)
+    Sd = smg.Stokes(nx, labels=dl, autotune=False)
+    x = torch.from_numpy(np.random.default_rng(17).standard_normal(synthetic.packed_len(nx))).to(DEV)
+    ye, yd = Se.apply(x), Sd.apply(x)
+    assert torch.equal(ye, yd)
+    assert not torch.equal(Se.precondition(ye), Sd.precondition(ye))
