@@ -25,6 +25,11 @@ template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, 
 template <class T, class TB>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const TB *b, TB *gh, const T *delta, cudaStream_t s);
 template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s);
+// colours c and c ^ 1 (i bit only) in one launch, one block per group of whole x-rows; false (nothing
+// launched) if a row is longer than 512 cells of one colour
+template <class T, class TB>
+bool launch_dgs_p_fwd_pair(const Lev &L, T *x, const TB *b, T *delta, int colour, cudaStream_t s);
+template <class T, class TB> bool launch_dgs_p_bwd_pair(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s);
 // symmetric distributive weighted Jacobi on V2 (Sec. 3.1), weight w; t: level-size scratch, delta: per cell
 template <class T, class TB>
 void launch_dwj_sym(const Lev &L, T *x, const TB *b, T *t, T *delta, double w, cudaStream_t s);

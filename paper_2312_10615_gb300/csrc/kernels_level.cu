@@ -275,14 +275,9 @@ template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, 
 // neighbours whose colour came earlier in this sweep (pre-gather); k_dgs_p_gather applies the rest
 // after the last colour.  delta is stored per cell and stays 0 outside V2.
 template <class T, class TB, class IDX>
-__global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const TB *__restrict__ b,
-                                                   T *__restrict__ delta, int colour, Coef<T> K, T dP) {
-    pdl_wait();
-    int lo[3], cnt[3];
-    v2_colour_range(L, colour, lo, cnt);
-    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
-    if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
-    const IDX i = lo[0] + 2 * ti, j = lo[1] + 2 * tj, k = lo[2] + 2 * tk;
+__device__ __forceinline__ void p_fwd_cell(const Lev &L, T *__restrict__ x, const TB *__restrict__ b,
+                                           T *__restrict__ delta, int colour, IDX i, IDX j, IDX k, const Coef<T> &K,
+                                           T dP) {
     const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
     const IDX sy = nx, sz = nx * ny;
     const IDX cl = i + nx * (j + ny * k);
@@ -309,6 +304,36 @@ __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, con
     w[sz] += fd;
     pp[0] = p + T(6) * K.eh2 * dl;
     dc[0] = dl;
+}
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const TB *__restrict__ b,
+                                                   T *__restrict__ delta, int colour, Coef<T> K, T dP) {
+    pdl_wait();
+    int lo[3], cnt[3];
+    v2_colour_range(L, colour, lo, cnt);
+    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
+    if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
+    p_fwd_cell<T, TB, IDX>(L, x, b, delta, colour, (IDX)(lo[0] + 2 * ti), (IDX)(lo[1] + 2 * tj), (IDX)(lo[2] + 2 * tk),
+                           K, dP);
+}
+// Two colours that differ in the i bit only (c, then c ^ 1) in one launch.  A cell of colour c ^ 1
+// reads what colour c wrote only in its own x-row: its two x-faces, written by the colour-c cells
+// on either side, and their deltas; its y- and z-faces and the deltas of its y/z neighbours belong
+// to colours whose j or k bit differs.  One block holds whole x-rows (thread x = cell along the
+// row), so a __syncthreads orders the two colours.
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(512) k_dgs_p_fwd_pair(Lev L, T *__restrict__ x, const TB *__restrict__ b,
+                                                        T *__restrict__ delta, int colour, Coef<T> K, T dP) {
+    pdl_wait();
+    int lo[3], cnt[3], lo2[3], cnt2[3];
+    v2_colour_range(L, colour, lo, cnt);
+    v2_colour_range(L, colour ^ 1, lo2, cnt2);  // same j and k ranges
+    const int ti = threadIdx.x, tj = blockIdx.y * blockDim.y + threadIdx.y, tk = blockIdx.z;
+    const bool row = tj < cnt[1] && tk < cnt[2];
+    const IDX j = (IDX)(lo[1] + 2 * tj), k = (IDX)(lo[2] + 2 * tk);
+    if (row && ti < cnt[0]) p_fwd_cell<T, TB, IDX>(L, x, b, delta, colour, (IDX)(lo[0] + 2 * ti), j, k, K, dP);
+    __syncthreads();
+    if (row && ti < cnt2[0]) p_fwd_cell<T, TB, IDX>(L, x, b, delta, colour ^ 1, (IDX)(lo2[0] + 2 * ti), j, k, K, dP);
 }
 
 template <class T>
@@ -383,14 +408,8 @@ __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict_
 }
 
 template <class T, class TB, class IDX>
-__global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const TB *__restrict__ ghs, int colour,
-                                                   Coef<T> K, T dP) {
-    pdl_wait();
-    int lo[3], cnt[3];
-    v2_colour_range(L, colour, lo, cnt);
-    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
-    if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
-    const IDX i = lo[0] + 2 * ti, j = lo[1] + 2 * tj, k = lo[2] + 2 * tk;
+__device__ __forceinline__ void p_bwd_cell(const Lev &L, T *__restrict__ x, const TB *__restrict__ ghs, IDX i, IDX j,
+                                           IDX k, const Coef<T> &K, T dP) {
     const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
     const IDX sy = nx, sz = nx * ny;
     const IDX cl = i + nx * (j + ny * k);
@@ -413,6 +432,32 @@ __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, con
     const T s = K.ih * ((ruh - rul) + (rvh - rvl) + (rwh - rwl)) + K.eh2 * (T(6) * rc - rn);
     pp[0] = pc + s / dP;
 }
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const TB *__restrict__ ghs, int colour,
+                                                   Coef<T> K, T dP) {
+    pdl_wait();
+    int lo[3], cnt[3];
+    v2_colour_range(L, colour, lo, cnt);
+    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
+    if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
+    p_bwd_cell<T, TB, IDX>(L, x, ghs, (IDX)(lo[0] + 2 * ti), (IDX)(lo[1] + 2 * tj), (IDX)(lo[2] + 2 * tk), K, dP);
+}
+// colours c and c ^ 1 of the backward pressure sweep in one launch: only pressures change, and a cell
+// reads the pressures of the other colour of the pair only at its two x-neighbours (same x-row)
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(512) k_dgs_p_bwd_pair(Lev L, T *__restrict__ x, const TB *__restrict__ ghs,
+                                                        int colour, Coef<T> K, T dP) {
+    pdl_wait();
+    int lo[3], cnt[3], lo2[3], cnt2[3];
+    v2_colour_range(L, colour, lo, cnt);
+    v2_colour_range(L, colour ^ 1, lo2, cnt2);
+    const int ti = threadIdx.x, tj = blockIdx.y * blockDim.y + threadIdx.y, tk = blockIdx.z;
+    const bool row = tj < cnt[1] && tk < cnt[2];
+    const IDX j = (IDX)(lo[1] + 2 * tj), k = (IDX)(lo[2] + 2 * tk);
+    if (row && ti < cnt[0]) p_bwd_cell<T, TB, IDX>(L, x, ghs, (IDX)(lo[0] + 2 * ti), j, k, K, dP);
+    __syncthreads();
+    if (row && ti < cnt2[0]) p_bwd_cell<T, TB, IDX>(L, x, ghs, (IDX)(lo2[0] + 2 * ti), j, k, K, dP);
+}
 
 template <class T> static T dgs_pressure_diag(const Lev &L) {
     return T(-6.0 * (1.0 + L.gamma * L.eta) / (L.h * L.h));
@@ -430,6 +475,42 @@ void launch_dgs_p_fwd(const Lev &L, T *x, const TB *b, T *delta, int colour, cud
     else
         launch_k(k_dgs_p_fwd<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour,
                  coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
+}
+// block shape of the colour-pair kernels: whole x-rows, rows stacked to about 256 threads; false if a
+// row of one colour has more than 512 cells
+inline bool pair_block(const Lev &L, int colour, dim3 &grid, dim3 &block) {
+    int lo[3], cnt[3], lo2[3], cnt2[3];
+    v2_colour_range(L, colour, lo, cnt);
+    v2_colour_range(L, colour ^ 1, lo2, cnt2);
+    const int rx = 32 * cdiv(cnt[0] > cnt2[0] ? cnt[0] : cnt2[0], 32);
+    if (rx == 0 || rx > 512 || (long long)cnt[1] * cnt[2] == 0) return false;
+    const int ry = rx >= 256 ? 1 : 256 / rx;
+    block = dim3(rx, ry, 1);
+    grid = dim3(1, cdiv(cnt[1], ry), cnt[2]);
+    return true;
+}
+template <class T, class TB>
+bool launch_dgs_p_fwd_pair(const Lev &L, T *x, const TB *b, T *delta, int colour, cudaStream_t s) {
+    dim3 grid, block;
+    if (!pair_block(L, colour, grid, block)) return false;
+    if (idx32(L))
+        launch_k(k_dgs_p_fwd_pair<T, TB, int>, grid, block, 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
+                 dgs_pressure_diag<T>(L));
+    else
+        launch_k(k_dgs_p_fwd_pair<T, TB, long long>, grid, block, 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
+                 dgs_pressure_diag<T>(L));
+    return true;
+}
+template <class T, class TB> bool launch_dgs_p_bwd_pair(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s) {
+    dim3 grid, block;
+    if (!pair_block(L, colour, grid, block)) return false;
+    if (idx32(L))
+        launch_k(k_dgs_p_bwd_pair<T, TB, int>, grid, block, 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
+                 dgs_pressure_diag<T>(L));
+    else
+        launch_k(k_dgs_p_bwd_pair<T, TB, long long>, grid, block, 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
+                 dgs_pressure_diag<T>(L));
+    return true;
 }
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s) {
     dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz);
@@ -1162,6 +1243,8 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template void launch_dgs_p_fwd<T, TB>(const Lev &, T *, const TB *, T *, int, cudaStream_t);                  \
     template void launch_dgs_p_bwd_prep<T, TB>(const Lev &, T *, const TB *, TB *, const T *, cudaStream_t);      \
     template void launch_dgs_p_bwd<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                       \
+    template bool launch_dgs_p_fwd_pair<T, TB>(const Lev &, T *, const TB *, T *, int, cudaStream_t);              \
+    template bool launch_dgs_p_bwd_pair<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                   \
     template void launch_vanka_compute<T, TB>(const Lev &, const T *, const TB *, const int *, int, const T *, T *,  \
                                               int, double, cudaStream_t);                                           \
     template void launch_vanka_sweep<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, T *, int,  \

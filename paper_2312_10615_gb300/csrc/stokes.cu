@@ -377,8 +377,13 @@ template <class T, class TB> void dgs_forward(stokes_s *h, int l, cudaStream_t s
     const TB *b = (const TB *)B.b;
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
-    for (int c = 0; c < 8; ++c)
-        prof(STOKES_K_DGS_P_FWD, l, s, [&] { launch_dgs_p_fwd<T, TB>(B.L, x, b, (T *)B.delta, c, s); });
+    for (int c = 0; c < 8; c += 2)
+        prof(STOKES_K_DGS_P_FWD, l, s, [&] {
+            if (!launch_dgs_p_fwd_pair<T, TB>(B.L, x, b, (T *)B.delta, c, s)) {
+                launch_dgs_p_fwd<T, TB>(B.L, x, b, (T *)B.delta, c, s);
+                launch_dgs_p_fwd<T, TB>(B.L, x, b, (T *)B.delta, c + 1, s);
+            }
+        });
 }
 // the forward sweep's pending neighbour-pressure part is applied by the first launch after it
 template <class T> void dgs_finish_forward(stokes_s *h, int l, cudaStream_t s) {
@@ -392,8 +397,13 @@ template <class T, class TB> void dgs_backward(stokes_s *h, int l, cudaStream_t 
     prof(STOKES_K_DGS_P_BWD_PREP, l, s, [&] {
         launch_dgs_p_bwd_prep<T, TB>(B.L, x, b, (TB *)B.r, forward_pending ? (const T *)B.delta : nullptr, s);
     });
-    for (int c = 7; c >= 0; --c)
-        prof(STOKES_K_DGS_P_BWD, l, s, [&] { launch_dgs_p_bwd<T, TB>(B.L, x, (const TB *)B.r, c, s); });
+    for (int c = 7; c >= 0; c -= 2)
+        prof(STOKES_K_DGS_P_BWD, l, s, [&] {
+            if (!launch_dgs_p_bwd_pair<T, TB>(B.L, x, (const TB *)B.r, c, s)) {
+                launch_dgs_p_bwd<T, TB>(B.L, x, (const TB *)B.r, c, s);
+                launch_dgs_p_bwd<T, TB>(B.L, x, (const TB *)B.r, c - 1, s);
+            }
+        });
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
     prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
 }
