@@ -158,13 +158,6 @@ __global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x
     }
 }
 
-template <class T, class TB>
-void launch_apply(const Lev &L, const T *x, const TB *b, TB *y, double gam, cudaStream_t s) {
-    if (idx32(L))
-        launch_k(k_apply<T, TB, int>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
-    else
-        launch_k(k_apply<T, TB, long long>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
-}
 
 // ------------------------------------------------------------------------------------------
 // Sec. 5: b = f on the unknowns with Dirichlet data g (ghost-extended layout) folded in
@@ -407,6 +400,252 @@ __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict_
     }
 }
 
+// ---- the residual and the backward-DGS prep, four entries per thread along x ----
+// Both are bound by instruction issue with one entry per thread.  On the box (no label flags) with
+// nx % 4 == 0 the rows of v, w and p start on 4-entry boundaries, so a thread takes four consecutive
+// entries with 16-byte loads of the centre and of the y/z neighbour rows and two scalar loads for
+// the x neighbours; index math and guards are paid once per four entries.  Each entry's arithmetic
+// is the one-entry code's,
+// in the same order.  The u rows (nx + 1 entries, not 4-aligned) take four entries per thread too,
+// with scalar loads.
+template <class T> struct V4 {
+    T v[4];
+};
+template <class T> __device__ __forceinline__ V4<T> ld4(const T *p);
+template <> __device__ __forceinline__ V4<float> ld4<float>(const float *p) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    return {{a.x, a.y, a.z, a.w}};
+}
+template <> __device__ __forceinline__ V4<double> ld4<double>(const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], c = reinterpret_cast<const double2 *>(p)[1];
+    return {{a.x, a.y, c.x, c.y}};
+}
+template <> __device__ __forceinline__ V4<bf16> ld4<bf16>(const bf16 *p) {
+    const __nv_bfloat162 a = reinterpret_cast<const __nv_bfloat162 *>(p)[0];
+    const __nv_bfloat162 c = reinterpret_cast<const __nv_bfloat162 *>(p)[1];
+    return {{a.x, a.y, c.x, c.y}};
+}
+template <class D, class T> __device__ __forceinline__ void st4(D *p, const T (&a)[4]) {
+    if constexpr (sizeof(D) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(cvt<float>(a[0]), cvt<float>(a[1]), cvt<float>(a[2]), cvt<float>(a[3]));
+    } else if constexpr (sizeof(D) == 8) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(cvt<double>(a[0]), cvt<double>(a[1]));
+        reinterpret_cast<double2 *>(p)[1] = make_double2(cvt<double>(a[2]), cvt<double>(a[3]));
+    } else {
+        __nv_bfloat162 lo, hi;
+        lo.x = cvt<bf16>(a[0]);
+        lo.y = cvt<bf16>(a[1]);
+        hi.x = cvt<bf16>(a[2]);
+        hi.y = cvt<bf16>(a[3]);
+        reinterpret_cast<__nv_bfloat162 *>(p)[0] = lo;
+        reinterpret_cast<__nv_bfloat162 *>(p)[1] = hi;
+    }
+}
+template <class T> __device__ __forceinline__ V4<T> zero4() { return {{T(0), T(0), T(0), T(0)}}; }
+
+// rows of four consecutive entries i0..i0+3 of component C (1, 2: faces; 3: cells) at (j, k); P adds
+// the pressure gradient / -gamma p as in row_at
+template <class T, int C, bool P, class IDX>
+__device__ __forceinline__ void rows4(const T *__restrict__ x, const Lev &L, int i0, int j, int k, const Coef<T> &K,
+                                      T (&out)[4]) {
+    const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
+    if constexpr (C < 3) {
+        const IDX sy = nx, sz = sy * (ny + (C == 1));
+        const T *xc = x + L.off[C] + ((IDX)i0 + sy * (IDX)j + sz * (IDX)k);
+        const V4<T> c = ld4(xc);
+        const T xl = i0 > 0 ? xc[-1] : T(0), xr = i0 + 4 < L.nx ? xc[4] : T(0);
+        const V4<T> ym = (C == 1 || j > 0) ? ld4(xc - sy) : zero4<T>();
+        const V4<T> yp = (C == 1 || j < L.ny - 1) ? ld4(xc + sy) : zero4<T>();
+        const V4<T> zm = (C == 2 || k > 0) ? ld4(xc - sz) : zero4<T>();
+        const V4<T> zp = (C == 2 || k < L.nz - 1) ? ld4(xc + sz) : zero4<T>();
+        V4<T> pc, pm;
+        if constexpr (P) {
+            const IDX cy = nx, cz = cy * ny;
+            const T *pp = x + L.off[3] + ((IDX)i0 + cy * (IDX)j + cz * (IDX)k);
+            pc = ld4(pp);
+            pm = ld4(pp - (C == 1 ? cy : cz));
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const T lft = e == 0 ? xl : c.v[e - 1], rgt = e == 3 ? xr : c.v[e + 1];
+            T s = T(6) * c.v[e];
+            s -= lft + rgt;
+            s -= ym.v[e] + yp.v[e];
+            s -= zm.v[e] + zp.v[e];
+            if constexpr (P) out[e] = K.eh2 * s + K.ih * (pc.v[e] - pm.v[e]);
+            else out[e] = K.eh2 * s;
+        }
+    } else {
+        const T *u = x + L.off[0] + ((IDX)i0 + (nx + 1) * ((IDX)j + ny * (IDX)k));
+        const T *v = x + L.off[1] + ((IDX)i0 + nx * ((IDX)j + (ny + 1) * (IDX)k));
+        const T *w = x + L.off[2] + ((IDX)i0 + nx * ((IDX)j + ny * (IDX)k));
+        T uu[5];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) uu[e] = u[e];
+        const V4<T> v0 = ld4(v), v1 = ld4(v + nx), w0 = ld4(w), w1 = ld4(w + nx * ny);
+        V4<T> pc;
+        if constexpr (P) pc = ld4(x + L.off[3] + ((IDX)i0 + nx * ((IDX)j + ny * (IDX)k)));
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const T div = (uu[e + 1] - uu[e]) + (v1.v[e] - v0.v[e]) + (w1.v[e] - w0.v[e]);
+            if constexpr (P) out[e] = -K.ih * div - K.gam * pc.v[e];
+            else out[e] = -K.ih * div;
+        }
+    }
+}
+
+// u rows (nx + 1 entries, not aligned): four consecutive entries i0..i0+3 with scalar loads; e_ok[e]
+// says whether entry i0 + e exists (i <= nx), act[e] whether it is an unknown (1 <= i <= nx - 1)
+template <class T, bool P, class IDX>
+__device__ __forceinline__ void rows4u(const T *__restrict__ x, const Lev &L, int i0, int j, int k, const Coef<T> &K,
+                                       T (&out)[4]) {
+    const IDX sy = (IDX)(L.nx + 1), sz = sy * (IDX)L.ny;
+    const T *xc = x + L.off[0] + ((IDX)i0 + sy * (IDX)j + sz * (IDX)k);
+    T c[6];  // entries i0 - 1 .. i0 + 4 of the row, 0 outside it
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const int i = i0 - 1 + e;
+        c[e] = (i >= 0 && i <= L.nx) ? xc[e - 1] : T(0);
+    }
+    const bool ym = j > 0, yp = j < L.ny - 1, zm = k > 0, zp = k < L.nz - 1;
+    const IDX cy = (IDX)L.nx, cz = cy * (IDX)L.ny;
+    const T *pc = x + L.off[3] + ((IDX)i0 + cy * (IDX)j + cz * (IDX)k);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int i = i0 + e;
+        out[e] = T(0);
+        if (i < 1 || i > L.nx - 1) continue;
+        T s = T(6) * c[e + 1];
+        s -= c[e] + c[e + 2];
+        s -= (ym ? xc[e - sy] : T(0)) + (yp ? xc[e + sy] : T(0));
+        s -= (zm ? xc[e - sz] : T(0)) + (zp ? xc[e + sz] : T(0));
+        if constexpr (P) out[e] = K.eh2 * s + K.ih * (pc[e] - pc[e - 1]);
+        else out[e] = K.eh2 * s;
+    }
+}
+
+// launch shape of the four-per-thread kernels: the component in the low two bits of blockIdx.z as in
+// the one-entry kernels; x tiles cover the longest row (u, nx + 1 entries) in groups of four
+inline dim3 grid4(const Lev &L) { return dim3(cdiv(L.nx + 1, 4 * BX), cdiv(L.ny + 1, BY), 4 * (L.nz + 1)); }
+// box only (no label flags), rows of v, w, p on 4-entry boundaries (nx % 4 == 0 and the v block at a
+// multiple of 4), and every array 16-byte aligned
+inline bool al16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+inline bool use_x4(const Lev &L, const void *a, const void *b, const void *c, const void *d = nullptr) {
+    return !L.flags && L.nx >= 4 && L.nx % 4 == 0 && L.off[1] % 4 == 0 && al16(a) && al16(b) && al16(c) && al16(d);
+}
+// u entries i0..i0+3 (those that exist): one-entry semantics with four entries per thread
+template <class T, class TB, class IDX>
+__device__ __forceinline__ void apply_u4(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
+                                         TB *__restrict__ y, const Coef<T> &K, int i0, int j, int k) {
+    if (i0 > L.nx || j >= L.ny || k >= L.nz) return;
+    const long long q = entry_index<0, IDX>(L, i0, j, k);
+    T v[4];
+    rows4u<T, true, IDX>(x, L, i0, j, k, K, v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int i = i0 + e;
+        if (i > L.nx) break;
+        T r = v[e];
+        if (b && i >= 1 && i <= L.nx - 1) r = T(ldv(b[q + e])) - r;
+        y[q + e] = cvt<TB>(r);
+    }
+}
+template <class T, class TB, int C, class IDX>
+__device__ __forceinline__ void apply_entry4(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
+                                             TB *__restrict__ y, const Coef<T> &K, int i0, int j, int k) {
+    if (i0 >= L.nx || j >= L.ny + (C == 1) || k >= L.nz + (C == 2)) return;
+    const long long q = entry_index<C, IDX>(L, i0, j, k);
+    T v[4] = {T(0), T(0), T(0), T(0)};
+    if (entry_active<C>(L, 0, j, k)) {  // the activity of v, w and p rows does not depend on i
+        rows4<T, C, true, IDX>(x, L, i0, j, k, K, v);
+        if (b) {
+            const V4<TB> bv = ld4(b + q);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = T(ldv(bv.v[e])) - v[e];
+        }
+    }
+    st4(y + q, v);
+}
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(256, 8) k_apply4(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
+                                                   TB *__restrict__ y, Coef<T> K) {
+    pdl_wait();
+    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const int i = 4 * (blockIdx.x * BX + threadIdx.x), j = blockIdx.y * BY + threadIdx.y;
+    switch (c) {
+    case 0: apply_u4<T, TB, IDX>(L, x, b, y, K, i, j, k); break;
+    case 1: apply_entry4<T, TB, 1, IDX>(L, x, b, y, K, i, j, k); break;
+    case 2: apply_entry4<T, TB, 2, IDX>(L, x, b, y, K, i, j, k); break;
+    default: apply_entry4<T, TB, 3, IDX>(L, x, b, y, K, i, j, k);
+    }
+}
+
+template <class T, class TB, class IDX>
+__device__ __forceinline__ void prep_u4(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
+                                        TB *__restrict__ gh, const Coef<T> &K, int i0, int j, int k) {
+    if (i0 > L.nx || j >= L.ny || k >= L.nz) return;
+    const long long q = entry_index<0, IDX>(L, i0, j, k);
+    T v[4];
+    rows4u<T, false, IDX>(x, L, i0, j, k, K, v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int i = i0 + e;
+        if (i > L.nx) break;
+        gh[q + e] = cvt<TB>(i >= 1 && i <= L.nx - 1 ? T(ldv(b[q + e])) - v[e] : T(0));
+    }
+}
+template <class T, class TB, int C, class IDX>
+__device__ __forceinline__ void prep_entry4(const Lev &L, T *__restrict__ x, const TB *__restrict__ b,
+                                            TB *__restrict__ gh, const T *__restrict__ delta, const Coef<T> &K, int i0,
+                                            int j, int k) {
+    if (i0 >= L.nx || j >= L.ny + (C == 1) || k >= L.nz + (C == 2)) return;
+    const long long q = entry_index<C, IDX>(L, i0, j, k);
+    T v[4] = {T(0), T(0), T(0), T(0)};
+    if (entry_active<C>(L, 0, j, k)) {
+        rows4<T, C, false, IDX>(x, L, i0, j, k, K, v);
+        const V4<TB> bv = ld4(b + q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = T(ldv(bv.v[e])) - v[e];
+    }
+    st4(gh + q, v);
+    if (C == 3 && delta) {
+        // the forward sweep's pending neighbour-pressure part (gather form), as in prep_entry
+        const IDX sy = (IDX)L.nx, sz = sy * (IDX)L.ny;
+        const T *dc = delta + ((IDX)i0 + sy * (IDX)j + sz * (IDX)k);
+        const V4<T> d0 = ld4(dc);
+        const T dl = i0 > 0 ? dc[-1] : T(0), dr = i0 + 4 < L.nx ? dc[4] : T(0);
+        const V4<T> dym = j > 0 ? ld4(dc - sy) : zero4<T>(), dyp = j < L.ny - 1 ? ld4(dc + sy) : zero4<T>();
+        const V4<T> dzm = k > 0 ? ld4(dc - sz) : zero4<T>(), dzp = k < L.nz - 1 ? ld4(dc + sz) : zero4<T>();
+        const bool v2jk = j >= 1 && k >= 1 && j <= L.ny - 2 && k <= L.nz - 2;
+        T *xp = x + q;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = i0 + e;
+            const bool v2 = v2jk && i >= 1 && i <= L.nx - 2;
+            const int colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+            T g = T(0);
+            if (!v2 || !(colour & 1)) g += (e == 0 ? dl : d0.v[e - 1]) + (e == 3 ? dr : d0.v[e + 1]);
+            if (!v2 || !(colour & 2)) g += dym.v[e] + dyp.v[e];
+            if (!v2 || !(colour & 4)) g += dzm.v[e] + dzp.v[e];
+            if (g != T(0)) xp[e] -= K.eh2 * g;
+        }
+    }
+}
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep4(Lev L, T *__restrict__ x, const TB *__restrict__ b,
+                                                            TB *__restrict__ gh, const T *__restrict__ delta,
+                                                            Coef<T> K) {
+    pdl_wait();
+    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const int i = 4 * (blockIdx.x * BX + threadIdx.x), j = blockIdx.y * BY + threadIdx.y;
+    switch (c) {
+    case 0: prep_u4<T, TB, IDX>(L, x, b, gh, K, i, j, k); break;
+    case 1: prep_entry4<T, TB, 1, IDX>(L, x, b, gh, delta, K, i, j, k); break;
+    case 2: prep_entry4<T, TB, 2, IDX>(L, x, b, gh, delta, K, i, j, k); break;
+    default: prep_entry4<T, TB, 3, IDX>(L, x, b, gh, delta, K, i, j, k);
+    }
+}
+
 template <class T, class TB, class IDX>
 __device__ __forceinline__ void p_bwd_cell(const Lev &L, T *__restrict__ x, const TB *__restrict__ ghs, IDX i, IDX j,
                                            IDX k, const Coef<T> &K, T dP) {
@@ -517,7 +756,27 @@ template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, 
     launch_k(k_dgs_p_gather<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, delta, coef<T>(L, L.gamma));
 }
 template <class T, class TB>
+void launch_apply(const Lev &L, const T *x, const TB *b, TB *y, double gam, cudaStream_t s) {
+    if (use_x4(L, x, b, y)) {
+        if (idx32(L)) launch_k(k_apply4<T, TB, int>, grid4(L), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+        else launch_k(k_apply4<T, TB, long long>, grid4(L), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+        return;
+    }
+    if (idx32(L))
+        launch_k(k_apply<T, TB, int>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+    else
+        launch_k(k_apply<T, TB, long long>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+}
+template <class T, class TB>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const TB *b, TB *gh, const T *delta, cudaStream_t s) {
+    if (use_x4(L, x, b, gh, delta)) {
+        if (idx32(L))
+            launch_k(k_dgs_p_bwd_prep4<T, TB, int>, grid4(L), dim3(kBlock3), 0, s, L, x, b, gh, delta, coef<T>(L, L.gamma));
+        else
+            launch_k(k_dgs_p_bwd_prep4<T, TB, long long>, grid4(L), dim3(kBlock3), 0, s, L, x, b, gh, delta,
+                     coef<T>(L, L.gamma));
+        return;
+    }
     if (idx32(L))
         launch_k(k_dgs_p_bwd_prep<T, TB, int>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta,
                  coef<T>(L, L.gamma));
