@@ -230,6 +230,29 @@ def roofline(prof, n, e, peak, traffic_db, precision):
 
 # ------------------------------------------------------------------------------------------ native arm
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time in ms (the whole job ends with it); ms itself on one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def batch_problems(rank, count):
+    """One rank's independent problems: cube sizes uniform over BATCH_SIZES (PCG64 seed 4000 + rank) and
+    bump seeds rank * 100000 + i, disjoint across ranks (replicas: no data is exchanged)."""
+    import numpy as np
+    rng = np.random.default_rng(4000 + rank)
+    return [int(v) for v in rng.choice(BATCH_SIZES, size=count)], [rank * 100000 + i for i in range(count)]
+
+
+def whole_job_value(units_per_rank, world, ms):
+    """Units per second of all ranks together, each rank having processed units_per_rank in ms."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def run_e2e(smg, S, rhs_dev, npk, args, barrier, stream, world, n):
     """sqmr_solve through the C ABI with pinned HOST rhs / x0 / x: the H2D copies of the inputs and the
     D2H copy of the solution happen inside the call, inside the timed region."""
@@ -254,10 +277,8 @@ def run_e2e(smg, S, rhs_dev, npk, args, barrier, stream, world, n):
         ms_e2e += max(ev0.elapsed_time(ev1), (time.perf_counter() - t0) * 1e3)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    return {"value": unknowns(n) * args.steps * world / (ms_e2e * 1e-3), "unit": UNIT,
+        ms_e2e = max_over_ranks(ms_e2e, dist, "cuda")
+    return {"value": whole_job_value(unknowns(n) * args.steps, world, ms_e2e), "unit": UNIT,
             "h2d_bytes_per_step": 2 * npk * 8, "d2h_bytes_per_step": npk * 8,
             "note": "sqmr_solve with pinned host rhs/x0/x, each call timed (its copies inside); the host "
                     "zeroing of x0 before each call is not timed"}
@@ -272,14 +293,12 @@ def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
     concurrent streams).  Beside it: the same problems solved one after another (FP32 V-cycle, and the plain
     FP64 V-cycle).  sqmr_solve_batch returns once every problem has converged, so a step is timed on the
     host with the device synchronised on both sides."""
-    import numpy as np
-    rng = np.random.default_rng(4000 + rank)
-    sizes = [int(v) for v in rng.choice(BATCH_SIZES, size=args.batch)]
+    sizes, bump_seeds = batch_problems(rank, args.batch)
     S32, rhs, xs = [], [], []
     for i, n in enumerate(sizes):
         S = smg.Stokes(n, precision=smg.PREC_FP32)
         S32.append(S)
-        rhs.append(S.rhs(synthetic.bumps(n, seed=rank * 100000 + i, device=dev)["f"], None))
+        rhs.append(S.rhs(synthetic.bumps(n, seed=bump_seeds[i], device=dev)["f"], None))
         xs.append(torch.zeros(S.n, dtype=torch.float64, device=dev))
     total_unknowns = sum(unknowns(n) for n in sizes)
 
@@ -289,11 +308,7 @@ def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
         torch.cuda.synchronize()
 
     def maxrank(ms):
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ms, dist, dev)
 
     def batch_step():
         for x in xs:
@@ -419,12 +434,8 @@ def run_cavity(args, smg, synthetic, torch, dev, rank, world, dist):
             its.append((info.iterations, info.rel_residual))
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        res[name] = {"value": nunk * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps,
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        res[name] = {"value": whole_job_value(nunk * args.steps, world, ms), "ms_per_step": ms / args.steps,
                      "iterations": [i for i, _ in its], "rel_residual": [r for _, r in its], "levels": S.levels}
         S.close()
     if rank == 0:
@@ -633,7 +644,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--n", type=int, default=None, help="cells per axis (default 256; 128 for --mode cavity)")
+    ap.add_argument("--n", "--cells", dest="n", type=int, default=None,
+                    help="cells per axis (default 256; 128 for --mode cavity, warmstart, comparators); --cells is the "
+                         "spelling to use under torchrun, whose own options start with --n")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 V-cycle solve beside the headline")
@@ -745,19 +758,14 @@ def main():
             collect.append((info.iterations, info.rel_residual))
         ev1.record(stream)
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
 
     # headline: FP32 V-cycle, FP64 SQMR
     its32 = []
     with ClockSampler(local) as clk:
         ms32 = timed(S32, args.steps, args.warmup, its32)
     assert all(r < args.tol for _, r in its32), its32
-    value = unknowns(n) * args.steps * world / (ms32 * 1e-3)
+    value = whole_job_value(unknowns(n) * args.steps, world, ms32)
 
     prof32 = smg.stokes_profile_iteration(S32.h)
     launches_iter = sum(v[1] for v in prof32.values())
