@@ -105,7 +105,10 @@ typedef struct {
 
 typedef struct {
     int iterations;        /* SQMR iterations performed (Alg. 4 loop index j) */
-    double rel_residual;   /* true ||b - L x||_2 / ||b||_2 of the returned x, recomputed in FP64 */
+    double rel_residual;   /* true ||b - L x||_2 / ||b||_2 of the returned x, explicit FP64: the residual
+                            * that confirmed convergence (removing the pressure mean afterwards changes
+                            * L x only by rounding, a constant pressure lies in ker L), else recomputed
+                            * at exit */
     int status;            /* same value as the call's return code */
     int vcycles;           /* preconditioner applications (iterations + 1) */
 } sqmr_info_t;

@@ -1086,6 +1086,7 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
     double nb = std::sqrt(bb);
     int it = 0, status = STOKES_OK;
     double rel = 0.0;
+    bool rel_confirmed = false;  // rel holds the explicit FP64 residual of the returned x (up to the pressure shift)
     if (!std::isfinite(nb)) {
         status = STOKES_ERR_NAN;
         goto finish;
@@ -1135,7 +1136,11 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
             double r2 = 0.0;
             if ((rc = residual_norm2(h, h->bvec, h->x, h->w, &r2, s))) return rc;
             rel = std::sqrt(r2) / nb;
-            if (rel < tol) { status = STOKES_OK; break; }
+            if (rel < tol) {
+                status = STOKES_OK;
+                rel_confirmed = true;
+                break;
+            }
             CK(cudaMemcpyAsync(h->r, h->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         }
     }
@@ -1146,7 +1151,10 @@ finish:
     launch_scalars_aux(5, h->partials, kRedBlocks, h->st, h->hout, (double)h->ncell_active, s);
     launch_psub(L, h->x, h->st, s);
     CKLAUNCH();
-    {
+    // the residual reported: after a converged confirmation it is the one just computed (subtracting a
+    // constant from the interior pressures changes L x only by rounding: the constant lies in ker L);
+    // otherwise the explicit FP64 residual of the returned x
+    if (!rel_confirmed) {
         double r2 = 0.0;
         if ((rc = residual_norm2(h, h->bvec, h->x, nullptr, &r2, s))) return rc;
         rel = nb > 0 ? std::sqrt(r2) / nb : 0.0;

@@ -561,3 +561,16 @@ def test_apply_on_unaligned_buffers_matches_aligned():
     smg.stokes_apply(S.h, xs[1:], ys[1:])
     assert rel_err(ys[1:], ya.cpu().numpy()) < 1e-15
     assert rel_err(ya, o.apply(x)) < 1e-13
+
+
+@pytest.mark.parametrize("precision", [smg.PREC_FP64, smg.PREC_FP32])
+def test_reported_residual_matches_recomputed(precision):
+    # the converged solve reports the residual of its confirmation step; the returned x (pressure mean
+    # removed afterwards) has the same residual up to rounding
+    o, S = pair((32, 32, 32), precision=precision)
+    b = o.rhs(synthetic.bumps(32, seed=9)["f"].numpy(), None)
+    x, info = S.solve(cuda(b), tol=1e-9)
+    assert info.status == 0
+    ref = smg.stokes_residual_norm(S.h, cuda(b), x) / np.linalg.norm(b)
+    assert ref < 1e-9
+    assert info.rel_residual == pytest.approx(ref, rel=1e-6, abs=1e-15)
