@@ -44,7 +44,7 @@ extern "C" {
 #define STOKES_ERR_NOT_CONVERGED -5 /* SQMR: max_iter reached before the tolerance */
 #define STOKES_ERR_NAN -6           /* a NaN/Inf appeared in the SQMR scalars */
 #define STOKES_ERR_TIMEOUT -7       /* a device-side grid barrier ran out of its iteration limit */
-#define STOKES_ERR_UNSUPPORTED -8   /* valid request this build does not implement */
+#define STOKES_ERR_UNSUPPORTED -8   /* valid request the library does not implement */
 
 /* precision of the V-cycle (the SQMR recurrences, the true-residual check and the coarsest
  * solve always run in FP64) */
