@@ -190,12 +190,13 @@ def _assemble(fn, n, active):
     return C
 
 
-@pytest.mark.parametrize("variant", ["", "additive", "dwj", "kb2"])
+@pytest.mark.parametrize("variant", ["", "additive", "dwj", "kb2", "wcycle"])
 def test_labelled_vcycle_symmetric(variant):
     n = 8
     lab = synthetic.porous_labels(n, seed=3, nspheres=4, rmin=0.15, rmax=0.3)
-    o = oracle.Oracle(n, eta=1e-3, levels=2, coarsest_max=4, labels=lab, kb=2 if variant == "kb2" else 1,
-                      additive=variant == "additive", dwj=variant == "dwj")
+    o = oracle.Oracle(n, eta=1e-3, levels=3 if variant == "wcycle" else 2, coarsest_max=2, labels=lab,
+                      kb=2 if variant == "kb2" else 1, additive=variant == "additive", dwj=variant == "dwj",
+                      cycle=2 if variant == "wcycle" else 1)
     act, _ = o.masks()
     W = _assemble(o.vcycle, o.n(), act)
     assert np.max(np.abs(W)) > 0
