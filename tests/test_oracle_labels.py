@@ -335,3 +335,17 @@ def test_exterior_sqmr_matches_direct_solve():
     ref = np.linalg.lstsq(_assemble(o.apply, o.n(), act), b[cols], rcond=None)[0]
     ref[-int(pact.sum()):] -= ref[-int(pact.sum()):].mean()
     assert np.max(np.abs(x[cols] - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_explicit_box_labels_reproduce_table1():
+    # Table 1 (3D 128^3 driven cavity): the box written out as labels, through the labelled
+    # classification, gives the printed total and boundary DOF counts
+    import os
+    golden = os.path.join(os.path.dirname(__file__), "golden", "table1_box.txt")
+    rows = [l for l in open(golden) if l.strip() and not l.startswith("#")]
+    for row in rows:
+        parts = [p.strip() for p in row.split(",")]
+        nx, ny, nz, total, boundary = map(int, parts[1:])
+        lab = np.ones((nz + 2, ny + 2, nx + 2), np.uint8)
+        lab[1:-1, 1:-1, 1:-1] = 0
+        assert oracle.count_dofs(nx, ny, nz, lab) == (total, boundary)
