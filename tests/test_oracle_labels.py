@@ -349,3 +349,27 @@ def test_explicit_box_labels_reproduce_table1():
         lab = np.ones((nz + 2, ny + 2, nx + 2), np.uint8)
         lab[1:-1, 1:-1, 1:-1] = 0
         assert oracle.count_dofs(nx, ny, nz, lab) == (total, boundary)
+
+
+def test_labelled_restriction_is_scaled_transpose_of_prolongation():
+    # Sec. 2: R = P^T / 8 also where obstacles and exterior cells remove fine and coarse unknowns; P
+    # reaches no fine DOF that is not an unknown, R reads none
+    n = 8
+    lab = synthetic.porous_labels(n, seed=2, nspheres=4, rmin=0.15, rmax=0.3, exterior_every=2)
+    o = oracle.Oracle(n, levels=2, coarsest_max=4, labels=lab)
+    act0 = o.masks(0)[0].astype(bool)
+    act1 = o.masks(1)[0].astype(bool)
+    n0, n1 = o.n(0), o.n(1)
+    P = np.zeros((n0, n1))
+    for c in np.nonzero(act1)[0]:
+        e = np.zeros(n1)
+        e[c] = 1.0
+        P[:, c] = o.prolong_add(e, np.zeros(n0))
+    R = np.zeros((n1, n0))
+    for f in np.nonzero(act0)[0]:
+        e = np.zeros(n0)
+        e[f] = 1.0
+        R[:, f] = o.restrict(e)
+    assert np.max(np.abs(P)) > 0
+    assert np.max(np.abs(8.0 * R - P.T)) < 1e-15
+    assert np.max(np.abs(P[~act0])) == 0.0 and np.max(np.abs(R[~act1])) == 0.0
