@@ -373,3 +373,19 @@ def test_labelled_restriction_is_scaled_transpose_of_prolongation():
     assert np.max(np.abs(P)) > 0
     assert np.max(np.abs(8.0 * R - P.T)) < 1e-15
     assert np.max(np.abs(P[~act0])) == 0.0 and np.max(np.abs(R[~act1])) == 0.0
+
+
+def test_labelled_coarse_solve_is_the_inverse_of_the_coarse_operator():
+    # Alg. 1: the coarsest level is solved exactly with L~ of that level (labels coarsened per Sec. 5)
+    n = 8
+    lab = synthetic.porous_labels(n, seed=6, nspheres=4, rmin=0.15, rmax=0.3, exterior_every=2)
+    o = oracle.Oracle(n, levels=2, coarsest_max=4, labels=lab)
+    lc = o.nlevels - 1
+    act = o.masks(lc)[0].astype(bool)
+    cols = np.nonzero(act)[0]
+    A = _assemble(lambda e: o.apply(e, level=lc, penalised=True), o.n(lc), act)
+    b = _rand(o.n(lc), 21) * act
+    x = o.coarse_solve(b)
+    ref = np.linalg.solve(A, b[cols])
+    assert np.max(np.abs(x[cols] - ref)) <= 1e-10 * np.max(np.abs(ref))
+    assert not x[~act].any()
