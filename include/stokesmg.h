@@ -242,8 +242,11 @@ int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launch
  * anything.  The paper has no counterpart; this exists for callers that cannot allocate device
  * memory where they need the check (a fixed-budget memory pool, a host callback, an allocator-free
  * hook): creating a handle allocates the whole hierarchy.
- * b, x: packed FP64 vectors in device memory, read in place (entries of x off the unknowns are
- * ignored).  out: one double in device memory, written asynchronously on `stream`.
+ * b, x: packed FP64 vectors in device memory of the CURRENT device, read in place (entries of x
+ * off the unknowns are ignored).  out: one double in device memory of the current device, written
+ * asynchronously on `stream`, which must belong to the current device (NULL: the legacy default
+ * stream).  Pointers to host memory or to another GPU's memory, a stream of another device, a
+ * non-finite h or viscosity, or viscosity <= 0 return STOKES_ERR_INVALID_ARG.
  * Scratch: a fixed device array of 16384 doubles (128 KiB) inside the library, present on every
  * GPU that loads it until exit; grids needing more partial sums than that (more than 16384 blocks
  * of 32 x 8 x 16 cell positions, about 380^3) return STOKES_ERR_INVALID_ARG, as do host pointers.

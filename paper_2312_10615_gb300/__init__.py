@@ -145,6 +145,11 @@ def _ptr(a):
     raise TypeError(f"unsupported vector type {type(a)}")
 
 
+def _numel(a):
+    """Number of entries of a torch tensor or numpy array."""
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
 def _stream(stream):
     if stream is None:
         try:
@@ -272,6 +277,12 @@ def stokes_set_level_schedule(h, level, mode, blocks=0):
 def stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, b, x, out, stream=None):
     """||b - L x||_2 written into the 1-element device tensor `out`, without any allocation in the
     library (for callers that cannot allocate; see include/stokesmg.h)."""
+    n = (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1) + nx * ny * nz
+    for name, t in (("b", b), ("x", x)):
+        if _numel(t) < n:
+            raise StokesError(ERR_INVALID_ARG, f"stokes_residual_norm_noalloc: {name} holds {_numel(t)} < {n} entries")
+    if _numel(out) < 1:
+        raise StokesError(ERR_INVALID_ARG, "stokes_residual_norm_noalloc: out holds no entry")
     _check(lib().stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, _ptr(b), _ptr(x), _ptr(out),
                                               _stream(stream)), "stokes_residual_norm_noalloc")
 

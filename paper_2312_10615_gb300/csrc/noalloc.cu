@@ -77,23 +77,25 @@ __global__ void __launch_bounds__(256) k_noalloc_finish(const double *__restrict
     if (threadIdx.x == 0) *out = sqrt(sh[0]);
 }
 
-bool device_pointer(const void *p) {
+// p is device (or managed) memory of device dev: memory of another GPU would be read through the
+// peer path, or fault where no peer access is enabled
+bool device_pointer(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
 
 extern "C" int stokes_residual_norm_noalloc(int nx, int ny, int nz, double h, double viscosity, const double *b,
                                             const double *x, double *out, void *stream) {
-    if (nx < 2 || ny < 2 || nz < 2 || !(viscosity > 0.0) || !b || !x || !out) return STOKES_ERR_INVALID_ARG;
+    if (nx < 2 || ny < 2 || nz < 2 || !b || !x || !out) return STOKES_ERR_INVALID_ARG;
+    if (!(viscosity > 0.0) || !std::isfinite(viscosity) || !std::isfinite(h)) return STOKES_ERR_INVALID_ARG;
     if (nx > 2047 || ny > 2047 || nz > 1023) return STOKES_ERR_INVALID_ARG;
-    // the caller's vectors are read in place: staging host data would need an allocation
-    if (!device_pointer(b) || !device_pointer(x) || !device_pointer(out)) return STOKES_ERR_INVALID_ARG;
     dim3 grid((nx + 1 + NBX - 1) / NBX, (ny + 1 + NBY - 1) / NBY, (nz + 1 + NKZ - 1) / NKZ);
     long long nparts = (long long)grid.x * grid.y * grid.z;
     if (nparts > kNoAllocMaxParts) return STOKES_ERR_INVALID_ARG;  // grid too large for the fixed scratch
@@ -101,6 +103,17 @@ extern "C" int stokes_residual_norm_noalloc(int nx, int ny, int nz, double h, do
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return STOKES_ERR_CUDA;
+    }
+    // the caller's vectors are read in place, on the current device: staging host data would need an
+    // allocation, and memory of another GPU is not this launch's to read
+    if (!device_pointer(b, dev) || !device_pointer(x, dev) || !device_pointer(out, dev)) return STOKES_ERR_INVALID_ARG;
+    if (stream) {
+        int sdev = -1;
+        if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return STOKES_ERR_INVALID_ARG;
+        }
+        if (sdev != dev) return STOKES_ERR_INVALID_ARG;
     }
     double *parts = nullptr;
     {
