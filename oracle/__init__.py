@@ -52,6 +52,7 @@ def _load():
                                      ctypes.POINTER(vp)]),
         "og_destroy": (None, [vp]),
         "og_nlevels": (ctypes.c_int, [vp]),
+        "og_has_neumann": (ctypes.c_int, [vp]),
         "og_level_n": (ctypes.c_long, [vp, ctypes.c_int]),
         "og_level_dims": (None, [vp, ctypes.c_int, _i]),
         "og_level_masks": (None, [vp, ctypes.c_int, _u8, _u8]),
@@ -128,6 +129,10 @@ class Oracle:
             self._h = ctypes.c_void_p()
 
     # -- sizes / classification ----------------------------------------------------------
+    def has_neumann(self):
+        """True when some unknown face borders an exterior cell (Sec. 5): no pressure null space."""
+        return bool(self.lib.og_has_neumann(self._h))
+
     def n(self, level=0):
         return self.lib.og_level_n(self._h, level)
 

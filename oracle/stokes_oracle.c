@@ -24,7 +24,10 @@
  *  - scaling: A = (eta/h^2)(7-point stencil), B^T = gradient/h, B = -divergence/h.
  *  - a Dirichlet face neighbour keeps its value (grid-cell precision), the diagonal
  *    stays 6 eta/h^2; inside the preconditioner the Dirichlet values are zero.
- *  - V1 = all active DOFs of interior cells that share a face with a non-interior cell.
+ *  - V1 = all active DOFs of interior cells that lie within one cell (26-neighbourhood) of a
+ *    Dirichlet cell or within two cells (Chebyshev distance) of an exterior cell.  With exterior
+ *    cells absent this is the face-neighbour set on the box; the rule as a whole reproduces the
+ *    total and boundary DOF counts of Table 1 for the box and for every cylinder row.
  *  - DGS traversal order: V2 velocities with (i+j+k) even, then odd, then V2 pressures in
  *    8 colours (i mod 2, j mod 2, k mod 2); the backward sweep is the exact reverse.  DGS relaxes the V2 rows and
  *    distributes along the full column M_{.j} (Alg. 2), which for a V2 pressure next to the
@@ -36,13 +39,15 @@
  *  - prolongation of a face value: weight 1 (coincident) or 1/2,1/2 along the normal,
  *    3/4,1/4 along each tangential axis; coarse DOFs that are not active contribute 0.
  *  - convergence: true relative residual ||b - L x||_2 / ||b||_2 < tol.
- *  - exterior cells (Sec. 5): a face between an interior and an exterior cell carries a
- *    homogeneous Neumann condition, taken as the known value zero (the paper's examples use zero
- *    and move nonzero data to the right-hand side without changing the operator); faces with no
- *    interior cell beside them are inactive and drop out of every stencil.  On the unknowns the
- *    operator is therefore the one of Dirichlet cells with zero data; exterior cells differ from
- *    Dirichlet cells in coarsening (an exterior child does not make its coarse cell Dirichlet)
- *    and in the data: g is read on faces of Dirichlet cells only.
+ *  - exterior cells (Sec. 5): the velocity on a face between an interior and an exterior cell is an
+ *    unknown (Table 1 counts it) whose equation carries the homogeneous Neumann condition as a
+ *    natural (do-nothing) outflow condition: the pressure of an exterior cell is the known value 0,
+ *    and a viscous difference term of the velocity stencil drops out (diagonal and neighbour alike)
+ *    when it crosses an exterior cell along the face normal, or when the tangential neighbour face
+ *    has no interior cell beside it (an inactive face).  Dropped terms are symmetric pairs, so L stays
+ *    symmetric; nonzero Neumann data would enter the right-hand side only.  Faces with no interior
+ *    cell beside them that are not faces of a Dirichlet cell are inactive.  When some unknown face
+ *    borders an exterior cell the pressure has no null space and is not shifted to zero mean.
  */
 #include <math.h>
 #include <stdint.h>
@@ -68,7 +73,8 @@ typedef struct {
     long ov, ow, op;        /* offsets of v, w, p */
     uint8_t *lab;           /* (nx+2)(ny+2)(nz+2) cell labels including the ghost shell */
     uint8_t *active;        /* per packed entry */
-    uint8_t *v1;            /* per packed entry: active DOF of a cell next to a non-interior cell */
+    uint8_t *v1;            /* per packed entry: active DOF of a cell proximal to a non-interior cell */
+    int neumann;            /* some unknown face borders an exterior cell (no pressure null space) */
     long *order;            /* DGS traversal order of the V2 DOFs */
     long norder;
     double *dgs_d;          /* d_j = L~_j . M_{.j} per packed entry (V2 entries only) */
@@ -125,14 +131,33 @@ static void decode(const og_level *L, long q, int *c, int *i, int *j, int *k) {
 
 static inline void unit(int d, int *e) { e[0] = d == 0; e[1] = d == 1; e[2] = d == 2; }
 
-/* Sec. 5: a face is active when both cells beside it are interior, Dirichlet when either is Dirichlet. */
-static inline int face_active(const og_level *L, int c, int i, int j, int k) {
-    int e[3]; unit(c, e);
-    return lab_at(L, i - e[0], j - e[1], k - e[2]) == LAB_INTERIOR && lab_at(L, i, j, k) == LAB_INTERIOR;
-}
+/* Sec. 5: a face of a Dirichlet cell is Dirichlet; otherwise a face with an interior cell beside it
+ * is an unknown (between two interior cells, or a Neumann face between an interior and an exterior
+ * cell); a face between two exterior cells is inactive. */
 static inline int face_dirichlet(const og_level *L, int c, int i, int j, int k) {
     int e[3]; unit(c, e);
     return lab_at(L, i - e[0], j - e[1], k - e[2]) == LAB_DIRICHLET || lab_at(L, i, j, k) == LAB_DIRICHLET;
+}
+static inline int face_active(const og_level *L, int c, int i, int j, int k) {
+    int e[3]; unit(c, e);
+    if (face_dirichlet(L, c, i, j, k)) return 0;
+    return lab_at(L, i - e[0], j - e[1], k - e[2]) == LAB_INTERIOR || lab_at(L, i, j, k) == LAB_INTERIOR;
+}
+static inline int face_inactive(const og_level *L, int c, int i, int j, int k) {
+    return !face_dirichlet(L, c, i, j, k) && !face_active(L, c, i, j, k);
+}
+
+/* does the viscous term between face (c,i,j,k) and its same-component neighbour one cell away along
+ * axis d (sgn = +1 or -1) drop out?  Along the normal (d = c) the term crosses the cell between the
+ * two faces, and drops when that cell is exterior (the zero-normal-derivative condition of a Neumann
+ * face); along a tangential axis it drops when the neighbour face is inactive. */
+static inline int nbr_dropped(const og_level *L, int c, int i, int j, int k, int d, int sgn) {
+    int e[3]; unit(d, e);
+    if (d == c) {
+        int a = i - (sgn < 0) * e[0], b = j - (sgn < 0) * e[1], cc = k - (sgn < 0) * e[2];
+        return lab_at(L, a, b, cc) == LAB_EXTERIOR;
+    }
+    return face_inactive(L, c, i + sgn * e[0], j + sgn * e[1], k + sgn * e[2]);
 }
 
 /* value of an unknown in x; entries that are not active DOFs count as zero */
@@ -144,18 +169,22 @@ static inline double xval(const og_level *L, const double *x, int c, int i, int 
 
 /* ------------------------------------------------------------------------------------ */
 /* Eq. (2): one row of L (gam = 0) or of L~ (gam = gamma, Sec. 4) applied to x.           */
-/* velocity row:  eta/h^2 (6 u_f - sum of 6 same-component neighbours) + (p_+ - p_-)/h    */
+/* velocity row:  eta/h^2 (sum over the 6 same-component neighbours g of (u_f - u_g))        */
+/*                + (p_+ - p_-)/h; terms that drop out (nbr_dropped) are left out of the sum,  */
+/*                Dirichlet neighbours and exterior pressures count zero                      */
 /* pressure row: -(sum over axes of (u_hi - u_lo))/h - gam p_c                            */
 static double og_row(const og_level *L, long q, const double *x, double gam) {
     int c, i, j, k, e[3];
     decode(L, q, &c, &i, &j, &k);
     double h = L->h;
     if (c < 3) {
-        double s = 6.0 * x[q];
+        double s = 0.0;
         for (int d = 0; d < 3; ++d) {
             unit(d, e);
-            s -= xval(L, x, c, i + e[0], j + e[1], k + e[2]);
-            s -= xval(L, x, c, i - e[0], j - e[1], k - e[2]);
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                if (nbr_dropped(L, c, i, j, k, d, sgn)) continue;
+                s += x[q] - xval(L, x, c, i + sgn * e[0], j + sgn * e[1], k + sgn * e[2]);
+            }
         }
         unit(c, e);
         double pp = xval(L, x, 3, i, j, k);
@@ -568,19 +597,28 @@ static int level_init(og_level *L, int nx, int ny, int nz, double h, double eta,
         int c, i, j, k;
         decode(L, q, &c, &i, &j, &k);
         L->active[q] = c < 3 ? (uint8_t)face_active(L, c, i, j, k) : (uint8_t)(lab_at(L, i, j, k) == LAB_INTERIOR);
+        if (c < 3 && L->active[q]) {
+            int e0[3]; unit(c, e0);
+            if (lab_at(L, i, j, k) == LAB_EXTERIOR || lab_at(L, i - e0[0], j - e0[1], k - e0[2]) == LAB_EXTERIOR)
+                L->neumann = 1;
+        }
     }
-    /* Sec. 5: V1 = every active DOF of an interior cell that has a non-interior face neighbour */
+    /* Sec. 5: V1 = every active DOF of an interior cell "proximal" to a Dirichlet or an exterior cell:
+     * a Dirichlet cell within Chebyshev distance 1 (the 26 neighbours) or an exterior cell within
+     * Chebyshev distance 2 */
     int e[3];
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 if (lab_at(L, i, j, k) != LAB_INTERIOR) continue;
                 int prox = 0;
-                for (int d = 0; d < 3; ++d) {
-                    unit(d, e);
-                    if (lab_at(L, i + e[0], j + e[1], k + e[2]) != LAB_INTERIOR) prox = 1;
-                    if (lab_at(L, i - e[0], j - e[1], k - e[2]) != LAB_INTERIOR) prox = 1;
-                }
+                for (int dk = -2; dk <= 2; ++dk)
+                    for (int dj = -2; dj <= 2; ++dj)
+                        for (int di = -2; di <= 2; ++di) {
+                            int l = lab_at(L, i + di, j + dj, k + dk);
+                            int near1 = di >= -1 && di <= 1 && dj >= -1 && dj <= 1 && dk >= -1 && dk <= 1;
+                            if ((l == LAB_DIRICHLET && near1) || l == LAB_EXTERIOR) prox = 1;
+                        }
                 if (!prox) continue;
                 long D[7];
                 int m = og_patch(L, i, j, k, D);
@@ -714,6 +752,7 @@ int og_create(int nx, int ny, int nz, double h, double eta, double gamma, int le
 }
 
 int og_nlevels(const og_hier *H) { return H->nlev; }
+int og_has_neumann(const og_hier *H) { return H->lev[0].neumann; }
 long og_level_n(const og_hier *H, int l) { return H->lev[l].n; }
 void og_level_dims(const og_hier *H, int l, int *dims) { dims[0] = H->lev[l].nx; dims[1] = H->lev[l].ny; dims[2] = H->lev[l].nz; }
 void og_level_masks(const og_hier *H, int l, uint8_t *active, uint8_t *v1) {
@@ -769,6 +808,7 @@ void og_rhs(og_hier *H, const double *f, const double *g, double *b) {
                 unit(d, e);
                 for (int sgn = -1; sgn <= 1; sgn += 2) {
                     int a = i + sgn * e[0], bb = j + sgn * e[1], cc = k + sgn * e[2];
+                    if (nbr_dropped(L, c, i, j, k, d, sgn)) continue;
                     if (face_dirichlet(L, c, a, bb, cc) && g) v += L->eta / (h * h) * gval(L, g, c, a, bb, cc);
                 }
             }
@@ -903,8 +943,8 @@ int og_sqmr(og_hier *H, const double *b, double *x, double tol, int maxit, int p
     }
     if (j > maxit) j = maxit;
 done:
-    /* pressure fixed to zero mean */
-    {
+    /* pressure fixed to zero mean (only where constant pressures form a null space: no Neumann face) */
+    if (!L->neumann) {
         double sum = 0.0; long cnt = 0;
         for (long a = L->op; a < n; ++a) if (L->active[a]) { sum += x[a]; ++cnt; }
         if (cnt) for (long a = L->op; a < n; ++a) if (L->active[a]) x[a] -= sum / cnt;

@@ -22,6 +22,9 @@ Workloads:
   interior cells cut off from the largest 6-connected interior region are made Dirichlet.
   ``plug_flow`` gives the channel's Dirichlet data: u = 1 on the open inflow side (x = 0), the same flux
   out of the open outflow side (x = 1), no-slip on the other walls and on the obstacles.
+* ``channel_labels`` / ``channel_inflow``: a channel along x whose last columns of cells are exterior
+  (an open outflow, Sec. 7 cylinder examples), optionally with a z-aligned cylinder of Dirichlet cells,
+  and its inflow data: the fully developed duct profile on the x = 0 side, nothing at the outlet.
 
 Random numbers come from numpy's PCG64 seeded per problem; evaluation runs in torch float64 on
 whatever device is asked for (CPU for the oracle, CUDA to build large inputs quickly).
@@ -278,6 +281,43 @@ def plug_flow(nx, ny=None, nz=None, labels=None, device="cpu"):
     u = torch.zeros(nz + 2, ny + 2, nx + 1, dtype=torch.float64, device=device)
     u[1:-1, 1:-1, 0] = open_in
     u[1:-1, 1:-1, nx] = open_out * (open_in.sum() / open_out.sum())
+    v = torch.zeros((nz + 2) * (ny + 1) * (nx + 2), dtype=torch.float64, device=device)
+    w = torch.zeros((nz + 1) * (ny + 2) * (nx + 2), dtype=torch.float64, device=device)
+    return torch.cat([u.reshape(-1), v, w])
+
+
+def channel_labels(nx, ny=None, nz=None, outlet=1, cylinder=None):
+    """Channel along x with an open outflow: the last `outlet` columns of cells (i >= nx - outlet) are
+    exterior (label 2), the ghost shell is Dirichlet, and an optional z-aligned cylinder of Dirichlet
+    cells -- cylinder = (cx, cy, r) in cells; a cell is inside when its centre lies strictly inside the
+    circle -- stands in the flow.  Returns uint8 (nz+2, ny+2, nx+2)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    lab = _shell(nx, ny, nz)
+    if cylinder is not None:
+        cx, cy, r = cylinder
+        yc, xc = np.meshgrid(np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+        inside = (xc - cx) ** 2 + (yc - cy) ** 2 < r * r
+        lab[1:-1, 1:-1, 1:-1][:, inside] = 1
+    lab[1:-1, 1:-1, 1 + nx - outlet:1 + nx] = 2
+    return _connected(lab)
+
+
+def channel_inflow(nx, ny=None, nz=None, labels=None, mean=1.0, device="cpu"):
+    """Ghost-extended Dirichlet data of a channel along x with an open (exterior) outlet: on the x = 0
+    side the fully developed duct profile u = 16 U y z (1 - y)(1 - z) in units of the side lengths
+    (mean-velocity scale U = mean), on faces of interior cells only; zero on every other face (no-slip
+    walls and obstacles).  Nothing is prescribed at the outlet."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    yc = (torch.arange(ny, dtype=torch.float64, device=device) + 0.5) / ny
+    zc = (torch.arange(nz, dtype=torch.float64, device=device) + 0.5) / nz
+    prof = 16.0 * mean * (zc * (1 - zc))[:, None] * (yc * (1 - yc))[None, :]
+    if labels is not None:
+        lab = torch.as_tensor(np.asarray(labels).reshape(nz + 2, ny + 2, nx + 2))
+        prof = prof * (lab[1:-1, 1:-1, 1] == 0).to(torch.float64).to(device)
+    u = torch.zeros(nz + 2, ny + 2, nx + 1, dtype=torch.float64, device=device)
+    u[1:-1, 1:-1, 0] = prof
     v = torch.zeros((nz + 2) * (ny + 1) * (nx + 2), dtype=torch.float64, device=device)
     w = torch.zeros((nz + 1) * (ny + 2) * (nx + 2), dtype=torch.float64, device=device)
     return torch.cat([u.reshape(-1), v, w])

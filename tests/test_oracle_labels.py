@@ -85,23 +85,28 @@ def test_labelled_apply_is_masked_box_apply(seed):
 
 
 def test_labelled_classification_by_brute_force():
-    # active faces: both adjacent cells interior; active pressures: interior cells; V1: every
-    # active unknown of an interior cell with a non-interior face neighbour (Sec. 5)
+    # Sec. 5, written out cell by cell: a face is Dirichlet if either cell beside it is Dirichlet, else an
+    # unknown if either cell is interior (between two interior cells, or a Neumann face next to an exterior
+    # cell), else inactive; pressures of interior cells are unknowns.  V1: every unknown of an interior
+    # cell with a Dirichlet cell among its 26 neighbours or an exterior cell within two cells
     n = 6
     lab = _frame_labels(n, 0)
     lab[3, 3, 3] = lab[2, 4, 3] = 1  # two obstacle cells, (i, j, k) = (2, 2, 2) and (2, 3, 1)
+    lab[1 + 5, 1 + 1, 1 + 4] = lab[1 + 5, 1 + 1, 1 + 5] = 2  # two exterior cells, (4, 1, 5) and (5, 1, 5)
     o = oracle.Oracle(n, levels=1, coarsest_max=n, labels=lab)
     act, v1 = o.masks()
-    L = lambda i, j, k: lab[k + 1, j + 1, i + 1]
+    L = lambda i, j, k: lab[k + 1, j + 1, i + 1] if min(i, j, k) >= -1 and max(i, j, k) <= n else 1
     shapes = _sizes(n)
     ea, ev = [], []
     cellv1 = np.zeros((n, n, n), bool)
     for k in range(n):
         for j in range(n):
             for i in range(n):
-                if L(i, j, k) == 0:
-                    cellv1[k, j, i] = any(L(i + a, j + b, k + c) != 0 for a, b, c in
-                                          ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)))
+                if L(i, j, k) != 0:
+                    continue
+                near = [L(i + a, j + b, k + c) for a in range(-2, 3) for b in range(-2, 3) for c in range(-2, 3)]
+                near1 = [L(i + a, j + b, k + c) for a in range(-1, 2) for b in range(-1, 2) for c in range(-1, 2)]
+                cellv1[k, j, i] = 1 in near1 or 2 in near
     for c, s in enumerate(shapes):
         A = np.zeros(s, np.uint8)
         V = np.zeros(s, np.uint8)
@@ -114,13 +119,17 @@ def test_labelled_classification_by_brute_force():
                         continue
                     e = [(1, 0, 0), (0, 1, 0), (0, 0, 1)][c]
                     mi, mj, mk = i - e[0], j - e[1], k - e[2]
-                    A[k, j, i] = L(i, j, k) == 0 and L(mi, mj, mk) == 0
+                    pair = (L(i, j, k), L(mi, mj, mk))
+                    A[k, j, i] = 1 not in pair and 0 in pair
                     if A[k, j, i]:
-                        V[k, j, i] = (k < n and j < n and i < n and cellv1[k, j, i]) or cellv1[mk, mj, mi]
+                        V[k, j, i] = (k < n and j < n and i < n and cellv1[k, j, i]) or \
+                            (min(mi, mj, mk) >= 0 and cellv1[mk, mj, mi])
         ea.append(A.reshape(-1))
         ev.append(V.reshape(-1))
     assert np.array_equal(act, np.concatenate(ea))
     assert np.array_equal(v1, np.concatenate(ev))
+    # the Neumann faces of the two exterior cells are unknowns
+    assert o.has_neumann()
 
 
 def test_coarse_label_is_dirichlet_if_any_child_is():
@@ -243,17 +252,17 @@ def test_labelled_iterations_stay_flat():
 
 
 # ----------------------------------------------------------------------------------------------
-# exterior cells (Sec. 5): homogeneous Neumann faces, inactive faces, the coarsening rule
+# exterior cells (Sec. 5): Neumann faces as do-nothing outflow unknowns, inactive faces, coarsening
 
 
 def _mixed(n, seed):
     return synthetic.porous_labels(n, seed=seed, nspheres=8, rmin=0.12, rmax=0.25, exterior_every=2)
 
 
-def test_exterior_operator_equals_dirichlet_zero_on_the_finest_level():
-    # reading of Sec. 5: a face between an interior and an exterior cell is a homogeneous Neumann
-    # condition taken as the known value 0, and faces without an interior neighbour drop out, so on
-    # the unknowns the operator and the V1/V2 split are those of Dirichlet cells with zero data
+def test_exterior_and_dirichlet_labellings_differ_on_the_finest_level():
+    # reading of Sec. 5: a face between an interior and an exterior cell is an unknown carrying the
+    # homogeneous Neumann (do-nothing) condition, so exterior cells are not Dirichlet cells with zero
+    # data: the unknown set grows by the Neumann faces and the operator rows next to them change
     n = 12
     lab = _mixed(n, 1)
     assert (lab == 2).any() and (lab[1:-1, 1:-1, 1:-1] == 1).any()
@@ -262,22 +271,39 @@ def test_exterior_operator_equals_dirichlet_zero_on_the_finest_level():
     od = oracle.Oracle(n, eta=0.7, gamma=0.01, levels=2, coarsest_max=6, labels=dl)
     ae, ve = oe.masks()
     ad, vd = od.masks()
-    assert np.array_equal(ae, ad) and np.array_equal(ve, vd)
-    x = _rand(oe.n(), 2) * ae
-    for pen in (False, True):
-        y = oe.apply(x, penalised=pen)
-        assert np.max(np.abs(y - od.apply(x, penalised=pen))) <= 1e-14 * np.max(np.abs(y))
+    assert not (ad & ~ae).any() and (ae & ~ad).sum() > 0  # Neumann faces: unknowns with exterior cells only
+    assert oe.has_neumann() and not od.has_neumann()
+    x = _rand(oe.n(), 2) * ad
+    ye, yd = oe.apply(x), od.apply(x)
+    diff = np.abs(ye - yd)[ad]
+    assert diff.max() > 1e-3 * np.abs(yd).max()
+    # away from exterior cells (V2 rows of the Dirichlet labelling) the rows agree
+    v2 = ad & ~vd
+    assert np.max(np.abs(ye - yd)[v2]) <= 1e-13 * np.abs(yd).max()
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.01])
+def test_exterior_operator_symmetric(gamma):
+    # the dropped viscous terms at Neumann faces are symmetric pairs and B^T stays the transpose of B
+    n = 8
+    lab = synthetic.porous_labels(n, seed=3, nspheres=4, rmin=0.15, rmax=0.3, exterior_every=2)
+    o = oracle.Oracle(n, eta=0.7, gamma=gamma, levels=1, coarsest_max=n, labels=lab)
+    act = o.masks()[0]
+    A = _assemble(lambda e: o.apply(e, penalised=gamma > 0), o.n(), act)
+    assert np.max(np.abs(A - A.T)) <= 1e-14 * np.max(np.abs(A))
+    # the pressure has no null space once a Neumann face exists
+    assert o.has_neumann()
+    s = np.linalg.svd(A, compute_uv=False)
+    assert s[-1] > 1e-8 * s[0]
 
 
 def test_exterior_rhs_reads_dirichlet_faces_only():
+    # the data g is read on faces of Dirichlet cells only, and not across an exterior cell (a dropped term)
     n = 12
     lab = _mixed(n, 1)
-    dl = np.where(lab == 2, 1, lab).astype(np.uint8)
     oe = oracle.Oracle(n, levels=2, coarsest_max=6, labels=lab)
-    od = oracle.Oracle(n, levels=2, coarsest_max=6, labels=dl)
     f = _rand(oe.n(), 3)
     g = _rand(synthetic.ghost_len(n), 4)
-    # the same data with zeros on every face that touches no Dirichlet cell (Neumann / inactive faces)
     L = lambda i, j, k: lab[k + 1, j + 1, i + 1]
     gz, o = g.copy(), 0
     for c, (sz, sy, sx) in enumerate(_ghost_sizes(n)):
@@ -291,8 +317,116 @@ def test_exterior_rhs_reads_dirichlet_faces_only():
                     o += 1
     assert not np.array_equal(gz, g)
     be = oe.rhs(f, g)
-    assert np.max(np.abs(be - od.rhs(f, gz))) <= 1e-13 * np.max(np.abs(be))
-    assert np.max(np.abs(be - od.rhs(f, g))) > 1e-3 * np.max(np.abs(be))  # the data does differ
+    assert np.max(np.abs(be - oe.rhs(f, gz))) <= 1e-13 * np.max(np.abs(be))
+    assert np.max(np.abs(be - oe.rhs(f, np.zeros_like(g)))) > 1e-3 * np.max(np.abs(be))  # the data does enter
+
+
+def _plane_poiseuille(nx, ny, outlet, U, eta):
+    """Labels, Dirichlet data and the exact discrete solution of plane Poiseuille flow in a channel
+    along x, walls at y = 0 and y = ny h, two cell layers in z whose ghost faces carry the exact
+    velocity (so the flow is z-independent) and `outlet` exterior columns at the end.  The velocity
+    u(y) = 4 U y (H - y) / H^2 is quadratic, so the MAC second difference is exact; the pressure
+    p = G (x_e - x), G = 8 U eta / H^2, is linear and zero at x_e, the centre of the first exterior
+    cell (the do-nothing condition sets the exterior pressure to 0)."""
+    nz = 2
+    h = 1.0 / ny
+    H = ny * h
+    lab = synthetic.channel_labels(nx, ny, nz, outlet=outlet)
+    prof = lambda y: 4.0 * U * y * (H - y) / H ** 2
+    # ghost-extended u data: every u face (walls, ghosts in y and z) carries the exact profile
+    yg = (np.arange(-1, ny + 1) + 0.5) * h
+    ug = np.broadcast_to(prof(yg)[None, :, None], (nz + 2, ny + 2, nx + 1)).copy()
+    ug[:, :, 1 + nx - outlet:] = 0.0  # beyond the outflow face nothing is prescribed
+    g = np.concatenate([ug.reshape(-1), np.zeros((nz + 2) * (ny + 1) * (nx + 2)),
+                        np.zeros((nz + 1) * (ny + 2) * (nx + 2))])
+    xe = (nx - outlet + 0.5) * h
+    G = 8.0 * U * eta / H ** 2
+    yc = (np.arange(ny) + 0.5) * h
+    ue = np.zeros((nz, ny, nx + 1))
+    ue[:, :, 1:nx - outlet + 1] = prof(yc)[None, :, None]  # unknown faces up to the outflow face
+    pe = np.zeros((nz, ny, nx))
+    xc = (np.arange(nx) + 0.5) * h
+    pe[:, :, :nx - outlet] = G * (xe - xc[:nx - outlet])[None, None, :]
+    exact = np.concatenate([ue.reshape(-1), np.zeros(nx * (ny + 1) * nz), np.zeros(nx * ny * (nz + 1)),
+                            pe.reshape(-1)])
+    return lab, g, exact, h
+
+
+@pytest.mark.parametrize("eta", [1.0, 1e-3])
+def test_plane_poiseuille_through_an_exterior_outlet_is_exact(eta):
+    # Sec. 7 channel flows: a homogeneous Neumann condition on the outflow lets the fully developed
+    # profile leave the domain unchanged; the discrete solution is the exact Poiseuille flow (quadratic
+    # velocity, linear pressure), with no data at the outlet
+    nx, ny, outlet = 16, 8, 2
+    lab, g, exact, h = _plane_poiseuille(nx, ny, outlet, U=1.0, eta=eta)
+    o = oracle.Oracle(nx, ny, 2, h=h, eta=eta, levels=2, coarsest_max=8, labels=lab)
+    assert o.has_neumann()
+    act = o.masks()[0]
+    b = o.rhs(None, g)
+    x, rc, it, rr, _ = o.sqmr(b, tol=1e-13, maxit=200)
+    assert rc == 0 and rr < 1e-13, (rc, it, rr)
+    assert np.max(np.abs((x - exact)[act])) <= 1e-9 * np.max(np.abs(exact))
+    # flux balance: what enters at x = 0 leaves through the Neumann faces of the outflow
+    u = x[:(nx + 1) * ny * 2].reshape(2, ny, nx + 1)
+    inflow = g[:(nx + 1) * (ny + 2) * 4].reshape(4, ny + 2, nx + 1)[1:-1, 1:-1, 0].sum()
+    assert abs(u[:, :, nx - outlet].sum() - inflow) <= 1e-10 * inflow
+
+
+def test_exterior_outlet_differs_from_a_closed_end():
+    # the same channel with Dirichlet (closed) cells at the end cannot carry the inflow: its solve has
+    # no solution with nonzero net inflow (continuity), while the exterior outlet carries all of it
+    nx, ny, outlet = 16, 8, 2
+    lab, g, exact, h = _plane_poiseuille(nx, ny, outlet, U=1.0, eta=1.0)
+    closed = np.where(lab == 2, 1, lab).astype(np.uint8)
+    oc = oracle.Oracle(nx, ny, 2, h=h, levels=2, coarsest_max=8, labels=closed)
+    gc = g.copy()
+    gu = gc[:(nx + 1) * (ny + 2) * 4].reshape(4, ny + 2, nx + 1)
+    gu[:, :, nx - outlet:] = 0.0  # no-slip data on the closed end
+    bc = oc.rhs(None, gc)
+    act = oc.masks()[0]
+    npc = nx * ny * 2
+    # sum of the continuity right-hand side = net inflow / h: nonzero, so L x = b is inconsistent
+    assert abs(bc[-npc:][act[-npc:]].sum()) > 1.0
+
+
+def test_duct_outflow_converges_with_flux_balance_and_symmetry():
+    # 3D stand-in of the Sec. 7 cylinder example: a square duct with a z-aligned cylinder, the duct
+    # inflow profile at x = 0 and an exterior outlet; MG-SQMR converges, the outflow carries the
+    # inflow's flux, and the flow is mirror-symmetric in z (the geometry and data are)
+    nx, ny, nz = 32, 16, 16
+    lab = synthetic.channel_labels(nx, ny, nz, outlet=4, cylinder=(8.0, 8.0, 2.5))
+    g = synthetic.channel_inflow(nx, ny, nz, labels=lab).numpy()
+    o = oracle.Oracle(nx, ny, nz, h=1.0 / ny, eta=1e-3, gamma=1e-3, kb=2, coarsest_max=4, labels=lab)
+    b = o.rhs(None, g)
+    x, rc, it, rr, _ = o.sqmr(b, tol=1e-10, maxit=200)
+    assert rc == 0 and rr < 1e-10, (rc, it, rr)
+    u, v, w, p = synthetic.unpack(x, nx, ny, nz)
+    gu = g[:(nx + 1) * (ny + 2) * (nz + 2)].reshape(nz + 2, ny + 2, nx + 1)
+    inflow = gu[1:-1, 1:-1, 0].sum()
+    assert abs(u[:, :, nx - 4].sum() - inflow) <= 1e-8 * inflow
+    assert np.max(np.abs(u - u[::-1])) <= 1e-7 * np.max(np.abs(u))
+    assert np.max(np.abs(w + w[::-1])) <= 1e-7 * np.max(np.abs(u))
+    assert it <= 40, it
+
+
+def test_table1_cylinder_rows():
+    # Table 1 cylinder rows: with the Sec. 7 geometry, the exterior outflow column and the V1 reading,
+    # the labelled classification gives the printed total (and, in 3D, boundary) DOF counts
+    import os
+    golden = os.path.join(os.path.dirname(__file__), "golden", "table1_cylinder.txt")
+    rows = [l for l in open(golden) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 5
+    for row in rows:
+        parts = [p.strip() for p in row.split(",")]
+        nx, ny, nz = map(int, parts[1:4])
+        h, cx, cy, r = map(float, parts[4:8])
+        total, boundary = int(parts[8]), int(parts[9])
+        # nx interior columns plus one exterior column beyond the outflow face
+        lab = synthetic.channel_labels(nx + 1, ny, nz, outlet=1, cylinder=(cx / h, cy / h, r / h))
+        na, nv = oracle.count_dofs(nx + 1, ny, nz, lab)
+        assert na == total, (parts[0], na, total)
+        if boundary >= 0:
+            assert nv == boundary, (parts[0], nv, boundary)
 
 
 @pytest.mark.parametrize("kind,coarse_p_active", [(2, True), (1, False)])
@@ -327,13 +461,12 @@ def test_exterior_sqmr_matches_direct_solve():
     o = oracle.Oracle(n, levels=2, coarsest_max=4, labels=lab)
     act = o.masks()[0].astype(bool)
     pact = act[-n ** 3:]
+    assert o.has_neumann()  # Neumann faces fix the pressure level: L is nonsingular, no mean to remove
     b = _rand(o.n(), 13) * act
-    b[-n ** 3:][pact] -= b[-n ** 3:][pact].mean()
     x, rc, it, rr, _ = o.sqmr(b, tol=1e-13, maxit=300)
     assert rc == 0 and rr < 1e-13
     cols = np.nonzero(act)[0]
-    ref = np.linalg.lstsq(_assemble(o.apply, o.n(), act), b[cols], rcond=None)[0]
-    ref[-int(pact.sum()):] -= ref[-int(pact.sum()):].mean()
+    ref = np.linalg.solve(_assemble(o.apply, o.n(), act), b[cols])
     assert np.max(np.abs(x[cols] - ref)) <= 1e-9 * np.max(np.abs(ref))
 
 
