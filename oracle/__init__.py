@@ -23,11 +23,11 @@ OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_UNSUPPORTED, ERR_SIN
 
 
 def build(force=False):
-    """Compile the oracle with gcc (plain -O2, single-threaded)."""
+    """Compile the oracle with gcc (plain -O2; OpenMP for the order-free loops, one thread by default)."""
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + ".tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -53,6 +53,7 @@ def _load():
         "og_destroy": (None, [vp]),
         "og_nlevels": (ctypes.c_int, [vp]),
         "og_has_neumann": (ctypes.c_int, [vp]),
+        "og_set_threads": (ctypes.c_int, [ctypes.c_int]),
         "og_level_n": (ctypes.c_long, [vp, ctypes.c_int]),
         "og_level_dims": (None, [vp, ctypes.c_int, _i]),
         "og_level_masks": (None, [vp, ctypes.c_int, _u8, _u8]),
@@ -85,6 +86,12 @@ def _load():
 def _dp(a):
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(_d)
+
+
+def set_threads(n):
+    """Threads of the oracle's order-free loops (operator rows, prolongation, one Vanka colour's patch
+    corrections); results are bit-identical for every count.  Returns the count in effect."""
+    return _load().og_set_threads(int(n))
 
 
 def auto_levels(nx, ny, nz, coarsest_max=8):

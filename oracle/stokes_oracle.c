@@ -8,7 +8,11 @@
  *
  * Everything here is written to be checked against the paper by eye: one degree of
  * freedom (DOF) at a time, one row of the operator at a time, sequential loops, no
- * blocking, fusion or reordering beyond what the paper's algorithms state.
+ * blocking, fusion or reordering beyond what the paper's algorithms state.  Loops whose
+ * iterations are independent (operator rows, prolongation rows, the patch corrections of one
+ * Vanka colour, computed from the pre-colour state) may run on several OpenMP threads
+ * (og_set_threads); every result is the same, bit for bit, for any thread count.  The DGS
+ * sweeps, scatters and every reduction stay sequential.
  *
  *   discretisation ............ Sec. 2, Eq. (2); penalised operator L~ in Sec. 4
  *   cell labels / DOF classes . Sec. 5
@@ -53,6 +57,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define LAB_INTERIOR 0
 #define LAB_DIRICHLET 1
@@ -77,10 +84,12 @@ typedef struct {
     int neumann;            /* some unknown face borders an exterior cell (no pressure null space) */
     long *order;            /* DGS traversal order of the V2 DOFs */
     long norder;
+    long gstart[11];        /* order[gstart[g] .. gstart[g+1]) = group g: velocity parities 0, 1, pressure colours 0..7 */
     double *dgs_d;          /* d_j = L~_j . M_{.j} per packed entry (V2 entries only) */
     long *vcell[8];         /* V1 cells (linear cell index) per colour */
     long nvcell[8];
     double *scratch;        /* zero vector, used to evaluate single matrix entries */
+    double **tzero;         /* per-thread zero vectors of the threaded Vanka loops (thread >= 1) */
     double *x, *b, *r;      /* per-level work vectors */
     /* coarsest level only: dense LU of L~ on the active DOFs */
     long nc;
@@ -96,6 +105,10 @@ typedef struct {
     int cycle;    /* coarse-grid visits per level: 1 V-cycle (Alg. 1), 2 W-cycle (Sec. 8.2) */
     og_level *lev;
 } og_hier;
+
+/* threads of the order-free loops (1 = sequential) */
+static int og_threads = 1;
+static inline int nthreads(void) { return og_threads; }
 
 /* ------------------------------------------------------------------------------------ */
 /* index helpers                                                                         */
@@ -201,15 +214,26 @@ static double og_row(const og_level *L, long q, const double *x, double gam) {
 
 /* y = L x (gam = 0) or L~ x on the active rows; every other entry of y is 0 */
 static void og_apply_level(const og_level *L, const double *x, double *y, double gam) {
+#pragma omp parallel for schedule(static) num_threads(nthreads())
     for (long q = 0; q < L->n; ++q) y[q] = L->active[q] ? og_row(L, q, x, gam) : 0.0;
 }
 
-/* single matrix entry L~_{a,b}, evaluated as row a applied to the unit vector e_b */
-static double og_entry(og_level *L, long a, long b, double gam) {
-    L->scratch[b] = 1.0;
-    double v = og_row(L, a, L->scratch, gam);
-    L->scratch[b] = 0.0;
+/* single matrix entry L~_{a,b}, evaluated as row a applied to the unit vector e_b held in a zero
+ * vector z (the level's own, or one per thread) */
+static double og_entry_z(const og_level *L, double *z, long a, long b, double gam) {
+    z[b] = 1.0;
+    double v = og_row(L, a, z, gam);
+    z[b] = 0.0;
     return v;
+}
+static double og_entry(og_level *L, long a, long b, double gam) { return og_entry_z(L, L->scratch, a, b, gam); }
+
+/* zero vector of the level for thread t (t = 0: the level's own scratch), allocated on first use */
+static double *thread_zero(og_level *L, int t) {
+    if (t == 0) return L->scratch;
+    if (!L->tzero) L->tzero = (double **)calloc(64, sizeof(double *));
+    if (!L->tzero[t]) L->tzero[t] = (double *)calloc(L->n, sizeof(double));
+    return L->tzero[t];
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -292,28 +316,56 @@ static int og_mcol(const og_level *L, long q, long *idx, double *val) {
     return m;
 }
 
-/* Alg. 2, forward sweep over the V2 rows: x <- x + (b_j - L~_j x)/d_j M_{.j} in traversal order */
+/* Alg. 2, forward sweep over the V2 rows: x <- x + (b_j - L~_j x)/d_j M_{.j} in traversal order.
+ * The order is a sequence of groups (V2 velocities of one parity of i+j+k, then V2 pressures of one
+ * colour); the DOFs of one group are decoupled in L~M, so a DOF's residual does not read what the
+ * updates of its own group write.  With several threads the residuals of a group are therefore
+ * computed first, in parallel, and the updates then applied in traversal order: the same numbers, in
+ * the same order, as the one-DOF-at-a-time loop. */
 static void og_dgs_forward(og_level *L, double *x, const double *b) {
     long idx[16]; double val[16];
-    for (long t = 0; t < L->norder; ++t) {
-        long q = L->order[t];
-        double r = b[q] - og_row(L, q, x, L->gamma);
-        double delta = r / L->dgs_d[q];
-        int m = og_mcol(L, q, idx, val);
-        for (int u = 0; u < m; ++u) x[idx[u]] += delta * val[u];
+    if (nthreads() == 1) {
+        for (long t = 0; t < L->norder; ++t) {
+            long q = L->order[t];
+            double r = b[q] - og_row(L, q, x, L->gamma);
+            double delta = r / L->dgs_d[q];
+            int m = og_mcol(L, q, idx, val);
+            for (int u = 0; u < m; ++u) x[idx[u]] += delta * val[u];
+        }
+        return;
     }
+    double *delta = (double *)malloc(sizeof(double) * (L->norder + 1));
+    for (int g = 0; g < 10; ++g) {
+        long t0 = L->gstart[g], t1 = L->gstart[g + 1];
+#pragma omp parallel for schedule(static) num_threads(nthreads())
+        for (long t = t0; t < t1; ++t) {
+            long q = L->order[t];
+            delta[t] = (b[q] - og_row(L, q, x, L->gamma)) / L->dgs_d[q];
+        }
+        for (long t = t0; t < t1; ++t) {
+            int m = og_mcol(L, L->order[t], idx, val);
+            for (int u = 0; u < m; ++u) x[idx[u]] += delta[t] * val[u];
+        }
+    }
+    free(delta);
 }
 
 /* Eq. (ldist) / Eq. (SDGS), backward sweep: Gauss-Seidel on M^T L~ x = M^T b in exactly the
- * reverse order, x_j <- x_j + M_{.j}^T (b - L~ x) / d_j  (the update x + G~^{-T} M^T (b - L~ x)) */
+ * reverse order, x_j <- x_j + M_{.j}^T (b - L~ x) / d_j  (the update x + G~^{-T} M^T (b - L~ x)).
+ * Each update changes x_j alone, and within a group no DOF reads another's x_j: a group's updates
+ * are independent and may run in parallel. */
 static void og_dgs_backward(og_level *L, double *x, const double *b) {
-    long idx[16]; double val[16];
-    for (long t = L->norder - 1; t >= 0; --t) {
-        long q = L->order[t];
-        int m = og_mcol(L, q, idx, val);
-        double s = 0.0;
-        for (int u = 0; u < m; ++u) s += val[u] * (b[idx[u]] - og_row(L, idx[u], x, L->gamma));
-        x[q] += s / L->dgs_d[q];
+    for (int g = 9; g >= 0; --g) {
+        long t0 = L->gstart[g], t1 = L->gstart[g + 1];
+#pragma omp parallel for schedule(static) num_threads(nthreads())
+        for (long t = t1 - 1; t >= t0; --t) {
+            long idx[16]; double val[16];
+            long q = L->order[t];
+            int m = og_mcol(L, q, idx, val);
+            double s = 0.0;
+            for (int u = 0; u < m; ++u) s += val[u] * (b[idx[u]] - og_row(L, idx[u], x, L->gamma));
+            x[q] += s / L->dgs_d[q];
+        }
     }
 }
 
@@ -332,6 +384,41 @@ static int og_patch(const og_level *L, int i, int j, int k, long *dofs) {
     return m;
 }
 
+/* Sec. 3.2: correction of the patch of V1 cell cl, (C L~ C^T)^{-1} C (b - L~ x), from the state x;
+ * the local matrix is built entry by entry (z: a zero vector) and solved by Gaussian elimination.
+ * D receives the patch's DOFs; returns their number. */
+static int og_patch_correction(const og_level *L, double *z, const double *x, const double *b, long cl, long *D,
+                               double *corr) {
+    int i = (int)(cl % L->nx), j = (int)((cl / L->nx) % L->ny), k = (int)(cl / ((long)L->nx * L->ny));
+    int m = og_patch(L, i, j, k, D);
+    double K[49], rl[7];
+    long piv[7];
+    for (int a = 0; a < m; ++a) {
+        rl[a] = b[D[a]] - og_row(L, D[a], x, L->gamma);
+        for (int bb = 0; bb < m; ++bb) K[a * m + bb] = og_entry_z(L, z, D[a], D[bb], L->gamma);
+    }
+    og_lu(m, K, piv);
+    og_lu_solve(m, K, piv, rl);
+    for (int a = 0; a < m; ++a) corr[a] = rl[a];
+    return m;
+}
+
+/* patch corrections of cells[0..ncell) from the same state x (independent: threads may share them) */
+static void og_patch_corrections(og_level *L, const double *x, const double *b, const long *cells, long ncell,
+                                 long *dofs, int *nd, double *corr) {
+    int nt = nthreads();
+    for (int t = 1; t < nt; ++t) thread_zero(L, t);
+#pragma omp parallel for schedule(static) num_threads(nt)
+    for (long t = 0; t < ncell; ++t) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        nd[t] = og_patch_correction(L, tid == 0 ? L->scratch : L->tzero[tid], x, b, cells[t], dofs + 7 * t,
+                                    corr + 7 * t);
+    }
+}
+
 /* one colour of the multiplicative Vanka sweep: every patch correction
  * x_D += (C_D L~ C_D^T)^{-1} C_D (b - L~ x) is computed from the state before the colour */
 static void og_vanka_colour(og_level *L, double *x, const double *b, int col) {
@@ -340,22 +427,7 @@ static void og_vanka_colour(og_level *L, double *x, const double *b, int col) {
     long *dofs = (long *)malloc(sizeof(long) * 7 * ncell);
     int *nd = (int *)malloc(sizeof(int) * ncell);
     double *corr = (double *)malloc(sizeof(double) * 7 * ncell);
-    for (long t = 0; t < ncell; ++t) {
-        long cl = L->vcell[col][t];
-        int i = (int)(cl % L->nx), j = (int)((cl / L->nx) % L->ny), k = (int)(cl / ((long)L->nx * L->ny));
-        long *D = dofs + 7 * t;
-        int m = og_patch(L, i, j, k, D);
-        nd[t] = m;
-        double K[49], rl[7];
-        long piv[7];
-        for (int a = 0; a < m; ++a) {
-            rl[a] = b[D[a]] - og_row(L, D[a], x, L->gamma);
-            for (int bb = 0; bb < m; ++bb) K[a * m + bb] = og_entry(L, D[a], D[bb], L->gamma);
-        }
-        og_lu(m, K, piv);
-        og_lu_solve(m, K, piv, rl);
-        for (int a = 0; a < m; ++a) corr[7 * t + a] = rl[a];
-    }
+    og_patch_corrections(L, x, b, L->vcell[col], ncell, dofs, nd, corr);
     for (long t = 0; t < ncell; ++t)
         for (int a = 0; a < nd[t]; ++a) x[dofs[7 * t + a]] += corr[7 * t + a];
     free(dofs); free(nd); free(corr);
@@ -375,23 +447,10 @@ static void og_vanka_additive(og_level *L, double *x, const double *b) {
     int *nd = (int *)malloc(sizeof(int) * ntot);
     double *corr = (double *)malloc(sizeof(double) * 7 * ntot);
     long t = 0;
-    for (int col = 0; col < 8; ++col)
-        for (long u = 0; u < L->nvcell[col]; ++u, ++t) {
-            long cl = L->vcell[col][u];
-            int i = (int)(cl % L->nx), j = (int)((cl / L->nx) % L->ny), k = (int)(cl / ((long)L->nx * L->ny));
-            long *D = dofs + 7 * t;
-            int m = og_patch(L, i, j, k, D);
-            nd[t] = m;
-            double K[49], rl[7];
-            long piv[7];
-            for (int a = 0; a < m; ++a) {
-                rl[a] = b[D[a]] - og_row(L, D[a], x, L->gamma);
-                for (int bb = 0; bb < m; ++bb) K[a * m + bb] = og_entry(L, D[a], D[bb], L->gamma);
-            }
-            og_lu(m, K, piv);
-            og_lu_solve(m, K, piv, rl);
-            for (int a = 0; a < m; ++a) corr[7 * t + a] = rl[a];
-        }
+    for (int col = 0; col < 8; ++col) {
+        og_patch_corrections(L, x, b, L->vcell[col], L->nvcell[col], dofs + 7 * t, nd + t, corr + 7 * t);
+        t += L->nvcell[col];
+    }
     for (t = 0; t < ntot; ++t)
         for (int a = 0; a < nd[t]; ++a) x[dofs[7 * t + a]] += OG_ADDITIVE_DAMPING * corr[7 * t + a];
     free(dofs); free(nd); free(corr);
@@ -421,6 +480,7 @@ static void og_dwj_step(og_level *L, double *x, const double *b, int pressure, i
     long idx[16]; double val[16];
     double *r = (double *)malloc(sizeof(double) * L->n);
     double *dx = (double *)calloc(L->n, sizeof(double));
+#pragma omp parallel for schedule(static) num_threads(nthreads())
     for (long q = 0; q < L->n; ++q) r[q] = L->active[q] ? b[q] - og_row(L, q, x, L->gamma) : 0.0;
     for (long t = 0; t < L->norder; ++t) {
         long q = L->order[t];
@@ -504,10 +564,11 @@ static void og_restrict(const og_level *F, const og_level *C, const double *rf, 
     }
 }
 
-/* xf += P ec */
+/* xf += P ec (rows independent) */
 static void og_prolong_add(const og_level *F, const og_level *C, const double *ec, double *xf) {
-    long cq[8]; double w[8];
+#pragma omp parallel for schedule(static) num_threads(nthreads())
     for (long q = 0; q < F->n; ++q) {
+        long cq[8]; double w[8];
         if (!F->active[q]) continue;
         int m = og_pweights(F, C, q, cq, w);
         double s = 0.0;
@@ -550,6 +611,10 @@ static void og_vcycle_level(og_hier *H, int l, const double *b, double *x) { og_
 static void level_free(og_level *L) {
     free(L->lab); free(L->active); free(L->v1); free(L->order); free(L->dgs_d);
     for (int c = 0; c < 8; ++c) free(L->vcell[c]);
+    if (L->tzero) {
+        for (int t = 0; t < 64; ++t) free(L->tzero[t]);
+        free(L->tzero);
+    }
     free(L->scratch); free(L->x); free(L->b); free(L->r);
     free(L->cidx); free(L->lu); free(L->piv);
     memset(L, 0, sizeof(*L));
@@ -640,18 +705,23 @@ static int level_init(og_level *L, int nx, int ny, int nz, double h, double eta,
      * (i mod 2) + 2 (j mod 2) + 4 (k mod 2), colours 0..7.  Inside a group the order is the
      * packed order; DOFs of one group are decoupled in L~M. */
     L->norder = 0;
-    for (int par = 0; par < 2; ++par)
+    for (int par = 0; par < 2; ++par) {
+        L->gstart[par] = L->norder;
         for (long q = 0; q < L->op; ++q) {
             int c, i, j, k;
             decode(L, q, &c, &i, &j, &k);
             if (L->active[q] && !L->v1[q] && ((i + j + k) & 1) == par) L->order[L->norder++] = q;
         }
-    for (int col = 0; col < 8; ++col)
+    }
+    for (int col = 0; col < 8; ++col) {
+        L->gstart[2 + col] = L->norder;
         for (long q = L->op; q < L->n; ++q) {
             int c, i, j, k;
             decode(L, q, &c, &i, &j, &k);
             if (L->active[q] && !L->v1[q] && (i & 1) + 2 * (j & 1) + 4 * (k & 1) == col) L->order[L->norder++] = q;
         }
+    }
+    L->gstart[10] = L->norder;
     /* Alg. 2: d_j = L~_{j,} . M_{,j} (row j of L~ applied to column j of M) */
     long idx[16]; double val[16];
     for (long t = 0; t < L->norder; ++t) {
@@ -752,6 +822,16 @@ int og_create(int nx, int ny, int nz, double h, double eta, double gamma, int le
 }
 
 int og_nlevels(const og_hier *H) { return H->nlev; }
+/* threads of the order-free loops (1..64; the result does not depend on it); returns the count set */
+int og_set_threads(int n) {
+    if (n < 1) n = 1;
+    if (n > 64) n = 64;
+#ifndef _OPENMP
+    n = 1;
+#endif
+    og_threads = n;
+    return n;
+}
 int og_has_neumann(const og_hier *H) { return H->lev[0].neumann; }
 long og_level_n(const og_hier *H, int l) { return H->lev[l].n; }
 void og_level_dims(const og_hier *H, int l, int *dims) { dims[0] = H->lev[l].nx; dims[1] = H->lev[l].ny; dims[2] = H->lev[l].nz; }

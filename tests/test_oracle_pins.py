@@ -521,3 +521,30 @@ def test_pure_multigrid_converges_to_the_penalised_solution():
     assert np.max(np.abs(x[act] - ref)) <= 1e-9 * np.max(np.abs(ref))
     rates = hist[1:] / hist[:-1]
     assert np.all(rates < 0.5), rates
+
+
+# ----------------------------------------------------------------------------------------------
+# the threaded oracle (order-free loops on several OpenMP threads) is the sequential one, bit for bit
+
+
+@pytest.mark.parametrize("variant", ["", "additive", "dwj"])
+@pytest.mark.parametrize("domain", ["box", "mixed"])
+def test_threaded_oracle_is_bit_identical(domain, variant):
+    import synthetic
+    n = 16
+    lab = None if domain == "box" else synthetic.porous_labels(n, seed=2, nspheres=5, rmin=0.1, rmax=0.2,
+                                                                exterior_every=2)
+    o = oracle.Oracle(n, eta=1e-3, coarsest_max=8, labels=lab, additive=variant == "additive",
+                      dwj=variant == "dwj")
+    act = o.masks()[0]
+    b = np.random.default_rng(3).standard_normal(o.n()) * act
+    outs = []
+    try:
+        for th in (1, 4):
+            oracle.set_threads(th)
+            x, rc, it, rr, _ = o.sqmr(b, tol=1e-30, maxit=3, fixed_iters=3)
+            outs.append((o.vcycle(b), o.smooth(np.zeros(o.n()), b), o.apply(b), x))
+    finally:
+        oracle.set_threads(1)
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
