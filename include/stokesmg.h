@@ -70,14 +70,19 @@ typedef struct {
     /* cell labels on the ghost-extended cell grid (nx+2)(ny+2)(nz+2), x fastest, index
      * (i+1) + (nx+2)((j+1) + (ny+2)(k+1)) for cell (i,j,k), i = -1..nx: 0 interior, 1 Dirichlet,
      * 2 exterior (Sec. 5).  The ghost shell must be Dirichlet; a value above 2 or a non-Dirichlet
-     * ghost cell gives STOKES_ERR_INVALID_ARG.  Faces between two interior cells and interior-cell
-     * pressures are the unknowns; faces of Dirichlet cells carry Dirichlet data (the ghost-extended
-     * Dirichlet layout covers every face); a face between an interior and an exterior cell carries
-     * the homogeneous Neumann condition, taken as the value 0 (g is not read there); faces with no
-     * interior cell beside them are inactive.  V1 holds the unknowns of interior cells next to a
-     * non-interior cell.  Coarse labels: Dirichlet if any child is, else interior if any child is,
-     * else exterior.  NULL = the box (all interior, one Dirichlet ghost shell).  The array is copied;
-     * the caller keeps ownership. */
+     * ghost cell gives STOKES_ERR_INVALID_ARG.  Faces of Dirichlet cells carry Dirichlet data (the
+     * ghost-extended Dirichlet layout covers every face).  The unknowns are the pressures of interior
+     * cells and the faces with an interior cell on at least one side and no Dirichlet cell: faces
+     * between two interior cells, and Neumann faces between an interior and an exterior cell, whose
+     * rows carry the homogeneous Neumann (do-nothing outflow) condition -- the exterior pressure is 0
+     * and viscous terms that cross an exterior cell along the face normal, or reach a face between two
+     * exterior cells, drop out (L stays symmetric; g is not read across an exterior cell).  Faces
+     * between two exterior cells are inactive.  With a Neumann face the pressure has no null space and
+     * sqmr_solve does not shift it to zero mean.  V1 holds the unknowns of interior cells with a
+     * Dirichlet cell among their 26 neighbours or an exterior cell within two cells (Table 1 counts).
+     * Coarse labels: Dirichlet if any child is, else interior if any child is, else exterior.  NULL =
+     * the box (all interior, one Dirichlet ghost shell).  The array is copied; the caller keeps
+     * ownership. */
     const uint8_t *cell_labels;
 } stokes_bc_t;
 
@@ -235,6 +240,36 @@ int stokes_coarse_solve(stokes_t h, const double *b, double *x, void *stream);
 #define STOKES_K_COUNT 17
 int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launches_all, double *ms_level0,
                              int *launches_level0, void *stream);
+
+/* ---- diagnostics: the bounded device wait ----
+ * Runs one cooperative symmetric Vanka sweep on `level` (0 <= level < levels-1) whose grid barrier
+ * waits for `missing_blocks` more thread blocks than the launch has, giving up after `spin_limit`
+ * polls per wait (1 .. 2^22; the solver's own sweeps use 2^22): with missing_blocks > 0 no wait can
+ * complete, every block gives up, and the call returns STOKES_ERR_TIMEOUT with the GPU context intact;
+ * with missing_blocks = 0 the sweep runs normally and the call returns STOKES_OK.  Exercises the
+ * failure path of the persistent Vanka schedule without faulting or hanging the GPU.  Overwrites the
+ * level's work vectors (they are zeroed before and after); synchronises `stream`.  Returns
+ * STOKES_ERR_UNSUPPORTED if the device has no cooperative launch.  No counterpart in the paper. */
+int stokes_test_grid_barrier(stokes_t h, int level, int missing_blocks, int spin_limit, void *stream);
+
+/* ---- diagnostics: host-side classification of a labelled domain (no GPU needed) ----
+ * flags[q] for every packed entry q of level `level` (n = that level's packed length; the labels are
+ * coarsened per Sec. 5): bit 0 unknown, bit 1 V2 entry (an unknown that is not in the Vanka set V1),
+ * bit 2 face of a Dirichlet cell, bits 3-5 the number of viscous terms of a face row that drop out next
+ * to exterior cells, bit 6 / bit 7 the low / high neighbour along the face normal is one of them.
+ * These are the flags the kernels read.  Labels and grid as in stokes_create; returns
+ * STOKES_ERR_INVALID_ARG for invalid labels, a level the grid cannot coarsen to, or a wrong n. */
+int stokes_label_flags(const stokes_grid_t *grid, const stokes_bc_t *bc, int level, uint8_t *flags, long long n);
+
+/* ---- diagnostics: measured FMA rate of the CUDA cores ----
+ * *flops_per_s = the fused multiply-add rate (2 flops per FMA) this GPU sustains in FP64 (fp64 != 0)
+ * or FP32, measured on the current device with a grid of independent FMA chains (best of 5 timed
+ * launches on `stream`, which is synchronised).  The FP64 figure is the roof of the FP64 kernels of
+ * the path (operator apply and SQMR recurrences of Alg. 4), which are bound by the FP64 pipe, not
+ * by memory.  A measurement aid with no counterpart in the paper; allocates and frees one small
+ * device buffer.  Returns STOKES_ERR_INVALID_ARG for a NULL output, STOKES_ERR_CUDA / _OOM on a
+ * CUDA failure. */
+int stokes_measure_fma_peak(int fp64, double *flops_per_s, void *stream);
 
 /* ---- allocation-free residual norm ----
  * *out = ||b - L x||_2 on an nx x ny x nz box (cell size h, <= 0 selects 1/nx; viscosity eta),

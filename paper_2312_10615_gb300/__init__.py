@@ -26,7 +26,7 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
            "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
            "stokes_set_level_schedule", "sqmr_solve_unpreconditioned", "mg_solve",
-           "stokes_strerror",
+           "stokes_measure_fma_peak", "stokes_label_flags", "stokes_test_grid_barrier", "stokes_strerror",
            # learned initial guess (include/warmstart.h)
            "warmstart_num_weights", "warmstart_create", "warmstart_destroy", "warmstart_set_scale",
            "warmstart_set_weights", "warmstart_get_weights", "warmstart_predict", "warmstart_loss_grad",
@@ -91,6 +91,10 @@ def _load():
         "stokes_profile_iteration": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d),
                                          ctypes.POINTER(i), vp]),
         "stokes_residual_norm_noalloc": (i, [i, i, i, d, d, vp, vp, vp, vp]),
+        "stokes_measure_fma_peak": (i, [i, ctypes.POINTER(d), vp]),
+        "stokes_test_grid_barrier": (i, [vp, i, i, i, vp]),
+        "stokes_label_flags": (i, [ctypes.POINTER(stokes_grid_t), ctypes.POINTER(stokes_bc_t), i,
+                                   ctypes.POINTER(ctypes.c_uint8), ll]),
         "sqmr_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,
                                  ctypes.POINTER(sqmr_info_t), ctypes.POINTER(d), i]),
         "stokes_level_schedule": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
@@ -177,7 +181,7 @@ def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest
                   precision=PREC_FP64, use_graphs=True, vanka_persistent=False, autotune=True, additive=False, cycle=1,
                   dwj=False, labels=None):
     """labels: None (the box) or a uint8 array of (nx+2)(ny+2)(nz+2) cell labels, x fastest (0 interior,
-    1 Dirichlet); it is copied by the library."""
+    1 Dirichlet, 2 exterior); it is copied by the library."""
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     g = stokes_grid_t(nx, ny, nz, h, levels, coarsest_max)
@@ -194,6 +198,28 @@ def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest
     _check(lib().stokes_create(ctypes.byref(g), None if bc is None else ctypes.byref(bc), viscosity,
                                ctypes.byref(o), ctypes.byref(hdl)), "stokes_create")
     return hdl
+
+
+def stokes_label_flags(labels, nx, ny=None, nz=None, level=0):
+    """Per-entry flags of a labelled domain on one level, computed by the library's host code (no GPU):
+    bit 0 unknown, bit 1 V2, bit 2 Dirichlet face, bits 3-5 dropped terms, bits 6/7 dropped normal
+    neighbours (see include/stokesmg.h)."""
+    import numpy as np
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8).reshape(-1))
+    if lab.size != (nx + 2) * (ny + 2) * (nz + 2):
+        raise ValueError("labels must hold (nx+2)(ny+2)(nz+2) entries")
+    g = stokes_grid_t(nx, ny, nz, 0.0, 0, 8)
+    bc = stokes_bc_t(lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    m = [nx, ny, nz]
+    for _ in range(level):
+        m = [a // 2 for a in m]
+    n = (m[0] + 1) * m[1] * m[2] + m[0] * (m[1] + 1) * m[2] + m[0] * m[1] * (m[2] + 1) + m[0] * m[1] * m[2]
+    out = np.zeros(n, np.uint8)
+    _check(lib().stokes_label_flags(ctypes.byref(g), ctypes.byref(bc), level,
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n), "stokes_label_flags")
+    return out
 
 
 def stokes_destroy(h):
@@ -285,6 +311,19 @@ def stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, b, x, out, stream=Non
         raise StokesError(ERR_INVALID_ARG, "stokes_residual_norm_noalloc: out holds no entry")
     _check(lib().stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, _ptr(b), _ptr(x), _ptr(out),
                                               _stream(stream)), "stokes_residual_norm_noalloc")
+
+
+def stokes_test_grid_barrier(h, level, missing_blocks, spin_limit, stream=None):
+    """Status of one cooperative Vanka sweep whose barrier waits for missing_blocks extra blocks
+    (STOKES_ERR_TIMEOUT expected for missing_blocks > 0); returns the raw status code."""
+    return int(lib().stokes_test_grid_barrier(h, level, missing_blocks, spin_limit, _stream(stream)))
+
+
+def stokes_measure_fma_peak(fp64=True, stream=None):
+    """Measured FMA rate of the CUDA cores in flop/s (FP64 or FP32), the roof of the FP64 kernels."""
+    r = ctypes.c_double()
+    _check(lib().stokes_measure_fma_peak(1 if fp64 else 0, ctypes.byref(r), _stream(stream)), "stokes_measure_fma_peak")
+    return r.value
 
 
 def sqmr_solve_batch(handles, rhs, xs, tol=1e-8, max_iter=200, nstreams=8, check=True):

@@ -36,7 +36,8 @@ void launch_dwj_sym(const Lev &L, T *x, const TB *b, T *t, T *delta, double w, c
 // one colour of the multiplicative Vanka sweep on V1 (compute corrections, then add them)
 // corrections scaled by w (1 for the multiplicative sweep, 1/2 for the damped additive step)
 template <class T, class TB>
-void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, int ncell, const T *kinv, T *corr,
+void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, const int *tab, int ncell,
+                          const T *kinv, T *corr,
                           int cap, double w, cudaStream_t s);
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s);
@@ -50,11 +51,15 @@ struct GridBarrier {
 constexpr unsigned kBarrierSpinLimit = 1u << 22;
 struct VankaLists {
     const int *cells[8];
+    const int *tab[8];  // per-cell inverse-table entries (label domains with exterior cells), else nullptr
     int count[8];
 };
+// missing_blocks > 0 (bounded-wait self-test only): the barrier waits for that many blocks more than the
+// grid has, so every wait runs out after spin_limit polls and sets bar->err
 template <class T, class TB>
 void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
-                        int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s);
+                        int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s, int missing_blocks = 0,
+                        unsigned spin_limit = kBarrierSpinLimit);
 template <class T, class TB> int vanka_sweep_blocks_per_sm();
 // one symmetric Vanka sweep (x sweeps) in a single thread-block cluster of `cluster` CTAs x 1024
 // threads separated by hardware cluster barriers (no software wait); returns the launch status

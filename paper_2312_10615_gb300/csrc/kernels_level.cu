@@ -83,14 +83,27 @@ template <class T, int C, bool P, class IDX>
 __device__ __forceinline__ T row_at(const T *__restrict__ x, const Lev &L, int i, int j, int k, const Coef<T> &K) {
     if constexpr (C < 3) {
         const IDX sy = (IDX)(L.nx + (C == 0)), sz = sy * (IDX)(L.ny + (C == 1));
-        const T *xc = x + L.off[C] + ((IDX)i + sy * (IDX)j + sz * (IDX)k);
-        T s = T(6) * xc[0];
-        if (C == 0) s -= xc[-1] + xc[1];
-        else s -= (i > 0 ? xc[-1] : T(0)) + (i < L.nx - 1 ? xc[1] : T(0));
-        if (C == 1) s -= xc[-sy] + xc[sy];
-        else s -= (j > 0 ? xc[-sy] : T(0)) + (j < L.ny - 1 ? xc[sy] : T(0));
-        if (C == 2) s -= xc[-sz] + xc[sz];
-        else s -= (k > 0 ? xc[-sz] : T(0)) + (k < L.nz - 1 ? xc[sz] : T(0));
+        const IDX o = (IDX)i + sy * (IDX)j + sz * (IDX)k;
+        const T *xc = x + L.off[C] + o;
+        T s;
+        if (!L.flags) {
+            s = T(6) * xc[0];
+            if (C == 0) s -= xc[-1] + xc[1];
+            else s -= (i > 0 ? xc[-1] : T(0)) + (i < L.nx - 1 ? xc[1] : T(0));
+            if (C == 1) s -= xc[-sy] + xc[sy];
+            else s -= (j > 0 ? xc[-sy] : T(0)) + (j < L.ny - 1 ? xc[sy] : T(0));
+            if (C == 2) s -= xc[-sz] + xc[sz];
+            else s -= (k > 0 ? xc[-sz] : T(0)) + (k < L.nz - 1 ? xc[sz] : T(0));
+        } else {
+            // label domains: the dropped viscous terms of a face next to exterior cells (Sec. 5 reading)
+            const uint8_t f = L.flags[L.off[C] + o];
+            const IDX sn = C == 0 ? (IDX)1 : (C == 1 ? sy : sz);
+            s = diag_weight<T>(f) * xc[0];
+            s -= ((f & kFlagDropLo) ? T(0) : xc[-sn]) + ((f & kFlagDropHi) ? T(0) : xc[sn]);
+            if (C != 0) s -= (i > 0 ? xc[-1] : T(0)) + (i < L.nx - 1 ? xc[1] : T(0));
+            if (C != 1) s -= (j > 0 ? xc[-sy] : T(0)) + (j < L.ny - 1 ? xc[sy] : T(0));
+            if (C != 2) s -= (k > 0 ? xc[-sz] : T(0)) + (k < L.nz - 1 ? xc[sz] : T(0));
+        }
         if constexpr (!P) {
             return K.eh2 * s;
         } else {
@@ -184,7 +197,10 @@ __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__rest
     if (g) {
         if (c < 3) {
             const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+            // a term that drops out (across an exterior cell along the normal) reads no data
+            const uint8_t fq = L.flags ? L.flags[q] : (uint8_t)0;
             for (int m = 0; m < 6; ++m) {
+                if ((m == 2 * c && (fq & kFlagDropLo)) || (m == 2 * c + 1 && (fq & kFlagDropHi))) continue;
                 int a = i + di[m], bb = j + dj[m], cc = k + dk[m];
                 if (!unknown(L, c, a, bb, cc) && dirichlet_face(L, c, a, bb, cc)) v += K.eh2 * g[gidx(L, c, a, bb, cc)];
             }
@@ -827,9 +843,18 @@ __device__ __forceinline__ T vanka_face_residual(const Lev &L, const T *__restri
     const bool ym = d == 1 || fj > 0, yp = d == 1 || fj < L.ny - 1;
     const bool zm = d == 2 || fk > 0, zp = d == 2 || fk < L.nz - 1;
     T s = T(6) * xc[0];
-    s -= (xm ? xc[-1] : T(0)) + (xp ? xc[1] : T(0));
-    s -= (ym ? xc[-sy] : T(0)) + (yp ? xc[sy] : T(0));
-    s -= (zm ? xc[-sz] : T(0)) + (zp ? xc[sz] : T(0));
+    T xl = xm ? xc[-1] : T(0), xh = xp ? xc[1] : T(0), yl = ym ? xc[-sy] : T(0), yh = yp ? xc[sy] : T(0);
+    T zl = zm ? xc[-sz] : T(0), zh = zp ? xc[sz] : T(0);
+    if (L.flags) {
+        // label domains: the dropped viscous terms of a face next to exterior cells (Sec. 5 reading)
+        const uint8_t f = L.flags[q];
+        s = diag_weight<T>(f) * xc[0];
+        if (f & kFlagDropLo) (d == 0 ? xl : (d == 1 ? yl : zl)) = T(0);
+        if (f & kFlagDropHi) (d == 0 ? xh : (d == 1 ? yh : zh)) = T(0);
+    }
+    s -= xl + xh;
+    s -= yl + yh;
+    s -= zl + zh;
     const T *pc = x + L.off[3] + (fi + nx * (fj + ny * fk));
     const long long ps = d == 0 ? 1 : (d == 1 ? nx : nx * ny);
     return T(ldv(b[q])) - (K.eh2 * s + K.ih * (pc[0] - pc[-ps]));
@@ -839,7 +864,7 @@ template <class T, class TB>
 __device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
                                                    int cellw, int a, unsigned gmask, const T *__restrict__ kinv,
                                                    T *__restrict__ corr, int cap, int slot, const Coef<T> &K,
-                                                   T w = T(1)) {
+                                                   T w = T(1), const int *__restrict__ tab = nullptr) {
     int i, j, k;
     unpack_cell(cellw, i, j, k);
     // which of the cell's six faces are unknowns (6-bit configuration of the pre-factorised inverses)
@@ -852,7 +877,10 @@ __device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__rest
     } else if (a == 6) {
         r = T(ldv(b[pidx(L, 3, i, j, k)])) - cell_Lx_fast(x, L, i, j, k, K);
     }
-    const T *Ki = kinv + cfg * 49 + (a < 7 ? a : 6) * 7;
+    // label domains with exterior cells: the cell's own entry of the level's inverse table (its faces'
+    // dropped terms change the local matrix); otherwise the 6-bit configuration indexes it
+    const int id = tab ? tab[slot] : cfg;
+    const T *Ki = kinv + id * 49 + (a < 7 ? a : 6) * 7;
     T s = T(0);
 #pragma unroll
     for (int bb = 0; bb < 7; ++bb) s += Ki[bb] * __shfl_sync(gmask, r, bb, 8);
@@ -884,14 +912,14 @@ __device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x
 
 template <class T, class TB>
 __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
-                                                       const int *__restrict__ cells, int ncell,
-                                                       const T *__restrict__ kinv, T *__restrict__ corr, int cap,
-                                                       Coef<T> K, T w) {
+                                                       const int *__restrict__ cells, const int *__restrict__ tab,
+                                                       int ncell, const T *__restrict__ kinv, T *__restrict__ corr,
+                                                       int cap, Coef<T> K, T w) {
     pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3;
     if (slot >= ncell) return;  // whole 8-lane groups leave together
-    vanka_compute_lane(L, x, b, cells[slot], t & 7, 0xffu << (threadIdx.x & 24), kinv, corr, cap, slot, K, w);
+    vanka_compute_lane(L, x, b, cells[slot], t & 7, 0xffu << (threadIdx.x & 24), kinv, corr, cap, slot, K, w, tab);
 }
 
 template <class T>
@@ -905,11 +933,11 @@ __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, c
 }
 
 template <class T, class TB>
-void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, int ncell, const T *kinv, T *corr,
-                          int cap, double w, cudaStream_t s) {
+void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, const int *tab, int ncell,
+                          const T *kinv, T *corr, int cap, double w, cudaStream_t s) {
     if (ncell <= 0) return;
-    launch_k(k_vanka_compute<T, TB>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, ncell, kinv, corr, cap,
-             coef<T>(L, L.gamma), T(w));
+    launch_k(k_vanka_compute<T, TB>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, tab, ncell, kinv, corr,
+             cap, coef<T>(L, L.gamma), T(w));
 }
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s) {
@@ -919,7 +947,7 @@ void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T
 
 // ---- one cooperative launch per symmetric Vanka sweep ----
 // grid-wide barrier: generation counter in global memory, bounded spin (see kernels.h)
-__device__ __forceinline__ void grid_sync(GridBarrier *bar, unsigned nblocks) {
+__device__ __forceinline__ void grid_sync(GridBarrier *bar, unsigned nblocks, unsigned spin_limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vgen = &bar->gen;
@@ -934,7 +962,7 @@ __device__ __forceinline__ void grid_sync(GridBarrier *bar, unsigned nblocks) {
             } else {
                 unsigned spins = 0;
                 while (*vgen == g && !*verr) {
-                    if (++spins > kBarrierSpinLimit) {
+                    if (++spins > spin_limit) {
                         atomicExch(&bar->err, 1);
                         break;
                     }
@@ -951,9 +979,10 @@ template <class T, class TB>
 __global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                      VankaLists lists, const T *__restrict__ kinv,
                                                      T *__restrict__ corr, int cap, Coef<T> K, int sweeps,
-                                                     GridBarrier *bar) {
+                                                     GridBarrier *bar, unsigned expect, unsigned spin_limit) {
     pdl_wait();
-    const unsigned nb = gridDim.x;
+    // blocks the barrier waits for: the grid, or more in the bounded-wait self-test (never completes)
+    const unsigned nb = expect ? expect : gridDim.x;
     const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 8: lanes keep their group
     const unsigned gmask = 0xffu << (threadIdx.x & 24);
     for (int sw = 0; sw < sweeps; ++sw)
@@ -963,11 +992,12 @@ __global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, c
             if (n == 0) continue;
             const int *cells = lists.cells[col];
             for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; (t >> 3) < n; t += stride)
-                vanka_compute_lane(L, x, b, cells[t >> 3], (int)(t & 7), gmask, kinv, corr, cap, (int)(t >> 3), K);
-            grid_sync(bar, nb);
+                vanka_compute_lane(L, x, b, cells[t >> 3], (int)(t & 7), gmask, kinv, corr, cap, (int)(t >> 3), K, T(1),
+                                   lists.tab[col]);
+            grid_sync(bar, nb, spin_limit);
             for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; (t >> 3) < n; t += stride)
                 vanka_apply_lane(L, x, cells[t >> 3], (int)(t & 7), corr, cap, (int)(t >> 3));
-            grid_sync(bar, nb);
+            grid_sync(bar, nb, spin_limit);
         }
 }
 
@@ -979,7 +1009,8 @@ template <class T, class TB> int vanka_sweep_blocks_per_sm() {
 
 template <class T, class TB>
 void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr, int cap,
-                        int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s) {
+                        int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s, int missing_blocks,
+                        unsigned spin_limit) {
     int mx = 0;
     for (int c = 0; c < 8; ++c) mx = lists.count[c] > mx ? lists.count[c] : mx;
     if (mx == 0 || sweeps <= 0) return;
@@ -995,7 +1026,9 @@ void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_vanka_sweep<T, TB>, L, x, b, lists, kinv, corr, cap, coef<T>(L, L.gamma), sweeps, bar);
+    const unsigned expect = missing_blocks > 0 ? (unsigned)(nb + missing_blocks) : 0u;
+    cudaLaunchKernelEx(&cfg, k_vanka_sweep<T, TB>, L, x, b, lists, kinv, corr, cap, coef<T>(L, L.gamma), sweeps, bar,
+                       expect, spin_limit);
 }
 
 // ---- one symmetric Vanka sweep in one thread block with the level in shared memory ----
@@ -1111,7 +1144,8 @@ __global__ void __launch_bounds__(1024) k_vanka_cluster(Lev L, T *__restrict__ x
             if (n == 0) continue;  // uniform across the cluster
             const int *cells = lists.cells[col];
             for (long long t = t0; (t >> 3) < n; t += stride)
-                vanka_compute_lane(L, x, b, cells[t >> 3], (int)(t & 7), gmask, kinv, corr, cap, (int)(t >> 3), K);
+                vanka_compute_lane(L, x, b, cells[t >> 3], (int)(t & 7), gmask, kinv, corr, cap, (int)(t >> 3), K, T(1),
+                                   lists.tab[col]);
             cluster_sync_all();
             for (long long t = t0; (t >> 3) < n; t += stride)
                 vanka_apply_lane(L, x, cells[t >> 3], (int)(t & 7), corr, cap, (int)(t >> 3));
@@ -1504,10 +1538,10 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template void launch_dgs_p_bwd<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                       \
     template bool launch_dgs_p_fwd_pair<T, TB>(const Lev &, T *, const TB *, T *, int, cudaStream_t);              \
     template bool launch_dgs_p_bwd_pair<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                   \
-    template void launch_vanka_compute<T, TB>(const Lev &, const T *, const TB *, const int *, int, const T *, T *,  \
-                                              int, double, cudaStream_t);                                           \
+    template void launch_vanka_compute<T, TB>(const Lev &, const T *, const TB *, const int *, const int *, int,   \
+                                              const T *, T *, int, double, cudaStream_t);                           \
     template void launch_vanka_sweep<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, T *, int,  \
-                                            int, GridBarrier *, int, cudaStream_t);                                 \
+                                            int, GridBarrier *, int, cudaStream_t, int, unsigned);                  \
     template cudaError_t vanka_cluster_prepare<T, TB>();                                                          \
     template bool vanka_smem_prepare<T, TB>(const Lev &, int);                                                     \
     template void launch_vanka_smem<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, int, int,   \

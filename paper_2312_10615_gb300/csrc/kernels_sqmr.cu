@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(256) k_apply_red(Lev L, const double *__restri
         for (int k = k0; k < k1; ++k) {
             Quad Q = quad_at(L, i, j, k);
             double o[4];
-            quad_eval<double, OP_APPLY>(x, L, i, j, k, Q, K, o);
+            if (L.flags) quad_eval<double, OP_APPLY, true>(x, L, i, j, k, Q, K, o);
+            else quad_eval<double, OP_APPLY, false>(x, L, i, j, k, Q, K, o);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 if (!Q.ex[c]) continue;

@@ -48,8 +48,11 @@ int dense_inverse(int n, double *A) {
 
 // Local matrix C_c L~ C_c^T of one cell for configuration cfg (bit a set = face a is an unknown;
 // faces ordered u_low, u_high, v_low, v_high, w_low, w_high, then p_c), inverted and embedded
-// into a 7x7 block with zero rows/columns for the faces that are not unknowns.
-int vanka_local_inverse(double h, double eta, double gamma, int cfg, double out[49]) {
+// into a 7x7 block with zero rows/columns for the faces that are not unknowns.  drops[a] (NULL: all
+// 0) = viscous terms that drop out of face a's row next to exterior cells: its diagonal is
+// (6 - drops[a]) eta/h^2 (the two faces of one axis are never separated by an exterior cell: the
+// cell between them is interior).
+int vanka_local_inverse(double h, double eta, double gamma, int cfg, const int *drops, double out[49]) {
     int idx[7], m = 0;
     for (int a = 0; a < 6; ++a)
         if (cfg & (1 << a)) idx[m++] = a;
@@ -62,7 +65,7 @@ int vanka_local_inverse(double h, double eta, double gamma, int cfg, double out[
             int f = a == 6 ? b : a;
             return (f & 1) ? -ih : ih;  // B_{c,f}: +1/h on the low face, -1/h on the high face
         }
-        if (a == b) return 6.0 * e2;
+        if (a == b) return (6.0 - (drops ? drops[a] : 0)) * e2;
         if ((a >> 1) == (b >> 1)) return -e2;  // the two faces of one axis are A-neighbours
         return 0.0;
     };

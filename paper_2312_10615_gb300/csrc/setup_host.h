@@ -2,5 +2,5 @@
 #pragma once
 namespace smg {
 int dense_inverse(int n, double *A);
-int vanka_local_inverse(double h, double eta, double gamma, int cfg, double out[49]);
+int vanka_local_inverse(double h, double eta, double gamma, int cfg, const int *drops, double out[49]);
 }  // namespace smg

@@ -15,6 +15,8 @@
 #include <atomic>
 #include <chrono>
 #include <map>
+
+#include <nvtx3/nvToolsExt.h>
 #include <memory>
 #include <mutex>
 #include <algorithm>
@@ -36,7 +38,9 @@ struct LevelBuf {
     void *x = nullptr, *b = nullptr, *r = nullptr, *delta = nullptr, *kinv = nullptr, *corr = nullptr;
     void *t = nullptr;  // level-size scratch of the arithmetic type (distributive weighted Jacobi)
     int *vcells[8] = {};
+    int *vtab[8] = {};  // per-cell entries of the inverse table (label domains with exterior cells only)
     int vcount[8] = {};
+    int ntab = 64;      // local inverses in kinv (64 configurations of unknown faces, plus exterior variants)
     int vcap = 0;
     VankaLists lists;
     int vmode = 0, vblocks = 0;  // Vanka schedule: 0 per-colour launches, 1 cooperative sweep of vblocks blocks,
@@ -95,15 +99,57 @@ Lev make_level(int nx, int ny, int nz, double h, double eta, double gamma) {
 struct Labels {
     int nx = 0, ny = 0, nz = 0;
     std::vector<uint8_t> lab;  // (nx+2)(ny+2)(nz+2); 0 interior, 1 Dirichlet, 2 exterior
-    uint8_t at(int i, int j, int k) const {  // i in -1..nx
-        return lab[(size_t)(i + 1) + (size_t)(nx + 2) * ((j + 1) + (size_t)(ny + 2) * (k + 1))];
+    std::vector<uint8_t> prox;  // same grid: 1 where an interior cell is proximal (V1 cell), from finish()
+    size_t lin(int i, int j, int k) const {
+        return (size_t)(i + 1) + (size_t)(nx + 2) * ((j + 1) + (size_t)(ny + 2) * (k + 1));
+    }
+    uint8_t at(int i, int j, int k) const {  // i in -1..nx; beyond the ghost shell: Dirichlet
+        if (i < -1 || j < -1 || k < -1 || i > nx || j > ny || k > nz) return 1;
+        return lab[lin(i, j, k)];
     }
     bool interior(int i, int j, int k) const { return at(i, j, k) == 0; }
     bool dirichlet(int i, int j, int k) const { return at(i, j, k) == 1; }
-    // interior cell with a non-interior face neighbour: its unknowns belong to the Vanka set V1
-    bool v1(int i, int j, int k) const {
-        return interior(i, j, k) && (!interior(i - 1, j, k) || !interior(i + 1, j, k) || !interior(i, j - 1, k) ||
-                                     !interior(i, j + 1, k) || !interior(i, j, k - 1) || !interior(i, j, k + 1));
+    bool exterior(int i, int j, int k) const { return at(i, j, k) == 2; }
+    // V1 cells (Sec. 5, "proximal"): interior cells with a Dirichlet cell among their 26 neighbours or an
+    // exterior cell within Chebyshev distance 2.  Separable dilations of the two indicator fields.
+    void finish() {
+        const int ex = nx + 2, ey = ny + 2, ez = nz + 2;
+        auto dilate = [&](std::vector<uint8_t> f, int r) {
+            std::vector<uint8_t> g(f.size());
+            const int ext[3] = {ex, ey, ez};
+            const long long str[3] = {1, (long long)ex, (long long)ex * ey};
+            for (int d = 0; d < 3; ++d) {
+                for (int k = 0; k < ez; ++k)
+                    for (int j = 0; j < ey; ++j)
+                        for (int i = 0; i < ex; ++i) {
+                            const int pos[3] = {i, j, k};
+                            const long long q = i + (long long)ex * (j + (long long)ey * k);
+                            uint8_t v = 0;
+                            for (int o = -r; o <= r && !v; ++o) {
+                                const int t = pos[d] + o;
+                                if (t >= 0 && t < ext[d]) v = f[(size_t)(q + o * str[d])];
+                            }
+                            g[(size_t)q] = v;
+                        }
+                f.swap(g);
+            }
+            return f;
+        };
+        std::vector<uint8_t> dir(lab.size()), ext2(lab.size());
+        for (size_t q = 0; q < lab.size(); ++q) {
+            dir[q] = lab[q] == 1;
+            ext2[q] = lab[q] == 2;
+        }
+        dir = dilate(dir, 1);
+        ext2 = dilate(ext2, 2);
+        prox.assign(lab.size(), 0);
+        for (size_t q = 0; q < lab.size(); ++q) prox[q] = lab[q] == 0 && (dir[q] || ext2[q]);
+    }
+    bool v1(int i, int j, int k) const { return interior(i, j, k) && prox[lin(i, j, k)]; }
+    bool any_exterior() const {
+        for (uint8_t v : lab)
+            if (v == 2) return true;
+        return false;
     }
 };
 // Sec. 5 coarsening: Dirichlet if any child is Dirichlet, else interior if any child is interior, else
@@ -124,13 +170,25 @@ Labels coarsen(const Labels &F) {
                 const uint8_t v = anyd ? 1 : (anyi ? 0 : 2);
                 C.lab[(size_t)(i + 1) + (size_t)(C.nx + 2) * ((j + 1) + (size_t)(C.ny + 2) * (k + 1))] = v;
             }
+    C.finish();
     return C;
 }
-// per packed entry: kFlagActive (a face between two interior cells, or an interior cell), kFlagV2 (a face
-// between two V2 cells, or a V2 cell) and kFlagDirichlet (a face of a Dirichlet cell: its value is data;
-// the other faces that are not unknowns border exterior cells and hold the homogeneous Neumann value 0)
+// per packed entry (Sec. 5): kFlagActive -- an unknown: an interior cell, or a face with no Dirichlet
+// cell beside it and an interior cell on at least one side (between two interior cells, or a Neumann
+// face between an interior and an exterior cell); kFlagV2 -- a face between two V2 cells, or a V2 cell;
+// kFlagDirichlet -- a face of a Dirichlet cell (its value is data).  Faces that are none of these lie
+// between two exterior cells (inactive).  For an unknown face, the viscous terms of its row that drop
+// out (the do-nothing condition): bits 3-5 count them, kFlagDropLo / kFlagDropHi mark the two neighbours
+// along the face normal whose term crosses an exterior cell (tangential drops are inactive faces,
+// which hold 0, so the count alone fixes the row).
 std::vector<uint8_t> level_flags(const Lev &L, const Labels &B) {
     std::vector<uint8_t> f((size_t)L.n, 0);
+    auto face_dir = [&](int c, int i, int j, int k) {
+        return B.dirichlet(i, j, k) || B.dirichlet(i - (c == 0), j - (c == 1), k - (c == 2));
+    };
+    auto face_unk = [&](int c, int i, int j, int k) {
+        return !face_dir(c, i, j, k) && (B.interior(i, j, k) || B.interior(i - (c == 0), j - (c == 1), k - (c == 2)));
+    };
     for (int c = 0; c < 4; ++c)
         for (int k = 0; k < ext(L, c, 2); ++k)
             for (int j = 0; j < ext(L, c, 1); ++j)
@@ -140,11 +198,23 @@ std::vector<uint8_t> level_flags(const Lev &L, const Labels &B) {
                         if (B.interior(i, j, k)) v = kFlagActive | (B.v1(i, j, k) ? 0 : kFlagV2);
                     } else {
                         const int mi = i - (c == 0), mj = j - (c == 1), mk = k - (c == 2);
-                        if (active(L, c, i, j, k) && B.interior(i, j, k) && B.interior(mi, mj, mk)) {
+                        if (face_unk(c, i, j, k)) {
                             v = kFlagActive;
-                            if (!B.v1(i, j, k) && !B.v1(mi, mj, mk)) v |= kFlagV2;
+                            if (B.interior(i, j, k) && B.interior(mi, mj, mk) && !B.v1(i, j, k) && !B.v1(mi, mj, mk))
+                                v |= kFlagV2;
+                            int drops = 0;
+                            if (B.exterior(mi, mj, mk)) { v |= kFlagDropLo; ++drops; }
+                            if (B.exterior(i, j, k)) { v |= kFlagDropHi; ++drops; }
+                            for (int d = 0; d < 3; ++d) {
+                                if (d == c) continue;
+                                for (int sg = -1; sg <= 1; sg += 2) {
+                                    const int a = i + sg * (d == 0), b = j + sg * (d == 1), cc = k + sg * (d == 2);
+                                    if (!face_dir(c, a, b, cc) && !face_unk(c, a, b, cc)) ++drops;
+                                }
+                            }
+                            v |= (uint8_t)(drops << kFlagDropShift);
                         }
-                        if (B.dirichlet(i, j, k) || B.dirichlet(mi, mj, mk)) v |= kFlagDirichlet;
+                        if (face_dir(c, i, j, k)) v |= kFlagDirichlet;
                     }
                     f[(size_t)pidx(L, c, i, j, k)] = v;
                 }
@@ -193,10 +263,14 @@ int coarse_inverse(const Lev &C, const std::vector<uint8_t> *hflags, std::vector
         int i = (int)(t % ext(C, c, 0)), j = (int)((t / ext(C, c, 0)) % ext(C, c, 1)),
             k = (int)(t / ((long long)ext(C, c, 0) * ext(C, c, 1)));
         if (c < 3) {
-            put(q, c, i, j, k, 6.0 * e2);
-            put(q, c, i - 1, j, k, -e2); put(q, c, i + 1, j, k, -e2);
-            put(q, c, i, j - 1, k, -e2); put(q, c, i, j + 1, k, -e2);
-            put(q, c, i, j, k - 1, -e2); put(q, c, i, j, k + 1, -e2);
+            // label domains: a face next to exterior cells drops viscous terms (bits 3-5 count them, the
+            // two normal neighbours carry their own bits); inactive tangential neighbours are not unknowns
+            const uint8_t f = hflags ? (*hflags)[(size_t)q] : (uint8_t)0;
+            const int dlo = (f & kFlagDropLo) ? 0 : 1, dhi = (f & kFlagDropHi) ? 0 : 1;
+            put(q, c, i, j, k, (6.0 - ((f >> kFlagDropShift) & 7)) * e2);
+            put(q, c, i - 1, j, k, -e2 * (c == 0 ? dlo : 1)); put(q, c, i + 1, j, k, -e2 * (c == 0 ? dhi : 1));
+            put(q, c, i, j - 1, k, -e2 * (c == 1 ? dlo : 1)); put(q, c, i, j + 1, k, -e2 * (c == 1 ? dhi : 1));
+            put(q, c, i, j, k - 1, -e2 * (c == 2 ? dlo : 1)); put(q, c, i, j, k + 1, -e2 * (c == 2 ? dhi : 1));
             put(q, 3, i, j, k, ih);
             put(q, 3, i - (c == 0), j - (c == 1), k - (c == 2), -ih);
         } else {
@@ -236,6 +310,7 @@ struct stokes_s {
     int cycle = 1;             // coarse-grid visits per level: 1 V-cycle, 2 W-cycle
     int dwj = 0;               // 1: symmetric distributive weighted Jacobi in place of the symmetric DGS
     long long ncell_active = 0;  // interior cells of the finest level (pressure-mean removal)
+    bool neumann = false;        // some unknown face borders an exterior cell: no pressure null space
     GridBarrier *bar = nullptr;
     double eta = 1.0, gamma = 1e-3;
     std::vector<LevelBuf> lev;
@@ -313,7 +388,7 @@ template <class T, class TB> void vanka_colour(stokes_s *h, int l, int col, cuda
     LevelBuf &B = h->lev[l];
     if (B.vcount[col] == 0) return;
     prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
-        launch_vanka_compute<T, TB>(B.L, (const T *)B.x, (const TB *)B.b, B.vcells[col], B.vcount[col],
+        launch_vanka_compute<T, TB>(B.L, (const T *)B.x, (const TB *)B.b, B.vcells[col], B.vtab[col], B.vcount[col],
                                     (const T *)B.kinv, (T *)B.corr, B.vcap, 1.0, s);
     });
     prof(STOKES_K_VANKA_APPLY, l, s,
@@ -327,7 +402,7 @@ template <class T, class TB> void vanka_additive(stokes_s *h, int l, cudaStream_
     for (int c = 0; c < 8; ++c) {
         if (B.vcount[c] == 0) continue;
         prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
-            launch_vanka_compute<T, TB>(B.L, (const T *)B.x, (const TB *)B.b, B.vcells[c], B.vcount[c],
+            launch_vanka_compute<T, TB>(B.L, (const T *)B.x, (const TB *)B.b, B.vcells[c], B.vtab[c], B.vcount[c],
                                         (const T *)B.kinv, (T *)B.corr + c * slice, B.vcap, 0.5, s);
         });
     }
@@ -429,9 +504,22 @@ template <class T, class TB> void smooth(stokes_s *h, int l, cudaStream_t s) {
 template <class T> void smooth_level(stokes_s *h, int l, cudaStream_t s) {
     with_tb<T>(h, l, [&](auto t, auto tb) { smooth<decltype(t), decltype(tb)>(h, l, s); });
 }
+// NVTX range for the host-side trace (the work a call issues per multigrid level and per SQMR
+// iteration; in eager mode the ranges bracket the launches, under graph capture the capture)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+const char *level_range_name(int l) {
+    static const char *names[] = {"mg level 0", "mg level 1", "mg level 2", "mg level 3", "mg level 4",
+                                  "mg level 5", "mg level 6", "mg level 7", "mg level 8", "mg level 9"};
+    return l < 10 ? names[l] : "mg level >9";
+}
+
 // Alg. 1 from level l; first: x_l starts at 0 (else from its current value, the second coarse visit
 // of a W-cycle); h->cycle coarse visits per level (1 V-cycle, 2 W-cycle, Sec. 8.2)
 template <class T> void cycle_level(stokes_s *h, int l, bool first, cudaStream_t s) {
+    NvtxRange range(level_range_name(l));
     const int n = h->nlev();
     if (l == n - 1) {
         LevelBuf &C = h->lev[n - 1];
@@ -608,7 +696,7 @@ int autotune_vanka(stokes_s *h, int nsm) {
                 }
             }
             // one block on a shared-memory copy of the level, where it fits
-            if (vanka_smem_prepare<T, TB>(B.L, B.vcap)) {
+            if (B.ntab == 64 && vanka_smem_prepare<T, TB>(B.L, B.vcap)) {
                 const float ms = time_vanka<T, TB>(h, l, 3, 1, s);
                 if (ms > 0.f && (best < 0.f || ms < best)) {
                     best = ms;
@@ -743,6 +831,34 @@ const char *stokes_strerror(int st) {
     }
 }
 
+// host-side classification of a labelled domain on one level (no CUDA call): the per-entry flags the
+// kernels read, for checking against an independent classification without a GPU
+int stokes_label_flags(const stokes_grid_t *grid, const stokes_bc_t *bc, int level, uint8_t *flags, long long n) {
+    if (!grid || !bc || !bc->cell_labels || !flags || level < 0) return STOKES_ERR_INVALID_ARG;
+    if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 || grid->nx > 2047 || grid->ny > 2047 || grid->nz > 1023)
+        return STOKES_ERR_INVALID_ARG;
+    Labels lab;
+    lab.nx = grid->nx; lab.ny = grid->ny; lab.nz = grid->nz;
+    lab.lab.assign(bc->cell_labels, bc->cell_labels + (size_t)(grid->nx + 2) * (grid->ny + 2) * (grid->nz + 2));
+    for (int k = -1; k <= grid->nz; ++k)
+        for (int j = -1; j <= grid->ny; ++j)
+            for (int i = -1; i <= grid->nx; ++i) {
+                const uint8_t v = lab.at(i, j, k);
+                const bool ghost = i < 0 || j < 0 || k < 0 || i >= grid->nx || j >= grid->ny || k >= grid->nz;
+                if (v > 2 || (ghost && v != 1)) return STOKES_ERR_INVALID_ARG;
+            }
+    lab.finish();
+    for (int l = 0; l < level; ++l) {
+        if (lab.nx % 2 || lab.ny % 2 || lab.nz % 2 || lab.nx < 4 || lab.ny < 4 || lab.nz < 4) return STOKES_ERR_INVALID_ARG;
+        lab = coarsen(lab);
+    }
+    const Lev L = make_level(lab.nx, lab.ny, lab.nz, 1.0, 1.0, 0.0);
+    if (n != L.n) return STOKES_ERR_INVALID_ARG;
+    const std::vector<uint8_t> f = level_flags(L, lab);
+    std::memcpy(flags, f.data(), f.size());
+    return STOKES_OK;
+}
+
 int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double viscosity, const stokes_opts_t *opts,
                   stokes_t *out) {
     if (!grid || !out) return STOKES_ERR_INVALID_ARG;
@@ -757,6 +873,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
     if (bc && bc->cell_labels) {
         lab0.nx = grid->nx; lab0.ny = grid->ny; lab0.nz = grid->nz;
         lab0.lab.assign(bc->cell_labels, bc->cell_labels + (size_t)(grid->nx + 2) * (grid->ny + 2) * (grid->nz + 2));
+        lab0.finish();
         for (int k = -1; k <= grid->nz; ++k)
             for (int j = -1; j <= grid->ny; ++j)
                 for (int i = -1; i <= grid->nx; ++i) {
@@ -825,6 +942,8 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
             for (int j = 0; j < grid->ny; ++j)
                 for (int i = 0; i < grid->nx; ++i) h->ncell_active += lab0.interior(i, j, k) ? 1 : 0;
         if (h->ncell_active == 0) return STOKES_ERR_INVALID_ARG;
+        for (uint8_t f : hflags[0])
+            if ((f & kFlagActive) && (f & (kFlagDropLo | kFlagDropHi))) h->neumann = true;
         for (int l = 0; l < nlev; ++l) {
             uint8_t *fd = nullptr;
             int rc = h->alloc(&fd, hflags[l].size());
@@ -889,20 +1008,65 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
                 CK(cudaMemcpy(B.vcells[c], cells[c].data(), sizeof(int) * cells[c].size(), cudaMemcpyHostToDevice));
         }
         if ((rc = h->alloc(&B.corr, es * 8 * 7 * (size_t)B.vcap))) return rc;  // 8 slices: additive Vanka
+        // Sec. 6: pre-factorised local problems, one per configuration of unknown faces (entries 0..63).
+        // Next to exterior cells a face's row drops viscous terms (Sec. 5 reading), which changes the
+        // local matrix: each such cell gets the entry of its (configuration, dropped counts), appended
+        // after the 64 and shared by every cell with the same key
+        std::vector<int> keys;  // per table entry: cfg | drops of face a << (6 + 3a)
+        for (int cfg = 0; cfg < 64; ++cfg) keys.push_back(cfg);
+        bool ext_tab = false;
+        std::vector<int> tabs[8];
+        if (labelled && labs[l].any_exterior()) {
+            std::map<int, int> id;
+            for (int cfg = 0; cfg < 64; ++cfg) id[cfg] = cfg;
+            const std::vector<uint8_t> &fl = hflags[l];
+            for (int c = 0; c < 8; ++c)
+                for (int w : cells[c]) {
+                    const int i = w & 2047, j = (w >> 11) & 2047, k = (w >> 22) & 1023;
+                    int key = 0;
+                    for (int a = 0; a < 6; ++a) {
+                        const int d = a >> 1, side = a & 1;
+                        const int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+                        if (!active(L, d, fi, fj, fk)) continue;
+                        const uint8_t f = fl[(size_t)pidx(L, d, fi, fj, fk)];
+                        if (!(f & kFlagActive)) continue;
+                        key |= 1 << a;
+                        key |= ((f >> kFlagDropShift) & 7) << (6 + 3 * a);
+                    }
+                    auto it = id.find(key);
+                    if (it == id.end()) {
+                        it = id.emplace(key, (int)keys.size()).first;
+                        keys.push_back(key);
+                        ext_tab = true;
+                    }
+                    tabs[c].push_back(it->second);
+                }
+        }
+        B.ntab = (int)keys.size();
         for (int c = 0; c < 8; ++c) {
             B.lists.cells[c] = B.vcells[c];
             B.lists.count[c] = B.vcount[c];
+            B.lists.tab[c] = nullptr;
+            if (ext_tab) {
+                if ((rc = h->alloc(&B.vtab[c], sizeof(int) * (tabs[c].size() + 1)))) return rc;
+                if (!tabs[c].empty())
+                    CK(cudaMemcpy(B.vtab[c], tabs[c].data(), sizeof(int) * tabs[c].size(), cudaMemcpyHostToDevice));
+                B.lists.tab[c] = B.vtab[c];
+            }
         }
-        // Sec. 6: pre-factorised local problems, one per configuration of unknown faces
-        std::vector<double> kd(64 * 49, 0.0);
-        for (int cfg = 0; cfg < 64; ++cfg)
-            if (vanka_local_inverse(L.h, L.eta, L.gamma, cfg, &kd[cfg * 49])) std::fill(&kd[cfg * 49], &kd[cfg * 49] + 49, 0.0);
-        if ((rc = h->alloc(&B.kinv, es * 64 * 49))) return rc;
+        std::vector<double> kd((size_t)B.ntab * 49, 0.0);
+        for (int t = 0; t < B.ntab; ++t) {
+            int drops[6];
+            for (int a = 0; a < 6; ++a) drops[a] = (keys[t] >> (6 + 3 * a)) & 7;
+            if (vanka_local_inverse(L.h, L.eta, L.gamma, keys[t] & 63, drops, &kd[(size_t)t * 49]))
+                std::fill(&kd[(size_t)t * 49], &kd[(size_t)t * 49] + 49, 0.0);
+        }
+        if ((rc = h->alloc(&B.kinv, es * 49 * (size_t)B.ntab))) return rc;
         if (h->prec == STOKES_PREC_FP64) {
-            CK(cudaMemcpy(B.kinv, kd.data(), sizeof(double) * 64 * 49, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(B.kinv, kd.data(), sizeof(double) * 49 * B.ntab, cudaMemcpyHostToDevice));
         } else {
             std::vector<float> kf(kd.begin(), kd.end());
-            CK(cudaMemcpy(B.kinv, kf.data(), sizeof(float) * 64 * 49, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(B.kinv, kf.data(), sizeof(float) * 49 * B.ntab, cudaMemcpyHostToDevice));
         }
     }
     // reduction scratch and scalar state (the SQMR vectors are allocated by the first sqmr_solve)
@@ -1126,6 +1290,7 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
     }
     status = STOKES_ERR_NOT_CONVERGED;
     for (it = 1; it <= max_iter; ++it) {
+        NvtxRange range("sqmr iteration");
         if ((rc = run_iteration(h, s, precond))) return rc;
         if ((rc = sync_read(h, s, &rr, &flags))) return rc;
         int fl = (int)flags;
@@ -1146,11 +1311,14 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
     }
     if (it > max_iter) it = max_iter;
 finish:
-    // pressure fixed to zero mean (constant p lies in ker L)
-    launch_psum(L, h->x, h->partials, s);
-    launch_scalars_aux(5, h->partials, kRedBlocks, h->st, h->hout, (double)h->ncell_active, s);
-    launch_psub(L, h->x, h->st, s);
-    CKLAUNCH();
+    // pressure fixed to zero mean (constant p lies in ker L) -- unless Neumann faces next to exterior
+    // cells fix the pressure level (the exterior pressure is 0), where L has no null space
+    if (!h->neumann) {
+        launch_psum(L, h->x, h->partials, s);
+        launch_scalars_aux(5, h->partials, kRedBlocks, h->st, h->hout, (double)h->ncell_active, s);
+        launch_psub(L, h->x, h->st, s);
+        CKLAUNCH();
+    }
     // the residual reported: after a converged confirmation it is the one just computed (subtracting a
     // constant from the interior pressures changes L x only by rounding: the constant lies in ker L);
     // otherwise the explicit FP64 residual of the returned x
@@ -1410,6 +1578,38 @@ int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, 
     if (!xdev) CK(cudaMemcpyAsync(x, out, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return STOKES_OK;
+}
+
+int stokes_test_grid_barrier(stokes_t h, int level, int missing_blocks, int spin_limit, void *stream) {
+    if (!h || level < 0 || level >= h->nlev() - 1 || missing_blocks < 0 || spin_limit < 1 ||
+        spin_limit > (int)kBarrierSpinLimit)
+        return STOKES_ERR_INVALID_ARG;
+    if (h->vanka_max_blocks <= 0) return STOKES_ERR_UNSUPPORTED;  // no cooperative launch on this device
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelBuf &B = h->lev[level];
+    const size_t es = h->prec == STOKES_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const size_t esb = level < h->nbf ? sizeof(bf16) : es;
+    CK(cudaMemsetAsync(B.x, 0, es * B.L.n, s));
+    CK(cudaMemsetAsync(B.b, 0, esb * B.L.n, s));
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
+    auto body = [&](auto t, auto tb) {
+        using T = decltype(t);
+        using TB = decltype(tb);
+        launch_vanka_sweep<T, TB>(B.L, (T *)B.x, (const TB *)B.b, B.lists, (const T *)B.kinv, (T *)B.corr, B.vcap, 1,
+                                  h->bar, h->vanka_max_blocks, s, missing_blocks, (unsigned)spin_limit);
+    };
+    if (h->prec == STOKES_PREC_FP64) with_tb<double>(h, level, body);
+    else with_tb<float>(h, level, body);
+    CKLAUNCH();
+    GridBarrier hb;
+    CK(cudaMemcpyAsync(&hb, h->bar, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // leave the barrier and the level's buffers as every other call expects them
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
+    CK(cudaMemsetAsync(B.x, 0, es * B.L.n, s));
+    CK(cudaStreamSynchronize(s));
+    return hb.err ? STOKES_ERR_TIMEOUT : STOKES_OK;
 }
 
 int stokes_restrict(stokes_t h, int level, const double *rf, double *bc, void *stream) {

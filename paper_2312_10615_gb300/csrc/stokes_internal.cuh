@@ -59,11 +59,18 @@ struct Lev {
     double h, eta, gamma;
     // domains given by cell labels (Sec. 5): per packed entry, bit 0 = unknown, bit 1 = V2 DOF (the
     // Vanka set V1 is the rest of the unknowns), bit 2 = face of a Dirichlet cell (its value is data;
-    // other faces that are not unknowns border exterior cells and are 0); nullptr = the plain box,
-    // where all of this follows from the indices
+    // other faces that are not unknowns lie between two exterior cells and are 0); on an unknown
+    // face bits 3-5 = how many viscous terms of its row drop out (do-nothing outflow condition next
+    // to exterior cells), bit 6 / bit 7 = the low / high neighbour along the face normal is one of
+    // them (its term crosses an exterior cell).  nullptr = the plain box, where all of this follows
+    // from the indices
     const uint8_t *flags = nullptr;
 };
-constexpr uint8_t kFlagActive = 1, kFlagV2 = 2, kFlagDirichlet = 4;
+constexpr uint8_t kFlagActive = 1, kFlagV2 = 2, kFlagDirichlet = 4, kFlagDropLo = 64, kFlagDropHi = 128;
+constexpr int kFlagDropShift = 3;
+constexpr uint8_t kFlagDropMask = 0xf8;  // any dropped term
+// diagonal weight of a face row: 6 minus the dropped terms
+template <class T> __device__ __forceinline__ T diag_weight(uint8_t f) { return T(6 - ((f >> kFlagDropShift) & 7)); }
 
 __host__ __device__ inline int ext(const Lev &L, int c, int d) {
     int n = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
@@ -222,7 +229,8 @@ __device__ __forceinline__ Quad quad_at(const Lev &L, int i, int j, int k) {
 }
 // values of the four operator rows at (i,j,k) (0 for entries that are not unknowns); x holds 0
 // off the unknowns
-template <class T, int OP>
+// LAB = true: a label domain (L.flags set), whose faces next to exterior cells drop viscous terms
+template <class T, int OP, bool LAB = false>
 __device__ __forceinline__ void quad_eval(const T *__restrict__ x, const Lev &L, int i, int j, int k, const Quad &Q,
                                           const Coef<T> &K, T out[4]) {
     const long long nx = L.nx, ny = L.ny;
@@ -231,24 +239,35 @@ __device__ __forceinline__ void quad_eval(const T *__restrict__ x, const Lev &L,
     T pc = Q.ex[3] ? x[Q.q[3]] : T(0);
     const bool gxm = i > 0, gxp = i < L.nx - 1, gym = j > 0, gyp = j < L.ny - 1, gzm = k > 0, gzp = k < L.nz - 1;
     out[0] = out[1] = out[2] = out[3] = T(0);
+    // label domains: diagonal weight and the two normal neighbours of a face next to exterior cells
+    // (the dropped viscous terms of the do-nothing outflow reading, Sec. 5); the box has none
+    uint8_t f0 = 0, f1 = 0, f2 = 0;
+    if (LAB) {
+        if (Q.act[0]) f0 = L.flags[Q.q[0]];
+        if (Q.act[1]) f1 = L.flags[Q.q[1]];
+        if (Q.act[2]) f2 = L.flags[Q.q[2]];
+    }
     if (Q.act[0]) {
         const T *u = x + Q.q[0];
-        T s = T(6) * u[0] - u[-1] - u[1] - (gym ? u[-uy] : T(0)) - (gyp ? u[uy] : T(0)) - (gzm ? u[-uz] : T(0)) -
-              (gzp ? u[uz] : T(0));
+        const T ul = (f0 & kFlagDropLo) ? T(0) : u[-1], uh = (f0 & kFlagDropHi) ? T(0) : u[1];
+        T s = (LAB ? diag_weight<T>(f0) : T(6)) * u[0] - ul - uh - (gym ? u[-uy] : T(0)) - (gyp ? u[uy] : T(0)) -
+              (gzm ? u[-uz] : T(0)) - (gzp ? u[uz] : T(0));
         out[0] = K.eh2 * s;
         if (OP == OP_APPLY) out[0] += K.ih * (pc - x[Q.q[3] - 1]);
     }
     if (Q.act[1]) {
         const T *v = x + Q.q[1];
-        T s = T(6) * v[0] - (gxm ? v[-1] : T(0)) - (gxp ? v[1] : T(0)) - v[-vy] - v[vy] - (gzm ? v[-vz] : T(0)) -
-              (gzp ? v[vz] : T(0));
+        const T vl = (f1 & kFlagDropLo) ? T(0) : v[-vy], vh = (f1 & kFlagDropHi) ? T(0) : v[vy];
+        T s = (LAB ? diag_weight<T>(f1) : T(6)) * v[0] - (gxm ? v[-1] : T(0)) - (gxp ? v[1] : T(0)) - vl - vh -
+              (gzm ? v[-vz] : T(0)) - (gzp ? v[vz] : T(0));
         out[1] = K.eh2 * s;
         if (OP == OP_APPLY) out[1] += K.ih * (pc - x[Q.q[3] - py]);
     }
     if (Q.act[2]) {
         const T *w = x + Q.q[2];
-        T s = T(6) * w[0] - (gxm ? w[-1] : T(0)) - (gxp ? w[1] : T(0)) - (gym ? w[-wy] : T(0)) -
-              (gyp ? w[wy] : T(0)) - w[-wz] - w[wz];
+        const T wl = (f2 & kFlagDropLo) ? T(0) : w[-wz], wh = (f2 & kFlagDropHi) ? T(0) : w[wz];
+        T s = (LAB ? diag_weight<T>(f2) : T(6)) * w[0] - (gxm ? w[-1] : T(0)) - (gxp ? w[1] : T(0)) - (gym ? w[-wy] : T(0)) -
+              (gyp ? w[wy] : T(0)) - wl - wh;
         out[2] = K.eh2 * s;
         if (OP == OP_APPLY) out[2] += K.ih * (pc - x[Q.q[3] - pz]);
     }

@@ -1,6 +1,7 @@
 """Parity of the CUDA path with the CPU oracle on domains given by cell labels (Sec. 5): Dirichlet
-obstacles inside the box (random spheres, a cylinder in a channel) and exterior cells (spheres whose
-faces carry homogeneous Neumann conditions).  Needs a GB300.
+obstacles inside the box (random spheres, a cylinder in a channel) and exterior cells (spheres of
+exterior cells, and a channel whose outlet columns are exterior: Neumann faces carrying the do-nothing
+outflow condition).  Needs a GB300.
 
 Tolerances (relative to the max-norm of the oracle result): as for the box, 1e-13 for the operator and
 the right-hand side, 1e-12 for a smoother sweep or a transfer, 1e-10 for the dense coarsest solve,
@@ -12,7 +13,11 @@ by the -gamma I term (gamma = 1e-3); rounding differences of the coarse solve ar
 the poor coarse grids of these thin domains 2^l times, and SQMR then stagnates for a few iterations
 (oracle residual history on the cylinder: 1.10, 0.521, 0.521, 0.521), where the quasi-minimal-residual
 iterate is ill-determined (6e-8 to 1e-2 apart after six iterations, with the preconditioners equal to
-1e-11).  Converged solutions (relative residual 1e-11) agree to 1e-9 for every variant.
+1e-11).  Converged solutions (relative residual 1e-11) agree to 1e-9 for every variant.  On the domains
+with exterior cells the six-iterate comparison gets 3e-6: their early SQMR iterations stall in the same
+way (oracle residual history of the channel with an exterior outlet: 1.0, 0.96, 1.16, 0.078, ...; with the
+additive Vanka 1.0, 1.08, 0.80, 1.02, ...), and the GPU iterates were measured 7e-8 to 7e-7 from the
+oracle's after six iterations while the V-cycles agree to 1e-11 and the converged solutions to 1e-9.
 """
 import numpy as np
 import pytest
@@ -54,11 +59,22 @@ def velocity_forcing(o, seed):
 DOMAINS = {
     "porous32": lambda: ((32, 32, 32), synthetic.porous_labels(32, seed=0, nspheres=10, rmin=0.08, rmax=0.18)),
     "cylinder48x24x16": lambda: ((48, 24, 16), synthetic.cylinder_labels(48, 24, 16, radius=0.2)),
-    # every other sphere made of exterior cells (homogeneous Neumann faces)
+    # every other sphere made of exterior cells (Neumann faces around them)
     "mixed32": lambda: ((32, 32, 32), synthetic.porous_labels(32, seed=0, nspheres=10, rmin=0.08, rmax=0.18,
                                                               exterior_every=2)),
+    # a channel with a cylinder and an open outlet: its last four columns of cells are exterior
+    "outlet48x24x16": lambda: ((48, 24, 16), synthetic.channel_labels(48, 24, 16, outlet=4, cylinder=(12.0, 12.0, 3.0))),
 }
 _cache = {}
+
+
+def dirichlet_data(name, lab, dims):
+    """The domain's Dirichlet data: plug flow through the box's x sides, or the duct inflow profile
+    of a channel with an exterior outlet (nothing is prescribed at the outlet)."""
+    nx, ny, nz = dims
+    if name.startswith("outlet"):
+        return synthetic.channel_inflow(nx, ny, nz, labels=lab).numpy()
+    return synthetic.plug_flow(nx, ny, nz, lab).numpy()
 
 
 def pair(name, precision=smg.PREC_FP64, **kw):
@@ -84,7 +100,7 @@ def test_labelled_apply_and_rhs(name):
     assert rel_err(y, o.apply(np.where(act, x, 0.0))) < 1e-13
     assert np.all(y[~act] == 0.0)
     f = np.random.default_rng(2).standard_normal(o.n())
-    g = synthetic.plug_flow(nx, ny, nz, lab).numpy() + 0.1 * np.random.default_rng(3).standard_normal(
+    g = dirichlet_data(name, lab, (nx, ny, nz)) + 0.1 * np.random.default_rng(3).standard_normal(
         synthetic.ghost_len(nx, ny, nz))
     b = S.rhs(cuda(f), cuda(g))
     assert rel_err(b, o.rhs(f, g)) < 1e-13
@@ -140,12 +156,12 @@ def test_labelled_vcycle_and_sqmr(name, kw):
     assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-11
     nx, ny, nz = o.dims
     f = velocity_forcing(o, 12)
-    b = o.rhs(f, synthetic.plug_flow(nx, ny, nz, lab).numpy())
+    b = o.rhs(f, dirichlet_data(name, lab, (nx, ny, nz)))
     if kw.get("cycle") != 2:
         x_ref, _, _, _, _ = o.sqmr(b, tol=1e-30, maxit=6, fixed_iters=6)
         x = torch.zeros(o.n(), dtype=torch.float64, device=DEV)
         info = smg.sqmr_solve(S.h, cuda(b), x, tol=1e-30, max_iter=6, check=False)
-        assert info.iterations == 6 and rel_err(x, x_ref) < 1e-8
+        assert info.iterations == 6 and rel_err(x, x_ref) < (3e-6 if (lab == 2).any() else 1e-8)
     x_ref, rc, _, _, _ = o.sqmr(b, tol=1e-11, maxit=100)
     assert rc == 0
     x2, info2 = S.solve(cuda(b), tol=1e-11, max_iter=100)
@@ -159,7 +175,7 @@ def test_labelled_fp32_solve(name):
     assert rel_err(S.precondition(cuda(s)), o.vcycle(s)) < 1e-4
     nx, ny, nz = o.dims
     f = velocity_forcing(o, 14)
-    g = synthetic.plug_flow(nx, ny, nz, lab).numpy()
+    g = dirichlet_data(name, lab, (nx, ny, nz))
     b_ref = o.rhs(f, g)
     x_ref, rc, _, _, _ = o.sqmr(b_ref, tol=1e-12, maxit=100)
     assert rc == 0
@@ -168,9 +184,12 @@ def test_labelled_fp32_solve(name):
     assert rel_err(x, x_ref) < 1e-7
     act, _ = o.masks()
     assert np.all(x.cpu().numpy()[~act.astype(bool)] == 0.0)
-    # pressure mean over the interior cells only
+    # pressure mean over the interior cells only -- unless Neumann faces fix the pressure level
     p = x.cpu().numpy()[-nx * ny * nz:][act[-nx * ny * nz:].astype(bool)]
-    assert abs(p.mean()) <= 1e-12 * np.abs(p).max()
+    if not o.has_neumann():
+        assert abs(p.mean()) <= 1e-12 * np.abs(p).max()
+    else:
+        assert abs(p.mean()) > 1e-6 * np.abs(p).max()  # not shifted: the exterior pressure 0 is the reference
 
 
 @pytest.mark.parametrize("mode,blocks", [(1, 8), (2, 8), (3, 1)])
@@ -235,14 +254,66 @@ def test_porous_128_fp32_solve():
     assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b)) < 1e-8
 
 
-def test_exterior_and_dirichlet_labellings_share_the_finest_operator():
-    # the reading of Sec. 5 the oracle pins: on the finest level exterior cells act as Dirichlet cells
-    # with zero data; the hierarchies differ (coarsening), so the V-cycles differ
+def test_exterior_and_dirichlet_labellings_differ_on_the_finest_operator():
+    # the reading of Sec. 5 the oracle pins: a face between an interior and an exterior cell is an
+    # unknown with the do-nothing outflow condition, so the exterior labelling's operator differs from
+    # the Dirichlet one's near exterior cells; the GPU follows the oracle for both
     (nx, ny, nz), lab = DOMAINS["mixed32"]()
     dl = np.where(lab == 2, 1, lab).astype(np.uint8)
     Se = smg.Stokes(nx, labels=lab, autotune=False)
     Sd = smg.Stokes(nx, labels=dl, autotune=False)
-    x = torch.from_numpy(np.random.default_rng(17).standard_normal(synthetic.packed_len(nx))).to(DEV)
-    ye, yd = Se.apply(x), Sd.apply(x)
-    assert torch.equal(ye, yd)
-    assert not torch.equal(Se.precondition(ye), Sd.precondition(ye))
+    oe = oracle.Oracle(nx, coarsest_max=8, labels=lab)
+    od = oracle.Oracle(nx, coarsest_max=8, labels=dl)
+    x = np.random.default_rng(17).standard_normal(synthetic.packed_len(nx))
+    ye, yd = Se.apply(cuda(x)), Sd.apply(cuda(x))
+    ae, ad = oe.masks()[0].astype(bool), od.masks()[0].astype(bool)
+    assert rel_err(ye, oe.apply(np.where(ae, x, 0.0))) < 1e-13
+    assert rel_err(yd, od.apply(np.where(ad, x, 0.0))) < 1e-13
+    assert (ae & ~ad).sum() > 0 and not torch.equal(ye, yd)
+
+
+def _outlet_problem(dims, outlet, cyl):
+    nx, ny, nz = dims
+    lab = synthetic.channel_labels(nx, ny, nz, outlet=outlet, cylinder=cyl)
+    return lab, synthetic.channel_inflow(nx, ny, nz, labels=lab)
+
+
+def test_channel_outlet_kb2_iterates_match_the_oracle():
+    # stand-in of the Sec. 7 3D cylinder (eta = gamma = 1e-3, k_b = 2, duct inflow, do-nothing outlet) at
+    # half size: six SQMR iterates of the FP64 path against the oracle's, then the converged solutions
+    dims, outlet = (128, 40, 40), 8
+    nx, ny, nz = dims
+    lab, g = _outlet_problem(dims, outlet, (0.5 / 1.275 * (nx - outlet), 0.2 / 0.41 * ny, 0.025 / 0.41 * ny))
+    o = oracle.Oracle(nx, ny, nz, h=1.0 / ny, eta=1e-3, gamma=1e-3, kb=2, coarsest_max=8, labels=lab)
+    S = smg.Stokes(nx, ny, nz, h=1.0 / ny, viscosity=1e-3, gamma=1e-3, kb_vanka=2, labels=lab)
+    assert S.levels == o.nlevels and o.has_neumann()
+    b = o.rhs(None, g.numpy())
+    bg = S.rhs(None, g.to(DEV))
+    assert rel_err(bg, b) < 1e-13
+    x_ref, _, _, _, _ = o.sqmr(b, tol=1e-30, maxit=6, fixed_iters=6)
+    x = torch.zeros(o.n(), dtype=torch.float64, device=DEV)
+    info = smg.sqmr_solve(S.h, cuda(b), x, tol=1e-30, max_iter=6, check=False)
+    assert info.iterations == 6 and rel_err(x, x_ref) < 1e-8
+    x2, info2 = S.solve(cuda(b), tol=1e-8, max_iter=100)
+    assert info2.status == 0 and info2.rel_residual < 1e-8
+
+
+def test_channel_outlet_full_size_fp32():
+    # the stand-in at full size (256 x 80 x 80 cells, 16 exterior outlet columns so the outlet survives
+    # coarsening to every level): the FP32 V-cycle SQMR reaches 1e-8, its FP64 residual is recomputed,
+    # the outlet's Neumann faces carry the inflow's flux and the flow is mirror-symmetric in z
+    dims, outlet = (256, 80, 80), 16
+    nx, ny, nz = dims
+    lab, g = _outlet_problem(dims, outlet, (0.5 / 1.275 * (nx - outlet), 0.2 / 0.41 * ny, 0.025 / 0.41 * ny))
+    S = smg.Stokes(nx, ny, nz, h=1.0 / ny, viscosity=1e-3, gamma=1e-3, kb_vanka=2, precision=smg.PREC_FP32,
+                   labels=lab)
+    b = S.rhs(None, g.to(DEV))
+    x, info = S.solve(b, tol=1e-8, max_iter=200)
+    assert info.status == 0 and info.rel_residual < 1e-8 and info.iterations < 60, (info.status, info.iterations)
+    r = b - S.apply(x)
+    assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b)) < 1e-8
+    u, v, w, p = synthetic.unpack(x.cpu().numpy(), nx, ny, nz)
+    gu = g.numpy()[:(nx + 1) * (ny + 2) * (nz + 2)].reshape(nz + 2, ny + 2, nx + 1)
+    inflow = gu[1:-1, 1:-1, 0].sum()
+    assert abs(u[:, :, nx - outlet].sum() - inflow) <= 1e-6 * inflow
+    assert np.max(np.abs(u - u[::-1])) <= 1e-5 * np.max(np.abs(u))
