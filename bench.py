@@ -64,18 +64,25 @@ def oracle_iterations(n, seed=0, tol=1e-8):
 
 # ------------------------------------------------------------------------------------------ CPU oracle
 
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1", "0xd49": "Arm Neoverse N2"}
+
+
 def host_info():
-    """nproc and the CPU model of this host (for the CPU-baseline records)."""
-    model = None
+    """nproc and the CPU model of this host (for the CPU-baseline records); Arm hosts report the CPU part."""
+    model, part = None, None
     try:
         for line in open("/proc/cpuinfo"):
-            k = line.split(":")[0].strip().lower()
-            if k in ("model name", "cpu part", "hardware") and ":" in line:
-                model = line.split(":", 1)[1].strip()
-                if k == "model name":
-                    break
+            if ":" not in line:
+                continue
+            k, v = (t.strip() for t in line.split(":", 1))
+            if k.lower() == "model name" and model is None:
+                model = v
+            if k.lower() == "cpu part" and part is None:
+                part = v
     except OSError:
         pass
+    if model is None and part is not None:
+        model = f"{ARM_PARTS.get(part, 'Arm')} (CPU part {part})"
     return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
@@ -944,6 +951,8 @@ def main():
             "vs_baseline": None, "dtype": "f64 SQMR + f32 V-cycle", "data": "synthetic",
             "config": bench_config(n, world), "vcycle_precision": "fp32", "sqmr_precision": "fp64",
             "vanka_schedule_per_level": [dict(zip(("mode", "blocks", "ms_per_sweep"), smg.stokes_level_schedule(S32.h, l)))
+                                         for l in range(S32.levels - 1)],
+            "transfer_tiles_per_level": [dict(zip(("restrict", "prolong", "ms"), smg.stokes_level_tiles(S32.h, l)))
                                          for l in range(S32.levels - 1)],
             "iterations": [it for it, _ in its32], "rel_residual": [r for _, r in its32],
             "kernel_ms_per_iteration": {k: round(v[0], 4) for k, v in prof32.items()},

@@ -198,6 +198,17 @@ int stokes_level_schedule(stokes_t h, int level, int *mode, int *blocks, float *
  * the same bits. */
 int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks);
 
+/* tiles of the transfers between `level` and level + 1 (0 <= level < levels-1): tiles[0..2] = block x,
+ * block y and coarse z-planes per thread of the restriction R from this level, tiles[3..5] the same for
+ * the prolongation P into it; *ms (optional, 2 floats) = the autotuner's time per launch of each (0 if
+ * not measured).  With opts.autotune the handle times 8 candidate tiles per transfer and level at
+ * creation and keeps the fastest; every tile computes the same bits (each entry is produced by one
+ * thread with the same arithmetic). */
+int stokes_level_tiles(stokes_t h, int level, int *tiles, float *ms);
+/* override them (block x * block y a multiple of 32 and at most 1024, 1 <= z-planes <= 64); the
+ * handle's captured graphs are re-captured on next use */
+int stokes_set_level_tiles(stokes_t h, int level, const int *tiles);
+
 /* *out = ||b - L x||_2 (FP64, deterministic reduction); synchronises the stream.  Uses the
  * handle's reduction scratch. */
 int stokes_residual_norm(stokes_t h, const double *b, const double *x, double *out, void *stream);

@@ -25,7 +25,8 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
            "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
-           "stokes_set_level_schedule", "sqmr_solve_unpreconditioned", "mg_solve",
+           "stokes_set_level_schedule", "stokes_level_tiles", "stokes_set_level_tiles", "sqmr_solve_unpreconditioned",
+           "mg_solve",
            "stokes_measure_fma_peak", "stokes_label_flags", "stokes_test_grid_barrier", "stokes_strerror",
            # learned initial guess (include/warmstart.h)
            "warmstart_num_weights", "warmstart_create", "warmstart_destroy", "warmstart_set_scale",
@@ -99,6 +100,8 @@ def _load():
                                  ctypes.POINTER(sqmr_info_t), ctypes.POINTER(d), i]),
         "stokes_level_schedule": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
         "stokes_set_level_schedule": (i, [vp, i, i, i]),
+        "stokes_level_tiles": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
+        "stokes_set_level_tiles": (i, [vp, i, ctypes.POINTER(i)]),
         "stokes_strerror": (ctypes.c_char_p, [i]),
         "warmstart_num_weights": (ll, []),
         "warmstart_create": (i, [i, i, d, ctypes.POINTER(vp)]),
@@ -298,6 +301,19 @@ def stokes_level_schedule(h, level):
 
 def stokes_set_level_schedule(h, level, mode, blocks=0):
     _check(lib().stokes_set_level_schedule(h, level, mode, blocks), "stokes_set_level_schedule")
+
+
+def stokes_level_tiles(h, level):
+    """((restrict bx, by, kz), (prolong bx, by, kz), (ms restrict, ms prolong)) of the transfers between
+    level and level + 1."""
+    t, m = (ctypes.c_int * 6)(), (ctypes.c_float * 2)()
+    _check(lib().stokes_level_tiles(h, level, t, m), "stokes_level_tiles")
+    return tuple(t[0:3]), tuple(t[3:6]), (m[0], m[1])
+
+
+def stokes_set_level_tiles(h, level, restrict_tile, prolong_tile):
+    t = (ctypes.c_int * 6)(*restrict_tile, *prolong_tile)
+    _check(lib().stokes_set_level_tiles(h, level, t), "stokes_set_level_tiles")
 
 
 def stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, b, x, out, stream=None):

@@ -74,8 +74,14 @@ template <class T, class TB>
 cudaError_t launch_vanka_cluster(const Lev &L, T *x, const TB *b, const VankaLists &lists, const T *kinv, T *corr,
                                  int cap, int sweeps, int cluster, cudaStream_t s);
 // transfers (Sec. 2): bc = R rf,  xf += P ec
-template <class T, class TF, class TC> void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s);
-template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s);
+// tile of a transfer launch: thread block bx x by over the coarse level's (x, y) positions, kz coarse
+// z-planes marched per thread (any tile gives the same bits)
+struct Tile {
+    int bx = 32, by = 8, kz = 8;
+};
+template <class T, class TF, class TC>
+void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s, Tile t = Tile());
+template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s, Tile t = Tile());
 // coarsest level: x = Kinv b over the compact unknown list (FP64 matrix)
 template <class T>
 void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, const T *b, T *x, cudaStream_t s);

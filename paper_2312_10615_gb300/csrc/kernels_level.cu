@@ -1360,12 +1360,24 @@ __device__ __forceinline__ T restrict_face(const Lev &F, const Lev &Cl, const TF
     return s * T(0.125);
 }
 
+// thread_entry with the launch's own tile: block (blockDim.x, blockDim.y) over (x, y), kz planes per thread
+__device__ __forceinline__ bool thread_entry_tile(const Lev &L, int gy, int kz, int &c, int &i, int &j, int &k0,
+                                                  int &k1) {
+    c = blockIdx.y / gy;
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    j = (blockIdx.y - c * gy) * blockDim.y + threadIdx.y;
+    k0 = blockIdx.z * kz;
+    int ez = ext(L, c, 2);
+    k1 = k0 + kz < ez ? k0 + kz : ez;
+    return i < ext(L, c, 0) && j < ext(L, c, 1) && k0 < ez;
+}
+
 template <class T, class TF, class TC>
-__global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, const TF *__restrict__ rf,
+__global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, int kz, const TF *__restrict__ rf,
                                                   TC *__restrict__ bc) {
     pdl_wait();
     int c, I, J, k0, k1;
-    if (!thread_entry(C, gy, c, I, J, k0, k1)) return;
+    if (!thread_entry_tile(C, gy, kz, c, I, J, k0, k1)) return;
     for (int Kk = k0; Kk < k1; ++Kk) {
     long long q = pidx(C, c, I, J, Kk);
     if (!unknown(C, c, I, J, Kk)) {
@@ -1444,11 +1456,11 @@ __device__ __forceinline__ void prolong_comp(const Lev &F, const Lev &Cl, const 
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, const T *__restrict__ ec, T *__restrict__ xf) {
+__global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, int kz, const T *__restrict__ ec, T *__restrict__ xf) {
     pdl_wait();
-    int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+    int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= Cl.nx || J >= Cl.ny) return;
-    int k0 = blockIdx.z * KZ, k1 = k0 + KZ < Cl.nz ? k0 + KZ : Cl.nz;
+    int k0 = blockIdx.z * kz, k1 = k0 + kz < Cl.nz ? k0 + kz : Cl.nz;
     const long long fy = F.nx, fz = (long long)F.nx * F.ny;
     for (int Kk = k0; Kk < k1; ++Kk) {
         T pcv = ec[pidx(Cl, 3, I, J, Kk)];
@@ -1464,14 +1476,20 @@ __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, const T *__restr
     }
 }
 
+// Transfers take a tile (block bx x by over the coarse (x, y) positions, kz coarse z-planes per
+// thread): every output entry is produced by one thread with the same arithmetic whatever the tile,
+// so all tiles give the same bits; the handle picks one per level by timing (coarse levels want
+// small tiles and one plane per thread: few entries, latency-bound).
 template <class T, class TF, class TC>
-void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s) {
-    Geo g = geo_components(C, 4);
-    launch_k(k_restrict<T, TF, TC>, dim3(g.grid), dim3(kBlock3), 0, s, F, C, g.gy, rf, bc);
+void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s, Tile t) {
+    const int mx = C.nx + 1, my = C.ny + 1, mz = C.nz + 1;
+    const int gy = cdiv(my, t.by);
+    launch_k(k_restrict<T, TF, TC>, dim3(cdiv(mx, t.bx), gy * 4, cdiv(mz, t.kz)), dim3(t.bx, t.by, 1), 0, s, F, C, gy,
+             t.kz, rf, bc);
 }
-template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s) {
-    dim3 grid(cdiv(C.nx, BX), cdiv(C.ny, BY), cdiv(C.nz, KZ));
-    launch_k(k_prolong<T>, dim3(grid), dim3(kBlock3), 0, s, F, C, ec, xf);
+template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s, Tile t) {
+    dim3 grid(cdiv(C.nx, t.bx), cdiv(C.ny, t.by), cdiv(C.nz, t.kz));
+    launch_k(k_prolong<T>, dim3(grid), dim3(t.bx, t.by, 1), 0, s, F, C, t.kz, ec, xf);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1553,8 +1571,8 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     SMG_INST_TB(T, T)                                                                                             \
     template void launch_dgs_p_gather<T>(const Lev &, T *, const T *, cudaStream_t);                              \
     template void launch_vanka_apply<T>(const Lev &, T *, const int *, int, const T *, int, cudaStream_t);        \
-    template void launch_restrict<T, T, T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);               \
-    template void launch_prolong<T>(const Lev &, const Lev &, const T *, T *, cudaStream_t);                      \
+    template void launch_restrict<T, T, T>(const Lev &, const Lev &, const T *, T *, cudaStream_t, Tile);               \
+    template void launch_prolong<T>(const Lev &, const Lev &, const T *, T *, cudaStream_t, Tile);                      \
     template void launch_coarse<T>(const Lev &, const int *, int, const double *, const T *, T *, cudaStream_t);
 SMG_INST(float)
 SMG_INST(double)
@@ -1563,9 +1581,9 @@ template void launch_dwj_sym<float, float>(const Lev &, float *, const float *, 
 template void launch_dwj_sym<double, double>(const Lev &, double *, const double *, double *, double *, double,
                                              cudaStream_t);
 template void launch_dwj_sym<float, bf16>(const Lev &, float *, const bf16 *, float *, float *, double, cudaStream_t);
-template void launch_restrict<float, bf16, bf16>(const Lev &, const Lev &, const bf16 *, bf16 *, cudaStream_t);
-template void launch_restrict<float, bf16, float>(const Lev &, const Lev &, const bf16 *, float *, cudaStream_t);
-template void launch_restrict<float, float, bf16>(const Lev &, const Lev &, const float *, bf16 *, cudaStream_t);
+template void launch_restrict<float, bf16, bf16>(const Lev &, const Lev &, const bf16 *, bf16 *, cudaStream_t, Tile);
+template void launch_restrict<float, bf16, float>(const Lev &, const Lev &, const bf16 *, float *, cudaStream_t, Tile);
+template void launch_restrict<float, float, bf16>(const Lev &, const Lev &, const float *, bf16 *, cudaStream_t, Tile);
 template void launch_convert<double, float>(long long, const double *, float *, cudaStream_t);
 template void launch_convert<float, double>(long long, const float *, double *, cudaStream_t);
 template void launch_convert<double, double>(long long, const double *, double *, cudaStream_t);

@@ -46,6 +46,8 @@ struct LevelBuf {
     int vmode = 0, vblocks = 0;  // Vanka schedule: 0 per-colour launches, 1 cooperative sweep of vblocks blocks,
                                  // 2 one-cluster sweep of vblocks CTAs
     float vms = 0.f;             // autotuner's time per symmetric sweep
+    Tile rtile, ptile;           // tiles of the restriction from / prolongation into this level
+    float rms = 0.f, pms = 0.f;  // autotuner's time per launch of each
 };
 
 int cuda_status(cudaError_t e) {
@@ -538,12 +540,13 @@ template <class T> void cycle_level(stokes_s *h, int l, bool first, cudaStream_t
         with_tb<T>(h, l + 1, [&](auto, auto tc) {
             using TC = decltype(tc);
             prof(STOKES_K_RESTRICT, l, s,
-                 [&] { launch_restrict<TT, TF, TC>(B.L, h->lev[l + 1].L, (const TF *)B.r, (TC *)h->lev[l + 1].b, s); });
+                 [&] { launch_restrict<TT, TF, TC>(B.L, h->lev[l + 1].L, (const TF *)B.r, (TC *)h->lev[l + 1].b, s,
+                                                   B.rtile); });
         });
     });
     for (int g = 0; g < h->cycle; ++g) cycle_level<T>(h, l + 1, g == 0, s);
     prof(STOKES_K_PROLONG, l, s,
-         [&] { launch_prolong<T>(B.L, h->lev[l + 1].L, (const T *)h->lev[l + 1].x, (T *)B.x, s); });
+         [&] { launch_prolong<T>(B.L, h->lev[l + 1].L, (const T *)h->lev[l + 1].x, (T *)B.x, s, B.ptile); });
     smooth_level<T>(h, l, s);
 }
 template <class T> void vcycle(stokes_s *h, cudaStream_t s) { cycle_level<T>(h, 0, true, s); }
@@ -724,6 +727,65 @@ int autotune_vanka(stokes_s *h, int nsm) {
         B.vms = best > 0.f ? best : 0.f;
     }
     CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+// ---- autotuner: per level, the tile (block shape, z-planes per thread) of the restriction and the
+// prolongation, timed on the level's own buffers; every candidate computes the same bits
+const Tile kTileCand[] = {{32, 8, 8}, {32, 8, 4}, {32, 8, 2}, {32, 8, 1}, {32, 4, 1}, {16, 8, 1}, {8, 8, 1}, {8, 4, 1}};
+constexpr int kNumTileCand = sizeof(kTileCand) / sizeof(kTileCand[0]);
+template <class Fn> float time_launches(Fn fn, cudaStream_t s, int reps = 8) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int r = 0; r < 2; ++r) fn();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) fn();
+    cudaEventRecord(e1, s);
+    float ms = -1.f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+int autotune_tiles(stokes_s *h) {
+    cudaStream_t s = h->cs;
+    for (int l = 0; l < h->nlev() - 1; ++l) {
+        LevelBuf &F = h->lev[l];
+        LevelBuf &C = h->lev[l + 1];
+        auto run = [&](auto t, auto tf) {
+            using T = decltype(t);
+            using TF = decltype(tf);
+            with_tb<T>(h, l + 1, [&](auto, auto tc) {
+                using TC = decltype(tc);
+                float best = -1.f;
+                for (int c = 0; c < kNumTileCand; ++c) {
+                    const Tile tl = kTileCand[c];
+                    const float ms = time_launches(
+                        [&] { launch_restrict<T, TF, TC>(F.L, C.L, (const TF *)F.r, (TC *)C.b, s, tl); }, s);
+                    if (ms > 0.f && (best < 0.f || ms < best)) { best = ms; F.rtile = tl; F.rms = ms; }
+                }
+            });
+            float best = -1.f;
+            for (int c = 0; c < kNumTileCand; ++c) {
+                const Tile tl = kTileCand[c];
+                const float ms =
+                    time_launches([&] { launch_prolong<T>(F.L, C.L, (const T *)C.x, (T *)F.x, s, tl); }, s);
+                if (ms > 0.f && (best < 0.f || ms < best)) { best = ms; F.ptile = tl; F.pms = ms; }
+            }
+        };
+        if (h->prec == STOKES_PREC_FP64) with_tb<double>(h, l, run);
+        else with_tb<float>(h, l, run);
+        // the timing runs leave arbitrary values in the level's work vectors: clear them
+        const size_t es = h->prec == STOKES_PREC_FP64 ? sizeof(double) : sizeof(float);
+        CK(cudaMemsetAsync(F.x, 0, es * F.L.n, s));
+        CK(cudaMemsetAsync(C.x, 0, es * C.L.n, s));
+    }
     CK(cudaStreamSynchronize(s));
     return 0;
 }
@@ -1092,6 +1154,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
         if (coop && h->vanka_max_blocks > 0 && !h->vanka_persistent && o.autotune && !h->additive) {
             if ((rc = autotune_vanka(h.get(), nsm))) return rc;
         }
+        if (o.autotune && (rc = autotune_tiles(h.get()))) return rc;
     }
     CK(cudaDeviceSynchronize());
     *out = h.release();
@@ -1506,6 +1569,39 @@ int stokes_level_schedule(stokes_t h, int level, int *mode, int *blocks, float *
     return STOKES_OK;
 }
 
+int stokes_level_tiles(stokes_t h, int level, int *tiles, float *ms) {
+    if (!h || level < 0 || level >= h->nlev() - 1 || !tiles) return STOKES_ERR_INVALID_ARG;
+    const LevelBuf &B = h->lev[level];
+    const Tile t[2] = {B.rtile, B.ptile};
+    for (int k = 0; k < 2; ++k) {
+        tiles[3 * k] = t[k].bx;
+        tiles[3 * k + 1] = t[k].by;
+        tiles[3 * k + 2] = t[k].kz;
+    }
+    if (ms) {
+        ms[0] = B.rms;
+        ms[1] = B.pms;
+    }
+    return STOKES_OK;
+}
+
+int stokes_set_level_tiles(stokes_t h, int level, const int *tiles) {
+    if (!h || level < 0 || level >= h->nlev() - 1 || !tiles) return STOKES_ERR_INVALID_ARG;
+    for (int k = 0; k < 2; ++k) {
+        const int bx = tiles[3 * k], by = tiles[3 * k + 1], kz = tiles[3 * k + 2];
+        if (bx < 1 || by < 1 || bx * by > 1024 || bx * by % 32 != 0 || kz < 1 || kz > 64) return STOKES_ERR_INVALID_ARG;
+    }
+    LevelBuf &B = h->lev[level];
+    B.rtile = Tile{tiles[0], tiles[1], tiles[2]};
+    B.ptile = Tile{tiles[3], tiles[4], tiles[5]};
+    B.rms = B.pms = 0.f;
+    // the captured graphs hold the old tiles
+    if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
+    if (h->g_iter) { cudaGraphExecDestroy(h->g_iter); h->g_iter = nullptr; }
+    if (h->g_iter_id) { cudaGraphExecDestroy(h->g_iter_id); h->g_iter_id = nullptr; }
+    return STOKES_OK;
+}
+
 int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
     if (!h || level < 0 || level >= h->nlev() - 1 || mode < 0 || mode > 3) return STOKES_ERR_INVALID_ARG;
     if (mode == 1 && (h->vanka_max_blocks <= 0 || blocks < 1 || blocks > h->vanka_max_blocks)) return STOKES_ERR_INVALID_ARG;
@@ -1627,7 +1723,7 @@ int stokes_restrict(stokes_t h, int level, const double *rf, double *bc, void *s
         using TF = decltype(tf);
         auto inner = [&](auto, auto tc) {
             using TC = decltype(tc);
-            launch_restrict<T, TF, TC>(F.L, C.L, (const TF *)F.r, (TC *)C.b, s);
+            launch_restrict<T, TF, TC>(F.L, C.L, (const TF *)F.r, (TC *)C.b, s, F.rtile);
         };
         with_tb<T>(h, level + 1, inner);
     };
@@ -1657,7 +1753,7 @@ int stokes_prolong_add(stokes_t h, int level, const double *ec, double *xf, void
     if ((rc = to_level(h, F.L, xd, F.x, s))) return rc;
     auto run = [&](auto tag) {
         using T = decltype(tag);
-        launch_prolong<T>(F.L, C.L, (const T *)C.x, (T *)F.x, s);
+        launch_prolong<T>(F.L, C.L, (const T *)C.x, (T *)F.x, s, F.ptile);
     };
     if (h->prec == STOKES_PREC_FP64) run(double());
     else run(float());
