@@ -954,6 +954,8 @@ def main():
                                          for l in range(S32.levels - 1)],
             "transfer_tiles_per_level": [dict(zip(("restrict", "prolong", "ms"), smg.stokes_level_tiles(S32.h, l)))
                                          for l in range(S32.levels - 1)],
+            "dgs_velocity_per_level": [dict(zip(("fused", "ms_in_place_vs_fused"), smg.stokes_level_dgs(S32.h, l)))
+                                       for l in range(S32.levels - 1)],
             "iterations": [it for it, _ in its32], "rel_residual": [r for _, r in its32],
             "kernel_ms_per_iteration": {k: round(v[0], 4) for k, v in prof32.items()},
             "kernel_ms_per_iteration_level0": {k: round(v[2], 4) for k, v in prof32.items()},

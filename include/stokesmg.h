@@ -189,13 +189,16 @@ int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rh
  * colour, 1 = one cooperative launch per symmetric sweep with *blocks thread blocks (grid barrier),
  * 2 = one launch per symmetric sweep in a single thread-block cluster of *blocks CTAs (hardware
  * cluster barriers), 3 = one launch per symmetric sweep in one thread block working on a
- * shared-memory copy of the level (small levels only; *blocks = 1); *ms = the autotuner's time per
- * symmetric sweep (0 if not measured).  Any output pointer may be NULL. */
+ * shared-memory copy of the level (small levels only; *blocks = 1), 4 = one launch per colour step on
+ * two copies of the level's Vanka state (each step reads one and writes the other; *blocks = 0);
+ * *ms = the autotuner's time per symmetric sweep (0 if not measured).  Any output pointer may be
+ * NULL. */
 int stokes_level_schedule(stokes_t h, int level, int *mode, int *blocks, float *ms);
 /* override the schedule of one level (mode and blocks as above; blocks <= the co-resident limit for
  * mode 1, <= 16 for mode 2; mode 3 returns STOKES_ERR_UNSUPPORTED if the level does not fit in
- * shared memory); the handle's captured graphs are re-captured on next use.  All schedules compute
- * the same bits. */
+ * shared memory, mode 4 if the handle has no second state copy: additive Vanka, vanka_persistent, or
+ * a level of 2^31 entries or more); the handle's captured graphs are re-captured on next use.  All
+ * schedules compute the same bits. */
 int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks);
 
 /* tiles of the transfers between `level` and level + 1 (0 <= level < levels-1): tiles[0..2] = block x,
@@ -208,6 +211,17 @@ int stokes_level_tiles(stokes_t h, int level, int *tiles, float *ms);
 /* override them (block x * block y a multiple of 32 and at most 1024, 1 <= z-planes <= 64); the
  * handle's captured graphs are re-captured on next use */
 int stokes_set_level_tiles(stokes_t h, int level, const int *tiles);
+
+/* how the symmetric DGS of a smoothed level runs its velocity blocks (Alg. 2 / Eq. ldist): *fused = 0,
+ * two in-place launches per direction (one per parity of i+j+k); 1, one out-of-place pass per direction
+ * that relaxes both parities (the second a plane behind the first, overlapped tiles) into the handle's
+ * second state buffer and back.  *ms (optional, 2 floats) = the autotuner's time per symmetric DGS for
+ * 0 and 1 (0 if not measured).  With opts.autotune the faster is kept per level; both compute the same
+ * bits. */
+int stokes_level_dgs(stokes_t h, int level, int *fused, float *ms);
+/* override it (fused = 1 returns STOKES_ERR_UNSUPPORTED with the distributive weighted Jacobi or
+ * without a second state buffer); the handle's captured graphs are re-captured on next use */
+int stokes_set_level_dgs(stokes_t h, int level, int fused);
 
 /* *out = ||b - L x||_2 (FP64, deterministic reduction); synchronises the stream.  Uses the
  * handle's reduction scratch. */

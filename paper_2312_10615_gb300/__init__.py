@@ -25,7 +25,8 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            "stokes_num_levels", "stokes_rhs", "stokes_apply", "mg_precondition", "sqmr_solve",
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
            "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
-           "stokes_set_level_schedule", "stokes_level_tiles", "stokes_set_level_tiles", "sqmr_solve_unpreconditioned",
+           "stokes_set_level_schedule", "stokes_level_tiles", "stokes_set_level_tiles", "stokes_level_dgs",
+           "stokes_set_level_dgs", "sqmr_solve_unpreconditioned",
            "mg_solve",
            "stokes_measure_fma_peak", "stokes_label_flags", "stokes_test_grid_barrier", "stokes_strerror",
            # learned initial guess (include/warmstart.h)
@@ -102,6 +103,8 @@ def _load():
         "stokes_set_level_schedule": (i, [vp, i, i, i]),
         "stokes_level_tiles": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
         "stokes_set_level_tiles": (i, [vp, i, ctypes.POINTER(i)]),
+        "stokes_level_dgs": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
+        "stokes_set_level_dgs": (i, [vp, i, i]),
         "stokes_strerror": (ctypes.c_char_p, [i]),
         "warmstart_num_weights": (ll, []),
         "warmstart_create": (i, [i, i, d, ctypes.POINTER(vp)]),
@@ -314,6 +317,17 @@ def stokes_level_tiles(h, level):
 def stokes_set_level_tiles(h, level, restrict_tile, prolong_tile):
     t = (ctypes.c_int * 6)(*restrict_tile, *prolong_tile)
     _check(lib().stokes_set_level_tiles(h, level, t), "stokes_set_level_tiles")
+
+
+def stokes_level_dgs(h, level):
+    """(fused, (ms in place, ms fused)) of the symmetric DGS velocity passes on a smoothed level."""
+    f, m = ctypes.c_int(), (ctypes.c_float * 2)()
+    _check(lib().stokes_level_dgs(h, level, ctypes.byref(f), m), "stokes_level_dgs")
+    return f.value, (m[0], m[1])
+
+
+def stokes_set_level_dgs(h, level, fused):
+    _check(lib().stokes_set_level_dgs(h, level, int(fused)), "stokes_set_level_dgs")
 
 
 def stokes_residual_norm_noalloc(nx, ny, nz, h, viscosity, b, x, out, stream=None):

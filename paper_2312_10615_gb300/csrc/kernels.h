@@ -16,6 +16,11 @@ template <class T, class TB> void launch_apply(const Lev &L, const T *x, const T
 void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaStream_t s);
 // symmetric DGS pieces (Alg. 2 / Eq. ldist) on the V2 set
 template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, int parity, cudaStream_t s);
+// both velocity parities of one DGS stage (pa first) in one out-of-place pass X -> Y; Y receives every
+// packed entry; bit-identical to launch_dgs_u(pa) then launch_dgs_u(1 - pa) in place
+template <class T, class TB>
+void launch_dgs_u_fused(const Lev &L, const T *X, T *Y, const TB *b, int pa, cudaStream_t s);
+template <class T, class TB> bool dgs_u_fused_prepare();
 template <class T, class TB>
 void launch_dgs_p_fwd(const Lev &L, T *x, const TB *b, T *delta, int colour, cudaStream_t s);
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s);
@@ -61,6 +66,13 @@ void launch_vanka_sweep(const Lev &L, T *x, const TB *b, const VankaLists &lists
                         int sweeps, GridBarrier *bar, int max_blocks, cudaStream_t s, int missing_blocks = 0,
                         unsigned spin_limit = kBarrierSpinLimit);
 template <class T, class TB> int vanka_sweep_blocks_per_sm();
+// `sweeps` symmetric Vanka sweeps, one launch per colour step on two copies of the state (x and x2,
+// ping-pong; x2 holds 0 off the unknowns), after copying the nshell DOFs the patches read or write
+// (shell) from x to x2 at the start of each sweep; the result is in x, bit-identical to the
+// two-launch form
+template <class T, class TB>
+void launch_vanka_pingpong(const Lev &L, T *x, T *x2, const TB *b, const VankaLists &lists, const int *shell,
+                           int nshell, const T *kinv, int sweeps, cudaStream_t s);
 // one symmetric Vanka sweep (x sweeps) in a single thread-block cluster of `cluster` CTAs x 1024
 // threads separated by hardware cluster barriers (no software wait); returns the launch status
 template <class T, class TB> cudaError_t vanka_cluster_prepare();

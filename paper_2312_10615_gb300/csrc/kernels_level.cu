@@ -228,12 +228,26 @@ void launch_rhs(const Lev &L, const double *f, const double *g, double *b, cudaS
 // Cell-centric: the thread of V2 cell (i,j,k) of the given parity updates its low faces u, v, w (all
 // three share the cell's parity), each if it lies in that component's V2 range.  Inside the V2
 // cell range every stencil neighbour exists, so no guards are needed.
+// one relaxed velocity face: x0 + (b - (eh2 (6 x0 - neighbours) + ih (p_plus - p_minus))) / (6 eh2).
+// The multiply-adds are spelled out as fma() calls, so every kernel that relaxes a face (the in-place
+// parity launches and the fused two-parity pass) rounds the same way and produces the same bits.
+template <class T>
+__device__ __forceinline__ T dgs_relax(T x0, T nxm, T nxp, T nym, T nyp, T nzm, T nzp, T pc, T pm, T bv,
+                                       const Coef<T> &K) {
+    T s = fma(T(6), x0, -nxm);
+    s = s - nxp;
+    s = s - nym;
+    s = s - nyp;
+    s = s - nzm;
+    s = s - nzp;
+    const T g = K.ih * (pc - pm);
+    const T r = bv - fma(K.eh2, s, g);
+    return x0 + r / (T(6) * K.eh2);
+}
 template <class T, class TB, class IDX>
 __device__ __forceinline__ void dgs_face(T *__restrict__ xq, const TB *__restrict__ bq, IDX sy, IDX sz, T pc, T pm,
                                          const Coef<T> &K) {
-    T s = T(6) * xq[0] - xq[-1] - xq[1] - xq[-sy] - xq[sy] - xq[-sz] - xq[sz];
-    T r = T(ldv(bq[0])) - (K.eh2 * s + K.ih * (pc - pm));
-    xq[0] += r / (T(6) * K.eh2);
+    xq[0] = dgs_relax<T>(xq[0], xq[-1], xq[1], xq[-sy], xq[sy], xq[-sz], xq[sz], pc, pm, T(ldv(bq[0])), K);
 }
 
 template <class T, class TB, class IDX>
@@ -274,6 +288,179 @@ template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, 
     dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), L.nz - 2);
     if (idx32(L)) launch_k(k_dgs_u<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
     else launch_k(k_dgs_u<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
+}
+
+// ------------------------------------------------------------------------------------------
+// The velocity block of Alg. 2 / Eq. ldist, both parities in one pass, out of place (X read, Y
+// written).  Phase A relaxes the V2 faces of parity pa from X, phase B those of parity 1 - pa from
+// the phase-A values -- the two in-place launches of k_dgs_u, the same arithmetic per face.  Blocks
+// own a 32 x 8 tile of cell positions and march a chunk of FZ planes in z: at plane k they run phase A
+// on the tile and a one-position ring around it (recomputed by the neighbouring blocks too:
+// overlapped tiling, so no block waits for another), then phase B on the tile at plane k-1, whose six
+// neighbours' phase-A values (planes k-2..k) are then final.  X is staged in shared memory four
+// planes deep with a two-position halo, the phase-A values three planes deep with a one-position ring.
+// Every packed entry of a position is written to Y once: an updated face, or X's value.
+constexpr int FX = 32, FY = 8, FZ = 16;
+constexpr int WX = FX + 4, WY = FY + 4;  // X window: tile + 2-position halo
+constexpr int AX = FX + 2, AY = FY + 2;  // phase-A window: tile + 1-position ring
+
+template <class T> struct DgsFusedSmem {
+    T x[4][4][WY][WX];  // [plane slot][component u v w p][y][x]
+    T a[3][3][AY][AX];  // [plane slot][component u v w][y][x]
+};
+
+// is face (c; i, j, k) a V2 face (relaxed by the DGS)?  i, j, k inside the component's array
+__device__ __forceinline__ bool dgs_v2_face(const Lev &L, int c, int i, int j, int k, long long q) {
+    const int n[3] = {L.nx, L.ny, L.nz}, id[3] = {i, j, k};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int lo = d == c ? 2 : 1, hi = n[d] - 2;
+        if (id[d] < lo || id[d] > hi) return false;
+    }
+    return !L.flags || (L.flags[q] & kFlagV2);
+}
+
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(FX * FY, 3) k_dgs_u_fused(Lev L, const T *__restrict__ X, T *__restrict__ Y,
+                                                            const TB *__restrict__ b, int pa, Coef<T> K) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    DgsFusedSmem<T> &S = *reinterpret_cast<DgsFusedSmem<T> *>(fsm);
+    pdl_wait();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY, k0 = blockIdx.z * FZ;
+    const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
+    // window positions this thread stages: (tx, ty), (tx + FX, ty), (tx, ty + FY), (tx + FX, ty + FY)
+    const bool hx = tx < WX - FX, hy = ty < WY - FY;
+    // packed offset of component C at cell position (i, j, k); in_arr: the entry exists
+    auto in_arr = [&](int c, int i, int j, int k) {
+        return i >= 0 && j >= 0 && k >= 0 && i < L.nx + (c == 0) && j < L.ny + (c == 1) && k < L.nz + (c == 2);
+    };
+    auto off = [&](int c, int i, int j, int k) -> IDX {
+        const IDX syc = c == 0 ? nx + 1 : nx;
+        const IDX szc = c == 0 ? (nx + 1) * ny : (c == 1 ? nx * (ny + 1) : nx * ny);
+        return (IDX)i + syc * (IDX)j + szc * (IDX)k;
+    };
+    const T *Xc[4] = {X + L.off[0], X + L.off[1], X + L.off[2], X + L.off[3]};
+    T *Yc[4] = {Y + L.off[0], Y + L.off[1], Y + L.off[2], Y + L.off[3]};
+    const TB *Bc[3] = {b + L.off[0], b + L.off[1], b + L.off[2]};
+    // registers holding the next plane's window values while the current plane is computed
+    T pre[4][4];
+    auto fetch = [&](int gk) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int xx = tx + ((q & 1) ? FX : 0), yy = ty + ((q & 2) ? FY : 0);
+                const bool want = ((q & 1) ? hx : true) && ((q & 2) ? hy : true);
+                const int gi = i0 - 2 + xx, gj = j0 - 2 + yy;
+                pre[c][q] = (want && in_arr(c, gi, gj, gk)) ? Xc[c][off(c, gi, gj, gk)] : T(0);
+            }
+    };
+    auto store = [&](int gk) {
+        const int sl = (gk + 4) & 3;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int xx = tx + ((q & 1) ? FX : 0), yy = ty + ((q & 2) ? FY : 0);
+                const bool want = ((q & 1) ? hx : true) && ((q & 2) ? hy : true);
+                if (want) S.x[sl][c][yy][xx] = pre[c][q];
+            }
+    };
+    auto relax = [&](T x0, T nxm, T nxp, T nym, T nyp, T nzm, T nzp, T pc, T pm, T bv) {
+        return dgs_relax<T>(x0, nxm, nxp, nym, nyp, nzm, nzp, pc, pm, bv, K);
+    };
+    fetch(k0 - 2);
+    store(k0 - 2);
+    fetch(k0 - 1);
+    store(k0 - 1);
+    fetch(k0);
+    for (int st = 0; st <= FZ + 1; ++st) {
+        const int k = k0 - 1 + st;  // phase A at plane k, phase B at plane k - 1
+        store(k + 1);
+        __syncthreads();
+        if (st <= FZ) fetch(k + 2);  // in flight while this plane is computed
+        // phase A on tile + ring at plane k
+        {
+            const int xs = (k + 4) & 3, xm = (k + 3) & 3, xp = (k + 5) & 3, as = (k + 3) % 3;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int xx = tx + ((q & 1) ? FX : 0), yy = ty + ((q & 2) ? FY : 0);
+                if (xx >= AX || yy >= AY) continue;
+                const int gi = i0 - 1 + xx, gj = j0 - 1 + yy;
+                const int wx = xx + 1, wy = yy + 1;
+                const bool par = ((gi + gj + k) & 1) == pa;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    T v = S.x[xs][c][wy][wx];
+                    if (par && k >= 0 && in_arr(c, gi, gj, k)) {
+                        const IDX o = off(c, gi, gj, k);
+                        if (dgs_v2_face(L, c, gi, gj, k, L.off[c] + o)) {
+                            const T pm = c == 0 ? S.x[xs][3][wy][wx - 1]
+                                                : (c == 1 ? S.x[xs][3][wy - 1][wx] : S.x[xm][3][wy][wx]);
+                            v = relax(v, S.x[xs][c][wy][wx - 1], S.x[xs][c][wy][wx + 1], S.x[xs][c][wy - 1][wx],
+                                      S.x[xs][c][wy + 1][wx], S.x[xm][c][wy][wx], S.x[xp][c][wy][wx],
+                                      S.x[xs][3][wy][wx], pm, T(ldv(Bc[c][o])));
+                        }
+                    }
+                    S.a[as][c][yy][xx] = v;
+                }
+            }
+        }
+        __syncthreads();
+        // phase B on the tile at plane k - 1, and the tile's entries of Y at that plane
+        const int kb = k - 1;
+        if (kb >= k0 && kb < k0 + FZ && kb <= L.nz) {
+            const int gi = i0 + tx, gj = j0 + ty;
+            const int wx = tx + 2, wy = ty + 2, ax = tx + 1, ay = ty + 1;
+            const int xs = (kb + 4) & 3, xm = (kb + 3) & 3;
+            const int as = (kb + 3) % 3, am = (kb + 2) % 3, ap = (kb + 4) % 3;
+            const bool par_a = ((gi + gj + kb) & 1) == pa;
+            if (gi <= L.nx && gj <= L.ny) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (!in_arr(c, gi, gj, kb)) continue;
+                    const IDX o = off(c, gi, gj, kb);
+                    T v;
+                    if (par_a) {
+                        v = S.a[as][c][ay][ax];
+                    } else if (dgs_v2_face(L, c, gi, gj, kb, L.off[c] + o)) {
+                        const T pm = c == 0 ? S.x[xs][3][wy][wx - 1]
+                                            : (c == 1 ? S.x[xs][3][wy - 1][wx] : S.x[xm][3][wy][wx]);
+                        v = relax(S.x[xs][c][wy][wx], S.a[as][c][ay][ax - 1], S.a[as][c][ay][ax + 1],
+                                  S.a[as][c][ay - 1][ax], S.a[as][c][ay + 1][ax], S.a[am][c][ay][ax],
+                                  S.a[ap][c][ay][ax], S.x[xs][3][wy][wx], pm, T(ldv(Bc[c][o])));
+                    } else {
+                        v = S.x[xs][c][wy][wx];
+                    }
+                    Yc[c][o] = v;
+                }
+                if (in_arr(3, gi, gj, kb)) Yc[3][off(3, gi, gj, kb)] = S.x[xs][3][wy][wx];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class T, class TB> size_t dgs_u_fused_smem() { return sizeof(DgsFusedSmem<T>); }
+
+// the shared-memory opt-in of the fused kernel, set once outside any capture
+template <class T, class TB> bool dgs_u_fused_prepare() {
+    return cudaFuncSetAttribute(k_dgs_u_fused<T, TB, int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(DgsFusedSmem<T>)) == cudaSuccess &&
+           cudaFuncSetAttribute(k_dgs_u_fused<T, TB, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(DgsFusedSmem<T>)) == cudaSuccess;
+}
+
+template <class T, class TB>
+void launch_dgs_u_fused(const Lev &L, const T *X, T *Y, const TB *b, int pa, cudaStream_t s) {
+    dim3 grid(cdiv(L.nx + 1, FX), cdiv(L.ny + 1, FY), cdiv(L.nz + 1, FZ));
+    if (idx32(L))
+        launch_k(k_dgs_u_fused<T, TB, int>, grid, dim3(FX, FY, 1), sizeof(DgsFusedSmem<T>), s, L, X, Y, b, pa,
+                 coef<T>(L, L.gamma));
+    else
+        launch_k(k_dgs_u_fused<T, TB, long long>, grid, dim3(FX, FY, 1), sizeof(DgsFusedSmem<T>), s, L, X, Y, b, pa,
+                 coef<T>(L, L.gamma));
 }
 
 // Alg. 2 pressure block, one colour (i mod 2, j mod 2, k mod 2):
@@ -860,23 +1047,63 @@ __device__ __forceinline__ T vanka_face_residual(const Lev &L, const T *__restri
     return T(ldv(b[q])) - (K.eh2 * s + K.ih * (pc[0] - pc[-ps]));
 }
 
-template <class T, class TB>
+// the face-lane residual of vanka_face_residual and the pressure-lane residual of cell_Lx_fast with
+// IDX-wide offsets (32-bit where the level allows): the same loads and the same arithmetic in the
+// same order, fewer address instructions
+template <class T, class TB, class IDX>
+__device__ __forceinline__ T vanka_residual_idx(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b, int a,
+                                                int i, int j, int k, const Coef<T> &K) {
+    const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
+    if (a == 6) {
+        const IDX cl = (IDX)i + nx * ((IDX)j + ny * (IDX)k);
+        const T *u = x + L.off[0] + ((IDX)i + (nx + 1) * ((IDX)j + ny * (IDX)k));
+        const T *v = x + L.off[1] + ((IDX)i + nx * ((IDX)j + (ny + 1) * (IDX)k));
+        const T *w = x + L.off[2] + cl;
+        const T div = (u[1] - u[0]) + (v[nx] - v[0]) + (w[nx * ny] - w[0]);
+        return T(ldv(b[L.off[3] + cl])) - (-K.ih * div - K.gam * x[L.off[3] + cl]);
+    }
+    const int d = a >> 1, side = a & 1;
+    const int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+    const IDX sy = nx + (IDX)(d == 0), sz = sy * (ny + (IDX)(d == 1));
+    const long long base = d == 0 ? L.off[0] : (d == 1 ? L.off[1] : L.off[2]);
+    const IDX o = (IDX)fi + sy * (IDX)fj + sz * (IDX)fk;
+    const T *xc = x + base + o;
+    const bool xm = d == 0 || fi > 0, xp = d == 0 || fi < L.nx - 1;
+    const bool ym = d == 1 || fj > 0, yp = d == 1 || fj < L.ny - 1;
+    const bool zm = d == 2 || fk > 0, zp = d == 2 || fk < L.nz - 1;
+    T s = T(6) * xc[0];
+    T xl = xm ? xc[-1] : T(0), xh = xp ? xc[1] : T(0), yl = ym ? xc[-sy] : T(0), yh = yp ? xc[sy] : T(0);
+    T zl = zm ? xc[-sz] : T(0), zh = zp ? xc[sz] : T(0);
+    if (L.flags) {
+        const uint8_t f = L.flags[base + o];
+        s = diag_weight<T>(f) * xc[0];
+        if (f & kFlagDropLo) (d == 0 ? xl : (d == 1 ? yl : zl)) = T(0);
+        if (f & kFlagDropHi) (d == 0 ? xh : (d == 1 ? yh : zh)) = T(0);
+    }
+    s -= xl + xh;
+    s -= yl + yh;
+    s -= zl + zh;
+    const T *pc = x + L.off[3] + ((IDX)fi + nx * ((IDX)fj + ny * (IDX)fk));
+    const IDX ps = d == 0 ? (IDX)1 : (d == 1 ? nx : nx * ny);
+    return T(ldv(b[base + o])) - (K.eh2 * s + K.ih * (pc[0] - pc[-ps]));
+}
+
+template <class T, class TB, class IDX = long long>
 __device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
                                                    int cellw, int a, unsigned gmask, const T *__restrict__ kinv,
                                                    T *__restrict__ corr, int cap, int slot, const Coef<T> &K,
                                                    T w = T(1), const int *__restrict__ tab = nullptr) {
     int i, j, k;
     unpack_cell(cellw, i, j, k);
-    // which of the cell's six faces are unknowns (6-bit configuration of the pre-factorised inverses)
-    const int cfg = (int)unknown(L, 0, i, j, k) | ((int)unknown(L, 0, i + 1, j, k) << 1) |
-                    ((int)unknown(L, 1, i, j, k) << 2) | ((int)unknown(L, 1, i, j + 1, k) << 3) |
-                    ((int)unknown(L, 2, i, j, k) << 4) | ((int)unknown(L, 2, i, j, k + 1) << 5);
+    // which of the cell's six faces are unknowns (6-bit configuration of the pre-factorised inverses);
+    // on the box a face of a cell is one unless it lies on a wall
+    const int cfg = L.flags ? ((int)unknown(L, 0, i, j, k) | ((int)unknown(L, 0, i + 1, j, k) << 1) |
+                               ((int)unknown(L, 1, i, j, k) << 2) | ((int)unknown(L, 1, i, j + 1, k) << 3) |
+                               ((int)unknown(L, 2, i, j, k) << 4) | ((int)unknown(L, 2, i, j, k + 1) << 5))
+                            : ((int)(i > 0) | ((int)(i < L.nx - 1) << 1) | ((int)(j > 0) << 2) |
+                               ((int)(j < L.ny - 1) << 3) | ((int)(k > 0) << 4) | ((int)(k < L.nz - 1) << 5));
     T r = T(0);
-    if (a < 6) {
-        if ((cfg >> a) & 1) r = vanka_face_residual(L, x, b, a, i, j, k, K);
-    } else if (a == 6) {
-        r = T(ldv(b[pidx(L, 3, i, j, k)])) - cell_Lx_fast(x, L, i, j, k, K);
-    }
+    if (a == 6 || (a < 6 && ((cfg >> a) & 1))) r = vanka_residual_idx<T, TB, IDX>(L, x, b, a, i, j, k, K);
     // label domains with exterior cells: the cell's own entry of the level's inverse table (its faces'
     // dropped terms change the local matrix); otherwise the 6-bit configuration indexes it
     const int id = tab ? tab[slot] : cfg;
@@ -910,7 +1137,7 @@ __device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x
     if (act) x[q] += corr[(long long)a * cap + slot];
 }
 
-template <class T, class TB>
+template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                        const int *__restrict__ cells, const int *__restrict__ tab,
                                                        int ncell, const T *__restrict__ kinv, T *__restrict__ corr,
@@ -919,7 +1146,8 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3;
     if (slot >= ncell) return;  // whole 8-lane groups leave together
-    vanka_compute_lane(L, x, b, cells[slot], t & 7, 0xffu << (threadIdx.x & 24), kinv, corr, cap, slot, K, w, tab);
+    vanka_compute_lane<T, TB, IDX>(L, x, b, cells[slot], t & 7, 0xffu << (threadIdx.x & 24), kinv, corr, cap, slot, K,
+                                   w, tab);
 }
 
 template <class T>
@@ -936,13 +1164,146 @@ template <class T, class TB>
 void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cells, const int *tab, int ncell,
                           const T *kinv, T *corr, int cap, double w, cudaStream_t s) {
     if (ncell <= 0) return;
-    launch_k(k_vanka_compute<T, TB>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, tab, ncell, kinv, corr,
-             cap, coef<T>(L, L.gamma), T(w));
+    if (idx32(L))
+        launch_k(k_vanka_compute<T, TB, int>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, tab, ncell,
+                 kinv, corr, cap, coef<T>(L, L.gamma), T(w));
+    else
+        launch_k(k_vanka_compute<T, TB, long long>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, tab,
+                 ncell, kinv, corr, cap, coef<T>(L, L.gamma), T(w));
 }
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s) {
     if (ncell <= 0) return;
     launch_k(k_vanka_apply<T>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, cells, ncell, corr, cap);
+}
+
+// ---- one launch per colour step: two copies of the level's Vanka state (ping-pong) ----
+// Step t (colour c) reads the state R and writes W: every DOF of a colour-c patch gets R + its patch
+// correction (computed from R, the pre-colour state, exactly as the two-launch form), and every DOF of a
+// patch of the previous step's colour that no colour-c patch holds gets R's value; W already equals R
+// everywhere else (it was the state of the step before, which differed from R only on the previous
+// colour's patches).  So W is the post-colour state and no grid-wide order is needed inside the step.
+// Same-colour patches share no DOF and a DOF of the previous colour's patch shared with a colour-c
+// patch is written by the colour-c lane only, so every entry of W is written by at most one thread.
+// Both copies agree on the ring of V2 DOFs the patches read (k_vanka_shell_copy at the start of each
+// sweep) and hold 0 off the unknowns.  An even number of steps (16 per symmetric sweep) returns the
+// state to the level's own vector.
+template <class T>
+__device__ __forceinline__ bool vanka_dof(const Lev &L, int cellw, int a, long long &q, int &d) {
+    int i, j, k;
+    unpack_cell(cellw, i, j, k);
+    const long long nx = L.nx, ny = L.ny;
+    if (a == 6) {
+        q = L.off[3] + (i + nx * (j + ny * k));
+        d = -1;
+        return true;
+    }
+    d = a >> 1;
+    const int side = a & 1;
+    const int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+    const long long sy = nx + (d == 0), sz = sy * (ny + (d == 1));
+    q = (d == 0 ? L.off[0] : (d == 1 ? L.off[1] : L.off[2])) + fi + sy * fj + sz * fk;
+    const int nrm = d == 0 ? fi : (d == 1 ? fj : fk), nn = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
+    return nrm >= 1 && nrm <= nn - 1 && (!L.flags || (L.flags[q] & kFlagActive));
+}
+// is the cell across face a of cell (i,j,k) a V1 cell of colour c?
+__device__ __forceinline__ bool across_is_v1_of_colour(const Lev &L, int cellw, int a, int c) {
+    int i, j, k;
+    unpack_cell(cellw, i, j, k);
+    const int d = a >> 1, sg = (a & 1) ? 1 : -1;
+    const int ni = i + (d == 0 ? sg : 0), nj = j + (d == 1 ? sg : 0), nk = k + (d == 2 ? sg : 0);
+    if (ni < 0 || nj < 0 || nk < 0 || ni >= L.nx || nj >= L.ny || nk >= L.nz) return false;
+    const int col = (ni & 1) | ((nj & 1) << 1) | ((nk & 1) << 2);
+    if (col != c) return false;
+    if (L.flags) {
+        const uint8_t f = L.flags[pidx(L, 3, ni, nj, nk)];
+        return (f & kFlagActive) && !(f & kFlagV2);
+    }
+    return !v2_cell_at(L, ni, nj, nk);
+}
+
+template <class T, class TB, class IDX>
+__global__ void __launch_bounds__(256) k_vanka_step(Lev L, const T *__restrict__ R, T *__restrict__ W,
+                                                    const TB *__restrict__ b, const int *__restrict__ cells,
+                                                    const int *__restrict__ tab, int ncell,
+                                                    const int *__restrict__ pcells, int npcell, int colour,
+                                                    const T *__restrict__ kinv, Coef<T> K) {
+    pdl_wait();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slot = t >> 3, a = t & 7;
+    if (slot < ncell) {
+        // the patch correction, as vanka_compute_lane, written as R + correction into W
+        const int cellw = cells[slot];
+        int i, j, k;
+        unpack_cell(cellw, i, j, k);
+        // which faces are unknowns: on the box a face of a cell is one unless it lies on a wall
+        const int cfg = L.flags ? ((int)unknown(L, 0, i, j, k) | ((int)unknown(L, 0, i + 1, j, k) << 1) |
+                                   ((int)unknown(L, 1, i, j, k) << 2) | ((int)unknown(L, 1, i, j + 1, k) << 3) |
+                                   ((int)unknown(L, 2, i, j, k) << 4) | ((int)unknown(L, 2, i, j, k + 1) << 5))
+                                : ((int)(i > 0) | ((int)(i < L.nx - 1) << 1) | ((int)(j > 0) << 2) |
+                                   ((int)(j < L.ny - 1) << 3) | ((int)(k > 0) << 4) | ((int)(k < L.nz - 1) << 5));
+        T r = T(0);
+        if (a == 6 || (a < 6 && ((cfg >> a) & 1))) r = vanka_residual_idx<T, TB, IDX>(L, R, b, a, i, j, k, K);
+        const int id = tab ? tab[slot] : cfg;
+        const T *Ki = kinv + id * 49 + (a < 7 ? a : 6) * 7;
+        const unsigned gmask = 0xffu << (threadIdx.x & 24);
+        T sacc = T(0);
+#pragma unroll
+        for (int bb = 0; bb < 7; ++bb) sacc += Ki[bb] * __shfl_sync(gmask, r, bb, 8);
+        long long q;
+        int d;
+        if (a < 7 && vanka_dof<T>(L, cellw, a, q, d)) W[q] = R[q] + T(1) * sacc;
+        return;
+    }
+    const int ps = slot - ncell;
+    if (ps >= npcell || a == 7) return;
+    // a DOF of the previous colour's patch: carry R's value over unless a colour-c patch writes it
+    const int cellw = pcells[ps];
+    long long q;
+    int d;
+    if (!vanka_dof<T>(L, cellw, a, q, d)) return;
+    if (d >= 0 && across_is_v1_of_colour(L, cellw, a, colour)) return;
+    W[q] = R[q];
+}
+
+// the second copy takes the level's current values on every DOF a Vanka patch reads or writes
+template <class T>
+__global__ void __launch_bounds__(256) k_vanka_shell_copy(const T *__restrict__ x, T *__restrict__ x2,
+                                                          const int *__restrict__ list, int n) {
+    pdl_wait();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const int q = list[t];
+        x2[q] = x[q];
+    }
+}
+
+template <class T, class TB>
+void launch_vanka_pingpong(const Lev &L, T *x, T *x2, const TB *b, const VankaLists &lists, const int *shell,
+                           int nshell, const T *kinv, int sweeps, cudaStream_t s) {
+    const Coef<T> K = coef<T>(L, L.gamma);
+    for (int sw = 0; sw < sweeps; ++sw) {
+        if (nshell > 0)
+            launch_k(k_vanka_shell_copy<T>, dim3(cdiv(nshell, 256)), dim3(256), 0, s, (const T *)x, x2, shell, nshell);
+        int prev = -1;
+        for (int t = 0; t < 16; ++t) {
+            const int c = t < 8 ? t : 15 - t;
+            const T *R = (t & 1) ? x2 : x;
+            T *W = (t & 1) ? x : x2;
+            const int nc = lists.count[c];
+            const int np = (prev >= 0 && prev != c) ? lists.count[prev] : 0;
+            const int *pc = prev >= 0 ? lists.cells[prev] : nullptr;
+            if (nc + np > 0) {
+                if (idx32(L))
+                    launch_k(k_vanka_step<T, TB, int>, dim3(cdiv(8LL * (nc + np), 256)), dim3(256), 0, s, L, R, W, b,
+                             lists.cells[c], lists.tab[c], nc, pc, np, c, kinv, K);
+                else
+                    launch_k(k_vanka_step<T, TB, long long>, dim3(cdiv(8LL * (nc + np), 256)), dim3(256), 0, s, L, R,
+                             W, b, lists.cells[c], lists.tab[c], nc, pc, np, c, kinv, K);
+            }
+            prev = c;
+        }
+    }
 }
 
 // ---- one cooperative launch per symmetric Vanka sweep ----
@@ -1551,6 +1912,8 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
 #define SMG_INST_TB(T, TB)                                                                                          \
     template void launch_apply<T, TB>(const Lev &, const T *, const TB *, TB *, double, cudaStream_t);             \
     template void launch_dgs_u<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                           \
+    template void launch_dgs_u_fused<T, TB>(const Lev &, const T *, T *, const TB *, int, cudaStream_t);           \
+    template bool dgs_u_fused_prepare<T, TB>();                                                                   \
     template void launch_dgs_p_fwd<T, TB>(const Lev &, T *, const TB *, T *, int, cudaStream_t);                  \
     template void launch_dgs_p_bwd_prep<T, TB>(const Lev &, T *, const TB *, TB *, const T *, cudaStream_t);      \
     template void launch_dgs_p_bwd<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                       \
@@ -1558,6 +1921,8 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
     template bool launch_dgs_p_bwd_pair<T, TB>(const Lev &, T *, const TB *, int, cudaStream_t);                   \
     template void launch_vanka_compute<T, TB>(const Lev &, const T *, const TB *, const int *, const int *, int,   \
                                               const T *, T *, int, double, cudaStream_t);                           \
+    template void launch_vanka_pingpong<T, TB>(const Lev &, T *, T *, const TB *, const VankaLists &, const int *, \
+                                               int, const T *, int, cudaStream_t);                                \
     template void launch_vanka_sweep<T, TB>(const Lev &, T *, const TB *, const VankaLists &, const T *, T *, int,  \
                                             int, GridBarrier *, int, cudaStream_t, int, unsigned);                  \
     template cudaError_t vanka_cluster_prepare<T, TB>();                                                          \

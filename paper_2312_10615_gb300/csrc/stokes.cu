@@ -41,10 +41,17 @@ struct LevelBuf {
     int *vtab[8] = {};  // per-cell entries of the inverse table (label domains with exterior cells only)
     int vcount[8] = {};
     int ntab = 64;      // local inverses in kinv (64 configurations of unknown faces, plus exterior variants)
+    void *x2 = nullptr;  // second copy of the level's state (one-launch-per-colour Vanka, fused velocity DGS),
+                         // 0 off the unknowns
+    int ufused = 0;      // symmetric DGS with the fused out-of-place velocity passes
+    float ums[2] = {0.f, 0.f};  // autotuner's time per symmetric DGS: in-place launches, fused passes
+    int *shell = nullptr;  // the DOFs a Vanka patch reads or writes (copied into x2 at each sweep's start)
+    int nshell = 0;
     int vcap = 0;
     VankaLists lists;
     int vmode = 0, vblocks = 0;  // Vanka schedule: 0 per-colour launches, 1 cooperative sweep of vblocks blocks,
-                                 // 2 one-cluster sweep of vblocks CTAs
+                                 // 2 one-cluster sweep of vblocks CTAs, 3 one block on a shared-memory copy,
+                                 // 4 one launch per colour step on two copies of the state
     float vms = 0.f;             // autotuner's time per symmetric sweep
     Tile rtile, ptile;           // tiles of the restriction from / prolongation into this level
     float rms = 0.f, pms = 0.f;  // autotuner's time per launch of each
@@ -422,6 +429,13 @@ template <class T, class TB> void vanka_sym(stokes_s *h, int l, cudaStream_t s, 
         for (int k = 0; k < sweeps; ++k) vanka_additive<T, TB>(h, l, s);
         return;
     }
+    if (B.vmode == 4 && !h->vanka_persistent && B.x2 && B.shell) {
+        prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
+            launch_vanka_pingpong<T, TB>(B.L, (T *)B.x, (T *)B.x2, (const TB *)B.b, B.lists, B.shell, B.nshell,
+                                         (const T *)B.kinv, sweeps, s);
+        });
+        return;
+    }
     if (B.vmode == 3 && !h->vanka_persistent) {
         prof(STOKES_K_VANKA_COMPUTE, l, s, [&] {
             launch_vanka_smem<T, TB>(B.L, (T *)B.x, (const TB *)B.b, B.lists, (const T *)B.kinv, B.vcap, sweeps, s);
@@ -448,12 +462,20 @@ template <class T, class TB> void vanka_sym(stokes_s *h, int l, cudaStream_t s, 
         for (int c = 7; c >= 0; --c) vanka_colour<T, TB>(h, l, c, s);
     }
 }
-template <class T, class TB> void dgs_forward(stokes_s *h, int l, cudaStream_t s) {
+// fused: both velocity parities in one out-of-place pass from the level's x into its second buffer x2,
+// the pressure colours then run on x2, and dgs_backward's fused velocity pass brings the state back
+// into x (the symmetric DGS only; the same bits as the in-place launches)
+template <class T, class TB> void dgs_forward(stokes_s *h, int l, cudaStream_t s, bool fused = false) {
     LevelBuf &B = h->lev[l];
     T *x = (T *)B.x;
     const TB *b = (const TB *)B.b;
-    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
-    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
+    if (fused) {
+        prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u_fused<T, TB>(B.L, (const T *)B.x, (T *)B.x2, b, 0, s); });
+        x = (T *)B.x2;
+    } else {
+        prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
+        prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
+    }
     for (int c = 0; c < 8; c += 2)
         prof(STOKES_K_DGS_P_FWD, l, s, [&] {
             if (!launch_dgs_p_fwd_pair<T, TB>(B.L, x, b, (T *)B.delta, c, s)) {
@@ -467,9 +489,10 @@ template <class T> void dgs_finish_forward(stokes_s *h, int l, cudaStream_t s) {
     LevelBuf &B = h->lev[l];
     prof(STOKES_K_DGS_P_GATHER, l, s, [&] { launch_dgs_p_gather<T>(B.L, (T *)B.x, (const T *)B.delta, s); });
 }
-template <class T, class TB> void dgs_backward(stokes_s *h, int l, cudaStream_t s, bool forward_pending) {
+template <class T, class TB>
+void dgs_backward(stokes_s *h, int l, cudaStream_t s, bool forward_pending, bool fused = false) {
     LevelBuf &B = h->lev[l];
-    T *x = (T *)B.x;
+    T *x = fused ? (T *)B.x2 : (T *)B.x;
     const TB *b = (const TB *)B.b;
     prof(STOKES_K_DGS_P_BWD_PREP, l, s, [&] {
         launch_dgs_p_bwd_prep<T, TB>(B.L, x, b, (TB *)B.r, forward_pending ? (const T *)B.delta : nullptr, s);
@@ -481,8 +504,12 @@ template <class T, class TB> void dgs_backward(stokes_s *h, int l, cudaStream_t 
                 launch_dgs_p_bwd<T, TB>(B.L, x, (const TB *)B.r, c - 1, s);
             }
         });
-    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
-    prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
+    if (fused) {
+        prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u_fused<T, TB>(B.L, (const T *)B.x2, (T *)B.x, b, 1, s); });
+    } else {
+        prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 1, s); });
+        prof(STOKES_K_DGS_U, l, s, [&] { launch_dgs_u<T, TB>(B.L, x, b, 0, s); });
+    }
 }
 // Sec. 3.1 variant: symmetric distributive weighted Jacobi, weight 6/7 (the paper gives none; the
 // classical pointwise-Jacobi smoothing weight of the 7-point Laplacian)
@@ -495,8 +522,9 @@ template <class T, class TB> void dist_sym(stokes_s *h, int l, cudaStream_t s) {
         });
         return;
     }
-    dgs_forward<T, TB>(h, l, s);
-    dgs_backward<T, TB>(h, l, s, true);
+    const bool fused = B.ufused && B.x2;
+    dgs_forward<T, TB>(h, l, s, fused);
+    dgs_backward<T, TB>(h, l, s, true, fused);
 }
 template <class T, class TB> void smooth(stokes_s *h, int l, cudaStream_t s) {
     vanka_sym<T, TB>(h, l, s, h->kb);
@@ -698,6 +726,15 @@ int autotune_vanka(stokes_s *h, int nsm) {
                     best_blocks = nb;
                 }
             }
+            // one launch per colour step on two copies of the state
+            if (B.x2 && B.shell) {
+                const float ms = time_vanka<T, TB>(h, l, 4, 0, s);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    best_mode = 4;
+                    best_blocks = 0;
+                }
+            }
             // one block on a shared-memory copy of the level, where it fits
             if (B.ntab == 64 && vanka_smem_prepare<T, TB>(B.L, B.vcap)) {
                 const float ms = time_vanka<T, TB>(h, l, 3, 1, s);
@@ -785,6 +822,41 @@ int autotune_tiles(stokes_s *h) {
         const size_t es = h->prec == STOKES_PREC_FP64 ? sizeof(double) : sizeof(float);
         CK(cudaMemsetAsync(F.x, 0, es * F.L.n, s));
         CK(cudaMemsetAsync(C.x, 0, es * C.L.n, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+// ---- the velocity passes of the symmetric DGS: two in-place launches per stage, or one fused
+// out-of-place pass (x -> x2 -> x); with autotune the faster per level, timed on the level's buffers
+int setup_dgs_fused(stokes_s *h, bool tune) {
+    cudaStream_t s = h->cs;
+    bool ok = true;
+    if (h->prec == STOKES_PREC_FP64) ok = dgs_u_fused_prepare<double, double>();
+    else ok = dgs_u_fused_prepare<float, float>() && dgs_u_fused_prepare<float, bf16>();
+    cudaGetLastError();
+    for (int l = 0; l < h->nlev() - 1; ++l) {
+        LevelBuf &B = h->lev[l];
+        B.ufused = 0;
+        if (!ok || !B.x2 || h->dwj || !tune) continue;
+        float t[2] = {-1.f, -1.f};
+        for (int f = 0; f < 2; ++f) {
+            B.ufused = f;
+            auto run = [&](auto tt, auto tb) {
+                using T = decltype(tt);
+                using TB = decltype(tb);
+                t[f] = time_launches([&] { dist_sym<T, TB>(h, l, s); }, s, 5);
+            };
+            if (h->prec == STOKES_PREC_FP64) with_tb<double>(h, l, run);
+            else with_tb<float>(h, l, run);
+        }
+        B.ufused = (t[1] > 0.f && t[0] > 0.f && t[1] < t[0]) ? 1 : 0;
+        B.ums[0] = t[0];
+        B.ums[1] = t[1];
+        // the timing runs leave arbitrary values in the level's buffers: both copies back to 0
+        const size_t es = h->prec == STOKES_PREC_FP64 ? sizeof(double) : sizeof(float);
+        CK(cudaMemsetAsync(B.x, 0, es * B.L.n, s));
+        CK(cudaMemsetAsync(B.x2, 0, es * B.L.n, s));
     }
     CK(cudaStreamSynchronize(s));
     return 0;
@@ -1130,6 +1202,47 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
             std::vector<float> kf(kd.begin(), kd.end());
             CK(cudaMemcpy(B.kinv, kf.data(), sizeof(float) * 49 * B.ntab, cudaMemcpyHostToDevice));
         }
+        // the one-launch-per-colour Vanka schedule: a second copy of the state and the list of DOFs the
+        // patches read or write (patch unknowns, their same-component neighbours and the pressures beside
+        // each patch face)
+        if (L.n < (1LL << 31)) {
+            if ((rc = h->alloc(&B.x2, es * L.n))) return rc;
+            CK(cudaMemset(B.x2, 0, es * L.n));
+        }
+        if (B.x2 && !h->additive && !h->vanka_persistent) {
+            const std::vector<uint8_t> *fl = labelled ? &hflags[l] : nullptr;
+            auto unk = [&](int c, int i, int j, int k) {
+                return i >= 0 && j >= 0 && k >= 0 && i < ext(L, c, 0) && j < ext(L, c, 1) && k < ext(L, c, 2) &&
+                       active(L, c, i, j, k) && (!fl || ((*fl)[(size_t)pidx(L, c, i, j, k)] & kFlagActive));
+            };
+            std::vector<uint8_t> mark((size_t)L.n, 0);
+            auto put = [&](int c, int i, int j, int k) {
+                if (unk(c, i, j, k)) mark[(size_t)pidx(L, c, i, j, k)] = 1;
+            };
+            for (int c = 0; c < 8; ++c)
+                for (int w : cells[c]) {
+                    const int i = w & 2047, j = (w >> 11) & 2047, k = (w >> 22) & 1023;
+                    put(3, i, j, k);
+                    for (int a = 0; a < 6; ++a) {
+                        const int d = a >> 1, side = a & 1;
+                        const int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+                        if (!unk(d, fi, fj, fk)) continue;
+                        put(d, fi, fj, fk);
+                        for (int e = 0; e < 3; ++e)
+                            for (int sg = -1; sg <= 1; sg += 2)
+                                put(d, fi + sg * (e == 0), fj + sg * (e == 1), fk + sg * (e == 2));
+                        put(3, fi, fj, fk);
+                        put(3, fi - (d == 0), fj - (d == 1), fk - (d == 2));
+                    }
+                }
+            std::vector<int> shell;
+            for (size_t q = 0; q < mark.size(); ++q)
+                if (mark[q]) shell.push_back((int)q);
+            B.nshell = (int)shell.size();
+            if ((rc = h->alloc(&B.shell, sizeof(int) * (shell.size() + 1)))) return rc;
+            if (!shell.empty())
+                CK(cudaMemcpy(B.shell, shell.data(), sizeof(int) * shell.size(), cudaMemcpyHostToDevice));
+        }
     }
     // reduction scratch and scalar state (the SQMR vectors are allocated by the first sqmr_solve)
     {
@@ -1155,6 +1268,7 @@ int stokes_create(const stokes_grid_t *grid, const stokes_bc_t *bc, double visco
             if ((rc = autotune_vanka(h.get(), nsm))) return rc;
         }
         if (o.autotune && (rc = autotune_tiles(h.get()))) return rc;
+        if ((rc = setup_dgs_fused(h.get(), o.autotune != 0))) return rc;
     }
     CK(cudaDeviceSynchronize());
     *out = h.release();
@@ -1602,8 +1716,31 @@ int stokes_set_level_tiles(stokes_t h, int level, const int *tiles) {
     return STOKES_OK;
 }
 
+int stokes_level_dgs(stokes_t h, int level, int *fused, float *ms) {
+    if (!h || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
+    const LevelBuf &B = h->lev[level];
+    if (fused) *fused = B.ufused;
+    if (ms) {
+        ms[0] = B.ums[0];
+        ms[1] = B.ums[1];
+    }
+    return STOKES_OK;
+}
+
+int stokes_set_level_dgs(stokes_t h, int level, int fused) {
+    if (!h || level < 0 || level >= h->nlev() - 1 || (fused != 0 && fused != 1)) return STOKES_ERR_INVALID_ARG;
+    LevelBuf &B = h->lev[level];
+    if (fused && (!B.x2 || h->dwj)) return STOKES_ERR_UNSUPPORTED;
+    B.ufused = fused;
+    if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
+    if (h->g_iter) { cudaGraphExecDestroy(h->g_iter); h->g_iter = nullptr; }
+    if (h->g_iter_id) { cudaGraphExecDestroy(h->g_iter_id); h->g_iter_id = nullptr; }
+    return STOKES_OK;
+}
+
 int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
-    if (!h || level < 0 || level >= h->nlev() - 1 || mode < 0 || mode > 3) return STOKES_ERR_INVALID_ARG;
+    if (!h || level < 0 || level >= h->nlev() - 1 || mode < 0 || mode > 4) return STOKES_ERR_INVALID_ARG;
+    if (mode == 4 && !h->lev[level].shell) return STOKES_ERR_UNSUPPORTED;
     if (mode == 1 && (h->vanka_max_blocks <= 0 || blocks < 1 || blocks > h->vanka_max_blocks)) return STOKES_ERR_INVALID_ARG;
     if (mode == 2 && (blocks < 1 || blocks > 16)) return STOKES_ERR_INVALID_ARG;
     if (mode == 3) {
@@ -1628,7 +1765,7 @@ int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
     }
     LevelBuf &B = h->lev[level];
     B.vmode = mode;
-    B.vblocks = mode == 0 ? 0 : blocks;
+    B.vblocks = (mode == 0 || mode == 4) ? 0 : blocks;
     B.vms = 0.f;
     // the captured graphs hold the old schedule
     if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }

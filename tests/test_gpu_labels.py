@@ -192,6 +192,30 @@ def test_labelled_fp32_solve(name):
         assert abs(p.mean()) > 1e-6 * np.abs(p).max()  # not shifted: the exterior pressure 0 is the reference
 
 
+@pytest.mark.parametrize("name", ["porous32", "mixed32", "outlet48x24x16"])
+def test_labelled_one_launch_per_colour_step_bit_identical(name):
+    (nx, ny, nz), lab = DOMAINS[name]()
+    Sp = smg.Stokes(nx, ny, nz, precision=smg.PREC_FP32, autotune=False, labels=lab)
+    Sg = smg.Stokes(nx, ny, nz, precision=smg.PREC_FP32, autotune=False, labels=lab)
+    for l in range(Sg.levels - 1):
+        smg.stokes_set_level_schedule(Sg.h, l, 4, 0)
+    o = oracle.Oracle(nx, ny, nz, coarsest_max=8, labels=lab)
+    s = rand_masked(o, 15)
+    assert torch.equal(Sp.precondition(cuda(s)), Sg.precondition(cuda(s)))
+
+
+@pytest.mark.parametrize("name", ["porous32", "outlet48x24x16"])
+def test_labelled_fused_velocity_dgs_bit_identical(name):
+    (nx, ny, nz), lab = DOMAINS[name]()
+    Sp = smg.Stokes(nx, ny, nz, precision=smg.PREC_FP32, autotune=False, labels=lab)
+    Sf = smg.Stokes(nx, ny, nz, precision=smg.PREC_FP32, autotune=False, labels=lab)
+    for l in range(Sf.levels - 1):
+        smg.stokes_set_level_dgs(Sf.h, l, 1)
+    o = oracle.Oracle(nx, ny, nz, coarsest_max=8, labels=lab)
+    s = rand_masked(o, 16)
+    assert torch.equal(Sp.precondition(cuda(s)), Sf.precondition(cuda(s)))
+
+
 @pytest.mark.parametrize("mode,blocks", [(1, 8), (2, 8), (3, 1)])
 def test_labelled_vanka_schedules_bit_identical(mode, blocks):
     (nx, ny, nz), lab = DOMAINS["porous32"]()

@@ -231,6 +231,54 @@ def test_shared_memory_vanka_sweep_matches_per_colour_launches():
     Sm.close()
 
 
+@pytest.mark.parametrize("kb", [1, 2])
+@pytest.mark.parametrize("precision", [smg.PREC_FP64, smg.PREC_FP32, smg.PREC_MIXED_BF16])
+def test_one_launch_per_colour_step_matches_per_colour_launches(precision, kb):
+    # two copies of the Vanka state, one launch per colour step: bit-identical V-cycles and solves
+    n = 48
+    Sp = smg.Stokes(n, precision=precision, kb_vanka=kb, autotune=False)
+    Sg = smg.Stokes(n, precision=precision, kb_vanka=kb, autotune=False)
+    for l in range(Sg.levels - 1):
+        smg.stokes_set_level_schedule(Sg.h, l, 4, 0)
+        assert smg.stokes_level_schedule(Sg.h, l)[:2] == (4, 0)
+    s = cuda(np.random.default_rng(30).standard_normal(Sg.n))
+    assert torch.equal(Sp.precondition(s), Sg.precondition(s))
+    b = Sg.rhs(synthetic.bumps(n, seed=6, device=DEV)["f"], None)
+    xp, ip = Sp.solve(b, tol=1e-8)
+    xg, ig = Sg.solve(b, tol=1e-8)
+    assert ip.iterations == ig.iterations and torch.equal(xp, xg)
+    Sp.close()
+    Sg.close()
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 64), (48, 24, 16)])
+@pytest.mark.parametrize("precision", [smg.PREC_FP64, smg.PREC_FP32, smg.PREC_MIXED_BF16])
+def test_fused_velocity_dgs_matches_in_place_launches(precision, dims):
+    # both velocity parities of a DGS stage in one out-of-place pass: the same bits as the two
+    # in-place launches, for the V-cycle, one symmetric DGS sweep and a whole solve
+    nx, ny, nz = dims
+    Sp = smg.Stokes(nx, ny, nz, precision=precision, autotune=False)
+    Sf = smg.Stokes(nx, ny, nz, precision=precision, autotune=False)
+    for l in range(Sf.levels - 1):
+        assert smg.stokes_level_dgs(Sp.h, l)[0] == 0
+        smg.stokes_set_level_dgs(Sf.h, l, 1)
+        assert smg.stokes_level_dgs(Sf.h, l)[0] == 1
+    s = cuda(np.random.default_rng(31).standard_normal(Sf.n))
+    assert torch.equal(Sp.precondition(s), Sf.precondition(s))
+    xs, bs = cuda(np.random.default_rng(32).standard_normal(Sf.n)), cuda(np.random.default_rng(33).standard_normal(Sf.n))
+    a, c = xs.clone(), xs.clone()
+    smg.stokes_smooth(Sp.h, 0, 1, a, bs)
+    smg.stokes_smooth(Sf.h, 0, 1, c, bs)
+    assert torch.equal(a, c)
+    if nx == ny == nz:
+        b = Sf.rhs(synthetic.bumps(nx, seed=7, device=DEV)["f"], None)
+        xp, ip = Sp.solve(b, tol=1e-8)
+        xf, i_f = Sf.solve(b, tol=1e-8)
+        assert ip.iterations == i_f.iterations and torch.equal(xp, xf)
+    Sp.close()
+    Sf.close()
+
+
 @pytest.mark.parametrize("precision", [smg.PREC_FP64, smg.PREC_FP32, smg.PREC_MIXED_BF16])
 def test_autotuned_schedule_is_bit_identical(precision):
     # the autotuner only picks how the Vanka sweeps are launched, never what they compute
@@ -238,7 +286,7 @@ def test_autotuned_schedule_is_bit_identical(precision):
     Sp = smg.Stokes(64, precision=precision, autotune=False)
     for l in range(Sa.levels - 1):
         mode, blocks, ms = smg.stokes_level_schedule(Sa.h, l)
-        assert mode in (0, 1, 2, 3) and ms > 0 and (mode == 0 or blocks >= 1)
+        assert mode in (0, 1, 2, 3, 4) and ms > 0 and (mode in (0, 4) or blocks >= 1)
     s = cuda(np.random.default_rng(27).standard_normal(Sa.n))
     assert float(torch.max(torch.abs(Sa.precondition(s) - Sp.precondition(s)))) == 0.0
     b = Sa.rhs(synthetic.bumps(64, seed=4, device=DEV)["f"], None)
