@@ -301,6 +301,19 @@ def roofline(prof, n, e, peak, traffic_db, precision, total_ms=None, fp64_measur
 
 # ------------------------------------------------------------------------------------------ native arm
 
+def apply_schedule(smg, S, sched):
+    """Set every level's Vanka schedule, transfer tiles and DGS velocity form from a recorded choice."""
+    for l in range(S.levels - 1):
+        if l < len(sched.get("vanka", [])):
+            mode, blocks = sched["vanka"][l]
+            smg.stokes_set_level_schedule(S.h, l, mode, blocks)
+        if l < len(sched.get("tiles", [])):
+            rt, pt = sched["tiles"][l]
+            smg.stokes_set_level_tiles(S.h, l, rt, pt)
+        if l < len(sched.get("dgs_fused", [])):
+            smg.stokes_set_level_dgs(S.h, l, sched["dgs_fused"][l])
+
+
 def max_over_ranks(ms, dist, device):
     """The slowest rank's time in ms (the whole job ends with it); ms itself on one process."""
     if dist is None:
@@ -747,6 +760,10 @@ def main():
     ap.add_argument("--batch", type=int, default=64, help="problems per batch (--mode batch)")
     ap.add_argument("--streams", type=int, default=8, help="concurrent streams / host threads (--mode batch)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of --mode vcycle")
+    ap.add_argument("--schedule", default=None,
+                    help="JSON of per-level schedule choices (vanka, tiles, dgs_fused) to apply instead of the "
+                         "autotuner's, e.g. profiles/schedule_solve256_fp32.json -- for profiler runs, whose "
+                         "timings would steer the autotuner")
     args = ap.parse_args()
     if args.n is None:
         args.n = 128 if args.mode in ("cavity", "warmstart", "comparators") else 256
@@ -808,7 +825,9 @@ def main():
         return
     seeds = [(rank * 1000 + s) % 5 for s in range(5)]
     rhs = {}
-    S32 = smg.Stokes(n, precision=smg.PREC_FP32, autotune=not args.no_autotune)
+    S32 = smg.Stokes(n, precision=smg.PREC_FP32, autotune=not (args.no_autotune or args.schedule))
+    if args.schedule:
+        apply_schedule(smg, S32, json.load(open(args.schedule)))
     for sd in sorted(set(seeds)):
         rhs[sd] = S32.rhs(synthetic.bumps(n, seed=sd, device=dev)["f"], None)
     x = torch.zeros(npk, dtype=torch.float64, device=dev)
