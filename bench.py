@@ -276,9 +276,11 @@ def roofline(prof, n, e, peak, traffic_db, precision, total_ms=None, fp64_measur
     if kind in ("apply_dot", "update_x"):
         # FP64 kernels of SQMR: bound by the DP pipe; count DP instructions (per packed entry: apply
         # ~9.25 = 3/4 face rows x 9 + 1/4 cell rows x 6 + the dot's DFMA; update_x 8)
+        # (update_x: the critical r/q kernel and the deferred d/x kernel together, 5 + 3 per entry; the
+        # kind's total time per iteration is the denominator)
         per = 9.25 if kind == "apply_dot" else 8.0
         npk = packed_len(n)
-        achieved = per * npk / (avg_ms * 1e-3) / 1e9
+        achieved = per * npk / (ms0 * 1e-3) / 1e9
         out = {"kernel": kind, "bound": "alu", "achieved": achieved, "peak": DP_INSTR_PEAK_G,
                "peak_source": "nominal FP64 rate 1.25 TFLOP/s = 625 G DP instructions/s (2 DFMA/SM/cycle, 152 SMs, "
                               "2.07 GHz)",

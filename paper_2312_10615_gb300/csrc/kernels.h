@@ -107,7 +107,7 @@ template <class A, class B> void launch_convert(long long n, const A *in, B *out
 struct SqmrState {
     double rho, sigma, alpha, tau, nu, nu_prev, c2, coefA, coefB, beta, rho_new;
     double tt, st, rr, bb, pmean;
-    int breakdown, nonfinite, iter, pad;
+    int breakdown, nonfinite, iter, dx_pending;
 };
 
 constexpr int kRedBlocks = 1184;  // 152 SMs x 8 resident 256-thread blocks: grid of every reduction kernel
@@ -130,10 +130,14 @@ void launch_scalars_aux(int stage, const double *partials, int nparts, SqmrState
 // s -= alpha w ; optionally b32 = (T) s for a lower-precision V-cycle
 template <class T>
 void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream);
-// d = coefA d + coefB q ; x += d ; r = (1-c2) r + c2 s ; q = t + beta q ; partials of |r|^2
+// the d, x, r, q recurrences of Alg. 4 in two parts: r = (1-c2) r + c2 s ; qn = t + beta qo ; partials of
+// |r|^2 (the part the next iteration needs) and, when st->dx_pending, d = coefA d + coefB qo ; x += d (the
+// iterate, deferred into the next iteration)
 template <class T>
-void launch_update_x(long long n, double *x, double *d, double *q, const T *t, double *r, const double *sv,
-                     const SqmrState *st, double *partials, cudaStream_t s);
+void launch_update_rq(long long n, const double *qo, double *qn, const T *t, double *r, const double *sv,
+                      const SqmrState *st, double *partials, cudaStream_t s);
+void launch_update_dx(long long n, double *x, double *d, const double *qo, const SqmrState *st, cudaStream_t s,
+                      int blocks = 0);
 // q = t (widening), d = 0
 template <class T> void launch_init_q(long long n, const T *t, double *q, double *d, cudaStream_t s);
 template <class T> void launch_add_to(long long n, const T *t, double *x, cudaStream_t s);

@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partia
         st->rho = st->rho_new;
         st->nu_prev = st->nu;
         st->iter += 1;
+        st->dx_pending = 1;  // d_j, x_j still to be applied (k_update_dx, with this iteration's coefA / coefB)
         if (!isfinite(p0)) st->nonfinite = 1;
         host_out[0] = p0;
         host_out[1] = (double)(st->breakdown | (st->nonfinite << 1));
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partia
         st->nu_prev = 0.0;
         st->iter = 0;
         st->breakdown = 0;
+        st->dx_pending = 0;
         st->nonfinite = (!isfinite(p0) || !isfinite(p1)) ? 1 : 0;
         host_out[0] = p0;
         host_out[1] = p1;
@@ -214,31 +216,52 @@ void launch_update_s(long long n, double *s, const double *w, const SqmrState *s
 // d_j = c^2 nu_{j-1}^2 d_{j-1} + c^2 alpha q_{j-1};  x_j = x_{j-1} + d_j;
 // r_j = (1 - c^2) r_{j-1} + c^2 s_j  (true residual of the QMR-smoothed iterate);
 // q_j = t + beta q_{j-1};  partial |r_j|^2
+// The d, x, r, q recurrences of Alg. 4 in two kernels.  The part the next iteration needs -- the recursive true
+// residual r_j = (1 - c_j^2) r_{j-1} + c_j^2 s_j, its norm and q_j = t_j + beta_j q_{j-1} (written into the
+// other of two q buffers, so q_{j-1} survives) -- and the part nothing in the iteration reads: the
+// iterate, d_j = A_j d_{j-1} + B_j q_{j-1}, x_j = x_{j-1} + d_j.  The second is deferred into the next
+// iteration, beside its V-cycle; it runs only while st->dx_pending is set (by the iteration's last
+// scalar step; cleared when the update has been applied outside the loop).  Same arithmetic per entry.
 template <class T>
-__global__ void __launch_bounds__(256) k_update_x(long long n, double *__restrict__ x, double *__restrict__ d,
-                                                  double *__restrict__ q, const T *__restrict__ tv,
-                                                  double *__restrict__ r, const double *__restrict__ sv,
-                                                  const SqmrState *__restrict__ st, double *partials) {
+__global__ void __launch_bounds__(256) k_update_rq(long long n, const double *__restrict__ qo, double *__restrict__ qn,
+                                                   const T *__restrict__ tv, double *__restrict__ r,
+                                                   const double *__restrict__ sv, const SqmrState *__restrict__ st,
+                                                   double *partials) {
     pdl_wait();
-    double A = st->coefA, B = st->coefB, c2 = st->c2, beta = st->beta;
+    const double c2 = st->c2, beta = st->beta;
     double v[1] = {0.0};
 #pragma unroll 1
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        double qo = q[t];
-        double dn = A * d[t] + B * qo;
-        d[t] = dn;
-        x[t] += dn;
-        double rn = (1.0 - c2) * r[t] + c2 * sv[t];
+        const double q0 = qo[t];
+        const double rn = (1.0 - c2) * r[t] + c2 * sv[t];
         r[t] = rn;
-        q[t] = (double)tv[t] + beta * qo;
+        qn[t] = (double)tv[t] + beta * q0;
         v[0] += rn * rn;
     }
     block_store<1>(v, partials, blockIdx.x);
 }
+__global__ void __launch_bounds__(256) k_update_dx(long long n, double *__restrict__ x, double *__restrict__ d,
+                                                   const double *__restrict__ qo, const SqmrState *__restrict__ st) {
+    pdl_wait();
+    if (!st->dx_pending) return;
+    const double A = st->coefA, B = st->coefB;
+#pragma unroll 1
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const double dn = A * d[t] + B * qo[t];
+        d[t] = dn;
+        x[t] += dn;
+    }
+}
 template <class T>
-void launch_update_x(long long n, double *x, double *d, double *q, const T *t, double *r, const double *sv,
-                     const SqmrState *st, double *partials, cudaStream_t s) {
-    launch_k(k_update_x<T>, dim3(kRedBlocks), dim3(kBlock), 0, s, n, x, d, q, t, r, sv, st, partials);
+void launch_update_rq(long long n, const double *qo, double *qn, const T *t, double *r, const double *sv,
+                      const SqmrState *st, double *partials, cudaStream_t s) {
+    launch_k(k_update_rq<T>, dim3(kRedBlocks), dim3(kBlock), 0, s, n, qo, qn, t, r, sv, st, partials);
+}
+// blocks: the full reduction grid when it runs alone; a few per SM when it runs beside the V-cycle, so
+// that the V-cycle's kernels keep most of every SM's thread slots
+void launch_update_dx(long long n, double *x, double *d, const double *qo, const SqmrState *st, cudaStream_t s,
+                      int blocks) {
+    launch_k(k_update_dx, dim3(blocks > 0 ? blocks : kRedBlocks), dim3(kBlock), 0, s, n, x, d, qo, st);
 }
 
 template <class T>
@@ -281,10 +304,10 @@ template void launch_dot2<double>(long long, const double *, const double *, dou
 template void launch_update_s<float>(long long, double *, const double *, const SqmrState *, float *, cudaStream_t);
 template void launch_update_s<double>(long long, double *, const double *, const SqmrState *, double *, cudaStream_t);
 template void launch_update_s<bf16>(long long, double *, const double *, const SqmrState *, bf16 *, cudaStream_t);
-template void launch_update_x<float>(long long, double *, double *, double *, const float *, double *,
-                                     const double *, const SqmrState *, double *, cudaStream_t);
-template void launch_update_x<double>(long long, double *, double *, double *, const double *, double *,
-                                      const double *, const SqmrState *, double *, cudaStream_t);
+template void launch_update_rq<float>(long long, const double *, double *, const float *, double *, const double *,
+                                      const SqmrState *, double *, cudaStream_t);
+template void launch_update_rq<double>(long long, const double *, double *, const double *, double *, const double *,
+                                       const SqmrState *, double *, cudaStream_t);
 // x += t (the pure-multigrid update x_{k+1} = x_k + W^+ (b - L~ x_k), t in the V-cycle's precision)
 template <class T>
 __global__ void __launch_bounds__(256) k_add_to(long long n, const T *__restrict__ tv, double *__restrict__ x) {

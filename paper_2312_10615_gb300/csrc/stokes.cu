@@ -14,6 +14,7 @@
 #include <cstring>
 #include <atomic>
 #include <chrono>
+#include <functional>
 #include <map>
 
 #include <nvtx3/nvToolsExt.h>
@@ -333,14 +334,26 @@ struct stokes_s {
     SqmrState *st = nullptr;
     double *hout = nullptr;  // mapped pinned host memory written by the scalar kernel
     cudaStream_t cs = nullptr;
-    cudaGraphExec_t g_vcycle = nullptr, g_iter = nullptr, g_iter_id = nullptr;
+    cudaGraphExec_t g_vcycle = nullptr, g_iter[2] = {nullptr, nullptr}, g_iter_id[2] = {nullptr, nullptr};
+    double *q2 = nullptr;  // second SQMR direction buffer: iteration j writes q_j into (j odd ? q2 : q)
+    int dx_blocks = 0;     // grid of the deferred iterate update beside the V-cycle (4 blocks per SM)
+    // the deferred iterate update (d_j, x_j) runs on a side stream beside the next iteration's V-cycle
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::function<void(cudaStream_t)> fork;  // one-shot hook called by the V-cycle after the finest restriction
+    std::function<void(cudaStream_t)> join;  // one-shot hook called by the V-cycle before the finest prolongation
     double *mgr = nullptr;  // FP64 residual of the pure-multigrid solver (FP32 V-cycles), on first use
     std::vector<void *> allocs;
 
     ~stokes_s() {
         if (g_vcycle) cudaGraphExecDestroy(g_vcycle);
-        if (g_iter) cudaGraphExecDestroy(g_iter);
-        if (g_iter_id) cudaGraphExecDestroy(g_iter_id);
+        for (int p = 0; p < 2; ++p) {
+            if (g_iter[p]) cudaGraphExecDestroy(g_iter[p]);
+            if (g_iter_id[p]) cudaGraphExecDestroy(g_iter_id[p]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         for (void *p : allocs) cudaFree(p);
         if (hout) cudaFreeHost(hout);
         if (cs) cudaStreamDestroy(cs);
@@ -572,7 +585,17 @@ template <class T> void cycle_level(stokes_s *h, int l, bool first, cudaStream_t
                                                    B.rtile); });
         });
     });
+    if (l == 0 && h->fork) {  // the coarse levels leave the finest level's bandwidth mostly idle
+        auto f = h->fork;
+        h->fork = nullptr;
+        f(s);
+    }
     for (int g = 0; g < h->cycle; ++g) cycle_level<T>(h, l + 1, g == 0, s);
+    if (l == 0 && h->join) {  // back on the finest level: the side work has had the coarse levels
+        auto f = h->join;
+        h->join = nullptr;
+        f(s);
+    }
     prof(STOKES_K_PROLONG, l, s,
          [&] { launch_prolong<T>(B.L, h->lev[l + 1].L, (const T *)h->lev[l + 1].x, (T *)B.x, s, B.ptile); });
     smooth_level<T>(h, l, s);
@@ -590,14 +613,19 @@ template <class T> void identity_precond(stokes_s *h, cudaStream_t s) {
     else launch_convert<double, float>(n, h->s, (float *)h->lev[0].x, s);
 }
 
-// one SQMR iteration (Alg. 4, loop body) on the finest level; precond = false: plain SQMR
-template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s, bool precond) {
+// one SQMR iteration (Alg. 4, loop body) on the finest level; precond = false: plain SQMR.  parity = j & 1
+// of the iteration j: q_{j-1} is read from one of the two direction buffers and q_j written into the other
+// (qbuf), and the previous iteration's deferred iterate update (d_{j-1}, x_{j-1}, which reads q_{j-2}) runs
+// on the side stream beside this iteration's coarse levels, joined before anything overwrites its inputs
+double *qbuf(stokes_s *h, int parity) { return parity ? h->q2 : h->q; }
+template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s, bool precond, int parity) {
     const Lev &L = h->lev[0].L;
     long long n = L.n;
     T *t = (T *)h->lev[0].x;
+    double *qprev = qbuf(h, parity ^ 1), *qnext = qbuf(h, parity);
     // t <- L q_{j-1}, sigma = q^T t ; alpha = rho / sigma
     int np = reduce_parts(L);
-    prof(STOKES_K_APPLY_DOT, 0, s, [&] { launch_apply_dot(L, h->q, h->w, h->partials, s); });
+    prof(STOKES_K_APPLY_DOT, 0, s, [&] { launch_apply_dot(L, qprev, h->w, h->partials, s); });
     prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(0, h->partials, np, h->st, h->hout, s); });
     // s_j = s_{j-1} - alpha t
     with_tb<T>(h, 0, [&](auto, auto tb) {
@@ -606,23 +634,60 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s, bool precond
             launch_update_s<TB>(n, h->s, h->w, h->st, h->prec == STOKES_PREC_FP64 ? nullptr : (TB *)h->lev[0].b, s);
         });
     });
-    if (precond) vcycle<T>(h, s);  // t <- V-cycle(L~, s_j, 0, n)
-    else identity_precond<T>(h, s);
+    // the previous iteration's d and x (pending flag on the device), on the side stream
+    bool forked = false;
+    auto lazy = [&](cudaStream_t ms) {
+        cudaEventRecord(h->ev_fork, ms);
+        cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+        prof(STOKES_K_UPDATE_X, 0, h->side,
+             [&] { launch_update_dx(n, h->x, h->d, qnext, h->st, h->side, h->dx_blocks); });
+        cudaEventRecord(h->ev_join, h->side);
+        forked = true;
+    };
+    bool joined = false;
+    auto rejoin = [&](cudaStream_t ms) {
+        cudaStreamWaitEvent(ms, h->ev_join, 0);
+        joined = true;
+    };
+    if (precond) {
+        h->fork = lazy;
+        h->join = rejoin;
+        vcycle<T>(h, s);  // t <- V-cycle(L~, s_j, 0, n)
+        h->fork = nullptr;
+        h->join = nullptr;
+    } else {
+        lazy(s);
+        identity_precond<T>(h, s);
+    }
+    if (!forked) lazy(s);
+    if (!joined) rejoin(s);
     // |t|^2, rho_j = s_j^T t ; nu, c, tau, beta
     prof(STOKES_K_DOT2, 0, s, [&] { launch_dot2<T>(n, t, h->s, h->partials, s); });
     prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(1, h->partials, kRedBlocks, h->st, h->hout, s); });
-    // d_j, x_j, recursive true residual r_j, q_j ; |r_j|^2 to the host
+    // recursive true residual r_j, q_j ; |r_j|^2 to the host ; d_j, x_j pending
     prof(STOKES_K_UPDATE_X, 0, s,
-         [&] { launch_update_x<T>(n, h->x, h->d, h->q, t, h->r, h->s, h->st, h->partials, s); });
+         [&] { launch_update_rq<T>(n, qprev, qnext, t, h->r, h->s, h->st, h->partials, s); });
     prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(2, h->partials, kRedBlocks, h->st, h->hout, s); });
 }
-void sqmr_iteration_any(stokes_s *h, cudaStream_t s) {
-    if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s, true);
-    else sqmr_iteration<float>(h, s, true);
+// apply the deferred d_j, x_j of the last completed iteration j (reads q_{j-1}) and clear the flag
+void flush_iterate(stokes_s *h, int last_iter, cudaStream_t s) {
+    launch_update_dx(h->n0(), h->x, h->d, qbuf(h, (last_iter - 1) & 1), h->st, s);
+    cudaMemsetAsync(&h->st->dx_pending, 0, sizeof(int), s);
 }
-void sqmr_iteration_plain(stokes_s *h, cudaStream_t s) {
-    if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s, false);
-    else sqmr_iteration<float>(h, s, false);
+void sqmr_iteration_any(stokes_s *h, cudaStream_t s, int parity) {
+    if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s, true, parity);
+    else sqmr_iteration<float>(h, s, true, parity);
+}
+void sqmr_iteration_plain(stokes_s *h, cudaStream_t s, int parity) {
+    if (h->prec == STOKES_PREC_FP64) sqmr_iteration<double>(h, s, false, parity);
+    else sqmr_iteration<float>(h, s, false, parity);
+}
+void drop_graphs(stokes_s *h) {
+    if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
+    for (int p = 0; p < 2; ++p) {
+        if (h->g_iter[p]) { cudaGraphExecDestroy(h->g_iter[p]); h->g_iter[p] = nullptr; }
+        if (h->g_iter_id[p]) { cudaGraphExecDestroy(h->g_iter_id[p]); h->g_iter_id[p] = nullptr; }
+    }
 }
 
 template <class F> int capture(stokes_s *h, F body, cudaGraphExec_t *out) {
@@ -651,17 +716,17 @@ int run_vcycle(stokes_s *h, cudaStream_t s) {
     return 0;
 }
 
-int run_iteration(stokes_s *h, cudaStream_t s, bool precond = true) {
-    cudaGraphExec_t &g = precond ? h->g_iter : h->g_iter_id;
-    void (*body)(stokes_s *, cudaStream_t) = precond ? sqmr_iteration_any : sqmr_iteration_plain;
+int run_iteration(stokes_s *h, cudaStream_t s, bool precond, int parity) {
+    cudaGraphExec_t &g = precond ? h->g_iter[parity] : h->g_iter_id[parity];
+    void (*fn)(stokes_s *, cudaStream_t, int) = precond ? sqmr_iteration_any : sqmr_iteration_plain;
     if (h->use_graphs) {
         if (!g) {
-            int rc = capture(h, body, &g);
+            int rc = capture(h, [&](stokes_s *hh, cudaStream_t cs) { fn(hh, cs, parity); }, &g);
             if (rc) return rc;
         }
         CK(cudaGraphLaunch(g, s));
     } else {
-        body(h, s);
+        fn(h, s, parity);
         CKLAUNCH();
     }
     return 0;
@@ -1389,6 +1454,15 @@ int ensure_sqmr(stokes_s *h) {
     int rc;
     if ((rc = h->alloc(&h->x, sizeof(double) * n))) return rc;
     if ((rc = h->alloc(&h->q, sizeof(double) * n))) return rc;
+    if ((rc = h->alloc(&h->q2, sizeof(double) * n))) return rc;
+    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    {
+        int nsm = 0;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
+        h->dx_blocks = 4 * nsm;
+    }
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     if ((rc = h->alloc(&h->d, sizeof(double) * n))) return rc;
     if ((rc = h->alloc(&h->r, sizeof(double) * n))) return rc;
     if ((rc = h->alloc(&h->w, sizeof(double) * n))) return rc;
@@ -1428,6 +1502,7 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
     int it = 0, status = STOKES_OK;
     double rel = 0.0;
     bool rel_confirmed = false;  // rel holds the explicit FP64 residual of the returned x (up to the pressure shift)
+    int pending = 0;             // iteration whose deferred d / x update has not been applied yet (0: none)
     if (!std::isfinite(nb)) {
         status = STOKES_ERR_NAN;
         goto finish;
@@ -1468,13 +1543,17 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
     status = STOKES_ERR_NOT_CONVERGED;
     for (it = 1; it <= max_iter; ++it) {
         NvtxRange range("sqmr iteration");
-        if ((rc = run_iteration(h, s, precond))) return rc;
+        if ((rc = run_iteration(h, s, precond, it & 1))) return rc;
+        pending = it;
         if ((rc = sync_read(h, s, &rr, &flags))) return rc;
         int fl = (int)flags;
         if (fl & 2 || !std::isfinite(rr)) { status = STOKES_ERR_NAN; break; }
         if (fl & 1) { status = STOKES_ERR_BREAKDOWN; break; }
         if (std::sqrt(rr) / nb < tol) {
-            // confirm with the explicit FP64 residual b - L x_j; keep iterating from it otherwise
+            // confirm with the explicit FP64 residual b - L x_j (x_j first takes its deferred update);
+            // keep iterating from it otherwise
+            flush_iterate(h, it, s);
+            pending = 0;
             double r2 = 0.0;
             if ((rc = residual_norm2(h, h->bvec, h->x, h->w, &r2, s))) return rc;
             rel = std::sqrt(r2) / nb;
@@ -1487,6 +1566,10 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
         }
     }
     if (it > max_iter) it = max_iter;
+    if (pending) {  // the last iteration's d and x
+        flush_iterate(h, pending, s);
+        pending = 0;
+    }
 finish:
     // pressure fixed to zero mean (constant p lies in ker L) -- unless Neumann faces next to exterior
     // cells fix the pressure level (the exterior pressure is 0), where L has no null space
@@ -1614,7 +1697,7 @@ int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launch
     P.ev.resize(8192);
     for (auto &e : P.ev) CK(cudaEventCreate(&e));
     g_prof = &P;
-    sqmr_iteration_any(h, s);
+    sqmr_iteration_any(h, s, 1);
     g_prof = nullptr;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1710,9 +1793,7 @@ int stokes_set_level_tiles(stokes_t h, int level, const int *tiles) {
     B.ptile = Tile{tiles[3], tiles[4], tiles[5]};
     B.rms = B.pms = 0.f;
     // the captured graphs hold the old tiles
-    if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
-    if (h->g_iter) { cudaGraphExecDestroy(h->g_iter); h->g_iter = nullptr; }
-    if (h->g_iter_id) { cudaGraphExecDestroy(h->g_iter_id); h->g_iter_id = nullptr; }
+    drop_graphs(h);
     return STOKES_OK;
 }
 
@@ -1732,9 +1813,7 @@ int stokes_set_level_dgs(stokes_t h, int level, int fused) {
     LevelBuf &B = h->lev[level];
     if (fused && (!B.x2 || h->dwj)) return STOKES_ERR_UNSUPPORTED;
     B.ufused = fused;
-    if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
-    if (h->g_iter) { cudaGraphExecDestroy(h->g_iter); h->g_iter = nullptr; }
-    if (h->g_iter_id) { cudaGraphExecDestroy(h->g_iter_id); h->g_iter_id = nullptr; }
+    drop_graphs(h);
     return STOKES_OK;
 }
 
@@ -1768,9 +1847,7 @@ int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
     B.vblocks = (mode == 0 || mode == 4) ? 0 : blocks;
     B.vms = 0.f;
     // the captured graphs hold the old schedule
-    if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
-    if (h->g_iter) { cudaGraphExecDestroy(h->g_iter); h->g_iter = nullptr; }
-    if (h->g_iter_id) { cudaGraphExecDestroy(h->g_iter_id); h->g_iter_id = nullptr; }
+    drop_graphs(h);
     return STOKES_OK;
 }
 
