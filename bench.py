@@ -587,8 +587,25 @@ def run_warmstart(args, smg, synthetic, torch, dev, rank, world):
             losses.append((st, loss))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
-    # held-out evaluation
+    # the network's forward pass on each engine (CUDA events, 20 passes after 3 warm-up passes)
     stream = torch.cuda.current_stream()
+    b_probe = rhs(seeds[0])
+    x_probe = torch.empty_like(b_probe)
+    predict_ms = {}
+    for name, eng in (("tensor_cores", 1), ("cuda_cores", 0)):
+        ws.set_engine(eng)
+        for _ in range(3):
+            ws.predict(b_probe, x_probe)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(20):
+            ws.predict(b_probe, x_probe)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        predict_ms[name] = ev0.elapsed_time(ev1) / 20
+    ws.set_engine(1)
+    conv_flop = 2 * 27 * 16 * (4 * n ** 3 + 16 * (2 * n ** 3 + 3 * (n // 2) ** 3 + 3 * (n // 4) ** 3 + 2 * (n // 8) ** 3))
+    # held-out evaluation
     rows = []
     for k in range(args.test):
         i = args.train + k
@@ -627,6 +644,10 @@ def run_warmstart(args, smg, synthetic, torch, dev, rank, world):
             "learned_x0": {"iterations_mean": float(r[:, 2].mean()), "ms_mean": float(r[:, 3].mean()),
                            "value": unknowns(n) / (r[:, 3].mean() * 1e-3), "guess_used": float(r[:, 4].mean()),
                            "x0_rel_error_mean": float(r[:, 5].mean()), "max_rel_residual": float(r[:, 6].max())},
+            "network_forward": {"ms_tensor_cores": predict_ms["tensor_cores"], "ms_cuda_cores": predict_ms["cuda_cores"],
+                                "conv_gflop": conv_flop * 1e-9,
+                                "conv_tflops_tensor_cores": conv_flop / (predict_ms["tensor_cores"] * 1e-3) * 1e-12,
+                                "engine": "BF16 tensor cores (tcgen05 convolution, mma.sync weight gradient)"},
             "training": {"solves_s": gen_s, "train_s": train_s, "steps": steps, "ms_per_step": train_s * 1e3 / steps,
                          "loss_trace": losses[:: max(1, len(losses) // 12)] + losses[-1:],
                          "data_iterations_mean": float(np.mean(its0))},

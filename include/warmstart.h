@@ -25,6 +25,9 @@
  * [27][16][16], W11 [16][4]; tap t = 9 (dz+1) + 3 (dy+1) + (dx+1); last index fastest.
  * STORAGE: activations are kept as FP32 or BF16 (WARMSTART_STORE_*); every convolution accumulates
  * in FP32; gradients, weights and Adam moments are FP32.
+ * ENGINE: with BF16 storage the 3x3x3 convolutions, their data gradients and weight gradients take
+ * BF16 operands on the tensor cores (weights and FP32 gradients rounded to BF16 where they enter a
+ * product); with FP32 storage, or warmstart_set_engine(ws, 0), they run in FP32 on the CUDA cores.
  *
  * POINTERS: b, x0, xstar, x are packed FP64 device vectors (layout of stokesmg.h); weight and
  * gradient arrays may be host or device memory.  The handle owns its activation, gradient,
@@ -53,6 +56,8 @@ long long warmstart_num_weights(void);
 int warmstart_create(int n, int storage, double scale, warmstart_t *out);
 int warmstart_destroy(warmstart_t ws);
 int warmstart_set_scale(warmstart_t ws, double scale);
+/* tensor_cores = 1 (default) or 0: where BF16-storage convolutions run (see ENGINE) */
+int warmstart_set_engine(warmstart_t ws, int tensor_cores);
 
 /* copy num_weights FP32 weights in (resets the Adam moments and step count) / out; synchronous */
 int warmstart_set_weights(warmstart_t ws, const float *w);
@@ -73,6 +78,9 @@ int warmstart_loss_grad(warmstart_t ws, stokes_t h, const double *b, const doubl
 /* one Adam update (Kingma & Ba, Algorithm 1) of the weights from the handle's gradient buffer */
 int warmstart_adam_step(warmstart_t ws, double lr, double beta1, double beta2, double eps, void *stream);
 
+/* Tensor-core kernels report a bounded wait that ran out as STOKES_ERR_TIMEOUT from the next call that
+ * synchronises (warmstart_loss_grad with loss or grad, warmstart_solve). */
+
 /* SQMR solve of stokes handle h from the network's guess: x <- network(b); the guess is kept only
  * if it lowers both the residual (||b - L x|| < ||b||) and SQMR's first quantity tau_0 =
  * ||M (b - L x)|| (Alg. 4, M = the V-cycle) below its value for x0 = 0, ||M b||; otherwise x <- 0.
@@ -82,6 +90,19 @@ int warmstart_adam_step(warmstart_t ws, double lr, double beta1, double beta2, d
  * device. */
 int warmstart_solve(warmstart_t ws, stokes_t h, const double *b, double *x, double tol, int max_iter,
                     sqmr_info_t *info, int *used_guess, void *stream);
+
+/* ---- checks of single network operations (device pointers; synchronous) ----
+ * op 0: out (BF16 [n^3][16]) = act(conv(x (BF16 [n^3][ci]), w [27][ci][16]))
+ * op 1: out (FP32 [n^3][16]) = data gradient of a 16 -> 16 layer w [27][16][16] for the output
+ *       gradient x (FP32 [n^3][16]): out[v] = sum_t x[v - off_t] w[t]^T
+ * op 2: out (FP32 [27][ci][16]) = weight gradient sum_v x[v + off_t][ci] g[v][co] (x BF16 [n^3][ci],
+ *       g FP32 [n^3][16])
+ * ci is 4 or 16 (16 for op 1); engine 0 = CUDA cores (FP32 arithmetic), 1 = tensor cores (BF16
+ * operands, FP32 accumulation; STOKES_ERR_UNSUPPORTED where that form does not apply). */
+int warmstart_conv_check(int n, int ci, int op, int engine, const void *x, const float *g, const float *w, void *out,
+                         void *stream);
+/* one tcgen05 tensor-core MMA: d (FP32 [128][16]) = a (BF16 [128][16]) b^T (b BF16 [16][16], [n][k]) */
+int warmstart_mma_check(const void *a, const void *b, float *d, void *stream);
 
 #ifdef __cplusplus
 }

@@ -32,7 +32,8 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            # learned initial guess (include/warmstart.h)
            "warmstart_num_weights", "warmstart_create", "warmstart_destroy", "warmstart_set_scale",
            "warmstart_set_weights", "warmstart_get_weights", "warmstart_predict", "warmstart_loss_grad",
-           "warmstart_adam_step", "warmstart_solve"]
+           "warmstart_adam_step", "warmstart_solve", "warmstart_set_engine", "warmstart_conv_check",
+           "warmstart_mma_check"]
 
 # kernel kinds reported by stokes_profile_iteration (STOKES_K_* in the header)
 KERNEL_KINDS = ["apply_dot", "update_s", "dot2", "update_x", "scalars", "memset", "vanka_compute", "vanka_apply",
@@ -116,6 +117,9 @@ def _load():
         "warmstart_loss_grad": (i, [vp, vp, vp, vp, ctypes.POINTER(d), vp, vp]),
         "warmstart_adam_step": (i, [vp, d, d, d, d, vp]),
         "warmstart_solve": (i, [vp, vp, vp, vp, d, i, ctypes.POINTER(sqmr_info_t), ctypes.POINTER(i), vp]),
+        "warmstart_set_engine": (i, [vp, i]),
+        "warmstart_conv_check": (i, [i, i, i, i, vp, vp, vp, vp, vp]),
+        "warmstart_mma_check": (i, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -483,6 +487,10 @@ class WarmStart:
     def set_scale(self, scale):
         _check(lib().warmstart_set_scale(self.h, float(scale)), "warmstart_set_scale")
 
+    def set_engine(self, tensor_cores):
+        """BF16 storage: convolutions on the tensor cores (True, the default) or the CUDA cores."""
+        _check(lib().warmstart_set_engine(self.h, 1 if tensor_cores else 0), "warmstart_set_engine")
+
     def set_weights(self, w):
         w = np.ascontiguousarray(w, dtype=np.float32) if isinstance(w, np.ndarray) else w
         assert (w.size if isinstance(w, np.ndarray) else w.numel()) == warmstart_num_weights()
@@ -527,3 +535,23 @@ class WarmStart:
         if check:
             _check(rc, "warmstart_solve")
         return x, info, bool(used.value)
+
+
+def _raw(a):
+    """Raw pointer of a contiguous torch tensor of any dtype (None -> NULL)."""
+    if a is None:
+        return None
+    if not a.is_contiguous():
+        raise TypeError("tensors must be contiguous")
+    return a.data_ptr()
+
+
+def warmstart_conv_check(n, ci, op, engine, x, w, out, g=None, stream=None):
+    """One network operation on device tensors (op 0 convolution + activation, 1 data gradient, 2 weight
+    gradient) on the CUDA cores (engine 0) or the tensor cores (engine 1); returns the status code."""
+    return int(lib().warmstart_conv_check(n, ci, op, engine, _raw(x), _raw(g), _raw(w), _raw(out), _stream(stream)))
+
+
+def warmstart_mma_check(a, b, d, stream=None):
+    """d = a b^T by one tcgen05 MMA (a BF16 [128, 16], b BF16 [16, 16], d FP32 [128, 16]); status code."""
+    return int(lib().warmstart_mma_check(_raw(a), _raw(b), _raw(d), _stream(stream)))

@@ -334,6 +334,7 @@ struct stokes_s {
     SqmrState *st = nullptr;
     double *hout = nullptr;  // mapped pinned host memory written by the scalar kernel
     cudaStream_t cs = nullptr;
+    cudaStream_t zs = nullptr;  // zero-fills new buffers (alloc)
     cudaGraphExec_t g_vcycle = nullptr, g_iter[2] = {nullptr, nullptr}, g_iter_id[2] = {nullptr, nullptr};
     double *q2 = nullptr;  // second SQMR direction buffer: iteration j writes q_j into (j odd ? q2 : q)
     int dx_blocks = 0;     // grid of the deferred iterate update beside the V-cycle (4 blocks per SM)
@@ -354,16 +355,22 @@ struct stokes_s {
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (side) cudaStreamDestroy(side);
+        if (zs) cudaStreamDestroy(zs);
         for (void *p : allocs) cudaFree(p);
         if (hout) cudaFreeHost(hout);
         if (cs) cudaStreamDestroy(cs);
     }
+    // zero-filled device buffer, complete before the call returns: the zeroing runs on the handle's own
+    // non-blocking stream and is waited for, so work the caller then issues on any stream (buffers the
+    // first solve allocates, on the caller's stream) sees the zeros
     template <class P> int alloc(P **p, size_t bytes) {
         void *v = nullptr;
         cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
         if (e != cudaSuccess) return cuda_status(e);
         allocs.push_back(v);
-        e = cudaMemset(v, 0, bytes ? bytes : 16);
+        if (!zs && (e = cudaStreamCreateWithFlags(&zs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e);
+        e = cudaMemsetAsync(v, 0, bytes ? bytes : 16, zs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(zs);
         if (e != cudaSuccess) return cuda_status(e);
         *p = (P *)v;
         return 0;

@@ -3,14 +3,16 @@
 // that starts the paper's SQMR (Alg. 4) from the network's guess.
 //
 // Activations are channels-last, one voxel's channels contiguous ([voxel][C], x fastest among the
-// voxels), stored FP32 or BF16; every convolution accumulates in FP32 on the CUDA cores (the
-// network is 16 channels wide, far too narrow to keep a 128-wide tensor-core tile busy).  The
-// 3x3x3 convolution keeps its 27 x CI x CO weights in shared memory (read as warp-wide broadcasts)
-// and each thread produces two neighbouring voxels; the weight gradient stages a halo tile of the
-// input and a tile of the output gradient in shared memory and accumulates per-tap sums in
-// registers across a grid-stride loop of tiles; per-block partial sums are added in a fixed order
-// (deterministic).  The data-gradient of a convolution is the same kernel with the taps mirrored and
-// the channel roles exchanged.
+// voxels), stored FP32 or BF16; every convolution accumulates in FP32.  With BF16 storage the 3x3x3
+// convolutions, their data gradients and weight gradients run on the tensor cores (warmstart_tc.cu:
+// tcgen05 implicit GEMM with the voxels as M, and mma.sync for the weight gradient).  With FP32
+// storage (and where the tensor-core form does not apply) they run on the CUDA cores: the
+// convolution keeps its 27 x CI x CO weights in shared memory (read as warp-wide broadcasts) and each
+// thread produces two neighbouring voxels; the weight gradient stages a halo tile of the input and a
+// tile of the output gradient in shared memory and accumulates per-tap sums in registers across a
+// grid-stride loop of tiles.  Per-block partial sums are added in a fixed order (deterministic).  The
+// data-gradient of a convolution is the same kernel with the taps mirrored and the channel roles
+// exchanged.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -19,6 +21,7 @@
 
 #include "stokes_internal.cuh"
 #include "warmstart.h"
+#include "warmstart_tc.h"
 
 using smg::launch_k;
 using smg::pdl_wait;
@@ -536,6 +539,8 @@ int cuda_rc(cudaError_t e) {
 
 struct warmstart_s {
     int n = 0, storage = WARMSTART_STORE_FP32, dev = 0;
+    int tensor_cores = 1;  // BF16 storage: convolutions on the tensor cores (0: CUDA cores)
+    int *tcerr = nullptr;  // set by a tensor-core kernel whose bounded wait ran out
     double scale = 1.0;
     long long N[4] = {0, 0, 0, 0};
     Pk pk;
@@ -563,6 +568,36 @@ namespace {
 const float *Wl(warmstart_s *h, int l) { return h->w + w_off(l); }
 float *Gl(warmstart_s *h, int l) { return h->g + w_off(l); }
 
+// forward convolution with activation, 16 output channels: tensor cores for BF16 activations
+template <int CI, class S> void conv_fwd(warmstart_s *h, int n, const S *X, const float *W, S *Y, cudaStream_t s) {
+    if constexpr (sizeof(S) == 2) {
+        if (h->tensor_cores && wstc::conv3_fwd(n, CI, X, W, Y, h->tcerr, s)) return;
+    }
+    conv3<CI, CH, S, S, false, true>(n, X, W, Y, s);
+}
+// data gradient of a 16 -> 16 layer (FP32 gradients; BF16 operands on the tensor cores)
+template <class S> void conv_bwd(warmstart_s *h, int n, const float *G, const float *W, float *Y, cudaStream_t s) {
+    if constexpr (sizeof(S) == 2) {
+        if (h->tensor_cores && wstc::conv3_bwd(n, G, W, Y, h->tcerr, s)) return;
+    }
+    conv3<CH, CH, float, float, true, false>(n, G, W, Y, s);
+}
+// weight gradient
+template <int CI, class S>
+void wgrad(warmstart_s *h, int n, const S *X, const float *G, float *partials, float *out, cudaStream_t s) {
+    if constexpr (sizeof(S) == 2) {
+        if (h->tensor_cores) {
+            const int nb = wstc::wgrad3(n, CI, X, G, partials, s);
+            if (nb > 0) {
+                launch_k(k_colsum, dim3(cdiv(27 * CI * CH, 256)), dim3(256), 0, s, (const float *)partials, nb,
+                         27 * CI * CH, out);
+                return;
+            }
+        }
+    }
+    wgrad3<CI, CH, S>(n, X, G, partials, out, s);
+}
+
 template <class S> void forward(warmstart_s *h, const double *b, double *x0, cudaStream_t s) {
     const int n0 = h->n;
     const int nl[4] = {n0, n0 / 2, n0 / 4, n0 / 8};
@@ -575,20 +610,20 @@ template <class S> void forward(warmstart_s *h, const double *b, double *x0, cud
     for (int l = 0; l < 3; ++l) { Sk[l] = (S *)h->s[l]; U[l] = (S *)h->u[l]; C[l] = (S *)h->c[l]; }
     S *B3 = (S *)h->b3;
     launch_k(k_in_map<S>, dim3(cdiv(h->N[0], 256)), dim3(256), 0, s, n0, h->pk, b, (const double *)h->sc, X0);
-    conv3<4, CH, S, S, false, true>(nl[0], X0, Wl(h, 0), A[0], s);
-    conv3<CH, CH, S, S, false, true>(nl[0], A[0], Wl(h, 1), Sk[0], s);
+    conv_fwd<4, S>(h, nl[0], X0, Wl(h, 0), A[0], s);
+    conv_fwd<CH, S>(h, nl[0], A[0], Wl(h, 1), Sk[0], s);
     for (int l = 1; l <= 2; ++l) {
         launch_k(k_pool<S>, dim3(cdiv(h->N[l], 256)), dim3(256), 0, s, nl[l], (const S *)Sk[l - 1], Pl[l]);
-        conv3<CH, CH, S, S, false, true>(nl[l], Pl[l], Wl(h, 2 * l), A[l], s);
-        conv3<CH, CH, S, S, false, true>(nl[l], A[l], Wl(h, 2 * l + 1), Sk[l], s);
+        conv_fwd<CH, S>(h, nl[l], Pl[l], Wl(h, 2 * l), A[l], s);
+        conv_fwd<CH, S>(h, nl[l], A[l], Wl(h, 2 * l + 1), Sk[l], s);
     }
     launch_k(k_pool<S>, dim3(cdiv(h->N[3], 256)), dim3(256), 0, s, nl[3], (const S *)Sk[2], Pl[3]);
-    conv3<CH, CH, S, S, false, true>(nl[3], Pl[3], Wl(h, 6), A[3], s);
-    conv3<CH, CH, S, S, false, true>(nl[3], A[3], Wl(h, 7), B3, s);
+    conv_fwd<CH, S>(h, nl[3], Pl[3], Wl(h, 6), A[3], s);
+    conv_fwd<CH, S>(h, nl[3], A[3], Wl(h, 7), B3, s);
     const S *below = B3;
     for (int l = 2; l >= 0; --l) {
         launch_k(k_up_add<S>, dim3(cdiv(h->N[l], 256)), dim3(256), 0, s, nl[l], below, (const S *)Sk[l], U[l]);
-        conv3<CH, CH, S, S, false, true>(nl[l], U[l], Wl(h, 10 - l), C[l], s);
+        conv_fwd<CH, S>(h, nl[l], U[l], Wl(h, 10 - l), C[l], s);
         below = C[l];
     }
     launch_k(k_conv1<S>, dim3(cdiv(h->N[0], 256)), dim3(256), 0, s, h->N[0], (const S *)C[0], Wl(h, 11), h->P);
@@ -636,33 +671,45 @@ template <class S> void backward(warmstart_s *h, cudaStream_t s) {
     launch_k(k_colsum, dim3(1), dim3(256), 0, s, (const float *)h->wpart, NRED, CH * 4, Gl(h, 11));
     // decoder, levels 0..2: gA[l] holds dz of the c_l convolution
     for (int l = 0; l <= 2; ++l) {
-        wgrad3<CH, CH, S>(nl[l], U[l], gA[l], h->wpart, Gl(h, 10 - l), s);
-        conv3<CH, CH, float, float, true, false>(nl[l], gA[l], Wl(h, 10 - l), gB[l], s);  // du_l (also d skip_l)
+        wgrad<CH, S>(h, nl[l], U[l], gA[l], h->wpart, Gl(h, 10 - l), s);
+        conv_bwd<S>(h, nl[l], gA[l], Wl(h, 10 - l), gB[l], s);  // du_l (also d skip_l)
         launch_k(k_upT, nb(l + 1), dim3(256), 0, s, nl[l + 1], (const float *)gB[l], gA[l + 1]);
         launch_k(k_act_bwd<S>, nb(l + 1), dim3(256), 0, s, h->N[l + 1], gA[l + 1], l + 1 <= 2 ? (const S *)C[l + 1] : (const S *)B3);
     }
     // level 3: b3 = act(conv(a3, W7)), a3 = act(conv(p3, W6))
-    wgrad3<CH, CH, S>(nl[3], A[3], gA[3], h->wpart, Gl(h, 7), s);
-    conv3<CH, CH, float, float, true, false>(nl[3], gA[3], Wl(h, 7), gB[3], s);
+    wgrad<CH, S>(h, nl[3], A[3], gA[3], h->wpart, Gl(h, 7), s);
+    conv_bwd<S>(h, nl[3], gA[3], Wl(h, 7), gB[3], s);
     launch_k(k_act_bwd<S>, nb(3), dim3(256), 0, s, h->N[3], gB[3], (const S *)A[3]);
-    wgrad3<CH, CH, S>(nl[3], Pl[3], gB[3], h->wpart, Gl(h, 6), s);
-    conv3<CH, CH, float, float, true, false>(nl[3], gB[3], Wl(h, 6), gA[3], s);  // d p3
+    wgrad<CH, S>(h, nl[3], Pl[3], gB[3], h->wpart, Gl(h, 6), s);
+    conv_bwd<S>(h, nl[3], gB[3], Wl(h, 6), gA[3], s);  // d p3
     // encoder, levels 2..0: gB[l] holds du_l; add the pooled gradient to get d s_l
     const float *dpool = gA[3];
     for (int l = 2; l >= 0; --l) {
         launch_k(k_add_poolT, nb(l), dim3(256), 0, s, nl[l], gB[l], dpool);
         launch_k(k_act_bwd<S>, nb(l), dim3(256), 0, s, h->N[l], gB[l], (const S *)Sk[l]);
-        wgrad3<CH, CH, S>(nl[l], A[l], gB[l], h->wpart, Gl(h, 2 * l + 1), s);
-        conv3<CH, CH, float, float, true, false>(nl[l], gB[l], Wl(h, 2 * l + 1), gA[l], s);
+        wgrad<CH, S>(h, nl[l], A[l], gB[l], h->wpart, Gl(h, 2 * l + 1), s);
+        conv_bwd<S>(h, nl[l], gB[l], Wl(h, 2 * l + 1), gA[l], s);
         launch_k(k_act_bwd<S>, nb(l), dim3(256), 0, s, h->N[l], gA[l], (const S *)A[l]);
         if (l > 0) {
-            wgrad3<CH, CH, S>(nl[l], Pl[l], gA[l], h->wpart, Gl(h, 2 * l), s);
-            conv3<CH, CH, float, float, true, false>(nl[l], gA[l], Wl(h, 2 * l), gB[l], s);  // d p_l
+            wgrad<CH, S>(h, nl[l], Pl[l], gA[l], h->wpart, Gl(h, 2 * l), s);
+            conv_bwd<S>(h, nl[l], gA[l], Wl(h, 2 * l), gB[l], s);  // d p_l
             dpool = gB[l];
         } else {
-            wgrad3<4, CH, S>(nl[0], X0, gA[0], h->wpart, Gl(h, 0), s);
+            wgrad<4, S>(h, nl[0], X0, gA[0], h->wpart, Gl(h, 0), s);
         }
     }
+}
+
+// STOKES_ERR_TIMEOUT (and the flag cleared) if a tensor-core kernel's bounded wait ran out since the last
+// check; synchronises the stream
+int tc_check(warmstart_s *h, cudaStream_t s) {
+    int f = 0;
+    cudaError_t e = cudaMemcpyAsync(&f, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if (!f) return STOKES_OK;
+    e = cudaMemsetAsync(h->tcerr, 0, sizeof(int), s);
+    return e == cudaSuccess ? STOKES_ERR_TIMEOUT : cuda_rc(e);
 }
 
 }  // namespace
@@ -716,6 +763,9 @@ int warmstart_create(int n, int storage, double scale, warmstart_t *out) {
     A((void **)&h->xp, h->pk.npk * sizeof(double));
     A((void **)&h->xd, h->pk.npk * sizeof(double));
     A((void **)&h->xr, h->pk.npk * sizeof(double));
+    A((void **)&h->tcerr, sizeof(int));
+    // the zero fills above run on the legacy stream: complete them before any caller stream uses the buffers
+    if (rc == STOKES_OK) rc = cuda_rc(cudaDeviceSynchronize());
     if (rc != STOKES_OK) {
         delete h;
         return rc;
@@ -730,6 +780,12 @@ int warmstart_destroy(warmstart_t h) {
     return STOKES_OK;
 }
 
+int warmstart_set_engine(warmstart_t h, int tensor_cores) {
+    if (!h || (tensor_cores != 0 && tensor_cores != 1)) return STOKES_ERR_INVALID_ARG;
+    h->tensor_cores = tensor_cores;
+    return STOKES_OK;
+}
+
 int warmstart_set_scale(warmstart_t h, double scale) {
     if (!h || !(scale > 0.0)) return STOKES_ERR_INVALID_ARG;
     h->scale = scale;
@@ -741,6 +797,7 @@ int warmstart_set_weights(warmstart_t h, const float *w) {
     cudaError_t e = cudaMemcpy(h->w, w, W_COUNT * 4, is_device(w) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->m, 0, W_COUNT * 4);
     if (e == cudaSuccess) e = cudaMemset(h->v, 0, W_COUNT * 4);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();  // synchronous for the caller's streams too
     h->step = 0;
     return cuda_rc(e);
 }
@@ -785,7 +842,8 @@ int warmstart_loss_grad(warmstart_t h, stokes_t st, const double *b, const doubl
     } else if (e == cudaSuccess && grad) {
         e = cudaStreamSynchronize(s);
     }
-    return cuda_rc(e);
+    if (e != cudaSuccess) return cuda_rc(e);
+    return (loss || grad) ? tc_check(h, s) : STOKES_OK;
 }
 
 int warmstart_adam_step(warmstart_t h, double lr, double beta1, double beta2, double eps, void *stream) {
@@ -827,6 +885,8 @@ int warmstart_solve(warmstart_t h, stokes_t st, const double *b, double *x, doub
     cudaError_t e = cudaMemcpyAsync(sc, h->sc, 10 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_rc(e);
+    rc = tc_check(h, s);
+    if (rc != STOKES_OK) return rc;
     // sc[0] = ||b||^2, sc[8] = ||b - L x0||^2, sc[4] = ||M (b - L x0)||^2, sc[6] = ||M b||^2
     const int use = std::isfinite(sc[4]) && std::isfinite(sc[8]) && sc[8] < sc[0] && sc[4] < sc[6];
     if (!use) {
@@ -835,6 +895,78 @@ int warmstart_solve(warmstart_t h, stokes_t st, const double *b, double *x, doub
     }
     if (used_guess) *used_guess = use;
     return sqmr_solve(st, b, x, tol, max_iter, info, stream);
+}
+
+
+int warmstart_conv_check(int n, int ci, int op, int engine, const void *x, const float *g, const float *w, void *out,
+                         void *stream) {
+    if (n < 1 || n > 1024 || (ci != 4 && ci != 16) || op < 0 || op > 2 || (engine != 0 && engine != 1) || !x || !w ||
+        !out || (op == 1 && ci != 16) || (op == 2 && !g) || !is_device(x) || !is_device(w) || !is_device(out) ||
+        (g && !is_device(g)))
+        return STOKES_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *err = nullptr;
+    float *part = nullptr;
+    cudaError_t e = cudaMalloc((void **)&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess && op == 2) e = cudaMalloc((void **)&part, (size_t)WG_BLOCKS * 27 * ci * CH * sizeof(float));
+    int rc = cuda_rc(e);
+    if (rc == STOKES_OK) {
+        bool ran = true;
+        if (op == 0) {
+            const bf16 *X = (const bf16 *)x;
+            bf16 *Y = (bf16 *)out;
+            if (engine) ran = wstc::conv3_fwd(n, ci, X, w, Y, err, s);
+            else if (ci == 4) conv3<4, CH, bf16, bf16, false, true>(n, X, w, Y, s);
+            else conv3<CH, CH, bf16, bf16, false, true>(n, X, w, Y, s);
+        } else if (op == 1) {
+            if (engine) ran = wstc::conv3_bwd(n, (const float *)x, w, (float *)out, err, s);
+            else conv3<CH, CH, float, float, true, false>(n, (const float *)x, w, (float *)out, s);
+        } else {
+            const bf16 *X = (const bf16 *)x;
+            if (engine) {
+                const int nb = wstc::wgrad3(n, ci, X, g, part, s);
+                ran = nb > 0;
+                if (ran)
+                    launch_k(k_colsum, dim3(cdiv(27 * ci * CH, 256)), dim3(256), 0, s, (const float *)part, nb,
+                             27 * ci * CH, (float *)out);
+            } else if (ci == 4) {
+                wgrad3<4, CH, bf16>(n, X, g, part, (float *)out, s);
+            } else {
+                wgrad3<CH, CH, bf16>(n, X, g, part, (float *)out, s);
+            }
+        }
+        if (!ran) rc = STOKES_ERR_UNSUPPORTED;
+        e = cudaGetLastError();
+        if (rc == STOKES_OK && e != cudaSuccess) rc = cuda_rc(e);
+        int f = 0;
+        e = cudaMemcpyAsync(&f, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (rc == STOKES_OK) rc = e != cudaSuccess ? cuda_rc(e) : (f ? STOKES_ERR_TIMEOUT : STOKES_OK);
+    }
+    if (err) cudaFree(err);
+    if (part) cudaFree(part);
+    return rc;
+}
+
+int warmstart_mma_check(const void *a, const void *b, float *d, void *stream) {
+    if (!a || !b || !d || !is_device(a) || !is_device(b) || !is_device(d)) return STOKES_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *err = nullptr;
+    cudaError_t e = cudaMalloc((void **)&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e != cudaSuccess) {
+        if (err) cudaFree(err);
+        return cuda_rc(e);
+    }
+    wstc::mma_selftest((const bf16 *)a, (const bf16 *)b, d, err, s);
+    int rc = cuda_rc(cudaGetLastError());
+    int f = 0;
+    e = cudaMemcpyAsync(&f, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (rc == STOKES_OK) rc = e != cudaSuccess ? cuda_rc(e) : (f ? STOKES_ERR_TIMEOUT : STOKES_OK);
+    cudaFree(err);
+    return rc;
 }
 
 }  // extern "C"

@@ -511,6 +511,26 @@ def test_batch_solve_matches_single_solves():
         S.close()
 
 
+def test_batch_on_fresh_handles():
+    # the first solve of a handle allocates its SQMR vectors; solved on the batch's own non-blocking
+    # streams, their zero fill must be complete before the solve's kernels run
+    sizes = [24, 32, 16, 48, 32, 24, 40, 16, 32, 24, 48, 16]
+    for rep in range(2):
+        handles, rhs, xs = [], [], []
+        for k, n in enumerate(sizes):
+            S = smg.Stokes(n, precision=smg.PREC_FP32)
+            handles.append(S)
+            rhs.append(S.rhs(synthetic.bumps(n, seed=50 + k + rep, device=DEV)["f"], None))
+            xs.append(torch.zeros_like(rhs[-1]))
+        infos, _ = smg.sqmr_solve_batch([S.h for S in handles], rhs, xs, tol=1e-8, nstreams=6)
+        for S, b, x2, info in zip(handles, rhs, xs, infos):
+            x1, info1 = S.solve(b, tol=1e-8)
+            assert info.status == 0 and info.iterations == info1.iterations
+            assert float(torch.max(torch.abs(x1 - x2))) == 0.0
+        for S in handles:
+            S.close()
+
+
 def test_residual_norm_entry():
     o, S = pair((24, 16, 20))
     b, x = rand_masked(o, 19), rand_masked(o, 20)

@@ -168,3 +168,59 @@ def test_invalid_sizes_rejected():
     with pytest.raises(smg.StokesError):
         ws.predict(torch.zeros(10, dtype=torch.float64))  # host tensor
     ws.close()
+
+
+def test_trained_network_on_held_out_seeds():
+    """Train the BF16 network (tensor-core convolutions) on the method's own solves of 64^3 bump problems,
+    then solve held-out seeds from the learned x0 and from x0 = 0 with the same handle and tolerance,
+    and compare mean iterations and time (the same recipe as the bench's initial-guess mode, smaller)"""
+    import time
+    n, ntrain, ntest = 64, 240, 40
+    S = smg.Stokes(n, precision=smg.PREC_FP32)
+    seeds = [30000 + i for i in range(ntrain + ntest)]
+
+    def rhs(sd):
+        return S.rhs(synthetic.bumps(n, seed=sd, nbumps=8, device=DEV)["f"], None)
+
+    xs, its0 = [], []
+    for sd in seeds:
+        b = rhs(sd)
+        x = torch.zeros_like(b)
+        info = smg.sqmr_solve(S.h, b, x, 1e-8, 200)
+        assert info.status == 0
+        its0.append(info.iterations)
+        xs.append(x.float())
+    scale = float(np.median([float(xs[i].double().norm() / rhs(seeds[i]).norm()) for i in range(32)]))
+    ws = smg.WarmStart(n, smg.STORE_BF16, scale=scale)
+    w = synthetic.net_weights(7).astype(np.float32)
+    w[-16 * 4:] = 0.0  # output layer 0: training starts from x0 = 0
+    ws.set_weights(w)
+    rng = np.random.default_rng(5)
+    steps = 2 * ntrain
+    for st in range(steps):
+        i = int(rng.integers(ntrain))
+        ws.train_step(rhs(seeds[i]), xs[i].double(), 1e-3 * 0.5 * (1 + np.cos(np.pi * st / steps)))
+    loss = np.mean([ws.loss_grad(rhs(seeds[ntrain + k]), xs[ntrain + k].double())[0] for k in range(ntest)])
+    rows = []
+    for k in range(ntest):
+        b = rhs(seeds[ntrain + k])
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info0 = smg.sqmr_solve(S.h, b, x, 1e-8, 200)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, infow, used = ws.solve(S, b, tol=1e-8)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        assert info0.status == 0 and infow.status == 0 and infow.rel_residual < 1e-8
+        rows.append((info0.iterations, t1 - t0, infow.iterations, t2 - t1, used))
+    r = np.array(rows, dtype=np.float64)
+    it0, itw = r[:, 0].mean(), r[:, 2].mean()
+    ms0, msw = 1e3 * r[:, 1].mean(), 1e3 * r[:, 3].mean()
+    print(f"held-out {n}^3 x{ntest}: x0 = 0 {it0:.2f} it {ms0:.2f} ms; learned x0 {itw:.2f} it {msw:.2f} ms; "
+          f"guess used {r[:, 4].mean():.2f}; error-form loss {loss:.3f}")
+    assert loss < 1.0          # the network learned a guess closer to x* than x0 = 0
+    assert itw <= it0 + 0.25   # and starting from it never costs iterations on average
+    ws.close()
+    S.close()
