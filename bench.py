@@ -375,10 +375,12 @@ BATCH_SIZES = (32, 48, 64, 96, 128)
 
 def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
     """Independent problems with cube sizes drawn uniformly from BATCH_SIZES (seeded per rank), Gaussian-bump
-    forcing per problem, FP32 V-cycle + FP64 SQMR to args.tol; solved with sqmr_solve_batch (args.streams
-    concurrent streams).  Beside it: the same problems solved one after another (FP32 V-cycle, and the plain
-    FP64 V-cycle).  sqmr_solve_batch returns once every problem has converged, so a step is timed on the
-    host with the device synchronised on both sides."""
+    forcing per problem, FP32 V-cycle + FP64 SQMR to args.tol.  Headline: the batched form -- the problems of
+    each size in one batched handle (stokes_create_batch: one launch per V-cycle and SQMR step for all of
+    them, the iteration one captured graph), the size classes concurrently on their own streams.  Beside
+    it: sqmr_solve_batch (one handle per problem, args.streams concurrent streams), and the problems solved
+    one after another (FP32 V-cycle, and the plain FP64 V-cycle).  A step returns once every problem has
+    converged, so it is timed on the host with the device synchronised on both sides."""
     sizes, bump_seeds = batch_problems(rank, args.batch)
     S32, rhs, xs = [], [], []
     for i, n in enumerate(sizes):
@@ -402,21 +404,64 @@ def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
         torch.cuda.synchronize()
         return smg.sqmr_solve_batch([S.h for S in S32], rhs, xs, args.tol, 200, nstreams=args.streams)
 
-    for _ in range(args.warmup):
-        batch_step()
-    barrier()
-    lat, its, res = [], [], []
-    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+    # the batched form: one handle per size class holding all problems of that size
+    classes = sorted(set(sizes))
+    members = {n: [i for i, m in enumerate(sizes) if m == n] for n in classes}
+    BH = {n: smg.Stokes(n, precision=smg.PREC_FP32, batch=len(members[n])) if len(members[n]) > 1
+          else smg.Stokes(n, precision=smg.PREC_FP32) for n in classes}
+    cstreams = {n: torch.cuda.Stream(device=dev) for n in classes}
+
+    def batched_step():
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            infos, done = batch_step()
-            lat += done
-            its.append([inf.iterations for inf in infos])
-            res += [inf.rel_residual for inf in infos]
+        infos, done, errs = [None] * len(sizes), [0.0] * len(sizes), []
+
+        def run(n):
+            try:
+                ii = members[n]
+                if len(ii) > 1:
+                    inf = smg.sqmr_solve_batched(BH[n].h, [rhs[i] for i in ii], [xs[i] for i in ii], args.tol, 200,
+                                                 stream=cstreams[n])
+                else:
+                    inf = [smg.sqmr_solve(BH[n].h, rhs[ii[0]], xs[ii[0]], args.tol, 200, stream=cstreams[n])]
+                t = (time.perf_counter() - t0) * 1e3
+                for i, f in zip(ii, inf):
+                    infos[i], done[i] = f, t
+            except Exception as e:  # noqa: BLE001 -- re-raised below on the main thread
+                errs.append(e)
+
+        threads = [threading.Thread(target=run, args=(n,)) for n in classes]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        if errs:
+            raise errs[0]
+        return infos, done
+
+    def timed(step):
+        for _ in range(args.warmup):
+            step()
         barrier()
-        ms = maxrank((time.perf_counter() - t0) * 1e3)
-    assert all(r < args.tol for r in res), max(res)
+        lat, its, res = [], [], []
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                infos, done = step()
+                lat += done
+                its.append([inf.iterations for inf in infos])
+                res += [inf.rel_residual for inf in infos]
+            barrier()
+            ms = maxrank((time.perf_counter() - t0) * 1e3)
+        assert all(r < args.tol for r in res), max(res)
+        return ms, lat, its, clk
+
+    ms, lat, its, clk = timed(batched_step)
     value = total_unknowns * args.steps * world / (ms * 1e-3)
+    ms_st, lat_st, its_st, _ = timed(batch_step)
+    value_st = total_unknowns * args.steps * world / (ms_st * 1e-3)
 
     def sequential(handles, k):
         durations = []
@@ -438,11 +483,19 @@ def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
     ms_seq64, dur64 = sequential(S64, 1)
     for S in S64:
         S.close()
+    # launches of the batched form: per class, its longest-running problem's iterations times the launches of
+    # one iteration of the fixed batched schedule (profiled on a one-problem handle with the same schedule),
+    # plus the per-problem setup and finish launches
     gpu_launches = 0
-    for S, row in zip(S32, zip(*its)):
-        prof = smg.stokes_profile_iteration(S.h)
+    for n in classes:
+        P = smg.Stokes(n, precision=smg.PREC_FP32, autotune=False)
+        prof = smg.stokes_profile_iteration(P.h)
         per_iter = sum(v[1] for v in prof.values())
-        gpu_launches += sum(row) * per_iter + per_iter + 16
+        P.close()
+        k = max(its[-1][i] for i in members[n])
+        gpu_launches += k * per_iter + per_iter + 16 * len(members[n])
+    for S in BH.values():
+        S.close()
     if rank == 0:
         q = lambda a, p: float(np.percentile(np.asarray(a), p))
         line = {
@@ -455,9 +508,16 @@ def run_batch(args, smg, synthetic, torch, dev, rank, world, dist):
                        "sizes": sizes, "unknowns_per_batch": total_unknowns, "streams": args.streams, "tol": args.tol,
                        "timer": "host clock, device synchronised on both sides (the batch call blocks until done)",
                        "parallelism": f"replicas x{world}"},
+            "form": "batched handles: one per size class (%s problems), one launch per V-cycle and SQMR step for "
+                    "all problems of the class, the iteration one CUDA graph; the classes concurrently on %d streams"
+                    % ({n: len(members[n]) for n in classes}, len(classes)),
             "iterations": its[-1],
             "latency_ms": {"p50": q(lat, 50), "p99": q(lat, 99), "max": max(lat),
-                           "meaning": "time from the batch call's start to the problem's solution"},
+                           "meaning": "time from the step's start to the problem's solution (its size class's end)"},
+            "streams_path": {"value": value_st, "unit": UNIT, "ms_per_step": ms_st / args.steps,
+                             "latency_ms": {"p50": q(lat_st, 50), "p99": q(lat_st, 99), "max": max(lat_st)},
+                             "form": "sqmr_solve_batch: one handle per problem, %d host threads with a stream each"
+                                     % args.streams},
             "sequential_fp32_vcycle": {"value": total_unknowns * world / (ms_seq32 * 1e-3), "unit": UNIT,
                                        "ms_per_batch": ms_seq32, "solve_ms_p50": q(dur32, 50), "solve_ms_p99": q(dur32, 99)},
             "sequential_fp64_vcycle": {"value": total_unknowns * world / (ms_seq64 * 1e-3), "unit": UNIT,

@@ -185,6 +185,27 @@ int mg_solve(stokes_t h, const double *rhs, double *x, double tol, int max_iter,
 int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rhs, double *const *x, double tol,
                      int max_iter, sqmr_info_t *infos, double *done_ms, int nstreams);
 
+/* Batched handle: nprob (2..4096) independent problems on ONE grid (same grid, bc, viscosity and
+ * options; nprob * 4 (nz + 1) <= 65535), created with stokes_create's arguments.  Every per-problem
+ * buffer of a multigrid level lies in one device allocation (problem p's copy at a fixed stride), so
+ * each step of the V-cycle (Alg. 1, Alg. 3) and of the SQMR iteration (Alg. 4) is ONE kernel launch
+ * for all problems, and the iteration is one captured CUDA graph.  The schedule is fixed (per-colour
+ * Vanka launches, in-place DGS; no autotuning, no distributive Jacobi, graphs on); results are
+ * bit-identical to solving each problem with stokes_create + sqmr_solve.  stokes_rhs works as for a
+ * single handle (it reads only the grid); the other single-problem calls return
+ * STOKES_ERR_INVALID_ARG on a batched handle.  Free with stokes_destroy. */
+int stokes_create_batch(int nprob, const stokes_grid_t *grid, const stokes_bc_t *bc, double viscosity,
+                        const stokes_opts_t *opts, stokes_t *out);
+/* problems in a handle (1 for stokes_create's handles, 0 for NULL) */
+int stokes_batch_size(stokes_t h);
+/* Alg. 4 for every problem of a batched handle: rhs[p], x[p] (x0 in, solution out) as sqmr_solve's
+ * (host or device).  Per-problem convergence: a problem stops (its state frozen on the device) at the
+ * iteration its own explicit FP64 residual confirms tol, as in sqmr_solve; the call returns when every
+ * problem has stopped.  infos (may be NULL) receives nprob results; returns STOKES_OK or the first
+ * problem's non-OK status. */
+int sqmr_solve_batched(stokes_t h, const double *const *rhs, double *const *x, double tol, int max_iter,
+                       sqmr_info_t *infos, void *stream);
+
 /* the Vanka schedule of a smoothed level (chosen by the autotuner): *mode 0 = two launches per
  * colour, 1 = one cooperative launch per symmetric sweep with *blocks thread blocks (grid barrier),
  * 2 = one launch per symmetric sweep in a single thread-block cluster of *blocks CTAs (hardware

@@ -26,7 +26,8 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            "stokes_residual_norm", "stokes_smooth", "stokes_restrict", "stokes_prolong_add", "stokes_coarse_solve",
            "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
            "stokes_set_level_schedule", "stokes_level_tiles", "stokes_set_level_tiles", "stokes_level_dgs",
-           "stokes_set_level_dgs", "sqmr_solve_unpreconditioned",
+           "stokes_set_level_dgs", "sqmr_solve_unpreconditioned", "stokes_create_batch", "stokes_batch_size",
+           "sqmr_solve_batched",
            "mg_solve",
            "stokes_measure_fma_peak", "stokes_label_flags", "stokes_test_grid_barrier", "stokes_strerror",
            # learned initial guess (include/warmstart.h)
@@ -100,6 +101,10 @@ def _load():
                                    ctypes.POINTER(ctypes.c_uint8), ll]),
         "sqmr_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,
                                  ctypes.POINTER(sqmr_info_t), ctypes.POINTER(d), i]),
+        "stokes_create_batch": (i, [i, ctypes.POINTER(stokes_grid_t), ctypes.POINTER(stokes_bc_t), d,
+                                    ctypes.POINTER(stokes_opts_t), ctypes.POINTER(vp)]),
+        "stokes_batch_size": (i, [vp]),
+        "sqmr_solve_batched": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, ctypes.POINTER(sqmr_info_t), vp]),
         "stokes_level_schedule": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
         "stokes_set_level_schedule": (i, [vp, i, i, i]),
         "stokes_level_tiles": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
@@ -189,9 +194,10 @@ def stokes_opts_default():
 
 def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest_max=8, gamma=1e-3, kb_vanka=1,
                   precision=PREC_FP64, use_graphs=True, vanka_persistent=False, autotune=True, additive=False, cycle=1,
-                  dwj=False, labels=None):
+                  dwj=False, labels=None, batch=1):
     """labels: None (the box) or a uint8 array of (nx+2)(ny+2)(nz+2) cell labels, x fastest (0 interior,
-    1 Dirichlet, 2 exterior); it is copied by the library."""
+    1 Dirichlet, 2 exterior); it is copied by the library.  batch > 1: a batched handle of that many
+    problems on this grid (stokes_create_batch; solve with sqmr_solve_batched)."""
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     g = stokes_grid_t(nx, ny, nz, h, levels, coarsest_max)
@@ -205,8 +211,12 @@ def stokes_create(nx, ny=None, nz=None, viscosity=1.0, h=0.0, levels=0, coarsest
             raise ValueError("labels must hold (nx+2)(ny+2)(nz+2) entries")
         bc = stokes_bc_t(lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     hdl = ctypes.c_void_p()
-    _check(lib().stokes_create(ctypes.byref(g), None if bc is None else ctypes.byref(bc), viscosity,
-                               ctypes.byref(o), ctypes.byref(hdl)), "stokes_create")
+    if batch > 1:
+        _check(lib().stokes_create_batch(int(batch), ctypes.byref(g), None if bc is None else ctypes.byref(bc),
+                                         viscosity, ctypes.byref(o), ctypes.byref(hdl)), "stokes_create_batch")
+    else:
+        _check(lib().stokes_create(ctypes.byref(g), None if bc is None else ctypes.byref(bc), viscosity,
+                                   ctypes.byref(o), ctypes.byref(hdl)), "stokes_create")
     return hdl
 
 
@@ -372,6 +382,22 @@ def sqmr_solve_batch(handles, rhs, xs, tol=1e-8, max_iter=200, nstreams=8, check
     if check:
         _check(rc, "sqmr_solve_batch")
     return list(infos), list(done)
+
+
+def sqmr_solve_batched(h, rhs, xs, tol=1e-8, max_iter=200, stream=None, check=True):
+    """All problems of a batched handle (one launch per step for all of them).  Returns the list of infos."""
+    n = len(rhs)
+    R = (ctypes.c_void_p * n)(*[_ptr(b) for b in rhs])
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    infos = (sqmr_info_t * n)()
+    rc = lib().sqmr_solve_batched(h, R, X, tol, max_iter, infos, _stream(stream))
+    if check:
+        _check(rc, "sqmr_solve_batched")
+    return list(infos)
+
+
+def stokes_batch_size(h):
+    return int(lib().stokes_batch_size(h))
 
 
 def sqmr_solve_unpreconditioned(h, rhs, x, tol=1e-8, max_iter=200, stream=None, check=True):

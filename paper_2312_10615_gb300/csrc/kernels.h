@@ -108,6 +108,13 @@ struct SqmrState {
     double rho, sigma, alpha, tau, nu, nu_prev, c2, coefA, coefB, beta, rho_new;
     double tt, st, rr, bb, pmean;
     int breakdown, nonfinite, iter, dx_pending;
+    int frozen, pad;  // batched solves: a problem that has converged keeps its state (its kernels return)
+};
+// problems of a batched launch of the SQMR kernels: nb problems, problem p's vectors, partials and state
+// at byte offset p * bs from problem 0's, its two host-visible values at host_out + 2 p
+struct Bat {
+    int nb = 1;
+    long long bs = 0;
 };
 
 constexpr int kRedBlocks = 1184;  // 152 SMs x 8 resident 256-thread blocks: grid of every reduction kernel
@@ -120,24 +127,26 @@ int launch_apply_dot(const Lev &L, const double *q, double *w, double *partials,
 // w = b - L x (w may be null) with partials of |b - Lx|^2
 int launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s);
 // partials of a.a (and optionally a.b)
-template <class T> void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s);
+template <class T>
+void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s, const Bat &bt = Bat());
 // scalar stages on one thread block: 0 alpha (after q.Lq), 1 nu/c/tau/beta (after |t|^2, s.t),
 // 2 residual norm (after |r|^2), 3 init (after |t|^2, s.t of the first V-cycle), 4 |b|^2, 5 pressure mean
 void launch_scalars(int stage, const double *partials, int nparts, SqmrState *st, double *host_out,
-                    cudaStream_t s);
+                    cudaStream_t s, const Bat &bt = Bat());
 void launch_scalars_aux(int stage, const double *partials, int nparts, SqmrState *st, double *host_out, double aux,
                         cudaStream_t s);
 // s -= alpha w ; optionally b32 = (T) s for a lower-precision V-cycle
 template <class T>
-void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream);
+void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream,
+                     const Bat &bt = Bat());
 // the d, x, r, q recurrences of Alg. 4 in two parts: r = (1-c2) r + c2 s ; qn = t + beta qo ; partials of
 // |r|^2 (the part the next iteration needs) and, when st->dx_pending, d = coefA d + coefB qo ; x += d (the
 // iterate, deferred into the next iteration)
 template <class T>
 void launch_update_rq(long long n, const double *qo, double *qn, const T *t, double *r, const double *sv,
-                      const SqmrState *st, double *partials, cudaStream_t s);
+                      const SqmrState *st, double *partials, cudaStream_t s, const Bat &bt = Bat());
 void launch_update_dx(long long n, double *x, double *d, const double *qo, const SqmrState *st, cudaStream_t s,
-                      int blocks = 0);
+                      int blocks = 0, const Bat &bt = Bat());
 // q = t (widening), d = 0
 template <class T> void launch_init_q(long long n, const T *t, double *q, double *d, cudaStream_t s);
 template <class T> void launch_add_to(long long n, const T *t, double *x, cudaStream_t s);

@@ -140,7 +140,7 @@ template <int C, class IDX> __device__ __forceinline__ long long entry_index(con
     const IDX sy = (IDX)(L.nx + (C == 0)), sz = sy * (IDX)(L.ny + (C == 1));
     return L.off[C] + (long long)((IDX)i + sy * (IDX)j + sz * (IDX)k);
 }
-inline dim3 entry_grid(const Lev &L) { return dim3(cdiv(L.nx + 1, BX), cdiv(L.ny + 1, BY), 4 * (L.nz + 1)); }
+inline dim3 entry_grid(const Lev &L) { return dim3(cdiv(L.nx + 1, BX), cdiv(L.ny + 1, BY), 4 * (L.nz + 1) * L.nb); }
 // offsets of every component fit 32 bits
 inline bool idx32(const Lev &L) { return (long long)(L.nx + 1) * (L.ny + 1) * (L.nz + 1) < (1LL << 31); }
 
@@ -161,7 +161,11 @@ template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                   TB *__restrict__ y, Coef<T> K) {
     pdl_wait();
-    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    b = bslot(b, L.bstride, zs.p);
+    y = bslot(y, L.bstride, zs.p);
+    const int c = zs.z & 3, k = zs.z >> 2;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
     case 0: apply_entry<T, TB, 0, IDX>(L, x, b, y, K, i, j, k); break;
@@ -254,9 +258,12 @@ template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, const TB *__restrict__ b, int parity,
                                                   Coef<T> K) {
     pdl_wait();
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    b = bslot(b, L.bstride, zs.p);
     const int j = 1 + blockIdx.y * BY + threadIdx.y;
     if (j > L.ny - 2) return;
-    const int k = 1 + blockIdx.z;
+    const int k = 1 + zs.z;
     int i = 1 + 2 * (blockIdx.x * BX + threadIdx.x);
     i += (i + j + k + parity) & 1;
     if (i > L.nx - 2) return;
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, cons
 
 template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, int parity, cudaStream_t s) {
     if (L.nx < 3 || L.ny < 3 || L.nz < 3) return;
-    dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), L.nz - 2);
+    dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), (L.nz - 2) * L.nb);
     if (idx32(L)) launch_k(k_dgs_u<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
     else launch_k(k_dgs_u<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
 }
@@ -505,9 +512,13 @@ template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                    T *__restrict__ delta, int colour, Coef<T> K, T dP) {
     pdl_wait();
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    b = bslot(b, L.bstride, zs.p);
+    delta = bslot(delta, L.bstride, zs.p);
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
-    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
+    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = zs.z;
     if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
     p_fwd_cell<T, TB, IDX>(L, x, b, delta, colour, (IDX)(lo[0] + 2 * ti), (IDX)(lo[1] + 2 * tj), (IDX)(lo[2] + 2 * tk),
                            K, dP);
@@ -521,10 +532,14 @@ template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(512) k_dgs_p_fwd_pair(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                         T *__restrict__ delta, int colour, Coef<T> K, T dP) {
     pdl_wait();
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    b = bslot(b, L.bstride, zs.p);
+    delta = bslot(delta, L.bstride, zs.p);
     int lo[3], cnt[3], lo2[3], cnt2[3];
     v2_colour_range(L, colour, lo, cnt);
     v2_colour_range(L, colour ^ 1, lo2, cnt2);  // same j and k ranges
-    const int ti = threadIdx.x, tj = blockIdx.y * blockDim.y + threadIdx.y, tk = blockIdx.z;
+    const int ti = threadIdx.x, tj = blockIdx.y * blockDim.y + threadIdx.y, tk = zs.z;
     const bool row = tj < cnt[1] && tk < cnt[2];
     const IDX j = (IDX)(lo[1] + 2 * tj), k = (IDX)(lo[2] + 2 * tk);
     if (row && ti < cnt[0]) p_fwd_cell<T, TB, IDX>(L, x, b, delta, colour, (IDX)(lo[0] + 2 * ti), j, k, K, dP);
@@ -536,7 +551,10 @@ template <class T>
 __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, const T *__restrict__ delta,
                                                       Coef<T> K) {
     pdl_wait();
-    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    delta = bslot(delta, L.bstride, zs.p);
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = zs.z;
     if (i >= L.nx || j >= L.ny || k >= L.nz) return;
     long long t = cell_lin(L, i, j, k);
     bool v2 = in_v2_cell(L, i, j, k);
@@ -593,7 +611,12 @@ __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict_
                                                            TB *__restrict__ gh, const T *__restrict__ delta,
                                                            Coef<T> K) {
     pdl_wait();
-    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    b = bslot(b, L.bstride, zs.p);
+    gh = bslot(gh, L.bstride, zs.p);
+    delta = bslot(delta, L.bstride, zs.p);
+    const int c = zs.z & 3, k = zs.z >> 2;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
     case 0: prep_entry<T, TB, 0, IDX>(L, x, b, gh, delta, K, i, j, k); break;
@@ -729,7 +752,7 @@ __device__ __forceinline__ void rows4u(const T *__restrict__ x, const Lev &L, in
 
 // launch shape of the four-per-thread kernels: the component in the low two bits of blockIdx.z as in
 // the one-entry kernels; x tiles cover the longest row (u, nx + 1 entries) in groups of four
-inline dim3 grid4(const Lev &L) { return dim3(cdiv(L.nx + 1, 4 * BX), cdiv(L.ny + 1, BY), 4 * (L.nz + 1)); }
+inline dim3 grid4(const Lev &L) { return dim3(cdiv(L.nx + 1, 4 * BX), cdiv(L.ny + 1, BY), 4 * (L.nz + 1) * L.nb); }
 // box only (no label flags), rows of v, w, p on 4-entry boundaries (nx % 4 == 0 and the v block at a
 // multiple of 4), and every array 16-byte aligned
 inline bool al16(const void *p) { return ((uintptr_t)p & 15) == 0; }
@@ -773,7 +796,11 @@ template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256, 8) k_apply4(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                    TB *__restrict__ y, Coef<T> K) {
     pdl_wait();
-    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    b = bslot(b, L.bstride, zs.p);
+    y = bslot(y, L.bstride, zs.p);
+    const int c = zs.z & 3, k = zs.z >> 2;
     const int i = 4 * (blockIdx.x * BX + threadIdx.x), j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
     case 0: apply_u4<T, TB, IDX>(L, x, b, y, K, i, j, k); break;
@@ -839,7 +866,12 @@ __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep4(Lev L, T *__restrict
                                                             TB *__restrict__ gh, const T *__restrict__ delta,
                                                             Coef<T> K) {
     pdl_wait();
-    const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    b = bslot(b, L.bstride, zs.p);
+    gh = bslot(gh, L.bstride, zs.p);
+    delta = bslot(delta, L.bstride, zs.p);
+    const int c = zs.z & 3, k = zs.z >> 2;
     const int i = 4 * (blockIdx.x * BX + threadIdx.x), j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
     case 0: prep_u4<T, TB, IDX>(L, x, b, gh, K, i, j, k); break;
@@ -878,9 +910,12 @@ template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const TB *__restrict__ ghs, int colour,
                                                    Coef<T> K, T dP) {
     pdl_wait();
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    ghs = bslot(ghs, L.bstride, zs.p);
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
-    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = blockIdx.z;
+    const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = zs.z;
     if (ti >= cnt[0] || tj >= cnt[1] || tk >= cnt[2]) return;
     p_bwd_cell<T, TB, IDX>(L, x, ghs, (IDX)(lo[0] + 2 * ti), (IDX)(lo[1] + 2 * tj), (IDX)(lo[2] + 2 * tk), K, dP);
 }
@@ -890,10 +925,13 @@ template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(512) k_dgs_p_bwd_pair(Lev L, T *__restrict__ x, const TB *__restrict__ ghs,
                                                         int colour, Coef<T> K, T dP) {
     pdl_wait();
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    ghs = bslot(ghs, L.bstride, zs.p);
     int lo[3], cnt[3], lo2[3], cnt2[3];
     v2_colour_range(L, colour, lo, cnt);
     v2_colour_range(L, colour ^ 1, lo2, cnt2);
-    const int ti = threadIdx.x, tj = blockIdx.y * blockDim.y + threadIdx.y, tk = blockIdx.z;
+    const int ti = threadIdx.x, tj = blockIdx.y * blockDim.y + threadIdx.y, tk = zs.z;
     const bool row = tj < cnt[1] && tk < cnt[2];
     const IDX j = (IDX)(lo[1] + 2 * tj), k = (IDX)(lo[2] + 2 * tk);
     if (row && ti < cnt[0]) p_bwd_cell<T, TB, IDX>(L, x, ghs, (IDX)(lo[0] + 2 * ti), j, k, K, dP);
@@ -910,7 +948,7 @@ void launch_dgs_p_fwd(const Lev &L, T *x, const TB *b, T *delta, int colour, cud
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
-    dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
+    dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2] * L.nb);
     if (idx32(L))
         launch_k(k_dgs_p_fwd<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
@@ -928,7 +966,7 @@ inline bool pair_block(const Lev &L, int colour, dim3 &grid, dim3 &block) {
     if (rx == 0 || rx > 512 || (long long)cnt[1] * cnt[2] == 0) return false;
     const int ry = rx >= 256 ? 1 : 256 / rx;
     block = dim3(rx, ry, 1);
-    grid = dim3(1, cdiv(cnt[1], ry), cnt[2]);
+    grid = dim3(1, cdiv(cnt[1], ry), cnt[2] * L.nb);
     return true;
 }
 template <class T, class TB>
@@ -955,7 +993,7 @@ template <class T, class TB> bool launch_dgs_p_bwd_pair(const Lev &L, T *x, cons
     return true;
 }
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s) {
-    dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz);
+    dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz * L.nb);
     launch_k(k_dgs_p_gather<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, delta, coef<T>(L, L.gamma));
 }
 template <class T, class TB>
@@ -991,7 +1029,7 @@ template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB 
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
-    dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2]);
+    dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2] * L.nb);
     if (idx32(L))
         launch_k(k_dgs_p_bwd<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
@@ -1143,6 +1181,9 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
                                                        int ncell, const T *__restrict__ kinv, T *__restrict__ corr,
                                                        int cap, Coef<T> K, T w) {
     pdl_wait();
+    x = bslot(x, L.bstride, (int)blockIdx.y);
+    b = bslot(b, L.bstride, (int)blockIdx.y);
+    corr = bslot(corr, L.bstride, (int)blockIdx.y);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3;
     if (slot >= ncell) return;  // whole 8-lane groups leave together
@@ -1154,6 +1195,8 @@ template <class T>
 __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, const int *__restrict__ cells,
                                                      int ncell, const T *__restrict__ corr, int cap) {
     pdl_wait();
+    x = bslot(x, L.bstride, (int)blockIdx.y);
+    corr = bslot(corr, L.bstride, (int)blockIdx.y);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3;
     if (slot >= ncell) return;
@@ -1165,16 +1208,16 @@ void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cell
                           const T *kinv, T *corr, int cap, double w, cudaStream_t s) {
     if (ncell <= 0) return;
     if (idx32(L))
-        launch_k(k_vanka_compute<T, TB, int>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, tab, ncell,
+        launch_k(k_vanka_compute<T, TB, int>, dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, b, cells, tab, ncell,
                  kinv, corr, cap, coef<T>(L, L.gamma), T(w));
     else
-        launch_k(k_vanka_compute<T, TB, long long>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, b, cells, tab,
+        launch_k(k_vanka_compute<T, TB, long long>, dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, b, cells, tab,
                  ncell, kinv, corr, cap, coef<T>(L, L.gamma), T(w));
 }
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    launch_k(k_vanka_apply<T>, dim3(cdiv(8LL * ncell, 256)), dim3(256), 0, s, L, x, cells, ncell, corr, cap);
+    launch_k(k_vanka_apply<T>, dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, cells, ncell, corr, cap);
 }
 
 // ---- one launch per colour step: two copies of the level's Vanka state (ping-pong) ----
@@ -1722,12 +1765,12 @@ __device__ __forceinline__ T restrict_face(const Lev &F, const Lev &Cl, const TF
 }
 
 // thread_entry with the launch's own tile: block (blockDim.x, blockDim.y) over (x, y), kz planes per thread
-__device__ __forceinline__ bool thread_entry_tile(const Lev &L, int gy, int kz, int &c, int &i, int &j, int &k0,
+__device__ __forceinline__ bool thread_entry_tile(const Lev &L, int gy, int kz, int zb, int &c, int &i, int &j, int &k0,
                                                   int &k1) {
     c = blockIdx.y / gy;
     i = blockIdx.x * blockDim.x + threadIdx.x;
     j = (blockIdx.y - c * gy) * blockDim.y + threadIdx.y;
-    k0 = blockIdx.z * kz;
+    k0 = zb * kz;
     int ez = ext(L, c, 2);
     k1 = k0 + kz < ez ? k0 + kz : ez;
     return i < ext(L, c, 0) && j < ext(L, c, 1) && k0 < ez;
@@ -1737,8 +1780,11 @@ template <class T, class TF, class TC>
 __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, int kz, const TF *__restrict__ rf,
                                                   TC *__restrict__ bc) {
     pdl_wait();
+    const ZSlot zs = zslot(C);
+    rf = bslot(rf, F.bstride, zs.p);
+    bc = bslot(bc, C.bstride, zs.p);
     int c, I, J, k0, k1;
-    if (!thread_entry_tile(C, gy, kz, c, I, J, k0, k1)) return;
+    if (!thread_entry_tile(C, gy, kz, zs.z, c, I, J, k0, k1)) return;
     for (int Kk = k0; Kk < k1; ++Kk) {
     long long q = pidx(C, c, I, J, Kk);
     if (!unknown(C, c, I, J, Kk)) {
@@ -1819,9 +1865,12 @@ __device__ __forceinline__ void prolong_comp(const Lev &F, const Lev &Cl, const 
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, int kz, const T *__restrict__ ec, T *__restrict__ xf) {
     pdl_wait();
+    const ZSlot zs = zslot(Cl);
+    ec = bslot(ec, Cl.bstride, zs.p);
+    xf = bslot(xf, F.bstride, zs.p);
     int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= Cl.nx || J >= Cl.ny) return;
-    int k0 = blockIdx.z * kz, k1 = k0 + kz < Cl.nz ? k0 + kz : Cl.nz;
+    int k0 = zs.z * kz, k1 = k0 + kz < Cl.nz ? k0 + kz : Cl.nz;
     const long long fy = F.nx, fz = (long long)F.nx * F.ny;
     for (int Kk = k0; Kk < k1; ++Kk) {
         T pcv = ec[pidx(Cl, 3, I, J, Kk)];
@@ -1845,11 +1894,11 @@ template <class T, class TF, class TC>
 void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s, Tile t) {
     const int mx = C.nx + 1, my = C.ny + 1, mz = C.nz + 1;
     const int gy = cdiv(my, t.by);
-    launch_k(k_restrict<T, TF, TC>, dim3(cdiv(mx, t.bx), gy * 4, cdiv(mz, t.kz)), dim3(t.bx, t.by, 1), 0, s, F, C, gy,
-             t.kz, rf, bc);
+    launch_k(k_restrict<T, TF, TC>, dim3(cdiv(mx, t.bx), gy * 4, cdiv(mz, t.kz) * C.nb), dim3(t.bx, t.by, 1), 0, s, F, C,
+             gy, t.kz, rf, bc);
 }
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s, Tile t) {
-    dim3 grid(cdiv(C.nx, t.bx), cdiv(C.ny, t.by), cdiv(C.nz, t.kz));
+    dim3 grid(cdiv(C.nx, t.bx), cdiv(C.ny, t.by), cdiv(C.nz, t.kz) * C.nb);
     launch_k(k_prolong<T>, dim3(grid), dim3(t.bx, t.by, 1), 0, s, F, C, t.kz, ec, xf);
 }
 
@@ -1858,8 +1907,10 @@ template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, 
 // deterministic lane-strided sums then a fixed shuffle tree)
 template <class T>
 __global__ void __launch_bounds__(256) k_coarse(const int *__restrict__ cidx, int nc, const double *__restrict__ kinv,
-                                                const T *__restrict__ b, T *__restrict__ x) {
+                                                const T *__restrict__ b, T *__restrict__ x, long long bstride) {
     pdl_wait();
+    b = bslot(b, bstride, (int)blockIdx.y);
+    x = bslot(x, bstride, (int)blockIdx.y);
     extern __shared__ double sb[];
     for (int m = threadIdx.x; m < nc; m += blockDim.x) sb[m] = (double)b[cidx[m]];
     __syncthreads();
@@ -1876,9 +1927,9 @@ __global__ void __launch_bounds__(256) k_coarse(const int *__restrict__ cidx, in
 
 template <class T>
 void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, const T *b, T *x, cudaStream_t s) {
-    (void)C;
     int rows_per_block = 256 / 32;
-    launch_k(k_coarse<T>, dim3((nc + rows_per_block - 1) / rows_per_block), dim3(256), nc * sizeof(double), s, cidx, nc, kinv, b, x);
+    launch_k(k_coarse<T>, dim3((nc + rows_per_block - 1) / rows_per_block, C.nb), dim3(256), nc * sizeof(double), s, cidx,
+             nc, kinv, b, x, C.bstride);
 }
 
 // ------------------------------------------------------------------------------------------

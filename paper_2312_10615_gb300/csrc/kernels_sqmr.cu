@@ -53,10 +53,15 @@ template <bool RESIDUAL>
 __global__ void __launch_bounds__(256) k_apply_red(Lev L, const double *__restrict__ x, const double *__restrict__ b,
                                                    double *__restrict__ w, double *partials, Coef<double> K) {
     pdl_wait();
+    const ZSlot zs = zslot(L);
+    x = bslot(x, L.bstride, zs.p);
+    b = bslot(b, L.bstride, zs.p);
+    w = bslot(w, L.bstride, zs.p);
+    partials = bslot(partials, L.bstride, zs.p);
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     double v[1] = {0.0};
     if (i <= L.nx && j <= L.ny) {
-        int k0 = blockIdx.z * KZR, k1 = k0 + KZR < L.nz + 1 ? k0 + KZR : L.nz + 1;
+        int k0 = zs.z * KZR, k1 = k0 + KZR < L.nz + 1 ? k0 + KZR : L.nz + 1;
         for (int k = k0; k < k1; ++k) {
             Quad Q = quad_at(L, i, j, k);
             double o[4];
@@ -79,23 +84,33 @@ __global__ void __launch_bounds__(256) k_apply_red(Lev L, const double *__restri
             }
         }
     }
-    block_store<1>(v, partials, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+    block_store<1>(v, partials, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zs.z));
+}
+// red_grid for all the problems of a batched level (z blocks of problem p follow those of p - 1)
+static dim3 red_grid_all(const Lev &L) {
+    dim3 g = red_grid(L);
+    g.z *= L.nb;
+    return g;
 }
 
 int launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s) {
-    launch_k(k_apply_red<false>, red_grid(L), dim3(BX, BY, 1), 0, s, L, q, nullptr, w, partials, coef<double>(L, 0.0));
+    launch_k(k_apply_red<false>, red_grid_all(L), dim3(BX, BY, 1), 0, s, L, q, nullptr, w, partials,
+             coef<double>(L, 0.0));
     return reduce_parts(L);
 }
 int launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s) {
-    launch_k(k_apply_red<true>, red_grid(L), dim3(BX, BY, 1), 0, s, L, x, b, w, partials, coef<double>(L, 0.0));
+    launch_k(k_apply_red<true>, red_grid_all(L), dim3(BX, BY, 1), 0, s, L, x, b, w, partials, coef<double>(L, 0.0));
     return reduce_parts(L);
 }
 
 // a.a and a.b
 template <class T>
 __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__ a, const double *__restrict__ b,
-                                              double *partials) {
+                                              double *partials, long long bs) {
     pdl_wait();
+    a = bslot(a, bs, (int)blockIdx.y);
+    b = bslot(b, bs, (int)blockIdx.y);
+    partials = bslot(partials, bs, (int)blockIdx.y);
     double v[2] = {0.0, 0.0};
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         double x = (double)a[t];
@@ -104,14 +119,19 @@ __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__
     }
     block_store<2>(v, partials, blockIdx.x);
 }
-template <class T> void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s) {
-    launch_k(k_dot2<T>, dim3(kRedBlocks), dim3(kBlock), 0, s, n, a, b, partials);
+template <class T>
+void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s, const Bat &bt) {
+    launch_k(k_dot2<T>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, a, b, partials, bt.bs);
 }
 
 // scalar recurrences of Alg. 4 (one block; fixed-order sum of the nparts partials)
 __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partials, int nparts, SqmrState *st,
-                                                 double *host_out, double aux) {
+                                                 double *host_out, double aux, long long bs) {
     pdl_wait();
+    partials = bslot(partials, bs, (int)blockIdx.x);
+    st = bslot(st, bs, (int)blockIdx.x);
+    host_out += 2 * blockIdx.x;
+    if (st->frozen && stage <= 2) return;
     __shared__ double sh[kRedParts][kBlock];
     double v[kRedParts] = {0.0, 0.0, 0.0};
     for (int t = threadIdx.x; t < nparts; t += blockDim.x)
@@ -188,19 +208,24 @@ __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partia
 }
 
 void launch_scalars(int stage, const double *partials, int nparts, SqmrState *st, double *host_out,
-                    cudaStream_t s) {
-    launch_k(k_scalars, dim3(1), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, 0.0);
+                    cudaStream_t s, const Bat &bt) {
+    launch_k(k_scalars, dim3(bt.nb), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, 0.0, bt.bs);
 }
 void launch_scalars_aux(int stage, const double *partials, int nparts, SqmrState *st, double *host_out, double aux,
                         cudaStream_t s) {
-    launch_k(k_scalars, dim3(1), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, aux);
+    launch_k(k_scalars, dim3(1), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, aux, 0LL);
 }
 
 // s_j = s_{j-1} - alpha t  (t = L q_{j-1}); optional narrowed copy for the V-cycle
 template <class T>
 __global__ void __launch_bounds__(256) k_update_s(long long n, double *__restrict__ s, const double *__restrict__ w,
-                                                  const SqmrState *__restrict__ st, T *__restrict__ bT) {
+                                                  const SqmrState *__restrict__ st, T *__restrict__ bT, long long bs) {
     pdl_wait();
+    s = bslot(s, bs, (int)blockIdx.y);
+    w = bslot(w, bs, (int)blockIdx.y);
+    st = bslot(st, bs, (int)blockIdx.y);
+    bT = bslot(bT, bs, (int)blockIdx.y);
+    if (st->frozen) return;
     double alpha = st->alpha;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         double v = s[t] - alpha * w[t];
@@ -209,8 +234,9 @@ __global__ void __launch_bounds__(256) k_update_s(long long n, double *__restric
     }
 }
 template <class T>
-void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream) {
-    launch_k(k_update_s<T>, dim3(kRedBlocks), dim3(kBlock), 0, stream, n, s, w, st, bT);
+void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream,
+                     const Bat &bt) {
+    launch_k(k_update_s<T>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, stream, n, s, w, st, bT, bt.bs);
 }
 
 // d_j = c^2 nu_{j-1}^2 d_{j-1} + c^2 alpha q_{j-1};  x_j = x_{j-1} + d_j;
@@ -226,8 +252,17 @@ template <class T>
 __global__ void __launch_bounds__(256) k_update_rq(long long n, const double *__restrict__ qo, double *__restrict__ qn,
                                                    const T *__restrict__ tv, double *__restrict__ r,
                                                    const double *__restrict__ sv, const SqmrState *__restrict__ st,
-                                                   double *partials) {
+                                                   double *partials, long long bs) {
     pdl_wait();
+    const int p = (int)blockIdx.y;
+    qo = bslot(qo, bs, p);
+    qn = bslot(qn, bs, p);
+    tv = bslot(tv, bs, p);
+    r = bslot(r, bs, p);
+    sv = bslot(sv, bs, p);
+    st = bslot(st, bs, p);
+    partials = bslot(partials, bs, p);
+    if (st->frozen) return;  // the whole block: one problem per blockIdx.y
     const double c2 = st->c2, beta = st->beta;
     double v[1] = {0.0};
 #pragma unroll 1
@@ -241,9 +276,15 @@ __global__ void __launch_bounds__(256) k_update_rq(long long n, const double *__
     block_store<1>(v, partials, blockIdx.x);
 }
 __global__ void __launch_bounds__(256) k_update_dx(long long n, double *__restrict__ x, double *__restrict__ d,
-                                                   const double *__restrict__ qo, const SqmrState *__restrict__ st) {
+                                                   const double *__restrict__ qo, const SqmrState *__restrict__ st,
+                                                   long long bs) {
     pdl_wait();
-    if (!st->dx_pending) return;
+    const int p = (int)blockIdx.y;
+    x = bslot(x, bs, p);
+    d = bslot(d, bs, p);
+    qo = bslot(qo, bs, p);
+    st = bslot(st, bs, p);
+    if (!st->dx_pending || st->frozen) return;
     const double A = st->coefA, B = st->coefB;
 #pragma unroll 1
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -254,14 +295,14 @@ __global__ void __launch_bounds__(256) k_update_dx(long long n, double *__restri
 }
 template <class T>
 void launch_update_rq(long long n, const double *qo, double *qn, const T *t, double *r, const double *sv,
-                      const SqmrState *st, double *partials, cudaStream_t s) {
-    launch_k(k_update_rq<T>, dim3(kRedBlocks), dim3(kBlock), 0, s, n, qo, qn, t, r, sv, st, partials);
+                      const SqmrState *st, double *partials, cudaStream_t s, const Bat &bt) {
+    launch_k(k_update_rq<T>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, qo, qn, t, r, sv, st, partials, bt.bs);
 }
 // blocks: the full reduction grid when it runs alone; a few per SM when it runs beside the V-cycle, so
 // that the V-cycle's kernels keep most of every SM's thread slots
 void launch_update_dx(long long n, double *x, double *d, const double *qo, const SqmrState *st, cudaStream_t s,
-                      int blocks) {
-    launch_k(k_update_dx, dim3(blocks > 0 ? blocks : kRedBlocks), dim3(kBlock), 0, s, n, x, d, qo, st);
+                      int blocks, const Bat &bt) {
+    launch_k(k_update_dx, dim3(blocks > 0 ? blocks : kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, x, d, qo, st, bt.bs);
 }
 
 template <class T>
@@ -299,15 +340,18 @@ void launch_psub(const Lev &L, double *x, const SqmrState *st, cudaStream_t s) {
     launch_k(k_psub, dim3(kRedBlocks), dim3(kBlock), 0, s, L, x, st);
 }
 
-template void launch_dot2<float>(long long, const float *, const double *, double *, cudaStream_t);
-template void launch_dot2<double>(long long, const double *, const double *, double *, cudaStream_t);
-template void launch_update_s<float>(long long, double *, const double *, const SqmrState *, float *, cudaStream_t);
-template void launch_update_s<double>(long long, double *, const double *, const SqmrState *, double *, cudaStream_t);
-template void launch_update_s<bf16>(long long, double *, const double *, const SqmrState *, bf16 *, cudaStream_t);
+template void launch_dot2<float>(long long, const float *, const double *, double *, cudaStream_t, const Bat &);
+template void launch_dot2<double>(long long, const double *, const double *, double *, cudaStream_t, const Bat &);
+template void launch_update_s<float>(long long, double *, const double *, const SqmrState *, float *, cudaStream_t,
+                                     const Bat &);
+template void launch_update_s<double>(long long, double *, const double *, const SqmrState *, double *, cudaStream_t,
+                                      const Bat &);
+template void launch_update_s<bf16>(long long, double *, const double *, const SqmrState *, bf16 *, cudaStream_t,
+                                    const Bat &);
 template void launch_update_rq<float>(long long, const double *, double *, const float *, double *, const double *,
-                                      const SqmrState *, double *, cudaStream_t);
+                                      const SqmrState *, double *, cudaStream_t, const Bat &);
 template void launch_update_rq<double>(long long, const double *, double *, const double *, double *, const double *,
-                                       const SqmrState *, double *, cudaStream_t);
+                                       const SqmrState *, double *, cudaStream_t, const Bat &);
 // x += t (the pure-multigrid update x_{k+1} = x_k + W^+ (b - L~ x_k), t in the V-cycle's precision)
 template <class T>
 __global__ void __launch_bounds__(256) k_add_to(long long n, const T *__restrict__ tv, double *__restrict__ x) {

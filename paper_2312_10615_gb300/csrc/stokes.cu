@@ -321,6 +321,11 @@ struct stokes_s {
     int dwj = 0;               // 1: symmetric distributive weighted Jacobi in place of the symmetric DGS
     long long ncell_active = 0;  // interior cells of the finest level (pressure-mean removal)
     bool neumann = false;        // some unknown face borders an exterior cell: no pressure null space
+    // batched handle (stokes_create_batch): nb problems of this grid; every per-problem buffer of level l
+    // lies in one allocation, problem p's at byte offset p * lev[l].L.bstride (level 0 also holds the SQMR
+    // vectors, the reduction partials and the scalar state); one launch per step covers all problems
+    int nb = 1;
+    Bat bat() const { return Bat{nb, nb > 1 ? lev[0].L.bstride : 0LL}; }
     GridBarrier *bar = nullptr;
     double eta = 1.0, gamma = 1e-3;
     std::vector<LevelBuf> lev;
@@ -578,7 +583,11 @@ template <class T> void cycle_level(stokes_s *h, int l, bool first, cudaStream_t
         return;
     }
     LevelBuf &B = h->lev[l];
-    if (first) prof(STOKES_K_MEMSET, l, s, [&] { cudaMemsetAsync(B.x, 0, sizeof(T) * B.L.n, s); });
+    if (first)
+        prof(STOKES_K_MEMSET, l, s, [&] {
+            if (B.L.nb > 1) cudaMemset2DAsync(B.x, (size_t)B.L.bstride, 0, sizeof(T) * B.L.n, B.L.nb, s);
+            else cudaMemsetAsync(B.x, 0, sizeof(T) * B.L.n, s);
+        });
     smooth_level<T>(h, l, s);
     with_tb<T>(h, l, [&](auto t, auto tf) {
         using TT = decltype(t);
@@ -632,13 +641,14 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s, bool precond
     double *qprev = qbuf(h, parity ^ 1), *qnext = qbuf(h, parity);
     // t <- L q_{j-1}, sigma = q^T t ; alpha = rho / sigma
     int np = reduce_parts(L);
+    const Bat bt = h->bat();
     prof(STOKES_K_APPLY_DOT, 0, s, [&] { launch_apply_dot(L, qprev, h->w, h->partials, s); });
-    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(0, h->partials, np, h->st, h->hout, s); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(0, h->partials, np, h->st, h->hout, s, bt); });
     // s_j = s_{j-1} - alpha t
     with_tb<T>(h, 0, [&](auto, auto tb) {
         using TB = decltype(tb);
         prof(STOKES_K_UPDATE_S, 0, s, [&] {
-            launch_update_s<TB>(n, h->s, h->w, h->st, h->prec == STOKES_PREC_FP64 ? nullptr : (TB *)h->lev[0].b, s);
+            launch_update_s<TB>(n, h->s, h->w, h->st, h->prec == STOKES_PREC_FP64 ? nullptr : (TB *)h->lev[0].b, s, bt);
         });
     });
     // the previous iteration's d and x (pending flag on the device), on the side stream
@@ -647,7 +657,7 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s, bool precond
         cudaEventRecord(h->ev_fork, ms);
         cudaStreamWaitEvent(h->side, h->ev_fork, 0);
         prof(STOKES_K_UPDATE_X, 0, h->side,
-             [&] { launch_update_dx(n, h->x, h->d, qnext, h->st, h->side, h->dx_blocks); });
+             [&] { launch_update_dx(n, h->x, h->d, qnext, h->st, h->side, h->dx_blocks, bt); });
         cudaEventRecord(h->ev_join, h->side);
         forked = true;
     };
@@ -669,12 +679,12 @@ template <class T> void sqmr_iteration(stokes_s *h, cudaStream_t s, bool precond
     if (!forked) lazy(s);
     if (!joined) rejoin(s);
     // |t|^2, rho_j = s_j^T t ; nu, c, tau, beta
-    prof(STOKES_K_DOT2, 0, s, [&] { launch_dot2<T>(n, t, h->s, h->partials, s); });
-    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(1, h->partials, kRedBlocks, h->st, h->hout, s); });
+    prof(STOKES_K_DOT2, 0, s, [&] { launch_dot2<T>(n, t, h->s, h->partials, s, bt); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(1, h->partials, kRedBlocks, h->st, h->hout, s, bt); });
     // recursive true residual r_j, q_j ; |r_j|^2 to the host ; d_j, x_j pending
     prof(STOKES_K_UPDATE_X, 0, s,
-         [&] { launch_update_rq<T>(n, qprev, qnext, t, h->r, h->s, h->st, h->partials, s); });
-    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(2, h->partials, kRedBlocks, h->st, h->hout, s); });
+         [&] { launch_update_rq<T>(n, qprev, qnext, t, h->r, h->s, h->st, h->partials, s, bt); });
+    prof(STOKES_K_SCALARS, 0, s, [&] { launch_scalars(2, h->partials, kRedBlocks, h->st, h->hout, s, bt); });
 }
 // apply the deferred d_j, x_j of the last completed iteration j (reads q_{j-1}) and clear the flag
 void flush_iterate(stokes_s *h, int last_iter, cudaStream_t s) {
@@ -1398,6 +1408,7 @@ int stokes_rhs(stokes_t h, const double *f, const double *g, double *b, void *st
 }
 
 int stokes_apply(stokes_t h, const double *x, double *y, void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || !x || !y) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1416,6 +1427,7 @@ int stokes_apply(stokes_t h, const double *x, double *y, void *stream) {
 }
 
 int mg_precondition(stokes_t h, const double *sv, double *tv, void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || !sv || !tv || (const double *)tv == sv) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1439,6 +1451,7 @@ int mg_precondition(stokes_t h, const double *sv, double *tv, void *stream) {
 }
 
 int stokes_residual_norm(stokes_t h, const double *b, const double *x, double *out, void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || !b || !x || !out) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1455,21 +1468,23 @@ int stokes_residual_norm(stokes_t h, const double *b, const double *x, double *o
 
 namespace {
 // FP64 vectors of Alg. 4 on the finest level, allocated on first use
+int ensure_side(stokes_s *h) {
+    if (h->side) return 0;
+    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
+    h->dx_blocks = 4 * nsm;
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    return 0;
+}
 int ensure_sqmr(stokes_s *h) {
-    if (h->x) return 0;
+    int rc = ensure_side(h);
+    if (rc || h->x) return rc;
     long long n = h->n0();
-    int rc;
     if ((rc = h->alloc(&h->x, sizeof(double) * n))) return rc;
     if ((rc = h->alloc(&h->q, sizeof(double) * n))) return rc;
     if ((rc = h->alloc(&h->q2, sizeof(double) * n))) return rc;
-    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-    {
-        int nsm = 0;
-        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
-        h->dx_blocks = 4 * nsm;
-    }
-    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     if ((rc = h->alloc(&h->d, sizeof(double) * n))) return rc;
     if ((rc = h->alloc(&h->r, sizeof(double) * n))) return rc;
     if ((rc = h->alloc(&h->w, sizeof(double) * n))) return rc;
@@ -1478,13 +1493,79 @@ int ensure_sqmr(stokes_s *h) {
     else if ((rc = h->alloc(&h->s, sizeof(double) * n))) return rc;
     return 0;
 }
+
+// Turn a freshly created handle into a batch of nb problems of its grid: every per-problem buffer of level l
+// (x, b, r, the DGS deltas, the Vanka corrections; on level 0 also the SQMR vectors, reduction partials and
+// scalar state) is re-laid in one allocation of nb slots of P_l bytes, problem p's copy at offset p P_l, and
+// every level's Lev carries (nb, P_l) so that one launch covers all problems.  The schedule is the one that
+// has a batched form: per-colour Vanka launches and in-place DGS (every schedule gives the same bits).
+int make_batched(stokes_s *h, int nb) {
+    const size_t es = h->prec == STOKES_PREC_FP64 ? sizeof(double) : sizeof(float);
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    const int nl = h->nlev();
+    for (int l = 0; l < nl; ++l) {
+        LevelBuf &B = h->lev[l];
+        const Lev &L = B.L;
+        const bool coarsest = l == nl - 1;
+        const size_t esb = l < h->nbf ? sizeof(bf16) : es;
+        std::vector<std::pair<void **, size_t>> bufs;
+        bufs.push_back({&B.x, es * L.n});
+        bufs.push_back({&B.b, (coarsest ? es : esb) * L.n});
+        if (!coarsest) {
+            bufs.push_back({&B.r, esb * L.n});
+            bufs.push_back({&B.delta, es * (size_t)L.nx * L.ny * L.nz});
+            bufs.push_back({&B.corr, es * 8 * 7 * (size_t)B.vcap});
+        }
+        void *partials = nullptr, *st = nullptr, *sv = nullptr;
+        if (l == 0) {
+            const size_t nv = sizeof(double) * L.n;
+            for (double **v : {&h->x, &h->q, &h->q2, &h->d, &h->r, &h->w, &h->bvec})
+                bufs.push_back({(void **)v, nv});
+            if (h->prec != STOKES_PREC_FP64) bufs.push_back({&sv, nv});
+            const int nparts = std::max(reduce_parts(L), kRedBlocks);
+            bufs.push_back({&partials, sizeof(double) * nparts * kRedParts});
+            bufs.push_back({&st, sizeof(SqmrState)});
+        }
+        size_t P = 0;
+        std::vector<size_t> off;
+        for (auto &b : bufs) {
+            off.push_back(P);
+            P += up(b.second);
+        }
+        uint8_t *arena = nullptr;
+        int rc = h->alloc(&arena, P * (size_t)nb);
+        if (rc) return rc;
+        for (size_t k = 0; k < bufs.size(); ++k) *bufs[k].first = arena + off[k];
+        if (l == 0) {
+            h->partials = (double *)partials;
+            h->st = (SqmrState *)st;
+            h->s = h->prec == STOKES_PREC_FP64 ? (double *)B.b : (double *)sv;
+        }
+        B.L.nb = nb;
+        B.L.bstride = (long long)P;
+        B.x2 = nullptr;
+        B.vmode = 0;
+        B.vblocks = 0;
+        B.ufused = 0;
+        B.rtile = Tile();
+        B.ptile = Tile();
+    }
+    h->nb = nb;
+    // two host-visible values per problem
+    if (h->hout) cudaFreeHost(h->hout);
+    h->hout = nullptr;
+    CK(cudaHostAlloc((void **)&h->hout, (2 * (size_t)nb + 2) * sizeof(double), cudaHostAllocMapped));
+    std::memset(h->hout, 0, (2 * (size_t)nb + 2) * sizeof(double));
+    drop_graphs(h);
+    return ensure_side(h);
+}
 }  // namespace
 
 namespace {
 int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info, void *stream,
               bool precond) {
     if (info) std::memset(info, 0, sizeof(*info));
-    if (!h || !rhs || !xv || !(tol > 0.0) || max_iter < 0) return STOKES_ERR_INVALID_ARG;
+    if (!h || !rhs || !xv || !(tol > 0.0) || max_iter < 0 || h->nb > 1) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
     const Lev &L = h->lev[0].L;
@@ -1611,6 +1692,203 @@ finish:
 }
 }  // namespace
 
+namespace {
+// Alg. 4 for every problem of a batched handle.  Each step of an iteration is one launch for all problems
+// (the captured iteration graph); the host reads every problem's recursive residual after each iteration
+// and confirms a converged problem with its own explicit FP64 residual, as the single solve does.  A
+// problem that has converged (or stopped on an error) is frozen on the device: its SQMR kernels return,
+// so its iterate keeps the bits of the single solve while the others go on.
+int sqmr_batched_impl(stokes_t h, const double *const *rhs, double *const *xv, double tol, int max_iter,
+                      sqmr_info_t *infos, void *stream) {
+    if (!h || h->nb < 2 || !rhs || !xv || !(tol > 0.0) || max_iter < 0) return STOKES_ERR_INVALID_ARG;
+    const int nb = h->nb;
+    if (infos) std::memset(infos, 0, sizeof(sqmr_info_t) * nb);
+    for (int p = 0; p < nb; ++p)
+        if (!rhs[p] || !xv[p]) return STOKES_ERR_INVALID_ARG;
+    DeviceGuard dg(h->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    Lev L1 = h->lev[0].L;  // one problem's slice of the finest level
+    L1.nb = 1;
+    L1.bstride = 0;
+    const long long n = L1.n, P = h->lev[0].L.bstride;
+    auto S = [&](auto *ptr, int p) { return bslot(ptr, P, p); };
+    static const int kZero = 0, kOne = 1;
+    auto freeze = [&](int p, const int *v) {
+        return cudaMemcpyAsync(&S(h->st, p)->frozen, v, sizeof(int), cudaMemcpyHostToDevice, s);
+    };
+    auto host = [&](int p, int k) { return h->hout[2 * p + k]; };
+    const int np1 = reduce_parts(L1);
+    std::vector<double> nbv(nb, 0.0), rel(nb, 0.0);
+    std::vector<int> status(nb, STOKES_ERR_NOT_CONVERGED), its(nb, 0), confirmed(nb, 0), active(nb, 1), pending(nb, 0);
+    // inputs
+    for (int p = 0; p < nb; ++p) {
+        CK(freeze(p, &kZero));
+        CK(cudaMemcpyAsync(S(h->bvec, p), rhs[p], sizeof(double) * n,
+                           is_device_ptr(rhs[p]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(S(h->x, p), xv[p], sizeof(double) * n,
+                           is_device_ptr(xv[p]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        launch_mask<double>(L1, S(h->bvec, p), s);
+        launch_mask<double>(L1, S(h->x, p), s);
+        launch_dot2<double>(n, S(h->bvec, p), nullptr, S(h->partials, p), s);
+        launch_scalars(4, S(h->partials, p), kRedBlocks, S(h->st, p), h->hout + 2 * p, s);
+    }
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(s));
+    for (int p = 0; p < nb; ++p) {
+        nbv[p] = std::sqrt(host(p, 0));
+        if (!std::isfinite(nbv[p])) {
+            status[p] = STOKES_ERR_NAN;
+            active[p] = 0;
+        } else if (nbv[p] == 0.0) {
+            CK(cudaMemsetAsync(S(h->x, p), 0, sizeof(double) * n, s));
+            status[p] = STOKES_OK;
+            active[p] = 0;
+        }
+    }
+    // s_0 = b - L x_0 ; r_0 = s_0
+    for (int p = 0; p < nb; ++p) {
+        if (!active[p]) continue;
+        launch_residual_dot(L1, S(h->bvec, p), S(h->x, p), S(h->s, p), S(h->partials, p), s);
+        launch_scalars(4, S(h->partials, p), np1, S(h->st, p), h->hout + 2 * p, s);
+        CK(cudaMemcpyAsync(S(h->r, p), S(h->s, p), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(s));
+    for (int p = 0; p < nb; ++p) {
+        if (!active[p]) continue;
+        rel[p] = std::sqrt(host(p, 0)) / nbv[p];
+        if (rel[p] < tol) {
+            status[p] = STOKES_OK;
+            active[p] = 0;
+        }
+    }
+    auto any_active = [&] {
+        for (int p = 0; p < nb; ++p)
+            if (active[p]) return true;
+        return false;
+    };
+    int rc = 0;
+    if (any_active()) {
+        // t = V-cycle(s_0) for all problems; q_0 = t ; tau_0, rho_0
+        for (int p = 0; p < nb; ++p) {
+            if (h->nbf > 0) launch_convert<double, bf16>(n, S(h->s, p), S((bf16 *)h->lev[0].b, p), s);
+            else if (h->prec != STOKES_PREC_FP64)
+                launch_convert<double, float>(n, S(h->s, p), S((float *)h->lev[0].b, p), s);
+        }
+        if ((rc = run_vcycle(h, s))) return rc;
+        for (int p = 0; p < nb; ++p) {
+            if (!active[p]) continue;
+            if (h->prec == STOKES_PREC_FP64) {
+                launch_dot2<double>(n, S((const double *)h->lev[0].x, p), S(h->s, p), S(h->partials, p), s);
+                launch_init_q<double>(n, S((const double *)h->lev[0].x, p), S(h->q, p), S(h->d, p), s);
+            } else {
+                launch_dot2<float>(n, S((const float *)h->lev[0].x, p), S(h->s, p), S(h->partials, p), s);
+                launch_init_q<float>(n, S((const float *)h->lev[0].x, p), S(h->q, p), S(h->d, p), s);
+            }
+            launch_scalars(3, S(h->partials, p), kRedBlocks, S(h->st, p), h->hout + 2 * p, s);
+        }
+        CKLAUNCH();
+        CK(cudaStreamSynchronize(s));
+        for (int p = 0; p < nb; ++p) {
+            if (!active[p]) continue;
+            const double tt = host(p, 0), st0 = host(p, 1);
+            if (!std::isfinite(tt) || !std::isfinite(st0)) status[p] = STOKES_ERR_NAN;
+            else if (tt == 0.0 || st0 == 0.0) status[p] = STOKES_ERR_BREAKDOWN;
+            else continue;
+            active[p] = 0;
+        }
+    }
+    for (int p = 0; p < nb; ++p)
+        if (!active[p]) CK(freeze(p, &kOne));
+    // the deferred d, x update of problem p's last iteration (as flush_iterate, on p's slice)
+    auto flush = [&](int p) -> int {
+        if (!pending[p]) return 0;
+        launch_update_dx(n, S(h->x, p), S(h->d, p), S(qbuf(h, (pending[p] - 1) & 1), p), S(h->st, p), s);
+        CK(cudaMemsetAsync(&S(h->st, p)->dx_pending, 0, sizeof(int), s));
+        pending[p] = 0;
+        return 0;
+    };
+    for (int it = 1; it <= max_iter && any_active(); ++it) {
+        NvtxRange range("sqmr batched iteration");
+        if ((rc = run_iteration(h, s, true, it & 1))) return rc;
+        for (int p = 0; p < nb; ++p)
+            if (active[p]) {
+                pending[p] = it;
+                its[p] = it;
+            }
+        CK(cudaStreamSynchronize(s));
+        for (int p = 0; p < nb; ++p) {
+            if (!active[p]) continue;
+            const double rr = host(p, 0);
+            const int fl = (int)host(p, 1);
+            if (fl & 2 || !std::isfinite(rr)) {
+                status[p] = STOKES_ERR_NAN;
+            } else if (fl & 1) {
+                status[p] = STOKES_ERR_BREAKDOWN;
+            } else if (std::sqrt(rr) / nbv[p] < tol) {
+                // confirm with the explicit FP64 residual of x_j (its deferred update first)
+                if ((rc = flush(p))) return rc;
+                launch_residual_dot(L1, S(h->bvec, p), S(h->x, p), S(h->w, p), S(h->partials, p), s);
+                launch_scalars(4, S(h->partials, p), np1, S(h->st, p), h->hout + 2 * p, s);
+                CKLAUNCH();
+                CK(cudaStreamSynchronize(s));
+                rel[p] = std::sqrt(host(p, 0)) / nbv[p];
+                if (rel[p] < tol) {
+                    status[p] = STOKES_OK;
+                    confirmed[p] = 1;
+                } else {
+                    CK(cudaMemcpyAsync(S(h->r, p), S(h->w, p), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                    continue;
+                }
+            } else {
+                continue;
+            }
+            if ((rc = flush(p))) return rc;
+            CK(freeze(p, &kOne));
+            active[p] = 0;
+        }
+    }
+    // problems still running used every iteration; then every problem's pressure level and reported residual
+    for (int p = 0; p < nb; ++p) {
+        if ((rc = flush(p))) return rc;
+        if (!h->neumann) {
+            launch_psum(L1, S(h->x, p), S(h->partials, p), s);
+            launch_scalars_aux(5, S(h->partials, p), kRedBlocks, S(h->st, p), h->hout + 2 * p,
+                               (double)h->ncell_active, s);
+            launch_psub(L1, S(h->x, p), S(h->st, p), s);
+        }
+        if (!confirmed[p] && nbv[p] > 0.0 && std::isfinite(nbv[p])) {
+            launch_residual_dot(L1, S(h->bvec, p), S(h->x, p), nullptr, S(h->partials, p), s);
+            launch_scalars(4, S(h->partials, p), np1, S(h->st, p), h->hout + 2 * p, s);
+            CKLAUNCH();
+            CK(cudaStreamSynchronize(s));
+            rel[p] = std::sqrt(host(p, 0)) / nbv[p];
+        }
+        CK(cudaMemcpyAsync(xv[p], S(h->x, p), sizeof(double) * n,
+                           is_device_ptr(xv[p]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        CK(freeze(p, &kZero));
+    }
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(s));
+    int first_bad = STOKES_OK;
+    for (int p = 0; p < nb; ++p) {
+        if (infos) {
+            infos[p].iterations = its[p];
+            infos[p].rel_residual = rel[p];
+            infos[p].status = status[p];
+            infos[p].vcycles = its[p] + (its[p] > 0 ? 1 : 0);
+        }
+        if (status[p] != STOKES_OK && first_bad == STOKES_OK) first_bad = status[p];
+    }
+    return first_bad;
+}
+}  // namespace
+
+extern "C" int sqmr_solve_batched(stokes_t h, const double *const *rhs, double *const *x, double tol, int max_iter,
+                                  sqmr_info_t *infos, void *stream) {
+    return sqmr_batched_impl(h, rhs, x, tol, max_iter, infos, stream);
+}
+
 extern "C" int sqmr_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info,
                           void *stream) {
     return sqmr_impl(h, rhs, xv, tol, max_iter, info, stream, true);
@@ -1626,6 +1904,7 @@ extern "C" int sqmr_solve_unpreconditioned(stokes_t h, const double *rhs, double
 // b - L~ x_k and its norm are FP64; the cycle runs in the handle's precision.
 extern "C" int mg_solve(stokes_t h, const double *rhs, double *xv, double tol, int max_iter, sqmr_info_t *info,
                         void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (info) std::memset(info, 0, sizeof(*info));
     if (!h || !rhs || !xv || !(tol > 0.0) || max_iter < 0) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
@@ -1694,6 +1973,7 @@ extern "C" int mg_solve(stokes_t h, const double *rhs, double *xv, double tol, i
 
 int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launches_all, double *ms_level0,
                              int *launches_level0, void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || nkinds < STOKES_K_COUNT || !ms_all || !launches_all || !ms_level0 || !launches_level0)
         return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
@@ -1725,12 +2005,44 @@ int stokes_profile_iteration(stokes_t h, int nkinds, double *ms_all, int *launch
     return STOKES_OK;
 }
 
+int stokes_create_batch(int nprob, const stokes_grid_t *grid, const stokes_bc_t *bc, double viscosity,
+                        const stokes_opts_t *opts, stokes_t *out) {
+    if (!out) return STOKES_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nprob < 2 || nprob > 4096 || !grid) return STOKES_ERR_INVALID_ARG;
+    stokes_opts_t o;
+    stokes_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.distributive_jacobi || !o.use_graphs) return STOKES_ERR_INVALID_ARG;
+    o.autotune = 0;  // the batched schedule is fixed: per-colour Vanka launches, in-place DGS
+    o.vanka_persistent = 0;
+    // the problems fold into gridDim.z of the 3D launches (at most 4 (nz + 1) z blocks per problem)
+    if ((long long)nprob * 4 * (grid->nz + 1) > 65535) return STOKES_ERR_INVALID_ARG;
+    stokes_t h = nullptr;
+    int rc = stokes_create(grid, bc, viscosity, &o, &h);
+    if (rc) return rc;
+    {
+        DeviceGuard dg(h->dev);
+        rc = make_batched(h, nprob);
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (!rc && e != cudaSuccess) rc = cuda_status(e);
+    }
+    if (rc) {
+        stokes_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return STOKES_OK;
+}
+
+int stokes_batch_size(stokes_t h) { return h ? h->nb : 0; }
+
 int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rhs, double *const *x, double tol,
                      int max_iter, sqmr_info_t *infos, double *done_ms, int nstreams) {
     if (nprob <= 0 || !handles || !rhs || !x) return STOKES_ERR_INVALID_ARG;
     int dev = -1;
     for (int i = 0; i < nprob; ++i) {
-        if (!handles[i] || !rhs[i] || !x[i]) return STOKES_ERR_INVALID_ARG;
+        if (!handles[i] || !rhs[i] || !x[i] || handles[i]->nb > 1) return STOKES_ERR_INVALID_ARG;
         if (dev < 0) dev = handles[i]->dev;
         if (handles[i]->dev != dev) return STOKES_ERR_INVALID_ARG;  // one device per batch
     }
@@ -1790,6 +2102,7 @@ int stokes_level_tiles(stokes_t h, int level, int *tiles, float *ms) {
 }
 
 int stokes_set_level_tiles(stokes_t h, int level, const int *tiles) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || level < 0 || level >= h->nlev() - 1 || !tiles) return STOKES_ERR_INVALID_ARG;
     for (int k = 0; k < 2; ++k) {
         const int bx = tiles[3 * k], by = tiles[3 * k + 1], kz = tiles[3 * k + 2];
@@ -1816,6 +2129,7 @@ int stokes_level_dgs(stokes_t h, int level, int *fused, float *ms) {
 }
 
 int stokes_set_level_dgs(stokes_t h, int level, int fused) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || level < 0 || level >= h->nlev() - 1 || (fused != 0 && fused != 1)) return STOKES_ERR_INVALID_ARG;
     LevelBuf &B = h->lev[level];
     if (fused && (!B.x2 || h->dwj)) return STOKES_ERR_UNSUPPORTED;
@@ -1825,6 +2139,7 @@ int stokes_set_level_dgs(stokes_t h, int level, int fused) {
 }
 
 int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || level < 0 || level >= h->nlev() - 1 || mode < 0 || mode > 4) return STOKES_ERR_INVALID_ARG;
     if (mode == 4 && !h->lev[level].shell) return STOKES_ERR_UNSUPPORTED;
     if (mode == 1 && (h->vanka_max_blocks <= 0 || blocks < 1 || blocks > h->vanka_max_blocks)) return STOKES_ERR_INVALID_ARG;
@@ -1859,6 +2174,7 @@ int stokes_set_level_schedule(stokes_t h, int level, int mode, int blocks) {
 }
 
 int stokes_smooth(stokes_t h, int level, int which, double *x, const double *b, void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || !x || !b || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
     if (!(which >= 0 && which <= 4) && !(which >= 10 && which <= 17)) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
@@ -1930,6 +2246,7 @@ int stokes_test_grid_barrier(stokes_t h, int level, int missing_blocks, int spin
 }
 
 int stokes_restrict(stokes_t h, int level, const double *rf, double *bc, void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || !rf || !bc || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1960,6 +2277,7 @@ int stokes_restrict(stokes_t h, int level, const double *rf, double *bc, void *s
 }
 
 int stokes_prolong_add(stokes_t h, int level, const double *ec, double *xf, void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || !ec || !xf || level < 0 || level >= h->nlev() - 1) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1990,6 +2308,7 @@ int stokes_prolong_add(stokes_t h, int level, const double *ec, double *xf, void
 }
 
 int stokes_coarse_solve(stokes_t h, const double *b, double *x, void *stream) {
+    if (h && h->nb > 1) return STOKES_ERR_INVALID_ARG;  // batched handles: sqmr_solve_batched only
     if (!h || !b || !x) return STOKES_ERR_INVALID_ARG;
     DeviceGuard dg(h->dev);
     cudaStream_t s = (cudaStream_t)stream;

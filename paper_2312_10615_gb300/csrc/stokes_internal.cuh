@@ -65,7 +65,26 @@ struct Lev {
     // them (its term crosses an exterior cell).  nullptr = the plain box, where all of this follows
     // from the indices
     const uint8_t *flags = nullptr;
+    // batched handles: nb problems of this same level, problem p's buffers at byte offset p * bstride from
+    // problem 0's (one stride per level for every per-problem buffer); a launch covers all of them, the
+    // problem index taken from the grid (blockIdx.z = p * zpp + z-block for the 3D launches, blockIdx.y
+    // for the 1D ones)
+    int nb = 1;
+    long long bstride = 0;
 };
+// problem slot of a batched 3D launch (gridDim.z = nb x the z blocks of one problem)
+struct ZSlot {
+    int p, z;
+};
+__device__ __forceinline__ ZSlot zslot(const Lev &L) {
+    if (L.nb == 1) return {0, (int)blockIdx.z};
+    const int zpp = (int)gridDim.z / L.nb, p = (int)blockIdx.z / zpp;
+    return {p, (int)blockIdx.z - p * zpp};
+}
+// problem p's copy of a per-problem buffer
+template <class P> __host__ __device__ __forceinline__ P *bslot(P *ptr, long long bstride, int p) {
+    return ptr ? (P *)((char *)ptr + (long long)p * bstride) : ptr;
+}
 constexpr uint8_t kFlagActive = 1, kFlagV2 = 2, kFlagDirichlet = 4, kFlagDropLo = 64, kFlagDropHi = 128;
 constexpr int kFlagDropShift = 3;
 constexpr uint8_t kFlagDropMask = 0xf8;  // any dropped term
