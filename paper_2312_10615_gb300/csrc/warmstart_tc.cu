@@ -121,6 +121,15 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// asynchronous global -> shared copies of 16 or 8 bytes; an invalid source copies zeros (no bytes read)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // shared-memory matrix descriptor, no swizzle: 16-byte rows, 8-row core matrices of 128 contiguous bytes;
 // lbo = byte distance between core matrices adjacent along K, sbo = along M (or N)
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -173,11 +182,12 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(const __grid_constant__ C
         if (k < CI) v = BWD ? Wt[((26 - t) * 16 + nn) * 16 + k] : Wt[(t * CI + k) * 16 + nn];
         *reinterpret_cast<bf16 *>(sp + t * 512 + (k >> 3) * 256 + nn * 16 + (k & 7) * 2) = __float2bfloat16_rn(v);
     }
-    // the positions past the staged slab (read only by discarded tile rows) are zero
-    for (int p = staged + tid; p < g.half_pos; p += kThreads) {
+    // the positions past the staged slab (read only by discarded tile rows) are zero; so is all of half 1
+    // for a 4-channel input (channels 8..15 do not exist)
+    for (int p = (CI < 16 ? 0 : staged) + tid; p < g.half_pos; p += kThreads)
         *reinterpret_cast<uint4 *>(sp + kWRegion + (size_t)p * 16) = make_uint4(0, 0, 0, 0);
+    for (int p = (CI < 16 ? 0 : staged) + tid; p < g.half_pos; p += kThreads)
         *reinterpret_cast<uint4 *>(sp + kWRegion + g.half_bytes + (size_t)p * 16) = make_uint4(0, 0, 0, 0);
-    }
     fence_async_smem();
     if (tid == 0) {
         mbar_init(bar_tma, 1);
@@ -190,6 +200,9 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(const __grid_constant__ C
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
+    int shift[27];  // staged-position offset of tap t = 9 (dz + 1) + 3 (dy + 1) + (dx + 1)
+#pragma unroll
+    for (int t = 0; t < 27; ++t) shift[t] = (t % 3 - 1) + ((t / 3) % 3 - 1) * g.W + (t / 9 - 1) * plane;
     uint32_t ph_tma = 0, ph_mma = 0;
     int bad = 0;
     for (int slab = blockIdx.x; slab < g.nslab; slab += gridDim.x) {
@@ -207,41 +220,71 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(const __grid_constant__ C
                 break;
             }
         } else {
-            for (int e = tid; e < 2 * staged; e += kThreads) {
-                const int h = e & 1, p = e >> 1;
-                const int zs = p / plane, r = p - zs * plane, ys = r / g.W, xs = r - ys * g.W;
-                const int gz = z0 + zs - 1, gy = y0 + ys - 1, gx = xs - 1;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (h * 8 < CI && gx >= 0 && gx < g.n && gy >= 0 && gy < g.n && gz >= 0 && gz < g.n) {
-                    const long long vox = ((long long)gz * g.n + gy) * g.n + gx;
-                    if constexpr (sizeof(TI) == 4) {
-                        const float4 *q = reinterpret_cast<const float4 *>(X + vox * CI + h * 8);
-                        const float4 a = q[0], b = q[1];
-                        v = make_uint4(pack2(a.x, a.y), pack2(a.z, a.w), pack2(b.x, b.y), pack2(b.z, b.w));
-                    } else if constexpr (CI == 16) {
-                        v = *reinterpret_cast<const uint4 *>(X + vox * CI + h * 8);
-                    } else {  // 4 channels: 8 bytes, the other 4 channels of the half are 0
-                        const uint2 a = *reinterpret_cast<const uint2 *>(X + vox * CI);
-                        v = make_uint4(a.x, a.y, 0, 0);
+            // one warp per staged row (z, y), lanes along x.  BF16 inputs: asynchronous copies, all in flight
+            // at once (a 4-channel input copies 8 bytes into half 0, whose upper 8 bytes and all of half 1
+            // hold the zeros written at the start); FP32 inputs: four voxels' loads batched per lane, rounded
+            // to BF16 on the way
+            for (int r = warp; r < g.Zs * g.Ys; r += kThreads / 32) {
+                const int zs = r / g.Ys, ys = r - zs * g.Ys;
+                const int gz = z0 + zs - 1, gy = y0 + ys - 1;
+                const bool row = gz >= 0 && gz < g.n && gy >= 0 && gy < g.n;
+                const long long rbase = row ? ((long long)gz * g.n + gy) * g.n : 0;
+                const uint32_t d0 = sH0 + (uint32_t)(r * g.W) * 16u;
+                if constexpr (sizeof(TI) == 2) {
+                    for (int xs = lane; xs < g.W; xs += 32) {
+                        const int gx = xs - 1;
+                        const bool in = row && gx >= 0 && gx < g.n;
+                        const TI *src = X + (in ? (rbase + gx) * CI : 0);
+                        if constexpr (CI == 16) {
+                            cp_async16(d0 + (uint32_t)xs * 16u, src, in);
+                            cp_async16(d0 + g.half_bytes + (uint32_t)xs * 16u, src + 8, in);
+                        } else {
+                            cp_async8(d0 + (uint32_t)xs * 16u, src, in);
+                        }
+                    }
+                } else {
+                    for (int x0 = lane; x0 < g.W; x0 += 128) {
+                        float4 q[4][4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int xs = x0 + 32 * u, gx = xs - 1;
+                            const bool in = xs < g.W && row && gx >= 0 && gx < g.n;
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                q[u][c] = in ? reinterpret_cast<const float4 *>(X + (rbase + gx) * 16)[c]
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int xs = x0 + 32 * u;
+                            if (xs >= g.W) break;
+                            uint8_t *dst = sp + kWRegion + (size_t)(r * g.W + xs) * 16;
+                            *reinterpret_cast<uint4 *>(dst) =
+                                make_uint4(pack2(q[u][0].x, q[u][0].y), pack2(q[u][0].z, q[u][0].w),
+                                           pack2(q[u][1].x, q[u][1].y), pack2(q[u][1].z, q[u][1].w));
+                            *reinterpret_cast<uint4 *>(dst + g.half_bytes) =
+                                make_uint4(pack2(q[u][2].x, q[u][2].y), pack2(q[u][2].z, q[u][2].w),
+                                           pack2(q[u][3].x, q[u][3].y), pack2(q[u][3].z, q[u][3].w));
+                        }
                     }
                 }
-                *reinterpret_cast<uint4 *>(sp + kWRegion + (size_t)h * g.half_bytes + (size_t)p * 16) = v;
             }
+            if constexpr (sizeof(TI) == 2) cp_async_wait_all();
             fence_async_smem();
             __syncthreads();
         }
         tc_fence_after();
         if (tid == 0) {
-            const uint32_t lbo = sH1 - sH0;
+            // descriptors of a tile's first tap; tap t adds its position shift to the A start field (16-byte
+            // units, the staged array lies below 256 KB so the field neither under- nor overflows) and t x 512
+            // bytes to B's
+            const uint64_t b0 = sdesc(sW, 256, 128);
             for (int i = 0; i < g.tiles; ++i) {
-                const int s0 = tile_start(g, i);
-#pragma unroll 1
-                for (int t = 0; t < 27; ++t) {
-                    const int shift = (t % 3 - 1) + ((t / 3) % 3 - 1) * g.W + (t / 9 - 1) * plane;
-                    const uint64_t a = sdesc(sH0 + (uint32_t)(s0 + shift) * 16u, lbo, 128);
-                    const uint64_t b = sdesc(sW + (uint32_t)t * 512u, 256, 128);
-                    mma_bf16(tmem + (uint32_t)i * 16u, a, b, kIdesc, t > 0);
-                }
+                const uint64_t a0 = sdesc(sH0 + (uint32_t)tile_start(g, i) * 16u, sH1 - sH0, 128);
+                const uint32_t d = tmem + (uint32_t)i * 16u;
+#pragma unroll
+                for (int t = 0; t < 27; ++t)
+                    mma_bf16(d, a0 + (uint64_t)(int64_t)shift[t], b0 + (uint64_t)(t * 32), kIdesc, t > 0);
             }
             mma_commit(bar_mma);
         }
@@ -382,40 +425,51 @@ __global__ void __launch_bounds__(kThreads) k_wgrad3_mma(int n, const bf16 *__re
     const int ntx = (n + WX - 1) / WX, nty = (n + WY - 1) / WY, ntz = (n + WZ - 1) / WZ;
     const int ntiles = ntx * nty * ntz;
     const uint32_t sx0 = smem_u32(sx), sg0 = smem_u32(sg);
+    if (CI < 16) {  // channels 4..15 of every staged voxel stay 0 (the copies write 8 bytes of half 0)
+        for (int e = tid; e < 2 * WXH; e += kThreads) reinterpret_cast<uint4 *>(sx)[e] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+    }
     // ldmatrix row owned by this lane: A (X, shifted) matrices (vox 0-7, h0) (0-7, h1) (8-15, h0) (8-15, h1);
     // B (G) matrices (vox 0-7, h0) (8-15, h0) (0-7, h1) (8-15, h1)
     const int a_vox = (lane & 7) + ((lane >> 4) << 3), a_h = (lane >> 3) & 1;
     const int b_vox = (lane & 7) + (((lane >> 3) & 1) << 3), b_h = lane >> 4;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int bx = (tile % ntx) * WX, by = ((tile / ntx) % nty) * WY, bz = (tile / (ntx * nty)) * WZ;
-        for (int e = tid; e < 2 * WXH; e += kThreads) {
-            const int h = e & 1, p = e >> 1;
+        // X halo by asynchronous copies (a 4-channel input: 8 bytes into half 0 of pre-zeroed slots)
+        for (int e = tid; e < (CI == 16 ? 2 : 1) * WXH; e += kThreads) {
+            const int h = CI == 16 ? (e & 1) : 0, p = CI == 16 ? (e >> 1) : e;
             const int xs = p % WHX, ys = (p / WHX) % WHY, zs = p / (WHX * WHY);
             const int gx = bx + xs - 1, gy = by + ys - 1, gz = bz + zs - 1;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (h * 8 < CI && gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n) {
-                const long long vox = ((long long)gz * n + gy) * n + gx;
-                if constexpr (CI == 16) {
-                    v = *reinterpret_cast<const uint4 *>(X + vox * 16 + h * 8);
-                } else {
-                    const uint2 a = *reinterpret_cast<const uint2 *>(X + vox * CI);
-                    v = make_uint4(a.x, a.y, 0, 0);
-                }
-            }
-            *reinterpret_cast<uint4 *>(sx + (size_t)h * WXH * 16 + (size_t)p * 16) = v;
+            const bool in = gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n;
+            const bf16 *src = X + (in ? (((long long)gz * n + gy) * n + gx) * CI + h * 8 : 0);
+            const uint32_t dst = sx0 + (uint32_t)(h * WXH + p) * 16u;
+            if constexpr (CI == 16) cp_async16(dst, src, in);
+            else cp_async8(dst, src, in);
         }
-        for (int e = tid; e < 2 * WGV; e += kThreads) {
-            const int h = e & 1, p = e >> 1;
-            const int xs = p % WX, ys = (p / WX) % WY, zs = p / (WX * WY);
-            const int gx = bx + xs, gy = by + ys, gz = bz + zs;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (gx < n && gy < n && gz < n) {
-                const float4 *q = reinterpret_cast<const float4 *>(G + (((long long)gz * n + gy) * n + gx) * 16 + h * 8);
-                const float4 a = q[0], b = q[1];
-                v = make_uint4(pack2(a.x, a.y), pack2(a.z, a.w), pack2(b.x, b.y), pack2(b.z, b.w));
+        // G rounded to BF16, four 16-byte halves per thread loaded before any is stored
+        for (int e0 = tid; e0 < 2 * WGV; e0 += 4 * kThreads) {
+            float4 q[4][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * kThreads, h = e & 1, p = e >> 1;
+                const int xs = p % WX, ys = (p / WX) % WY, zs = p / (WX * WY);
+                const int gx = bx + xs, gy = by + ys, gz = bz + zs;
+                const bool in = e < 2 * WGV && gx < n && gy < n && gz < n;
+                const float4 *src =
+                    reinterpret_cast<const float4 *>(G + (in ? (((long long)gz * n + gy) * n + gx) * 16 + h * 8 : 0));
+                q[u][0] = in ? src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+                q[u][1] = in ? src[1] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            *reinterpret_cast<uint4 *>(sg + (size_t)h * WGV * 16 + (size_t)p * 16) = v;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * kThreads, h = e & 1, p = e >> 1;
+                if (e >= 2 * WGV) break;
+                *reinterpret_cast<uint4 *>(sg + (size_t)h * WGV * 16 + (size_t)p * 16) =
+                    make_uint4(pack2(q[u][0].x, q[u][0].y), pack2(q[u][0].z, q[u][0].w), pack2(q[u][1].x, q[u][1].y),
+                               pack2(q[u][1].z, q[u][1].w));
+            }
         }
+        cp_async_wait_all();
         __syncthreads();
 #pragma unroll 1
         for (int row = 0; row < WY * WZ; ++row) {
