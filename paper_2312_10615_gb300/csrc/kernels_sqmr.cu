@@ -112,7 +112,29 @@ __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__
     b = bslot(b, bs, (int)blockIdx.y);
     partials = bslot(partials, bs, (int)blockIdx.y);
     double v[2] = {0.0, 0.0};
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    // groups of four entries with 16-byte loads (the vectors start 256-byte aligned), then the tail
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = n >> 2;
+    for (long long g = gid; g < n4; g += stride) {
+        double x[4], y[4] = {0.0, 0.0, 0.0, 0.0};
+        if constexpr (sizeof(T) == 4) {
+            const float4 q = reinterpret_cast<const float4 *>(a)[g];
+            x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+        } else {
+            const double2 q0 = reinterpret_cast<const double2 *>(a)[2 * g], q1 = reinterpret_cast<const double2 *>(a)[2 * g + 1];
+            x[0] = q0.x; x[1] = q0.y; x[2] = q1.x; x[3] = q1.y;
+        }
+        if (b) {
+            const double2 r0 = reinterpret_cast<const double2 *>(b)[2 * g], r1 = reinterpret_cast<const double2 *>(b)[2 * g + 1];
+            y[0] = r0.x; y[1] = r0.y; y[2] = r1.x; y[3] = r1.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[0] += x[k] * x[k];
+            v[1] += x[k] * y[k];
+        }
+    }
+    for (long long t = 4 * n4 + gid; t < n; t += stride) {
         double x = (double)a[t];
         v[0] += x * x;
         if (b) v[1] += x * b[t];
