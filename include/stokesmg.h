@@ -155,8 +155,12 @@ int mg_precondition(stokes_t h, const double *s, double *t, void *stream);
 /* Alg. 4: MG-preconditioned SQMR on L.  rhs: packed b; x: x0 on entry, the solution on exit
  * (pressure mean removed).  Stops when the true relative residual ||b - Lx||/||b|| < tol
  * (tracked by the exact recursion r_j = (1 - c_j^2) r_{j-1} + c_j^2 s_j and confirmed by an
- * explicit FP64 b - Lx).  Synchronises the stream once per iteration (convergence flag) and
- * fills *info (may be NULL).  Returns STOKES_ERR_NOT_CONVERGED / BREAKDOWN / NAN with x holding
+ * explicit FP64 b - Lx).  With graphs on (the default) the iterations run as one CUDA graph: a
+ * while node around the iteration, whose stopping test (recursive residual below tol, breakdown,
+ * non-finite value, max_iter) runs on the device, so the stream is synchronised only when that test
+ * stops the loop (to confirm convergence by the explicit residual, then go on if it does not); if the
+ * driver refuses such a graph, or with graphs off, the host synchronises once per iteration.  Fills
+ * *info (may be NULL).  Returns STOKES_ERR_NOT_CONVERGED / BREAKDOWN / NAN with x holding
  * the last iterate. */
 int sqmr_solve(stokes_t h, const double *rhs, double *x, double tol, int max_iter, sqmr_info_t *info, void *stream);
 
@@ -198,6 +202,9 @@ int stokes_create_batch(int nprob, const stokes_grid_t *grid, const stokes_bc_t 
                         const stokes_opts_t *opts, stokes_t *out);
 /* problems in a handle (1 for stokes_create's handles, 0 for NULL) */
 int stokes_batch_size(stokes_t h);
+/* 1 if this handle's SQMR loop has been built and runs as one device-side graph (after its first
+ * sqmr_solve), 0 otherwise */
+int stokes_device_loop(stokes_t h);
 /* Alg. 4 for every problem of a batched handle: rhs[p], x[p] (x0 in, solution out) as sqmr_solve's
  * (host or device).  Per-problem convergence: a problem stops (its state frozen on the device) at the
  * iteration its own explicit FP64 residual confirms tol, as in sqmr_solve; the call returns when every

@@ -27,7 +27,7 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
            "stokes_set_level_schedule", "stokes_level_tiles", "stokes_set_level_tiles", "stokes_level_dgs",
            "stokes_set_level_dgs", "sqmr_solve_unpreconditioned", "stokes_create_batch", "stokes_batch_size",
-           "sqmr_solve_batched",
+           "sqmr_solve_batched", "stokes_device_loop",
            "mg_solve",
            "stokes_measure_fma_peak", "stokes_label_flags", "stokes_test_grid_barrier", "stokes_strerror",
            # learned initial guess (include/warmstart.h)
@@ -104,6 +104,7 @@ def _load():
         "stokes_create_batch": (i, [i, ctypes.POINTER(stokes_grid_t), ctypes.POINTER(stokes_bc_t), d,
                                     ctypes.POINTER(stokes_opts_t), ctypes.POINTER(vp)]),
         "stokes_batch_size": (i, [vp]),
+        "stokes_device_loop": (i, [vp]),
         "sqmr_solve_batched": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, ctypes.POINTER(sqmr_info_t), vp]),
         "stokes_level_schedule": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
         "stokes_set_level_schedule": (i, [vp, i, i, i]),
@@ -398,6 +399,11 @@ def sqmr_solve_batched(h, rhs, xs, tol=1e-8, max_iter=200, stream=None, check=Tr
 
 def stokes_batch_size(h):
     return int(lib().stokes_batch_size(h))
+
+
+def stokes_device_loop(h):
+    """True once the handle's SQMR loop runs as one device-side graph."""
+    return bool(lib().stokes_device_loop(h))
 
 
 def sqmr_solve_unpreconditioned(h, rhs, x, tol=1e-8, max_iter=200, stream=None, check=True):

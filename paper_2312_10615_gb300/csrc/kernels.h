@@ -147,6 +147,16 @@ void launch_update_rq(long long n, const double *qo, double *qn, const T *t, dou
                       const SqmrState *st, double *partials, cudaStream_t s, const Bat &bt = Bat());
 void launch_update_dx(long long n, double *x, double *d, const double *qo, const SqmrState *st, cudaStream_t s,
                       int blocks = 0, const Bat &bt = Bat());
+// the graph-resident SQMR loop (a while node around one or two iterations): after an iteration, continue
+// unless it broke down, produced a non-finite value, brought the recursive residual below tol
+// (sqrt(rr) / nb < tol, the host's own test) or reached max_iter; sets the while handle and, with
+// set_if, the handle of the node that runs the body's second iteration; host_out[2] = iterations done
+struct LoopCtl {
+    double nb, tol;
+    int max_iter, pad;
+};
+void launch_loop_check(const SqmrState *st, const LoopCtl *lc, cudaGraphConditionalHandle hw,
+                       cudaGraphConditionalHandle hi, int set_if, double *host_out, cudaStream_t s);
 // q = t (widening), d = 0
 template <class T> void launch_init_q(long long n, const T *t, double *q, double *d, cudaStream_t s);
 template <class T> void launch_add_to(long long n, const T *t, double *x, cudaStream_t s);

@@ -327,6 +327,21 @@ void launch_update_dx(long long n, double *x, double *d, const double *qo, const
     launch_k(k_update_dx, dim3(blocks > 0 ? blocks : kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, x, d, qo, st, bt.bs);
 }
 
+__global__ void k_loop_check(const SqmrState *__restrict__ st, const LoopCtl *__restrict__ lc,
+                             cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hi, int set_if, double *host_out) {
+    if (threadIdx.x != 0) return;
+    const double rr = st->rr;
+    const bool stop = st->breakdown || st->nonfinite || !isfinite(rr) || sqrt(rr) / lc->nb < lc->tol ||
+                      st->iter >= lc->max_iter;
+    cudaGraphSetConditional(hw, stop ? 0u : 1u);
+    if (set_if) cudaGraphSetConditional(hi, stop ? 0u : 1u);
+    host_out[2] = (double)st->iter;
+}
+void launch_loop_check(const SqmrState *st, const LoopCtl *lc, cudaGraphConditionalHandle hw,
+                       cudaGraphConditionalHandle hi, int set_if, double *host_out, cudaStream_t s) {
+    k_loop_check<<<1, 32, 0, s>>>(st, lc, hw, hi, set_if, host_out);
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_init_q(long long n, const T *__restrict__ tv, double *__restrict__ q,
                                                 double *__restrict__ d) {

@@ -341,6 +341,12 @@ struct stokes_s {
     cudaStream_t cs = nullptr;
     cudaStream_t zs = nullptr;  // zero-fills new buffers (alloc)
     cudaGraphExec_t g_vcycle = nullptr, g_iter[2] = {nullptr, nullptr}, g_iter_id[2] = {nullptr, nullptr};
+    // the SQMR loop as one graph (a while node around the iteration; [preconditioned][parity of its first
+    // iteration]); loop_mode 0 = not built yet, 1 = built, -1 = this driver refused it (the host drives
+    // the loop one iteration graph at a time)
+    cudaGraphExec_t g_loop[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int loop_mode = 0;
+    LoopCtl *lctl = nullptr;  // device copy of the loop's stopping test
     double *q2 = nullptr;  // second SQMR direction buffer: iteration j writes q_j into (j odd ? q2 : q)
     int dx_blocks = 0;     // grid of the deferred iterate update beside the V-cycle (4 blocks per SM)
     // the deferred iterate update (d_j, x_j) runs on a side stream beside the next iteration's V-cycle
@@ -357,6 +363,9 @@ struct stokes_s {
             if (g_iter[p]) cudaGraphExecDestroy(g_iter[p]);
             if (g_iter_id[p]) cudaGraphExecDestroy(g_iter_id[p]);
         }
+        for (auto &row : g_loop)
+            for (cudaGraphExec_t g : row)
+                if (g) cudaGraphExecDestroy(g);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (side) cudaStreamDestroy(side);
@@ -701,6 +710,10 @@ void sqmr_iteration_plain(stokes_s *h, cudaStream_t s, int parity) {
 }
 void drop_graphs(stokes_s *h) {
     if (h->g_vcycle) { cudaGraphExecDestroy(h->g_vcycle); h->g_vcycle = nullptr; }
+    for (auto &row : h->g_loop)
+        for (cudaGraphExec_t &g : row)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (h->loop_mode > 0) h->loop_mode = 0;
     for (int p = 0; p < 2; ++p) {
         if (h->g_iter[p]) { cudaGraphExecDestroy(h->g_iter[p]); h->g_iter[p] = nullptr; }
         if (h->g_iter_id[p]) { cudaGraphExecDestroy(h->g_iter_id[p]); h->g_iter_id[p] = nullptr; }
@@ -747,6 +760,102 @@ int run_iteration(stokes_s *h, cudaStream_t s, bool precond, int parity) {
         CKLAUNCH();
     }
     return 0;
+}
+
+// The SQMR loop in one graph: while (go) { iteration p; test; if (go) { iteration 1 - p; test } }.  The
+// test kernel (launch_loop_check) sets the while node's handle and the if node's, so consecutive
+// iterations run without the host; the graph returns when an iteration stops the loop, and the host then
+// does what it does after every iteration of its own loop (explicit residual, flush, restart).
+int build_loop(stokes_s *h, bool precond, int p0, cudaGraphExec_t *out) {
+    void (*fn)(stokes_s *, cudaStream_t, int) = precond ? sqmr_iteration_any : sqmr_iteration_plain;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    cudaGraphConditionalHandle hw = 0, hi = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hi, g, 0, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp);
+    // capture one iteration and its test into a body graph
+    auto capture_into = [&](cudaGraph_t body, int parity, int set_if) {
+        cudaError_t ce = cudaStreamBeginCaptureToGraph(h->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return ce;
+        fn(h, h->cs, parity);
+        launch_loop_check(h->st, h->lctl, hw, hi, set_if, h->hout, h->cs);
+        cudaGraph_t got = nullptr;
+        ce = cudaStreamEndCapture(h->cs, &got);
+        return ce;
+    };
+    cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess) e = capture_into(body, p0, 1);
+    // the body's last node (the test) carries the if node
+    cudaGraphNode_t sink = nullptr;
+    if (e == cudaSuccess) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(body, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(body, nodes.data(), &nn);
+        int nsink = 0;
+        for (size_t k = 0; e == cudaSuccess && k < nn; ++k) {
+            size_t nd = 0;
+            e = cudaGraphNodeGetDependentNodes(nodes[k], nullptr, nullptr, &nd);
+            if (e == cudaSuccess && nd == 0) {
+                sink = nodes[k];
+                ++nsink;
+            }
+        }
+        if (e == cudaSuccess && nsink != 1) e = cudaErrorInvalidValue;
+    }
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hi;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t in = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&in, body, &sink, nullptr, 1, &ip);
+    if (e == cudaSuccess) e = capture_into(ip.conditional.phGraph_out[0], p0 ^ 1, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(h->cs, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(h->cs, &junk);
+            if (junk) cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    *out = ex;
+    return 0;
+}
+// the loop graphs of this solve kind, built on first use; false: use the host-driven loop
+bool ensure_loop(stokes_s *h, bool precond) {
+    if (!h->use_graphs || h->nb > 1 || h->loop_mode < 0) return false;
+    if (!h->lctl && h->alloc(&h->lctl, sizeof(LoopCtl))) return false;
+    cudaGraphExec_t *g = h->g_loop[precond ? 1 : 0];
+    if (g[0] && g[1]) return true;
+    // first with the kernels' programmatic launch edges, then without them
+    for (int plain = 0; plain < 2; ++plain) {
+        t_plain_launches = plain != 0;
+        int rc = 0;
+        for (int p = 0; p < 2 && !rc; ++p)
+            if (!g[p]) rc = build_loop(h, precond, p, &g[p]);
+        t_plain_launches = false;
+        if (!rc) {
+            h->loop_mode = 1;
+            return true;
+        }
+        for (int p = 0; p < 2; ++p)
+            if (g[p]) { cudaGraphExecDestroy(g[p]); g[p] = nullptr; }
+    }
+    h->loop_mode = -1;
+    return false;
 }
 
 // ---- autotuner: per smoothed level, time the Vanka schedule candidates on the level's own buffers
@@ -1590,6 +1699,7 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
     int it = 0, status = STOKES_OK;
     double rel = 0.0;
     bool rel_confirmed = false;  // rel holds the explicit FP64 residual of the returned x (up to the pressure shift)
+    bool use_loop = false;       // the SQMR loop runs as one graph (g_loop)
     int pending = 0;             // iteration whose deferred d / x update has not been applied yet (0: none)
     if (!std::isfinite(nb)) {
         status = STOKES_ERR_NAN;
@@ -1629,11 +1739,23 @@ int sqmr_impl(stokes_t h, const double *rhs, double *xv, double tol, int max_ite
         if (tt == 0.0 || st0 == 0.0) { status = STOKES_ERR_BREAKDOWN; goto finish; }
     }
     status = STOKES_ERR_NOT_CONVERGED;
+    if (max_iter > 0 && ensure_loop(h, precond)) {
+        const LoopCtl lc = {nb, tol, max_iter, 0};
+        CK(cudaMemcpyAsync(h->lctl, &lc, sizeof(lc), cudaMemcpyHostToDevice, s));
+        use_loop = true;
+    }
     for (it = 1; it <= max_iter; ++it) {
         NvtxRange range("sqmr iteration");
-        if ((rc = run_iteration(h, s, precond, it & 1))) return rc;
+        if (use_loop) {
+            // iterations it, it + 1, ... on the device until one stops the loop
+            CK(cudaGraphLaunch(h->g_loop[precond ? 1 : 0][it & 1], s));
+            if ((rc = sync_read(h, s, &rr, &flags))) return rc;
+            it = (int)h->hout[2];
+        } else {
+            if ((rc = run_iteration(h, s, precond, it & 1))) return rc;
+            if ((rc = sync_read(h, s, &rr, &flags))) return rc;
+        }
         pending = it;
-        if ((rc = sync_read(h, s, &rr, &flags))) return rc;
         int fl = (int)flags;
         if (fl & 2 || !std::isfinite(rr)) { status = STOKES_ERR_NAN; break; }
         if (fl & 1) { status = STOKES_ERR_BREAKDOWN; break; }
@@ -2036,6 +2158,8 @@ int stokes_create_batch(int nprob, const stokes_grid_t *grid, const stokes_bc_t 
 }
 
 int stokes_batch_size(stokes_t h) { return h ? h->nb : 0; }
+
+int stokes_device_loop(stokes_t h) { return h && h->loop_mode > 0 ? 1 : 0; }
 
 int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rhs, double *const *x, double tol,
                      int max_iter, sqmr_info_t *infos, double *done_ms, int nstreams) {

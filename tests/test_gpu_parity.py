@@ -305,6 +305,31 @@ def test_graph_and_eager_paths_agree():
     Se.close()
 
 
+@pytest.mark.parametrize("precision", [smg.PREC_FP32, smg.PREC_FP64])
+def test_device_loop_equals_host_loop(precision):
+    # the SQMR loop as one graph (while node, stopping test on the device) against the host-driven eager
+    # loop: same iteration counts, statuses and bits -- converged, cut off by max_iter, restarted after
+    # an explicit residual that did not confirm, and unpreconditioned
+    n = 32
+    Sg = smg.Stokes(n, precision=precision)
+    Se = smg.Stokes(n, precision=precision, use_graphs=False)
+    b = Sg.rhs(synthetic.bumps(n, seed=8, device=DEV)["f"], None)
+    for tol, maxit in ((1e-8, 200), (1e-30, 7), (1e-13, 60)):
+        xg, xe = torch.zeros_like(b), torch.zeros_like(b)
+        ig = smg.sqmr_solve(Sg.h, b, xg, tol, maxit, check=False)
+        ie = smg.sqmr_solve(Se.h, b, xe, tol, maxit, check=False)
+        assert (ig.status, ig.iterations, ig.rel_residual) == (ie.status, ie.iterations, ie.rel_residual)
+        assert float(torch.max(torch.abs(xg - xe))) == 0.0
+    xg, xe = torch.zeros_like(b), torch.zeros_like(b)
+    ig = smg.sqmr_solve_unpreconditioned(Sg.h, b, xg, 1e-6, 400, check=False)
+    ie = smg.sqmr_solve_unpreconditioned(Se.h, b, xe, 1e-6, 400, check=False)
+    assert (ig.status, ig.iterations) == (ie.status, ie.iterations)
+    assert float(torch.max(torch.abs(xg - xe))) == 0.0
+    assert smg.stokes_device_loop(Sg.h) and not smg.stokes_device_loop(Se.h)
+    Sg.close()
+    Se.close()
+
+
 # ---------------------------------------------------------------------------------------------- a9, a10
 
 def test_sqmr_manufactured_32_parity():
