@@ -202,9 +202,12 @@ int stokes_create_batch(int nprob, const stokes_grid_t *grid, const stokes_bc_t 
                         const stokes_opts_t *opts, stokes_t *out);
 /* problems in a handle (1 for stokes_create's handles, 0 for NULL) */
 int stokes_batch_size(stokes_t h);
-/* 1 if this handle's SQMR loop has been built and runs as one device-side graph (after its first
- * sqmr_solve), 0 otherwise */
+/* how this handle's SQMR loop runs (known after its first sqmr_solve): 0 host-driven (one iteration
+ * graph per launch, a synchronisation per iteration), 1 one device-side graph with the kernels'
+ * programmatic launch edges, 2 one device-side graph without them (the driver refused them there) */
 int stokes_device_loop(stokes_t h);
+/* enable = 1 (default) lets sqmr_solve run its loop as one device-side graph; 0 keeps the host loop */
+int stokes_set_device_loop(stokes_t h, int enable);
 /* Alg. 4 for every problem of a batched handle: rhs[p], x[p] (x0 in, solution out) as sqmr_solve's
  * (host or device).  Per-problem convergence: a problem stops (its state frozen on the device) at the
  * iteration its own explicit FP64 residual confirms tol, as in sqmr_solve; the call returns when every

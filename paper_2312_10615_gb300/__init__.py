@@ -27,7 +27,7 @@ EXPORTS = ["stokes_opts_default", "stokes_create", "stokes_destroy", "stokes_vec
            "stokes_profile_iteration", "stokes_residual_norm_noalloc", "sqmr_solve_batch", "stokes_level_schedule",
            "stokes_set_level_schedule", "stokes_level_tiles", "stokes_set_level_tiles", "stokes_level_dgs",
            "stokes_set_level_dgs", "sqmr_solve_unpreconditioned", "stokes_create_batch", "stokes_batch_size",
-           "sqmr_solve_batched", "stokes_device_loop",
+           "sqmr_solve_batched", "stokes_device_loop", "stokes_set_device_loop",
            "mg_solve",
            "stokes_measure_fma_peak", "stokes_label_flags", "stokes_test_grid_barrier", "stokes_strerror",
            # learned initial guess (include/warmstart.h)
@@ -105,6 +105,7 @@ def _load():
                                     ctypes.POINTER(stokes_opts_t), ctypes.POINTER(vp)]),
         "stokes_batch_size": (i, [vp]),
         "stokes_device_loop": (i, [vp]),
+        "stokes_set_device_loop": (i, [vp, i]),
         "sqmr_solve_batched": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, ctypes.POINTER(sqmr_info_t), vp]),
         "stokes_level_schedule": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]),
         "stokes_set_level_schedule": (i, [vp, i, i, i]),
@@ -402,8 +403,12 @@ def stokes_batch_size(h):
 
 
 def stokes_device_loop(h):
-    """True once the handle's SQMR loop runs as one device-side graph."""
-    return bool(lib().stokes_device_loop(h))
+    """0 host loop, 1 device-side graph with programmatic launch edges, 2 without them."""
+    return int(lib().stokes_device_loop(h))
+
+
+def stokes_set_device_loop(h, enable):
+    _check(lib().stokes_set_device_loop(h, 1 if enable else 0), "stokes_set_device_loop")
 
 
 def sqmr_solve_unpreconditioned(h, rhs, x, tol=1e-8, max_iter=200, stream=None, check=True):

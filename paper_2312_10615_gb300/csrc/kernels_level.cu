@@ -19,6 +19,9 @@ constexpr int KZ = 8;  // z-planes marched by one thread (fewer, longer-lived bl
 const dim3 kBlock3(BX, BY, 1);
 
 inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
+// the batched instantiation of a kernel (problem index from the grid, per-problem offsets) only where a
+// launch covers several problems; a one-problem launch runs the plain kernel
+#define BSEL(nb, ...) ((nb) > 1 ? __VA_ARGS__, true> : __VA_ARGS__, false>)
 
 // geometry of a launch over the packed entries of ncomp components: grid (x tiles, y tiles x ncomp, z)
 struct Geo {
@@ -157,14 +160,14 @@ __device__ __forceinline__ void apply_entry(const Lev &L, const T *__restrict__ 
     y[q] = cvt<TB>(v);
 }
 
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                   TB *__restrict__ y, Coef<T> K) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    b = bslot(b, L.bstride, zs.p);
-    y = bslot(y, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
+    if constexpr (BATCH) y = bslot(y, L.bstride, zs.p);
     const int c = zs.z & 3, k = zs.z >> 2;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
@@ -254,13 +257,13 @@ __device__ __forceinline__ void dgs_face(T *__restrict__ xq, const TB *__restric
     xq[0] = dgs_relax<T>(xq[0], xq[-1], xq[1], xq[-sy], xq[sy], xq[-sz], xq[sz], pc, pm, T(ldv(bq[0])), K);
 }
 
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, const TB *__restrict__ b, int parity,
                                                   Coef<T> K) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    b = bslot(b, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
     const int j = 1 + blockIdx.y * BY + threadIdx.y;
     if (j > L.ny - 2) return;
     const int k = 1 + zs.z;
@@ -293,8 +296,8 @@ __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, cons
 template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, int parity, cudaStream_t s) {
     if (L.nx < 3 || L.ny < 3 || L.nz < 3) return;
     dim3 grid(cdiv((L.nx - 2 + 1) / 2, BX), cdiv(L.ny - 2, BY), (L.nz - 2) * L.nb);
-    if (idx32(L)) launch_k(k_dgs_u<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
-    else launch_k(k_dgs_u<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
+    if (idx32(L)) launch_k(BSEL(L.nb, k_dgs_u<T, TB, int), dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
+    else launch_k(BSEL(L.nb, k_dgs_u<T, TB, long long), dim3(grid), dim3(kBlock3), 0, s, L, x, b, parity, coef<T>(L, L.gamma));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -508,14 +511,14 @@ __device__ __forceinline__ void p_fwd_cell(const Lev &L, T *__restrict__ x, cons
     pp[0] = p + T(6) * K.eh2 * dl;
     dc[0] = dl;
 }
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                    T *__restrict__ delta, int colour, Coef<T> K, T dP) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    b = bslot(b, L.bstride, zs.p);
-    delta = bslot(delta, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
+    if constexpr (BATCH) delta = bslot(delta, L.bstride, zs.p);
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = zs.z;
@@ -528,14 +531,14 @@ __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, con
 // on either side, and their deltas; its y- and z-faces and the deltas of its y/z neighbours belong
 // to colours whose j or k bit differs.  One block holds whole x-rows (thread x = cell along the
 // row), so a __syncthreads orders the two colours.
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(512) k_dgs_p_fwd_pair(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                         T *__restrict__ delta, int colour, Coef<T> K, T dP) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    b = bslot(b, L.bstride, zs.p);
-    delta = bslot(delta, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
+    if constexpr (BATCH) delta = bslot(delta, L.bstride, zs.p);
     int lo[3], cnt[3], lo2[3], cnt2[3];
     v2_colour_range(L, colour, lo, cnt);
     v2_colour_range(L, colour ^ 1, lo2, cnt2);  // same j and k ranges
@@ -547,13 +550,13 @@ __global__ void __launch_bounds__(512) k_dgs_p_fwd_pair(Lev L, T *__restrict__ x
     if (row && ti < cnt2[0]) p_fwd_cell<T, TB, IDX>(L, x, b, delta, colour ^ 1, (IDX)(lo2[0] + 2 * ti), j, k, K, dP);
 }
 
-template <class T>
+template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, const T *__restrict__ delta,
                                                       Coef<T> K) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    delta = bslot(delta, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) delta = bslot(delta, L.bstride, zs.p);
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = zs.z;
     if (i >= L.nx || j >= L.ny || k >= L.nz) return;
     long long t = cell_lin(L, i, j, k);
@@ -606,16 +609,16 @@ __device__ __forceinline__ void prep_entry(const Lev &L, T *__restrict__ x, cons
     }
 }
 
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                            TB *__restrict__ gh, const T *__restrict__ delta,
                                                            Coef<T> K) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    b = bslot(b, L.bstride, zs.p);
-    gh = bslot(gh, L.bstride, zs.p);
-    delta = bslot(delta, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
+    if constexpr (BATCH) gh = bslot(gh, L.bstride, zs.p);
+    if constexpr (BATCH) delta = bslot(delta, L.bstride, zs.p);
     const int c = zs.z & 3, k = zs.z >> 2;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
@@ -792,14 +795,14 @@ __device__ __forceinline__ void apply_entry4(const Lev &L, const T *__restrict__
     }
     st4(y + q, v);
 }
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_apply4(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                    TB *__restrict__ y, Coef<T> K) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    b = bslot(b, L.bstride, zs.p);
-    y = bslot(y, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
+    if constexpr (BATCH) y = bslot(y, L.bstride, zs.p);
     const int c = zs.z & 3, k = zs.z >> 2;
     const int i = 4 * (blockIdx.x * BX + threadIdx.x), j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
@@ -861,16 +864,16 @@ __device__ __forceinline__ void prep_entry4(const Lev &L, T *__restrict__ x, con
         }
     }
 }
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep4(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                             TB *__restrict__ gh, const T *__restrict__ delta,
                                                             Coef<T> K) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    b = bslot(b, L.bstride, zs.p);
-    gh = bslot(gh, L.bstride, zs.p);
-    delta = bslot(delta, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
+    if constexpr (BATCH) gh = bslot(gh, L.bstride, zs.p);
+    if constexpr (BATCH) delta = bslot(delta, L.bstride, zs.p);
     const int c = zs.z & 3, k = zs.z >> 2;
     const int i = 4 * (blockIdx.x * BX + threadIdx.x), j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
@@ -906,13 +909,13 @@ __device__ __forceinline__ void p_bwd_cell(const Lev &L, T *__restrict__ x, cons
     const T s = K.ih * ((ruh - rul) + (rvh - rvl) + (rwh - rwl)) + K.eh2 * (T(6) * rc - rn);
     pp[0] = pc + s / dP;
 }
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const TB *__restrict__ ghs, int colour,
                                                    Coef<T> K, T dP) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    ghs = bslot(ghs, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) ghs = bslot(ghs, L.bstride, zs.p);
     int lo[3], cnt[3];
     v2_colour_range(L, colour, lo, cnt);
     const int ti = blockIdx.x * BX + threadIdx.x, tj = blockIdx.y * BY + threadIdx.y, tk = zs.z;
@@ -921,13 +924,13 @@ __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, con
 }
 // colours c and c ^ 1 of the backward pressure sweep in one launch: only pressures change, and a cell
 // reads the pressures of the other colour of the pair only at its two x-neighbours (same x-row)
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(512) k_dgs_p_bwd_pair(Lev L, T *__restrict__ x, const TB *__restrict__ ghs,
                                                         int colour, Coef<T> K, T dP) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    ghs = bslot(ghs, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) ghs = bslot(ghs, L.bstride, zs.p);
     int lo[3], cnt[3], lo2[3], cnt2[3];
     v2_colour_range(L, colour, lo, cnt);
     v2_colour_range(L, colour ^ 1, lo2, cnt2);
@@ -950,10 +953,10 @@ void launch_dgs_p_fwd(const Lev &L, T *x, const TB *b, T *delta, int colour, cud
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
     dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2] * L.nb);
     if (idx32(L))
-        launch_k(k_dgs_p_fwd<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
+        launch_k(BSEL(L.nb, k_dgs_p_fwd<T, TB, int), dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
     else
-        launch_k(k_dgs_p_fwd<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour,
+        launch_k(BSEL(L.nb, k_dgs_p_fwd<T, TB, long long), dim3(grid), dim3(kBlock3), 0, s, L, x, b, delta, colour,
                  coef<T>(L, L.gamma), dgs_pressure_diag<T>(L));
 }
 // block shape of the colour-pair kernels: whole x-rows, rows stacked to about 256 threads; false if a
@@ -974,10 +977,10 @@ bool launch_dgs_p_fwd_pair(const Lev &L, T *x, const TB *b, T *delta, int colour
     dim3 grid, block;
     if (!pair_block(L, colour, grid, block)) return false;
     if (idx32(L))
-        launch_k(k_dgs_p_fwd_pair<T, TB, int>, grid, block, 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
+        launch_k(BSEL(L.nb, k_dgs_p_fwd_pair<T, TB, int), grid, block, 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
     else
-        launch_k(k_dgs_p_fwd_pair<T, TB, long long>, grid, block, 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
+        launch_k(BSEL(L.nb, k_dgs_p_fwd_pair<T, TB, long long), grid, block, 0, s, L, x, b, delta, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
     return true;
 }
@@ -985,44 +988,44 @@ template <class T, class TB> bool launch_dgs_p_bwd_pair(const Lev &L, T *x, cons
     dim3 grid, block;
     if (!pair_block(L, colour, grid, block)) return false;
     if (idx32(L))
-        launch_k(k_dgs_p_bwd_pair<T, TB, int>, grid, block, 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
+        launch_k(BSEL(L.nb, k_dgs_p_bwd_pair<T, TB, int), grid, block, 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
     else
-        launch_k(k_dgs_p_bwd_pair<T, TB, long long>, grid, block, 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
+        launch_k(BSEL(L.nb, k_dgs_p_bwd_pair<T, TB, long long), grid, block, 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
     return true;
 }
 template <class T> void launch_dgs_p_gather(const Lev &L, T *x, const T *delta, cudaStream_t s) {
     dim3 grid(cdiv(L.nx, BX), cdiv(L.ny, BY), L.nz * L.nb);
-    launch_k(k_dgs_p_gather<T>, dim3(grid), dim3(kBlock3), 0, s, L, x, delta, coef<T>(L, L.gamma));
+    launch_k(BSEL(L.nb, k_dgs_p_gather<T), dim3(grid), dim3(kBlock3), 0, s, L, x, delta, coef<T>(L, L.gamma));
 }
 template <class T, class TB>
 void launch_apply(const Lev &L, const T *x, const TB *b, TB *y, double gam, cudaStream_t s) {
     if (use_x4(L, x, b, y)) {
-        if (idx32(L)) launch_k(k_apply4<T, TB, int>, grid4(L), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
-        else launch_k(k_apply4<T, TB, long long>, grid4(L), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+        if (idx32(L)) launch_k(BSEL(L.nb, k_apply4<T, TB, int), grid4(L), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+        else launch_k(BSEL(L.nb, k_apply4<T, TB, long long), grid4(L), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
         return;
     }
     if (idx32(L))
-        launch_k(k_apply<T, TB, int>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+        launch_k(BSEL(L.nb, k_apply<T, TB, int), dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
     else
-        launch_k(k_apply<T, TB, long long>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
+        launch_k(BSEL(L.nb, k_apply<T, TB, long long), dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, y, coef<T>(L, gam));
 }
 template <class T, class TB>
 void launch_dgs_p_bwd_prep(const Lev &L, T *x, const TB *b, TB *gh, const T *delta, cudaStream_t s) {
     if (use_x4(L, x, b, gh, delta)) {
         if (idx32(L))
-            launch_k(k_dgs_p_bwd_prep4<T, TB, int>, grid4(L), dim3(kBlock3), 0, s, L, x, b, gh, delta, coef<T>(L, L.gamma));
+            launch_k(BSEL(L.nb, k_dgs_p_bwd_prep4<T, TB, int), grid4(L), dim3(kBlock3), 0, s, L, x, b, gh, delta, coef<T>(L, L.gamma));
         else
-            launch_k(k_dgs_p_bwd_prep4<T, TB, long long>, grid4(L), dim3(kBlock3), 0, s, L, x, b, gh, delta,
+            launch_k(BSEL(L.nb, k_dgs_p_bwd_prep4<T, TB, long long), grid4(L), dim3(kBlock3), 0, s, L, x, b, gh, delta,
                      coef<T>(L, L.gamma));
         return;
     }
     if (idx32(L))
-        launch_k(k_dgs_p_bwd_prep<T, TB, int>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta,
+        launch_k(BSEL(L.nb, k_dgs_p_bwd_prep<T, TB, int), dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta,
                  coef<T>(L, L.gamma));
     else
-        launch_k(k_dgs_p_bwd_prep<T, TB, long long>, dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta,
+        launch_k(BSEL(L.nb, k_dgs_p_bwd_prep<T, TB, long long), dim3(entry_grid(L)), dim3(kBlock3), 0, s, L, x, b, gh, delta,
                  coef<T>(L, L.gamma));
 }
 template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB *gh, int colour, cudaStream_t s) {
@@ -1031,10 +1034,10 @@ template <class T, class TB> void launch_dgs_p_bwd(const Lev &L, T *x, const TB 
     if ((long long)cnt[0] * cnt[1] * cnt[2] == 0) return;
     dim3 grid(cdiv(cnt[0], BX), cdiv(cnt[1], BY), cnt[2] * L.nb);
     if (idx32(L))
-        launch_k(k_dgs_p_bwd<T, TB, int>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
+        launch_k(BSEL(L.nb, k_dgs_p_bwd<T, TB, int), dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
     else
-        launch_k(k_dgs_p_bwd<T, TB, long long>, dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
+        launch_k(BSEL(L.nb, k_dgs_p_bwd<T, TB, long long), dim3(grid), dim3(kBlock3), 0, s, L, x, gh, colour, coef<T>(L, L.gamma),
                  dgs_pressure_diag<T>(L));
 }
 
@@ -1175,15 +1178,15 @@ __device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x
     if (act) x[q] += corr[(long long)a * cap + slot];
 }
 
-template <class T, class TB, class IDX>
+template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                        const int *__restrict__ cells, const int *__restrict__ tab,
                                                        int ncell, const T *__restrict__ kinv, T *__restrict__ corr,
                                                        int cap, Coef<T> K, T w) {
     pdl_wait();
-    x = bslot(x, L.bstride, (int)blockIdx.y);
-    b = bslot(b, L.bstride, (int)blockIdx.y);
-    corr = bslot(corr, L.bstride, (int)blockIdx.y);
+    if constexpr (BATCH) x = bslot(x, L.bstride, (int)blockIdx.y);
+    if constexpr (BATCH) b = bslot(b, L.bstride, (int)blockIdx.y);
+    if constexpr (BATCH) corr = bslot(corr, L.bstride, (int)blockIdx.y);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3;
     if (slot >= ncell) return;  // whole 8-lane groups leave together
@@ -1191,12 +1194,12 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
                                    w, tab);
 }
 
-template <class T>
+template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, const int *__restrict__ cells,
                                                      int ncell, const T *__restrict__ corr, int cap) {
     pdl_wait();
-    x = bslot(x, L.bstride, (int)blockIdx.y);
-    corr = bslot(corr, L.bstride, (int)blockIdx.y);
+    if constexpr (BATCH) x = bslot(x, L.bstride, (int)blockIdx.y);
+    if constexpr (BATCH) corr = bslot(corr, L.bstride, (int)blockIdx.y);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3;
     if (slot >= ncell) return;
@@ -1208,16 +1211,16 @@ void launch_vanka_compute(const Lev &L, const T *x, const TB *b, const int *cell
                           const T *kinv, T *corr, int cap, double w, cudaStream_t s) {
     if (ncell <= 0) return;
     if (idx32(L))
-        launch_k(k_vanka_compute<T, TB, int>, dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, b, cells, tab, ncell,
+        launch_k(BSEL(L.nb, k_vanka_compute<T, TB, int), dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, b, cells, tab, ncell,
                  kinv, corr, cap, coef<T>(L, L.gamma), T(w));
     else
-        launch_k(k_vanka_compute<T, TB, long long>, dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, b, cells, tab,
+        launch_k(BSEL(L.nb, k_vanka_compute<T, TB, long long), dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, b, cells, tab,
                  ncell, kinv, corr, cap, coef<T>(L, L.gamma), T(w));
 }
 template <class T>
 void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T *corr, int cap, cudaStream_t s) {
     if (ncell <= 0) return;
-    launch_k(k_vanka_apply<T>, dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, cells, ncell, corr, cap);
+    launch_k(BSEL(L.nb, k_vanka_apply<T), dim3(cdiv(8LL * ncell, 256), L.nb), dim3(256), 0, s, L, x, cells, ncell, corr, cap);
 }
 
 // ---- one launch per colour step: two copies of the level's Vanka state (ping-pong) ----
@@ -1776,13 +1779,13 @@ __device__ __forceinline__ bool thread_entry_tile(const Lev &L, int gy, int kz, 
     return i < ext(L, c, 0) && j < ext(L, c, 1) && k0 < ez;
 }
 
-template <class T, class TF, class TC>
+template <class T, class TF, class TC, bool BATCH>
 __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, int kz, const TF *__restrict__ rf,
                                                   TC *__restrict__ bc) {
     pdl_wait();
-    const ZSlot zs = zslot(C);
-    rf = bslot(rf, F.bstride, zs.p);
-    bc = bslot(bc, C.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(C) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) rf = bslot(rf, F.bstride, zs.p);
+    if constexpr (BATCH) bc = bslot(bc, C.bstride, zs.p);
     int c, I, J, k0, k1;
     if (!thread_entry_tile(C, gy, kz, zs.z, c, I, J, k0, k1)) return;
     for (int Kk = k0; Kk < k1; ++Kk) {
@@ -1862,12 +1865,12 @@ __device__ __forceinline__ void prolong_comp(const Lev &F, const Lev &Cl, const 
     }
 }
 
-template <class T>
+template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, int kz, const T *__restrict__ ec, T *__restrict__ xf) {
     pdl_wait();
-    const ZSlot zs = zslot(Cl);
-    ec = bslot(ec, Cl.bstride, zs.p);
-    xf = bslot(xf, F.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(Cl) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) ec = bslot(ec, Cl.bstride, zs.p);
+    if constexpr (BATCH) xf = bslot(xf, F.bstride, zs.p);
     int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= Cl.nx || J >= Cl.ny) return;
     int k0 = zs.z * kz, k1 = k0 + kz < Cl.nz ? k0 + kz : Cl.nz;
@@ -1894,23 +1897,23 @@ template <class T, class TF, class TC>
 void launch_restrict(const Lev &F, const Lev &C, const TF *rf, TC *bc, cudaStream_t s, Tile t) {
     const int mx = C.nx + 1, my = C.ny + 1, mz = C.nz + 1;
     const int gy = cdiv(my, t.by);
-    launch_k(k_restrict<T, TF, TC>, dim3(cdiv(mx, t.bx), gy * 4, cdiv(mz, t.kz) * C.nb), dim3(t.bx, t.by, 1), 0, s, F, C,
+    launch_k(BSEL(C.nb, k_restrict<T, TF, TC), dim3(cdiv(mx, t.bx), gy * 4, cdiv(mz, t.kz) * C.nb), dim3(t.bx, t.by, 1), 0, s, F, C,
              gy, t.kz, rf, bc);
 }
 template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, T *xf, cudaStream_t s, Tile t) {
     dim3 grid(cdiv(C.nx, t.bx), cdiv(C.ny, t.by), cdiv(C.nz, t.kz) * C.nb);
-    launch_k(k_prolong<T>, dim3(grid), dim3(t.bx, t.by, 1), 0, s, F, C, t.kz, ec, xf);
+    launch_k(BSEL(C.nb, k_prolong<T), dim3(grid), dim3(t.bx, t.by, 1), 0, s, F, C, t.kz, ec, xf);
 }
 
 // ------------------------------------------------------------------------------------------
 // Alg. 1 exact coarsest solve: x[cidx[r]] = sum_k Kinv[r][k] b[cidx[k]] (FP64, one warp per row,
 // deterministic lane-strided sums then a fixed shuffle tree)
-template <class T>
+template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_coarse(const int *__restrict__ cidx, int nc, const double *__restrict__ kinv,
                                                 const T *__restrict__ b, T *__restrict__ x, long long bstride) {
     pdl_wait();
-    b = bslot(b, bstride, (int)blockIdx.y);
-    x = bslot(x, bstride, (int)blockIdx.y);
+    if constexpr (BATCH) b = bslot(b, bstride, (int)blockIdx.y);
+    if constexpr (BATCH) x = bslot(x, bstride, (int)blockIdx.y);
     extern __shared__ double sb[];
     for (int m = threadIdx.x; m < nc; m += blockDim.x) sb[m] = (double)b[cidx[m]];
     __syncthreads();
@@ -1928,7 +1931,7 @@ __global__ void __launch_bounds__(256) k_coarse(const int *__restrict__ cidx, in
 template <class T>
 void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, const T *b, T *x, cudaStream_t s) {
     int rows_per_block = 256 / 32;
-    launch_k(k_coarse<T>, dim3((nc + rows_per_block - 1) / rows_per_block, C.nb), dim3(256), nc * sizeof(double), s, cidx,
+    launch_k(BSEL(C.nb, k_coarse<T), dim3((nc + rows_per_block - 1) / rows_per_block, C.nb), dim3(256), nc * sizeof(double), s, cidx,
              nc, kinv, b, x, C.bstride);
 }
 

@@ -49,15 +49,15 @@ int reduce_parts(const Lev &L) {
     return (int)(g.x * g.y * g.z);
 }
 
-template <bool RESIDUAL>
+template <bool RESIDUAL, bool BATCH>
 __global__ void __launch_bounds__(256) k_apply_red(Lev L, const double *__restrict__ x, const double *__restrict__ b,
                                                    double *__restrict__ w, double *partials, Coef<double> K) {
     pdl_wait();
-    const ZSlot zs = zslot(L);
-    x = bslot(x, L.bstride, zs.p);
-    b = bslot(b, L.bstride, zs.p);
-    w = bslot(w, L.bstride, zs.p);
-    partials = bslot(partials, L.bstride, zs.p);
+    const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
+    if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
+    if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
+    if constexpr (BATCH) w = bslot(w, L.bstride, zs.p);
+    if constexpr (BATCH) partials = bslot(partials, L.bstride, zs.p);
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     double v[1] = {0.0};
     if (i <= L.nx && j <= L.ny) {
@@ -94,23 +94,23 @@ static dim3 red_grid_all(const Lev &L) {
 }
 
 int launch_apply_dot(const Lev &L, const double *q, double *w, double *partials, cudaStream_t s) {
-    launch_k(k_apply_red<false>, red_grid_all(L), dim3(BX, BY, 1), 0, s, L, q, nullptr, w, partials,
+    launch_k(L.nb > 1 ? k_apply_red<false, true> : k_apply_red<false, false>, red_grid_all(L), dim3(BX, BY, 1), 0, s, L, q, nullptr, w, partials,
              coef<double>(L, 0.0));
     return reduce_parts(L);
 }
 int launch_residual_dot(const Lev &L, const double *b, const double *x, double *w, double *partials, cudaStream_t s) {
-    launch_k(k_apply_red<true>, red_grid_all(L), dim3(BX, BY, 1), 0, s, L, x, b, w, partials, coef<double>(L, 0.0));
+    launch_k(L.nb > 1 ? k_apply_red<true, true> : k_apply_red<true, false>, red_grid_all(L), dim3(BX, BY, 1), 0, s, L, x, b, w, partials, coef<double>(L, 0.0));
     return reduce_parts(L);
 }
 
 // a.a and a.b
-template <class T>
+template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__ a, const double *__restrict__ b,
                                               double *partials, long long bs) {
     pdl_wait();
-    a = bslot(a, bs, (int)blockIdx.y);
-    b = bslot(b, bs, (int)blockIdx.y);
-    partials = bslot(partials, bs, (int)blockIdx.y);
+    if constexpr (BATCH) a = bslot(a, bs, (int)blockIdx.y);
+    if constexpr (BATCH) b = bslot(b, bs, (int)blockIdx.y);
+    if constexpr (BATCH) partials = bslot(partials, bs, (int)blockIdx.y);
     double v[2] = {0.0, 0.0};
     // groups of four entries with 16-byte loads (the vectors start 256-byte aligned), then the tail
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
@@ -143,17 +143,20 @@ __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__
 }
 template <class T>
 void launch_dot2(long long n, const T *a, const double *b, double *partials, cudaStream_t s, const Bat &bt) {
-    launch_k(k_dot2<T>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, a, b, partials, bt.bs);
+    launch_k(bt.nb > 1 ? k_dot2<T, true> : k_dot2<T, false>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, a, b, partials, bt.bs);
 }
 
 // scalar recurrences of Alg. 4 (one block; fixed-order sum of the nparts partials)
+template <bool BATCH>
 __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partials, int nparts, SqmrState *st,
                                                  double *host_out, double aux, long long bs) {
     pdl_wait();
-    partials = bslot(partials, bs, (int)blockIdx.x);
-    st = bslot(st, bs, (int)blockIdx.x);
-    host_out += 2 * blockIdx.x;
-    if (st->frozen && stage <= 2) return;
+    if constexpr (BATCH) partials = bslot(partials, bs, (int)blockIdx.x);
+    if constexpr (BATCH) st = bslot(st, bs, (int)blockIdx.x);
+    if constexpr (BATCH) {
+        host_out += 2 * blockIdx.x;
+        if (st->frozen && stage <= 2) return;
+    }
     __shared__ double sh[kRedParts][kBlock];
     double v[kRedParts] = {0.0, 0.0, 0.0};
     for (int t = threadIdx.x; t < nparts; t += blockDim.x)
@@ -231,23 +234,24 @@ __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partia
 
 void launch_scalars(int stage, const double *partials, int nparts, SqmrState *st, double *host_out,
                     cudaStream_t s, const Bat &bt) {
-    launch_k(k_scalars, dim3(bt.nb), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, 0.0, bt.bs);
+    launch_k(bt.nb > 1 ? k_scalars<true> : k_scalars<false>, dim3(bt.nb), dim3(kBlock), 0, s, stage, partials, nparts,
+             st, host_out, 0.0, bt.bs);
 }
 void launch_scalars_aux(int stage, const double *partials, int nparts, SqmrState *st, double *host_out, double aux,
                         cudaStream_t s) {
-    launch_k(k_scalars, dim3(1), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, aux, 0LL);
+    launch_k(k_scalars<false>, dim3(1), dim3(kBlock), 0, s, stage, partials, nparts, st, host_out, aux, 0LL);
 }
 
 // s_j = s_{j-1} - alpha t  (t = L q_{j-1}); optional narrowed copy for the V-cycle
-template <class T>
+template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_update_s(long long n, double *__restrict__ s, const double *__restrict__ w,
                                                   const SqmrState *__restrict__ st, T *__restrict__ bT, long long bs) {
     pdl_wait();
-    s = bslot(s, bs, (int)blockIdx.y);
-    w = bslot(w, bs, (int)blockIdx.y);
-    st = bslot(st, bs, (int)blockIdx.y);
-    bT = bslot(bT, bs, (int)blockIdx.y);
-    if (st->frozen) return;
+    if constexpr (BATCH) s = bslot(s, bs, (int)blockIdx.y);
+    if constexpr (BATCH) w = bslot(w, bs, (int)blockIdx.y);
+    if constexpr (BATCH) st = bslot(st, bs, (int)blockIdx.y);
+    if constexpr (BATCH) bT = bslot(bT, bs, (int)blockIdx.y);
+    if (BATCH && st->frozen) return;
     double alpha = st->alpha;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         double v = s[t] - alpha * w[t];
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(256) k_update_s(long long n, double *__restric
 template <class T>
 void launch_update_s(long long n, double *s, const double *w, const SqmrState *st, T *bT, cudaStream_t stream,
                      const Bat &bt) {
-    launch_k(k_update_s<T>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, stream, n, s, w, st, bT, bt.bs);
+    launch_k(bt.nb > 1 ? k_update_s<T, true> : k_update_s<T, false>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, stream, n, s, w, st, bT, bt.bs);
 }
 
 // d_j = c^2 nu_{j-1}^2 d_{j-1} + c^2 alpha q_{j-1};  x_j = x_{j-1} + d_j;
@@ -270,21 +274,21 @@ void launch_update_s(long long n, double *s, const double *w, const SqmrState *s
 // iterate, d_j = A_j d_{j-1} + B_j q_{j-1}, x_j = x_{j-1} + d_j.  The second is deferred into the next
 // iteration, beside its V-cycle; it runs only while st->dx_pending is set (by the iteration's last
 // scalar step; cleared when the update has been applied outside the loop).  Same arithmetic per entry.
-template <class T>
+template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_update_rq(long long n, const double *__restrict__ qo, double *__restrict__ qn,
                                                    const T *__restrict__ tv, double *__restrict__ r,
                                                    const double *__restrict__ sv, const SqmrState *__restrict__ st,
                                                    double *partials, long long bs) {
     pdl_wait();
     const int p = (int)blockIdx.y;
-    qo = bslot(qo, bs, p);
-    qn = bslot(qn, bs, p);
-    tv = bslot(tv, bs, p);
-    r = bslot(r, bs, p);
-    sv = bslot(sv, bs, p);
-    st = bslot(st, bs, p);
-    partials = bslot(partials, bs, p);
-    if (st->frozen) return;  // the whole block: one problem per blockIdx.y
+    if constexpr (BATCH) qo = bslot(qo, bs, p);
+    if constexpr (BATCH) qn = bslot(qn, bs, p);
+    if constexpr (BATCH) tv = bslot(tv, bs, p);
+    if constexpr (BATCH) r = bslot(r, bs, p);
+    if constexpr (BATCH) sv = bslot(sv, bs, p);
+    if constexpr (BATCH) st = bslot(st, bs, p);
+    if constexpr (BATCH) partials = bslot(partials, bs, p);
+    if (BATCH && st->frozen) return;  // the whole block: one problem per blockIdx.y
     const double c2 = st->c2, beta = st->beta;
     double v[1] = {0.0};
 #pragma unroll 1
@@ -297,16 +301,17 @@ __global__ void __launch_bounds__(256) k_update_rq(long long n, const double *__
     }
     block_store<1>(v, partials, blockIdx.x);
 }
+template <bool BATCH>
 __global__ void __launch_bounds__(256) k_update_dx(long long n, double *__restrict__ x, double *__restrict__ d,
                                                    const double *__restrict__ qo, const SqmrState *__restrict__ st,
                                                    long long bs) {
     pdl_wait();
     const int p = (int)blockIdx.y;
-    x = bslot(x, bs, p);
-    d = bslot(d, bs, p);
-    qo = bslot(qo, bs, p);
-    st = bslot(st, bs, p);
-    if (!st->dx_pending || st->frozen) return;
+    if constexpr (BATCH) x = bslot(x, bs, p);
+    if constexpr (BATCH) d = bslot(d, bs, p);
+    if constexpr (BATCH) qo = bslot(qo, bs, p);
+    if constexpr (BATCH) st = bslot(st, bs, p);
+    if (!st->dx_pending || (BATCH && st->frozen)) return;
     const double A = st->coefA, B = st->coefB;
 #pragma unroll 1
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -318,13 +323,13 @@ __global__ void __launch_bounds__(256) k_update_dx(long long n, double *__restri
 template <class T>
 void launch_update_rq(long long n, const double *qo, double *qn, const T *t, double *r, const double *sv,
                       const SqmrState *st, double *partials, cudaStream_t s, const Bat &bt) {
-    launch_k(k_update_rq<T>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, qo, qn, t, r, sv, st, partials, bt.bs);
+    launch_k(bt.nb > 1 ? k_update_rq<T, true> : k_update_rq<T, false>, dim3(kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, qo, qn, t, r, sv, st, partials, bt.bs);
 }
 // blocks: the full reduction grid when it runs alone; a few per SM when it runs beside the V-cycle, so
 // that the V-cycle's kernels keep most of every SM's thread slots
 void launch_update_dx(long long n, double *x, double *d, const double *qo, const SqmrState *st, cudaStream_t s,
                       int blocks, const Bat &bt) {
-    launch_k(k_update_dx, dim3(blocks > 0 ? blocks : kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, x, d, qo, st, bt.bs);
+    launch_k(bt.nb > 1 ? k_update_dx<true> : k_update_dx<false>, dim3(blocks > 0 ? blocks : kRedBlocks, bt.nb), dim3(kBlock), 0, s, n, x, d, qo, st, bt.bs);
 }
 
 __global__ void k_loop_check(const SqmrState *__restrict__ st, const LoopCtl *__restrict__ lc,

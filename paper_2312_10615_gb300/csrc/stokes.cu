@@ -342,10 +342,12 @@ struct stokes_s {
     cudaStream_t zs = nullptr;  // zero-fills new buffers (alloc)
     cudaGraphExec_t g_vcycle = nullptr, g_iter[2] = {nullptr, nullptr}, g_iter_id[2] = {nullptr, nullptr};
     // the SQMR loop as one graph (a while node around the iteration; [preconditioned][parity of its first
-    // iteration]); loop_mode 0 = not built yet, 1 = built, -1 = this driver refused it (the host drives
-    // the loop one iteration graph at a time)
+    // iteration]); loop_mode 0 = not built yet, 1 = built with the kernels' programmatic launch edges,
+    // 2 = built without them, -1 = this driver refused it (the host drives the loop one iteration graph at
+    // a time); device_loop = 0 keeps the host loop
     cudaGraphExec_t g_loop[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int loop_mode = 0;
+    int device_loop = 1;
     LoopCtl *lctl = nullptr;  // device copy of the loop's stopping test
     double *q2 = nullptr;  // second SQMR direction buffer: iteration j writes q_j into (j odd ? q2 : q)
     int dx_blocks = 0;     // grid of the deferred iterate update beside the V-cycle (4 blocks per SM)
@@ -836,7 +838,7 @@ int build_loop(stokes_s *h, bool precond, int p0, cudaGraphExec_t *out) {
 }
 // the loop graphs of this solve kind, built on first use; false: use the host-driven loop
 bool ensure_loop(stokes_s *h, bool precond) {
-    if (!h->use_graphs || h->nb > 1 || h->loop_mode < 0) return false;
+    if (!h->use_graphs || h->nb > 1 || h->loop_mode < 0 || !h->device_loop) return false;
     if (!h->lctl && h->alloc(&h->lctl, sizeof(LoopCtl))) return false;
     cudaGraphExec_t *g = h->g_loop[precond ? 1 : 0];
     if (g[0] && g[1]) return true;
@@ -848,7 +850,7 @@ bool ensure_loop(stokes_s *h, bool precond) {
             if (!g[p]) rc = build_loop(h, precond, p, &g[p]);
         t_plain_launches = false;
         if (!rc) {
-            h->loop_mode = 1;
+            h->loop_mode = 1 + plain;
             return true;
         }
         for (int p = 0; p < 2; ++p)
@@ -2159,7 +2161,13 @@ int stokes_create_batch(int nprob, const stokes_grid_t *grid, const stokes_bc_t 
 
 int stokes_batch_size(stokes_t h) { return h ? h->nb : 0; }
 
-int stokes_device_loop(stokes_t h) { return h && h->loop_mode > 0 ? 1 : 0; }
+int stokes_device_loop(stokes_t h) { return h && h->loop_mode > 0 && h->device_loop ? h->loop_mode : 0; }
+
+int stokes_set_device_loop(stokes_t h, int enable) {
+    if (!h || (enable != 0 && enable != 1)) return STOKES_ERR_INVALID_ARG;
+    h->device_loop = enable;
+    return STOKES_OK;
+}
 
 int sqmr_solve_batch(int nprob, const stokes_t *handles, const double *const *rhs, double *const *x, double tol,
                      int max_iter, sqmr_info_t *infos, double *done_ms, int nstreams) {
