@@ -163,7 +163,7 @@ __device__ __forceinline__ void apply_entry(const Lev &L, const T *__restrict__ 
 template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_apply(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                   TB *__restrict__ y, Coef<T> K) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
@@ -191,7 +191,7 @@ __device__ __forceinline__ long long gidx(const Lev &L, int c, int i, int j, int
 
 __global__ void __launch_bounds__(256) k_rhs(Lev L, int gy, const double *__restrict__ f, const double *__restrict__ g,
                                              double *__restrict__ b, Coef<double> K) {
-    pdl_wait();
+    pdl_enter();
     int c, i, j, k0, k1;
     if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
     for (int k = k0; k < k1; ++k) {
@@ -260,7 +260,7 @@ __device__ __forceinline__ void dgs_face(T *__restrict__ xq, const TB *__restric
 template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_dgs_u(Lev L, T *__restrict__ x, const TB *__restrict__ b, int parity,
                                                   Coef<T> K) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(FX * FY, 3) k_dgs_u_fused(Lev L, const T *__re
                                                             const TB *__restrict__ b, int pa, Coef<T> K) {
     extern __shared__ __align__(16) unsigned char fsm[];
     DgsFusedSmem<T> &S = *reinterpret_cast<DgsFusedSmem<T> *>(fsm);
-    pdl_wait();
+    pdl_enter();
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY, k0 = blockIdx.z * FZ;
     const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
@@ -514,7 +514,7 @@ __device__ __forceinline__ void p_fwd_cell(const Lev &L, T *__restrict__ x, cons
 template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                    T *__restrict__ delta, int colour, Coef<T> K, T dP) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(256) k_dgs_p_fwd(Lev L, T *__restrict__ x, con
 template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(512) k_dgs_p_fwd_pair(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                         T *__restrict__ delta, int colour, Coef<T> K, T dP) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(512) k_dgs_p_fwd_pair(Lev L, T *__restrict__ x
 template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_dgs_p_gather(Lev L, T *__restrict__ x, const T *__restrict__ delta,
                                                       Coef<T> K) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) delta = bslot(delta, L.bstride, zs.p);
@@ -613,7 +613,7 @@ template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                            TB *__restrict__ gh, const T *__restrict__ delta,
                                                            Coef<T> K) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
@@ -798,7 +798,7 @@ __device__ __forceinline__ void apply_entry4(const Lev &L, const T *__restrict__
 template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_apply4(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                    TB *__restrict__ y, Coef<T> K) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
@@ -868,7 +868,7 @@ template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256, 8) k_dgs_p_bwd_prep4(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                             TB *__restrict__ gh, const T *__restrict__ delta,
                                                             Coef<T> K) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
@@ -912,7 +912,7 @@ __device__ __forceinline__ void p_bwd_cell(const Lev &L, T *__restrict__ x, cons
 template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, const TB *__restrict__ ghs, int colour,
                                                    Coef<T> K, T dP) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) ghs = bslot(ghs, L.bstride, zs.p);
@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(256) k_dgs_p_bwd(Lev L, T *__restrict__ x, con
 template <class T, class TB, class IDX, bool BATCH>
 __global__ void __launch_bounds__(512) k_dgs_p_bwd_pair(Lev L, T *__restrict__ x, const TB *__restrict__ ghs,
                                                         int colour, Coef<T> K, T dP) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) ghs = bslot(ghs, L.bstride, zs.p);
@@ -1129,53 +1129,75 @@ __device__ __forceinline__ T vanka_residual_idx(const Lev &L, const T *__restric
     return T(ldv(b[base + o])) - (K.eh2 * s + K.ih * (pc[0] - pc[-ps]));
 }
 
+// the part of a Vanka lane that reads only the level's static data (cell list, label flags, inverse
+// table): the cell, its 6-bit face configuration and where the lane's row of the local inverse lies.
+// Nothing here is written during a solve, so kernels read it before waiting for the previous kernel.
+template <class T> struct VankaLane {
+    int i, j, k, cfg;
+    const T *Ki;
+};
+template <class T>
+__device__ __forceinline__ void vanka_lane_setup(const Lev &L, int cellw, int a, const T *__restrict__ kinv,
+                                                 const int *__restrict__ tab, int slot, VankaLane<T> &v) {
+    unpack_cell(cellw, v.i, v.j, v.k);
+    const int i = v.i, j = v.j, k = v.k;
+    // which of the cell's six faces are unknowns (6-bit configuration of the pre-factorised inverses);
+    // on the box a face of a cell is one unless it lies on a wall
+    v.cfg = L.flags ? ((int)unknown(L, 0, i, j, k) | ((int)unknown(L, 0, i + 1, j, k) << 1) |
+                       ((int)unknown(L, 1, i, j, k) << 2) | ((int)unknown(L, 1, i, j + 1, k) << 3) |
+                       ((int)unknown(L, 2, i, j, k) << 4) | ((int)unknown(L, 2, i, j, k + 1) << 5))
+                    : ((int)(i > 0) | ((int)(i < L.nx - 1) << 1) | ((int)(j > 0) << 2) | ((int)(j < L.ny - 1) << 3) |
+                       ((int)(k > 0) << 4) | ((int)(k < L.nz - 1) << 5));
+    // label domains with exterior cells: the cell's own entry of the level's inverse table (its faces'
+    // dropped terms change the local matrix); otherwise the 6-bit configuration indexes it
+    const int id = tab ? tab[slot] : v.cfg;
+    v.Ki = kinv + id * 49 + (a < 7 ? a : 6) * 7;
+}
+// the rest of the lane: its residual from the current state, row a of K^{-1} r, the stored correction
+template <class T, class TB, class IDX>
+__device__ __forceinline__ void vanka_lane_finish(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
+                                                  const VankaLane<T> &v, int a, unsigned gmask, T *__restrict__ corr,
+                                                  int cap, int slot, const Coef<T> &K, T w) {
+    T r = T(0);
+    if (a == 6 || (a < 6 && ((v.cfg >> a) & 1))) r = vanka_residual_idx<T, TB, IDX>(L, x, b, a, v.i, v.j, v.k, K);
+    T s = T(0);
+#pragma unroll
+    for (int bb = 0; bb < 7; ++bb) s += v.Ki[bb] * __shfl_sync(gmask, r, bb, 8);
+    if (a < 7) corr[(long long)a * cap + slot] = w * s;  // w = 1 (multiplicative) is exact
+}
 template <class T, class TB, class IDX = long long>
 __device__ __forceinline__ void vanka_compute_lane(const Lev &L, const T *__restrict__ x, const TB *__restrict__ b,
                                                    int cellw, int a, unsigned gmask, const T *__restrict__ kinv,
                                                    T *__restrict__ corr, int cap, int slot, const Coef<T> &K,
                                                    T w = T(1), const int *__restrict__ tab = nullptr) {
-    int i, j, k;
-    unpack_cell(cellw, i, j, k);
-    // which of the cell's six faces are unknowns (6-bit configuration of the pre-factorised inverses);
-    // on the box a face of a cell is one unless it lies on a wall
-    const int cfg = L.flags ? ((int)unknown(L, 0, i, j, k) | ((int)unknown(L, 0, i + 1, j, k) << 1) |
-                               ((int)unknown(L, 1, i, j, k) << 2) | ((int)unknown(L, 1, i, j + 1, k) << 3) |
-                               ((int)unknown(L, 2, i, j, k) << 4) | ((int)unknown(L, 2, i, j, k + 1) << 5))
-                            : ((int)(i > 0) | ((int)(i < L.nx - 1) << 1) | ((int)(j > 0) << 2) |
-                               ((int)(j < L.ny - 1) << 3) | ((int)(k > 0) << 4) | ((int)(k < L.nz - 1) << 5));
-    T r = T(0);
-    if (a == 6 || (a < 6 && ((cfg >> a) & 1))) r = vanka_residual_idx<T, TB, IDX>(L, x, b, a, i, j, k, K);
-    // label domains with exterior cells: the cell's own entry of the level's inverse table (its faces'
-    // dropped terms change the local matrix); otherwise the 6-bit configuration indexes it
-    const int id = tab ? tab[slot] : cfg;
-    const T *Ki = kinv + id * 49 + (a < 7 ? a : 6) * 7;
-    T s = T(0);
-#pragma unroll
-    for (int bb = 0; bb < 7; ++bb) s += Ki[bb] * __shfl_sync(gmask, r, bb, 8);
-    if (a < 7) corr[(long long)a * cap + slot] = w * s;  // w = 1 (multiplicative) is exact
+    VankaLane<T> v;
+    vanka_lane_setup<T>(L, cellw, a, kinv, tab, slot, v);
+    vanka_lane_finish<T, TB, IDX>(L, x, b, v, a, gmask, corr, cap, slot, K, w);
 }
 
-template <class T>
-__device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x, int cellw, int a,
-                                                 const T *__restrict__ corr, int cap, int slot) {
-    if (a == 7) return;
+// the entry a Vanka lane updates (static: cell list and label flags); false for lane 7 and for faces that
+// are not unknowns
+__device__ __forceinline__ bool vanka_apply_target(const Lev &L, int cellw, int a, long long &q) {
+    if (a == 7) return false;
     int i, j, k;
     unpack_cell(cellw, i, j, k);
     const long long nx = L.nx, ny = L.ny;
-    long long q;
-    bool act;
     if (a == 6) {
         q = L.off[3] + (i + nx * (j + ny * k));
-        act = true;
-    } else {
-        const int d = a >> 1, side = a & 1;
-        const int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
-        const long long sy = nx + (d == 0), sz = sy * (ny + (d == 1));
-        q = (d == 0 ? L.off[0] : (d == 1 ? L.off[1] : L.off[2])) + fi + sy * fj + sz * fk;
-        const int nrm = d == 0 ? fi : (d == 1 ? fj : fk), nn = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
-        act = nrm >= 1 && nrm <= nn - 1 && (!L.flags || (L.flags[q] & kFlagActive));
+        return true;
     }
-    if (act) x[q] += corr[(long long)a * cap + slot];
+    const int d = a >> 1, side = a & 1;
+    const int fi = i + (d == 0 ? side : 0), fj = j + (d == 1 ? side : 0), fk = k + (d == 2 ? side : 0);
+    const long long sy = nx + (d == 0), sz = sy * (ny + (d == 1));
+    q = (d == 0 ? L.off[0] : (d == 1 ? L.off[1] : L.off[2])) + fi + sy * fj + sz * fk;
+    const int nrm = d == 0 ? fi : (d == 1 ? fj : fk), nn = d == 0 ? L.nx : (d == 1 ? L.ny : L.nz);
+    return nrm >= 1 && nrm <= nn - 1 && (!L.flags || (L.flags[q] & kFlagActive));
+}
+template <class T>
+__device__ __forceinline__ void vanka_apply_lane(const Lev &L, T *__restrict__ x, int cellw, int a,
+                                                 const T *__restrict__ corr, int cap, int slot) {
+    long long q;
+    if (vanka_apply_target(L, cellw, a, q)) x[q] += corr[(long long)a * cap + slot];
 }
 
 template <class T, class TB, class IDX, bool BATCH>
@@ -1183,27 +1205,30 @@ __global__ void __launch_bounds__(256) k_vanka_compute(Lev L, const T *__restric
                                                        const int *__restrict__ cells, const int *__restrict__ tab,
                                                        int ncell, const T *__restrict__ kinv, T *__restrict__ corr,
                                                        int cap, Coef<T> K, T w) {
-    pdl_wait();
     if constexpr (BATCH) x = bslot(x, L.bstride, (int)blockIdx.y);
     if constexpr (BATCH) b = bslot(b, L.bstride, (int)blockIdx.y);
     if constexpr (BATCH) corr = bslot(corr, L.bstride, (int)blockIdx.y);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int slot = t >> 3;
+    const int slot = t >> 3, a = t & 7;
     if (slot >= ncell) return;  // whole 8-lane groups leave together
-    vanka_compute_lane<T, TB, IDX>(L, x, b, cells[slot], t & 7, 0xffu << (threadIdx.x & 24), kinv, corr, cap, slot, K,
-                                   w, tab);
+    // the static part (cell, configuration, inverse table entry) overlaps the previous kernel's tail
+    VankaLane<T> v;
+    vanka_lane_setup<T>(L, cells[slot], a, kinv, tab, slot, v);
+    pdl_enter();
+    vanka_lane_finish<T, TB, IDX>(L, x, b, v, a, 0xffu << (threadIdx.x & 24), corr, cap, slot, K, w);
 }
 
 template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_vanka_apply(Lev L, T *__restrict__ x, const int *__restrict__ cells,
                                                      int ncell, const T *__restrict__ corr, int cap) {
-    pdl_wait();
     if constexpr (BATCH) x = bslot(x, L.bstride, (int)blockIdx.y);
     if constexpr (BATCH) corr = bslot(corr, L.bstride, (int)blockIdx.y);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3;
-    if (slot >= ncell) return;
-    vanka_apply_lane(L, x, cells[slot], t & 7, corr, cap, slot);
+    long long q;
+    if (slot >= ncell || !vanka_apply_target(L, cells[slot], t & 7, q)) return;  // static: before the wait
+    pdl_enter();
+    x[q] += corr[(long long)(t & 7) * cap + slot];
 }
 
 template <class T, class TB>
@@ -1274,31 +1299,25 @@ __global__ void __launch_bounds__(256) k_vanka_step(Lev L, const T *__restrict__
                                                     const int *__restrict__ tab, int ncell,
                                                     const int *__restrict__ pcells, int npcell, int colour,
                                                     const T *__restrict__ kinv, Coef<T> K) {
-    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3, a = t & 7;
     if (slot < ncell) {
-        // the patch correction, as vanka_compute_lane, written as R + correction into W
+        // the patch correction, as vanka_compute_lane, written as R + correction into W; the static part
+        // (cell, configuration, inverse table entry, target entry) before the wait for the previous kernel
         const int cellw = cells[slot];
-        int i, j, k;
-        unpack_cell(cellw, i, j, k);
-        // which faces are unknowns: on the box a face of a cell is one unless it lies on a wall
-        const int cfg = L.flags ? ((int)unknown(L, 0, i, j, k) | ((int)unknown(L, 0, i + 1, j, k) << 1) |
-                                   ((int)unknown(L, 1, i, j, k) << 2) | ((int)unknown(L, 1, i, j + 1, k) << 3) |
-                                   ((int)unknown(L, 2, i, j, k) << 4) | ((int)unknown(L, 2, i, j, k + 1) << 5))
-                                : ((int)(i > 0) | ((int)(i < L.nx - 1) << 1) | ((int)(j > 0) << 2) |
-                                   ((int)(j < L.ny - 1) << 3) | ((int)(k > 0) << 4) | ((int)(k < L.nz - 1) << 5));
+        VankaLane<T> v;
+        vanka_lane_setup<T>(L, cellw, a, kinv, tab, slot, v);
+        long long q;
+        int d;
+        const bool wr = a < 7 && vanka_dof<T>(L, cellw, a, q, d);
+        pdl_enter();
         T r = T(0);
-        if (a == 6 || (a < 6 && ((cfg >> a) & 1))) r = vanka_residual_idx<T, TB, IDX>(L, R, b, a, i, j, k, K);
-        const int id = tab ? tab[slot] : cfg;
-        const T *Ki = kinv + id * 49 + (a < 7 ? a : 6) * 7;
+        if (a == 6 || (a < 6 && ((v.cfg >> a) & 1))) r = vanka_residual_idx<T, TB, IDX>(L, R, b, a, v.i, v.j, v.k, K);
         const unsigned gmask = 0xffu << (threadIdx.x & 24);
         T sacc = T(0);
 #pragma unroll
-        for (int bb = 0; bb < 7; ++bb) sacc += Ki[bb] * __shfl_sync(gmask, r, bb, 8);
-        long long q;
-        int d;
-        if (a < 7 && vanka_dof<T>(L, cellw, a, q, d)) W[q] = R[q] + T(1) * sacc;
+        for (int bb = 0; bb < 7; ++bb) sacc += v.Ki[bb] * __shfl_sync(gmask, r, bb, 8);
+        if (wr) W[q] = R[q] + T(1) * sacc;
         return;
     }
     const int ps = slot - ncell;
@@ -1309,6 +1328,7 @@ __global__ void __launch_bounds__(256) k_vanka_step(Lev L, const T *__restrict__
     int d;
     if (!vanka_dof<T>(L, cellw, a, q, d)) return;
     if (d >= 0 && across_is_v1_of_colour(L, cellw, a, colour)) return;
+    pdl_enter();
     W[q] = R[q];
 }
 
@@ -1316,10 +1336,10 @@ __global__ void __launch_bounds__(256) k_vanka_step(Lev L, const T *__restrict__
 template <class T>
 __global__ void __launch_bounds__(256) k_vanka_shell_copy(const T *__restrict__ x, T *__restrict__ x2,
                                                           const int *__restrict__ list, int n) {
-    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) {
-        const int q = list[t];
+        const int q = list[t];  // static list: read before the wait
+        pdl_enter();
         x2[q] = x[q];
     }
 }
@@ -1387,7 +1407,7 @@ __global__ void __launch_bounds__(256) k_vanka_sweep(Lev L, T *__restrict__ x, c
                                                      VankaLists lists, const T *__restrict__ kinv,
                                                      T *__restrict__ corr, int cap, Coef<T> K, int sweeps,
                                                      GridBarrier *bar, unsigned expect, unsigned spin_limit) {
-    pdl_wait();
+    pdl_enter();
     // blocks the barrier waits for: the grid, or more in the bounded-wait self-test (never completes)
     const unsigned nb = expect ? expect : gridDim.x;
     const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 8: lanes keep their group
@@ -1469,7 +1489,7 @@ __global__ void __launch_bounds__(1024) k_vanka_smem(Lev L, T *__restrict__ x, c
     T *cs = reinterpret_cast<T *>(vsm + lay.co);
     T *ks = reinterpret_cast<T *>(vsm + lay.ko);
     int *cl = reinterpret_cast<int *>(vsm + lay.lo);
-    pdl_wait();
+    pdl_enter();
     const int n = (int)L.n;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         xs[e] = x[e];
@@ -1540,7 +1560,7 @@ template <class T, class TB>
 __global__ void __launch_bounds__(1024) k_vanka_cluster(Lev L, T *__restrict__ x, const TB *__restrict__ b,
                                                         VankaLists lists, const T *__restrict__ kinv,
                                                         T *__restrict__ corr, int cap, Coef<T> K, int sweeps) {
-    pdl_wait();
+    pdl_enter();
     const long long stride = (long long)cluster_size() * blockDim.x;  // a multiple of 8: lanes keep their group
     const long long t0 = (long long)cluster_rank() * blockDim.x + threadIdx.x;
     const unsigned gmask = 0xffu << (threadIdx.x & 24);
@@ -1611,7 +1631,7 @@ __device__ __forceinline__ void dwj_face_entry(const Lev &L, const T *__restrict
 template <class T, class TB, class IDX>
 __global__ void __launch_bounds__(256, 8) k_dwj_face(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                      T *__restrict__ t, Coef<T> K, T w) {
-    pdl_wait();
+    pdl_enter();
     const int c = blockIdx.z % 3, k = blockIdx.z / 3;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
@@ -1623,7 +1643,7 @@ __global__ void __launch_bounds__(256, 8) k_dwj_face(Lev L, const T *__restrict_
 // x_f += t_f on the face entries
 template <class T>
 __global__ void __launch_bounds__(256) k_add_faces(long long nf, T *__restrict__ x, const T *__restrict__ t) {
-    pdl_wait();
+    pdl_enter();
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += (long long)gridDim.x * blockDim.x)
         x[q] += t[q];
 }
@@ -1631,7 +1651,7 @@ __global__ void __launch_bounds__(256) k_add_faces(long long nf, T *__restrict__
 template <class T, class TB>
 __global__ void __launch_bounds__(256) k_dwj_pdelta(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                     T *__restrict__ delta, Coef<T> K, T dP) {
-    pdl_wait();
+    pdl_enter();
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     if (i >= L.nx || j >= L.ny || k >= L.nz) return;
     const long long cl = cell_lin(L, i, j, k);
@@ -1663,7 +1683,7 @@ __device__ __forceinline__ void dwj_dist_entry(const Lev &L, T *__restrict__ x, 
 template <class T>
 __global__ void __launch_bounds__(256, 8) k_dwj_pdist(Lev L, T *__restrict__ x, const T *__restrict__ delta, Coef<T> K,
                                                       T w) {
-    pdl_wait();
+    pdl_enter();
     const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
@@ -1684,7 +1704,7 @@ __device__ __forceinline__ void resid_entry(const Lev &L, const T *__restrict__ 
 template <class T, class TB>
 __global__ void __launch_bounds__(256, 8) k_resid_t(Lev L, const T *__restrict__ x, const TB *__restrict__ b,
                                                     T *__restrict__ r, Coef<T> K) {
-    pdl_wait();
+    pdl_enter();
     const int c = blockIdx.z & 3, k = blockIdx.z >> 2;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     switch (c) {
@@ -1698,7 +1718,7 @@ __global__ void __launch_bounds__(256, 8) k_resid_t(Lev L, const T *__restrict__
 template <class T>
 __global__ void __launch_bounds__(256) k_dwj_pleft(Lev L, T *__restrict__ x, const T *__restrict__ r, Coef<T> K, T w,
                                                    T dP) {
-    pdl_wait();
+    pdl_enter();
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     if (i >= L.nx || j >= L.ny || k >= L.nz || !in_v2_cell(L, i, j, k)) return;
     const long long nx = L.nx, ny = L.ny, sy = nx, sz = nx * ny;
@@ -1782,7 +1802,7 @@ __device__ __forceinline__ bool thread_entry_tile(const Lev &L, int gy, int kz, 
 template <class T, class TF, class TC, bool BATCH>
 __global__ void __launch_bounds__(256) k_restrict(Lev F, Lev C, int gy, int kz, const TF *__restrict__ rf,
                                                   TC *__restrict__ bc) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(C) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) rf = bslot(rf, F.bstride, zs.p);
     if constexpr (BATCH) bc = bslot(bc, C.bstride, zs.p);
@@ -1867,7 +1887,7 @@ __device__ __forceinline__ void prolong_comp(const Lev &F, const Lev &Cl, const 
 
 template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_prolong(Lev F, Lev Cl, int kz, const T *__restrict__ ec, T *__restrict__ xf) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(Cl) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) ec = bslot(ec, Cl.bstride, zs.p);
     if constexpr (BATCH) xf = bslot(xf, F.bstride, zs.p);
@@ -1911,7 +1931,7 @@ template <class T> void launch_prolong(const Lev &F, const Lev &C, const T *ec, 
 template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_coarse(const int *__restrict__ cidx, int nc, const double *__restrict__ kinv,
                                                 const T *__restrict__ b, T *__restrict__ x, long long bstride) {
-    pdl_wait();
+    pdl_enter();
     if constexpr (BATCH) b = bslot(b, bstride, (int)blockIdx.y);
     if constexpr (BATCH) x = bslot(x, bstride, (int)blockIdx.y);
     extern __shared__ double sb[];
@@ -1937,7 +1957,7 @@ void launch_coarse(const Lev &C, const int *cidx, int nc, const double *kinv, co
 
 // ------------------------------------------------------------------------------------------
 template <class T> __global__ void __launch_bounds__(256) k_mask(Lev L, int gy, T *__restrict__ x) {
-    pdl_wait();
+    pdl_enter();
     int c, i, j, k0, k1;
     if (!thread_entry(L, gy, c, i, j, k0, k1)) return;
     for (int k = k0; k < k1; ++k)
@@ -1952,7 +1972,7 @@ template void launch_mask<double>(const Lev &, double *, cudaStream_t);
 template void launch_mask<bf16>(const Lev &, bf16 *, cudaStream_t);
 
 template <class A, class B> __global__ void k_convert(long long n, const A *__restrict__ in, B *__restrict__ out) {
-    pdl_wait();
+    pdl_enter();
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         out[t] = cvt<B>(in[t]);
 }

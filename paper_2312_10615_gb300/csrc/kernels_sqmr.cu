@@ -52,7 +52,7 @@ int reduce_parts(const Lev &L) {
 template <bool RESIDUAL, bool BATCH>
 __global__ void __launch_bounds__(256) k_apply_red(Lev L, const double *__restrict__ x, const double *__restrict__ b,
                                                    double *__restrict__ w, double *partials, Coef<double> K) {
-    pdl_wait();
+    pdl_enter();
     const ZSlot zs = BATCH ? zslot(L) : ZSlot{0, (int)blockIdx.z};
     if constexpr (BATCH) x = bslot(x, L.bstride, zs.p);
     if constexpr (BATCH) b = bslot(b, L.bstride, zs.p);
@@ -107,7 +107,7 @@ int launch_residual_dot(const Lev &L, const double *b, const double *x, double *
 template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_dot2(long long n, const T *__restrict__ a, const double *__restrict__ b,
                                               double *partials, long long bs) {
-    pdl_wait();
+    pdl_enter();
     if constexpr (BATCH) a = bslot(a, bs, (int)blockIdx.y);
     if constexpr (BATCH) b = bslot(b, bs, (int)blockIdx.y);
     if constexpr (BATCH) partials = bslot(partials, bs, (int)blockIdx.y);
@@ -150,7 +150,7 @@ void launch_dot2(long long n, const T *a, const double *b, double *partials, cud
 template <bool BATCH>
 __global__ void __launch_bounds__(256) k_scalars(int stage, const double *partials, int nparts, SqmrState *st,
                                                  double *host_out, double aux, long long bs) {
-    pdl_wait();
+    pdl_enter();
     if constexpr (BATCH) partials = bslot(partials, bs, (int)blockIdx.x);
     if constexpr (BATCH) st = bslot(st, bs, (int)blockIdx.x);
     if constexpr (BATCH) {
@@ -246,7 +246,7 @@ void launch_scalars_aux(int stage, const double *partials, int nparts, SqmrState
 template <class T, bool BATCH>
 __global__ void __launch_bounds__(256) k_update_s(long long n, double *__restrict__ s, const double *__restrict__ w,
                                                   const SqmrState *__restrict__ st, T *__restrict__ bT, long long bs) {
-    pdl_wait();
+    pdl_enter();
     if constexpr (BATCH) s = bslot(s, bs, (int)blockIdx.y);
     if constexpr (BATCH) w = bslot(w, bs, (int)blockIdx.y);
     if constexpr (BATCH) st = bslot(st, bs, (int)blockIdx.y);
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256) k_update_rq(long long n, const double *__
                                                    const T *__restrict__ tv, double *__restrict__ r,
                                                    const double *__restrict__ sv, const SqmrState *__restrict__ st,
                                                    double *partials, long long bs) {
-    pdl_wait();
+    pdl_enter();
     const int p = (int)blockIdx.y;
     if constexpr (BATCH) qo = bslot(qo, bs, p);
     if constexpr (BATCH) qn = bslot(qn, bs, p);
@@ -305,7 +305,7 @@ template <bool BATCH>
 __global__ void __launch_bounds__(256) k_update_dx(long long n, double *__restrict__ x, double *__restrict__ d,
                                                    const double *__restrict__ qo, const SqmrState *__restrict__ st,
                                                    long long bs) {
-    pdl_wait();
+    pdl_enter();
     const int p = (int)blockIdx.y;
     if constexpr (BATCH) x = bslot(x, bs, p);
     if constexpr (BATCH) d = bslot(d, bs, p);
@@ -350,7 +350,7 @@ void launch_loop_check(const SqmrState *st, const LoopCtl *lc, cudaGraphConditio
 template <class T>
 __global__ void __launch_bounds__(256) k_init_q(long long n, const T *__restrict__ tv, double *__restrict__ q,
                                                 double *__restrict__ d) {
-    pdl_wait();
+    pdl_enter();
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         q[t] = (double)tv[t];
         d[t] = 0.0;
@@ -361,7 +361,7 @@ template <class T> void launch_init_q(long long n, const T *t, double *q, double
 }
 
 __global__ void __launch_bounds__(256) k_psum(Lev L, const double *__restrict__ x, double *partials) {
-    pdl_wait();
+    pdl_enter();
     double v[1] = {0.0};
     long long np = L.n - L.off[3];
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256) k_psum(Lev L, const double *__restrict__ 
     block_store<1>(v, partials, blockIdx.x);
 }
 __global__ void __launch_bounds__(256) k_psub(Lev L, double *__restrict__ x, const SqmrState *__restrict__ st) {
-    pdl_wait();
+    pdl_enter();
     double m = st->pmean;
     long long np = L.n - L.off[3];
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (long long)gridDim.x * blockDim.x)
@@ -397,7 +397,7 @@ template void launch_update_rq<double>(long long, const double *, double *, cons
 // x += t (the pure-multigrid update x_{k+1} = x_k + W^+ (b - L~ x_k), t in the V-cycle's precision)
 template <class T>
 __global__ void __launch_bounds__(256) k_add_to(long long n, const T *__restrict__ tv, double *__restrict__ x) {
-    pdl_wait();
+    pdl_enter();
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         x[t] += (double)tv[t];
 }

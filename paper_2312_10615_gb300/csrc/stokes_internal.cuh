@@ -36,6 +36,20 @@ __device__ __forceinline__ void pdl_wait() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #endif
 }
+// griddepcontrol.launch_dependents: the next kernel in the stream may be scheduled once every block of
+// this one has passed this point (or exited), so its blocks are resident and waiting in pdl_wait() when
+// this kernel's last blocks finish.  It orders nothing: the next kernel still sees this one's writes only
+// after its own pdl_wait(), which waits for this kernel's completion.
+__device__ __forceinline__ void pdl_trigger() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+#endif
+}
+// the solver kernels' entry: wait for the previous kernel, then let the next one be scheduled
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
 
 // set on a thread while it captures launches into a graph that must not carry programmatic edges
 inline thread_local bool t_plain_launches = false;
