@@ -303,21 +303,37 @@ template <class T, class TB> void launch_dgs_u(const Lev &L, T *x, const TB *b, 
 // ------------------------------------------------------------------------------------------
 // The velocity block of Alg. 2 / Eq. ldist, both parities in one pass, out of place (X read, Y
 // written).  Phase A relaxes the V2 faces of parity pa from X, phase B those of parity 1 - pa from
-// the phase-A values -- the two in-place launches of k_dgs_u, the same arithmetic per face.  Blocks
-// own a 32 x 8 tile of cell positions and march a chunk of FZ planes in z: at plane k they run phase A
-// on the tile and a one-position ring around it (recomputed by the neighbouring blocks too:
-// overlapped tiling, so no block waits for another), then phase B on the tile at plane k-1, whose six
-// neighbours' phase-A values (planes k-2..k) are then final.  X is staged in shared memory four
-// planes deep with a two-position halo, the phase-A values three planes deep with a one-position ring.
-// Every packed entry of a position is written to Y once: an updated face, or X's value.
-constexpr int FX = 32, FY = 8, FZ = 16;
-constexpr int WX = FX + 4, WY = FY + 4;  // X window: tile + 2-position halo
-constexpr int AX = FX + 2, AY = FY + 2;  // phase-A window: tile + 1-position ring
+// the phase-A values -- the two in-place launches of k_dgs_u, the same arithmetic per face.
+// A block is a window of FW x FH cell positions, one thread each, marching a chunk of planes in z;
+// it writes the entries of the inner FTX x FTY tile (a two-position halo on every side).  The planes
+// of X (u v w p) and of b stream into a ring of FNS shared-memory slots with asynchronous copies issued
+// FP planes ahead, so several planes of loads are in flight while the block computes.  At step k the
+// block relaxes phase A at plane k + 1 on the tile and a one-position ring (neighbours from the slots
+// of planes k, k + 1, k + 2), then phase B at plane k on the tile (in-plane phase-A neighbours from
+// shared memory, the z neighbours' phase-A values from the thread's own registers) and writes the
+// tile's entries of Y at plane k.  The ring's phase-A values are recomputed by the neighbouring blocks
+// too (overlapped tiling), so no block waits for another; one barrier per plane.  Every packed entry of
+// Y is written once: an updated face, or X's value.
+constexpr int FW = 32, FH = 16;            // window (threads) of one block
+constexpr int FTX = FW - 4, FTY = FH - 4;  // tile written by the block
+constexpr int FZMAX = 32;                  // planes per block at most
+constexpr int FP = 4;                      // planes copied ahead
+constexpr int FNS = FP + 2;                // plane slots: planes k - 1 .. k + FP are distinct
 
 template <class T> struct DgsFusedSmem {
-    T x[4][4][WY][WX];  // [plane slot][component u v w p][y][x]
-    T a[3][3][AY][AX];  // [plane slot][component u v w][y][x]
+    T x[FNS][4][FH][FW];  // [plane slot][component u v w p][y][x]
+    T b[FNS][3][FH][FW];  // [plane slot][component u v w][y][x]
+    T a[2][3][FH][FW];    // phase-A values: [plane slot][component u v w][y][x]
 };
+
+// asynchronous copy of one N-byte value into shared memory (zero-filled when !valid; nothing is read)
+template <int N> __device__ __forceinline__ void cp_async_n(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(N), "r"(valid ? N : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // is face (c; i, j, k) a V2 face (relaxed by the DGS)?  i, j, k inside the component's array
 __device__ __forceinline__ bool dgs_v2_face(const Lev &L, int c, int i, int j, int k, long long q) {
@@ -331,125 +347,108 @@ __device__ __forceinline__ bool dgs_v2_face(const Lev &L, int c, int i, int j, i
 }
 
 template <class T, class TB, class IDX>
-__global__ void __launch_bounds__(FX * FY, 3) k_dgs_u_fused(Lev L, const T *__restrict__ X, T *__restrict__ Y,
-                                                            const TB *__restrict__ b, int pa, Coef<T> K) {
+__global__ void __launch_bounds__(FW *FH, sizeof(T) == 4 ? 2 : 1)
+    k_dgs_u_fused(Lev L, const T *__restrict__ X, T *__restrict__ Y, const TB *__restrict__ b, int pa, int fz,
+                  Coef<T> K) {
     extern __shared__ __align__(16) unsigned char fsm[];
     DgsFusedSmem<T> &S = *reinterpret_cast<DgsFusedSmem<T> *>(fsm);
-    pdl_enter();
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY, k0 = blockIdx.z * FZ;
+    const int wx = threadIdx.x, wy = threadIdx.y;
+    const int gi = (int)blockIdx.x * FTX - 2 + wx, gj = (int)blockIdx.y * FTY - 2 + wy;
+    const int k0 = (int)blockIdx.z * fz, k1 = min(k0 + fz, L.nz + 1);  // phase B (and Y) at planes k0..k1-1
+    const bool ring = wx >= 1 && wx <= FW - 2 && wy >= 1 && wy <= FH - 2;  // phase A here
+    const bool tile = wx >= 2 && wx <= FW - 3 && wy >= 2 && wy <= FH - 3;  // phase B and Y here
     const IDX nx = (IDX)L.nx, ny = (IDX)L.ny;
-    // window positions this thread stages: (tx, ty), (tx + FX, ty), (tx, ty + FY), (tx + FX, ty + FY)
-    const bool hx = tx < WX - FX, hy = ty < WY - FY;
-    // packed offset of component C at cell position (i, j, k); in_arr: the entry exists
-    auto in_arr = [&](int c, int i, int j, int k) {
-        return i >= 0 && j >= 0 && k >= 0 && i < L.nx + (c == 0) && j < L.ny + (c == 1) && k < L.nz + (c == 2);
-    };
-    auto off = [&](int c, int i, int j, int k) -> IDX {
+    // this thread's column of each component: offset at plane 0, plane stride, planes, in the array
+    IDX cb[4], cz[4];
+    int ce[4];
+    bool cv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
         const IDX syc = c == 0 ? nx + 1 : nx;
-        const IDX szc = c == 0 ? (nx + 1) * ny : (c == 1 ? nx * (ny + 1) : nx * ny);
-        return (IDX)i + syc * (IDX)j + szc * (IDX)k;
-    };
+        cz[c] = c == 0 ? (nx + 1) * ny : (c == 1 ? nx * (ny + 1) : nx * ny);
+        cv[c] = gi >= 0 && gj >= 0 && gi < L.nx + (c == 0) && gj < L.ny + (c == 1);
+        cb[c] = cv[c] ? (IDX)gi + syc * (IDX)gj : (IDX)0;
+        ce[c] = L.nz + (c == 2);
+    }
     const T *Xc[4] = {X + L.off[0], X + L.off[1], X + L.off[2], X + L.off[3]};
     T *Yc[4] = {Y + L.off[0], Y + L.off[1], Y + L.off[2], Y + L.off[3]};
     const TB *Bc[3] = {b + L.off[0], b + L.off[1], b + L.off[2]};
-    // registers holding the next plane's window values while the current plane is computed
-    T pre[4][4];
-    auto fetch = [&](int gk) {
+    const int kb = k0 - 2;  // first plane staged; plane m lives in slot (m - kb) % FNS
+    // copy this thread's entries of plane m (X, and b where phase A or B may relax) into its slot
+    auto stage = [&](int m) {
+        const int sl = (m - kb) % FNS;
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int xx = tx + ((q & 1) ? FX : 0), yy = ty + ((q & 2) ? FY : 0);
-                const bool want = ((q & 1) ? hx : true) && ((q & 2) ? hy : true);
-                const int gi = i0 - 2 + xx, gj = j0 - 2 + yy;
-                pre[c][q] = (want && in_arr(c, gi, gj, gk)) ? Xc[c][off(c, gi, gj, gk)] : T(0);
-            }
-    };
-    auto store = [&](int gk) {
-        const int sl = (gk + 4) & 3;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int xx = tx + ((q & 1) ? FX : 0), yy = ty + ((q & 2) ? FY : 0);
-                const bool want = ((q & 1) ? hx : true) && ((q & 2) ? hy : true);
-                if (want) S.x[sl][c][yy][xx] = pre[c][q];
-            }
-    };
-    auto relax = [&](T x0, T nxm, T nxp, T nym, T nyp, T nzm, T nzp, T pc, T pm, T bv) {
-        return dgs_relax<T>(x0, nxm, nxp, nym, nyp, nzm, nzp, pc, pm, bv, K);
-    };
-    fetch(k0 - 2);
-    store(k0 - 2);
-    fetch(k0 - 1);
-    store(k0 - 1);
-    fetch(k0);
-    for (int st = 0; st <= FZ + 1; ++st) {
-        const int k = k0 - 1 + st;  // phase A at plane k, phase B at plane k - 1
-        store(k + 1);
-        __syncthreads();
-        if (st <= FZ) fetch(k + 2);  // in flight while this plane is computed
-        // phase A on tile + ring at plane k
-        {
-            const int xs = (k + 4) & 3, xm = (k + 3) & 3, xp = (k + 5) & 3, as = (k + 3) % 3;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int xx = tx + ((q & 1) ? FX : 0), yy = ty + ((q & 2) ? FY : 0);
-                if (xx >= AX || yy >= AY) continue;
-                const int gi = i0 - 1 + xx, gj = j0 - 1 + yy;
-                const int wx = xx + 1, wy = yy + 1;
-                const bool par = ((gi + gj + k) & 1) == pa;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    T v = S.x[xs][c][wy][wx];
-                    if (par && k >= 0 && in_arr(c, gi, gj, k)) {
-                        const IDX o = off(c, gi, gj, k);
-                        if (dgs_v2_face(L, c, gi, gj, k, L.off[c] + o)) {
-                            const T pm = c == 0 ? S.x[xs][3][wy][wx - 1]
-                                                : (c == 1 ? S.x[xs][3][wy - 1][wx] : S.x[xm][3][wy][wx]);
-                            v = relax(v, S.x[xs][c][wy][wx - 1], S.x[xs][c][wy][wx + 1], S.x[xs][c][wy - 1][wx],
-                                      S.x[xs][c][wy + 1][wx], S.x[xm][c][wy][wx], S.x[xp][c][wy][wx],
-                                      S.x[xs][3][wy][wx], pm, T(ldv(Bc[c][o])));
-                        }
-                    }
-                    S.a[as][c][yy][xx] = v;
-                }
-            }
+        for (int c = 0; c < 4; ++c) {
+            const bool in = cv[c] && m >= 0 && m < ce[c];
+            cp_async_n<sizeof(T)>(&S.x[sl][c][wy][wx], in ? Xc[c] + cb[c] + cz[c] * (IDX)m : Xc[c], in);
         }
-        __syncthreads();
-        // phase B on the tile at plane k - 1, and the tile's entries of Y at that plane
-        const int kb = k - 1;
-        if (kb >= k0 && kb < k0 + FZ && kb <= L.nz) {
-            const int gi = i0 + tx, gj = j0 + ty;
-            const int wx = tx + 2, wy = ty + 2, ax = tx + 1, ay = ty + 1;
-            const int xs = (kb + 4) & 3, xm = (kb + 3) & 3;
-            const int as = (kb + 3) % 3, am = (kb + 2) % 3, ap = (kb + 4) % 3;
-            const bool par_a = ((gi + gj + kb) & 1) == pa;
-            if (gi <= L.nx && gj <= L.ny) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (!in_arr(c, gi, gj, kb)) continue;
-                    const IDX o = off(c, gi, gj, kb);
-                    T v;
-                    if (par_a) {
-                        v = S.a[as][c][ay][ax];
-                    } else if (dgs_v2_face(L, c, gi, gj, kb, L.off[c] + o)) {
-                        const T pm = c == 0 ? S.x[xs][3][wy][wx - 1]
-                                            : (c == 1 ? S.x[xs][3][wy - 1][wx] : S.x[xm][3][wy][wx]);
-                        v = relax(S.x[xs][c][wy][wx], S.a[as][c][ay][ax - 1], S.a[as][c][ay][ax + 1],
-                                  S.a[as][c][ay - 1][ax], S.a[as][c][ay + 1][ax], S.a[am][c][ay][ax],
-                                  S.a[ap][c][ay][ax], S.x[xs][3][wy][wx], pm, T(ldv(Bc[c][o])));
-                    } else {
-                        v = S.x[xs][c][wy][wx];
-                    }
-                    Yc[c][o] = v;
-                }
-                if (in_arr(3, gi, gj, kb)) Yc[3][off(3, gi, gj, kb)] = S.x[xs][3][wy][wx];
-            }
+        for (int c = 0; c < 3; ++c) {
+            const bool in = ring && cv[c] && m >= 0 && m < ce[c];
+            if constexpr (sizeof(TB) == sizeof(T))
+                cp_async_n<sizeof(T)>(&S.b[sl][c][wy][wx], in ? (const void *)(Bc[c] + cb[c] + cz[c] * (IDX)m) : (const void *)Bc[c], in);
+            else
+                S.b[sl][c][wy][wx] = in ? T(ldv(Bc[c][cb[c] + cz[c] * (IDX)m])) : T(0);
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    pdl_enter();
+#pragma unroll 1
+    for (int m = kb; m < kb + FP; ++m) stage(m);
+    T pm1 = (cv[3] && kb - 1 >= 0) ? Xc[3][cb[3] + cz[3] * (IDX)(kb - 1)] : T(0);  // p at plane k - 1
+    T am[3] = {T(0), T(0), T(0)}, a0[3] = {T(0), T(0), T(0)};                      // phase A at k - 1, k
+#pragma unroll 1
+    for (int k = kb, it = 0; k < k1; ++k, ++it) {
+        stage(k + FP);
+        cp_async_wait<FP - 2>();  // planes up to k + 2 have landed (this thread's copies)
+        __syncthreads();          // ... and every thread's
+        const int s0 = it % FNS, s1 = (it + 1) % FNS, s2 = (it + 2) % FNS, a1s = (it + 1) & 1, a0s = it & 1;
+        // phase A at plane k + 1 (tile and ring)
+        const int kp = k + 1;
+        const bool parA = ((gi + gj + kp) & 1) == pa;
+        T an[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T v = S.x[s1][c][wy][wx];
+            if (ring && parA && cv[c] && kp >= 0 && kp < ce[c] &&
+                dgs_v2_face(L, c, gi, gj, kp, L.off[c] + cb[c] + cz[c] * (IDX)kp)) {
+                const T pmv = c == 0 ? S.x[s1][3][wy][wx - 1] : (c == 1 ? S.x[s1][3][wy - 1][wx] : S.x[s0][3][wy][wx]);
+                v = dgs_relax<T>(v, S.x[s1][c][wy][wx - 1], S.x[s1][c][wy][wx + 1], S.x[s1][c][wy - 1][wx],
+                                 S.x[s1][c][wy + 1][wx], S.x[s0][c][wy][wx], S.x[s2][c][wy][wx], S.x[s1][3][wy][wx],
+                                 pmv, S.b[s1][c][wy][wx], K);
+            }
+            an[c] = v;
+            S.a[a1s][c][wy][wx] = v;
+        }
+        // phase B at plane k (tile), from the phase-A values of planes k - 1, k, k + 1; Y at plane k
+        const T pc = S.x[s0][3][wy][wx];
+        if (tile && k >= k0) {
+            const bool parB = ((gi + gj + k) & 1) == pa;  // these faces keep their phase-A value
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!cv[c] || k >= ce[c]) continue;
+                const IDX o = cb[c] + cz[c] * (IDX)k;
+                const T x0 = S.x[s0][c][wy][wx];
+                T v = x0;
+                if (parB) {
+                    v = a0[c];
+                } else if (dgs_v2_face(L, c, gi, gj, k, L.off[c] + o)) {
+                    const T pmv = c == 0 ? S.x[s0][3][wy][wx - 1] : (c == 1 ? S.x[s0][3][wy - 1][wx] : pm1);
+                    v = dgs_relax<T>(x0, S.a[a0s][c][wy][wx - 1], S.a[a0s][c][wy][wx + 1], S.a[a0s][c][wy - 1][wx],
+                                     S.a[a0s][c][wy + 1][wx], am[c], an[c], pc, pmv, S.b[s0][c][wy][wx], K);
+                }
+                Yc[c][o] = v;
+            }
+            if (cv[3] && k < ce[3]) Yc[3][cb[3] + cz[3] * (IDX)k] = pc;
+        }
+        pm1 = pc;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            am[c] = a0[c];
+            a0[c] = an[c];
+        }
     }
+    cp_async_wait<0>();  // no copy outlives the block
 }
 
 template <class T, class TB> size_t dgs_u_fused_smem() { return sizeof(DgsFusedSmem<T>); }
@@ -464,12 +463,14 @@ template <class T, class TB> bool dgs_u_fused_prepare() {
 
 template <class T, class TB>
 void launch_dgs_u_fused(const Lev &L, const T *X, T *Y, const TB *b, int pa, cudaStream_t s) {
-    dim3 grid(cdiv(L.nx + 1, FX), cdiv(L.ny + 1, FY), cdiv(L.nz + 1, FZ));
+    // z chunks of at most FZMAX planes, as even as possible (every chunk re-reads two planes either side)
+    const int nch = cdiv(L.nz + 1, FZMAX), fz = cdiv(L.nz + 1, nch);
+    dim3 grid(cdiv(L.nx + 1, FTX), cdiv(L.ny + 1, FTY), cdiv(L.nz + 1, fz));
     if (idx32(L))
-        launch_k(k_dgs_u_fused<T, TB, int>, grid, dim3(FX, FY, 1), sizeof(DgsFusedSmem<T>), s, L, X, Y, b, pa,
+        launch_k(k_dgs_u_fused<T, TB, int>, grid, dim3(FW, FH, 1), sizeof(DgsFusedSmem<T>), s, L, X, Y, b, pa, fz,
                  coef<T>(L, L.gamma));
     else
-        launch_k(k_dgs_u_fused<T, TB, long long>, grid, dim3(FX, FY, 1), sizeof(DgsFusedSmem<T>), s, L, X, Y, b, pa,
+        launch_k(k_dgs_u_fused<T, TB, long long>, grid, dim3(FW, FH, 1), sizeof(DgsFusedSmem<T>), s, L, X, Y, b, pa, fz,
                  coef<T>(L, L.gamma));
 }
 
