@@ -847,6 +847,9 @@ def main():
                     help="JSON of per-level schedule choices (vanka, tiles, dgs_fused) to apply instead of the "
                          "autotuner's, e.g. profiles/schedule_solve256_fp32.json -- for profiler runs, whose "
                          "timings would steer the autotuner")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the SQMR loop from the host, one iteration graph at a time, instead of the device-side "
+                         "loop graph -- for profiler runs, which list the kernels of every iteration this way")
     args = ap.parse_args()
     if args.n is None:
         args.n = 128 if args.mode in ("cavity", "warmstart", "comparators") else 256
@@ -911,6 +914,8 @@ def main():
     S32 = smg.Stokes(n, precision=smg.PREC_FP32, autotune=not (args.no_autotune or args.schedule))
     if args.schedule:
         apply_schedule(smg, S32, json.load(open(args.schedule)))
+    if args.host_loop:
+        smg.stokes_set_device_loop(S32.h, False)
     for sd in sorted(set(seeds)):
         rhs[sd] = S32.rhs(synthetic.bumps(n, seed=sd, device=dev)["f"], None)
     x = torch.zeros(npk, dtype=torch.float64, device=dev)
