@@ -1257,6 +1257,8 @@ void launch_vanka_apply(const Lev &L, T *x, const int *cells, int ncell, const T
 // colour's patches).  So W is the post-colour state and no grid-wide order is needed inside the step.
 // Same-colour patches share no DOF and a DOF of the previous colour's patch shared with a colour-c
 // patch is written by the colour-c lane only, so every entry of W is written by at most one thread.
+// Lane a of slot s does both: DOF a of the s-th colour-c patch and DOF a of the s-th patch of the previous
+// colour, so a step has as many threads as the longer of the two cell lists.
 // Both copies agree on the ring of V2 DOFs the patches read (k_vanka_shell_copy at the start of each
 // sweep) and hold 0 off the unknowns.  An even number of steps (16 per symmetric sweep) returns the
 // state to the level's own vector.
@@ -1302,6 +1304,15 @@ __global__ void __launch_bounds__(256) k_vanka_step(Lev L, const T *__restrict__
                                                     const T *__restrict__ kinv, Coef<T> K) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int slot = t >> 3, a = t & 7;
+    // lane a of slot s also carries DOF a of the previous colour's s-th patch over from R, unless a colour-c
+    // patch writes it (static: which entry, and whether it is carried)
+    long long qc = 0;
+    bool carry = false;
+    if (slot < npcell && a != 7) {
+        const int pw = pcells[slot];
+        int dc;
+        carry = vanka_dof<T>(L, pw, a, qc, dc) && !(dc >= 0 && across_is_v1_of_colour(L, pw, a, colour));
+    }
     if (slot < ncell) {
         // the patch correction, as vanka_compute_lane, written as R + correction into W; the static part
         // (cell, configuration, inverse table entry, target entry) before the wait for the previous kernel
@@ -1312,6 +1323,7 @@ __global__ void __launch_bounds__(256) k_vanka_step(Lev L, const T *__restrict__
         int d;
         const bool wr = a < 7 && vanka_dof<T>(L, cellw, a, q, d);
         pdl_enter();
+        const T cval = carry ? R[qc] : T(0);
         T r = T(0);
         if (a == 6 || (a < 6 && ((v.cfg >> a) & 1))) r = vanka_residual_idx<T, TB, IDX>(L, R, b, a, v.i, v.j, v.k, K);
         const unsigned gmask = 0xffu << (threadIdx.x & 24);
@@ -1319,18 +1331,12 @@ __global__ void __launch_bounds__(256) k_vanka_step(Lev L, const T *__restrict__
 #pragma unroll
         for (int bb = 0; bb < 7; ++bb) sacc += v.Ki[bb] * __shfl_sync(gmask, r, bb, 8);
         if (wr) W[q] = R[q] + T(1) * sacc;
+        if (carry) W[qc] = cval;
         return;
     }
-    const int ps = slot - ncell;
-    if (ps >= npcell || a == 7) return;
-    // a DOF of the previous colour's patch: carry R's value over unless a colour-c patch writes it
-    const int cellw = pcells[ps];
-    long long q;
-    int d;
-    if (!vanka_dof<T>(L, cellw, a, q, d)) return;
-    if (d >= 0 && across_is_v1_of_colour(L, cellw, a, colour)) return;
+    if (!carry) return;
     pdl_enter();
-    W[q] = R[q];
+    W[qc] = R[qc];
 }
 
 // the second copy takes the level's current values on every DOF a Vanka patch reads or writes
@@ -1360,13 +1366,14 @@ void launch_vanka_pingpong(const Lev &L, T *x, T *x2, const TB *b, const VankaLi
             const int nc = lists.count[c];
             const int np = (prev >= 0 && prev != c) ? lists.count[prev] : 0;
             const int *pc = prev >= 0 ? lists.cells[prev] : nullptr;
-            if (nc + np > 0) {
+            const int ns = nc > np ? nc : np;  // slot s: patch s of colour c and patch s of the previous colour
+            if (ns > 0) {
                 if (idx32(L))
-                    launch_k(k_vanka_step<T, TB, int>, dim3(cdiv(8LL * (nc + np), 256)), dim3(256), 0, s, L, R, W, b,
+                    launch_k(k_vanka_step<T, TB, int>, dim3(cdiv(8LL * ns, 256)), dim3(256), 0, s, L, R, W, b,
                              lists.cells[c], lists.tab[c], nc, pc, np, c, kinv, K);
                 else
-                    launch_k(k_vanka_step<T, TB, long long>, dim3(cdiv(8LL * (nc + np), 256)), dim3(256), 0, s, L, R,
-                             W, b, lists.cells[c], lists.tab[c], nc, pc, np, c, kinv, K);
+                    launch_k(k_vanka_step<T, TB, long long>, dim3(cdiv(8LL * ns, 256)), dim3(256), 0, s, L, R, W, b,
+                             lists.cells[c], lists.tab[c], nc, pc, np, c, kinv, K);
             }
             prev = c;
         }
