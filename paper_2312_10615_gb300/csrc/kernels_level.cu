@@ -38,14 +38,6 @@ inline Geo geo_components(const Lev &L, int ncomp) {
 
 // V2 index ranges of the box problem: faces of component c with normal index in [2, n-2] and
 // tangential indices in [1, n-2]; cells with every index in [1, n-2].
-__host__ __device__ inline void v2_face_range(const Lev &L, int c, int lo[3], int cnt[3]) {
-    int n[3] = {L.nx, L.ny, L.nz};
-    for (int d = 0; d < 3; ++d) {
-        lo[d] = d == c ? 2 : 1;
-        cnt[d] = d == c ? n[d] - 3 : n[d] - 2;
-        if (cnt[d] < 0) cnt[d] = 0;
-    }
-}
 // cells of colour (bx, by, bz) inside the V2 cell range [1, n-2]
 __host__ __device__ inline void v2_colour_range(const Lev &L, int colour, int lo[3], int cnt[3]) {
     int n[3] = {L.nx, L.ny, L.nz};
