@@ -264,7 +264,9 @@ __device__ __forceinline__ Quad quad_at(const Lev &L, int i, int j, int k) {
     return Q;
 }
 // values of the four operator rows at (i,j,k) (0 for entries that are not unknowns); x holds 0
-// off the unknowns
+// off the unknowns.  A face row is formed as (w eta/h^2) x_f - (eta/h^2) (sum of its six neighbours),
+// w = 6 on the box: one FP64 operation fewer per face than eta/h^2 (w x_f - neighbours), and the FP64
+// operator apply is bound by the FP64 issue rate on this GPU
 // LAB = true: a label domain (L.flags set), whose faces next to exterior cells drop viscous terms
 template <class T, int OP, bool LAB = false>
 __device__ __forceinline__ void quad_eval(const T *__restrict__ x, const Lev &L, int i, int j, int k, const Quad &Q,
@@ -286,25 +288,25 @@ __device__ __forceinline__ void quad_eval(const T *__restrict__ x, const Lev &L,
     if (Q.act[0]) {
         const T *u = x + Q.q[0];
         const T ul = (f0 & kFlagDropLo) ? T(0) : u[-1], uh = (f0 & kFlagDropHi) ? T(0) : u[1];
-        T s = (LAB ? diag_weight<T>(f0) : T(6)) * u[0] - ul - uh - (gym ? u[-uy] : T(0)) - (gyp ? u[uy] : T(0)) -
-              (gzm ? u[-uz] : T(0)) - (gzp ? u[uz] : T(0));
-        out[0] = K.eh2 * s;
+        const T ns = ((ul + uh) + ((gym ? u[-uy] : T(0)) + (gyp ? u[uy] : T(0)))) +
+                     ((gzm ? u[-uz] : T(0)) + (gzp ? u[uz] : T(0)));
+        out[0] = ((LAB ? diag_weight<T>(f0) : T(6)) * K.eh2) * u[0] - K.eh2 * ns;
         if (OP == OP_APPLY) out[0] += K.ih * (pc - x[Q.q[3] - 1]);
     }
     if (Q.act[1]) {
         const T *v = x + Q.q[1];
         const T vl = (f1 & kFlagDropLo) ? T(0) : v[-vy], vh = (f1 & kFlagDropHi) ? T(0) : v[vy];
-        T s = (LAB ? diag_weight<T>(f1) : T(6)) * v[0] - (gxm ? v[-1] : T(0)) - (gxp ? v[1] : T(0)) - vl - vh -
-              (gzm ? v[-vz] : T(0)) - (gzp ? v[vz] : T(0));
-        out[1] = K.eh2 * s;
+        const T ns = (((gxm ? v[-1] : T(0)) + (gxp ? v[1] : T(0))) + (vl + vh)) +
+                     ((gzm ? v[-vz] : T(0)) + (gzp ? v[vz] : T(0)));
+        out[1] = ((LAB ? diag_weight<T>(f1) : T(6)) * K.eh2) * v[0] - K.eh2 * ns;
         if (OP == OP_APPLY) out[1] += K.ih * (pc - x[Q.q[3] - py]);
     }
     if (Q.act[2]) {
         const T *w = x + Q.q[2];
         const T wl = (f2 & kFlagDropLo) ? T(0) : w[-wz], wh = (f2 & kFlagDropHi) ? T(0) : w[wz];
-        T s = (LAB ? diag_weight<T>(f2) : T(6)) * w[0] - (gxm ? w[-1] : T(0)) - (gxp ? w[1] : T(0)) - (gym ? w[-wy] : T(0)) -
-              (gyp ? w[wy] : T(0)) - wl - wh;
-        out[2] = K.eh2 * s;
+        const T ns = (((gxm ? w[-1] : T(0)) + (gxp ? w[1] : T(0))) + ((gym ? w[-wy] : T(0)) + (gyp ? w[wy] : T(0)))) +
+                     (wl + wh);
+        out[2] = ((LAB ? diag_weight<T>(f2) : T(6)) * K.eh2) * w[0] - K.eh2 * ns;
         if (OP == OP_APPLY) out[2] += K.ih * (pc - x[Q.q[3] - pz]);
     }
     if (Q.act[3]) {
