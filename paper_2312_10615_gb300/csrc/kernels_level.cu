@@ -339,7 +339,7 @@ __device__ __forceinline__ bool dgs_v2_face(const Lev &L, int c, int i, int j, i
 }
 
 template <class T, class TB, class IDX>
-__global__ void __launch_bounds__(FW *FH, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(FW * FH, sizeof(T) == 4 ? 2 : 1)
     k_dgs_u_fused(Lev L, const T *__restrict__ X, T *__restrict__ Y, const TB *__restrict__ b, int pa, int fz,
                   Coef<T> K) {
     extern __shared__ __align__(16) unsigned char fsm[];
